@@ -1,0 +1,151 @@
+"""Seeded synthetic convolutional-sparse-coding problems.
+
+This module only draws inputs: a dictionary D[K,P,L], a sparse activation
+signal Z[K,T-L+1] and an observed signal X[P,T] built with the generative
+model of Sec. 2.1 (Eq. model): X = sum_k Z_k * D_k + noise.  It contains none
+of the solver's arithmetic (no correlation with D, no coordinate update, no
+objective); the CPU oracle, the CUDA path, the tests and the benchmark all
+take their inputs from here and compute everything else on their own.
+
+Random numbers come from a counter-based generator (SplitMix64, Steele,
+Lea & Flood, OOPSLA 2014) so that the same seed gives the same arrays on
+every machine and numpy version: uniforms are exact functions of
+(seed, stream, index); normals use the Box-Muller transform.
+
+Recipe (Sec. 4, "Long convolutional Sparse Coding Signals"): every entry of D
+is N(0,1) and each atom D_k (over its P x L entries) is rescaled to unit
+l2 norm; Z_k[t] = Bernoulli(rho) * N(0, sigma_z^2); the noise is white
+N(0, sigma^2).  Arrays are stored as float32.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def _mix64(x: np.ndarray) -> np.ndarray:
+    """SplitMix64 output function (bijective 64-bit finaliser)."""
+    x = x.copy()
+    x ^= x >> np.uint64(30)
+    x *= _M1
+    x ^= x >> np.uint64(27)
+    x *= _M2
+    x ^= x >> np.uint64(31)
+    return x
+
+
+def _bits(seed: int, stream: int, n: int) -> np.ndarray:
+    """n 64-bit words: SplitMix64 state seed' + (i+1)*golden, i = 0..n-1."""
+    with np.errstate(over="ignore"):
+        key = _mix64(np.array([(seed * 0x100000001B3 + stream * 0x632BE59BD9B4E019)
+                               & 0xFFFFFFFFFFFFFFFF], dtype=np.uint64))[0]
+        ctr = np.arange(1, n + 1, dtype=np.uint64)
+        return _mix64(key + ctr * _GOLDEN)
+
+
+def uniform(seed: int, stream: int, n: int) -> np.ndarray:
+    """n float64 uniforms in the open interval (0, 1)."""
+    b = _bits(seed, stream, n) >> np.uint64(11)
+    return (b.astype(np.float64) + 0.5) * (1.0 / 9007199254740992.0)
+
+
+def normal(seed: int, stream: int, n: int) -> np.ndarray:
+    """n float64 standard normals (Box-Muller on two uniform streams)."""
+    u1 = uniform(seed, 2 * stream, n)
+    u2 = uniform(seed, 2 * stream + 1, n)
+    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+
+
+@dataclasses.dataclass
+class Problem:
+    """One synthetic problem. D[K,P,L], Z_true[K,Tz], X[P,T], all float32."""
+    D: np.ndarray
+    Z_true: np.ndarray
+    X: np.ndarray
+    seed: int
+    rho: float
+    sigma: float
+
+    @property
+    def K(self) -> int:
+        return self.D.shape[0]
+
+    @property
+    def P(self) -> int:
+        return self.D.shape[1]
+
+    @property
+    def L(self) -> int:
+        return self.D.shape[2]
+
+    @property
+    def T(self) -> int:
+        return self.X.shape[1]
+
+    @property
+    def Tz(self) -> int:
+        return self.T - self.L + 1
+
+
+def make_dictionary(K: int, P: int, L: int, seed: int) -> np.ndarray:
+    """K unit-norm Gaussian atoms of shape [P, L] (float32)."""
+    D = normal(seed, 1, K * P * L).reshape(K, P, L)
+    D /= np.sqrt((D * D).sum(axis=(1, 2), keepdims=True))
+    return D.astype(np.float32)
+
+
+def make_problem(K: int, P: int, L: int, T: int, rho: float, sigma: float,
+                 seed: int, sigma_z: float = 1.0, D: np.ndarray | None = None) -> Problem:
+    """Draw D (unless given), a Bernoulli-Gaussian Z and X = sum_k Z_k*D_k + noise.
+
+    The model sum is accumulated in float64 from the float32 dictionary and
+    the float32 activations, then rounded once to float32.
+    """
+    if T < L:
+        raise ValueError("T must be >= L")
+    if D is None:
+        D = make_dictionary(K, P, L, seed)
+    D = np.ascontiguousarray(D, dtype=np.float32)
+    K, P, L = D.shape
+    Tz = T - L + 1
+    mask = uniform(seed, 3, K * Tz) < rho
+    amp = normal(seed, 4, K * Tz) * sigma_z
+    Z = np.where(mask, amp, 0.0).reshape(K, Tz).astype(np.float32)
+
+    X = np.zeros((P, T), dtype=np.float64)
+    ks, ts = np.nonzero(Z)
+    if ks.size:
+        zv = Z[ks, ts].astype(np.float64)
+        idx = (ts[:, None] + np.arange(L)[None, :]).ravel()
+        for p in range(P):
+            w = (zv[:, None] * D[ks, p, :].astype(np.float64)).ravel()
+            X[p] += np.bincount(idx, weights=w, minlength=T)
+    X += sigma * normal(seed, 5, P * T).reshape(P, T)
+    return Problem(D=D, Z_true=Z, X=X.astype(np.float32), seed=seed, rho=rho, sigma=sigma)
+
+
+# Workloads, named by what they are (shapes from the paper's Sec. 4 setting,
+# scaled as stated).  "segments" lists the segment counts M exercised.
+WORKLOADS = {
+    # short single-channel signal: greedy CD and locally greedy CD, 10 segments
+    "short_P1_K5_L16_T2000": dict(P=1, K=5, L=16, T=2000, rho=0.01, sigma=0.01,
+                                  segments=(1, 10), tol=1e-6),
+    # single long multichannel signal
+    "long_P7_K25_L64_T200000": dict(P=7, K=25, L=64, T=200_000, rho=0.005, sigma=0.1,
+                                    segments=(64, 256, 1024, 3072), tol=1e-6),
+    # very long single-channel recording (about 1.4 h at 1 kHz)
+    "verylong_P1_K25_L200_T5000000": dict(P=1, K=25, L=200, T=5_000_000, rho=0.002,
+                                          sigma=0.1, segments=(12_500,), tol=1e-6),
+}
+
+
+def make_workload(name: str, seed: int = 0, T: int | None = None) -> Problem:
+    """Problem for a named workload; T may be overridden for reduced-size cases."""
+    w = WORKLOADS[name]
+    return make_problem(K=w["K"], P=w["P"], L=w["L"], T=T if T is not None else w["T"],
+                        rho=w["rho"], sigma=w["sigma"], seed=seed)
