@@ -1,0 +1,362 @@
+#!/usr/bin/env python3
+"""Benchmark: segmented locally greedy convolutional coordinate descent on GB300.
+
+Workload (the long-signal setting of Sec. 4, at the sizes this project
+targets): one multichannel signal, P = 7 channels, K = 25 unit-norm Gaussian
+atoms of length L = 64, T = 200,000 samples, Bernoulli(0.005)-Gaussian
+activations, noise sigma = 0.1, lambda = 0.1 lambda_max, stopping rule
+max |Delta Z| < 1e-6 followed by the FP64 beta re-synchronisation.  Inputs
+are synthetic and seeded (rank r solves seed r: weak scaling, no collective
+on the data path).
+
+One step = csc_setup (DtD, norms) + csc_init (beta = D~*X) + csc_solve (phase
+schedule to convergence, FP64 resync, FP64 objective), inputs resident in
+HBM.  The problem state (about 60 MB) fits in L2, so L2 is flushed (a 256 MB
+write) between timed steps, outside the timed intervals.
+
+Printed: one JSON line.  value = applied coordinate updates per second of
+whole step time (summed over ranks / max over ranks of the time).
+time_to_gap_ms is the time from the step start until the objective is within
+a relative 1e-4 of the optimum E* stored in tests/golden/optimum.json (written
+by the FP64 oracle).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to 1e-4 objective gap & CD updates/s vs plain GPU; serve p50/p99 ms"
+WORKLOAD = "long_P7_K25_L64_T200000"
+GOLDEN = os.path.join(ROOT, "tests", "golden", "optimum.json")
+HBM_FALLBACK_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--segments", type=int, default=1024)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def golden(seed: int):
+    try:
+        with open(GOLDEN) as f:
+            return json.load(f).get(f"{WORKLOAD}/seed{seed}")
+    except OSError:
+        return None
+
+
+def input_hash(pb) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    h.update(pb.D.tobytes())
+    h.update(pb.X.tobytes())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "200"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def time_to_gap_ms(trace, init_ms, E_star, rel=1e-4):
+    E = trace["E_start"] - np.cumsum(trace["decrease"])
+    ok = np.nonzero((E - E_star) <= rel * E_star)[0]
+    if ok.size == 0:
+        return None
+    # first launch reaching the gap; launches without updates carry no time stamp
+    t = trace["t_ns"][: ok[0] + 1]
+    t = t[t >= 0]
+    return init_ms + (float(t[-1]) / 1e6 if t.size else 0.0)
+
+
+def cpu_baseline(pb, lam, tol, M):
+    """The FP64 oracle as it stands (single thread), on the full problem."""
+    import oracle
+    t = time.perf_counter()
+    r = oracle.locally_greedy_cd(pb.D, pb.X, lam, tol, M=M, mode="phase")
+    dt = time.perf_counter() - t
+    return {"value": r["n_updates"] / dt, "unit": "updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"full solve (DtD, D~*X, phase-schedule CD to max|dZ|<{tol:g}) of seed 0, "
+                      f"M={M}: {r['n_updates']} updates in {dt:.2f} s"}
+
+
+def run_reference(args):
+    """CPU oracle arm: rank 0 only; each step is the oracle's solve of seed 0,
+    bounded to 30,000 updates so that warmup + steps stay within minutes."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    from paper_1705_10087_gb300 import synth
+    import oracle
+    pb = synth.make_workload(WORKLOAD, seed=0)
+    g = golden(0)
+    lam = g["lambda"] if g else 0.1 * oracle.lambda_max(pb.D, pb.X)
+    cap = 30_000
+    times, ups = [], []
+    for i in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        r = oracle.locally_greedy_cd(pb.D, pb.X, lam, args.tol, M=args.segments, mode="phase",
+                                     max_updates=cap)
+        dt = time.perf_counter() - t
+        if i >= args.warmup:
+            times.append(dt)
+            ups.append(r["n_updates"])
+    v = sum(ups) / sum(times)
+    sample = (f"per step: oracle setup + D~*X + first {cap} updates of the phase-schedule "
+              f"solve (M={args.segments}) of seed 0, 1 thread")
+    print(json.dumps({
+        "metric": METRIC, "value": v, "unit": "updates/s", "impl": "reference",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "P": 7, "K": 25, "L": 64, "T": 200_000,
+                   "segments": args.segments, "tol": args.tol},
+        "cpu_baseline": {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (the solver has no CPU path)")
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1705_10087_gb300 import build, capi, synth
+    build.build()
+    capi.load()
+
+    pb = synth.make_workload(WORKLOAD, seed=rank)
+    g = golden(rank)
+    if g is not None and g.get("input_sha256_16") != input_hash(pb):
+        g = None  # generator does not reproduce the stored inputs on this machine
+    stream = torch.cuda.current_stream()
+    D = torch.from_numpy(pb.D).cuda()
+    X = torch.from_numpy(pb.X).cuda()
+    Z = torch.zeros((pb.K, pb.Tz), dtype=torch.float32, device="cuda")
+    opts = capi.make_opts(segments=args.segments, time_kernels=1)
+    h = capi.csc_setup(D, opts)
+    if g is not None:
+        lam = g["lambda"]
+    else:
+        capi.csc_init(h, X, 1.0)
+        lam = 0.1 * capi.csc_lambda_max(h)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step(ev):
+        ev[0].record(stream)
+        capi.csc_setup(D, opts, handle=h)
+        capi.csc_init(h, X, lam)
+        ev[1].record(stream)
+        status, E, st = capi.csc_solve(h, args.tol, 1 << 40, Z)
+        ev[2].record(stream)
+        if status != capi.CSC_OK:
+            raise RuntimeError(f"solve did not converge: {st}")
+        return E, st
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)]
+           for _ in range(args.warmup + args.steps)]
+    for i in range(args.warmup):
+        step(evs[i])
+        flush.zero_()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    phys = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
+    gpu_index = int(phys[local]) if phys and phys[0] not in ("",) and phys[local].isdigit() else local
+    launches0 = capi.csc_kernel_launches(h)
+    sts, Es = [], []
+    with ClockSampler(gpu_index) as clk:
+        for i in range(args.warmup, args.warmup + args.steps):
+            E, st = step(evs[i])
+            sts.append(st)
+            Es.append(E)
+            flush.zero_()
+        torch.cuda.synchronize()
+    launches = capi.csc_kernel_launches(h) - launches0
+    trace = capi.csc_get_trace(h)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    step_ms = [evs[i][0].elapsed_time(evs[i][2]) for i in range(args.warmup, args.warmup + args.steps)]
+    init_ms = [evs[i][0].elapsed_time(evs[i][1]) for i in range(args.warmup, args.warmup + args.steps)]
+    tot_ms = sum(step_ms)
+    updates = sum(s["updates"] for s in sts)
+    phase_ms = sum(s["phase_ms"] for s in sts)
+    phase_launches = sum(s["phase_launches"] for s in sts)
+    visits = sum(s["visits"] for s in sts)
+
+    # algorithmic bytes of the phase kernel: per visit the segment's beta window
+    # and Z in and out (16 K (w + 2L - 2)), per update one DtD column (4 K (2L-1))
+    K, L = pb.K, pb.L
+    w = pb.Tz / args.segments
+    alg_bytes = visits * 16.0 * K * (w + 2 * L - 2) + updates * 4.0 * K * (2 * L - 1)
+    achieved = alg_bytes / (phase_ms * 1e-3) / 1e9 if phase_ms > 0 else None
+    peak, peak_kind = peaks()
+
+    if world > 1:
+        t = torch.tensor([tot_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        u = torch.tensor([updates], dtype=torch.float64, device="cuda")
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        tot_ms_max, updates_all = float(t.item()), float(u.item())
+    else:
+        tot_ms_max, updates_all = tot_ms, float(updates)
+
+    ttg = time_to_gap_ms(trace, init_ms[-1], g["E_star"]) if g else None
+
+    # end to end through the public API with host buffers (pinned), copies inside
+    Dh = torch.from_numpy(pb.D).pin_memory()
+    Xh = torch.from_numpy(pb.X).pin_memory()
+    Zh = torch.zeros((pb.K, pb.Tz), dtype=torch.float32).pin_memory()
+    e2e_t, e2e_u = 0.0, 0
+    for i in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        capi.csc_setup(Dh, opts, handle=h)
+        capi.csc_init(h, Xh, lam)
+        status, E, st = capi.csc_solve(h, args.tol, 1 << 40, Zh)
+        e2e_t += time.perf_counter() - t0
+        e2e_u += st["updates"]
+    capi.csc_destroy(h)
+    if world > 1:
+        t = torch.tensor([e2e_t], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        u = torch.tensor([e2e_u], dtype=torch.float64, device="cuda")
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        e2e_value = float(u.item()) / float(t.item())
+    else:
+        e2e_value = e2e_u / e2e_t
+
+    if rank != 0:
+        dist.destroy_process_group() if world > 1 else None
+        return
+    line = {
+        "metric": METRIC, "value": updates_all / (tot_ms_max * 1e-3), "unit": "updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tot_ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "P": 7, "K": 25, "L": 64, "T": 200_000,
+                   "segments": args.segments, "phases": sts[-1]["phases"], "tol": args.tol,
+                   "lambda": "0.1*lambda_max", "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"replicas x{world}, one signal per GPU"},
+        "time_to_gap_ms": ttg,
+        "init_ms": statistics.mean(init_ms),
+        "solve_ms": statistics.mean(s["solve_ms"] for s in sts),
+        "updates_per_step": updates / args.steps,
+        "sweeps": sts[-1]["sweeps"], "resyncs": sts[-1]["resyncs"],
+        "rel_gap_final": (Es[-1] - g["E_star"]) / g["E_star"] if g else None,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak if achieved else None, "traffic": None,
+                     "kernel": "phase_kernel", "peak_kind": peak_kind,
+                     "avg_launch_us": 1e3 * phase_ms / phase_launches if phase_launches else None,
+                     "launches": phase_launches},
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_value, "unit": "updates/s",
+                "h2d_bytes_per_step": int(pb.D.nbytes + pb.X.nbytes),
+                "d2h_bytes_per_step": int(pb.K * pb.Tz * 4 + 8)},
+        "clocks": clk.summary(),
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(pb, lam, args.tol, args.segments)
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

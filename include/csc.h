@@ -1,0 +1,191 @@
+/*
+ * csc.h - C ABI of the GB300 convolutional sparse coding solver.
+ *
+ * Problem (Eq. sparse_code, Sec. 2.1 of Moreau, Oudre & Vayatis, "DICOD",
+ * ICML 2018): given atoms D[K][P][L] and a signal X[P][T], find
+ *     Z* = argmin_Z  1/2 || X - sum_k Z_k * D_k ||_2^2 + lambda sum_k ||Z_k||_1,
+ * with Z[K][Tz], Tz = T - L + 1 ("valid" placement: atom k at offset t covers
+ * samples t..t+L-1 of X; X is zero outside [0,T), Sec. 2 "Notations").
+ * The paper writes W for the atom length and L for Tz.
+ *
+ * Method: locally greedy coordinate descent on M contiguous time segments
+ * (Sec. 2.2 DICOD, Alg. 2; Sec. 2.3 Alg. 3).  Each GPU thread block owns one
+ * segment, picks argmax |Delta Z| inside it, applies Eq. pb_coord and updates
+ * beta by Eq. beta_up on the window [t0-L+1, t0+L-1], writing directly into
+ * idle neighbouring segments (the paper's neighbour messages).  Segments run
+ * in c phases (segments m == p mod c together); c is chosen so that no two
+ * co-active segments touch the same beta entries, which makes every phase
+ * equivalent to a sequential run of its segments (hypothesis H2 of Theorem
+ * conv_dcp holds with A = c phases; H3 is not needed).
+ *
+ * Layouts (all row-major, float32 unless stated):
+ *   D      [K][P][L]        atom k, channel p, lag tau
+ *   X      [P][T]
+ *   Z      [K][Tz]
+ *   beta   [K][Tz]
+ *   DtD    [K][K][2L-1]     DtD[k0][k][s] = sum_p sum_tau D[k][p][tau] D[k0][p][tau+s-(L-1)]
+ *                           (= S_{k,k0}[s-(L-1)] of Eq. beta_up; the slice for one
+ *                           updated atom k0 is contiguous)
+ *
+ * Pointers: every array argument may be a device pointer (cudaMalloc, torch)
+ * or a host pointer (pageable or pinned); the library detects which with
+ * cudaPointerGetAttributes and copies host data itself.  The caller keeps
+ * ownership of every array it passes; the library copies what it keeps.
+ *
+ * Errors: every entry point returns an int status.  CSC_OK (0) is success;
+ * CSC_NOT_CONVERGED (1) means max_updates or the sweep limit was reached
+ * (Z and the objective are still valid).  Negative values are errors; the
+ * text of the last error of the calling thread is csc_last_error_string().
+ * No C++ exception crosses this boundary.
+ *
+ * Threads and streams: a handle is used by one host thread at a time; all of
+ * its GPU work is ordered on the stream given to csc_setup.  Calls that read
+ * results back (csc_solve, the getters) synchronise that stream.
+ */
+#ifndef CSC_H
+#define CSC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CSC_OK 0
+#define CSC_NOT_CONVERGED 1
+#define CSC_EINVAL (-1)   /* bad argument: sizes, lambda, tol, null pointer */
+#define CSC_ENOMEM (-2)   /* device or host allocation failed */
+#define CSC_ECUDA (-3)    /* a CUDA call or kernel failed */
+#define CSC_ETIMEOUT (-4) /* a bounded device wait gave up */
+#define CSC_ESTATE (-5)   /* call out of order (e.g. csc_solve before csc_init) */
+
+typedef struct csc_handle_s *csc_handle_t;
+
+typedef struct csc_opts {
+    int32_t segments;          /* M >= 1; 0 = automatic (width about 2L-2) */
+    int32_t updates_per_visit; /* u: updates a segment may apply per phase; 0 = until local
+                                  convergence (bounded internally by 2^20) */
+    int32_t max_resyncs;       /* FP64 beta re-synchronisations after the FP32 loop settles;
+                                  CD resumes after a resync that finds |Delta Z| >= tol.
+                                  -1 = default (3); 0 = none */
+    int32_t sweeps_per_poll;   /* sweeps enqueued between two host convergence polls;
+                                  0 = default (4) */
+    int32_t max_sweeps;        /* 0 = default (1,000,000) */
+    int32_t time_kernels;      /* 1 = time every phase launch with a CUDA event pair
+                                  (csc_stats.phase_ms); 0 = off */
+    int32_t reserved[2];       /* must be zero */
+} csc_opts;
+
+typedef struct csc_stats {
+    int64_t updates;          /* applied coordinate updates (each with |Delta Z| >= tol) */
+    int64_t sweeps;           /* full sweeps (c phases) launched */
+    int32_t segments;         /* M used */
+    int32_t phases;           /* c used */
+    int32_t resyncs;          /* FP64 re-synchronisations performed */
+    int32_t converged;        /* 1 if stopped because a sweep applied no update */
+    double objective;         /* E(Z) in FP64 from the explicit residual */
+    double max_drift;         /* max |beta_fp32 - beta_fp64| seen at a resync */
+    double kkt_zero_excess;   /* max over Z == 0 of |beta| - lambda (FP64 beta) */
+    double kkt_nonzero_gap;   /* max over Z != 0 of |Z - Sh(beta,lambda)/n| (FP64 beta) */
+    double max_delta_z;       /* max over all coordinates of |Z - Sh(beta,lambda)/n| */
+    double solve_ms;          /* device time from the first phase to the last resync */
+    double phase_ms;          /* summed duration of the phase launches (time_kernels = 1) */
+    int64_t phase_launches;   /* phase-kernel launches issued */
+    int64_t visits;           /* segment visits that applied at least one update */
+    int64_t kernel_launches;  /* all kernels this call launched */
+} csc_stats;
+
+/* Fill *o with the defaults (all zero / -1 as documented above). */
+void csc_default_opts(csc_opts *o);
+
+/*
+ * Step a1 (constants of Sec. 4 "computations for constants"; S of Eq. beta_up).
+ * Creates a handle (if *h == NULL) or re-uses *h, copies D, and computes
+ * DtD[K][K][2L-1] and the atom norms ||D_k||^2 (Eq. pb_coord) on the GPU.
+ *   D       [K][P][L] float32, host or device, caller-owned, read only
+ *   K,P,L   K >= 1, P >= 1, 1 <= L <= 512
+ *   opts    NULL for defaults
+ *   stream  cudaStream_t (NULL = legacy default stream)
+ * Re-using a handle invalidates any previous csc_init.
+ */
+int csc_setup(csc_handle_t *h, const float *D, int K, int P, int L, const csc_opts *opts,
+              void *stream);
+
+/*
+ * Step a2 (Alg. 1 initialisation; Alg. 2/3 "initialize beta and Z").
+ * Copies X, sets Z = Z0 (or 0) and computes beta = D~ * X (FP32 with
+ * compensated summation) and, for a warm start, subtracts the contribution of
+ * Z0 in FP64.  Also records lambda_max = max |D~ * X|.
+ *   X       [P][T] float32, host or device, caller-owned; T >= L and
+ *           K*(T-L+1) < 2^32 - 1 (flat coordinate indices are 32-bit)
+ *   lambda  > 0, absolute (not scaled)
+ *   Z0      NULL (cold start) or [K][T-L+1] float32 warm start
+ */
+int csc_init(csc_handle_t h, const float *X, int64_t T, double lambda, const float *Z0);
+
+/*
+ * Steps a3-a7: phase-scheduled locally greedy CD until a full sweep applies
+ * no update with |Delta Z| >= tol, then an FP64 resync of beta and a final
+ * FP64 objective / optimality check.  A coordinate counts as converged when
+ * its |Delta Z| computed in FP32 is below max(tol, 2^-21 |beta| / ||D_k||^2):
+ * smaller changes are under the resolution of the float32 state (a few ulps
+ * of beta) and chasing them only accumulates rounding drift.
+ *   tol          > 0 (the paper's epsilon)
+ *   max_updates  > 0, cap on applied updates (checked between phases)
+ *   Z_out        NULL or [K][T-L+1] float32, host or device, caller-owned
+ *   objective    NULL or receives E(Z) (FP64)
+ *   stats        NULL or receives csc_stats
+ * Returns CSC_OK, CSC_NOT_CONVERGED, or an error.  May be called again to
+ * continue from the current Z.
+ */
+int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, double *objective,
+              csc_stats *stats);
+
+/* Releases every device and host resource of the handle.  NULL is accepted. */
+int csc_destroy(csc_handle_t h);
+
+/* max_{k,t} |(D~_k * X)[t]| of the last csc_init: Z* = 0 iff lambda >= this. */
+int csc_lambda_max(csc_handle_t h, double *out);
+
+/* Copies the current beta [K][Tz] (float32) to host or device memory. */
+int csc_get_beta(csc_handle_t h, float *beta_out);
+
+/* Copies DtD [K][K][2L-1] (layout above) and the norms [K] (either may be NULL). */
+int csc_get_dtd(csc_handle_t h, float *dtd_out, float *norms_out);
+
+/* FP64 objective E(Z) of Eq. sparse_code for the handle's X and lambda and an
+ * arbitrary Z [K][Tz] (host or device). */
+int csc_objective(csc_handle_t h, const float *Z, double *out);
+
+/*
+ * Per-phase trace of the last csc_solve: for phase launch g (0-based, in
+ * launch order) the updates it applied, the objective decrease it achieved
+ * (sum of Prop. A.1 cost variations, FP64) and the device time in ns of the
+ * end of its last thread block, relative to the start of the solve.  The
+ * objective before the solve is *E_start.  Arrays hold cap entries; *n
+ * receives the number of phases recorded (may exceed cap).
+ */
+int csc_get_trace(csc_handle_t h, int64_t cap, int64_t *updates, double *decrease,
+                  int64_t *t_ns, int64_t *n, double *E_start);
+
+/*
+ * Host-only planning (no GPU): the segment schedule for Tz samples, atoms of
+ * length L and M segments (Sec. 2.2, 0-based): segment m is
+ * [floor(m*Tz/M), floor((m+1)*Tz/M)); *phases receives c, the number of
+ * phases such that co-active segments' update windows never overlap.
+ * starts may be NULL or hold M+1 entries.  M == 0 picks the automatic M.
+ * Returns CSC_EINVAL if M > Tz or sizes are not positive.
+ */
+int csc_plan(int64_t Tz, int L, int M, int *M_out, int *phases, int64_t *starts);
+
+/* Number of kernels launched through this handle since it was created. */
+int csc_kernel_launches(csc_handle_t h, int64_t *out);
+
+/* Text of the last error on the calling thread ("" if none). */
+const char *csc_last_error_string(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CSC_H */

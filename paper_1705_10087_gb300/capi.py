@@ -1,0 +1,216 @@
+"""Thin Python binding of the C ABI in include/csc.h (ctypes).
+
+The functions carry the C names and only marshal arguments: arrays may be
+torch tensors (CUDA or CPU) or numpy arrays and are passed as raw pointers;
+every computation runs in libcsc.so.  There is no fallback: if the library
+is missing, loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+CSC_OK = 0
+CSC_NOT_CONVERGED = 1
+CSC_EINVAL = -1
+CSC_ENOMEM = -2
+CSC_ECUDA = -3
+CSC_ETIMEOUT = -4
+CSC_ESTATE = -5
+
+
+class csc_opts(ctypes.Structure):
+    _fields_ = [("segments", ctypes.c_int32), ("updates_per_visit", ctypes.c_int32),
+                ("max_resyncs", ctypes.c_int32), ("sweeps_per_poll", ctypes.c_int32),
+                ("max_sweeps", ctypes.c_int32), ("time_kernels", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
+
+
+class csc_stats(ctypes.Structure):
+    _fields_ = [("updates", ctypes.c_int64), ("sweeps", ctypes.c_int64),
+                ("segments", ctypes.c_int32), ("phases", ctypes.c_int32),
+                ("resyncs", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("objective", ctypes.c_double), ("max_drift", ctypes.c_double),
+                ("kkt_zero_excess", ctypes.c_double), ("kkt_nonzero_gap", ctypes.c_double),
+                ("max_delta_z", ctypes.c_double), ("solve_ms", ctypes.c_double),
+                ("phase_ms", ctypes.c_double), ("phase_launches", ctypes.c_int64),
+                ("visits", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class CscError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"csc error {status}: {message}")
+        self.status = status
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libcsc.so (build it first with build.build()); raises if absent."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise OSError(f"{path} is not built: run paper_1705_10087_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    lib.csc_default_opts.argtypes = [ctypes.POINTER(csc_opts)]
+    lib.csc_default_opts.restype = None
+    lib.csc_setup.argtypes = [ctypes.POINTER(_vp), _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                              ctypes.POINTER(csc_opts), _vp]
+    lib.csc_init.argtypes = [_vp, _vp, _i64, ctypes.c_double, _vp]
+    lib.csc_solve.argtypes = [_vp, ctypes.c_double, _i64, _vp, ctypes.POINTER(ctypes.c_double),
+                              ctypes.POINTER(csc_stats)]
+    lib.csc_destroy.argtypes = [_vp]
+    lib.csc_lambda_max.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
+    lib.csc_get_beta.argtypes = [_vp, _vp]
+    lib.csc_get_dtd.argtypes = [_vp, _vp, _vp]
+    lib.csc_objective.argtypes = [_vp, _vp, ctypes.POINTER(ctypes.c_double)]
+    lib.csc_get_trace.argtypes = [_vp, _i64, _vp, _vp, _vp, ctypes.POINTER(_i64),
+                                  ctypes.POINTER(ctypes.c_double)]
+    lib.csc_plan.argtypes = [_i64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                             ctypes.POINTER(ctypes.c_int), _vp]
+    lib.csc_kernel_launches.argtypes = [_vp, ctypes.POINTER(_i64)]
+    lib.csc_last_error_string.argtypes = []
+    lib.csc_last_error_string.restype = ctypes.c_char_p
+    for name in ("csc_setup", "csc_init", "csc_solve", "csc_destroy", "csc_lambda_max",
+                 "csc_get_beta", "csc_get_dtd", "csc_objective", "csc_get_trace", "csc_plan",
+                 "csc_kernel_launches"):
+        getattr(lib, name).restype = ctypes.c_int
+    if path == _build.LIB:
+        _lib = lib
+    return lib
+
+
+def csc_last_error_string() -> str:
+    return load().csc_last_error_string().decode()
+
+
+def _check(status: int) -> int:
+    if status < 0:
+        raise CscError(status, csc_last_error_string())
+    return status
+
+
+def _ptr(a, writable: bool = False):
+    """Raw pointer of a float32 contiguous torch tensor or numpy array."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float32 or not a.flags.c_contiguous:
+            raise TypeError("numpy arrays must be C-contiguous float32")
+        if writable and not a.flags.writeable:
+            raise TypeError("output array is read-only")
+        return a.ctypes.data
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.dtype != torch.float32 or not a.is_contiguous():
+            raise TypeError("tensors must be contiguous float32")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)!r}")
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def make_opts(segments: int = 0, updates_per_visit: int = 0, max_resyncs: int = -1,
+              sweeps_per_poll: int = 0, max_sweeps: int = 0, time_kernels: int = 0) -> csc_opts:
+    o = csc_opts()
+    load().csc_default_opts(ctypes.byref(o))
+    o.segments, o.updates_per_visit = segments, updates_per_visit
+    o.max_resyncs, o.sweeps_per_poll, o.max_sweeps = max_resyncs, sweeps_per_poll, max_sweeps
+    o.time_kernels = time_kernels
+    return o
+
+
+def csc_setup(D, opts: csc_opts | None = None, stream=None, handle=None):
+    """D [K,P,L] float32 -> handle (a ctypes c_void_p); re-uses ``handle`` if given."""
+    K, P, L = (int(x) for x in D.shape)
+    h = handle if handle is not None else _vp()
+    _check(load().csc_setup(ctypes.byref(h), _ptr(D), K, P, L,
+                            ctypes.byref(opts) if opts is not None else None, _stream(stream)))
+    return h
+
+
+def csc_init(h, X, lam: float, Z0=None) -> None:
+    _check(load().csc_init(h, _ptr(X), int(X.shape[1]), float(lam), _ptr(Z0)))
+
+
+def csc_solve(h, tol: float, max_updates: int = 1 << 62, Z_out=None):
+    """Returns (status, objective, stats dict)."""
+    obj = ctypes.c_double(0.0)
+    st = csc_stats()
+    status = _check(load().csc_solve(h, float(tol), int(max_updates), _ptr(Z_out, True),
+                                     ctypes.byref(obj), ctypes.byref(st)))
+    return status, obj.value, st.as_dict()
+
+
+def csc_destroy(h) -> None:
+    _check(load().csc_destroy(h))
+
+
+def csc_lambda_max(h) -> float:
+    v = ctypes.c_double(0.0)
+    _check(load().csc_lambda_max(h, ctypes.byref(v)))
+    return v.value
+
+
+def csc_get_beta(h, out) -> None:
+    _check(load().csc_get_beta(h, _ptr(out, True)))
+
+
+def csc_get_dtd(h, dtd_out=None, norms_out=None) -> None:
+    _check(load().csc_get_dtd(h, _ptr(dtd_out, True), _ptr(norms_out, True)))
+
+
+def csc_objective(h, Z) -> float:
+    v = ctypes.c_double(0.0)
+    _check(load().csc_objective(h, _ptr(Z), ctypes.byref(v)))
+    return v.value
+
+
+def csc_get_trace(h, cap: int = 1 << 16) -> dict:
+    upd = np.zeros(cap, np.int64)
+    dec = np.zeros(cap, np.float64)
+    tns = np.zeros(cap, np.int64)
+    n = _i64(0)
+    e0 = ctypes.c_double(0.0)
+    _check(load().csc_get_trace(h, cap, upd.ctypes.data, dec.ctypes.data, tns.ctypes.data,
+                                ctypes.byref(n), ctypes.byref(e0)))
+    m = min(int(n.value), cap)
+    return {"updates": upd[:m], "decrease": dec[:m], "t_ns": tns[:m], "n": int(n.value),
+            "E_start": e0.value}
+
+
+def csc_kernel_launches(h) -> int:
+    v = _i64(0)
+    _check(load().csc_kernel_launches(h, ctypes.byref(v)))
+    return v.value
+
+
+def csc_plan(Tz: int, L: int, M: int = 0):
+    """Host-only schedule: returns (M, phases, starts[M+1])."""
+    Mo = ctypes.c_int(0)
+    c = ctypes.c_int(0)
+    _check(load().csc_plan(int(Tz), int(L), int(M), ctypes.byref(Mo), ctypes.byref(c), None))
+    starts = np.zeros(Mo.value + 1, np.int64)
+    _check(load().csc_plan(int(Tz), int(L), Mo.value, None, None, starts.ctypes.data))
+    return Mo.value, c.value, starts

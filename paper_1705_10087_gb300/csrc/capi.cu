@@ -1,0 +1,636 @@
+// C ABI entry points (include/csc.h) and the host-side orchestration of the
+// solver: handle state, pointer-kind detection, the phase loop with its
+// convergence polls and FP64 resync rounds.
+#include <cmath>
+#include <cstdarg>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "csc_internal.cuh"
+
+using namespace csc;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CSC_CUDA(expr)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (expr);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(e_ == cudaErrorMemoryAllocation ? CSC_ENOMEM : CSC_ECUDA,        \
+                        "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, \
+                        __LINE__);                                                       \
+    } while (0)
+
+// Small device-side state of a handle (one allocation).
+struct Scratch {
+    long long upd[kPhaseRing];
+    double dec[kPhaseRing];
+    unsigned long long tend[kPhaseRing];
+    long long total;
+    int done;
+    int pad;
+    long long visits;
+    unsigned int lmax_bits;
+    unsigned long long tstart;
+    unsigned long long red[8];
+    double obj[2];
+};
+
+// Host mirror of what the solve loop polls (pinned).
+struct Poll {
+    long long total;
+    int done;
+    int pad;
+};
+
+bool is_device_pointer(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+cudaError_t copy_in(void *dst, const void *src, size_t bytes, cudaStream_t s)
+{
+    return cudaMemcpyAsync(dst, src, bytes,
+                           is_device_pointer(src) ? cudaMemcpyDeviceToDevice
+                                                  : cudaMemcpyHostToDevice,
+                           s);
+}
+
+cudaError_t copy_out(void *dst, const void *src, size_t bytes, cudaStream_t s)
+{
+    return cudaMemcpyAsync(dst, src, bytes,
+                           is_device_pointer(dst) ? cudaMemcpyDeviceToDevice
+                                                  : cudaMemcpyDeviceToHost,
+                           s);
+}
+
+int phase_count_host(int64_t Tz, int M, int L)
+{
+    if (M <= 1)
+        return 1;
+    const int64_t wmin = Tz / M;
+    if (wmin < 1)
+        return -1;
+    const int64_t need = 2 * (int64_t)L - 2;
+    int64_t c = 1 + (need + wmin - 1) / wmin;
+    return (int)(c > M ? M : c);
+}
+
+int auto_segments(int64_t Tz, int L)
+{
+    const int64_t w = 2 * (int64_t)L - 2 > 1 ? 2 * (int64_t)L - 2 : 1;
+    int64_t M = Tz / w;
+    if (M < 1)
+        M = 1;
+    if (M > (1 << 30))
+        M = 1 << 30;
+    return (int)M;
+}
+
+template <class T>
+cudaError_t grow(T **p, size_t *cap, size_t n)
+{
+    if (*cap >= n && *p)
+        return cudaSuccess;
+    if (*p)
+        cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), sizeof(T) * (n ? n : 1));
+    if (e == cudaSuccess)
+        *cap = n;
+    return e;
+}
+
+}  // namespace
+
+struct csc_handle_s {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    csc_opts opts{};
+    int K = 0, P = 0, L = 0;
+    float *D = nullptr, *C = nullptr, *norms = nullptr;
+    size_t cap_D = 0, cap_C = 0, cap_n = 0;
+    // problem state
+    bool initialized = false;
+    int64_t T = 0, Tz = 0;
+    double lambda = 0.0, lambda_max = 0.0;
+    float *X = nullptr, *beta = nullptr, *beta0 = nullptr, *Z = nullptr;
+    size_t cap_X = 0, cap_beta = 0, cap_beta0 = 0, cap_Z = 0;
+    double *partials = nullptr;
+    size_t cap_partials = 0;
+    unsigned char *dirty = nullptr;
+    size_t cap_dirty = 0;
+    float *tmpZ = nullptr;
+    size_t cap_tmpZ = 0;
+    Scratch *sc = nullptr;
+    Poll *poll = nullptr;  // pinned
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t *kev = nullptr;  // per-launch timing events (2 per launch of a poll batch)
+    int n_kev = 0;
+    int64_t launches = 0;        // kernels launched through this handle
+    // last solve
+    int64_t g_used = 0;
+    double E_start = 0.0;
+};
+
+extern "C" {
+
+const char *csc_last_error_string(void)
+{
+    return g_err.c_str();
+}
+
+void csc_default_opts(csc_opts *o)
+{
+    if (!o)
+        return;
+    std::memset(o, 0, sizeof *o);
+    o->max_resyncs = -1;
+}
+
+int csc_plan(int64_t Tz, int L, int M, int *M_out, int *phases, int64_t *starts)
+{
+    if (Tz < 1 || L < 1 || M < 0)
+        return fail(CSC_EINVAL, "csc_plan: need Tz >= 1, L >= 1, M >= 0");
+    if (M == 0)
+        M = auto_segments(Tz, L);
+    if (M > Tz)
+        return fail(CSC_EINVAL, "csc_plan: M = %d exceeds Tz = %lld", M, (long long)Tz);
+    if (M_out)
+        *M_out = M;
+    if (phases)
+        *phases = phase_count_host(Tz, M, L);
+    if (starts)
+        for (int m = 0; m <= M; m++)
+            starts[m] = seg_start(Tz, M, m);
+    return CSC_OK;
+}
+
+int csc_destroy(csc_handle_t h)
+{
+    if (!h)
+        return CSC_OK;
+    cudaSetDevice(h->device);
+    if (h->stream)
+        cudaStreamSynchronize(h->stream);
+    cudaFree(h->D);
+    cudaFree(h->C);
+    cudaFree(h->norms);
+    cudaFree(h->X);
+    cudaFree(h->beta);
+    cudaFree(h->beta0);
+    cudaFree(h->Z);
+    cudaFree(h->partials);
+    cudaFree(h->dirty);
+    cudaFree(h->tmpZ);
+    cudaFree(h->sc);
+    if (h->poll)
+        cudaFreeHost(h->poll);
+    if (h->ev0)
+        cudaEventDestroy(h->ev0);
+    if (h->ev1)
+        cudaEventDestroy(h->ev1);
+    for (int i = 0; i < h->n_kev; i++)
+        cudaEventDestroy(h->kev[i]);
+    delete[] h->kev;
+    delete h;
+    return CSC_OK;
+}
+
+int csc_setup(csc_handle_t *hp, const float *D, int K, int P, int L, const csc_opts *opts,
+              void *stream)
+{
+    if (!hp || !D)
+        return fail(CSC_EINVAL, "csc_setup: null handle pointer or D");
+    if (K < 1 || K > 256 || P < 1 || L < 1 || L > kMaxL)
+        return fail(CSC_EINVAL, "csc_setup: need 1 <= K <= 256, P >= 1, 1 <= L <= %d (got %d,%d,%d)",
+                    kMaxL, K, P, L);
+    csc_opts o;
+    csc_default_opts(&o);
+    if (opts) {
+        o = *opts;
+        if (o.segments < 0 || o.updates_per_visit < 0 || o.max_resyncs < -1 ||
+            o.sweeps_per_poll < 0 || o.max_sweeps < 0 || o.time_kernels < 0 ||
+            o.time_kernels > 1 || o.reserved[0] || o.reserved[1])
+            return fail(CSC_EINVAL, "csc_setup: invalid options");
+    }
+    csc_handle_t h = *hp;
+    bool fresh = false;
+    if (!h) {
+        h = new (std::nothrow) csc_handle_s();
+        if (!h)
+            return fail(CSC_ENOMEM, "csc_setup: host allocation failed");
+        fresh = true;
+        if (cudaGetDevice(&h->device) != cudaSuccess) {
+            delete h;
+            return fail(CSC_ECUDA, "csc_setup: no CUDA device");
+        }
+    }
+    cudaSetDevice(h->device);
+    h->stream = (cudaStream_t)stream;
+    h->opts = o;
+    h->K = K;
+    h->P = P;
+    h->L = L;
+    h->initialized = false;
+    auto body = [&]() -> int {
+        CSC_CUDA(grow(&h->D, &h->cap_D, (size_t)K * P * L));
+        CSC_CUDA(grow(&h->C, &h->cap_C, (size_t)K * K * (2 * L - 1)));
+        CSC_CUDA(grow(&h->norms, &h->cap_n, (size_t)K));
+        if (!h->sc)
+            CSC_CUDA(cudaMalloc(&h->sc, sizeof(Scratch)));
+        if (!h->poll)
+            CSC_CUDA(cudaHostAlloc(&h->poll, sizeof(Poll), cudaHostAllocDefault));
+        if (!h->ev0)
+            CSC_CUDA(cudaEventCreate(&h->ev0));
+        if (!h->ev1)
+            CSC_CUDA(cudaEventCreate(&h->ev1));
+        CSC_CUDA(copy_in(h->D, D, sizeof(float) * K * P * L, h->stream));
+        CSC_CUDA(launch_dtd(h->D, K, P, L, h->C, h->norms, h->stream));
+        h->launches += 1;
+        return CSC_OK;
+    };
+    int rc = body();
+    if (rc != CSC_OK) {
+        if (fresh)
+            csc_destroy(h);
+        return rc;
+    }
+    *hp = h;
+    return CSC_OK;
+}
+
+int csc_init(csc_handle_t h, const float *X, int64_t T, double lambda, const float *Z0)
+{
+    if (!h || !X)
+        return fail(CSC_EINVAL, "csc_init: null handle or X");
+    if (T < h->L)
+        return fail(CSC_EINVAL, "csc_init: T = %lld < L = %d", (long long)T, h->L);
+    if (!(lambda > 0.0) || !std::isfinite(lambda))
+        return fail(CSC_EINVAL, "csc_init: lambda must be positive and finite");
+    const int64_t Tz = T - h->L + 1;
+    if ((uint64_t)h->K * (uint64_t)Tz >= 0xFFFFFFFFull)
+        return fail(CSC_EINVAL, "csc_init: K*(T-L+1) must be below 2^32-1");
+    cudaSetDevice(h->device);
+    h->initialized = false;
+    cudaStream_t s = h->stream;
+    const size_t nz = (size_t)h->K * Tz;
+    CSC_CUDA(grow(&h->X, &h->cap_X, (size_t)h->P * T));
+    CSC_CUDA(grow(&h->beta, &h->cap_beta, nz));
+    CSC_CUDA(grow(&h->beta0, &h->cap_beta0, nz));
+    CSC_CUDA(grow(&h->Z, &h->cap_Z, nz));
+    CSC_CUDA(grow(&h->partials, &h->cap_partials, 2 * (size_t)objective_blocks(T)));
+    CSC_CUDA(copy_in(h->X, X, sizeof(float) * h->P * T, s));
+    CSC_CUDA(cudaMemsetAsync(&h->sc->lmax_bits, 0, sizeof(unsigned), s));
+    CSC_CUDA(launch_dtx(h->D, h->X, h->K, h->P, h->L, T, h->beta0, &h->sc->lmax_bits, s));
+    h->launches += 1;
+    if (Z0) {
+        h->launches += 1;
+        CSC_CUDA(copy_in(h->Z, Z0, sizeof(float) * nz, s));
+        CSC_CUDA(cudaMemsetAsync(h->sc->red, 0, sizeof(h->sc->red), s));
+        CSC_CUDA(cudaMemcpyAsync(h->beta, h->beta0, sizeof(float) * nz, cudaMemcpyDeviceToDevice, s));
+        CSC_CUDA(launch_resync(h->beta0, h->beta, h->Z, h->C, h->norms, h->K, h->L, Tz, lambda,
+                               (float)lambda, 1, h->sc->red, s));
+    } else {
+        CSC_CUDA(cudaMemsetAsync(h->Z, 0, sizeof(float) * nz, s));
+        CSC_CUDA(cudaMemcpyAsync(h->beta, h->beta0, sizeof(float) * nz, cudaMemcpyDeviceToDevice, s));
+    }
+    unsigned bits = 0;
+    CSC_CUDA(cudaMemcpyAsync(&bits, &h->sc->lmax_bits, sizeof bits, cudaMemcpyDeviceToHost, s));
+    CSC_CUDA(cudaStreamSynchronize(s));
+    float lm;
+    std::memcpy(&lm, &bits, sizeof lm);
+    h->lambda_max = lm;
+    h->T = T;
+    h->Tz = Tz;
+    h->lambda = lambda;
+    h->initialized = true;
+    return CSC_OK;
+}
+
+int csc_lambda_max(csc_handle_t h, double *out)
+{
+    if (!h || !out)
+        return fail(CSC_EINVAL, "csc_lambda_max: null argument");
+    if (!h->initialized)
+        return fail(CSC_ESTATE, "csc_lambda_max: call csc_init first");
+    *out = h->lambda_max;
+    return CSC_OK;
+}
+
+int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, double *objective,
+              csc_stats *stats)
+{
+    if (!h)
+        return fail(CSC_EINVAL, "csc_solve: null handle");
+    if (!h->initialized)
+        return fail(CSC_ESTATE, "csc_solve: call csc_init first");
+    if (!(tol > 0.0) || max_updates < 1)
+        return fail(CSC_EINVAL, "csc_solve: need tol > 0 and max_updates >= 1");
+    cudaSetDevice(h->device);
+    cudaStream_t s = h->stream;
+    const int64_t Tz = h->Tz;
+    const int M = h->opts.segments ? h->opts.segments : auto_segments(Tz, h->L);
+    if (M > Tz)
+        return fail(CSC_EINVAL, "csc_solve: %d segments exceed Tz = %lld", M, (long long)Tz);
+    const int c = phase_count_host(Tz, M, h->L);
+    const PhaseConfig cfg = phase_config(h->K, h->L, Tz, M);
+    const int S = h->opts.sweeps_per_poll ? h->opts.sweeps_per_poll : 4;
+    const int64_t max_sweeps = h->opts.max_sweeps ? h->opts.max_sweeps : 1000000;
+    const int max_resyncs = h->opts.max_resyncs < 0 ? 3 : h->opts.max_resyncs;
+    const bool timed = h->opts.time_kernels != 0;
+    Scratch *sc = h->sc;
+    const int64_t launches0 = h->launches;
+
+    if (timed && h->n_kev < 2 * S * c) {
+        for (int i = 0; i < h->n_kev; i++)
+            cudaEventDestroy(h->kev[i]);
+        delete[] h->kev;
+        h->n_kev = 0;
+        h->kev = new (std::nothrow) cudaEvent_t[2 * S * c];
+        if (!h->kev)
+            return fail(CSC_ENOMEM, "csc_solve: host allocation failed");
+        for (int i = 0; i < 2 * S * c; i++) {
+            CSC_CUDA(cudaEventCreate(&h->kev[i]));
+            h->n_kev = i + 1;
+        }
+    }
+
+    CSC_CUDA(grow(&h->dirty, &h->cap_dirty, (size_t)M));
+    CSC_CUDA(cudaMemsetAsync(h->dirty, 1, (size_t)M, s));
+    CSC_CUDA(cudaMemsetAsync(sc, 0, offsetof(Scratch, lmax_bits), s));
+    CSC_CUDA(cudaMemsetAsync(sc->red, 0, sizeof(sc->red), s));
+    CSC_CUDA(cudaEventRecord(h->ev0, s));
+    CSC_CUDA(launch_stamp(&sc->tstart, s));
+    CSC_CUDA(launch_objective(h->D, h->X, h->Z, h->K, h->P, h->L, h->T, h->lambda, h->partials,
+                              &sc->obj[0], s));
+    h->launches += 3;
+
+    PhaseParams pp;
+    pp.beta = h->beta;
+    pp.Z = h->Z;
+    pp.C = h->C;
+    pp.norms = h->norms;
+    pp.dirty = h->dirty;
+    pp.upd = sc->upd;
+    pp.dec = sc->dec;
+    pp.tend = sc->tend;
+    pp.total = &sc->total;
+    pp.visits = &sc->visits;
+    pp.done = &sc->done;
+    pp.Tz = Tz;
+    pp.max_updates = max_updates;
+    pp.M = M;
+    pp.c = c;
+    pp.K = h->K;
+    pp.L = h->L;
+    pp.u = h->opts.updates_per_visit ? h->opts.updates_per_visit : kDefaultMaxVisit;
+    pp.lam = (float)h->lambda;
+    pp.tol = (float)tol;
+    {
+        const int64_t wmax = (Tz + M - 1) / M;
+        const int64_t wt = wmax + 2 * (int64_t)(h->L - 1);
+        pp.wt_max = (int)(wt > Tz ? Tz : wt);
+        pp.w_max = (int)wmax;
+    }
+
+    int status = CSC_OK;
+    bool converged = false, report_fresh = false;
+    int resyncs = 0;
+    double drift = 0.0, phase_ms = 0.0;
+    int64_t g = 0, effective = 0, phase_launches = 0;
+    for (;;) {
+        const int64_t g_round = g;
+        CSC_CUDA(cudaMemsetAsync(&sc->done, 0, sizeof(int), s));
+        bool round_done = false;
+        for (;;) {
+            int nb = 0;  // launches in this poll batch
+            for (int i = 0; i < S; i++)
+                for (int p = 0; p < c; p++) {
+                    if (g >= kPhaseRing) {
+                        const int slot = (int)(g & (kPhaseRing - 1));
+                        CSC_CUDA(cudaMemsetAsync(&sc->upd[slot], 0, sizeof(long long), s));
+                        CSC_CUDA(cudaMemsetAsync(&sc->dec[slot], 0, sizeof(double), s));
+                        CSC_CUDA(cudaMemsetAsync(&sc->tend[slot], 0, sizeof(unsigned long long), s));
+                    }
+                    pp.p = p;
+                    pp.g = (int)g;
+                    pp.g_round = (int)g_round;
+                    if (timed)
+                        CSC_CUDA(cudaEventRecord(h->kev[2 * nb], s));
+                    CSC_CUDA(launch_phase(pp, cfg, s));
+                    if (timed)
+                        CSC_CUDA(cudaEventRecord(h->kev[2 * nb + 1], s));
+                    nb++;
+                    g++;
+                }
+            phase_launches += nb;
+            h->launches += nb;
+            CSC_CUDA(cudaMemcpyAsync(h->poll, &sc->total, sizeof(long long) + sizeof(int),
+                                     cudaMemcpyDeviceToHost, s));
+            CSC_CUDA(cudaStreamSynchronize(s));
+            if (timed)
+                for (int i = 0; i < nb; i++) {
+                    float ms = 0.f;
+                    CSC_CUDA(cudaEventElapsedTime(&ms, h->kev[2 * i], h->kev[2 * i + 1]));
+                    phase_ms += ms;
+                }
+            if (h->poll->total >= max_updates && !h->poll->done) {
+                status = CSC_NOT_CONVERGED;
+                break;
+            }
+            if (h->poll->done) {
+                // done = 1 + index of the launch that saw a full sweep without
+                // updates: launches [g_round, done-1) did the work of this round
+                effective += (h->poll->done - 1) - g_round;
+                round_done = true;
+                break;
+            }
+            if (g / c >= max_sweeps) {
+                status = CSC_NOT_CONVERGED;
+                break;
+            }
+        }
+        if (!round_done) {
+            effective += g - g_round;
+            break;
+        }
+        if (resyncs >= max_resyncs) {
+            converged = true;
+            break;
+        }
+        CSC_CUDA(cudaMemsetAsync(sc->red, 0, sizeof(sc->red), s));
+        CSC_CUDA(launch_resync(h->beta0, h->beta, h->Z, h->C, h->norms, h->K, h->L, Tz,
+                               h->lambda, (float)h->lambda, 1, sc->red, s));
+        h->launches += 1;
+        unsigned long long red[8];
+        CSC_CUDA(cudaMemcpyAsync(red, sc->red, sizeof red, cudaMemcpyDeviceToHost, s));
+        CSC_CUDA(cudaStreamSynchronize(s));
+        resyncs++;
+        double d0, dz32;
+        std::memcpy(&d0, &red[0], sizeof d0);
+        std::memcpy(&dz32, &red[4], sizeof dz32);
+        drift = d0 > drift ? d0 : drift;
+        if (dz32 < tol) {
+            converged = true;
+            report_fresh = true;
+            break;
+        }
+        CSC_CUDA(cudaMemsetAsync(h->dirty, 1, (size_t)M, s));
+    }
+    if (!report_fresh) {
+        // optimality report against a fresh FP64 beta, leaving beta unchanged
+        CSC_CUDA(cudaMemsetAsync(sc->red, 0, sizeof(sc->red), s));
+        CSC_CUDA(launch_resync(h->beta0, h->beta, h->Z, h->C, h->norms, h->K, h->L, Tz,
+                               h->lambda, (float)h->lambda, 0, sc->red, s));
+        h->launches += 1;
+    }
+    CSC_CUDA(cudaEventRecord(h->ev1, s));
+    CSC_CUDA(launch_objective(h->D, h->X, h->Z, h->K, h->P, h->L, h->T, h->lambda, h->partials,
+                              &sc->obj[1], s));
+    h->launches += 2;
+    if (Z_out)
+        CSC_CUDA(copy_out(Z_out, h->Z, sizeof(float) * h->K * Tz, s));
+    unsigned long long red[8];
+    double obj[2];
+    long long total = 0, visits = 0;
+    CSC_CUDA(cudaMemcpyAsync(red, sc->red, sizeof red, cudaMemcpyDeviceToHost, s));
+    CSC_CUDA(cudaMemcpyAsync(obj, sc->obj, sizeof obj, cudaMemcpyDeviceToHost, s));
+    CSC_CUDA(cudaMemcpyAsync(&total, &sc->total, sizeof total, cudaMemcpyDeviceToHost, s));
+    CSC_CUDA(cudaMemcpyAsync(&visits, &sc->visits, sizeof visits, cudaMemcpyDeviceToHost, s));
+    CSC_CUDA(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    CSC_CUDA(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    h->g_used = g;
+    h->E_start = obj[0];
+    if (objective)
+        *objective = obj[1];
+    if (stats) {
+        double v[5];
+        std::memcpy(v, red, sizeof v);
+        stats->updates = total;
+        stats->sweeps = (effective + c - 1) / c;
+        stats->segments = M;
+        stats->phases = c;
+        stats->resyncs = resyncs;
+        stats->converged = converged ? 1 : 0;
+        stats->objective = obj[1];
+        stats->max_drift = drift;
+        stats->kkt_zero_excess = v[1];
+        stats->kkt_nonzero_gap = v[2];
+        stats->max_delta_z = v[3];
+        stats->solve_ms = ms;
+        stats->phase_ms = phase_ms;
+        stats->phase_launches = phase_launches;
+        stats->visits = visits;
+        stats->kernel_launches = h->launches - launches0;
+    }
+    return status != CSC_OK ? status : (converged ? CSC_OK : CSC_NOT_CONVERGED);
+}
+
+int csc_kernel_launches(csc_handle_t h, int64_t *out)
+{
+    if (!h || !out)
+        return fail(CSC_EINVAL, "csc_kernel_launches: null argument");
+    *out = h->launches;
+    return CSC_OK;
+}
+
+int csc_get_beta(csc_handle_t h, float *beta_out)
+{
+    if (!h || !beta_out)
+        return fail(CSC_EINVAL, "csc_get_beta: null argument");
+    if (!h->initialized)
+        return fail(CSC_ESTATE, "csc_get_beta: call csc_init first");
+    cudaSetDevice(h->device);
+    CSC_CUDA(copy_out(beta_out, h->beta, sizeof(float) * h->K * h->Tz, h->stream));
+    CSC_CUDA(cudaStreamSynchronize(h->stream));
+    return CSC_OK;
+}
+
+int csc_get_dtd(csc_handle_t h, float *dtd_out, float *norms_out)
+{
+    if (!h)
+        return fail(CSC_EINVAL, "csc_get_dtd: null handle");
+    cudaSetDevice(h->device);
+    if (dtd_out)
+        CSC_CUDA(copy_out(dtd_out, h->C, sizeof(float) * h->K * h->K * (2 * h->L - 1), h->stream));
+    if (norms_out)
+        CSC_CUDA(copy_out(norms_out, h->norms, sizeof(float) * h->K, h->stream));
+    CSC_CUDA(cudaStreamSynchronize(h->stream));
+    return CSC_OK;
+}
+
+int csc_objective(csc_handle_t h, const float *Z, double *out)
+{
+    if (!h || !Z || !out)
+        return fail(CSC_EINVAL, "csc_objective: null argument");
+    if (!h->initialized)
+        return fail(CSC_ESTATE, "csc_objective: call csc_init first");
+    cudaSetDevice(h->device);
+    cudaStream_t s = h->stream;
+    const size_t nz = (size_t)h->K * h->Tz;
+    const float *Zd = Z;
+    if (!is_device_pointer(Z)) {
+        CSC_CUDA(grow(&h->tmpZ, &h->cap_tmpZ, nz));
+        CSC_CUDA(cudaMemcpyAsync(h->tmpZ, Z, sizeof(float) * nz, cudaMemcpyHostToDevice, s));
+        Zd = h->tmpZ;
+    }
+    CSC_CUDA(launch_objective(h->D, h->X, Zd, h->K, h->P, h->L, h->T, h->lambda, h->partials,
+                              &h->sc->obj[1], s));
+    h->launches += 2;
+    CSC_CUDA(cudaMemcpyAsync(out, &h->sc->obj[1], sizeof(double), cudaMemcpyDeviceToHost, s));
+    CSC_CUDA(cudaStreamSynchronize(s));
+    return CSC_OK;
+}
+
+int csc_get_trace(csc_handle_t h, int64_t cap, int64_t *updates, double *decrease,
+                  int64_t *t_ns, int64_t *n, double *E_start)
+{
+    if (!h || cap < 0 || (cap > 0 && (!updates || !decrease || !t_ns)))
+        return fail(CSC_EINVAL, "csc_get_trace: bad arguments");
+    cudaSetDevice(h->device);
+    const int64_t g = h->g_used < kPhaseRing ? h->g_used : kPhaseRing;
+    const int64_t m = cap < g ? cap : g;
+    if (n)
+        *n = h->g_used;
+    if (E_start)
+        *E_start = h->E_start;
+    if (m == 0)
+        return CSC_OK;
+    unsigned long long t0 = 0;
+    CSC_CUDA(cudaMemcpyAsync(updates, h->sc->upd, sizeof(long long) * m, cudaMemcpyDeviceToHost,
+                             h->stream));
+    CSC_CUDA(cudaMemcpyAsync(decrease, h->sc->dec, sizeof(double) * m, cudaMemcpyDeviceToHost,
+                             h->stream));
+    CSC_CUDA(cudaMemcpyAsync(t_ns, h->sc->tend, sizeof(int64_t) * m, cudaMemcpyDeviceToHost,
+                             h->stream));
+    CSC_CUDA(cudaMemcpyAsync(&t0, &h->sc->tstart, sizeof t0, cudaMemcpyDeviceToHost, h->stream));
+    CSC_CUDA(cudaStreamSynchronize(h->stream));
+    for (int64_t i = 0; i < m; i++)
+        t_ns[i] = t_ns[i] ? (int64_t)((unsigned long long)t_ns[i] - t0) : -1;
+    return CSC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,324 @@
+// FP64 kernels (the only FP64 arithmetic on the GPU): the periodic / final
+// re-synchronisation of beta with its definition (Sec. 2.1) and the objective
+// E(Z) of Eq. sparse_code from the explicit residual.
+//
+// Both exploit that Z is sparse: a block gathers the nonzeros of Z that can
+// reach its tile (compacted in a fixed order, so results are deterministic)
+// and every thread accumulates its outputs over that list in FP64.
+#include "csc_internal.cuh"
+
+namespace csc {
+
+namespace {
+
+constexpr int kChunk = 64;  // Z columns scanned per compaction round
+
+struct NZ {
+    int k;
+    int t;  // absolute time index (fits: Tz < 2^31 enforced by the 32-bit flat index)
+    float z;
+};
+
+// Ordered compaction of the nonzeros of Z[:, c0:c1) (k-major) into list.
+// Returns the count (same value in every thread).  Block-wide barriers.
+__device__ int compact_nonzeros(const float *__restrict__ Z, int K, int64_t Tz, int64_t c0,
+                                int64_t c1, NZ *list, int *warp_counts)
+{
+    const int tid = threadIdx.x, B = blockDim.x, lane = tid & 31, warp = tid >> 5,
+              nw = B >> 5;
+    const int width = (int)(c1 - c0);
+    const int n = K * width;
+    int base = 0;
+    for (int r0 = 0; r0 < n; r0 += B) {
+        const int i = r0 + tid;
+        float z = 0.f;
+        int k = 0, t = 0;
+        if (i < n) {
+            k = i / width;
+            t = (int)(c0 + i % width);
+            z = Z[(int64_t)k * Tz + t];
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, z != 0.f);
+        if (lane == 0)
+            warp_counts[warp] = __popc(bal);
+        __syncthreads();
+        int off = base;
+        for (int q = 0; q < warp; q++)
+            off += warp_counts[q];
+        int tot = base;
+        for (int q = 0; q < nw; q++)
+            tot += warp_counts[q];
+        if (z != 0.f) {
+            const int pos = off + __popc(bal & ((1u << lane) - 1u));
+            list[pos] = NZ{k, t, z};
+        }
+        __syncthreads();
+        base = tot;
+    }
+    return base;
+}
+
+constexpr int kResyncCols = 64;   // output columns per block
+constexpr int kResyncThreads = 256;
+constexpr int kResyncGroups = kResyncThreads / kResyncCols;  // atom groups
+
+template <int KPT>
+__global__ void __launch_bounds__(kResyncThreads)
+    resync_kernel(const float *__restrict__ beta0, float *__restrict__ beta,
+                  const float *__restrict__ Z, const float *__restrict__ C,
+                  const float *__restrict__ norms, int K, int L, int64_t Tz, double lam,
+                  float lam_f, int write_beta, unsigned long long *__restrict__ red)
+{
+    __shared__ NZ list[32 * kChunk];
+    __shared__ int warp_counts[32];
+    __shared__ double bred[4][kResyncThreads / 32];
+    __shared__ float bred32[kResyncThreads / 32];
+    const int W2 = 2 * L - 1;
+    const int tid = threadIdx.x;
+    const int col = tid % kResyncCols, grp = tid / kResyncCols;
+    const int64_t c0 = (int64_t)blockIdx.x * kResyncCols;
+    const int64_t t = c0 + col;
+    double acc[KPT];
+#pragma unroll
+    for (int i = 0; i < KPT; i++)
+        acc[i] = 0.0;
+
+    // nonzeros that reach [c0, c0+cols): Z columns in [c0-(L-1), c0+cols+(L-1))
+    const int64_t lo = c0 - (L - 1) > 0 ? c0 - (L - 1) : 0;
+    const int64_t hi = c0 + kResyncCols + (L - 1) < Tz ? c0 + kResyncCols + (L - 1) : Tz;
+    const int chunk = (32 * kChunk) / K < kChunk ? (32 * kChunk) / K : kChunk;
+    for (int64_t a = lo; a < hi; a += chunk) {
+        const int64_t b = a + chunk < hi ? a + chunk : hi;
+        const int n = compact_nonzeros(Z, K, Tz, a, b, list, warp_counts);
+        if (t < Tz) {
+            for (int i = 0; i < n; i++) {
+                const NZ e = list[i];
+                const int d = (int)(t - e.t) + (L - 1);
+                if (d < 0 || d >= W2)
+                    continue;
+                const double zd = (double)e.z;
+                const float *Cl = C + (int64_t)e.k * K * W2 + d;
+#pragma unroll
+                for (int q = 0; q < KPT; q++) {
+                    const int k = grp + q * kResyncGroups;
+                    if (k < K && !(k == e.k && d == L - 1))
+                        acc[q] += (double)__ldg(Cl + (int64_t)k * W2) * zd;
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    double drift = 0.0, zex = 0.0, nzg = 0.0, all = 0.0;
+    float dz32 = 0.f;
+    if (t < Tz) {
+#pragma unroll
+        for (int q = 0; q < KPT; q++) {
+            const int k = grp + q * kResyncGroups;
+            if (k >= K)
+                continue;
+            const int64_t ix = (int64_t)k * Tz + t;
+            const double b64 = (double)beta0[ix] - acc[q];
+            const float bold = beta[ix];
+            drift = fmax(drift, fabs((double)bold - b64));
+            const float b32 = (float)b64;
+            if (write_beta)
+                beta[ix] = b32;
+            const float z = Z[ix];
+            const float n = norms[k];
+            const double gap = fabs((double)z - soft_d(b64, lam) / (double)n);
+            if (z == 0.f)
+                zex = fmax(zex, fabs(b64) - lam);
+            else
+                nzg = fmax(nzg, gap);
+            all = fmax(all, gap);
+            const float b_used = write_beta ? b32 : bold;
+            const float d32 = fabsf(__fdiv_rn(soft_f(b_used, lam_f), n) - z);
+            if (d32 >= resolution_floor(b_used, n))
+                dz32 = fmaxf(dz32, d32);
+        }
+    }
+    // block reduce (max) and one atomic per block and quantity
+    for (int off = 16; off > 0; off >>= 1) {
+        drift = fmax(drift, __shfl_xor_sync(0xffffffffu, drift, off));
+        zex = fmax(zex, __shfl_xor_sync(0xffffffffu, zex, off));
+        nzg = fmax(nzg, __shfl_xor_sync(0xffffffffu, nzg, off));
+        all = fmax(all, __shfl_xor_sync(0xffffffffu, all, off));
+        dz32 = fmaxf(dz32, __shfl_xor_sync(0xffffffffu, dz32, off));
+    }
+    const int warp = tid >> 5, lane = tid & 31;
+    if (lane == 0) {
+        bred[0][warp] = drift;
+        bred[1][warp] = zex;
+        bred[2][warp] = nzg;
+        bred[3][warp] = all;
+        bred32[warp] = dz32;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double v[4] = {0, 0, 0, 0};
+        float v32 = 0.f;
+        for (int w = 0; w < kResyncThreads / 32; w++) {
+            for (int q = 0; q < 4; q++)
+                v[q] = fmax(v[q], bred[q][w]);
+            v32 = fmaxf(v32, bred32[w]);
+        }
+        for (int q = 0; q < 4; q++)
+            atomicMax(&red[q], (unsigned long long)__double_as_longlong(fmax(v[q], 0.0)));
+        atomicMax(&red[4], (unsigned long long)__double_as_longlong((double)v32));
+    }
+}
+
+constexpr int kObjTile = 256;  // samples per block, one per thread
+constexpr int kObjP = 8;       // channels accumulated per pass
+
+// partial[b] = (sum over the block's samples t of sum_p R[p][t]^2,
+//               sum over the block's columns t < Tz of sum_k |Z[k][t]|)
+// with R = X - sum_k Z_k * D_k, (Z*D)[t] = sum_tau Z[t-tau] D[tau] (Sec. 2).
+__global__ void __launch_bounds__(kObjTile)
+    objective_kernel(const float *__restrict__ D, const float *__restrict__ X,
+                     const float *__restrict__ Z, int K, int P, int L, int64_t T,
+                     double *__restrict__ partials)
+{
+    __shared__ NZ list[32 * kChunk];
+    __shared__ int warp_counts[32];
+    __shared__ double bsum[2][kObjTile / 32];
+    const int64_t Tz = T - L + 1;
+    const int tid = threadIdx.x;
+    const int64_t c0 = (int64_t)blockIdx.x * kObjTile;
+    const int64_t t = c0 + tid;
+    double sq = 0.0, l1 = 0.0;
+    // Z columns that reach samples [c0, c0+tile): [c0-(L-1), c0+tile) within [0,Tz)
+    const int64_t lo = c0 - (L - 1) > 0 ? c0 - (L - 1) : 0;
+    const int64_t hi = c0 + kObjTile < Tz ? c0 + kObjTile : Tz;
+    const int chunk = (32 * kChunk) / K < kChunk ? (32 * kChunk) / K : kChunk;
+    for (int p0 = 0; p0 < P; p0 += kObjP) {
+        double acc[kObjP];
+#pragma unroll
+        for (int q = 0; q < kObjP; q++)
+            acc[q] = 0.0;
+        for (int64_t a = lo; a < hi; a += chunk) {
+            const int64_t b = a + chunk < hi ? a + chunk : hi;
+            const int n = compact_nonzeros(Z, K, Tz, a, b, list, warp_counts);
+            if (t < T) {
+                for (int i = 0; i < n; i++) {
+                    const NZ e = list[i];
+                    const int tau = (int)(t - e.t);
+                    if (tau < 0 || tau >= L)
+                        continue;
+                    const double zd = (double)e.z;
+                    const float *Dk = D + (int64_t)e.k * P * L + tau;
+#pragma unroll
+                    for (int q = 0; q < kObjP; q++)
+                        if (p0 + q < P)
+                            acc[q] += (double)__ldg(Dk + (int64_t)(p0 + q) * L) * zd;
+                }
+            }
+            __syncthreads();
+        }
+        if (t < T) {
+#pragma unroll
+            for (int q = 0; q < kObjP; q++)
+                if (p0 + q < P) {
+                    const double r = (double)X[(int64_t)(p0 + q) * T + t] - acc[q];
+                    sq += r * r;
+                }
+        }
+    }
+    if (t < Tz)
+        for (int k = 0; k < K; k++)
+            l1 += fabs((double)Z[(int64_t)k * Tz + t]);
+    for (int off = 16; off > 0; off >>= 1) {
+        sq += __shfl_xor_sync(0xffffffffu, sq, off);
+        l1 += __shfl_xor_sync(0xffffffffu, l1, off);
+    }
+    if ((tid & 31) == 0) {
+        bsum[0][tid >> 5] = sq;
+        bsum[1][tid >> 5] = l1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < kObjTile / 32; w++) {
+            a += bsum[0][w];
+            b += bsum[1][w];
+        }
+        partials[2 * blockIdx.x] = a;
+        partials[2 * blockIdx.x + 1] = b;
+    }
+}
+
+// Fixed-order sum of the partials: E = sq/2 + lam * l1.
+__global__ void objective_final_kernel(const double *__restrict__ partials, int nblocks,
+                                       double lam, double *__restrict__ out)
+{
+    __shared__ double s[2][256];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
+        a += partials[2 * i];
+        b += partials[2 * i + 1];
+    }
+    s[0][threadIdx.x] = a;
+    s[1][threadIdx.x] = b;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            s[0][threadIdx.x] += s[0][threadIdx.x + h];
+            s[1][threadIdx.x] += s[1][threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        *out = 0.5 * s[0][0] + lam * s[1][0];
+}
+
+template <int KPT>
+cudaError_t resync_launch(const float *beta0, float *beta, const float *Z, const float *C,
+                          const float *norms, int K, int L, int64_t Tz, double lam, float lam_f,
+                          int write_beta, unsigned long long *red, cudaStream_t s)
+{
+    const unsigned grid = (unsigned)((Tz + kResyncCols - 1) / kResyncCols);
+    resync_kernel<KPT><<<grid, kResyncThreads, 0, s>>>(beta0, beta, Z, C, norms, K, L, Tz, lam,
+                                                       lam_f, write_beta, red);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_resync(const float *beta0, float *beta, const float *Z, const float *C,
+                          const float *norms, int K, int L, int64_t Tz, double lam,
+                          float lam_f, int write_beta, unsigned long long *red, cudaStream_t s)
+{
+    const int kpt = (K + kResyncGroups - 1) / kResyncGroups;
+    if (kpt <= 2)
+        return resync_launch<2>(beta0, beta, Z, C, norms, K, L, Tz, lam, lam_f, write_beta, red, s);
+    if (kpt <= 8)
+        return resync_launch<8>(beta0, beta, Z, C, norms, K, L, Tz, lam, lam_f, write_beta, red, s);
+    if (kpt <= 16)
+        return resync_launch<16>(beta0, beta, Z, C, norms, K, L, Tz, lam, lam_f, write_beta, red,
+                                 s);
+    if (kpt <= 64)
+        return resync_launch<64>(beta0, beta, Z, C, norms, K, L, Tz, lam, lam_f, write_beta, red,
+                                 s);
+    return cudaErrorInvalidValue;
+}
+
+int objective_blocks(int64_t T)
+{
+    return (int)((T + kObjTile - 1) / kObjTile);
+}
+
+cudaError_t launch_objective(const float *D, const float *X, const float *Z, int K, int P, int L,
+                             int64_t T, double lam, double *partials, double *out,
+                             cudaStream_t s)
+{
+    const int nb = objective_blocks(T);
+    objective_kernel<<<nb, kObjTile, 0, s>>>(D, X, Z, K, P, L, T, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    objective_final_kernel<<<1, 256, 0, s>>>(partials, nb, lam, out);
+    return cudaGetLastError();
+}
+
+}  // namespace csc

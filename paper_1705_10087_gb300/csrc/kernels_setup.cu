@@ -1,0 +1,166 @@
+// Setup kernels: the atom cross-correlation table DtD with the norms (step a1)
+// and the initial beta = D~ * X with lambda_max (step a2).
+//
+// Both are dense contractions accumulated in FP32 with compensated summation:
+// FMA partial sums over 8 consecutive lags, added into a Kahan accumulator, so
+// that the rounding error stays at the level of the final rounding (well below
+// the 1e-6 support threshold the solver is checked at).
+#include "csc_internal.cuh"
+
+namespace csc {
+
+namespace {
+
+// DtD[k0][k][s] = sum_p sum_tau D[k][p][tau] * D[k0][p][tau + s - (L-1)]
+// = S_{k,k0}[s-(L-1)] of Eq. beta_up (Sec. 2.1).  One thread per entry.
+__global__ void dtd_kernel(const float *__restrict__ D, int K, int P, int L,
+                           float *__restrict__ C, float *__restrict__ norms)
+{
+    const int W2 = 2 * L - 1;
+    const long long n = (long long)K * K * W2;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(idx % W2);
+        const int k = (int)((idx / W2) % K);
+        const int k0 = (int)(idx / ((long long)W2 * K));
+        const int lag = s - (L - 1);
+        const int tlo = lag < 0 ? -lag : 0;
+        const int thi = lag > 0 ? L - lag : L;
+        KahanF acc;
+        for (int p = 0; p < P; p++) {
+            const float *a = D + ((long long)k * P + p) * L;
+            const float *b = D + ((long long)k0 * P + p) * L + lag;
+            for (int t8 = tlo; t8 < thi; t8 += 8) {
+                float part = 0.f;
+                const int te = min(t8 + 8, thi);
+                for (int t = t8; t < te; t++)
+                    part = fmaf(__ldg(a + t), __ldg(b + t), part);
+                acc.add(part);
+            }
+        }
+        const float v = acc.value();
+        C[idx] = v;
+        if (k == k0 && lag == 0)
+            norms[k] = v;
+    }
+}
+
+constexpr int kDtxTile = 256;   // output samples per block (one per thread)
+constexpr int kDtxAtoms = 8;    // atoms per block
+
+// beta0[k][t] = sum_p sum_tau D[k][p][tau] X[p][t+tau] (Alg. 1 initialisation),
+// plus max |beta0| for lambda_max.  Block: 256 consecutive t, 8 atoms; X and D
+// tiles staged in shared memory (lags padded to a multiple of 8 with zeros).
+__global__ void __launch_bounds__(kDtxTile) dtx_kernel(const float *__restrict__ D,
+                                                       const float *__restrict__ X, int K, int P,
+                                                       int L, long long T,
+                                                       float *__restrict__ beta0,
+                                                       unsigned int *__restrict__ absmax_bits)
+{
+    extern __shared__ float sm[];
+    const int L8 = (L + 7) & ~7;
+    const int xw = kDtxTile + L8;  // X tile width (covers t + tau for tau < L8)
+    float *xs = sm;                               // [P][xw]
+    float *ds = sm + (size_t)P * xw;              // [kDtxAtoms][P][L8]
+    const long long Tz = T - L + 1;
+    const long long t0 = (long long)blockIdx.x * kDtxTile;
+    const int k0 = blockIdx.y * kDtxAtoms;
+    const int nk = min(kDtxAtoms, K - k0);
+
+    for (int i = threadIdx.x; i < P * xw; i += blockDim.x) {
+        const int p = i / xw, j = i % xw;
+        const long long t = t0 + j;
+        xs[i] = t < T ? X[(long long)p * T + t] : 0.f;
+    }
+    for (int i = threadIdx.x; i < kDtxAtoms * P * L8; i += blockDim.x) {
+        const int kk = i / (P * L8), r = i % (P * L8), p = r / L8, tau = r % L8;
+        ds[i] = (kk < nk && tau < L) ? D[((long long)(k0 + kk) * P + p) * L + tau] : 0.f;
+    }
+    __syncthreads();
+
+    const int j = threadIdx.x;
+    KahanF acc[kDtxAtoms];
+    for (int p = 0; p < P; p++) {
+        const float *xr = xs + (size_t)p * xw + j;
+        for (int tb = 0; tb < L8; tb += 8) {
+            float x[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++)
+                x[q] = xr[tb + q];
+#pragma unroll
+            for (int kk = 0; kk < kDtxAtoms; kk++) {
+                const float4 *dv = reinterpret_cast<const float4 *>(ds + ((size_t)kk * P + p) * L8 + tb);
+                const float4 d0 = dv[0], d1 = dv[1];
+                float part = d0.x * x[0];
+                part = fmaf(d0.y, x[1], part);
+                part = fmaf(d0.z, x[2], part);
+                part = fmaf(d0.w, x[3], part);
+                part = fmaf(d1.x, x[4], part);
+                part = fmaf(d1.y, x[5], part);
+                part = fmaf(d1.z, x[6], part);
+                part = fmaf(d1.w, x[7], part);
+                acc[kk].add(part);
+            }
+        }
+    }
+    const long long t = t0 + j;
+    float amax = 0.f;
+    if (t < Tz) {
+#pragma unroll
+        for (int kk = 0; kk < kDtxAtoms; kk++) {
+            if (kk < nk) {
+                const float v = acc[kk].value();
+                beta0[(long long)(k0 + kk) * Tz + t] = v;
+                amax = fmaxf(amax, fabsf(v));
+            }
+        }
+    }
+    // block max of |beta0| -> one atomic per warp (non-negative floats order as uints)
+    for (int off = 16; off > 0; off >>= 1)
+        amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(absmax_bits, __float_as_uint(amax));
+}
+
+__global__ void stamp_kernel(unsigned long long *out)
+{
+    *out = globaltimer_ns();
+}
+
+}  // namespace
+
+cudaError_t launch_dtd(const float *D, int K, int P, int L, float *C, float *norms,
+                       cudaStream_t s)
+{
+    const long long n = (long long)K * K * (2 * L - 1);
+    const int block = 256;
+    const long long grid = (n + block - 1) / block;
+    dtd_kernel<<<(unsigned)(grid < 65535 * 32 ? grid : 65535 * 32), block, 0, s>>>(D, K, P, L, C,
+                                                                                   norms);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dtx(const float *D, const float *X, int K, int P, int L, int64_t T,
+                       float *beta0, unsigned int *absmax_bits, cudaStream_t s)
+{
+    const int L8 = (L + 7) & ~7;
+    const size_t smem = sizeof(float) * ((size_t)P * (kDtxTile + L8) + (size_t)kDtxAtoms * P * L8);
+    if (smem > (size_t)kMaxSmem)
+        return cudaErrorInvalidConfiguration;
+    cudaError_t e = cudaFuncSetAttribute(dtx_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    const int64_t Tz = T - L + 1;
+    dim3 grid((unsigned)((Tz + kDtxTile - 1) / kDtxTile), (unsigned)((K + kDtxAtoms - 1) / kDtxAtoms));
+    dtx_kernel<<<grid, kDtxTile, smem, s>>>(D, X, K, P, L, T, beta0, absmax_bits);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stamp(unsigned long long *out, cudaStream_t s)
+{
+    stamp_kernel<<<1, 1, 0, s>>>(out);
+    return cudaGetLastError();
+}
+
+}  // namespace csc

@@ -1,0 +1,86 @@
+"""C-ABI contract checks that need no GPU: the library builds and loads, it
+exports every entry point include/csc.h declares, host-only planning agrees
+with the oracle's independent segment schedule, and argument validation
+rejects bad calls before touching a device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1705_10087_gb300 import build, capi
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                      "csc.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return capi.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(csc_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_library_built_for_sm103a():
+    out = os.popen(f"/usr/local/cuda/bin/cuobjdump --list-elf {build.LIB} 2>&1").read()
+    assert "sm_103a" in out
+
+
+@pytest.mark.parametrize("Tz,L,M", [(199_937, 64, 64), (199_937, 64, 256), (199_937, 64, 1024),
+                                    (199_937, 64, 3072), (1985, 16, 10), (1985, 16, 1),
+                                    (4_999_801, 200, 12_500), (7, 3, 7), (50, 1, 9)])
+def test_plan_matches_oracle_schedule(lib, Tz, L, M):
+    Mo, c, starts = capi.csc_plan(Tz, L, M)
+    assert Mo == M
+    assert c == oracle.phase_count(Tz, M, L)
+    assert list(starts) == [oracle.segment_start(Tz, M, m) for m in range(M + 1)]
+
+
+def test_plan_automatic_segments_use_two_phases(lib):
+    for Tz, L in [(199_937, 64), (4_999_801, 200), (1985, 16)]:
+        M, c, starts = capi.csc_plan(Tz, L, 0)
+        assert np.diff(starts).min() >= 2 * L - 2
+        assert c == 2
+
+
+def test_plan_rejects_bad_sizes(lib):
+    with pytest.raises(capi.CscError) as e:
+        capi.csc_plan(10, 3, 11)
+    assert e.value.status == capi.CSC_EINVAL
+    assert "exceeds" in capi.csc_last_error_string()
+
+
+def test_argument_validation_needs_no_device(lib):
+    h = ctypes.c_void_p()
+    D = np.zeros((2, 1, 4), np.float32)
+    assert lib.csc_setup(ctypes.byref(h), D.ctypes.data, 0, 1, 4, None, None) == capi.CSC_EINVAL
+    assert lib.csc_setup(ctypes.byref(h), D.ctypes.data, 2, 1, 513, None, None) == capi.CSC_EINVAL
+    assert lib.csc_setup(ctypes.byref(h), None, 2, 1, 4, None, None) == capi.CSC_EINVAL
+    o = capi.make_opts()
+    o.reserved[0] = 7
+    assert lib.csc_setup(ctypes.byref(h), D.ctypes.data, 2, 1, 4, ctypes.byref(o),
+                         None) == capi.CSC_EINVAL
+    assert lib.csc_init(None, D.ctypes.data, 10, 1.0, None) == capi.CSC_EINVAL
+    assert lib.csc_solve(None, 1e-6, 10, None, None, None) == capi.CSC_EINVAL
+    assert lib.csc_destroy(None) == capi.CSC_OK
+    assert "csc_solve" in capi.csc_last_error_string()
+
+
+def test_default_opts(lib):
+    o = capi.csc_opts()
+    lib.csc_default_opts(ctypes.byref(o))
+    assert (o.segments, o.updates_per_visit, o.max_resyncs) == (0, 0, -1)
