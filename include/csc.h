@@ -178,6 +178,28 @@ int csc_get_trace(csc_handle_t h, int64_t cap, int64_t *updates, double *decreas
  */
 int csc_plan(int64_t Tz, int L, int M, int *M_out, int *phases, int64_t *starts);
 
+/*
+ * E(Z) of Eq. sparse_code in FP64, like csc_objective, for callers that must
+ * not allocate device memory: code running under a fixed device-memory budget
+ * (e.g. a serving loop that admits requests by HBM budget and cannot grow it
+ * mid-request) or latency-critical code that cannot take the implicit device
+ * synchronisation of cudaMalloc/cudaFree.  The paper has no counterpart; this
+ * is a deployment interface.  It needs no handle and calls no cudaMalloc,
+ * cudaFree or allocating library routine.
+ *   D [K][P][L], X [P][T], Z [K][T-L+1]  float32 DEVICE arrays, caller-owned
+ *   lambda >= 0;  E_out: one double, host or device memory
+ *   stream  cudaStream_t (NULL = legacy default stream)
+ * Scratch: a static device array of 1 MiB that every GPU loading this library
+ * keeps until process exit; it limits T to 16,777,216 samples (larger T gives
+ * CSC_EINVAL).  The first call on a device looks up that array's address
+ * (cudaGetSymbolAddress, with the device current); make that first call
+ * before any stream capture.  All calls share the array: calls whose GPU
+ * work may overlap (other streams, other threads) race and must be ordered
+ * by the caller.  With a host E_out the call synchronises the stream.
+ */
+int csc_objective_noalloc(const float *D, int K, int P, int L, const float *X, int64_t T,
+                          const float *Z, double lambda, double *E_out, void *stream);
+
 /* Number of kernels launched through this handle since it was created. */
 int csc_kernel_launches(csc_handle_t h, int64_t *out);
 

@@ -85,11 +85,13 @@ def load(path: str | None = None):
     lib.csc_plan.argtypes = [_i64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                              ctypes.POINTER(ctypes.c_int), _vp]
     lib.csc_kernel_launches.argtypes = [_vp, ctypes.POINTER(_i64)]
+    lib.csc_objective_noalloc.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp,
+                                          _i64, _vp, ctypes.c_double, _vp, _vp]
     lib.csc_last_error_string.argtypes = []
     lib.csc_last_error_string.restype = ctypes.c_char_p
     for name in ("csc_setup", "csc_init", "csc_solve", "csc_destroy", "csc_lambda_max",
                  "csc_get_beta", "csc_get_dtd", "csc_objective", "csc_get_trace", "csc_plan",
-                 "csc_kernel_launches"):
+                 "csc_kernel_launches", "csc_objective_noalloc"):
         getattr(lib, name).restype = ctypes.c_int
     if path == _build.LIB:
         _lib = lib
@@ -198,6 +200,23 @@ def csc_get_trace(h, cap: int = 1 << 16) -> dict:
     m = min(int(n.value), cap)
     return {"updates": upd[:m], "decrease": dec[:m], "t_ns": tns[:m], "n": int(n.value),
             "E_start": e0.value}
+
+
+def csc_objective_noalloc(D, X, Z, lam: float, out=None, stream=None) -> float:
+    """E(Z) through the allocation-free entry point; D, X, Z must be CUDA tensors.
+    ``out`` may be a one-element float64 CUDA tensor to receive E on the device."""
+    K, P, L = (int(x) for x in D.shape)
+    if out is None:
+        v = ctypes.c_double(0.0)
+        _check(load().csc_objective_noalloc(_ptr(D), K, P, L, _ptr(X), int(X.shape[1]), _ptr(Z),
+                                            float(lam), ctypes.addressof(v), _stream(stream)))
+        return v.value
+    import torch
+    if out.dtype != torch.float64 or out.numel() != 1 or not out.is_cuda:
+        raise TypeError("out must be a one-element float64 CUDA tensor")
+    _check(load().csc_objective_noalloc(_ptr(D), K, P, L, _ptr(X), int(X.shape[1]), _ptr(Z),
+                                        float(lam), out.data_ptr(), _stream(stream)))
+    return float(out.item())
 
 
 def csc_kernel_launches(h) -> int:

@@ -124,6 +124,18 @@ cudaError_t grow(T **p, size_t *cap, size_t n)
 
 }  // namespace
 
+// Error recording for entry points defined in other translation units.
+int csc_record_error(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
 struct csc_handle_s {
     int device = 0;
     cudaStream_t stream = nullptr;
