@@ -147,14 +147,15 @@ struct csc_handle_s {
     bool initialized = false;
     int64_t T = 0, Tz = 0;
     double lambda = 0.0, lambda_max = 0.0;
-    float *X = nullptr, *beta = nullptr, *beta0 = nullptr, *Z = nullptr;
-    size_t cap_X = 0, cap_beta = 0, cap_beta0 = 0, cap_Z = 0;
+    // r = beta - ||D_k||^2 Z, the form of beta the kernels keep (csc_internal.cuh)
+    float *X = nullptr, *r = nullptr, *beta0 = nullptr, *Z = nullptr;
+    size_t cap_X = 0, cap_r = 0, cap_beta0 = 0, cap_Z = 0;
     double *partials = nullptr;
     size_t cap_partials = 0;
     unsigned char *dirty = nullptr;
     size_t cap_dirty = 0;
-    float *tmpZ = nullptr;
-    size_t cap_tmpZ = 0;
+    float *tmpZ = nullptr, *tmpB = nullptr;
+    size_t cap_tmpZ = 0, cap_tmpB = 0;
     Scratch *sc = nullptr;
     Poll *poll = nullptr;  // pinned
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -210,12 +211,13 @@ int csc_destroy(csc_handle_t h)
     cudaFree(h->C);
     cudaFree(h->norms);
     cudaFree(h->X);
-    cudaFree(h->beta);
+    cudaFree(h->r);
     cudaFree(h->beta0);
     cudaFree(h->Z);
     cudaFree(h->partials);
     cudaFree(h->dirty);
     cudaFree(h->tmpZ);
+    cudaFree(h->tmpB);
     cudaFree(h->sc);
     if (h->poll)
         cudaFreeHost(h->poll);
@@ -309,7 +311,7 @@ int csc_init(csc_handle_t h, const float *X, int64_t T, double lambda, const flo
     cudaStream_t s = h->stream;
     const size_t nz = (size_t)h->K * Tz;
     CSC_CUDA(grow(&h->X, &h->cap_X, (size_t)h->P * T));
-    CSC_CUDA(grow(&h->beta, &h->cap_beta, nz));
+    CSC_CUDA(grow(&h->r, &h->cap_r, nz));
     CSC_CUDA(grow(&h->beta0, &h->cap_beta0, nz));
     CSC_CUDA(grow(&h->Z, &h->cap_Z, nz));
     CSC_CUDA(grow(&h->partials, &h->cap_partials, 2 * (size_t)objective_blocks(T)));
@@ -321,12 +323,12 @@ int csc_init(csc_handle_t h, const float *X, int64_t T, double lambda, const flo
         h->launches += 1;
         CSC_CUDA(copy_in(h->Z, Z0, sizeof(float) * nz, s));
         CSC_CUDA(cudaMemsetAsync(h->sc->red, 0, sizeof(h->sc->red), s));
-        CSC_CUDA(cudaMemcpyAsync(h->beta, h->beta0, sizeof(float) * nz, cudaMemcpyDeviceToDevice, s));
-        CSC_CUDA(launch_resync(h->beta0, h->beta, h->Z, h->C, h->norms, h->K, h->L, Tz, lambda,
+        CSC_CUDA(cudaMemcpyAsync(h->r, h->beta0, sizeof(float) * nz, cudaMemcpyDeviceToDevice, s));
+        CSC_CUDA(launch_resync(h->beta0, h->r, h->Z, h->C, h->norms, h->K, h->L, Tz, lambda,
                                (float)lambda, 1, h->sc->red, s));
     } else {
         CSC_CUDA(cudaMemsetAsync(h->Z, 0, sizeof(float) * nz, s));
-        CSC_CUDA(cudaMemcpyAsync(h->beta, h->beta0, sizeof(float) * nz, cudaMemcpyDeviceToDevice, s));
+        CSC_CUDA(cudaMemcpyAsync(h->r, h->beta0, sizeof(float) * nz, cudaMemcpyDeviceToDevice, s));
     }
     unsigned bits = 0;
     CSC_CUDA(cudaMemcpyAsync(&bits, &h->sc->lmax_bits, sizeof bits, cudaMemcpyDeviceToHost, s));
@@ -400,7 +402,7 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
     h->launches += 3;
 
     PhaseParams pp;
-    pp.beta = h->beta;
+    pp.r = h->r;
     pp.Z = h->Z;
     pp.C = h->C;
     pp.norms = h->norms;
@@ -419,13 +421,11 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
     pp.L = h->L;
     pp.u = h->opts.updates_per_visit ? h->opts.updates_per_visit : kDefaultMaxVisit;
     pp.lam = (float)h->lambda;
-    pp.tol = (float)tol;
-    {
-        const int64_t wmax = (Tz + M - 1) / M;
-        const int64_t wt = wmax + 2 * (int64_t)(h->L - 1);
-        pp.wt_max = (int)(wt > Tz ? Tz : wt);
-        pp.w_max = (int)wmax;
-    }
+    // CD runs to tol/2 and a resync accepts at tol: coordinates left just under
+    // the inner tolerance then stay under tol after the exact FP64 refresh,
+    // instead of bouncing back above it round after round
+    pp.tol = (float)(max_resyncs > 0 ? 0.5 * tol : tol);
+    pp.w_max = (int)((Tz + M - 1) / M);
 
     int status = CSC_OK;
     bool converged = false, report_fresh = false;
@@ -493,7 +493,7 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
             break;
         }
         CSC_CUDA(cudaMemsetAsync(sc->red, 0, sizeof(sc->red), s));
-        CSC_CUDA(launch_resync(h->beta0, h->beta, h->Z, h->C, h->norms, h->K, h->L, Tz,
+        CSC_CUDA(launch_resync(h->beta0, h->r, h->Z, h->C, h->norms, h->K, h->L, Tz,
                                h->lambda, (float)h->lambda, 1, sc->red, s));
         h->launches += 1;
         unsigned long long red[8];
@@ -514,7 +514,7 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
     if (!report_fresh) {
         // optimality report against a fresh FP64 beta, leaving beta unchanged
         CSC_CUDA(cudaMemsetAsync(sc->red, 0, sizeof(sc->red), s));
-        CSC_CUDA(launch_resync(h->beta0, h->beta, h->Z, h->C, h->norms, h->K, h->L, Tz,
+        CSC_CUDA(launch_resync(h->beta0, h->r, h->Z, h->C, h->norms, h->K, h->L, Tz,
                                h->lambda, (float)h->lambda, 0, sc->red, s));
         h->launches += 1;
     }
@@ -576,7 +576,17 @@ int csc_get_beta(csc_handle_t h, float *beta_out)
     if (!h->initialized)
         return fail(CSC_ESTATE, "csc_get_beta: call csc_init first");
     cudaSetDevice(h->device);
-    CSC_CUDA(copy_out(beta_out, h->beta, sizeof(float) * h->K * h->Tz, h->stream));
+    const size_t nz = (size_t)h->K * h->Tz;
+    // beta = r + ||D_k||^2 Z (the kernels keep r)
+    if (is_device_pointer(beta_out)) {
+        CSC_CUDA(launch_beta_from_r(h->r, h->Z, h->norms, h->K, h->Tz, beta_out, h->stream));
+    } else {
+        CSC_CUDA(grow(&h->tmpB, &h->cap_tmpB, nz));
+        CSC_CUDA(launch_beta_from_r(h->r, h->Z, h->norms, h->K, h->Tz, h->tmpB, h->stream));
+        CSC_CUDA(cudaMemcpyAsync(beta_out, h->tmpB, sizeof(float) * nz, cudaMemcpyDeviceToHost,
+                                 h->stream));
+    }
+    h->launches += 1;
     CSC_CUDA(cudaStreamSynchronize(h->stream));
     return CSC_OK;
 }

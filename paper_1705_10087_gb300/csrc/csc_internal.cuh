@@ -34,13 +34,41 @@ __device__ __forceinline__ double soft_d(double u, double lam)
     return a > 0.0 ? copysign(a, u) : 0.0;
 }
 
-// Smallest |Z' - Z| that the FP32 state resolves at a coordinate: Z' is
-// Sh(beta)/n computed from a float beta, so changes under about four ulps of
-// beta (2^-21 |beta| / n) are rounding noise.  Coordinates below it count as
-// converged (max(tol, floor) is the effective stopping threshold).
-__device__ __forceinline__ float resolution_floor(float beta, float n)
+// The solver keeps, instead of beta, r = beta - ||D_k||^2 Z: the correlation
+// of each atom with the full residual X - sum Z*D (the beta of Sec. 2.1 with
+// the coordinate's own term kept).  At the optimum |r| <= lambda everywhere,
+// so r is small exactly where beta is large (active atoms) and its float32
+// rounding is up to |beta|/lambda times finer.  Eq. beta_up becomes
+// r_k[t] -= S_{k,k0}[t-t0] dZ for every (k,t), own coordinate included.
+//
+// coord_step: the coordinate optimum of Eq. pb_coord for one coordinate held
+// as (r, z): Z' = Sh(r + n z, lambda) / n.  While Z' keeps the sign of z the
+// change is Z' - z = (r - lambda sign z) / n, evaluated without forming
+// r + n z (no cancellation).  Returns the change actually representable,
+// fl(z + d) - z, in *delta and the new value in *znew; the change is reported
+// as 0 when it is below the float32 resolution of the pair (about four ulps
+// of r/n plus two ulps of z), where updates are rounding noise.
+__device__ __forceinline__ void coord_step(float r, float z, float n, float rn, float lam,
+                                           float *znew, float *delta)
 {
-    return fabsf(beta) * 4.76837158203125e-07f / n;
+    float d;
+    if (z == 0.f) {
+        d = soft_f(r, lam) * rn;
+    } else {
+        const float s = z > 0.f ? 1.f : -1.f;
+        const float b = fmaf(n, z, r);
+        d = b * s > lam ? (r - lam * s) * rn : soft_f(b, lam) * rn - z;
+    }
+    const float zn = z + d;
+    const float dd = zn - z;
+    const float floor_ = fabsf(r) * 4.76837158203125e-07f * rn + fabsf(z) * 2.384185791015625e-07f;
+    if (fabsf(dd) < floor_) {
+        *znew = z;
+        *delta = 0.f;
+    } else {
+        *znew = zn;
+        *delta = dd;
+    }
 }
 
 __device__ __forceinline__ unsigned long long globaltimer_ns()
@@ -67,7 +95,7 @@ struct KahanF {
 
 // Parameters of one phase launch (see kernel_phase.cu).
 struct PhaseParams {
-    float *beta;               // [K][Tz]
+    float *r;                  // r = beta - n Z, [K][Tz]
     float *Z;                  // [K][Tz]
     const float *C;            // DtD [K][K][W2]
     const float *norms;        // [K]
@@ -85,7 +113,7 @@ struct PhaseParams {
     int g_round;  // first launch index of the current CD round
     int u;        // cap on updates per visit
     float lam, tol;
-    int wt_max, w_max;  // tile extents used for the shared-memory layout
+    int w_max;  // widest segment (shared-memory layout)
 };
 
 struct PhaseConfig {
@@ -102,13 +130,18 @@ cudaError_t launch_dtd(const float *D, int K, int P, int L, float *C, float *nor
 cudaError_t launch_dtx(const float *D, const float *X, int K, int P, int L, int64_t T,
                        float *beta0, unsigned int *absmax_bits, cudaStream_t s);
 
-// FP64 re-synchronisation: beta = fp32(beta0 - sum_{(l,t')!=(k,t)} S Z) and the
-// optimality report.  red[0..4] receive (as non-negative double bit patterns
-// for atomicMax): drift, zero_excess, nonzero_gap, max_delta_z (FP64), and
-// max |Delta Z| computed in FP32 from the rounded beta.
-cudaError_t launch_resync(const float *beta0, float *beta, const float *Z, const float *C,
+// FP64 re-synchronisation of r with its definition, r = D~*X - sum_{l,t'} S Z
+// (beta0 = D~*X), rounded once to float, and the optimality report.
+// red[0..4] receive (as non-negative double bit patterns for atomicMax): the
+// drift max |r_old - r_fp64|, zero_excess, nonzero_gap, max_delta_z (FP64
+// beta = r + n Z), and max |Delta Z| of coord_step on the float state.
+cudaError_t launch_resync(const float *beta0, float *r, const float *Z, const float *C,
                           const float *norms, int K, int L, int64_t Tz, double lam,
-                          float lam_f, int write_beta, unsigned long long *red, cudaStream_t s);
+                          float lam_f, int write_r, unsigned long long *red, cudaStream_t s);
+
+// out = r + n Z (beta of Sec. 2.1) in float.
+cudaError_t launch_beta_from_r(const float *r, const float *Z, const float *norms, int K,
+                               int64_t Tz, float *out, cudaStream_t s);
 
 // FP64 objective E(Z) (Eq. sparse_code) into *out, via per-block partials.
 int objective_blocks(int64_t T);

@@ -4,28 +4,39 @@
 // sending (k0, t0, Delta Z) to its neighbours when an update lands within L
 // of the border (Sec. 2.2, Fig. DCP).  Here a thread block is a worker: in
 // phase p the blocks own the segments m == p (mod c) and every other segment
-// is idle.  c is such that the beta windows [s_m-L+1, e_m+L-1) of co-active
-// segments never meet, so a block may write Eq. beta_up straight into the
-// idle neighbours' beta (the paper's message) and every phase equals a
-// sequential run of its segments (Alg. 3 restricted to one phase).
+// is idle.  c is such that the windows [s_m-L+1, e_m+L-1) of co-active
+// segments never meet, so a block may apply Eq. beta_up straight to the idle
+// neighbours' state (the paper's message, here a fire-and-forget reduction
+// into their r in global memory) and every phase equals a sequential run of
+// its segments (Alg. 3 restricted to one phase).
 //
+// State: r = beta - ||D_k||^2 Z and Z (see coord_step in csc_internal.cuh).
 // Per visit a block
-//   1. loads beta on its window and Z on its segment into shared memory
-//      (or works on global memory when the tile does not fit),
+//   1. loads r and Z of its own segment into shared memory (or works on
+//      global memory when the segment does not fit),
 //   2. keeps, per owned column t, the best coordinate over k of
-//      |Delta Z_k[t]| = |Z_k[t] - Sh(beta_k[t], lambda)/||D_k||^2| (Eq. pb_coord)
-//      as a 64-bit key (|Delta Z| bits << 32 | ~(k*Tz + t)): the max key is
-//      the largest |Delta Z| with ties to the lowest flat index,
-//   3. repeats: block argmax (warp shuffle max, one barrier), stop if the
-//      best |Delta Z| < tol (Alg. 1 stopping rule) or after u updates,
-//      else Z_k0[t0] <- Z' and beta_k[t] -= S_{k,k0}[t-t0] (Z' - Z_old) on
-//      the window (Eq. beta_up with the sign fixed by the beta definition),
-//      re-evaluating only the columns of the window,
-//   4. writes the tile back, marks the neighbours it spilled into as dirty
-//      and adds its count and its objective decrease (Prop. A.1) to the
+//      |Delta Z_k[t]| = |Sh(beta_k[t], lambda)/||D_k||^2 - Z_k[t]| (Eq. pb_coord,
+//      evaluated from r by coord_step) as a 64-bit key
+//      (|Delta Z| bits << 32 | ~(k*Tz + t)): the max key is the largest
+//      |Delta Z| with ties to the lowest flat index,
+//   3. repeats: block argmax (warp max + one barrier), stop if the best
+//      |Delta Z| < tol (Alg. 1 stopping rule) or after u updates, else
+//      Z_k0[t0] <- Z' and r_k[t] -= S_{k,k0}[t-t0] (Z' - Z_old) for every k
+//      and t in [t0-L+1, t0+L-1] (Eq. beta_up, sign fixed by the beta
+//      definition, written for r); own columns are updated in shared memory
+//      and re-evaluated, the others (idle neighbours) by atomicAdd,
+//   4. writes its segment back, marks the neighbours it spilled into as
+//      dirty and adds its count and objective decrease (Prop. A.1) to the
 //      per-launch trace.
+// Thread i owns the segment columns jj == i (mod blockDim) and handles, in an
+// update, the window column t with (t - s) == i (mod blockDim); blockDim >=
+// 2L-1, so the 2L-1 window columns go to distinct threads and each own
+// column is only ever touched by its owner.
 // A segment that ended its last visit converged and was not spilled into
-// since is clean and is skipped: beta and Z on it have not changed.
+// since is clean and is skipped: r and Z on it have not changed.
+#include <algorithm>
+#include <type_traits>
+
 #include "csc_internal.cuh"
 
 namespace csc {
@@ -33,6 +44,7 @@ namespace csc {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kCoefBatch = 16;         // DtD coefficients loaded per round trip
 
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
 {
@@ -43,14 +55,60 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
     return ((unsigned long long)hmax << 32) | lmax;
 }
 
-template <bool SMEM>
-__global__ void __launch_bounds__(1024) phase_kernel(PhaseParams pp)
+// Shared-memory layout of a block, in bytes from the start (16-byte aligned
+// pieces).  w = widest segment; with smem the segment's r and Z are staged.
+struct Layout {
+    size_t key, slot_key, cz, cd, ck, slot_z, slot_d, slot_k, slot_j, nrm, rnrm, r, z, total;
+    __host__ __device__ Layout(int K, int w, bool smem)
+    {
+        size_t o = 0;
+        key = o;
+        o = up(o + 8 * (size_t)w);
+        slot_key = o;
+        o = up(o + 8 * 64);
+        cz = o;
+        o = up(o + 4 * (size_t)w);
+        cd = o;
+        o = up(o + 4 * (size_t)w);
+        ck = o;
+        o = up(o + 4 * (size_t)w);
+        slot_z = o;
+        o = up(o + 4 * 64);
+        slot_d = o;
+        o = up(o + 4 * 64);
+        slot_k = o;
+        o = up(o + 4 * 64);
+        slot_j = o;
+        o = up(o + 4 * 64);
+        nrm = o;
+        o = up(o + 4 * (size_t)K);
+        rnrm = o;
+        o = up(o + 4 * (size_t)K);
+        r = o;
+        if (smem)
+            o = up(o + 4 * (size_t)K * w);
+        z = o;
+        if (smem)
+            o = up(o + 4 * (size_t)K * w);
+        total = o;
+    }
+    __host__ __device__ static size_t up(size_t x) { return (x + 15) & ~(size_t)15; }
+};
+
+// MAXT: the block size the instantiation is launched with.  Blocks of 128
+// threads (atoms up to 64 samples) are compiled for 5 resident blocks per SM,
+// so that the several hundred co-active segments of a phase fit in one wave;
+// larger blocks get the full register file.
+template <bool SMEM, int MAXT>
+__global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseParams pp)
 {
+    using Idx = typename std::conditional<SMEM, int, int64_t>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_go;
+    __shared__ double s_dec[32];
 
     // ---- early exits, decided by one thread so the block stays uniform ----
     // (total is being incremented by other blocks of this launch)
-    __shared__ int s_go;
     const int m = pp.p + pp.c * (int)blockIdx.x;  // < M by the grid size
     if (threadIdx.x == 0) {
         int go = 1;
@@ -60,10 +118,10 @@ __global__ void __launch_bounds__(1024) phase_kernel(PhaseParams pp)
             go = 0;  // out of budget: not a converged sweep, so done stays unset
         } else if (pp.g - pp.g_round >= pp.c) {
             // a full sweep (the previous c launches of this round) applied nothing
-            long long s = 0;
+            long long sum = 0;
             for (int j = pp.g - pp.c; j < pp.g; j++)
-                s += *(volatile long long *)&pp.upd[j & (kPhaseRing - 1)];
-            if (s == 0) {
+                sum += *(volatile long long *)&pp.upd[j & (kPhaseRing - 1)];
+            if (sum == 0) {
                 if (blockIdx.x == 0)
                     *(volatile int *)pp.done = pp.g + 1;
                 go = 0;
@@ -81,90 +139,83 @@ __global__ void __launch_bounds__(1024) phase_kernel(PhaseParams pp)
     const int64_t Tz = pp.Tz;
     const int64_t s = seg_start(Tz, pp.M, m), e = seg_start(Tz, pp.M, m + 1);
     const int w = (int)(e - s);
-    const int64_t ts = s - (L - 1) > 0 ? s - (L - 1) : 0;
-    const int64_t te = e + (L - 1) < Tz ? e + (L - 1) : Tz;
-    const int Wt = (int)(te - ts);
-    const int j0 = (int)(s - ts);  // tile column of the segment's first sample
-    const int tid = threadIdx.x, B = blockDim.x, lane = tid & 31, warp = tid >> 5;
-    const int nwarps = B >> 5;
-
-    // ---- shared-memory layout ------------------------------------------
-    unsigned char *ptr = smem_raw;
-    unsigned long long *ckey = reinterpret_cast<unsigned long long *>(ptr);
-    ptr += sizeof(unsigned long long) * pp.wt_max;
-    unsigned long long *wkey = reinterpret_cast<unsigned long long *>(ptr);  // [2][32]
-    ptr += sizeof(unsigned long long) * 64;
-    float *cz = reinterpret_cast<float *>(ptr);
-    ptr += sizeof(float) * pp.wt_max;
-    float *cd = reinterpret_cast<float *>(ptr);
-    ptr += sizeof(float) * pp.wt_max;
-    float *wz = reinterpret_cast<float *>(ptr);  // [2][32]
-    ptr += sizeof(float) * 64;
-    float *wd = reinterpret_cast<float *>(ptr);  // [2][32]
-    ptr += sizeof(float) * 64;
-    float *nrm = reinterpret_cast<float *>(ptr);  // [K]
-    ptr += sizeof(float) * ((K + 3) & ~3);
-
-    float *bb;  // beta on the window: bb[k * bstride + j], j tile column
-    float *zb;  // Z on the segment:   zb[k * zstride + j - j0]
-    int64_t bstride, zstride;
-    if (SMEM) {
-        bb = reinterpret_cast<float *>(ptr);
-        zb = bb + (size_t)K * pp.wt_max;
-        bstride = pp.wt_max;
-        zstride = pp.w_max;
-        for (int k = 0; k < K; k++) {
-            const float *src = pp.beta + (int64_t)k * Tz + ts;
-            for (int j = tid; j < Wt; j += B)
-                bb[(int64_t)k * bstride + j] = src[j];
-            const float *zsrc = pp.Z + (int64_t)k * Tz + s;
-            for (int j = tid; j < w; j += B)
-                zb[(int64_t)k * zstride + j] = zsrc[j];
-        }
-    } else {
-        bb = pp.beta + ts;
-        zb = pp.Z + s;
-        bstride = Tz;
-        zstride = Tz;
-    }
-    for (int k = tid; k < K; k += B)
-        nrm[k] = pp.norms[k];
-    __syncthreads();
-
+    // blockDim == MAXT, a power of two >= 2L-1 (see phase_config)
+    constexpr int B = MAXT;
+    constexpr int nwarps = B >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float lam = pp.lam, tol = pp.tol;
 
-    // best coordinate of tile column j (owned segment column) over k
-    auto col_eval = [&](int j) {
-        const int jj = j - j0;
+    const Layout lay(K, pp.w_max, SMEM);
+    unsigned long long *ckey = reinterpret_cast<unsigned long long *>(smem_raw + lay.key);
+    unsigned long long *slot_key = reinterpret_cast<unsigned long long *>(smem_raw + lay.slot_key);
+    float *cz = reinterpret_cast<float *>(smem_raw + lay.cz);
+    float *cd = reinterpret_cast<float *>(smem_raw + lay.cd);
+    int *ck = reinterpret_cast<int *>(smem_raw + lay.ck);
+    float *slot_z = reinterpret_cast<float *>(smem_raw + lay.slot_z);
+    float *slot_d = reinterpret_cast<float *>(smem_raw + lay.slot_d);
+    int *slot_k = reinterpret_cast<int *>(smem_raw + lay.slot_k);
+    int *slot_j = reinterpret_cast<int *>(smem_raw + lay.slot_j);
+    float *nrm = reinterpret_cast<float *>(smem_raw + lay.nrm);    // ||D_k||^2
+    float *rnrm = reinterpret_cast<float *>(smem_raw + lay.rnrm);  // 1 / ||D_k||^2
+
+    // own segment: rs[k * stride + jj], zs[k * stride + jj], jj = t - s
+    float *rs;
+    float *zs;
+    Idx stride;
+    if (SMEM) {
+        rs = reinterpret_cast<float *>(smem_raw + lay.r);
+        zs = reinterpret_cast<float *>(smem_raw + lay.z);
+        stride = (Idx)pp.w_max;
+        for (int k = 0; k < K; k++) {
+            const float *rsrc = pp.r + (int64_t)k * Tz + s;
+            const float *zsrc = pp.Z + (int64_t)k * Tz + s;
+            for (int jj = tid; jj < w; jj += B) {
+                rs[k * stride + jj] = rsrc[jj];
+                zs[k * stride + jj] = zsrc[jj];
+            }
+        }
+    } else {
+        rs = pp.r + s;
+        zs = pp.Z + s;
+        stride = (Idx)Tz;
+    }
+    for (int k = tid; k < K; k += B) {
+        nrm[k] = pp.norms[k];
+        rnrm[k] = __frcp_rn(pp.norms[k]);
+    }
+    __syncthreads();
+
+    // best coordinate of own column jj over k
+    auto col_eval = [&](int jj) {
+        const float *rc = rs + jj;
+        const float *zc = zs + jj;
         float best = -1.f, bz = 0.f, bdz = 0.f;
         int bk = 0;
+#pragma unroll 5
         for (int k = 0; k < K; k++) {
-            const float b = bb[(int64_t)k * bstride + j];
-            const float z = zb[(int64_t)k * zstride + jj];
-            const float zp = __fdiv_rn(soft_f(b, lam), nrm[k]);
-            const float d = zp - z;
-            // below the FP32 resolution of Z' (a few ulps of beta) the change is
-            // rounding noise, not descent: count the coordinate as converged
-            const float ad = fabsf(d) >= resolution_floor(b, nrm[k]) ? fabsf(d) : 0.f;
+            const float r = rc[k * stride], z = zc[k * stride];
+            // inactive and inside the threshold: Z' = Sh(r, lam)/n = 0 = z exactly
+            if (z == 0.f && fabsf(r) <= lam)
+                continue;
+            float zn, d;
+            coord_step(r, z, nrm[k], rnrm[k], lam, &zn, &d);
+            const float ad = fabsf(d);
             if (ad > best) {
                 best = ad;
                 bk = k;
-                bz = zp;
+                bz = zn;
                 bdz = d;
             }
         }
-        const unsigned flat = (unsigned)((int64_t)bk * Tz + (ts + j));
-        ckey[j] = ((unsigned long long)__float_as_uint(best) << 32) | (unsigned)(~flat);
-        cz[j] = bz;
-        cd[j] = bdz;
+        const unsigned flat = (unsigned)bk * (unsigned)Tz + (unsigned)(s + jj);
+        ckey[jj] = best > 0.f ? ((unsigned long long)__float_as_uint(best) << 32) | (unsigned)(~flat)
+                              : 0ull;
+        cz[jj] = bz;
+        cd[jj] = bdz;
+        ck[jj] = bk;
     };
-
-    for (int j = tid; j < Wt; j += B) {
-        if (j >= j0 && j < j0 + w)
-            col_eval(j);
-        else
-            ckey[j] = 0ull;
-    }
+    for (int jj = tid; jj < w; jj += B)
+        col_eval(jj);
     // (no barrier needed: each thread reads back only its own columns)
 
     int buf = 0, nupd = 0;
@@ -174,32 +225,31 @@ __global__ void __launch_bounds__(1024) phase_kernel(PhaseParams pp)
     for (int it = 0;; it++) {
         // ---- block argmax of the cached column keys ----------------------
         unsigned long long my = 0ull;
-        float mz = 0.f, md = 0.f;
-        for (int j = tid; j < Wt; j += B) {
-            const unsigned long long kk = ckey[j];
+        int myj = 0;
+        for (int jj = tid; jj < w; jj += B) {
+            const unsigned long long kk = ckey[jj];
             if (kk > my) {
                 my = kk;
-                mz = cz[j];
-                md = cd[j];
+                myj = jj;
             }
         }
         const unsigned long long wm = warp_max_u64(my);
-        const int src = __ffs(__ballot_sync(kFull, my == wm)) - 1;
-        const float wzv = __shfl_sync(kFull, mz, src), wdv = __shfl_sync(kFull, md, src);
-        if (lane == 0) {
-            wkey[buf * 32 + warp] = wm;
-            wz[buf * 32 + warp] = wzv;
-            wd[buf * 32 + warp] = wdv;
+        const unsigned win = __ballot_sync(kFull, my == wm);
+        if (lane == __ffs(win) - 1) {
+            slot_key[buf * 32 + warp] = wm;
+            slot_z[buf * 32 + warp] = cz[myj];
+            slot_d[buf * 32 + warp] = cd[myj];
+            slot_k[buf * 32 + warp] = ck[myj];
+            slot_j[buf * 32 + warp] = myj;
         }
         __syncthreads();
         unsigned long long bk = 0ull;
-        float znew = 0.f, delta = 0.f;
+        int bw = 0;
         for (int i = 0; i < nwarps; i++) {
-            const unsigned long long kk = wkey[buf * 32 + i];
+            const unsigned long long kk = slot_key[buf * 32 + i];
             if (kk > bk) {
                 bk = kk;
-                znew = wz[buf * 32 + i];
-                delta = wd[buf * 32 + i];
+                bw = i;
             }
         }
         const float adz = __uint_as_float((unsigned)(bk >> 32));
@@ -209,36 +259,53 @@ __global__ void __launch_bounds__(1024) phase_kernel(PhaseParams pp)
             capped = true;
             break;
         }
-        const unsigned flat = ~(unsigned)(bk & 0xffffffffu);
-        const int k0 = (int)(flat / (uint64_t)Tz);
-        const int64_t t0 = (int64_t)flat - (int64_t)k0 * Tz;
+        const float znew = slot_z[buf * 32 + bw], delta = slot_d[buf * 32 + bw];
+        const int k0 = slot_k[buf * 32 + bw];
+        const int64_t t0 = s + slot_j[buf * 32 + bw];
 
-        if (tid == 0) {
-            // Prop. A.1: E(Z) - E(Z') = n/2 (z^2 - u^2) - beta (z - u) + lam (|z| - |u|)
-            const double n = nrm[k0], u = znew, z = (double)znew - (double)delta;
-            const double b = bb[(int64_t)k0 * bstride + (t0 - ts)];
-            decrease += 0.5 * n * (z * z - u * u) - b * (z - u) + (double)lam * (fabs(z) - fabs(u));
-        }
-
-        // ---- Eq. beta_up on the window, re-evaluate its columns ---------
-        const float *Ck0 = pp.C + (int64_t)k0 * K * W2;
-        const int64_t wlo = t0 - (L - 1) > ts ? t0 - (L - 1) : ts;
-        const int64_t whi = t0 + (L - 1) < te - 1 ? t0 + (L - 1) : te - 1;
-        for (int j = tid; j < Wt; j += B) {
-            const int64_t t = ts + j;
-            if (t < wlo || t > whi)
-                continue;
-            const int sidx = (int)(t - t0) + (L - 1);
-            for (int k = 0; k < K; k++) {
-                if (k == k0 && t == t0)
-                    continue;
-                float *bp = bb + (int64_t)k * bstride + j;
-                *bp = *bp - __ldg(Ck0 + (int64_t)k * W2 + sidx) * delta;
+        // ---- Eq. beta_up (r form) on the window -------------------------
+        const int64_t tlo = t0 - (L - 1);
+        const int off = (tid - (int)(tlo - s)) & (B - 1);  // window position of this thread
+        const int64_t t = tlo + off;
+        if (off < W2 && t >= 0 && t < Tz) {
+            const float *Ck0 = pp.C + ((int64_t)k0 * K) * W2 + off;
+            const bool own = t >= s && t < e;
+            const int jj = (int)(t - s);
+            if (t == t0) {
+                // Prop. A.1 from the owner's r before this update touches it:
+                // E(Z) - E(Z') = dZ (r - n dZ / 2) + lam (|z| - |u|), dZ = u - z
+                const double n = nrm[k0], d = delta, u = znew, z = (double)znew - d;
+                const double r0 = rs[k0 * stride + jj];
+                decrease += d * (r0 - 0.5 * n * d) + (double)lam * (fabs(z) - fabs(u));
             }
-            if (t == t0)
-                zb[(int64_t)k0 * zstride + (j - j0)] = znew;
-            if (j >= j0 && j < j0 + w)
-                col_eval(j);
+            for (int kb = 0; kb < K; kb += kCoefBatch) {
+                // the column's coefficients S_{k,k0}[t-t0] first: independent
+                // loads, one L2 round trip per kCoefBatch atoms
+                float cv[kCoefBatch];
+#pragma unroll
+                for (int i = 0; i < kCoefBatch; i++)
+                    cv[i] = kb + i < K ? __ldg(Ck0 + (int64_t)(kb + i) * W2) : 0.f;
+                if (own) {
+#pragma unroll
+                    for (int i = 0; i < kCoefBatch; i++)
+                        if (kb + i < K) {
+                            float *rp = rs + (kb + i) * stride + jj;
+                            *rp = fmaf(-cv[i], delta, *rp);
+                        }
+                } else {
+                    // an idle neighbour's column: no other block touches it this phase
+                    float *rg = pp.r + t;
+#pragma unroll
+                    for (int i = 0; i < kCoefBatch; i++)
+                        if (kb + i < K)
+                            atomicAdd(rg + (int64_t)(kb + i) * Tz, -cv[i] * delta);
+                }
+            }
+            if (own) {
+                if (t == t0)
+                    zs[k0 * stride + jj] = znew;
+                col_eval(jj);
+            }
         }
         nupd++;
         tmin = t0 < tmin ? t0 : tmin;
@@ -249,25 +316,35 @@ __global__ void __launch_bounds__(1024) phase_kernel(PhaseParams pp)
     // ---- write back, spill bookkeeping, trace ---------------------------
     if (SMEM && nupd > 0) {
         for (int k = 0; k < K; k++) {
-            float *dst = pp.beta + (int64_t)k * Tz + ts;
-            for (int j = tid; j < Wt; j += B)
-                dst[j] = bb[(int64_t)k * bstride + j];
+            float *rdst = pp.r + (int64_t)k * Tz + s;
             float *zdst = pp.Z + (int64_t)k * Tz + s;
-            for (int j = tid; j < w; j += B)
-                zdst[j] = zb[(int64_t)k * zstride + j];
+            for (int jj = tid; jj < w; jj += B) {
+                rdst[jj] = rs[k * stride + jj];
+                zdst[jj] = zs[k * stride + jj];
+            }
         }
     }
+    // objective decrease of the visit: sum over the threads that owned t0
+    for (int o = 16; o > 0; o >>= 1)
+        decrease += __shfl_xor_sync(kFull, decrease, o);
+    if (lane == 0)
+        s_dec[warp] = decrease;
+    __syncthreads();
     if (tid == 0) {
+        decrease = 0.0;
+        for (int i = 0; i < nwarps; i++)
+            decrease += s_dec[i];
         pp.dirty[m] = capped ? 1 : 0;
         if (nupd > 0) {
-            // neighbours whose beta changed: segments meeting [tmin-L+1, tmax+L-1]
+            // neighbours whose r changed: segments meeting [tmin-L+1, tmax+L-1]
             const int64_t lo = tmin - (L - 1), hi = tmax + (L - 1);
             for (int mm = m - 1; mm >= 0 && seg_start(Tz, pp.M, mm + 1) > lo; mm--)
                 pp.dirty[mm] = 1;
             for (int mm = m + 1; mm < pp.M && seg_start(Tz, pp.M, mm) <= hi; mm++)
                 pp.dirty[mm] = 1;
             const int slot = pp.g & (kPhaseRing - 1);
-            atomicAdd(reinterpret_cast<unsigned long long *>(&pp.upd[slot]), (unsigned long long)nupd);
+            atomicAdd(reinterpret_cast<unsigned long long *>(&pp.upd[slot]),
+                      (unsigned long long)nupd);
             atomicAdd(reinterpret_cast<unsigned long long *>(pp.total), (unsigned long long)nupd);
             atomicAdd(reinterpret_cast<unsigned long long *>(pp.visits), 1ull);
             atomicAdd(&pp.dec[slot], decrease);
@@ -276,28 +353,19 @@ __global__ void __launch_bounds__(1024) phase_kernel(PhaseParams pp)
     }
 }
 
-size_t smem_bytes(int K, int wt_max, int w_max, bool tile)
-{
-    size_t b = sizeof(unsigned long long) * ((size_t)wt_max + 64) +
-               sizeof(float) * (2 * (size_t)wt_max + 128 + (((size_t)K + 3) & ~(size_t)3));
-    if (tile)
-        b += sizeof(float) * (size_t)K * ((size_t)wt_max + w_max);
-    return b;
-}
-
 }  // namespace
 
 PhaseConfig phase_config(int K, int L, int64_t Tz, int M)
 {
     const int64_t wmax = (Tz + M - 1) / M;  // widest segment
-    int64_t wtmax = wmax + 2 * (int64_t)(L - 1);
-    if (wtmax > Tz)
-        wtmax = Tz;
     PhaseConfig cfg;
-    cfg.tile_in_smem = smem_bytes(K, (int)wtmax, (int)wmax, true) <= (size_t)kMaxSmem;
-    cfg.smem = smem_bytes(K, (int)wtmax, (int)wmax, cfg.tile_in_smem);
-    int b = (int)((wtmax + 31) / 32 * 32);
-    cfg.block = b < 1024 ? (b < 64 ? 64 : b) : 1024;
+    cfg.tile_in_smem = Layout(K, (int)wmax, true).total <= (size_t)kMaxSmem;
+    cfg.smem = Layout(K, (int)wmax, cfg.tile_in_smem).total;
+    // An update touches the 2L-1 window columns: with at least that many threads
+    // each of them goes to its own thread, however wide the segment; more threads
+    // would idle in the update and only cost registers and occupancy.  The block
+    // is a power of two (128, 512 or 1024) so that ownership is a mask.
+    cfg.block = 2 * L - 1 <= 128 ? 128 : (2 * L - 1 <= 512 ? 512 : 1024);
     return cfg;
 }
 
@@ -308,21 +376,25 @@ cudaError_t launch_phase(const PhaseParams &pp, const PhaseConfig &cfg, cudaStre
         return cudaSuccess;
     if (cfg.smem > (size_t)kMaxSmem)
         return cudaErrorInvalidConfiguration;
-    if (cfg.tile_in_smem) {
-        cudaError_t e = cudaFuncSetAttribute(phase_kernel<true>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cfg.block < 2 * pp.L - 1)
+        return cudaErrorInvalidConfiguration;  // each window column needs its own thread
+    auto go = [&](auto kern) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)cfg.smem);
         if (e != cudaSuccess)
             return e;
-        phase_kernel<true><<<active, cfg.block, cfg.smem, s>>>(pp);
-    } else {
-        cudaError_t e = cudaFuncSetAttribute(phase_kernel<false>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)cfg.smem);
-        if (e != cudaSuccess)
-            return e;
-        phase_kernel<false><<<active, cfg.block, cfg.smem, s>>>(pp);
-    }
+        kern<<<active, cfg.block, cfg.smem, s>>>(pp);
+        return cudaSuccess;
+    };
+    cudaError_t e;
+    if (cfg.block == 128)
+        e = cfg.tile_in_smem ? go(phase_kernel<true, 128>) : go(phase_kernel<false, 128>);
+    else if (cfg.block == 512)
+        e = cfg.tile_in_smem ? go(phase_kernel<true, 512>) : go(phase_kernel<false, 512>);
+    else
+        e = cfg.tile_in_smem ? go(phase_kernel<true, 1024>) : go(phase_kernel<false, 1024>);
+    if (e != cudaSuccess)
+        return e;
     return cudaGetLastError();
 }
 

@@ -1,6 +1,7 @@
 // FP64 kernels (the only FP64 arithmetic on the GPU): the periodic / final
-// re-synchronisation of beta with its definition (Sec. 2.1) and the objective
-// E(Z) of Eq. sparse_code from the explicit residual.
+// re-synchronisation of the solver state r = beta - n Z with its definition
+// (Sec. 2.1) and the objective E(Z) of Eq. sparse_code from the explicit
+// residual.
 //
 // Both exploit that Z is sparse: a block gathers the nonzeros of Z that can
 // reach its tile (compacted in a fixed order, so results are deterministic)
@@ -58,16 +59,32 @@ __device__ int compact_nonzeros(const float *__restrict__ Z, int K, int64_t Tz, 
     return base;
 }
 
+// Double-float accumulation (hi + lo, about 48 significant bits) of products
+// of floats, with error-free transformations: the rounding error of a*b is
+// fma(a, b, -p) (exact), that of hi + p is Knuth's TwoSum.  The _rn
+// intrinsics keep the compiler from contracting or reassociating them.  This
+// runs on the FP32 pipes, which GB300 has about 64 times more of than FP64.
+__device__ __forceinline__ void df_add_prod(float &hi, float &lo, float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    const float pe = __fmaf_rn(a, b, -p);
+    const float s = __fadd_rn(hi, p);
+    const float bv = __fsub_rn(s, hi);
+    const float se = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(p, bv));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(se, pe));
+}
+
 constexpr int kResyncCols = 64;   // output columns per block
 constexpr int kResyncThreads = 256;
 constexpr int kResyncGroups = kResyncThreads / kResyncCols;  // atom groups
 
 template <int KPT>
 __global__ void __launch_bounds__(kResyncThreads)
-    resync_kernel(const float *__restrict__ beta0, float *__restrict__ beta,
+    resync_kernel(const float *__restrict__ beta0, float *__restrict__ rr,
                   const float *__restrict__ Z, const float *__restrict__ C,
                   const float *__restrict__ norms, int K, int L, int64_t Tz, double lam,
-                  float lam_f, int write_beta, unsigned long long *__restrict__ red)
+                  float lam_f, int write_r, unsigned long long *__restrict__ red)
 {
     __shared__ NZ list[32 * kChunk];
     __shared__ int warp_counts[32];
@@ -78,10 +95,12 @@ __global__ void __launch_bounds__(kResyncThreads)
     const int col = tid % kResyncCols, grp = tid / kResyncCols;
     const int64_t c0 = (int64_t)blockIdx.x * kResyncCols;
     const int64_t t = c0 + col;
-    double acc[KPT];
+    float acc_hi[KPT], acc_lo[KPT];
 #pragma unroll
-    for (int i = 0; i < KPT; i++)
-        acc[i] = 0.0;
+    for (int i = 0; i < KPT; i++) {
+        acc_hi[i] = 0.f;
+        acc_lo[i] = 0.f;
+    }
 
     // nonzeros that reach [c0, c0+cols): Z columns in [c0-(L-1), c0+cols+(L-1))
     const int64_t lo = c0 - (L - 1) > 0 ? c0 - (L - 1) : 0;
@@ -96,13 +115,12 @@ __global__ void __launch_bounds__(kResyncThreads)
                 const int d = (int)(t - e.t) + (L - 1);
                 if (d < 0 || d >= W2)
                     continue;
-                const double zd = (double)e.z;
                 const float *Cl = C + (int64_t)e.k * K * W2 + d;
 #pragma unroll
                 for (int q = 0; q < KPT; q++) {
                     const int k = grp + q * kResyncGroups;
-                    if (k < K && !(k == e.k && d == L - 1))
-                        acc[q] += (double)__ldg(Cl + (int64_t)k * W2) * zd;
+                    if (k < K)
+                        df_add_prod(acc_hi[q], acc_lo[q], __ldg(Cl + (int64_t)k * W2), e.z);
                 }
             }
         }
@@ -118,24 +136,25 @@ __global__ void __launch_bounds__(kResyncThreads)
             if (k >= K)
                 continue;
             const int64_t ix = (int64_t)k * Tz + t;
-            const double b64 = (double)beta0[ix] - acc[q];
-            const float bold = beta[ix];
-            drift = fmax(drift, fabs((double)bold - b64));
-            const float b32 = (float)b64;
-            if (write_beta)
-                beta[ix] = b32;
+            const double r64 = (double)beta0[ix] - ((double)acc_hi[q] + (double)acc_lo[q]);
+            const float rold = rr[ix];
+            drift = fmax(drift, fabs((double)rold - r64));
+            const float r32 = (float)r64;
+            if (write_r)
+                rr[ix] = r32;
             const float z = Z[ix];
             const float n = norms[k];
-            const double gap = fabs((double)z - soft_d(b64, lam) / (double)n);
+            const double b64 = r64 + (double)n * (double)z;  // beta of Sec. 2.1
+            const double gap = fabs(soft_d(b64, lam) / (double)n - (double)z);
             if (z == 0.f)
                 zex = fmax(zex, fabs(b64) - lam);
             else
                 nzg = fmax(nzg, gap);
             all = fmax(all, gap);
-            const float b_used = write_beta ? b32 : bold;
-            const float d32 = fabsf(__fdiv_rn(soft_f(b_used, lam_f), n) - z);
-            if (d32 >= resolution_floor(b_used, n))
-                dz32 = fmaxf(dz32, d32);
+            // the phase kernel's own test on the float state it will see
+            float zn, d32;
+            coord_step(write_r ? r32 : rold, z, n, __frcp_rn(n), lam_f, &zn, &d32);
+            dz32 = fmaxf(dz32, fabsf(d32));
         }
     }
     // block reduce (max) and one atomic per block and quantity
@@ -272,35 +291,53 @@ __global__ void objective_final_kernel(const double *__restrict__ partials, int 
         *out = 0.5 * s[0][0] + lam * s[1][0];
 }
 
+__global__ void beta_from_r_kernel(const float *__restrict__ r, const float *__restrict__ Z,
+                                   const float *__restrict__ norms, int K, int64_t Tz,
+                                   float *__restrict__ out)
+{
+    const int64_t n = (int64_t)K * Tz;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = fmaf(norms[i / Tz], Z[i], r[i]);
+}
+
 template <int KPT>
-cudaError_t resync_launch(const float *beta0, float *beta, const float *Z, const float *C,
+cudaError_t resync_launch(const float *beta0, float *r, const float *Z, const float *C,
                           const float *norms, int K, int L, int64_t Tz, double lam, float lam_f,
-                          int write_beta, unsigned long long *red, cudaStream_t s)
+                          int write_r, unsigned long long *red, cudaStream_t s)
 {
     const unsigned grid = (unsigned)((Tz + kResyncCols - 1) / kResyncCols);
-    resync_kernel<KPT><<<grid, kResyncThreads, 0, s>>>(beta0, beta, Z, C, norms, K, L, Tz, lam,
-                                                       lam_f, write_beta, red);
+    resync_kernel<KPT><<<grid, kResyncThreads, 0, s>>>(beta0, r, Z, C, norms, K, L, Tz, lam,
+                                                       lam_f, write_r, red);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_resync(const float *beta0, float *beta, const float *Z, const float *C,
+cudaError_t launch_resync(const float *beta0, float *r, const float *Z, const float *C,
                           const float *norms, int K, int L, int64_t Tz, double lam,
-                          float lam_f, int write_beta, unsigned long long *red, cudaStream_t s)
+                          float lam_f, int write_r, unsigned long long *red, cudaStream_t s)
 {
     const int kpt = (K + kResyncGroups - 1) / kResyncGroups;
     if (kpt <= 2)
-        return resync_launch<2>(beta0, beta, Z, C, norms, K, L, Tz, lam, lam_f, write_beta, red, s);
+        return resync_launch<2>(beta0, r, Z, C, norms, K, L, Tz, lam, lam_f, write_r, red, s);
     if (kpt <= 8)
-        return resync_launch<8>(beta0, beta, Z, C, norms, K, L, Tz, lam, lam_f, write_beta, red, s);
+        return resync_launch<8>(beta0, r, Z, C, norms, K, L, Tz, lam, lam_f, write_r, red, s);
     if (kpt <= 16)
-        return resync_launch<16>(beta0, beta, Z, C, norms, K, L, Tz, lam, lam_f, write_beta, red,
-                                 s);
+        return resync_launch<16>(beta0, r, Z, C, norms, K, L, Tz, lam, lam_f, write_r, red, s);
     if (kpt <= 64)
-        return resync_launch<64>(beta0, beta, Z, C, norms, K, L, Tz, lam, lam_f, write_beta, red,
-                                 s);
+        return resync_launch<64>(beta0, r, Z, C, norms, K, L, Tz, lam, lam_f, write_r, red, s);
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_beta_from_r(const float *r, const float *Z, const float *norms, int K,
+                               int64_t Tz, float *out, cudaStream_t s)
+{
+    const int64_t n = (int64_t)K * Tz;
+    const int64_t grid = (n + 255) / 256;
+    beta_from_r_kernel<<<(unsigned)(grid < 152 * 64 ? grid : 152 * 64), 256, 0, s>>>(r, Z, norms,
+                                                                                   K, Tz, out);
+    return cudaGetLastError();
 }
 
 int objective_blocks(int64_t T)
