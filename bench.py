@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--segments", type=int, default=1024)
+    ap.add_argument("--updates-per-visit", type=int, default=16)
+    ap.add_argument("--no-sweep", action="store_true", help="skip the segment-count sweep")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -149,15 +151,15 @@ def time_to_gap_ms(trace, init_ms, E_star, rel=1e-4):
     return init_ms + (float(t[-1]) / 1e6 if t.size else 0.0)
 
 
-def cpu_baseline(pb, lam, tol, M):
+def cpu_baseline(pb, lam, tol, M, u):
     """The FP64 oracle as it stands (single thread), on the full problem."""
     import oracle
     t = time.perf_counter()
-    r = oracle.locally_greedy_cd(pb.D, pb.X, lam, tol, M=M, mode="phase")
+    r = oracle.locally_greedy_cd(pb.D, pb.X, lam, tol, M=M, mode="phase", updates_per_visit=u)
     dt = time.perf_counter() - t
     return {"value": r["n_updates"] / dt, "unit": "updates/s", "cores": 1, "kind": "oracle",
             "sample": f"full solve (DtD, D~*X, phase-schedule CD to max|dZ|<{tol:g}) of seed 0, "
-                      f"M={M}: {r['n_updates']} updates in {dt:.2f} s"}
+                      f"M={M}, u={u}: {r['n_updates']} updates in {dt:.2f} s"}
 
 
 def run_reference(args):
@@ -175,7 +177,7 @@ def run_reference(args):
     for i in range(args.warmup + args.steps):
         t = time.perf_counter()
         r = oracle.locally_greedy_cd(pb.D, pb.X, lam, args.tol, M=args.segments, mode="phase",
-                                     max_updates=cap)
+                                     updates_per_visit=args.updates_per_visit, max_updates=cap)
         dt = time.perf_counter() - t
         if i >= args.warmup:
             times.append(dt)
@@ -189,7 +191,8 @@ def run_reference(args):
         "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "P": 7, "K": 25, "L": 64, "T": 200_000,
-                   "segments": args.segments, "tol": args.tol},
+                   "segments": args.segments, "updates_per_visit": args.updates_per_visit,
+                   "tol": args.tol},
         "cpu_baseline": {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": v, "unit": "updates/s", "h2d_bytes_per_step": 0,
@@ -225,7 +228,8 @@ def main():
     D = torch.from_numpy(pb.D).cuda()
     X = torch.from_numpy(pb.X).cuda()
     Z = torch.zeros((pb.K, pb.Tz), dtype=torch.float32, device="cuda")
-    opts = capi.make_opts(segments=args.segments, time_kernels=1)
+    opts = capi.make_opts(segments=args.segments, updates_per_visit=args.updates_per_visit,
+                          time_kernels=1)
     h = capi.csc_setup(D, opts)
     if g is not None:
         lam = g["lambda"]
@@ -312,6 +316,24 @@ def main():
         status, E, st = capi.csc_solve(h, args.tol, 1 << 40, Zh)
         e2e_t += time.perf_counter() - t0
         e2e_u += st["updates"]
+    # the workload's segment-count sweep (not part of the timed steps)
+    sweep = {}
+    if world == 1 and not args.no_sweep:
+        for M in (64, 256, 1024, 3072):
+            o = capi.make_opts(segments=M, updates_per_visit=args.updates_per_visit)
+            best = None
+            for _ in range(3):
+                capi.csc_setup(D, o, handle=h)
+                capi.csc_init(h, X, lam)
+                status, E, st = capi.csc_solve(h, args.tol, 1 << 40, Z)
+                tr = capi.csc_get_trace(h)
+                if best is None or st["solve_ms"] < best["solve_ms"]:
+                    best = {"solve_ms": st["solve_ms"], "updates": st["updates"],
+                            "updates_per_s": st["updates"] / (st["solve_ms"] * 1e-3),
+                            "sweeps": st["sweeps"], "phases": st["phases"],
+                            "time_to_gap_solve_ms": time_to_gap_ms(tr, 0.0, g["E_star"]) if g else None,
+                            "rel_gap_final": (E - g["E_star"]) / g["E_star"] if g else None}
+            sweep[str(M)] = best
     capi.csc_destroy(h)
     if world > 1:
         t = torch.tensor([e2e_t], dtype=torch.float64, device="cuda")
@@ -331,7 +353,8 @@ def main():
         "ms_per_step": tot_ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "P": 7, "K": 25, "L": 64, "T": 200_000,
-                   "segments": args.segments, "phases": sts[-1]["phases"], "tol": args.tol,
+                   "segments": args.segments, "updates_per_visit": args.updates_per_visit,
+                   "phases": sts[-1]["phases"], "tol": args.tol,
                    "lambda": "0.1*lambda_max", "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world}, one signal per GPU"},
         "time_to_gap_ms": ttg,
@@ -351,8 +374,11 @@ def main():
                 "d2h_bytes_per_step": int(pb.K * pb.Tz * 4 + 8)},
         "clocks": clk.summary(),
     }
+    if sweep:
+        line["segment_sweep"] = sweep
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(pb, lam, args.tol, args.segments)
+        line["cpu_baseline"] = cpu_baseline(pb, lam, args.tol, args.segments,
+                                            args.updates_per_visit)
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
