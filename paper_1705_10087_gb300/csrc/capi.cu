@@ -141,8 +141,8 @@ struct csc_handle_s {
     cudaStream_t stream = nullptr;
     csc_opts opts{};
     int K = 0, P = 0, L = 0;
-    float *D = nullptr, *C = nullptr, *norms = nullptr;
-    size_t cap_D = 0, cap_C = 0, cap_n = 0;
+    float *D = nullptr, *C = nullptr, *Ct = nullptr, *norms = nullptr;
+    size_t cap_D = 0, cap_C = 0, cap_Ct = 0, cap_n = 0;
     // problem state
     bool initialized = false;
     int64_t T = 0, Tz = 0;
@@ -209,6 +209,7 @@ int csc_destroy(csc_handle_t h)
         cudaStreamSynchronize(h->stream);
     cudaFree(h->D);
     cudaFree(h->C);
+    cudaFree(h->Ct);
     cudaFree(h->norms);
     cudaFree(h->X);
     cudaFree(h->r);
@@ -271,6 +272,7 @@ int csc_setup(csc_handle_t *hp, const float *D, int K, int P, int L, const csc_o
     auto body = [&]() -> int {
         CSC_CUDA(grow(&h->D, &h->cap_D, (size_t)K * P * L));
         CSC_CUDA(grow(&h->C, &h->cap_C, (size_t)K * K * (2 * L - 1)));
+        CSC_CUDA(grow(&h->Ct, &h->cap_Ct, (size_t)K * (2 * L - 1) * coef_pad(K)));
         CSC_CUDA(grow(&h->norms, &h->cap_n, (size_t)K));
         if (!h->sc)
             CSC_CUDA(cudaMalloc(&h->sc, sizeof(Scratch)));
@@ -282,7 +284,8 @@ int csc_setup(csc_handle_t *hp, const float *D, int K, int P, int L, const csc_o
             CSC_CUDA(cudaEventCreate(&h->ev1));
         CSC_CUDA(copy_in(h->D, D, sizeof(float) * K * P * L, h->stream));
         CSC_CUDA(launch_dtd(h->D, K, P, L, h->C, h->norms, h->stream));
-        h->launches += 1;
+        CSC_CUDA(launch_coef_by_lag(h->C, K, L, h->Ct, h->stream));
+        h->launches += 2;
         return CSC_OK;
     };
     int rc = body();
@@ -405,6 +408,8 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
     pp.r = h->r;
     pp.Z = h->Z;
     pp.C = h->C;
+    pp.Ct = h->Ct;
+    pp.Kp = coef_pad(h->K);
     pp.norms = h->norms;
     pp.dirty = h->dirty;
     pp.upd = sc->upd;

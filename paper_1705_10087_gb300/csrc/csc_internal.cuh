@@ -98,6 +98,7 @@ struct PhaseParams {
     float *r;                  // r = beta - n Z, [K][Tz]
     float *Z;                  // [K][Tz]
     const float *C;            // DtD [K][K][W2]
+    const float *Ct;           // DtD by lag: Ct[(k0 * W2 + s) * Kp + k] = DtD[k0][k][s], 0 for k >= K
     const float *norms;        // [K]
     unsigned char *dirty;      // [M] segment needs a visit
     long long *upd;            // [kPhaseRing] updates per phase launch
@@ -108,7 +109,7 @@ struct PhaseParams {
     int *done;                 // set once a full sweep applied nothing
     int64_t Tz;
     long long max_updates;
-    int M, c, p, K, L;
+    int M, c, p, K, Kp, L;  // Kp = K rounded up to a multiple of 4
     int g;        // launch index (monotone within a solve)
     int g_round;  // first launch index of the current CD round
     int u;        // cap on updates per visit
@@ -127,6 +128,11 @@ cudaError_t launch_phase(const PhaseParams &pp, const PhaseConfig &cfg, cudaStre
 
 cudaError_t launch_dtd(const float *D, int K, int P, int L, float *C, float *norms,
                        cudaStream_t s);
+// Ct[(k0 * W2 + s) * Kp + k] = C[(k0 * K + k) * W2 + s] (zero for k >= K): the K
+// coefficients an update of atom k0 applies at one lag are contiguous.
+__host__ __device__ __forceinline__ int coef_pad(int K) { return (K + 3) & ~3; }
+cudaError_t launch_coef_by_lag(const float *C, int K, int L, float *Ct, cudaStream_t s);
+
 cudaError_t launch_dtx(const float *D, const float *X, int K, int P, int L, int64_t T,
                        float *beta0, unsigned int *absmax_bits, cudaStream_t s);
 

@@ -44,7 +44,7 @@ namespace csc {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kCoefBatch = 16;         // DtD coefficients loaded per round trip
+constexpr int kCoefBatch = 16;         // DtD coefficients loaded per round trip (multiple of 4)
 
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
 {
@@ -84,12 +84,15 @@ struct Layout {
         o = up(o + 4 * (size_t)K);
         rnrm = o;
         o = up(o + 4 * (size_t)K);
+        // staged tiles are column-major [jj][k] with an odd row length K|1, so that
+        // lanes on consecutive columns hit distinct banks
+        const size_t ks = (size_t)(K | 1);
         r = o;
         if (smem)
-            o = up(o + 4 * (size_t)K * w);
+            o = up(o + 4 * ks * w);
         z = o;
         if (smem)
-            o = up(o + 4 * (size_t)K * w);
+            o = up(o + 4 * ks * w);
         total = o;
     }
     __host__ __device__ static size_t up(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -98,11 +101,15 @@ struct Layout {
 // MAXT: the block size the instantiation is launched with.  Blocks of 128
 // threads (atoms up to 64 samples) are compiled for 5 resident blocks per SM,
 // so that the several hundred co-active segments of a phase fit in one wave;
-// larger blocks get the full register file.
-template <bool SMEM, int MAXT>
+// larger blocks get the full register file.  KT > 0 fixes K at compile time
+// (loops over atoms unroll, tile offsets become immediates); KT = 0 reads K
+// from the parameters.
+template <bool SMEM, int MAXT, int KT>
 __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseParams pp)
 {
     using Idx = typename std::conditional<SMEM, int, int64_t>::type;
+    constexpr bool KFIX = KT > 0;
+    constexpr int KPC = (KT + 3) & ~3;  // padded coefficient row, compile-time K
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_go;
     __shared__ double s_dec[32];
@@ -135,7 +142,8 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseP
     if (!s_go)
         return;
 
-    const int K = pp.K, L = pp.L, W2 = 2 * L - 1;
+    const int K = KFIX ? KT : pp.K, L = pp.L, W2 = 2 * L - 1;
+    const int Kp = KFIX ? KPC : pp.Kp;
     const int64_t Tz = pp.Tz;
     const int64_t s = seg_start(Tz, pp.M, m), e = seg_start(Tz, pp.M, m + 1);
     const int w = (int)(e - s);
@@ -158,26 +166,30 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseP
     float *nrm = reinterpret_cast<float *>(smem_raw + lay.nrm);    // ||D_k||^2
     float *rnrm = reinterpret_cast<float *>(smem_raw + lay.rnrm);  // 1 / ||D_k||^2
 
-    // own segment: rs[k * stride + jj], zs[k * stride + jj], jj = t - s
+    // own segment: element (k, jj = t - s) at rs[jj * cst + k * kst]
+    //   staged (SMEM): column-major [jj][k], cst = K|1, kst = 1
+    //   in place:      the global [k][Tz] arrays, cst = 1, kst = Tz
     float *rs;
     float *zs;
-    Idx stride;
+    Idx cst, kst;
     if (SMEM) {
         rs = reinterpret_cast<float *>(smem_raw + lay.r);
         zs = reinterpret_cast<float *>(smem_raw + lay.z);
-        stride = (Idx)pp.w_max;
+        cst = (Idx)(K | 1);
+        kst = 1;
         for (int k = 0; k < K; k++) {
             const float *rsrc = pp.r + (int64_t)k * Tz + s;
             const float *zsrc = pp.Z + (int64_t)k * Tz + s;
             for (int jj = tid; jj < w; jj += B) {
-                rs[k * stride + jj] = rsrc[jj];
-                zs[k * stride + jj] = zsrc[jj];
+                rs[jj * cst + k] = rsrc[jj];
+                zs[jj * cst + k] = zsrc[jj];
             }
         }
     } else {
         rs = pp.r + s;
         zs = pp.Z + s;
-        stride = (Idx)Tz;
+        cst = 1;
+        kst = (Idx)Tz;
     }
     for (int k = tid; k < K; k += B) {
         nrm[k] = pp.norms[k];
@@ -187,16 +199,15 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseP
 
     // best coordinate of own column jj over k
     auto col_eval = [&](int jj) {
-        const float *rc = rs + jj;
-        const float *zc = zs + jj;
+        const float *rc = rs + jj * cst;
+        const float *zc = zs + jj * cst;
         float best = -1.f, bz = 0.f, bdz = 0.f;
         int bk = 0;
-#pragma unroll 5
-        for (int k = 0; k < K; k++) {
-            const float r = rc[k * stride], z = zc[k * stride];
+        auto visit = [&](int k) {
+            const float r = rc[k * kst], z = zc[k * kst];
             // inactive and inside the threshold: Z' = Sh(r, lam)/n = 0 = z exactly
             if (z == 0.f && fabsf(r) <= lam)
-                continue;
+                return;
             float zn, d;
             coord_step(r, z, nrm[k], rnrm[k], lam, &zn, &d);
             const float ad = fabsf(d);
@@ -206,6 +217,15 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseP
                 bz = zn;
                 bdz = d;
             }
+        };
+        if constexpr (KFIX) {
+#pragma unroll
+            for (int k = 0; k < KT; k++)
+                visit(k);
+        } else {
+#pragma unroll 5
+            for (int k = 0; k < K; k++)
+                visit(k);
         }
         const unsigned flat = (unsigned)bk * (unsigned)Tz + (unsigned)(s + jj);
         ckey[jj] = best > 0.f ? ((unsigned long long)__float_as_uint(best) << 32) | (unsigned)(~flat)
@@ -275,35 +295,56 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseP
                 // Prop. A.1 from the owner's r before this update touches it:
                 // E(Z) - E(Z') = dZ (r - n dZ / 2) + lam (|z| - |u|), dZ = u - z
                 const double n = nrm[k0], d = delta, u = znew, z = (double)znew - d;
-                const double r0 = rs[k0 * stride + jj];
+                const double r0 = rs[jj * cst + k0 * kst];
                 decrease += d * (r0 - 0.5 * n * d) + (double)lam * (fabs(z) - fabs(u));
             }
-            for (int kb = 0; kb < K; kb += kCoefBatch) {
-                // the column's coefficients S_{k,k0}[t-t0] first: independent
-                // loads, one L2 round trip per kCoefBatch atoms
-                float cv[kCoefBatch];
+            // the K coefficients S_{k,k0}[t-t0] of this lag are contiguous in Ct:
+            // fetch them first (independent vector loads, one L2 round trip per
+            // batch), then apply
+            const float *Ck = pp.Ct + ((int64_t)k0 * W2 + off) * Kp;
+            float *rcol = rs + jj * cst;
+            float *rg = pp.r + t;  // an idle neighbour's column (no other block touches it)
+            auto apply = [&](int k, float cv) {
+                if (own)
+                    rcol[k * kst] = fmaf(-cv, delta, rcol[k * kst]);
+                else
+                    atomicAdd(rg + (int64_t)k * Tz, -cv * delta);
+            };
+            if constexpr (KFIX) {
 #pragma unroll
-                for (int i = 0; i < kCoefBatch; i++)
-                    cv[i] = kb + i < K ? __ldg(Ck0 + (int64_t)(kb + i) * W2) : 0.f;
-                if (own) {
+                for (int kb = 0; kb < KPC; kb += kCoefBatch) {
+                    constexpr int NB = kCoefBatch;
+                    float cv[NB];
+#pragma unroll
+                    for (int q = 0; q < NB / 4; q++) {
+                        if (kb + 4 * q < KPC) {
+                            const float4 v = __ldg(reinterpret_cast<const float4 *>(Ck + kb) + q);
+                            cv[4 * q] = v.x;
+                            cv[4 * q + 1] = v.y;
+                            cv[4 * q + 2] = v.z;
+                            cv[4 * q + 3] = v.w;
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < NB; i++)
+                        if (kb + i < KT)
+                            apply(kb + i, cv[i]);
+                }
+            } else {
+                for (int kb = 0; kb < K; kb += kCoefBatch) {
+                    float cv[kCoefBatch];
 #pragma unroll
                     for (int i = 0; i < kCoefBatch; i++)
-                        if (kb + i < K) {
-                            float *rp = rs + (kb + i) * stride + jj;
-                            *rp = fmaf(-cv[i], delta, *rp);
-                        }
-                } else {
-                    // an idle neighbour's column: no other block touches it this phase
-                    float *rg = pp.r + t;
+                        cv[i] = kb + i < K ? __ldg(Ck + kb + i) : 0.f;
 #pragma unroll
                     for (int i = 0; i < kCoefBatch; i++)
                         if (kb + i < K)
-                            atomicAdd(rg + (int64_t)(kb + i) * Tz, -cv[i] * delta);
+                            apply(kb + i, cv[i]);
                 }
             }
             if (own) {
                 if (t == t0)
-                    zs[k0 * stride + jj] = znew;
+                    zs[jj * cst + k0 * kst] = znew;
                 col_eval(jj);
             }
         }
@@ -319,8 +360,8 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseP
             float *rdst = pp.r + (int64_t)k * Tz + s;
             float *zdst = pp.Z + (int64_t)k * Tz + s;
             for (int jj = tid; jj < w; jj += B) {
-                rdst[jj] = rs[k * stride + jj];
-                zdst[jj] = zs[k * stride + jj];
+                rdst[jj] = rs[jj * cst + k];
+                zdst[jj] = zs[jj * cst + k];
             }
         }
     }
@@ -387,12 +428,20 @@ cudaError_t launch_phase(const PhaseParams &pp, const PhaseConfig &cfg, cudaStre
         return cudaSuccess;
     };
     cudaError_t e;
-    if (cfg.block == 128)
-        e = cfg.tile_in_smem ? go(phase_kernel<true, 128>) : go(phase_kernel<false, 128>);
-    else if (cfg.block == 512)
-        e = cfg.tile_in_smem ? go(phase_kernel<true, 512>) : go(phase_kernel<false, 512>);
-    else
-        e = cfg.tile_in_smem ? go(phase_kernel<true, 1024>) : go(phase_kernel<false, 1024>);
+    const bool k25 = pp.K == 25;  // the workloads' atom count: compiled with K fixed
+    if (cfg.block == 128) {
+        if (k25)
+            e = cfg.tile_in_smem ? go(phase_kernel<true, 128, 25>) : go(phase_kernel<false, 128, 25>);
+        else
+            e = cfg.tile_in_smem ? go(phase_kernel<true, 128, 0>) : go(phase_kernel<false, 128, 0>);
+    } else if (cfg.block == 512) {
+        if (k25)
+            e = cfg.tile_in_smem ? go(phase_kernel<true, 512, 25>) : go(phase_kernel<false, 512, 25>);
+        else
+            e = cfg.tile_in_smem ? go(phase_kernel<true, 512, 0>) : go(phase_kernel<false, 512, 0>);
+    } else {
+        e = cfg.tile_in_smem ? go(phase_kernel<true, 1024, 0>) : go(phase_kernel<false, 1024, 0>);
+    }
     if (e != cudaSuccess)
         return e;
     return cudaGetLastError();

@@ -21,7 +21,8 @@ struct NZ {
 };
 
 // Ordered compaction of the nonzeros of Z[:, c0:c1) (k-major) into list.
-// Returns the count (same value in every thread).  Block-wide barriers.
+// Returns the count (same value in every thread).  Block-wide barriers; each
+// thread takes 4 consecutive elements per round (two barriers per 4*blockDim).
 __device__ int compact_nonzeros(const float *__restrict__ Z, int K, int64_t Tz, int64_t c0,
                                 int64_t c1, NZ *list, int *warp_counts)
 {
@@ -30,29 +31,41 @@ __device__ int compact_nonzeros(const float *__restrict__ Z, int K, int64_t Tz, 
     const int width = (int)(c1 - c0);
     const int n = K * width;
     int base = 0;
-    for (int r0 = 0; r0 < n; r0 += B) {
-        const int i = r0 + tid;
-        float z = 0.f;
-        int k = 0, t = 0;
-        if (i < n) {
-            k = i / width;
-            t = (int)(c0 + i % width);
-            z = Z[(int64_t)k * Tz + t];
+    for (int r0 = 0; r0 < n; r0 += 4 * B) {
+        float z[4];
+        int cnt = 0;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int i = r0 + 4 * tid + q;
+            z[q] = 0.f;
+            if (i < n)
+                z[q] = Z[(int64_t)(i / width) * Tz + c0 + i % width];
+            cnt += z[q] != 0.f;
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, z != 0.f);
-        if (lane == 0)
-            warp_counts[warp] = __popc(bal);
+        // inclusive warp scan of the counts
+        int inc = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o)
+                inc += v;
+        }
+        if (lane == 31)
+            warp_counts[warp] = inc;
         __syncthreads();
-        int off = base;
-        for (int q = 0; q < warp; q++)
-            off += warp_counts[q];
-        int tot = base;
-        for (int q = 0; q < nw; q++)
-            tot += warp_counts[q];
-        if (z != 0.f) {
-            const int pos = off + __popc(bal & ((1u << lane) - 1u));
-            list[pos] = NZ{k, t, z};
+        int off = base, tot = base;
+        for (int q = 0; q < nw; q++) {
+            const int wc = warp_counts[q];
+            off += q < warp ? wc : 0;
+            tot += wc;
         }
+        int pos = off + inc - cnt;
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            if (z[q] != 0.f) {
+                const int i = r0 + 4 * tid + q;
+                list[pos++] = NZ{i / width, (int)(c0 + i % width), z[q]};
+            }
         __syncthreads();
         base = tot;
     }
@@ -88,7 +101,7 @@ __global__ void __launch_bounds__(kResyncThreads)
 {
     __shared__ NZ list[32 * kChunk];
     __shared__ int warp_counts[32];
-    __shared__ double bred[4][kResyncThreads / 32];
+    __shared__ float bred[4][kResyncThreads / 32];
     __shared__ float bred32[kResyncThreads / 32];
     const int W2 = 2 * L - 1;
     const int tid = threadIdx.x;
@@ -127,8 +140,7 @@ __global__ void __launch_bounds__(kResyncThreads)
         __syncthreads();
     }
 
-    double drift = 0.0, zex = 0.0, nzg = 0.0, all = 0.0;
-    float dz32 = 0.f;
+    float drift = 0.f, zex = 0.f, nzg = 0.f, all = 0.f, dz32 = 0.f;
     if (t < Tz) {
 #pragma unroll
         for (int q = 0; q < KPT; q++) {
@@ -136,33 +148,44 @@ __global__ void __launch_bounds__(kResyncThreads)
             if (k >= K)
                 continue;
             const int64_t ix = (int64_t)k * Tz + t;
-            const double r64 = (double)beta0[ix] - ((double)acc_hi[q] + (double)acc_lo[q]);
+            // r = beta0 - (hi + lo), finished with TwoSum so that only the final
+            // float rounding remains
+            const float b0 = beta0[ix], hi = acc_hi[q], lo = acc_lo[q];
+            const float sm = __fsub_rn(b0, hi);
+            const float bv = __fsub_rn(sm, b0);
+            const float er = __fadd_rn(__fsub_rn(b0, __fsub_rn(sm, bv)), __fsub_rn(-hi, bv));
+            const float r32 = __fadd_rn(sm, __fsub_rn(er, lo));
             const float rold = rr[ix];
-            drift = fmax(drift, fabs((double)rold - r64));
-            const float r32 = (float)r64;
+            drift = fmaxf(drift, fabsf(rold - r32));
             if (write_r)
                 rr[ix] = r32;
             const float z = Z[ix];
-            const float n = norms[k];
-            const double b64 = r64 + (double)n * (double)z;  // beta of Sec. 2.1
-            const double gap = fabs(soft_d(b64, lam) / (double)n - (double)z);
-            if (z == 0.f)
-                zex = fmax(zex, fabs(b64) - lam);
-            else
-                nzg = fmax(nzg, gap);
-            all = fmax(all, gap);
+            const float n = norms[k], rn = __frcp_rn(n);
+            // optimality in the r form (Theorem A.1): z = 0 needs |beta| = |r| <= lam;
+            // otherwise |Z' - z| with Z' from Eq. pb_coord, without cancellation
+            float gap;
+            if (z == 0.f) {
+                zex = fmaxf(zex, fabsf(r32) - lam_f);
+                gap = soft_f(r32, lam_f) * rn;
+            } else {
+                const float sg = z > 0.f ? 1.f : -1.f;
+                const float b = fmaf(n, z, r32);
+                gap = b * sg > lam_f ? (r32 - lam_f * sg) * rn : soft_f(b, lam_f) * rn - z;
+                nzg = fmaxf(nzg, fabsf(gap));
+            }
+            all = fmaxf(all, fabsf(gap));
             // the phase kernel's own test on the float state it will see
             float zn, d32;
-            coord_step(write_r ? r32 : rold, z, n, __frcp_rn(n), lam_f, &zn, &d32);
+            coord_step(write_r ? r32 : rold, z, n, rn, lam_f, &zn, &d32);
             dz32 = fmaxf(dz32, fabsf(d32));
         }
     }
     // block reduce (max) and one atomic per block and quantity
     for (int off = 16; off > 0; off >>= 1) {
-        drift = fmax(drift, __shfl_xor_sync(0xffffffffu, drift, off));
-        zex = fmax(zex, __shfl_xor_sync(0xffffffffu, zex, off));
-        nzg = fmax(nzg, __shfl_xor_sync(0xffffffffu, nzg, off));
-        all = fmax(all, __shfl_xor_sync(0xffffffffu, all, off));
+        drift = fmaxf(drift, __shfl_xor_sync(0xffffffffu, drift, off));
+        zex = fmaxf(zex, __shfl_xor_sync(0xffffffffu, zex, off));
+        nzg = fmaxf(nzg, __shfl_xor_sync(0xffffffffu, nzg, off));
+        all = fmaxf(all, __shfl_xor_sync(0xffffffffu, all, off));
         dz32 = fmaxf(dz32, __shfl_xor_sync(0xffffffffu, dz32, off));
     }
     const int warp = tid >> 5, lane = tid & 31;
@@ -175,15 +198,15 @@ __global__ void __launch_bounds__(kResyncThreads)
     }
     __syncthreads();
     if (tid == 0) {
-        double v[4] = {0, 0, 0, 0};
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
         float v32 = 0.f;
         for (int w = 0; w < kResyncThreads / 32; w++) {
             for (int q = 0; q < 4; q++)
-                v[q] = fmax(v[q], bred[q][w]);
+                v[q] = fmaxf(v[q], bred[q][w]);
             v32 = fmaxf(v32, bred32[w]);
         }
         for (int q = 0; q < 4; q++)
-            atomicMax(&red[q], (unsigned long long)__double_as_longlong(fmax(v[q], 0.0)));
+            atomicMax(&red[q], (unsigned long long)__double_as_longlong((double)v[q]));
         atomicMax(&red[4], (unsigned long long)__double_as_longlong((double)v32));
     }
 }
@@ -212,10 +235,12 @@ __global__ void __launch_bounds__(kObjTile)
     const int64_t hi = c0 + kObjTile < Tz ? c0 + kObjTile : Tz;
     const int chunk = (32 * kChunk) / K < kChunk ? (32 * kChunk) / K : kChunk;
     for (int p0 = 0; p0 < P; p0 += kObjP) {
-        double acc[kObjP];
+        float acc_hi[kObjP], acc_lo[kObjP];
 #pragma unroll
-        for (int q = 0; q < kObjP; q++)
-            acc[q] = 0.0;
+        for (int q = 0; q < kObjP; q++) {
+            acc_hi[q] = 0.f;
+            acc_lo[q] = 0.f;
+        }
         for (int64_t a = lo; a < hi; a += chunk) {
             const int64_t b = a + chunk < hi ? a + chunk : hi;
             const int n = compact_nonzeros(Z, K, Tz, a, b, list, warp_counts);
@@ -225,12 +250,13 @@ __global__ void __launch_bounds__(kObjTile)
                     const int tau = (int)(t - e.t);
                     if (tau < 0 || tau >= L)
                         continue;
-                    const double zd = (double)e.z;
+                    if (tau == 0 && p0 == 0)
+                        l1 += fabs((double)e.z);  // each nonzero once, by the thread t = t'
                     const float *Dk = D + (int64_t)e.k * P * L + tau;
 #pragma unroll
                     for (int q = 0; q < kObjP; q++)
                         if (p0 + q < P)
-                            acc[q] += (double)__ldg(Dk + (int64_t)(p0 + q) * L) * zd;
+                            df_add_prod(acc_hi[q], acc_lo[q], __ldg(Dk + (int64_t)(p0 + q) * L), e.z);
                 }
             }
             __syncthreads();
@@ -239,14 +265,12 @@ __global__ void __launch_bounds__(kObjTile)
 #pragma unroll
             for (int q = 0; q < kObjP; q++)
                 if (p0 + q < P) {
-                    const double r = (double)X[(int64_t)(p0 + q) * T + t] - acc[q];
+                    const double r = (double)X[(int64_t)(p0 + q) * T + t] -
+                                     ((double)acc_hi[q] + (double)acc_lo[q]);
                     sq += r * r;
                 }
         }
     }
-    if (t < Tz)
-        for (int k = 0; k < K; k++)
-            l1 += fabs((double)Z[(int64_t)k * Tz + t]);
     for (int off = 16; off > 0; off >>= 1) {
         sq += __shfl_xor_sync(0xffffffffu, sq, off);
         l1 += __shfl_xor_sync(0xffffffffu, l1, off);

@@ -122,6 +122,21 @@ __global__ void __launch_bounds__(kDtxTile) dtx_kernel(const float *__restrict__
         atomicMax(absmax_bits, __float_as_uint(amax));
 }
 
+__global__ void coef_by_lag_kernel(const float *__restrict__ C, int K, int L, int Kp,
+                                   float *__restrict__ Ct)
+{
+    const int W2 = 2 * L - 1;
+    const long long n = (long long)K * W2 * Kp;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(i % Kp);
+        const long long ks = i / Kp;  // k0 * W2 + s
+        const int s = (int)(ks % W2);
+        const int k0 = (int)(ks / W2);
+        Ct[i] = k < K ? C[((long long)k0 * K + k) * W2 + s] : 0.f;
+    }
+}
+
 __global__ void stamp_kernel(unsigned long long *out)
 {
     *out = globaltimer_ns();
@@ -154,6 +169,15 @@ cudaError_t launch_dtx(const float *D, const float *X, int K, int P, int L, int6
     const int64_t Tz = T - L + 1;
     dim3 grid((unsigned)((Tz + kDtxTile - 1) / kDtxTile), (unsigned)((K + kDtxAtoms - 1) / kDtxAtoms));
     dtx_kernel<<<grid, kDtxTile, smem, s>>>(D, X, K, P, L, T, beta0, absmax_bits);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coef_by_lag(const float *C, int K, int L, float *Ct, cudaStream_t s)
+{
+    const long long n = (long long)K * (2 * L - 1) * coef_pad(K);
+    const long long grid = (n + 255) / 256;
+    coef_by_lag_kernel<<<(unsigned)(grid < 65535 ? grid : 65535), 256, 0, s>>>(C, K, L,
+                                                                            coef_pad(K), Ct);
     return cudaGetLastError();
 }
 
