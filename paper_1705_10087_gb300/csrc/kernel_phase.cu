@@ -58,7 +58,7 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
 // Shared-memory layout of a block, in bytes from the start (16-byte aligned
 // pieces).  w = widest segment; with smem the segment's r and Z are staged.
 struct Layout {
-    size_t key, slot_key, cz, cd, ck, slot_z, slot_d, slot_k, slot_j, nrm, rnrm, r, z, total;
+    size_t key, slot_key, cz, cd, ck, zm, slot_z, slot_d, slot_k, slot_j, nrm, rnrm, r, z, total;
     __host__ __device__ Layout(int K, int w, bool smem)
     {
         size_t o = 0;
@@ -71,6 +71,8 @@ struct Layout {
         cd = o;
         o = up(o + 4 * (size_t)w);
         ck = o;
+        o = up(o + 4 * (size_t)w);
+        zm = o;  // per column: bit k set when Z_k[t] != 0 (compile-time K <= 32)
         o = up(o + 4 * (size_t)w);
         slot_z = o;
         o = up(o + 4 * 64);
@@ -159,6 +161,8 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseP
     float *cz = reinterpret_cast<float *>(smem_raw + lay.cz);
     float *cd = reinterpret_cast<float *>(smem_raw + lay.cd);
     int *ck = reinterpret_cast<int *>(smem_raw + lay.ck);
+    unsigned *zmask = reinterpret_cast<unsigned *>(smem_raw + lay.zm);
+    static_assert(KT <= 32, "the nonzero mask of a column holds 32 atoms");
     float *slot_z = reinterpret_cast<float *>(smem_raw + lay.slot_z);
     float *slot_d = reinterpret_cast<float *>(smem_raw + lay.slot_d);
     int *slot_k = reinterpret_cast<int *>(smem_raw + lay.slot_k);
@@ -197,6 +201,37 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseP
     }
     __syncthreads();
 
+    // best coordinate of own column jj from its r values (registers) and the
+    // mask of entries that can move: z != 0 or |r| > lam (all others have
+    // Z' = Sh(r, lam)/n = 0 = z exactly); compile-time K only
+    auto col_finish = [&](int jj, const float (&rv)[KT > 0 ? KT : 1], unsigned need) {
+        float best = -1.f, bz = 0.f, bdz = 0.f;
+        int bk = 0;
+        if (need) {
+            const float *zc = zs + jj * cst;
+#pragma unroll
+            for (int k = 0; k < (KT > 0 ? KT : 1); k++) {
+                if ((need >> k) & 1u) {
+                    float zn, d;
+                    coord_step(rv[k], zc[k * kst], nrm[k], rnrm[k], lam, &zn, &d);
+                    const float ad = fabsf(d);
+                    if (ad > best) {
+                        best = ad;
+                        bk = k;
+                        bz = zn;
+                        bdz = d;
+                    }
+                }
+            }
+        }
+        const unsigned flat = (unsigned)bk * (unsigned)Tz + (unsigned)(s + jj);
+        ckey[jj] = best > 0.f ? ((unsigned long long)__float_as_uint(best) << 32) | (unsigned)(~flat)
+                              : 0ull;
+        cz[jj] = bz;
+        cd[jj] = bdz;
+        ck[jj] = bk;
+    };
+
     // best coordinate of own column jj over k
     auto col_eval = [&](int jj) {
         const float *rc = rs + jj * cst;
@@ -219,9 +254,17 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseP
             }
         };
         if constexpr (KFIX) {
+            float rv[KT];
+            unsigned need = 0, zb = 0;
 #pragma unroll
-            for (int k = 0; k < KT; k++)
-                visit(k);
+            for (int k = 0; k < KT; k++) {
+                rv[k] = rc[k * kst];
+                zb |= (zc[k * kst] != 0.f ? 1u : 0u) << k;
+                need |= (fabsf(rv[k]) > lam ? 1u : 0u) << k;
+            }
+            zmask[jj] = zb;
+            col_finish(jj, rv, need | zb);
+            return;
         } else {
 #pragma unroll 5
             for (int k = 0; k < K; k++)
@@ -288,7 +331,6 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseP
         const int off = (tid - (int)(tlo - s)) & (B - 1);  // window position of this thread
         const int64_t t = tlo + off;
         if (off < W2 && t >= 0 && t < Tz) {
-            const float *Ck0 = pp.C + ((int64_t)k0 * K) * W2 + off;
             const bool own = t >= s && t < e;
             const int jj = (int)(t - s);
             if (t == t0) {
@@ -311,24 +353,36 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseP
                     atomicAdd(rg + (int64_t)k * Tz, -cv * delta);
             };
             if constexpr (KFIX) {
+                // all K coefficients in one round trip (KPC/4 vector loads)
+                float cv[KPC];
 #pragma unroll
-                for (int kb = 0; kb < KPC; kb += kCoefBatch) {
-                    constexpr int NB = kCoefBatch;
-                    float cv[NB];
-#pragma unroll
-                    for (int q = 0; q < NB / 4; q++) {
-                        if (kb + 4 * q < KPC) {
-                            const float4 v = __ldg(reinterpret_cast<const float4 *>(Ck + kb) + q);
-                            cv[4 * q] = v.x;
-                            cv[4 * q + 1] = v.y;
-                            cv[4 * q + 2] = v.z;
-                            cv[4 * q + 3] = v.w;
-                        }
+                for (int q = 0; q < KPC / 4; q++) {
+                    const float4 v = __ldg(reinterpret_cast<const float4 *>(Ck) + q);
+                    cv[4 * q] = v.x;
+                    cv[4 * q + 1] = v.y;
+                    cv[4 * q + 2] = v.z;
+                    cv[4 * q + 3] = v.w;
+                }
+                if (own) {
+                    // apply and screen in registers, then evaluate the movable entries
+                    if (t == t0) {
+                        zs[jj * cst + k0 * kst] = znew;
+                        zmask[jj] = znew != 0.f ? (zmask[jj] | (1u << k0)) : (zmask[jj] & ~(1u << k0));
                     }
+                    float rv[KT];
+                    unsigned need = 0;
 #pragma unroll
-                    for (int i = 0; i < NB; i++)
-                        if (kb + i < KT)
-                            apply(kb + i, cv[i]);
+                    for (int k = 0; k < KT; k++) {
+                        const float r = fmaf(-cv[k], delta, rcol[k * kst]);
+                        rcol[k * kst] = r;
+                        rv[k] = r;
+                        need |= (fabsf(r) > lam ? 1u : 0u) << k;
+                    }
+                    col_finish(jj, rv, need | zmask[jj]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < KT; k++)
+                        atomicAdd(rg + (int64_t)k * Tz, -cv[k] * delta);
                 }
             } else {
                 for (int kb = 0; kb < K; kb += kCoefBatch) {
@@ -342,7 +396,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseP
                             apply(kb + i, cv[i]);
                 }
             }
-            if (own) {
+            if (!KFIX && own) {
                 if (t == t0)
                     zs[jj * cst + k0 * kst] = znew;
                 col_eval(jj);
