@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--segments", type=int, default=1024)
-    ap.add_argument("--updates-per-visit", type=int, default=16)
+    ap.add_argument("--updates-per-visit", type=int, default=24)
     ap.add_argument("--no-sweep", action="store_true", help="skip the segment-count sweep")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -138,6 +138,21 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": ["unavailable"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def phase_traffic():
+    """DRAM bytes per phase-kernel launch from the committed ncu summary, or None
+    when the kernel source changed since those counters were taken."""
+    import hashlib
+    try:
+        text = open(os.path.join(ROOT, "profiles", f"phase_kernel_{WORKLOAD}.md")).read()
+        src = open(os.path.join(ROOT, "paper_1705_10087_gb300", "csrc", "kernel_phase.cu"), "rb").read()
+    except OSError:
+        return None
+    fields = dict(ln.split(":", 1) for ln in text.splitlines() if ln.startswith(("kernel_source", "dram_")))
+    if fields.get("kernel_source_sha256_16", "").strip() != hashlib.sha256(src).hexdigest()[:16]:
+        return None
+    return float(fields["dram_bytes_per_launch"])
 
 
 def time_to_gap_ms(trace, init_ms, E_star, rel=1e-4):
@@ -364,7 +379,7 @@ def main():
         "sweeps": sts[-1]["sweeps"], "resyncs": sts[-1]["resyncs"],
         "rel_gap_final": (Es[-1] - g["E_star"]) / g["E_star"] if g else None,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak if achieved else None, "traffic": None,
+                     "frac": achieved / peak if achieved else None, "traffic": phase_traffic(),
                      "kernel": "phase_kernel", "peak_kind": peak_kind,
                      "avg_launch_us": 1e3 * phase_ms / phase_launches if phase_launches else None,
                      "launches": phase_launches},

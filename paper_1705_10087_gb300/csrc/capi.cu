@@ -49,6 +49,7 @@ struct Scratch {
     unsigned long long tstart;
     unsigned long long red[8];
     double obj[2];
+    double x2;  // sum X^2 of the last csc_init
 };
 
 // Host mirror of what the solve loop polls (pinned).
@@ -162,6 +163,7 @@ struct csc_handle_s {
     cudaEvent_t *kev = nullptr;  // per-launch timing events (2 per launch of a poll batch)
     int n_kev = 0;
     int64_t launches = 0;        // kernels launched through this handle
+    bool z_is_zero = false;  // Z == 0 since csc_init: E(Z) = sum X^2 / 2 is known
     // last solve
     int64_t g_used = 0;
     double E_start = 0.0;
@@ -320,7 +322,9 @@ int csc_init(csc_handle_t h, const float *X, int64_t T, double lambda, const flo
     CSC_CUDA(grow(&h->partials, &h->cap_partials, 2 * (size_t)objective_blocks(T)));
     CSC_CUDA(copy_in(h->X, X, sizeof(float) * h->P * T, s));
     CSC_CUDA(cudaMemsetAsync(&h->sc->lmax_bits, 0, sizeof(unsigned), s));
-    CSC_CUDA(launch_dtx(h->D, h->X, h->K, h->P, h->L, T, h->beta0, &h->sc->lmax_bits, s));
+    CSC_CUDA(cudaMemsetAsync(&h->sc->x2, 0, sizeof(double), s));
+    CSC_CUDA(launch_dtx(h->D, h->X, h->K, h->P, h->L, T, h->beta0, &h->sc->lmax_bits,
+                        &h->sc->x2, s));
     h->launches += 1;
     if (Z0) {
         h->launches += 1;
@@ -328,7 +332,7 @@ int csc_init(csc_handle_t h, const float *X, int64_t T, double lambda, const flo
         CSC_CUDA(cudaMemsetAsync(h->sc->red, 0, sizeof(h->sc->red), s));
         CSC_CUDA(cudaMemcpyAsync(h->r, h->beta0, sizeof(float) * nz, cudaMemcpyDeviceToDevice, s));
         CSC_CUDA(launch_resync(h->beta0, h->r, h->Z, h->C, h->norms, h->K, h->L, Tz, lambda,
-                               (float)lambda, 1, h->sc->red, s));
+                               (float)lambda, 1, h->sc->red, nullptr, 0, 0.f, s));
     } else {
         CSC_CUDA(cudaMemsetAsync(h->Z, 0, sizeof(float) * nz, s));
         CSC_CUDA(cudaMemcpyAsync(h->r, h->beta0, sizeof(float) * nz, cudaMemcpyDeviceToDevice, s));
@@ -342,6 +346,7 @@ int csc_init(csc_handle_t h, const float *X, int64_t T, double lambda, const flo
     h->T = T;
     h->Tz = Tz;
     h->lambda = lambda;
+    h->z_is_zero = Z0 == nullptr;
     h->initialized = true;
     return CSC_OK;
 }
@@ -400,9 +405,14 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
     CSC_CUDA(cudaMemsetAsync(sc->red, 0, sizeof(sc->red), s));
     CSC_CUDA(cudaEventRecord(h->ev0, s));
     CSC_CUDA(launch_stamp(&sc->tstart, s));
-    CSC_CUDA(launch_objective(h->D, h->X, h->Z, h->K, h->P, h->L, h->T, h->lambda, h->partials,
-                              &sc->obj[0], s));
-    h->launches += 3;
+    h->launches += 1;
+    const bool cold = h->z_is_zero;
+    if (!cold) {
+        CSC_CUDA(launch_objective(h->D, h->X, h->Z, h->K, h->P, h->L, h->T, h->lambda,
+                                  h->partials, &sc->obj[0], s));
+        h->launches += 2;
+    }
+    h->z_is_zero = false;
 
     PhaseParams pp;
     pp.r = h->r;
@@ -498,8 +508,11 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
             break;
         }
         CSC_CUDA(cudaMemsetAsync(sc->red, 0, sizeof(sc->red), s));
+        // segments come back dirty only where the refreshed state has a
+        // coordinate at or above the inner tolerance
+        CSC_CUDA(cudaMemsetAsync(h->dirty, 0, (size_t)M, s));
         CSC_CUDA(launch_resync(h->beta0, h->r, h->Z, h->C, h->norms, h->K, h->L, Tz,
-                               h->lambda, (float)h->lambda, 1, sc->red, s));
+                               h->lambda, (float)h->lambda, 1, sc->red, h->dirty, M, pp.tol, s));
         h->launches += 1;
         unsigned long long red[8];
         CSC_CUDA(cudaMemcpyAsync(red, sc->red, sizeof red, cudaMemcpyDeviceToHost, s));
@@ -514,13 +527,12 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
             report_fresh = true;
             break;
         }
-        CSC_CUDA(cudaMemsetAsync(h->dirty, 1, (size_t)M, s));
     }
     if (!report_fresh) {
         // optimality report against a fresh FP64 beta, leaving beta unchanged
         CSC_CUDA(cudaMemsetAsync(sc->red, 0, sizeof(sc->red), s));
         CSC_CUDA(launch_resync(h->beta0, h->r, h->Z, h->C, h->norms, h->K, h->L, Tz,
-                               h->lambda, (float)h->lambda, 0, sc->red, s));
+                               h->lambda, (float)h->lambda, 0, sc->red, nullptr, 0, 0.f, s));
         h->launches += 1;
     }
     CSC_CUDA(cudaEventRecord(h->ev1, s));
@@ -530,17 +542,18 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
     if (Z_out)
         CSC_CUDA(copy_out(Z_out, h->Z, sizeof(float) * h->K * Tz, s));
     unsigned long long red[8];
-    double obj[2];
+    double obj[2], x2 = 0.0;
     long long total = 0, visits = 0;
     CSC_CUDA(cudaMemcpyAsync(red, sc->red, sizeof red, cudaMemcpyDeviceToHost, s));
     CSC_CUDA(cudaMemcpyAsync(obj, sc->obj, sizeof obj, cudaMemcpyDeviceToHost, s));
+    CSC_CUDA(cudaMemcpyAsync(&x2, &sc->x2, sizeof x2, cudaMemcpyDeviceToHost, s));
     CSC_CUDA(cudaMemcpyAsync(&total, &sc->total, sizeof total, cudaMemcpyDeviceToHost, s));
     CSC_CUDA(cudaMemcpyAsync(&visits, &sc->visits, sizeof visits, cudaMemcpyDeviceToHost, s));
     CSC_CUDA(cudaStreamSynchronize(s));
     float ms = 0.f;
     CSC_CUDA(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
     h->g_used = g;
-    h->E_start = obj[0];
+    h->E_start = cold ? 0.5 * x2 : obj[0];
     if (objective)
         *objective = obj[1];
     if (stats) {

@@ -133,17 +133,23 @@ cudaError_t launch_dtd(const float *D, int K, int P, int L, float *C, float *nor
 __host__ __device__ __forceinline__ int coef_pad(int K) { return (K + 3) & ~3; }
 cudaError_t launch_coef_by_lag(const float *C, int K, int L, float *Ct, cudaStream_t s);
 
+// beta0 = D~ * X, max |beta0| into *absmax_bits, and sum X^2 added to *x2sum
+// (so E(0) = x2sum / 2).
 cudaError_t launch_dtx(const float *D, const float *X, int K, int P, int L, int64_t T,
-                       float *beta0, unsigned int *absmax_bits, cudaStream_t s);
+                       float *beta0, unsigned int *absmax_bits, double *x2sum, cudaStream_t s);
 
 // FP64 re-synchronisation of r with its definition, r = D~*X - sum_{l,t'} S Z
 // (beta0 = D~*X), rounded once to float, and the optimality report.
 // red[0..4] receive (as non-negative double bit patterns for atomicMax): the
 // drift max |r_old - r_fp64|, zero_excess, nonzero_gap, max_delta_z (FP64
 // beta = r + n Z), and max |Delta Z| of coord_step on the float state.
+// With dirty != NULL, also marks dirty[m] = 1 for every segment m of M that
+// holds a coordinate whose coord_step change on the new state is >= tol_mark
+// (the segments CD has to revisit after the refresh).
 cudaError_t launch_resync(const float *beta0, float *r, const float *Z, const float *C,
                           const float *norms, int K, int L, int64_t Tz, double lam,
-                          float lam_f, int write_r, unsigned long long *red, cudaStream_t s);
+                          float lam_f, int write_r, unsigned long long *red,
+                          unsigned char *dirty, int M, float tol_mark, cudaStream_t s);
 
 // out = r + n Z (beta of Sec. 2.1) in float.
 cudaError_t launch_beta_from_r(const float *r, const float *Z, const float *norms, int K,

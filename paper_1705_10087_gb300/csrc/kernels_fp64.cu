@@ -97,7 +97,8 @@ __global__ void __launch_bounds__(kResyncThreads)
     resync_kernel(const float *__restrict__ beta0, float *__restrict__ rr,
                   const float *__restrict__ Z, const float *__restrict__ C,
                   const float *__restrict__ norms, int K, int L, int64_t Tz, double lam,
-                  float lam_f, int write_r, unsigned long long *__restrict__ red)
+                  float lam_f, int write_r, unsigned long long *__restrict__ red,
+                  unsigned char *__restrict__ dirty, int M, float tol_mark)
 {
     __shared__ NZ list[32 * kChunk];
     __shared__ int warp_counts[32];
@@ -178,6 +179,15 @@ __global__ void __launch_bounds__(kResyncThreads)
             float zn, d32;
             coord_step(write_r ? r32 : rold, z, n, rn, lam_f, &zn, &d32);
             dz32 = fmaxf(dz32, fabsf(d32));
+            if (dirty && fabsf(d32) >= tol_mark) {
+                // the segment of t: the m with floor(m Tz / M) <= t < floor((m+1) Tz / M)
+                int m = (int)(((t + 1) * (int64_t)M - 1) / Tz);
+                while (m > 0 && seg_start(Tz, M, m) > t)
+                    m--;
+                while (m + 1 < M && seg_start(Tz, M, m + 1) <= t)
+                    m++;
+                dirty[m] = 1;
+            }
         }
     }
     // block reduce (max) and one atomic per block and quantity
@@ -328,11 +338,12 @@ __global__ void beta_from_r_kernel(const float *__restrict__ r, const float *__r
 template <int KPT>
 cudaError_t resync_launch(const float *beta0, float *r, const float *Z, const float *C,
                           const float *norms, int K, int L, int64_t Tz, double lam, float lam_f,
-                          int write_r, unsigned long long *red, cudaStream_t s)
+                          int write_r, unsigned long long *red, unsigned char *dirty, int M,
+                          float tol_mark, cudaStream_t s)
 {
     const unsigned grid = (unsigned)((Tz + kResyncCols - 1) / kResyncCols);
     resync_kernel<KPT><<<grid, kResyncThreads, 0, s>>>(beta0, r, Z, C, norms, K, L, Tz, lam,
-                                                       lam_f, write_r, red);
+                                                       lam_f, write_r, red, dirty, M, tol_mark);
     return cudaGetLastError();
 }
 
@@ -340,17 +351,22 @@ cudaError_t resync_launch(const float *beta0, float *r, const float *Z, const fl
 
 cudaError_t launch_resync(const float *beta0, float *r, const float *Z, const float *C,
                           const float *norms, int K, int L, int64_t Tz, double lam,
-                          float lam_f, int write_r, unsigned long long *red, cudaStream_t s)
+                          float lam_f, int write_r, unsigned long long *red,
+                          unsigned char *dirty, int M, float tol_mark, cudaStream_t s)
 {
     const int kpt = (K + kResyncGroups - 1) / kResyncGroups;
+#define CSC_RESYNC(N)                                                                          \
+    return resync_launch<N>(beta0, r, Z, C, norms, K, L, Tz, lam, lam_f, write_r, red, dirty, M, \
+                            tol_mark, s)
     if (kpt <= 2)
-        return resync_launch<2>(beta0, r, Z, C, norms, K, L, Tz, lam, lam_f, write_r, red, s);
+        CSC_RESYNC(2);
     if (kpt <= 8)
-        return resync_launch<8>(beta0, r, Z, C, norms, K, L, Tz, lam, lam_f, write_r, red, s);
+        CSC_RESYNC(8);
     if (kpt <= 16)
-        return resync_launch<16>(beta0, r, Z, C, norms, K, L, Tz, lam, lam_f, write_r, red, s);
+        CSC_RESYNC(16);
     if (kpt <= 64)
-        return resync_launch<64>(beta0, r, Z, C, norms, K, L, Tz, lam, lam_f, write_r, red, s);
+        CSC_RESYNC(64);
+#undef CSC_RESYNC
     return cudaErrorInvalidValue;
 }
 

@@ -45,32 +45,42 @@ __global__ void dtd_kernel(const float *__restrict__ D, int K, int P, int L,
     }
 }
 
-constexpr int kDtxTile = 256;   // output samples per block (one per thread)
-constexpr int kDtxAtoms = 8;    // atoms per block
+constexpr int kDtxThreads = 256;
+constexpr int kDtxT = 4;                            // consecutive outputs per thread
+constexpr int kDtxTile = kDtxThreads * kDtxT;       // output samples per block
+constexpr int kDtxAtoms = 8;                        // atoms per block
 
 // beta0[k][t] = sum_p sum_tau D[k][p][tau] X[p][t+tau] (Alg. 1 initialisation),
-// plus max |beta0| for lambda_max.  Block: 256 consecutive t, 8 atoms; X and D
-// tiles staged in shared memory (lags padded to a multiple of 8 with zeros).
-__global__ void __launch_bounds__(kDtxTile) dtx_kernel(const float *__restrict__ D,
-                                                       const float *__restrict__ X, int K, int P,
-                                                       int L, long long T,
-                                                       float *__restrict__ beta0,
-                                                       unsigned int *__restrict__ absmax_bits)
+// plus max |beta0| (lambda_max) and sum X^2 (2 E(0)).  Block: 1024 consecutive
+// t and 8 atoms; a thread owns 4 consecutive t, so each 8-lag step reads 12
+// samples of X (3 vector loads) and the 8 atoms' 8 lags (broadcast vector
+// loads) for 256 FMAs.  Lags are padded to a multiple of 8 with zeros.
+__global__ void __launch_bounds__(kDtxThreads) dtx_kernel(const float *__restrict__ D,
+                                                         const float *__restrict__ X, int K,
+                                                         int P, int L, long long T,
+                                                         float *__restrict__ beta0,
+                                                         unsigned int *__restrict__ absmax_bits,
+                                                         double *__restrict__ x2sum)
 {
-    extern __shared__ float sm[];
+    extern __shared__ __align__(16) float sm[];
     const int L8 = (L + 7) & ~7;
-    const int xw = kDtxTile + L8;  // X tile width (covers t + tau for tau < L8)
-    float *xs = sm;                               // [P][xw]
-    float *ds = sm + (size_t)P * xw;              // [kDtxAtoms][P][L8]
+    const int xw = kDtxTile + L8 + 4;  // X tile width, multiple of 4
+    float *xs = sm;                     // [P][xw]
+    float *ds = sm + (size_t)P * xw;    // [kDtxAtoms][P][L8]
     const long long Tz = T - L + 1;
     const long long t0 = (long long)blockIdx.x * kDtxTile;
     const int k0 = blockIdx.y * kDtxAtoms;
     const int nk = min(kDtxAtoms, K - k0);
 
+    double x2 = 0.0;
+    const bool last = t0 + kDtxTile >= Tz;  // the last block also owns samples [Tz, T)
     for (int i = threadIdx.x; i < P * xw; i += blockDim.x) {
         const int p = i / xw, j = i % xw;
         const long long t = t0 + j;
-        xs[i] = t < T ? X[(long long)p * T + t] : 0.f;
+        const float v = t < T ? X[(long long)p * T + t] : 0.f;
+        xs[i] = v;
+        if (blockIdx.y == 0 && (j < kDtxTile || last))
+            x2 += (double)v * (double)v;
     }
     for (int i = threadIdx.x; i < kDtxAtoms * P * L8; i += blockDim.x) {
         const int kk = i / (P * L8), r = i % (P * L8), p = r / L8, tau = r % L8;
@@ -78,48 +88,62 @@ __global__ void __launch_bounds__(kDtxTile) dtx_kernel(const float *__restrict__
     }
     __syncthreads();
 
-    const int j = threadIdx.x;
-    KahanF acc[kDtxAtoms];
+    const int j4 = threadIdx.x * kDtxT;
+    KahanF acc[kDtxAtoms][kDtxT];
     for (int p = 0; p < P; p++) {
-        const float *xr = xs + (size_t)p * xw + j;
+        const float *xr = xs + (size_t)p * xw + j4;
         for (int tb = 0; tb < L8; tb += 8) {
-            float x[8];
-#pragma unroll
-            for (int q = 0; q < 8; q++)
-                x[q] = xr[tb + q];
+            float x[12];
+            const float4 a0 = *reinterpret_cast<const float4 *>(xr + tb);
+            const float4 a1 = *reinterpret_cast<const float4 *>(xr + tb + 4);
+            const float4 a2 = *reinterpret_cast<const float4 *>(xr + tb + 8);
+            x[0] = a0.x; x[1] = a0.y; x[2] = a0.z; x[3] = a0.w;
+            x[4] = a1.x; x[5] = a1.y; x[6] = a1.z; x[7] = a1.w;
+            x[8] = a2.x; x[9] = a2.y; x[10] = a2.z; x[11] = a2.w;
 #pragma unroll
             for (int kk = 0; kk < kDtxAtoms; kk++) {
                 const float4 *dv = reinterpret_cast<const float4 *>(ds + ((size_t)kk * P + p) * L8 + tb);
                 const float4 d0 = dv[0], d1 = dv[1];
-                float part = d0.x * x[0];
-                part = fmaf(d0.y, x[1], part);
-                part = fmaf(d0.z, x[2], part);
-                part = fmaf(d0.w, x[3], part);
-                part = fmaf(d1.x, x[4], part);
-                part = fmaf(d1.y, x[5], part);
-                part = fmaf(d1.z, x[6], part);
-                part = fmaf(d1.w, x[7], part);
-                acc[kk].add(part);
+#pragma unroll
+                for (int q = 0; q < kDtxT; q++) {
+                    float part = d0.x * x[q];
+                    part = fmaf(d0.y, x[q + 1], part);
+                    part = fmaf(d0.z, x[q + 2], part);
+                    part = fmaf(d0.w, x[q + 3], part);
+                    part = fmaf(d1.x, x[q + 4], part);
+                    part = fmaf(d1.y, x[q + 5], part);
+                    part = fmaf(d1.z, x[q + 6], part);
+                    part = fmaf(d1.w, x[q + 7], part);
+                    acc[kk][q].add(part);
+                }
             }
         }
     }
-    const long long t = t0 + j;
     float amax = 0.f;
-    if (t < Tz) {
 #pragma unroll
-        for (int kk = 0; kk < kDtxAtoms; kk++) {
-            if (kk < nk) {
-                const float v = acc[kk].value();
-                beta0[(long long)(k0 + kk) * Tz + t] = v;
-                amax = fmaxf(amax, fabsf(v));
+    for (int q = 0; q < kDtxT; q++) {
+        const long long t = t0 + j4 + q;
+        if (t < Tz) {
+#pragma unroll
+            for (int kk = 0; kk < kDtxAtoms; kk++) {
+                if (kk < nk) {
+                    const float v = acc[kk][q].value();
+                    beta0[(long long)(k0 + kk) * Tz + t] = v;
+                    amax = fmaxf(amax, fabsf(v));
+                }
             }
         }
     }
     // block max of |beta0| -> one atomic per warp (non-negative floats order as uints)
-    for (int off = 16; off > 0; off >>= 1)
+    for (int off = 16; off > 0; off >>= 1) {
         amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
-    if ((threadIdx.x & 31) == 0)
+        x2 += __shfl_xor_sync(0xffffffffu, x2, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
         atomicMax(absmax_bits, __float_as_uint(amax));
+        if (blockIdx.y == 0)
+            atomicAdd(x2sum, x2);
+    }
 }
 
 __global__ void coef_by_lag_kernel(const float *__restrict__ C, int K, int L, int Kp,
@@ -156,10 +180,11 @@ cudaError_t launch_dtd(const float *D, int K, int P, int L, float *C, float *nor
 }
 
 cudaError_t launch_dtx(const float *D, const float *X, int K, int P, int L, int64_t T,
-                       float *beta0, unsigned int *absmax_bits, cudaStream_t s)
+                       float *beta0, unsigned int *absmax_bits, double *x2sum, cudaStream_t s)
 {
     const int L8 = (L + 7) & ~7;
-    const size_t smem = sizeof(float) * ((size_t)P * (kDtxTile + L8) + (size_t)kDtxAtoms * P * L8);
+    const size_t smem =
+        sizeof(float) * ((size_t)P * (kDtxTile + L8 + 4) + (size_t)kDtxAtoms * P * L8);
     if (smem > (size_t)kMaxSmem)
         return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(dtx_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -168,7 +193,7 @@ cudaError_t launch_dtx(const float *D, const float *X, int K, int P, int L, int6
         return e;
     const int64_t Tz = T - L + 1;
     dim3 grid((unsigned)((Tz + kDtxTile - 1) / kDtxTile), (unsigned)((K + kDtxAtoms - 1) / kDtxAtoms));
-    dtx_kernel<<<grid, kDtxTile, smem, s>>>(D, X, K, P, L, T, beta0, absmax_bits);
+    dtx_kernel<<<grid, kDtxThreads, smem, s>>>(D, X, K, P, L, T, beta0, absmax_bits, x2sum);
     return cudaGetLastError();
 }
 
