@@ -62,7 +62,8 @@ extern "C" {
 typedef struct csc_handle_s *csc_handle_t;
 
 typedef struct csc_opts {
-    int32_t segments;          /* M >= 1; 0 = automatic (width about 2L-2) */
+    int32_t segments;          /* M >= 1 for a single signal; 0 = automatic (see
+                                  segment_width).  Batches always use segment_width */
     int32_t updates_per_visit; /* u: updates a segment may apply per phase; 0 = until local
                                   convergence (bounded internally by 2^20) */
     int32_t max_resyncs;       /* FP64 beta re-synchronisations after the FP32 loop settles;
@@ -73,7 +74,11 @@ typedef struct csc_opts {
     int32_t max_sweeps;        /* 0 = default (1,000,000) */
     int32_t time_kernels;      /* 1 = time every phase launch with a CUDA event pair
                                   (csc_stats.phase_ms); 0 = off */
-    int32_t reserved[2];       /* must be zero */
+    int32_t segment_width;     /* target segment width in columns when segments is 0 or
+                                  the problem is a batch: each signal gets
+                                  max(1, floor(Tz_i / width)) segments.  0 = 2L-2, the
+                                  narrowest width that needs only 2 phases */
+    int32_t reserved[1];       /* must be zero */
 } csc_opts;
 
 typedef struct csc_stats {
@@ -141,10 +146,43 @@ int csc_init(csc_handle_t h, const float *X, int64_t T, double lambda, const flo
 int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, double *objective,
               csc_stats *stats);
 
+/*
+ * A batch of n independent problems sharing the atoms of csc_setup: signal i
+ * is X_i [P][T[i]] with its own lambda[i].  The signals are concatenated in
+ * time, X [P][sum T] (row p holds X_0[p], X_1[p], ... back to back), and so
+ * is Z: [K][sum T - L + 1], where the columns of signal i are
+ * [a_i, a_i + T[i] - L + 1) with a_i = T[0] + ... + T[i-1].  The L-1 columns
+ * after each signal's last valid one straddle two signals; they are kept at 0
+ * and belong to no problem (a warm start must hold 0 there).  Each signal is
+ * cut into its own segments (Sec. 2.2), so one solve runs the segments of all
+ * signals in the same phases and stops when every signal has converged; the
+ * result of each signal is that of solving it alone (Eq. sparse_code).
+ *   X       host or device, caller-owned; T[i] >= L; sum T - L + 1 < 2^31 - 1
+ *   T       [n] host array;  n >= 1
+ *   lambda  [n] host array, each > 0 and finite
+ *   Z0      NULL or the concatenated warm start
+ * csc_init(h, X, T, lambda, Z0) is csc_init_batch with n = 1.
+ */
+int csc_init_batch(csc_handle_t h, const float *X, const int64_t *T, int n, const double *lambda,
+                   const float *Z0);
+
+/* Replaces the lambdas of the current batch ([n] host array, each > 0) and
+ * keeps Z and beta: the next csc_solve continues from the current Z (a warm
+ * start along a regularisation path). */
+int csc_set_lambda(csc_handle_t h, const double *lambda);
+
+/* lambda_max of every signal of the current batch into out[n] (host). */
+int csc_lambda_max_batch(csc_handle_t h, double *out);
+
+/* E_i(Z) of every signal (host out[n]) from the last csc_solve or
+ * csc_objective; csc_solve's objective is their sum. */
+int csc_get_objectives(csc_handle_t h, double *out);
+
 /* Releases every device and host resource of the handle.  NULL is accepted. */
 int csc_destroy(csc_handle_t h);
 
-/* max_{k,t} |(D~_k * X)[t]| of the last csc_init: Z* = 0 iff lambda >= this. */
+/* max_{k,t} |(D~_k * X)[t]| of the last csc_init: Z* = 0 iff lambda >= this
+ * (for a batch, the largest over its signals). */
 int csc_lambda_max(csc_handle_t h, double *out);
 
 /* Copies the current beta [K][Tz] (float32) to host or device memory. */
@@ -154,7 +192,8 @@ int csc_get_beta(csc_handle_t h, float *beta_out);
 int csc_get_dtd(csc_handle_t h, float *dtd_out, float *norms_out);
 
 /* FP64 objective E(Z) of Eq. sparse_code for the handle's X and lambda and an
- * arbitrary Z [K][Tz] (host or device). */
+ * arbitrary Z [K][Tz] (host or device); for a batch, the sum over its signals
+ * (each one then available from csc_get_objectives). */
 int csc_objective(csc_handle_t h, const float *Z, double *out);
 
 /*

@@ -27,7 +27,7 @@ class csc_opts(ctypes.Structure):
     _fields_ = [("segments", ctypes.c_int32), ("updates_per_visit", ctypes.c_int32),
                 ("max_resyncs", ctypes.c_int32), ("sweeps_per_poll", ctypes.c_int32),
                 ("max_sweeps", ctypes.c_int32), ("time_kernels", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("segment_width", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class csc_stats(ctypes.Structure):
@@ -87,11 +87,16 @@ def load(path: str | None = None):
     lib.csc_kernel_launches.argtypes = [_vp, ctypes.POINTER(_i64)]
     lib.csc_objective_noalloc.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp,
                                           _i64, _vp, ctypes.c_double, _vp, _vp]
+    lib.csc_init_batch.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, _vp]
+    lib.csc_set_lambda.argtypes = [_vp, _vp]
+    lib.csc_lambda_max_batch.argtypes = [_vp, _vp]
+    lib.csc_get_objectives.argtypes = [_vp, _vp]
     lib.csc_last_error_string.argtypes = []
     lib.csc_last_error_string.restype = ctypes.c_char_p
     for name in ("csc_setup", "csc_init", "csc_solve", "csc_destroy", "csc_lambda_max",
                  "csc_get_beta", "csc_get_dtd", "csc_objective", "csc_get_trace", "csc_plan",
-                 "csc_kernel_launches", "csc_objective_noalloc"):
+                 "csc_kernel_launches", "csc_objective_noalloc", "csc_init_batch",
+                 "csc_set_lambda", "csc_lambda_max_batch", "csc_get_objectives"):
         getattr(lib, name).restype = ctypes.c_int
     if path == _build.LIB:
         _lib = lib
@@ -134,12 +139,13 @@ def _stream(stream):
 
 
 def make_opts(segments: int = 0, updates_per_visit: int = 0, max_resyncs: int = -1,
-              sweeps_per_poll: int = 0, max_sweeps: int = 0, time_kernels: int = 0) -> csc_opts:
+              sweeps_per_poll: int = 0, max_sweeps: int = 0, time_kernels: int = 0,
+              segment_width: int = 0) -> csc_opts:
     o = csc_opts()
     load().csc_default_opts(ctypes.byref(o))
     o.segments, o.updates_per_visit = segments, updates_per_visit
     o.max_resyncs, o.sweeps_per_poll, o.max_sweeps = max_resyncs, sweeps_per_poll, max_sweeps
-    o.time_kernels = time_kernels
+    o.time_kernels, o.segment_width = time_kernels, segment_width
     return o
 
 
@@ -154,6 +160,35 @@ def csc_setup(D, opts: csc_opts | None = None, stream=None, handle=None):
 
 def csc_init(h, X, lam: float, Z0=None) -> None:
     _check(load().csc_init(h, _ptr(X), int(X.shape[1]), float(lam), _ptr(Z0)))
+
+
+def csc_init_batch(h, X, T, lam, Z0=None) -> None:
+    """X [P, sum T] (signals concatenated in time); T and lam: one entry per signal."""
+    Ta = np.ascontiguousarray(np.asarray(T, dtype=np.int64).reshape(-1))
+    la = np.ascontiguousarray(np.asarray(lam, dtype=np.float64).reshape(-1))
+    if la.shape != Ta.shape:
+        raise ValueError("T and lam need one entry per signal")
+    if int(Ta.sum()) != int(X.shape[1]):
+        raise ValueError("X must hold sum(T) samples per channel")
+    _check(load().csc_init_batch(h, _ptr(X), Ta.ctypes.data, int(Ta.size), la.ctypes.data,
+                                 _ptr(Z0)))
+
+
+def csc_set_lambda(h, lam) -> None:
+    la = np.ascontiguousarray(np.asarray(lam, dtype=np.float64).reshape(-1))
+    _check(load().csc_set_lambda(h, la.ctypes.data))
+
+
+def csc_lambda_max_batch(h, n: int) -> np.ndarray:
+    out = np.zeros(n, np.float64)
+    _check(load().csc_lambda_max_batch(h, out.ctypes.data))
+    return out
+
+
+def csc_get_objectives(h, n: int) -> np.ndarray:
+    out = np.zeros(n, np.float64)
+    _check(load().csc_get_objectives(h, out.ctypes.data))
+    return out
 
 
 def csc_solve(h, tol: float, max_updates: int = 1 << 62, Z_out=None):

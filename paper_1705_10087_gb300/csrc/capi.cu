@@ -1,12 +1,18 @@
 // C ABI entry points (include/csc.h) and the host-side orchestration of the
-// solver: handle state, pointer-kind detection, the phase loop with its
-// convergence polls and FP64 resync rounds.
+// solver: handle state, pointer-kind detection, signal tables and segment
+// plans, the phase loop with its convergence polls and resync rounds.
+//
+// A problem is a batch of n >= 1 signals concatenated in time (csc_init is the
+// n = 1 case): see SignalView in csc_internal.cuh for why the concatenation is
+// exactly n separate problems.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "csc_internal.cuh"
 
@@ -85,6 +91,8 @@ cudaError_t copy_out(void *dst, const void *src, size_t bytes, cudaStream_t s)
                            s);
 }
 
+// Phases of the schedule for one signal: co-active segments m, m' (m == m'
+// mod c) must leave at least 2L-2 samples between them, (c-1) w_min >= 2L-2.
 int phase_count_host(int64_t Tz, int M, int L)
 {
     if (M <= 1)
@@ -97,10 +105,14 @@ int phase_count_host(int64_t Tz, int M, int L)
     return (int)(c > M ? M : c);
 }
 
+int64_t auto_width(int L)
+{
+    return 2 * (int64_t)L - 2 > 1 ? 2 * (int64_t)L - 2 : 1;
+}
+
 int auto_segments(int64_t Tz, int L)
 {
-    const int64_t w = 2 * (int64_t)L - 2 > 1 ? 2 * (int64_t)L - 2 : 1;
-    int64_t M = Tz / w;
+    int64_t M = Tz / auto_width(L);
     if (M < 1)
         M = 1;
     if (M > (1 << 30))
@@ -121,6 +133,15 @@ cudaError_t grow(T **p, size_t *cap, size_t n)
     if (e == cudaSuccess)
         *cap = n;
     return e;
+}
+
+template <class T>
+cudaError_t upload(T **p, size_t *cap, const std::vector<T> &v, cudaStream_t s)
+{
+    cudaError_t e = grow(p, cap, v.size());
+    if (e != cudaSuccess)
+        return e;
+    return cudaMemcpyAsync(*p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s);
 }
 
 }  // namespace
@@ -144,17 +165,42 @@ struct csc_handle_s {
     int K = 0, P = 0, L = 0;
     float *D = nullptr, *C = nullptr, *Ct = nullptr, *norms = nullptr;
     size_t cap_D = 0, cap_C = 0, cap_Ct = 0, cap_n = 0;
-    // problem state
+
+    // problem: n signals concatenated in time, T samples, Tz = T - L + 1 columns
     bool initialized = false;
     int64_t T = 0, Tz = 0;
-    double lambda = 0.0, lambda_max = 0.0;
+    int n = 0;
+    std::vector<int64_t> a;         // [n+1] sample starts
+    std::vector<double> lam;        // [n]
+    std::vector<double> lmax;       // [n]
+    std::vector<double> E_sig;      // [n] objectives of the last solve / csc_objective
+    std::vector<int64_t> tile_off;  // [n+1] first reduction tile of each signal
+    int64_t ntiles = 0;
+    int64_t *d_a = nullptr, *d_tile_s = nullptr, *d_tile_off = nullptr;
+    int *d_tile_sig = nullptr;
+    float *d_lam = nullptr;
+    double *d_lam_d = nullptr, *d_E = nullptr;
+    unsigned int *d_lmax = nullptr;
+    size_t cap_a = 0, cap_tile_s = 0, cap_tile_off = 0, cap_tile_sig = 0, cap_lam = 0,
+           cap_lam_d = 0, cap_E = 0, cap_lmax = 0;
+
     // r = beta - ||D_k||^2 Z, the form of beta the kernels keep (csc_internal.cuh)
     float *X = nullptr, *r = nullptr, *beta0 = nullptr, *Z = nullptr;
     size_t cap_X = 0, cap_r = 0, cap_beta0 = 0, cap_Z = 0;
     double *partials = nullptr;
     size_t cap_partials = 0;
+
+    // segment plan (rebuilt when the signals, lambdas or segment options change)
+    bool plan_ok = false;
+    int M = 0, c = 0, w_max = 0;
+    std::vector<int> phase_off;  // [c+1] into the phase list
+    int64_t *d_seg_s = nullptr, *d_seg_e = nullptr;
+    float *d_seg_lam = nullptr;
+    int *d_phase_list = nullptr;
+    size_t cap_seg_s = 0, cap_seg_e = 0, cap_seg_lam = 0, cap_phase = 0;
     unsigned char *dirty = nullptr;
     size_t cap_dirty = 0;
+
     float *tmpZ = nullptr, *tmpB = nullptr;
     size_t cap_tmpZ = 0, cap_tmpB = 0;
     Scratch *sc = nullptr;
@@ -163,11 +209,110 @@ struct csc_handle_s {
     cudaEvent_t *kev = nullptr;  // per-launch timing events (2 per launch of a poll batch)
     int n_kev = 0;
     int64_t launches = 0;        // kernels launched through this handle
-    bool z_is_zero = false;  // Z == 0 since csc_init: E(Z) = sum X^2 / 2 is known
+    bool z_is_zero = false;      // Z == 0 since csc_init: E(Z) = sum X^2 / 2 is known
     // last solve
     int64_t g_used = 0;
     double E_start = 0.0;
+
+    SignalView view() const { return SignalView{d_a, d_lam, n}; }
 };
+
+namespace {
+
+// Segments of every signal, their lambdas and the per-phase lists.
+int build_plan(csc_handle_t h)
+{
+    if (h->plan_ok)
+        return CSC_OK;
+    cudaStream_t s = h->stream;
+    const int L = h->L;
+    std::vector<int64_t> seg_s, seg_e;
+    std::vector<float> seg_lam;
+    std::vector<int> local;
+    int c = 1;
+    for (int i = 0; i < h->n; i++) {
+        const int64_t Tzi = h->a[i + 1] - h->a[i] - L + 1;
+        int Mi;
+        if (h->n == 1 && h->opts.segments > 0) {
+            Mi = h->opts.segments;
+            if (Mi > Tzi)
+                return fail(CSC_EINVAL, "csc_solve: %d segments exceed Tz = %lld", Mi,
+                            (long long)Tzi);
+        } else {
+            const int64_t w = h->opts.segment_width > 0 ? h->opts.segment_width : auto_width(L);
+            Mi = (int)std::max<int64_t>(1, Tzi / w);
+        }
+        c = std::max(c, phase_count_host(Tzi, Mi, L));
+        for (int m = 0; m < Mi; m++) {
+            seg_s.push_back(h->a[i] + seg_start(Tzi, Mi, m));
+            seg_e.push_back(h->a[i] + seg_start(Tzi, Mi, m + 1));
+            seg_lam.push_back((float)h->lam[i]);
+            local.push_back(m);
+        }
+    }
+    const int M = (int)seg_s.size();
+    int w_max = 1;
+    for (int m = 0; m < M; m++)
+        w_max = std::max<int>(w_max, (int)(seg_e[m] - seg_s[m]));
+    std::vector<int> list;
+    std::vector<int> off(c + 1, 0);
+    for (int p = 0; p < c; p++) {
+        off[p] = (int)list.size();
+        for (int m = 0; m < M; m++)
+            if (local[m] % c == p)
+                list.push_back(m);
+    }
+    off[c] = (int)list.size();
+    CSC_CUDA(upload(&h->d_seg_s, &h->cap_seg_s, seg_s, s));
+    CSC_CUDA(upload(&h->d_seg_e, &h->cap_seg_e, seg_e, s));
+    CSC_CUDA(upload(&h->d_seg_lam, &h->cap_seg_lam, seg_lam, s));
+    CSC_CUDA(upload(&h->d_phase_list, &h->cap_phase, list, s));
+    CSC_CUDA(grow(&h->dirty, &h->cap_dirty, (size_t)M));
+    // the host vectors must outlive the asynchronous copies
+    CSC_CUDA(cudaStreamSynchronize(s));
+    h->M = M;
+    h->c = c;
+    h->w_max = w_max;
+    h->phase_off = off;
+    h->plan_ok = true;
+    return CSC_OK;
+}
+
+// Per-signal objectives into h->E_sig (and their sum).
+int objectives(csc_handle_t h, const float *Zd, double *sum)
+{
+    cudaStream_t s = h->stream;
+    CSC_CUDA(launch_objective(h->D, h->X, Zd, h->K, h->P, h->L, h->T, h->view(), h->d_lam_d,
+                              h->d_tile_s, h->d_tile_sig, h->ntiles, h->d_tile_off, h->partials,
+                              h->d_E, s));
+    h->launches += 2;
+    CSC_CUDA(cudaMemcpyAsync(h->E_sig.data(), h->d_E, sizeof(double) * h->n,
+                             cudaMemcpyDeviceToHost, s));
+    CSC_CUDA(cudaStreamSynchronize(s));
+    double t = 0.0;
+    for (double v : h->E_sig)
+        t += v;
+    *sum = t;
+    return CSC_OK;
+}
+
+int set_lambdas(csc_handle_t h, const double *lambda)
+{
+    for (int i = 0; i < h->n; i++)
+        if (!(lambda[i] > 0.0) || !std::isfinite(lambda[i]))
+            return fail(CSC_EINVAL, "lambda[%d] must be positive and finite", i);
+    h->lam.assign(lambda, lambda + h->n);
+    std::vector<float> lf(h->n);
+    for (int i = 0; i < h->n; i++)
+        lf[i] = (float)h->lam[i];
+    CSC_CUDA(upload(&h->d_lam, &h->cap_lam, lf, h->stream));
+    CSC_CUDA(upload(&h->d_lam_d, &h->cap_lam_d, h->lam, h->stream));
+    CSC_CUDA(cudaStreamSynchronize(h->stream));
+    h->plan_ok = false;  // segment lambdas
+    return CSC_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -209,19 +354,13 @@ int csc_destroy(csc_handle_t h)
     cudaSetDevice(h->device);
     if (h->stream)
         cudaStreamSynchronize(h->stream);
-    cudaFree(h->D);
-    cudaFree(h->C);
-    cudaFree(h->Ct);
-    cudaFree(h->norms);
-    cudaFree(h->X);
-    cudaFree(h->r);
-    cudaFree(h->beta0);
-    cudaFree(h->Z);
-    cudaFree(h->partials);
-    cudaFree(h->dirty);
-    cudaFree(h->tmpZ);
-    cudaFree(h->tmpB);
-    cudaFree(h->sc);
+    void *bufs[] = {h->D,          h->C,          h->Ct,         h->norms,      h->X,
+                    h->r,          h->beta0,      h->Z,          h->partials,   h->dirty,
+                    h->tmpZ,       h->tmpB,       h->sc,         h->d_a,        h->d_tile_s,
+                    h->d_tile_off, h->d_tile_sig, h->d_lam,      h->d_lam_d,    h->d_E,
+                    h->d_lmax,     h->d_seg_s,    h->d_seg_e,    h->d_seg_lam,  h->d_phase_list};
+    for (void *p : bufs)
+        cudaFree(p);
     if (h->poll)
         cudaFreeHost(h->poll);
     if (h->ev0)
@@ -249,7 +388,7 @@ int csc_setup(csc_handle_t *hp, const float *D, int K, int P, int L, const csc_o
         o = *opts;
         if (o.segments < 0 || o.updates_per_visit < 0 || o.max_resyncs < -1 ||
             o.sweeps_per_poll < 0 || o.max_sweeps < 0 || o.time_kernels < 0 ||
-            o.time_kernels > 1 || o.reserved[0] || o.reserved[1])
+            o.time_kernels > 1 || o.segment_width < 0 || o.reserved[0])
             return fail(CSC_EINVAL, "csc_setup: invalid options");
     }
     csc_handle_t h = *hp;
@@ -271,6 +410,7 @@ int csc_setup(csc_handle_t *hp, const float *D, int K, int P, int L, const csc_o
     h->P = P;
     h->L = L;
     h->initialized = false;
+    h->plan_ok = false;
     auto body = [&]() -> int {
         CSC_CUDA(grow(&h->D, &h->cap_D, (size_t)K * P * L));
         CSC_CUDA(grow(&h->C, &h->cap_C, (size_t)K * K * (2 * L - 1)));
@@ -300,55 +440,110 @@ int csc_setup(csc_handle_t *hp, const float *D, int K, int P, int L, const csc_o
     return CSC_OK;
 }
 
-int csc_init(csc_handle_t h, const float *X, int64_t T, double lambda, const float *Z0)
+int csc_init_batch(csc_handle_t h, const float *X, const int64_t *T, int n, const double *lambda,
+                   const float *Z0)
 {
-    if (!h || !X)
-        return fail(CSC_EINVAL, "csc_init: null handle or X");
-    if (T < h->L)
-        return fail(CSC_EINVAL, "csc_init: T = %lld < L = %d", (long long)T, h->L);
-    if (!(lambda > 0.0) || !std::isfinite(lambda))
-        return fail(CSC_EINVAL, "csc_init: lambda must be positive and finite");
-    const int64_t Tz = T - h->L + 1;
-    if ((uint64_t)h->K * (uint64_t)Tz >= 0xFFFFFFFFull)
-        return fail(CSC_EINVAL, "csc_init: K*(T-L+1) must be below 2^32-1");
+    if (!h || !X || !T || !lambda)
+        return fail(CSC_EINVAL, "csc_init: null argument");
+    if (n < 1)
+        return fail(CSC_EINVAL, "csc_init: need at least one signal");
+    int64_t Ttot = 0;
+    for (int i = 0; i < n; i++) {
+        if (T[i] < h->L)
+            return fail(CSC_EINVAL, "csc_init: T[%d] = %lld < L = %d", i, (long long)T[i], h->L);
+        Ttot += T[i];
+    }
+    const int64_t Tz = Ttot - h->L + 1;
+    if (Tz >= ((int64_t)1 << 31) - 1)
+        return fail(CSC_EINVAL, "csc_init: T - L + 1 must be below 2^31 - 1 columns");
     cudaSetDevice(h->device);
     h->initialized = false;
+    h->plan_ok = false;
     cudaStream_t s = h->stream;
+    h->n = n;
+    h->T = Ttot;
+    h->Tz = Tz;
+    h->a.assign(n + 1, 0);
+    for (int i = 0; i < n; i++)
+        h->a[i + 1] = h->a[i] + T[i];
+    // reduction tiles: kTile samples of one signal
+    std::vector<int64_t> tile_s;
+    std::vector<int> tile_sig;
+    h->tile_off.assign(n + 1, 0);
+    for (int i = 0; i < n; i++) {
+        h->tile_off[i] = (int64_t)tile_s.size();
+        for (int64_t t = h->a[i]; t < h->a[i + 1]; t += kTile) {
+            tile_s.push_back(t);
+            tile_sig.push_back(i);
+        }
+    }
+    h->tile_off[n] = (int64_t)tile_s.size();
+    h->ntiles = (int64_t)tile_s.size();
+    h->E_sig.assign(n, 0.0);
+    h->lmax.assign(n, 0.0);
+    CSC_CUDA(upload(&h->d_a, &h->cap_a, h->a, s));
+    CSC_CUDA(upload(&h->d_tile_s, &h->cap_tile_s, tile_s, s));
+    CSC_CUDA(upload(&h->d_tile_sig, &h->cap_tile_sig, tile_sig, s));
+    CSC_CUDA(upload(&h->d_tile_off, &h->cap_tile_off, h->tile_off, s));
+    CSC_CUDA(grow(&h->d_E, &h->cap_E, (size_t)n));
+    CSC_CUDA(grow(&h->d_lmax, &h->cap_lmax, (size_t)n));
+    {
+        int rc = set_lambdas(h, lambda);  // also waits for the uploads above
+        if (rc != CSC_OK)
+            return rc;
+    }
     const size_t nz = (size_t)h->K * Tz;
-    CSC_CUDA(grow(&h->X, &h->cap_X, (size_t)h->P * T));
+    CSC_CUDA(grow(&h->X, &h->cap_X, (size_t)h->P * Ttot));
     CSC_CUDA(grow(&h->r, &h->cap_r, nz));
     CSC_CUDA(grow(&h->beta0, &h->cap_beta0, nz));
     CSC_CUDA(grow(&h->Z, &h->cap_Z, nz));
-    CSC_CUDA(grow(&h->partials, &h->cap_partials, 2 * (size_t)objective_blocks(T)));
-    CSC_CUDA(copy_in(h->X, X, sizeof(float) * h->P * T, s));
+    CSC_CUDA(grow(&h->partials, &h->cap_partials, 2 * (size_t)h->ntiles));
+    CSC_CUDA(copy_in(h->X, X, sizeof(float) * h->P * Ttot, s));
     CSC_CUDA(cudaMemsetAsync(&h->sc->lmax_bits, 0, sizeof(unsigned), s));
     CSC_CUDA(cudaMemsetAsync(&h->sc->x2, 0, sizeof(double), s));
-    CSC_CUDA(launch_dtx(h->D, h->X, h->K, h->P, h->L, T, h->beta0, &h->sc->lmax_bits,
+    CSC_CUDA(launch_dtx(h->D, h->X, h->K, h->P, h->L, Ttot, h->beta0, &h->sc->lmax_bits,
                         &h->sc->x2, s));
-    h->launches += 1;
+    CSC_CUDA(cudaMemsetAsync(h->d_lmax, 0, sizeof(unsigned) * n, s));
+    CSC_CUDA(launch_signal_absmax(h->beta0, h->K, h->L, Tz, h->view(), h->d_tile_s,
+                                  h->d_tile_sig, h->ntiles, h->d_lmax, s));
+    h->launches += 2;
     if (Z0) {
         h->launches += 1;
         CSC_CUDA(copy_in(h->Z, Z0, sizeof(float) * nz, s));
         CSC_CUDA(cudaMemsetAsync(h->sc->red, 0, sizeof(h->sc->red), s));
-        CSC_CUDA(cudaMemcpyAsync(h->r, h->beta0, sizeof(float) * nz, cudaMemcpyDeviceToDevice, s));
-        CSC_CUDA(launch_resync(h->beta0, h->r, h->Z, h->C, h->norms, h->K, h->L, Tz, lambda,
-                               (float)lambda, 1, h->sc->red, nullptr, 0, 0.f, s));
+        CSC_CUDA(launch_resync(h->beta0, h->r, h->Z, h->C, h->norms, h->K, h->L, Tz, h->view(),
+                               1, h->sc->red, nullptr, nullptr, 0, 0.f, s));
     } else {
         CSC_CUDA(cudaMemsetAsync(h->Z, 0, sizeof(float) * nz, s));
         CSC_CUDA(cudaMemcpyAsync(h->r, h->beta0, sizeof(float) * nz, cudaMemcpyDeviceToDevice, s));
     }
-    unsigned bits = 0;
-    CSC_CUDA(cudaMemcpyAsync(&bits, &h->sc->lmax_bits, sizeof bits, cudaMemcpyDeviceToHost, s));
+    std::vector<unsigned> bits(n);
+    CSC_CUDA(cudaMemcpyAsync(bits.data(), h->d_lmax, sizeof(unsigned) * n, cudaMemcpyDeviceToHost,
+                             s));
     CSC_CUDA(cudaStreamSynchronize(s));
-    float lm;
-    std::memcpy(&lm, &bits, sizeof lm);
-    h->lambda_max = lm;
-    h->T = T;
-    h->Tz = Tz;
-    h->lambda = lambda;
+    for (int i = 0; i < n; i++) {
+        float v;
+        std::memcpy(&v, &bits[i], sizeof v);
+        h->lmax[i] = v;
+    }
     h->z_is_zero = Z0 == nullptr;
     h->initialized = true;
     return CSC_OK;
+}
+
+int csc_init(csc_handle_t h, const float *X, int64_t T, double lambda, const float *Z0)
+{
+    return csc_init_batch(h, X, &T, 1, &lambda, Z0);
+}
+
+int csc_set_lambda(csc_handle_t h, const double *lambda)
+{
+    if (!h || !lambda)
+        return fail(CSC_EINVAL, "csc_set_lambda: null argument");
+    if (!h->initialized)
+        return fail(CSC_ESTATE, "csc_set_lambda: call csc_init first");
+    cudaSetDevice(h->device);
+    return set_lambdas(h, lambda);
 }
 
 int csc_lambda_max(csc_handle_t h, double *out)
@@ -357,7 +552,27 @@ int csc_lambda_max(csc_handle_t h, double *out)
         return fail(CSC_EINVAL, "csc_lambda_max: null argument");
     if (!h->initialized)
         return fail(CSC_ESTATE, "csc_lambda_max: call csc_init first");
-    *out = h->lambda_max;
+    *out = *std::max_element(h->lmax.begin(), h->lmax.end());
+    return CSC_OK;
+}
+
+int csc_lambda_max_batch(csc_handle_t h, double *out)
+{
+    if (!h || !out)
+        return fail(CSC_EINVAL, "csc_lambda_max_batch: null argument");
+    if (!h->initialized)
+        return fail(CSC_ESTATE, "csc_lambda_max_batch: call csc_init first");
+    std::copy(h->lmax.begin(), h->lmax.end(), out);
+    return CSC_OK;
+}
+
+int csc_get_objectives(csc_handle_t h, double *out)
+{
+    if (!h || !out)
+        return fail(CSC_EINVAL, "csc_get_objectives: null argument");
+    if (!h->initialized)
+        return fail(CSC_ESTATE, "csc_get_objectives: call csc_init first");
+    std::copy(h->E_sig.begin(), h->E_sig.end(), out);
     return CSC_OK;
 }
 
@@ -373,11 +588,13 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
     cudaSetDevice(h->device);
     cudaStream_t s = h->stream;
     const int64_t Tz = h->Tz;
-    const int M = h->opts.segments ? h->opts.segments : auto_segments(Tz, h->L);
-    if (M > Tz)
-        return fail(CSC_EINVAL, "csc_solve: %d segments exceed Tz = %lld", M, (long long)Tz);
-    const int c = phase_count_host(Tz, M, h->L);
-    const PhaseConfig cfg = phase_config(h->K, h->L, Tz, M);
+    {
+        int rc = build_plan(h);
+        if (rc != CSC_OK)
+            return rc;
+    }
+    const int M = h->M, c = h->c;
+    const PhaseConfig cfg = phase_config(h->K, h->L, h->w_max);
     const int S = h->opts.sweeps_per_poll ? h->opts.sweeps_per_poll : 4;
     const int64_t max_sweeps = h->opts.max_sweeps ? h->opts.max_sweeps : 1000000;
     const int max_resyncs = h->opts.max_resyncs < 0 ? 3 : h->opts.max_resyncs;
@@ -399,7 +616,6 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
         }
     }
 
-    CSC_CUDA(grow(&h->dirty, &h->cap_dirty, (size_t)M));
     CSC_CUDA(cudaMemsetAsync(h->dirty, 1, (size_t)M, s));
     CSC_CUDA(cudaMemsetAsync(sc, 0, offsetof(Scratch, lmax_bits), s));
     CSC_CUDA(cudaMemsetAsync(sc->red, 0, sizeof(sc->red), s));
@@ -407,10 +623,11 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
     CSC_CUDA(launch_stamp(&sc->tstart, s));
     h->launches += 1;
     const bool cold = h->z_is_zero;
+    double E0 = 0.0;
     if (!cold) {
-        CSC_CUDA(launch_objective(h->D, h->X, h->Z, h->K, h->P, h->L, h->T, h->lambda,
-                                  h->partials, &sc->obj[0], s));
-        h->launches += 2;
+        int rc = objectives(h, h->Z, &E0);
+        if (rc != CSC_OK)
+            return rc;
     }
     h->z_is_zero = false;
 
@@ -422,6 +639,9 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
     pp.Kp = coef_pad(h->K);
     pp.norms = h->norms;
     pp.dirty = h->dirty;
+    pp.seg_s = h->d_seg_s;
+    pp.seg_e = h->d_seg_e;
+    pp.seg_lam = h->d_seg_lam;
     pp.upd = sc->upd;
     pp.dec = sc->dec;
     pp.tend = sc->tend;
@@ -435,12 +655,11 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
     pp.K = h->K;
     pp.L = h->L;
     pp.u = h->opts.updates_per_visit ? h->opts.updates_per_visit : kDefaultMaxVisit;
-    pp.lam = (float)h->lambda;
     // CD runs to tol/2 and a resync accepts at tol: coordinates left just under
-    // the inner tolerance then stay under tol after the exact FP64 refresh,
-    // instead of bouncing back above it round after round
+    // the inner tolerance then stay under tol after the exact refresh, instead
+    // of bouncing back above it round after round
     pp.tol = (float)(max_resyncs > 0 ? 0.5 * tol : tol);
-    pp.w_max = (int)((Tz + M - 1) / M);
+    pp.w_max = h->w_max;
 
     int status = CSC_OK;
     bool converged = false, report_fresh = false;
@@ -464,9 +683,10 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
                     pp.p = p;
                     pp.g = (int)g;
                     pp.g_round = (int)g_round;
+                    pp.phase_list = h->d_phase_list + h->phase_off[p];
                     if (timed)
                         CSC_CUDA(cudaEventRecord(h->kev[2 * nb], s));
-                    CSC_CUDA(launch_phase(pp, cfg, s));
+                    CSC_CUDA(launch_phase(pp, cfg, h->phase_off[p + 1] - h->phase_off[p], s));
                     if (timed)
                         CSC_CUDA(cudaEventRecord(h->kev[2 * nb + 1], s));
                     nb++;
@@ -511,8 +731,8 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
         // segments come back dirty only where the refreshed state has a
         // coordinate at or above the inner tolerance
         CSC_CUDA(cudaMemsetAsync(h->dirty, 0, (size_t)M, s));
-        CSC_CUDA(launch_resync(h->beta0, h->r, h->Z, h->C, h->norms, h->K, h->L, Tz,
-                               h->lambda, (float)h->lambda, 1, sc->red, h->dirty, M, pp.tol, s));
+        CSC_CUDA(launch_resync(h->beta0, h->r, h->Z, h->C, h->norms, h->K, h->L, Tz, h->view(),
+                               1, sc->red, h->dirty, h->d_seg_s, M, pp.tol, s));
         h->launches += 1;
         unsigned long long red[8];
         CSC_CUDA(cudaMemcpyAsync(red, sc->red, sizeof red, cudaMemcpyDeviceToHost, s));
@@ -529,23 +749,25 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
         }
     }
     if (!report_fresh) {
-        // optimality report against a fresh FP64 beta, leaving beta unchanged
+        // optimality report against a fresh r, leaving r unchanged
         CSC_CUDA(cudaMemsetAsync(sc->red, 0, sizeof(sc->red), s));
-        CSC_CUDA(launch_resync(h->beta0, h->r, h->Z, h->C, h->norms, h->K, h->L, Tz,
-                               h->lambda, (float)h->lambda, 0, sc->red, nullptr, 0, 0.f, s));
+        CSC_CUDA(launch_resync(h->beta0, h->r, h->Z, h->C, h->norms, h->K, h->L, Tz, h->view(),
+                               0, sc->red, nullptr, nullptr, 0, 0.f, s));
         h->launches += 1;
     }
     CSC_CUDA(cudaEventRecord(h->ev1, s));
-    CSC_CUDA(launch_objective(h->D, h->X, h->Z, h->K, h->P, h->L, h->T, h->lambda, h->partials,
-                              &sc->obj[1], s));
-    h->launches += 2;
+    double E = 0.0;
+    {
+        int rc = objectives(h, h->Z, &E);
+        if (rc != CSC_OK)
+            return rc;
+    }
     if (Z_out)
         CSC_CUDA(copy_out(Z_out, h->Z, sizeof(float) * h->K * Tz, s));
     unsigned long long red[8];
-    double obj[2], x2 = 0.0;
+    double x2 = 0.0;
     long long total = 0, visits = 0;
     CSC_CUDA(cudaMemcpyAsync(red, sc->red, sizeof red, cudaMemcpyDeviceToHost, s));
-    CSC_CUDA(cudaMemcpyAsync(obj, sc->obj, sizeof obj, cudaMemcpyDeviceToHost, s));
     CSC_CUDA(cudaMemcpyAsync(&x2, &sc->x2, sizeof x2, cudaMemcpyDeviceToHost, s));
     CSC_CUDA(cudaMemcpyAsync(&total, &sc->total, sizeof total, cudaMemcpyDeviceToHost, s));
     CSC_CUDA(cudaMemcpyAsync(&visits, &sc->visits, sizeof visits, cudaMemcpyDeviceToHost, s));
@@ -553,9 +775,9 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
     float ms = 0.f;
     CSC_CUDA(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
     h->g_used = g;
-    h->E_start = cold ? 0.5 * x2 : obj[0];
+    h->E_start = cold ? 0.5 * x2 : E0;
     if (objective)
-        *objective = obj[1];
+        *objective = E;
     if (stats) {
         double v[5];
         std::memcpy(v, red, sizeof v);
@@ -565,7 +787,7 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
         stats->phases = c;
         stats->resyncs = resyncs;
         stats->converged = converged ? 1 : 0;
-        stats->objective = obj[1];
+        stats->objective = E;
         stats->max_drift = drift;
         stats->kkt_zero_excess = v[1];
         stats->kkt_nonzero_gap = v[2];
@@ -637,12 +859,7 @@ int csc_objective(csc_handle_t h, const float *Z, double *out)
         CSC_CUDA(cudaMemcpyAsync(h->tmpZ, Z, sizeof(float) * nz, cudaMemcpyHostToDevice, s));
         Zd = h->tmpZ;
     }
-    CSC_CUDA(launch_objective(h->D, h->X, Zd, h->K, h->P, h->L, h->T, h->lambda, h->partials,
-                              &h->sc->obj[1], s));
-    h->launches += 2;
-    CSC_CUDA(cudaMemcpyAsync(out, &h->sc->obj[1], sizeof(double), cudaMemcpyDeviceToHost, s));
-    CSC_CUDA(cudaStreamSynchronize(s));
-    return CSC_OK;
+    return objectives(h, Zd, out);
 }
 
 int csc_get_trace(csc_handle_t h, int64_t cap, int64_t *updates, double *decrease,

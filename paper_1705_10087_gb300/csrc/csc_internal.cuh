@@ -93,6 +93,32 @@ struct KahanF {
     __device__ __forceinline__ float value() const { return __fsub_rn(s, c); }
 };
 
+// Index of the interval holding x in a sorted array of n+1 boundaries:
+// the largest i in [0, n) with a[i] <= x (a[0] <= x < a[n] assumed).
+__host__ __device__ __forceinline__ int interval_of(const int64_t *a, int n, int64_t x)
+{
+    int lo = 0, hi = n;  // a[lo] <= x < a[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] <= x)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Signals of a batch: n signals concatenated in time; signal i owns samples
+// [a[i], a[i+1]) and its valid activation columns [a[i], a[i+1] - L + 1).
+// The L-1 columns [a[i+1] - L + 1, a[i+1]) straddle two signals: they belong
+// to no segment and stay 0, which makes the batch exactly n separate problems
+// (a valid column of signal i and one of signal i+1 are at least L apart).
+struct SignalView {
+    const int64_t *a;   // [n+1]
+    const float *lam;   // [n]
+    int n;
+};
+
 // Parameters of one phase launch (see kernel_phase.cu).
 struct PhaseParams {
     float *r;                  // r = beta - n Z, [K][Tz]
@@ -101,6 +127,10 @@ struct PhaseParams {
     const float *Ct;           // DtD by lag: Ct[(k0 * W2 + s) * Kp + k] = DtD[k0][k][s], 0 for k >= K
     const float *norms;        // [K]
     unsigned char *dirty;      // [M] segment needs a visit
+    const int64_t *seg_s;      // [M] first column of each segment
+    const int64_t *seg_e;      // [M] one past its last column
+    const float *seg_lam;      // [M] lambda of the segment's signal
+    const int *phase_list;     // segments of this phase (grid = their count)
     long long *upd;            // [kPhaseRing] updates per phase launch
     double *dec;               // [kPhaseRing] objective decrease per phase launch
     unsigned long long *tend;  // [kPhaseRing] globaltimer at the end of the launch
@@ -113,7 +143,7 @@ struct PhaseParams {
     int g;        // launch index (monotone within a solve)
     int g_round;  // first launch index of the current CD round
     int u;        // cap on updates per visit
-    float lam, tol;
+    float tol;
     int w_max;  // widest segment (shared-memory layout)
 };
 
@@ -123,8 +153,11 @@ struct PhaseConfig {
     bool tile_in_smem;
 };
 
-PhaseConfig phase_config(int K, int L, int64_t Tz, int M);
-cudaError_t launch_phase(const PhaseParams &pp, const PhaseConfig &cfg, cudaStream_t s);
+// w_max: widest segment of the plan.
+PhaseConfig phase_config(int K, int L, int w_max);
+// active = number of segments in pp.phase_list (the grid size).
+cudaError_t launch_phase(const PhaseParams &pp, const PhaseConfig &cfg, int active,
+                         cudaStream_t s);
 
 cudaError_t launch_dtd(const float *D, int K, int P, int L, float *C, float *norms,
                        cudaStream_t s);
@@ -138,28 +171,46 @@ cudaError_t launch_coef_by_lag(const float *C, int K, int L, float *Ct, cudaStre
 cudaError_t launch_dtx(const float *D, const float *X, int K, int P, int L, int64_t T,
                        float *beta0, unsigned int *absmax_bits, double *x2sum, cudaStream_t s);
 
-// FP64 re-synchronisation of r with its definition, r = D~*X - sum_{l,t'} S Z
-// (beta0 = D~*X), rounded once to float, and the optimality report.
-// red[0..4] receive (as non-negative double bit patterns for atomicMax): the
-// drift max |r_old - r_fp64|, zero_excess, nonzero_gap, max_delta_z (FP64
-// beta = r + n Z), and max |Delta Z| of coord_step on the float state.
-// With dirty != NULL, also marks dirty[m] = 1 for every segment m of M that
-// holds a coordinate whose coord_step change on the new state is >= tol_mark
-// (the segments CD has to revisit after the refresh).
+// Re-synchronisation of r with its definition, r = D~*X - sum_{l,t'} S Z
+// (beta0 = D~*X), accumulated in double-float and rounded once to float, and
+// the optimality report over the valid columns of every signal.  red[0..4]
+// receive (as non-negative double bit patterns for atomicMax): the drift
+// max |r_old - r_new|, zero_excess, nonzero_gap, max_delta_z, and the largest
+// coord_step change on the float state.  With dirty != NULL, also marks
+// dirty[m] = 1 for every segment m (bounds seg_s, M entries) that holds a
+// coordinate whose coord_step change on the new state is >= tol_mark.
 cudaError_t launch_resync(const float *beta0, float *r, const float *Z, const float *C,
-                          const float *norms, int K, int L, int64_t Tz, double lam,
-                          float lam_f, int write_r, unsigned long long *red,
-                          unsigned char *dirty, int M, float tol_mark, cudaStream_t s);
+                          const float *norms, int K, int L, int64_t Tz, SignalView sig,
+                          int write_r, unsigned long long *red, unsigned char *dirty,
+                          const int64_t *seg_s, int M, float tol_mark, cudaStream_t s);
 
 // out = r + n Z (beta of Sec. 2.1) in float.
 cudaError_t launch_beta_from_r(const float *r, const float *Z, const float *norms, int K,
                                int64_t Tz, float *out, cudaStream_t s);
 
-// FP64 objective E(Z) (Eq. sparse_code) into *out, via per-block partials.
-int objective_blocks(int64_t T);
+// Reduction tiles: kTile consecutive samples of one signal.
+constexpr int kTile = 256;
+
+// FP64 objective E_i(Z) (Eq. sparse_code) of every signal into out[i]: tile b
+// covers samples [tile_s[b], min(tile_s[b] + kTile, a[tile_sig[b] + 1])) and
+// its partial sums land in partials[2b..2b+1]; tile_off[i] = first tile of
+// signal i (n+1 entries, device).  lam_d: lambda per signal in double.
 cudaError_t launch_objective(const float *D, const float *X, const float *Z, int K, int P, int L,
-                             int64_t T, double lam, double *partials, double *out,
+                             int64_t T, SignalView sig, const double *lam_d,
+                             const int64_t *tile_s, const int *tile_sig, int64_t ntiles,
+                             const int64_t *tile_off, double *partials, double *out,
                              cudaStream_t s);
+
+// The same for one signal [0, T) with a scalar lambda and no tables: tiles are
+// consecutive and partials holds 2 * ceil(T / kTile) doubles; out[0] = E.
+cudaError_t launch_objective_single(const float *D, const float *X, const float *Z, int K, int P,
+                                    int L, int64_t T, double lambda, double *partials,
+                                    double *out, cudaStream_t s);
+
+// max |beta0| over the valid columns of each signal (out: float bits, zeroed).
+cudaError_t launch_signal_absmax(const float *beta0, int K, int L, int64_t Tz, SignalView sig,
+                                 const int64_t *tile_s, const int *tile_sig, int64_t ntiles,
+                                 unsigned int *out, cudaStream_t s);
 
 cudaError_t launch_stamp(unsigned long long *out, cudaStream_t s);
 

@@ -17,8 +17,8 @@
 //   2. keeps, per owned column t, the best coordinate over k of
 //      |Delta Z_k[t]| = |Sh(beta_k[t], lambda)/||D_k||^2 - Z_k[t]| (Eq. pb_coord,
 //      evaluated from r by coord_step) as a 64-bit key
-//      (|Delta Z| bits << 32 | ~(k*Tz + t)): the max key is the largest
-//      |Delta Z| with ties to the lowest flat index,
+//      (|Delta Z| bits << 32 | ~(k*w + t - s)): the max key is the largest
+//      |Delta Z| with ties to the lowest (k, t), i.e. the lowest k*Tz + t,
 //   3. repeats: block argmax (warp max + one barrier), stop if the best
 //      |Delta Z| < tol (Alg. 1 stopping rule) or after u updates, else
 //      Z_k0[t0] <- Z' and r_k[t] -= S_{k,k0}[t-t0] (Z' - Z_old) for every k
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseP
 
     // ---- early exits, decided by one thread so the block stays uniform ----
     // (total is being incremented by other blocks of this launch)
-    const int m = pp.p + pp.c * (int)blockIdx.x;  // < M by the grid size
+    const int m = pp.phase_list[blockIdx.x];  // a segment of this phase
     if (threadIdx.x == 0) {
         int go = 1;
         if (*(volatile int *)pp.done) {
@@ -147,13 +147,13 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseP
     const int K = KFIX ? KT : pp.K, L = pp.L, W2 = 2 * L - 1;
     const int Kp = KFIX ? KPC : pp.Kp;
     const int64_t Tz = pp.Tz;
-    const int64_t s = seg_start(Tz, pp.M, m), e = seg_start(Tz, pp.M, m + 1);
+    const int64_t s = pp.seg_s[m], e = pp.seg_e[m];
     const int w = (int)(e - s);
     // blockDim == MAXT, a power of two >= 2L-1 (see phase_config)
     constexpr int B = MAXT;
     constexpr int nwarps = B >> 5;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const float lam = pp.lam, tol = pp.tol;
+    const float lam = pp.seg_lam[m], tol = pp.tol;
 
     const Layout lay(K, pp.w_max, SMEM);
     unsigned long long *ckey = reinterpret_cast<unsigned long long *>(smem_raw + lay.key);
@@ -224,7 +224,8 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseP
                 }
             }
         }
-        const unsigned flat = (unsigned)bk * (unsigned)Tz + (unsigned)(s + jj);
+        // segment-local flat index: same order as k * Tz + t inside the segment
+        const unsigned flat = (unsigned)bk * (unsigned)pp.w_max + (unsigned)jj;
         ckey[jj] = best > 0.f ? ((unsigned long long)__float_as_uint(best) << 32) | (unsigned)(~flat)
                               : 0ull;
         cz[jj] = bz;
@@ -270,7 +271,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseP
             for (int k = 0; k < K; k++)
                 visit(k);
         }
-        const unsigned flat = (unsigned)bk * (unsigned)Tz + (unsigned)(s + jj);
+        const unsigned flat = (unsigned)bk * (unsigned)pp.w_max + (unsigned)jj;
         ckey[jj] = best > 0.f ? ((unsigned long long)__float_as_uint(best) << 32) | (unsigned)(~flat)
                               : 0ull;
         cz[jj] = bz;
@@ -433,9 +434,11 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseP
         if (nupd > 0) {
             // neighbours whose r changed: segments meeting [tmin-L+1, tmax+L-1]
             const int64_t lo = tmin - (L - 1), hi = tmax + (L - 1);
-            for (int mm = m - 1; mm >= 0 && seg_start(Tz, pp.M, mm + 1) > lo; mm--)
+            // (segments are ordered by position; those of another signal never
+            //  meet the range, the straddling columns keep them L apart)
+            for (int mm = m - 1; mm >= 0 && pp.seg_e[mm] > lo; mm--)
                 pp.dirty[mm] = 1;
-            for (int mm = m + 1; mm < pp.M && seg_start(Tz, pp.M, mm) <= hi; mm++)
+            for (int mm = m + 1; mm < pp.M && pp.seg_s[mm] <= hi; mm++)
                 pp.dirty[mm] = 1;
             const int slot = pp.g & (kPhaseRing - 1);
             atomicAdd(reinterpret_cast<unsigned long long *>(&pp.upd[slot]),
@@ -450,9 +453,8 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseP
 
 }  // namespace
 
-PhaseConfig phase_config(int K, int L, int64_t Tz, int M)
+PhaseConfig phase_config(int K, int L, int wmax)
 {
-    const int64_t wmax = (Tz + M - 1) / M;  // widest segment
     PhaseConfig cfg;
     cfg.tile_in_smem = Layout(K, (int)wmax, true).total <= (size_t)kMaxSmem;
     cfg.smem = Layout(K, (int)wmax, cfg.tile_in_smem).total;
@@ -464,9 +466,9 @@ PhaseConfig phase_config(int K, int L, int64_t Tz, int M)
     return cfg;
 }
 
-cudaError_t launch_phase(const PhaseParams &pp, const PhaseConfig &cfg, cudaStream_t s)
+cudaError_t launch_phase(const PhaseParams &pp, const PhaseConfig &cfg, int active,
+                         cudaStream_t s)
 {
-    const int active = pp.p < pp.M ? (pp.M - 1 - pp.p) / pp.c + 1 : 0;
     if (active == 0)
         return cudaSuccess;
     if (cfg.smem > (size_t)kMaxSmem)

@@ -1,11 +1,11 @@
-// FP64 kernels (the only FP64 arithmetic on the GPU): the periodic / final
-// re-synchronisation of the solver state r = beta - n Z with its definition
-// (Sec. 2.1) and the objective E(Z) of Eq. sparse_code from the explicit
-// residual.
+// The re-synchronisation of the solver state r = beta - n Z with its
+// definition (Sec. 2.1), the objective E(Z) of Eq. sparse_code from the
+// explicit residual (FP64, one value per signal), and per-signal lambda_max.
 //
 // Both exploit that Z is sparse: a block gathers the nonzeros of Z that can
 // reach its tile (compacted in a fixed order, so results are deterministic)
-// and every thread accumulates its outputs over that list in FP64.
+// and every thread accumulates its outputs over that list in double-float
+// (pairs of floats with error-free transformations), combined in FP64.
 #include "csc_internal.cuh"
 
 namespace csc {
@@ -16,7 +16,7 @@ constexpr int kChunk = 64;  // Z columns scanned per compaction round
 
 struct NZ {
     int k;
-    int t;  // absolute time index (fits: Tz < 2^31 enforced by the 32-bit flat index)
+    int t;  // absolute column index (Tz < 2^31 is checked by csc_init)
     float z;
 };
 
@@ -96,14 +96,14 @@ template <int KPT>
 __global__ void __launch_bounds__(kResyncThreads)
     resync_kernel(const float *__restrict__ beta0, float *__restrict__ rr,
                   const float *__restrict__ Z, const float *__restrict__ C,
-                  const float *__restrict__ norms, int K, int L, int64_t Tz, double lam,
-                  float lam_f, int write_r, unsigned long long *__restrict__ red,
-                  unsigned char *__restrict__ dirty, int M, float tol_mark)
+                  const float *__restrict__ norms, int K, int L, int64_t Tz, SignalView sig,
+                  int write_r, unsigned long long *__restrict__ red,
+                  unsigned char *__restrict__ dirty, const int64_t *__restrict__ seg_s, int M,
+                  float tol_mark)
 {
     __shared__ NZ list[32 * kChunk];
     __shared__ int warp_counts[32];
-    __shared__ float bred[4][kResyncThreads / 32];
-    __shared__ float bred32[kResyncThreads / 32];
+    __shared__ float bred[5][kResyncThreads / 32];
     const int W2 = 2 * L - 1;
     const int tid = threadIdx.x;
     const int col = tid % kResyncCols, grp = tid / kResyncCols;
@@ -142,6 +142,14 @@ __global__ void __launch_bounds__(kResyncThreads)
     }
 
     float drift = 0.f, zex = 0.f, nzg = 0.f, all = 0.f, dz32 = 0.f;
+    // the column's signal: valid columns are [a_i, a_{i+1} - L + 1)
+    bool valid = false;
+    float lam = 0.f;
+    if (t < Tz) {
+        const int i = interval_of(sig.a, sig.n, t);
+        valid = t <= sig.a[i + 1] - L;
+        lam = sig.lam[i];
+    }
     if (t < Tz) {
 #pragma unroll
         for (int q = 0; q < KPT; q++) {
@@ -151,43 +159,38 @@ __global__ void __launch_bounds__(kResyncThreads)
             const int64_t ix = (int64_t)k * Tz + t;
             // r = beta0 - (hi + lo), finished with TwoSum so that only the final
             // float rounding remains
-            const float b0 = beta0[ix], hi = acc_hi[q], lo = acc_lo[q];
-            const float sm = __fsub_rn(b0, hi);
+            const float b0 = beta0[ix], ah = acc_hi[q], al = acc_lo[q];
+            const float sm = __fsub_rn(b0, ah);
             const float bv = __fsub_rn(sm, b0);
-            const float er = __fadd_rn(__fsub_rn(b0, __fsub_rn(sm, bv)), __fsub_rn(-hi, bv));
-            const float r32 = __fadd_rn(sm, __fsub_rn(er, lo));
+            const float er = __fadd_rn(__fsub_rn(b0, __fsub_rn(sm, bv)), __fsub_rn(-ah, bv));
+            const float r32 = __fadd_rn(sm, __fsub_rn(er, al));
             const float rold = rr[ix];
-            drift = fmaxf(drift, fabsf(rold - r32));
             if (write_r)
                 rr[ix] = r32;
+            if (!valid)
+                continue;  // a straddling column: frozen at 0, not part of any problem
+            drift = fmaxf(drift, fabsf(rold - r32));
             const float z = Z[ix];
             const float n = norms[k], rn = __frcp_rn(n);
             // optimality in the r form (Theorem A.1): z = 0 needs |beta| = |r| <= lam;
             // otherwise |Z' - z| with Z' from Eq. pb_coord, without cancellation
             float gap;
             if (z == 0.f) {
-                zex = fmaxf(zex, fabsf(r32) - lam_f);
-                gap = soft_f(r32, lam_f) * rn;
+                zex = fmaxf(zex, fabsf(r32) - lam);
+                gap = soft_f(r32, lam) * rn;
             } else {
                 const float sg = z > 0.f ? 1.f : -1.f;
                 const float b = fmaf(n, z, r32);
-                gap = b * sg > lam_f ? (r32 - lam_f * sg) * rn : soft_f(b, lam_f) * rn - z;
+                gap = b * sg > lam ? (r32 - lam * sg) * rn : soft_f(b, lam) * rn - z;
                 nzg = fmaxf(nzg, fabsf(gap));
             }
             all = fmaxf(all, fabsf(gap));
             // the phase kernel's own test on the float state it will see
             float zn, d32;
-            coord_step(write_r ? r32 : rold, z, n, rn, lam_f, &zn, &d32);
+            coord_step(write_r ? r32 : rold, z, n, rn, lam, &zn, &d32);
             dz32 = fmaxf(dz32, fabsf(d32));
-            if (dirty && fabsf(d32) >= tol_mark) {
-                // the segment of t: the m with floor(m Tz / M) <= t < floor((m+1) Tz / M)
-                int m = (int)(((t + 1) * (int64_t)M - 1) / Tz);
-                while (m > 0 && seg_start(Tz, M, m) > t)
-                    m--;
-                while (m + 1 < M && seg_start(Tz, M, m + 1) <= t)
-                    m++;
-                dirty[m] = 1;
-            }
+            if (dirty && fabsf(d32) >= tol_mark)
+                dirty[interval_of(seg_s, M, t)] = 1;  // segments cover every valid column
         }
     }
     // block reduce (max) and one atomic per block and quantity
@@ -204,45 +207,45 @@ __global__ void __launch_bounds__(kResyncThreads)
         bred[1][warp] = zex;
         bred[2][warp] = nzg;
         bred[3][warp] = all;
-        bred32[warp] = dz32;
+        bred[4][warp] = dz32;
     }
     __syncthreads();
     if (tid == 0) {
-        float v[4] = {0.f, 0.f, 0.f, 0.f};
-        float v32 = 0.f;
-        for (int w = 0; w < kResyncThreads / 32; w++) {
-            for (int q = 0; q < 4; q++)
+        float v[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int w = 0; w < kResyncThreads / 32; w++)
+            for (int q = 0; q < 5; q++)
                 v[q] = fmaxf(v[q], bred[q][w]);
-            v32 = fmaxf(v32, bred32[w]);
-        }
-        for (int q = 0; q < 4; q++)
+        for (int q = 0; q < 5; q++)
             atomicMax(&red[q], (unsigned long long)__double_as_longlong((double)v[q]));
-        atomicMax(&red[4], (unsigned long long)__double_as_longlong((double)v32));
     }
 }
 
-constexpr int kObjTile = 256;  // samples per block, one per thread
-constexpr int kObjP = 8;       // channels accumulated per pass
+constexpr int kObjP = 8;  // channels accumulated per pass
 
-// partial[b] = (sum over the block's samples t of sum_p R[p][t]^2,
-//               sum over the block's columns t < Tz of sum_k |Z[k][t]|)
-// with R = X - sum_k Z_k * D_k, (Z*D)[t] = sum_tau Z[t-tau] D[tau] (Sec. 2).
-__global__ void __launch_bounds__(kObjTile)
+// Tile b (kTile samples of one signal): partials[2b] = sum over its samples of
+// sum_p R[p][t]^2 with R = X - sum_k Z_k * D_k ((Z*D)[t] = sum_tau Z[t-tau] D[tau],
+// Sec. 2), partials[2b+1] = sum of |Z| over its columns.
+__global__ void __launch_bounds__(kTile)
     objective_kernel(const float *__restrict__ D, const float *__restrict__ X,
                      const float *__restrict__ Z, int K, int P, int L, int64_t T,
-                     double *__restrict__ partials)
+                     SignalView sig, const int64_t *__restrict__ tile_s,
+                     const int *__restrict__ tile_sig, double *__restrict__ partials)
 {
     __shared__ NZ list[32 * kChunk];
     __shared__ int warp_counts[32];
-    __shared__ double bsum[2][kObjTile / 32];
+    __shared__ double bsum[2][kTile / 32];
     const int64_t Tz = T - L + 1;
     const int tid = threadIdx.x;
-    const int64_t c0 = (int64_t)blockIdx.x * kObjTile;
+    // without tile tables: one signal [0, T) cut into consecutive tiles
+    const int64_t c0 = tile_s ? tile_s[blockIdx.x] : (int64_t)blockIdx.x * kTile;
+    const int i_sig = tile_sig ? tile_sig[blockIdx.x] : 0;
+    const int64_t end = sig.a ? sig.a[i_sig + 1] : T;
+    const int64_t c1 = c0 + kTile < end ? c0 + kTile : end;
     const int64_t t = c0 + tid;
     double sq = 0.0, l1 = 0.0;
-    // Z columns that reach samples [c0, c0+tile): [c0-(L-1), c0+tile) within [0,Tz)
+    // Z columns that reach samples [c0, c1): [c0-(L-1), c1) within [0,Tz)
     const int64_t lo = c0 - (L - 1) > 0 ? c0 - (L - 1) : 0;
-    const int64_t hi = c0 + kObjTile < Tz ? c0 + kObjTile : Tz;
+    const int64_t hi = c1 < Tz ? c1 : Tz;
     const int chunk = (32 * kChunk) / K < kChunk ? (32 * kChunk) / K : kChunk;
     for (int p0 = 0; p0 < P; p0 += kObjP) {
         float acc_hi[kObjP], acc_lo[kObjP];
@@ -254,7 +257,7 @@ __global__ void __launch_bounds__(kObjTile)
         for (int64_t a = lo; a < hi; a += chunk) {
             const int64_t b = a + chunk < hi ? a + chunk : hi;
             const int n = compact_nonzeros(Z, K, Tz, a, b, list, warp_counts);
-            if (t < T) {
+            if (t < c1) {
                 for (int i = 0; i < n; i++) {
                     const NZ e = list[i];
                     const int tau = (int)(t - e.t);
@@ -271,7 +274,7 @@ __global__ void __launch_bounds__(kObjTile)
             }
             __syncthreads();
         }
-        if (t < T) {
+        if (t < c1) {
 #pragma unroll
             for (int q = 0; q < kObjP; q++)
                 if (p0 + q < P) {
@@ -292,7 +295,7 @@ __global__ void __launch_bounds__(kObjTile)
     __syncthreads();
     if (tid == 0) {
         double a = 0.0, b = 0.0;
-        for (int w = 0; w < kObjTile / 32; w++) {
+        for (int w = 0; w < kTile / 32; w++) {
             a += bsum[0][w];
             b += bsum[1][w];
         }
@@ -301,15 +304,20 @@ __global__ void __launch_bounds__(kObjTile)
     }
 }
 
-// Fixed-order sum of the partials: E = sq/2 + lam * l1.
-__global__ void objective_final_kernel(const double *__restrict__ partials, int nblocks,
-                                       double lam, double *__restrict__ out)
+// Block i: fixed-order sum of signal i's tile partials, E_i = sq/2 + lam_i * l1
+// (without tables: the one signal owns all ntiles tiles and lam0 is its lambda).
+__global__ void objective_final_kernel(const double *__restrict__ partials,
+                                       const int64_t *__restrict__ tile_off, int64_t ntiles,
+                                       const double *__restrict__ lam, double lam0,
+                                       double *__restrict__ out)
 {
     __shared__ double s[2][256];
+    const int i = blockIdx.x;
+    const int64_t j0 = tile_off ? tile_off[i] : 0, j1 = tile_off ? tile_off[i + 1] : ntiles;
     double a = 0.0, b = 0.0;
-    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
-        a += partials[2 * i];
-        b += partials[2 * i + 1];
+    for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+        a += partials[2 * j];
+        b += partials[2 * j + 1];
     }
     s[0][threadIdx.x] = a;
     s[1][threadIdx.x] = b;
@@ -322,7 +330,25 @@ __global__ void objective_final_kernel(const double *__restrict__ partials, int 
         __syncthreads();
     }
     if (threadIdx.x == 0)
-        *out = 0.5 * s[0][0] + lam * s[1][0];
+        out[i] = 0.5 * s[0][0] + (lam ? lam[i] : lam0) * s[1][0];
+}
+
+// max |beta0| over tile b's valid columns, into out[signal] (float bits).
+__global__ void __launch_bounds__(kTile)
+    signal_absmax_kernel(const float *__restrict__ beta0, int K, int L, int64_t Tz,
+                         SignalView sig, const int64_t *__restrict__ tile_s,
+                         const int *__restrict__ tile_sig, unsigned int *__restrict__ out)
+{
+    const int i = tile_sig[blockIdx.x];
+    const int64_t t = tile_s[blockIdx.x] + threadIdx.x;
+    float m = 0.f;
+    if (t <= sig.a[i + 1] - L && t < Tz)
+        for (int k = 0; k < K; k++)
+            m = fmaxf(m, fabsf(beta0[(int64_t)k * Tz + t]));
+    for (int off = 16; off > 0; off >>= 1)
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(&out[i], __float_as_uint(m));
 }
 
 __global__ void beta_from_r_kernel(const float *__restrict__ r, const float *__restrict__ Z,
@@ -337,27 +363,27 @@ __global__ void beta_from_r_kernel(const float *__restrict__ r, const float *__r
 
 template <int KPT>
 cudaError_t resync_launch(const float *beta0, float *r, const float *Z, const float *C,
-                          const float *norms, int K, int L, int64_t Tz, double lam, float lam_f,
-                          int write_r, unsigned long long *red, unsigned char *dirty, int M,
-                          float tol_mark, cudaStream_t s)
+                          const float *norms, int K, int L, int64_t Tz, SignalView sig,
+                          int write_r, unsigned long long *red, unsigned char *dirty,
+                          const int64_t *seg_s, int M, float tol_mark, cudaStream_t s)
 {
     const unsigned grid = (unsigned)((Tz + kResyncCols - 1) / kResyncCols);
-    resync_kernel<KPT><<<grid, kResyncThreads, 0, s>>>(beta0, r, Z, C, norms, K, L, Tz, lam,
-                                                       lam_f, write_r, red, dirty, M, tol_mark);
+    resync_kernel<KPT><<<grid, kResyncThreads, 0, s>>>(beta0, r, Z, C, norms, K, L, Tz, sig,
+                                                       write_r, red, dirty, seg_s, M, tol_mark);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_resync(const float *beta0, float *r, const float *Z, const float *C,
-                          const float *norms, int K, int L, int64_t Tz, double lam,
-                          float lam_f, int write_r, unsigned long long *red,
-                          unsigned char *dirty, int M, float tol_mark, cudaStream_t s)
+                          const float *norms, int K, int L, int64_t Tz, SignalView sig,
+                          int write_r, unsigned long long *red, unsigned char *dirty,
+                          const int64_t *seg_s, int M, float tol_mark, cudaStream_t s)
 {
     const int kpt = (K + kResyncGroups - 1) / kResyncGroups;
-#define CSC_RESYNC(N)                                                                          \
-    return resync_launch<N>(beta0, r, Z, C, norms, K, L, Tz, lam, lam_f, write_r, red, dirty, M, \
-                            tol_mark, s)
+#define CSC_RESYNC(N)                                                                        \
+    return resync_launch<N>(beta0, r, Z, C, norms, K, L, Tz, sig, write_r, red, dirty, seg_s, \
+                            M, tol_mark, s)
     if (kpt <= 2)
         CSC_RESYNC(2);
     if (kpt <= 8)
@@ -380,21 +406,46 @@ cudaError_t launch_beta_from_r(const float *r, const float *Z, const float *norm
     return cudaGetLastError();
 }
 
-int objective_blocks(int64_t T)
-{
-    return (int)((T + kObjTile - 1) / kObjTile);
-}
-
 cudaError_t launch_objective(const float *D, const float *X, const float *Z, int K, int P, int L,
-                             int64_t T, double lam, double *partials, double *out,
+                             int64_t T, SignalView sig, const double *lam_d,
+                             const int64_t *tile_s, const int *tile_sig, int64_t ntiles,
+                             const int64_t *tile_off, double *partials, double *out,
                              cudaStream_t s)
 {
-    const int nb = objective_blocks(T);
-    objective_kernel<<<nb, kObjTile, 0, s>>>(D, X, Z, K, P, L, T, partials);
+    if (ntiles <= 0)
+        return cudaSuccess;
+    objective_kernel<<<(unsigned)ntiles, kTile, 0, s>>>(D, X, Z, K, P, L, T, sig, tile_s,
+                                                        tile_sig, partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
-    objective_final_kernel<<<1, 256, 0, s>>>(partials, nb, lam, out);
+    objective_final_kernel<<<sig.n, 256, 0, s>>>(partials, tile_off, ntiles, lam_d, 0.0, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_objective_single(const float *D, const float *X, const float *Z, int K, int P,
+                                    int L, int64_t T, double lambda, double *partials,
+                                    double *out, cudaStream_t s)
+{
+    const int64_t ntiles = (T + kTile - 1) / kTile;
+    const SignalView one{nullptr, nullptr, 1};
+    objective_kernel<<<(unsigned)ntiles, kTile, 0, s>>>(D, X, Z, K, P, L, T, one, nullptr,
+                                                        nullptr, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    objective_final_kernel<<<1, 256, 0, s>>>(partials, nullptr, ntiles, nullptr, lambda, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_signal_absmax(const float *beta0, int K, int L, int64_t Tz, SignalView sig,
+                                 const int64_t *tile_s, const int *tile_sig, int64_t ntiles,
+                                 unsigned int *out, cudaStream_t s)
+{
+    if (ntiles <= 0)
+        return cudaSuccess;
+    signal_absmax_kernel<<<(unsigned)ntiles, kTile, 0, s>>>(beta0, K, L, Tz, sig, tile_s,
+                                                            tile_sig, out);
     return cudaGetLastError();
 }
 

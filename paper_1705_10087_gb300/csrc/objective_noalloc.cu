@@ -10,7 +10,7 @@
 //
 // That array is g_partials below: 2 * kNoAllocMaxBlocks doubles (1 MiB),
 // present on every GPU that loads this library until the process exits.  It
-// bounds the signal length to kNoAllocMaxBlocks * 256 = 16,777,216 samples.
+// bounds the signal length to kNoAllocMaxBlocks * kTile = 16,777,216 samples.
 // All calls share it: calls whose GPU work overlaps (two streams, two host
 // threads without ordering) race on it and must be serialised by the caller.
 // Each call overwrites every entry it later reads, so nothing is cleared.
@@ -59,12 +59,12 @@ extern "C" int csc_objective_noalloc(const float *D, int K, int P, int L, const 
                                 csc::kMaxL);
     if (!(lambda >= 0.0))
         return csc_record_error(CSC_EINVAL, "csc_objective_noalloc: lambda must be >= 0");
-    const int nb = csc::objective_blocks(T);
+    const int64_t nb = (T + csc::kTile - 1) / csc::kTile;
     if (nb > kNoAllocMaxBlocks)
         return csc_record_error(CSC_EINVAL,
                                 "csc_objective_noalloc: T = %lld exceeds the static scratch "
                                 "limit of %d samples",
-                                (long long)T, kNoAllocMaxBlocks * 256);
+                                (long long)T, kNoAllocMaxBlocks * csc::kTile);
     if (!device_resident(D) || !device_resident(X) || !device_resident(Z))
         return csc_record_error(CSC_EINVAL,
                                 "csc_objective_noalloc: D, X and Z must be device memory");
@@ -93,7 +93,7 @@ extern "C" int csc_objective_noalloc(const float *D, int K, int P, int L, const 
     cudaStream_t s = (cudaStream_t)stream;
     const bool out_on_device = device_resident(E_out);
     double *out = out_on_device ? E_out : scratch + 2 * kNoAllocMaxBlocks;
-    e = csc::launch_objective(D, X, Z, K, P, L, T, lambda, scratch, out, s);
+    e = csc::launch_objective_single(D, X, Z, K, P, L, T, lambda, scratch, out, s);
     if (e != cudaSuccess)
         return csc_record_error(CSC_ECUDA, "csc_objective_noalloc: launch failed: %s",
                                 cudaGetErrorString(e));

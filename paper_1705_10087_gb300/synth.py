@@ -48,17 +48,66 @@ def _bits(seed: int, stream: int, n: int) -> np.ndarray:
         return _mix64(key + ctr * _GOLDEN)
 
 
+def _bits_at(seed: int, stream: int, idx: np.ndarray) -> np.ndarray:
+    """Words number idx (0-based) of the stream: _bits(seed, stream, n)[idx]."""
+    with np.errstate(over="ignore"):
+        key = _mix64(np.array([(seed * 0x100000001B3 + stream * 0x632BE59BD9B4E019)
+                               & 0xFFFFFFFFFFFFFFFF], dtype=np.uint64))[0]
+        ctr = np.asarray(idx, dtype=np.uint64) + np.uint64(1)
+        return _mix64(key + ctr * _GOLDEN)
+
+
+def _to_unit(b: np.ndarray) -> np.ndarray:
+    return ((b >> np.uint64(11)).astype(np.float64) + 0.5) * (1.0 / 9007199254740992.0)
+
+
 def uniform(seed: int, stream: int, n: int) -> np.ndarray:
     """n float64 uniforms in the open interval (0, 1)."""
-    b = _bits(seed, stream, n) >> np.uint64(11)
-    return (b.astype(np.float64) + 0.5) * (1.0 / 9007199254740992.0)
+    return _to_unit(_bits(seed, stream, n))
+
+
+def uniform_at(seed: int, stream: int, idx: np.ndarray) -> np.ndarray:
+    """uniform(seed, stream, n)[idx] without drawing the others."""
+    return _to_unit(_bits_at(seed, stream, idx))
+
+
+def _box_muller(u1: np.ndarray, u2: np.ndarray) -> np.ndarray:
+    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
 
 
 def normal(seed: int, stream: int, n: int) -> np.ndarray:
     """n float64 standard normals (Box-Muller on two uniform streams)."""
-    u1 = uniform(seed, 2 * stream, n)
-    u2 = uniform(seed, 2 * stream + 1, n)
-    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+    return _box_muller(uniform(seed, 2 * stream, n), uniform(seed, 2 * stream + 1, n))
+
+
+def normal_at(seed: int, stream: int, idx: np.ndarray) -> np.ndarray:
+    """normal(seed, stream, n)[idx] without drawing the others."""
+    return _box_muller(uniform_at(seed, 2 * stream, idx), uniform_at(seed, 2 * stream + 1, idx))
+
+
+def bernoulli_support(seed: int, stream: int, n: int, rho: float) -> np.ndarray:
+    """Sorted indices of the successes of n Bernoulli(rho) trials, drawn as
+    geometric gaps (the number of failures before each success is
+    floor(log U / log(1 - rho)), U uniform): the same law as testing n
+    uniforms against rho, at a cost proportional to the successes."""
+    if rho <= 0.0 or n <= 0:
+        return np.zeros(0, np.int64)
+    if rho >= 1.0:
+        return np.arange(n, dtype=np.int64)
+    chunk = int(rho * n + 10.0 * np.sqrt(rho * n) + 16)
+    gaps = []
+    pos = -1
+    j = 0
+    while True:
+        u = uniform_at(seed, stream, np.arange(j, j + chunk))
+        g = np.floor(np.log(u) / np.log1p(-rho)).astype(np.int64) + 1
+        idx = pos + np.cumsum(g)
+        gaps.append(idx[idx < n])
+        if idx[-1] >= n:
+            break
+        pos = int(idx[-1])
+        j += chunk
+    return np.concatenate(gaps)
 
 
 @dataclasses.dataclass
@@ -100,11 +149,17 @@ def make_dictionary(K: int, P: int, L: int, seed: int) -> np.ndarray:
 
 
 def make_problem(K: int, P: int, L: int, T: int, rho: float, sigma: float,
-                 seed: int, sigma_z: float = 1.0, D: np.ndarray | None = None) -> Problem:
+                 seed: int, sigma_z: float = 1.0, D: np.ndarray | None = None,
+                 support: str = "dense") -> Problem:
     """Draw D (unless given), a Bernoulli-Gaussian Z and X = sum_k Z_k*D_k + noise.
 
-    The model sum is accumulated in float64 from the float32 dictionary and
-    the float32 activations, then rounded once to float32.
+    support="dense" tests one uniform per coordinate against rho and takes the
+    amplitude of coordinate i from normal number i; support="gaps" draws the
+    same Bernoulli law as geometric gaps (bernoulli_support) and takes the
+    amplitude of the j-th nonzero from normal number j (cheaper for long
+    signals; a different sample).  The model sum is accumulated in float64
+    from the float32 dictionary and the float32 activations, then rounded once
+    to float32.
     """
     if T < L:
         raise ValueError("T must be >= L")
@@ -113,9 +168,17 @@ def make_problem(K: int, P: int, L: int, T: int, rho: float, sigma: float,
     D = np.ascontiguousarray(D, dtype=np.float32)
     K, P, L = D.shape
     Tz = T - L + 1
-    mask = uniform(seed, 3, K * Tz) < rho
-    amp = normal(seed, 4, K * Tz) * sigma_z
-    Z = np.where(mask, amp, 0.0).reshape(K, Tz).astype(np.float32)
+    if support == "dense":
+        nz = np.flatnonzero(uniform(seed, 3, K * Tz) < rho)
+        amp = normal_at(seed, 4, nz)
+    elif support == "gaps":
+        nz = bernoulli_support(seed, 3, K * Tz, rho)
+        amp = normal_at(seed, 4, np.arange(nz.size))
+    else:
+        raise ValueError(f"unknown support mode {support!r}")
+    Z = np.zeros(K * Tz, np.float32)
+    Z[nz] = (amp * sigma_z).astype(np.float32)
+    Z = Z.reshape(K, Tz)
 
     X = np.zeros((P, T), dtype=np.float64)
     ks, ts = np.nonzero(Z)
@@ -142,6 +205,53 @@ WORKLOADS = {
     "verylong_P1_K25_L200_T5000000": dict(P=1, K=25, L=200, T=5_000_000, rho=0.002,
                                           sigma=0.1, segments=(12_500,), tol=1e-6),
 }
+
+
+# Batches: n signals with lengths uniform in [T_min, T_max], one shared dictionary.
+BATCH_WORKLOADS = {
+    # 512 multichannel signals of uneven length against one dictionary
+    "batch_P7_K25_L64_n512_T10000_500000": dict(P=7, K=25, L=64, n=512, T_min=10_000,
+                                                T_max=500_000, rho=0.005, sigma=0.1, tol=1e-6),
+}
+
+
+def batch_lengths(n: int, T_min: int, T_max: int, seed: int) -> np.ndarray:
+    """n lengths uniform on the integers [T_min, T_max]."""
+    u = uniform(seed, 6, n)
+    return np.minimum(T_min + np.floor(u * (T_max - T_min + 1)), T_max).astype(np.int64)
+
+
+def batch_signal(name: str, seed: int, i: int, T: int) -> Problem:
+    """Signal i of a batch workload: seed (seed << 20) + 1 + i, the dictionary
+    of `seed`, the Bernoulli support drawn as geometric gaps."""
+    w = BATCH_WORKLOADS[name]
+    D = make_dictionary(w["K"], w["P"], w["L"], seed)
+    return make_problem(K=w["K"], P=w["P"], L=w["L"], T=int(T), rho=w["rho"], sigma=w["sigma"],
+                        seed=(seed << 20) + 1 + i, D=D, support="gaps")
+
+
+def _batch_signal_args(args):
+    return batch_signal(*args)
+
+
+def make_batch(name: str, seed: int = 0, n: int | None = None, T_max: int | None = None,
+               workers: int = 0) -> list:
+    """Problems of a named batch workload, sharing the dictionary of `seed`.
+
+    n and T_max may be reduced for smaller cases (lengths are then drawn for
+    the reduced range).  workers > 1 draws the signals in that many spawned
+    processes (same arrays as workers = 0)."""
+    w = BATCH_WORKLOADS[name]
+    n = n if n is not None else w["n"]
+    T_max = T_max if T_max is not None else w["T_max"]
+    T_min = min(w["T_min"], T_max)
+    T = batch_lengths(n, T_min, T_max, seed)
+    args = [(name, seed, i, int(T[i])) for i in range(n)]
+    if workers > 1 and n > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(min(workers, n)) as pool:
+            return pool.map(_batch_signal_args, args, chunksize=max(1, n // (4 * workers)))
+    return [batch_signal(*a) for a in args]
 
 
 def make_workload(name: str, seed: int = 0, T: int | None = None) -> Problem:

@@ -38,3 +38,42 @@ def test_recipe_of_the_long_signal_workload():
     assert abs(dens - 0.005) < 0.0008
     noise = npref.residual(pb.D, pb.X, pb.Z_true.astype(np.float64))
     assert abs(noise.std() - 0.1) < 0.003
+
+
+def test_indexed_draws_equal_full_draws():
+    idx = np.array([0, 5, 17, 999, 3])
+    assert np.array_equal(synth.uniform_at(4, 7, idx), synth.uniform(4, 7, 1000)[idx])
+    assert np.array_equal(synth.normal_at(4, 7, idx), synth.normal(4, 7, 1000)[idx])
+
+
+def test_bernoulli_support_law():
+    # n Bernoulli(rho) trials drawn as geometric gaps: the count is Binomial(n, rho)
+    # and every index is hit with probability rho, whatever its position
+    n, rho = 2_000_000, 0.005
+    s = synth.bernoulli_support(11, 3, n, rho)
+    assert np.all(np.diff(s) > 0) and s[0] >= 0 and s[-1] < n
+    sd = np.sqrt(n * rho * (1 - rho))
+    assert abs(s.size - n * rho) < 5 * sd
+    # rate in the first and last tenth agree with rho (no drift along the signal)
+    for lo in (0, 9 * n // 10):
+        c = np.count_nonzero((s >= lo) & (s < lo + n // 10))
+        assert abs(c - n * rho / 10) < 5 * np.sqrt(n / 10 * rho)
+    # P(gap > g) = (1 - rho)^g: gaps beyond the median of the geometric law
+    g = np.diff(s)
+    med = np.log(0.5) / np.log1p(-rho)
+    assert abs(np.mean(g > med) - 0.5) < 5 * 0.5 / np.sqrt(g.size)
+    # edge cases
+    assert synth.bernoulli_support(1, 3, 0, 0.5).size == 0
+    assert synth.bernoulli_support(1, 3, 10, 0.0).size == 0
+    assert np.array_equal(synth.bernoulli_support(1, 3, 10, 1.0), np.arange(10))
+    assert np.array_equal(s, synth.bernoulli_support(11, 3, n, rho))
+
+
+def test_gaps_support_problem():
+    pb = synth.make_problem(K=5, P=2, L=8, T=50_000, rho=0.01, sigma=0.1, seed=3,
+                            support="gaps")
+    nz = np.count_nonzero(pb.Z_true)
+    N = 5 * (50_000 - 7)
+    assert abs(nz - 0.01 * N) < 5 * np.sqrt(0.01 * N)
+    amp = pb.Z_true[pb.Z_true != 0]
+    assert abs(amp.std() - 1.0) < 0.05 and abs(amp.mean()) < 0.05
