@@ -47,7 +47,7 @@ HBM_FALLBACK_GBS = 6800.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--segments", type=int, default=1024)
@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true", help="skip the segment-count sweep")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the 512-signal batched-vs-plain comparison")
     return ap.parse_args()
 
 
@@ -85,7 +87,7 @@ def input_hash(pb) -> str:
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -93,12 +95,16 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.lines = []
+        self.window = None  # (start, end) wall-clock seconds of the timed region
+
+    def mark(self, start: float, end: float):
+        self.window = (start, end)
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-i", str(self.gpu), "-lms", "200"], stdout=subprocess.PIPE,
+                 "-i", str(self.gpu), "-lms", "50"], stdout=subprocess.PIPE,
                 stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -120,18 +126,24 @@ class ClockSampler:
             self.thread.join(timeout=2)
 
     def summary(self):
+        import datetime
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx = float(f[2])
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                clk, cmax = float(f[2]), float(f[3])
             except ValueError:
                 continue
-            for n, v in zip(names, f[5:9]):
+            # samples inside the timed region only (50 ms sampling period)
+            if self.window and not (self.window[0] - 0.05 <= ts <= self.window[1] + 0.05):
+                continue
+            sm.append(clk)
+            mx = cmax
+            for n, v in zip(names, f[6:10]):
                 if v.lower() == "active":
                     reasons.add(n)
         if not sm:
@@ -164,6 +176,125 @@ def time_to_gap_ms(trace, init_ms, E_star, rel=1e-4):
     t = trace["t_ns"][: ok[0] + 1]
     t = t[t >= 0]
     return init_ms + (float(t[-1]) / 1e6 if t.size else 0.0)
+
+
+BATCH = "batch_P7_K25_L64_n512_T10000_500000"
+GOLDEN_BATCH = os.path.join(ROOT, "tests", "golden", "optimum_batch.json")
+
+
+def batch_leg(args, capi, torch):
+    """The 512-signal batch solved two ways to the same accuracy: batched (all
+    signals in one csc_init_batch + csc_solve) and plain (one csc_init +
+    csc_solve per signal, one handle, signals one after another).
+
+    For each way, the time to a relative objective gap <= 1e-4 on EVERY signal
+    is the solve time at the largest stopping tolerance (from a fixed grid)
+    whose solution meets that gap against E*_i of tests/golden/optimum_batch.json
+    (FP64 oracle); time = csc_init + csc_solve of all signals (CUDA events)."""
+    import hashlib
+    from paper_1705_10087_gb300 import batch, synth
+    t0 = time.perf_counter()
+    pbs = synth.make_batch(BATCH, seed=0, workers=min(16, os.cpu_count() or 1))
+    gen_s = time.perf_counter() - t0
+    D = pbs[0].D
+    X, T = batch.pack([pb.X for pb in pbs])
+    K, L = D.shape[0], D.shape[2]
+    n = len(pbs)
+    try:
+        with open(GOLDEN_BATCH) as f:
+            gb = json.load(f)
+        h = hashlib.sha256()
+        h.update(D.tobytes())
+        for pb in pbs:
+            h.update(hashlib.sha256(pb.X.tobytes()).hexdigest().encode())
+        if h.hexdigest()[:16] != gb["input_sha256_16"]:
+            gb = None
+    except (OSError, KeyError, ValueError):
+        gb = None
+    if gb is None:
+        return {"workload": BATCH, "unavailable": "no stored optimum for these inputs"}
+    lam = np.array(gb["lambda"])
+    E_star = np.array(gb["E_star"])
+    Dd = torch.from_numpy(D).cuda()
+    Xd = torch.from_numpy(X).cuda()
+    Xi = [torch.from_numpy(np.ascontiguousarray(pb.X)).cuda() for pb in pbs]
+    del pbs
+    Tz = int(T.sum()) - L + 1
+    Zd = torch.zeros((K, Tz), dtype=torch.float32, device="cuda")
+    Zi = torch.zeros(K * (int(T.max()) - L + 1), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    # autotune (segment width, updates per visit) on the first 32 signals
+    a = batch.offsets(T)
+    nt = min(32, n)
+    ht = capi.csc_setup(Dd, capi.make_opts(updates_per_visit=args.updates_per_visit))
+    try:
+        capi.csc_init_batch(ht, Xd[:, :int(a[nt])].contiguous(), T[:nt], lam[:nt])
+        tune = capi.csc_autotune(ht, args.tol)
+    finally:
+        capi.csc_destroy(ht)
+    u, wseg = tune["updates_per_visit"], tune["segment_width"]
+
+    def batched(tol):
+        hb = capi.csc_setup(Dd, capi.make_opts(updates_per_visit=u, segment_width=wseg))
+        try:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            capi.csc_init_batch(hb, Xd, T, lam)
+            status, E, st = capi.csc_solve(hb, tol, 1 << 40, Zd)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            Es = capi.csc_get_objectives(hb, n)
+            return e0.elapsed_time(e1), Es, st["updates"], status
+        finally:
+            capi.csc_destroy(hb)
+
+    def plain(tol):
+        hp = capi.csc_setup(Dd, capi.make_opts(updates_per_visit=u, segment_width=wseg))
+        try:
+            Es = np.zeros(n)
+            ups = 0
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            worst = capi.CSC_OK
+            for i in range(n):
+                capi.csc_init(hp, Xi[i], float(lam[i]))
+                status, E, st = capi.csc_solve(hp, tol, 1 << 40,
+                                               Zi[:K * (int(T[i]) - L + 1)].view(K, -1))
+                Es[i] = E
+                ups += st["updates"]
+                worst = max(worst, status)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1), Es, ups, worst
+        finally:
+            capi.csc_destroy(hp)
+
+    out = {"workload": BATCH, "signals": n, "samples": int(T.sum()), "P": 7, "K": K, "L": L,
+           "updates_per_visit": u, "segment_width": wseg, "autotune": tune, "gen_s": gen_s,
+           "gap_target": 1e-4, "E_star": "FP64 oracle per signal (stored)"}
+    grid = (1e-3, 3e-4, 1e-4, 3e-5, 1e-5, 3e-6, 1e-6)
+    for name, fn in (("batched", batched), ("plain", plain)):
+        fn(grid[0])  # warm-up (module load, allocations)
+        res = None
+        for tol in grid:
+            ms, Es, ups, status = min((fn(tol) for _ in range(2)), key=lambda r: r[0])
+            gap = float(np.max((Es - E_star) / E_star))
+            if gap <= 1e-4:
+                res = {"tol": tol, "ms": ms, "max_rel_gap": gap, "updates": ups,
+                       "updates_per_s": ups / (ms * 1e-3), "status": status}
+                break
+        ms6, Es6, ups6, st6 = fn(1e-6) if res is None or res["tol"] != 1e-6 else (
+            res["ms"], None, res["updates"], res["status"])
+        out[name] = {"time_to_gap": res, "converged_tol_1e-6_ms": ms6,
+                     "converged_updates": ups6}
+    if out["batched"]["time_to_gap"] and out["plain"]["time_to_gap"]:
+        out["speedup_time_to_gap"] = (out["plain"]["time_to_gap"]["ms"] /
+                                      out["batched"]["time_to_gap"]["ms"])
+    out["speedup_converged"] = (out["plain"]["converged_tol_1e-6_ms"] /
+                                out["batched"]["converged_tol_1e-6_ms"])
+    return out
 
 
 def cpu_baseline(pb, lam, tol, M, u):
@@ -278,12 +409,15 @@ def main():
     launches0 = capi.csc_kernel_launches(h)
     sts, Es = [], []
     with ClockSampler(gpu_index) as clk:
+        time.sleep(0.3)  # let the sampler start
+        w0 = time.time()
         for i in range(args.warmup, args.warmup + args.steps):
             E, st = step(evs[i])
             sts.append(st)
             Es.append(E)
             flush.zero_()
         torch.cuda.synchronize()
+        clk.mark(w0, time.time())
     launches = capi.csc_kernel_launches(h) - launches0
     trace = capi.csc_get_trace(h)
     if world > 1:
@@ -391,6 +525,8 @@ def main():
     }
     if sweep:
         line["segment_sweep"] = sweep
+    if world == 1 and not args.no_batch:
+        line["batch"] = batch_leg(args, capi, torch)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(pb, lam, args.tol, args.segments,
                                             args.updates_per_visit)

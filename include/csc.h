@@ -178,6 +178,31 @@ int csc_lambda_max_batch(csc_handle_t h, double *out);
  * csc_objective; csc_solve's objective is their sum. */
 int csc_get_objectives(csc_handle_t h, double *out);
 
+typedef struct csc_tune_result {
+    int32_t segment_width;     /* chosen width (columns) */
+    int32_t updates_per_visit; /* chosen u (0 = until local convergence) */
+    int32_t phases;            /* c of the chosen plan */
+    int32_t candidates;        /* solves timed */
+    double best_ms;            /* csc_stats.solve_ms of the choice */
+    double default_ms;         /* the same for width 2L-2 at the starting u (-1 if not run) */
+} csc_tune_result;
+
+/*
+ * Autotuner (a deployment tool; the paper has no counterpart, its Thm. speedup
+ * only predicts that narrower segments help until the phase count grows).
+ * Solves the current problem (csc_init / csc_init_batch) to tol once per
+ * candidate and keeps the fastest by device solve time: first the segment
+ * width among L-1, 2L-2, 3L-3, 4L-4, 6L-6 (which sets the number of phases c)
+ * at the handle's updates_per_visit (24 if 0), then updates_per_visit among
+ * 8, 24, 64 and 0 at that width.  Every candidate starts from the state the
+ * problem had when csc_autotune was called, and that state is restored
+ * afterwards; the choice is stored in the handle's options (segments = 0,
+ * segment_width, updates_per_visit) for the following solves and, when out is
+ * not NULL, reported.  Tune on a representative problem of the (K, L, P) at
+ * hand and re-use the result through csc_opts for others.
+ */
+int csc_autotune(csc_handle_t h, double tol, int64_t max_updates, csc_tune_result *out);
+
 /* Releases every device and host resource of the handle.  NULL is accepted. */
 int csc_destroy(csc_handle_t h);
 

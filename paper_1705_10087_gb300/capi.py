@@ -44,6 +44,15 @@ class csc_stats(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class csc_tune_result(ctypes.Structure):
+    _fields_ = [("segment_width", ctypes.c_int32), ("updates_per_visit", ctypes.c_int32),
+                ("phases", ctypes.c_int32), ("candidates", ctypes.c_int32),
+                ("best_ms", ctypes.c_double), ("default_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 class CscError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"csc error {status}: {message}")
@@ -91,12 +100,14 @@ def load(path: str | None = None):
     lib.csc_set_lambda.argtypes = [_vp, _vp]
     lib.csc_lambda_max_batch.argtypes = [_vp, _vp]
     lib.csc_get_objectives.argtypes = [_vp, _vp]
+    lib.csc_autotune.argtypes = [_vp, ctypes.c_double, _i64, ctypes.POINTER(csc_tune_result)]
     lib.csc_last_error_string.argtypes = []
     lib.csc_last_error_string.restype = ctypes.c_char_p
     for name in ("csc_setup", "csc_init", "csc_solve", "csc_destroy", "csc_lambda_max",
                  "csc_get_beta", "csc_get_dtd", "csc_objective", "csc_get_trace", "csc_plan",
                  "csc_kernel_launches", "csc_objective_noalloc", "csc_init_batch",
-                 "csc_set_lambda", "csc_lambda_max_batch", "csc_get_objectives"):
+                 "csc_set_lambda", "csc_lambda_max_batch", "csc_get_objectives",
+                 "csc_autotune"):
         getattr(lib, name).restype = ctypes.c_int
     if path == _build.LIB:
         _lib = lib
@@ -189,6 +200,12 @@ def csc_get_objectives(h, n: int) -> np.ndarray:
     out = np.zeros(n, np.float64)
     _check(load().csc_get_objectives(h, out.ctypes.data))
     return out
+
+
+def csc_autotune(h, tol: float, max_updates: int = 1 << 62) -> dict:
+    r = csc_tune_result()
+    _check(load().csc_autotune(h, float(tol), int(max_updates), ctypes.byref(r)))
+    return r.as_dict()
 
 
 def csc_solve(h, tol: float, max_updates: int = 1 << 62, Z_out=None):

@@ -3,8 +3,10 @@
 // plans, the phase loop with its convergence polls and resync rounds.
 //
 // A problem is a batch of n >= 1 signals concatenated in time (csc_init is the
-// n = 1 case): see SignalView in csc_internal.cuh for why the concatenation is
-// exactly n separate problems.
+// n = 1 case).  Each signal is described to the kernels by a SigDesc pointing
+// into the concatenated arrays (row stride = the concatenation's width), so
+// the kernels solve n separate problems; the L-1 columns after each signal's
+// last valid column belong to none of them and Z stays 0 there.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -174,15 +176,18 @@ struct csc_handle_s {
     std::vector<double> lam;        // [n]
     std::vector<double> lmax;       // [n]
     std::vector<double> E_sig;      // [n] objectives of the last solve / csc_objective
-    std::vector<int64_t> tile_off;  // [n+1] first reduction tile of each signal
-    int64_t ntiles = 0;
-    int64_t *d_a = nullptr, *d_tile_s = nullptr, *d_tile_off = nullptr;
-    int *d_tile_sig = nullptr;
-    float *d_lam = nullptr;
-    double *d_lam_d = nullptr, *d_E = nullptr;
+    std::vector<SigDesc> sigs;      // [n] descriptors of the signals
+    SigDesc *d_sig = nullptr;
+    size_t cap_sig = 0;
+    // objective / absmax tiles (kTile samples) and resync tiles (kResyncCols columns)
+    std::vector<int64_t> tile_off;  // [n+1] first objective tile of each signal
+    int64_t ntiles = 0, nrtiles = 0;
+    int64_t *d_tile_s = nullptr, *d_tile_off = nullptr, *d_rtile_s = nullptr;
+    int *d_tile_sig = nullptr, *d_rtile_sig = nullptr;
+    size_t cap_rtile_s = 0, cap_rtile_sig = 0;
+    double *d_E = nullptr;
     unsigned int *d_lmax = nullptr;
-    size_t cap_a = 0, cap_tile_s = 0, cap_tile_off = 0, cap_tile_sig = 0, cap_lam = 0,
-           cap_lam_d = 0, cap_E = 0, cap_lmax = 0;
+    size_t cap_tile_s = 0, cap_tile_off = 0, cap_tile_sig = 0, cap_E = 0, cap_lmax = 0;
 
     // r = beta - ||D_k||^2 Z, the form of beta the kernels keep (csc_internal.cuh)
     float *X = nullptr, *r = nullptr, *beta0 = nullptr, *Z = nullptr;
@@ -195,9 +200,9 @@ struct csc_handle_s {
     int M = 0, c = 0, w_max = 0;
     std::vector<int> phase_off;  // [c+1] into the phase list
     int64_t *d_seg_s = nullptr, *d_seg_e = nullptr;
-    float *d_seg_lam = nullptr;
+    int *d_seg_sig = nullptr;
     int *d_phase_list = nullptr;
-    size_t cap_seg_s = 0, cap_seg_e = 0, cap_seg_lam = 0, cap_phase = 0;
+    size_t cap_seg_s = 0, cap_seg_e = 0, cap_seg_sig = 0, cap_phase = 0;
     unsigned char *dirty = nullptr;
     size_t cap_dirty = 0;
 
@@ -214,7 +219,8 @@ struct csc_handle_s {
     int64_t g_used = 0;
     double E_start = 0.0;
 
-    SignalView view() const { return SignalView{d_a, d_lam, n}; }
+    Tiles obj_tiles() const { return Tiles{d_tile_sig, d_tile_s, ntiles}; }
+    Tiles resync_tiles() const { return Tiles{d_rtile_sig, d_rtile_s, nrtiles}; }
 };
 
 namespace {
@@ -227,7 +233,7 @@ int build_plan(csc_handle_t h)
     cudaStream_t s = h->stream;
     const int L = h->L;
     std::vector<int64_t> seg_s, seg_e;
-    std::vector<float> seg_lam;
+    std::vector<int> seg_sig;
     std::vector<int> local;
     int c = 1;
     for (int i = 0; i < h->n; i++) {
@@ -243,10 +249,13 @@ int build_plan(csc_handle_t h)
             Mi = (int)std::max<int64_t>(1, Tzi / w);
         }
         c = std::max(c, phase_count_host(Tzi, Mi, L));
+        h->sigs[i].seg0 = (int)seg_s.size();
+        h->sigs[i].nseg = Mi;
         for (int m = 0; m < Mi; m++) {
-            seg_s.push_back(h->a[i] + seg_start(Tzi, Mi, m));
-            seg_e.push_back(h->a[i] + seg_start(Tzi, Mi, m + 1));
-            seg_lam.push_back((float)h->lam[i]);
+            // columns local to the signal
+            seg_s.push_back(seg_start(Tzi, Mi, m));
+            seg_e.push_back(seg_start(Tzi, Mi, m + 1));
+            seg_sig.push_back(i);
             local.push_back(m);
         }
     }
@@ -265,7 +274,8 @@ int build_plan(csc_handle_t h)
     off[c] = (int)list.size();
     CSC_CUDA(upload(&h->d_seg_s, &h->cap_seg_s, seg_s, s));
     CSC_CUDA(upload(&h->d_seg_e, &h->cap_seg_e, seg_e, s));
-    CSC_CUDA(upload(&h->d_seg_lam, &h->cap_seg_lam, seg_lam, s));
+    CSC_CUDA(upload(&h->d_seg_sig, &h->cap_seg_sig, seg_sig, s));
+    CSC_CUDA(upload(&h->d_sig, &h->cap_sig, h->sigs, s));
     CSC_CUDA(upload(&h->d_phase_list, &h->cap_phase, list, s));
     CSC_CUDA(grow(&h->dirty, &h->cap_dirty, (size_t)M));
     // the host vectors must outlive the asynchronous copies
@@ -282,9 +292,8 @@ int build_plan(csc_handle_t h)
 int objectives(csc_handle_t h, const float *Zd, double *sum)
 {
     cudaStream_t s = h->stream;
-    CSC_CUDA(launch_objective(h->D, h->X, Zd, h->K, h->P, h->L, h->T, h->view(), h->d_lam_d,
-                              h->d_tile_s, h->d_tile_sig, h->ntiles, h->d_tile_off, h->partials,
-                              h->d_E, s));
+    CSC_CUDA(launch_objective(h->D, h->d_sig, h->n, h->obj_tiles(), h->d_tile_off, h->K, h->P,
+                              h->L, h->Z, Zd == h->Z ? nullptr : Zd, h->partials, h->d_E, s));
     h->launches += 2;
     CSC_CUDA(cudaMemcpyAsync(h->E_sig.data(), h->d_E, sizeof(double) * h->n,
                              cudaMemcpyDeviceToHost, s));
@@ -302,13 +311,12 @@ int set_lambdas(csc_handle_t h, const double *lambda)
         if (!(lambda[i] > 0.0) || !std::isfinite(lambda[i]))
             return fail(CSC_EINVAL, "lambda[%d] must be positive and finite", i);
     h->lam.assign(lambda, lambda + h->n);
-    std::vector<float> lf(h->n);
-    for (int i = 0; i < h->n; i++)
-        lf[i] = (float)h->lam[i];
-    CSC_CUDA(upload(&h->d_lam, &h->cap_lam, lf, h->stream));
-    CSC_CUDA(upload(&h->d_lam_d, &h->cap_lam_d, h->lam, h->stream));
+    for (int i = 0; i < h->n; i++) {
+        h->sigs[i].lam = (float)h->lam[i];
+        h->sigs[i].lam_d = h->lam[i];
+    }
+    CSC_CUDA(upload(&h->d_sig, &h->cap_sig, h->sigs, h->stream));
     CSC_CUDA(cudaStreamSynchronize(h->stream));
-    h->plan_ok = false;  // segment lambdas
     return CSC_OK;
 }
 
@@ -356,9 +364,9 @@ int csc_destroy(csc_handle_t h)
         cudaStreamSynchronize(h->stream);
     void *bufs[] = {h->D,          h->C,          h->Ct,         h->norms,      h->X,
                     h->r,          h->beta0,      h->Z,          h->partials,   h->dirty,
-                    h->tmpZ,       h->tmpB,       h->sc,         h->d_a,        h->d_tile_s,
-                    h->d_tile_off, h->d_tile_sig, h->d_lam,      h->d_lam_d,    h->d_E,
-                    h->d_lmax,     h->d_seg_s,    h->d_seg_e,    h->d_seg_lam,  h->d_phase_list};
+                    h->tmpZ,       h->tmpB,       h->sc,         h->d_sig,      h->d_tile_s,
+                    h->d_tile_off, h->d_tile_sig, h->d_rtile_s,  h->d_rtile_sig, h->d_E,
+                    h->d_lmax,     h->d_seg_s,    h->d_seg_e,    h->d_seg_sig,  h->d_phase_list};
     for (void *p : bufs)
         cudaFree(p);
     if (h->poll)
@@ -466,53 +474,71 @@ int csc_init_batch(csc_handle_t h, const float *X, const int64_t *T, int n, cons
     h->a.assign(n + 1, 0);
     for (int i = 0; i < n; i++)
         h->a[i + 1] = h->a[i] + T[i];
-    // reduction tiles: kTile samples of one signal
-    std::vector<int64_t> tile_s;
-    std::vector<int> tile_sig;
-    h->tile_off.assign(n + 1, 0);
-    for (int i = 0; i < n; i++) {
-        h->tile_off[i] = (int64_t)tile_s.size();
-        for (int64_t t = h->a[i]; t < h->a[i + 1]; t += kTile) {
-            tile_s.push_back(t);
-            tile_sig.push_back(i);
-        }
-    }
-    h->tile_off[n] = (int64_t)tile_s.size();
-    h->ntiles = (int64_t)tile_s.size();
-    h->E_sig.assign(n, 0.0);
-    h->lmax.assign(n, 0.0);
-    CSC_CUDA(upload(&h->d_a, &h->cap_a, h->a, s));
-    CSC_CUDA(upload(&h->d_tile_s, &h->cap_tile_s, tile_s, s));
-    CSC_CUDA(upload(&h->d_tile_sig, &h->cap_tile_sig, tile_sig, s));
-    CSC_CUDA(upload(&h->d_tile_off, &h->cap_tile_off, h->tile_off, s));
-    CSC_CUDA(grow(&h->d_E, &h->cap_E, (size_t)n));
-    CSC_CUDA(grow(&h->d_lmax, &h->cap_lmax, (size_t)n));
-    {
-        int rc = set_lambdas(h, lambda);  // also waits for the uploads above
-        if (rc != CSC_OK)
-            return rc;
-    }
     const size_t nz = (size_t)h->K * Tz;
     CSC_CUDA(grow(&h->X, &h->cap_X, (size_t)h->P * Ttot));
     CSC_CUDA(grow(&h->r, &h->cap_r, nz));
     CSC_CUDA(grow(&h->beta0, &h->cap_beta0, nz));
     CSC_CUDA(grow(&h->Z, &h->cap_Z, nz));
+    // descriptors into the concatenation and the tiles over each signal
+    h->sigs.assign(n, SigDesc{});
+    std::vector<int64_t> tile_s, rtile_s;
+    std::vector<int> tile_sig, rtile_sig;
+    h->tile_off.assign(n + 1, 0);
+    for (int i = 0; i < n; i++) {
+        SigDesc &d = h->sigs[i];
+        d.r = h->r + h->a[i];
+        d.Z = h->Z + h->a[i];
+        d.beta0 = h->beta0 + h->a[i];
+        d.X = h->X + h->a[i];
+        d.ld = Tz;
+        d.ldx = Ttot;
+        d.Tz = T[i] - h->L + 1;
+        h->tile_off[i] = (int64_t)tile_s.size();
+        for (int64_t t = 0; t < T[i]; t += kTile) {
+            tile_s.push_back(t);
+            tile_sig.push_back(i);
+        }
+        for (int64_t t = 0; t < d.Tz; t += kResyncCols) {
+            rtile_s.push_back(t);
+            rtile_sig.push_back(i);
+        }
+    }
+    h->tile_off[n] = (int64_t)tile_s.size();
+    h->ntiles = (int64_t)tile_s.size();
+    h->nrtiles = (int64_t)rtile_s.size();
+    h->E_sig.assign(n, 0.0);
+    h->lmax.assign(n, 0.0);
+    CSC_CUDA(upload(&h->d_tile_s, &h->cap_tile_s, tile_s, s));
+    CSC_CUDA(upload(&h->d_tile_sig, &h->cap_tile_sig, tile_sig, s));
+    CSC_CUDA(upload(&h->d_tile_off, &h->cap_tile_off, h->tile_off, s));
+    CSC_CUDA(upload(&h->d_rtile_s, &h->cap_rtile_s, rtile_s, s));
+    CSC_CUDA(upload(&h->d_rtile_sig, &h->cap_rtile_sig, rtile_sig, s));
+    CSC_CUDA(grow(&h->d_E, &h->cap_E, (size_t)n));
+    CSC_CUDA(grow(&h->d_lmax, &h->cap_lmax, (size_t)n));
     CSC_CUDA(grow(&h->partials, &h->cap_partials, 2 * (size_t)h->ntiles));
+    {
+        int rc = set_lambdas(h, lambda);  // uploads the descriptors; waits for the uploads
+        if (rc != CSC_OK)
+            return rc;
+    }
     CSC_CUDA(copy_in(h->X, X, sizeof(float) * h->P * Ttot, s));
     CSC_CUDA(cudaMemsetAsync(&h->sc->lmax_bits, 0, sizeof(unsigned), s));
     CSC_CUDA(cudaMemsetAsync(&h->sc->x2, 0, sizeof(double), s));
     CSC_CUDA(launch_dtx(h->D, h->X, h->K, h->P, h->L, Ttot, h->beta0, &h->sc->lmax_bits,
                         &h->sc->x2, s));
     CSC_CUDA(cudaMemsetAsync(h->d_lmax, 0, sizeof(unsigned) * n, s));
-    CSC_CUDA(launch_signal_absmax(h->beta0, h->K, h->L, Tz, h->view(), h->d_tile_s,
-                                  h->d_tile_sig, h->ntiles, h->d_lmax, s));
+    CSC_CUDA(launch_signal_absmax(h->d_sig, h->obj_tiles(), h->K, h->d_lmax, s));
     h->launches += 2;
     if (Z0) {
         h->launches += 1;
         CSC_CUDA(copy_in(h->Z, Z0, sizeof(float) * nz, s));
+        // the columns between signals belong to no problem: 0
+        for (int i = 0; i + 1 < n; i++)
+            CSC_CUDA(cudaMemset2DAsync(h->Z + h->a[i + 1] - h->L + 1, sizeof(float) * Tz, 0,
+                                       sizeof(float) * (h->L - 1), h->K, s));
         CSC_CUDA(cudaMemsetAsync(h->sc->red, 0, sizeof(h->sc->red), s));
-        CSC_CUDA(launch_resync(h->beta0, h->r, h->Z, h->C, h->norms, h->K, h->L, Tz, h->view(),
-                               1, h->sc->red, nullptr, nullptr, 0, 0.f, s));
+        CSC_CUDA(launch_resync(h->d_sig, h->resync_tiles(), h->C, h->norms, h->K, h->L, 1,
+                               h->sc->red, 0, nullptr, nullptr, 0.f, s));
     } else {
         CSC_CUDA(cudaMemsetAsync(h->Z, 0, sizeof(float) * nz, s));
         CSC_CUDA(cudaMemcpyAsync(h->r, h->beta0, sizeof(float) * nz, cudaMemcpyDeviceToDevice, s));
@@ -632,8 +658,6 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
     h->z_is_zero = false;
 
     PhaseParams pp;
-    pp.r = h->r;
-    pp.Z = h->Z;
     pp.C = h->C;
     pp.Ct = h->Ct;
     pp.Kp = coef_pad(h->K);
@@ -641,14 +665,14 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
     pp.dirty = h->dirty;
     pp.seg_s = h->d_seg_s;
     pp.seg_e = h->d_seg_e;
-    pp.seg_lam = h->d_seg_lam;
+    pp.sig = h->d_sig;
+    pp.seg_sig = h->d_seg_sig;
     pp.upd = sc->upd;
     pp.dec = sc->dec;
     pp.tend = sc->tend;
     pp.total = &sc->total;
     pp.visits = &sc->visits;
     pp.done = &sc->done;
-    pp.Tz = Tz;
     pp.max_updates = max_updates;
     pp.M = M;
     pp.c = c;
@@ -731,8 +755,8 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
         // segments come back dirty only where the refreshed state has a
         // coordinate at or above the inner tolerance
         CSC_CUDA(cudaMemsetAsync(h->dirty, 0, (size_t)M, s));
-        CSC_CUDA(launch_resync(h->beta0, h->r, h->Z, h->C, h->norms, h->K, h->L, Tz, h->view(),
-                               1, sc->red, h->dirty, h->d_seg_s, M, pp.tol, s));
+        CSC_CUDA(launch_resync(h->d_sig, h->resync_tiles(), h->C, h->norms, h->K, h->L, 1,
+                               sc->red, 0, h->dirty, h->d_seg_s, pp.tol, s));
         h->launches += 1;
         unsigned long long red[8];
         CSC_CUDA(cudaMemcpyAsync(red, sc->red, sizeof red, cudaMemcpyDeviceToHost, s));
@@ -751,8 +775,8 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
     if (!report_fresh) {
         // optimality report against a fresh r, leaving r unchanged
         CSC_CUDA(cudaMemsetAsync(sc->red, 0, sizeof(sc->red), s));
-        CSC_CUDA(launch_resync(h->beta0, h->r, h->Z, h->C, h->norms, h->K, h->L, Tz, h->view(),
-                               0, sc->red, nullptr, nullptr, 0, 0.f, s));
+        CSC_CUDA(launch_resync(h->d_sig, h->resync_tiles(), h->C, h->norms, h->K, h->L, 0,
+                               sc->red, 0, nullptr, nullptr, 0.f, s));
         h->launches += 1;
     }
     CSC_CUDA(cudaEventRecord(h->ev1, s));
@@ -799,6 +823,106 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
         stats->kernel_launches = h->launches - launches0;
     }
     return status != CSC_OK ? status : (converged ? CSC_OK : CSC_NOT_CONVERGED);
+}
+
+int csc_autotune(csc_handle_t h, double tol, int64_t max_updates, csc_tune_result *out)
+{
+    if (!h)
+        return fail(CSC_EINVAL, "csc_autotune: null handle");
+    if (!h->initialized)
+        return fail(CSC_ESTATE, "csc_autotune: call csc_init first");
+    if (!(tol > 0.0) || max_updates < 1)
+        return fail(CSC_EINVAL, "csc_autotune: need tol > 0 and max_updates >= 1");
+    cudaSetDevice(h->device);
+    cudaStream_t s = h->stream;
+    const size_t nz = (size_t)h->K * h->Tz;
+    // the starting point every candidate solves from
+    const bool cold = h->z_is_zero;
+    if (!cold) {
+        CSC_CUDA(grow(&h->tmpZ, &h->cap_tmpZ, nz));
+        CSC_CUDA(grow(&h->tmpB, &h->cap_tmpB, nz));
+        CSC_CUDA(cudaMemcpyAsync(h->tmpZ, h->Z, sizeof(float) * nz, cudaMemcpyDeviceToDevice, s));
+        CSC_CUDA(cudaMemcpyAsync(h->tmpB, h->r, sizeof(float) * nz, cudaMemcpyDeviceToDevice, s));
+    }
+    auto restore = [&]() -> int {
+        if (cold) {
+            CSC_CUDA(cudaMemsetAsync(h->Z, 0, sizeof(float) * nz, s));
+            CSC_CUDA(cudaMemcpyAsync(h->r, h->beta0, sizeof(float) * nz, cudaMemcpyDeviceToDevice,
+                                     s));
+            h->z_is_zero = true;
+        } else {
+            CSC_CUDA(cudaMemcpyAsync(h->Z, h->tmpZ, sizeof(float) * nz, cudaMemcpyDeviceToDevice,
+                                     s));
+            CSC_CUDA(cudaMemcpyAsync(h->r, h->tmpB, sizeof(float) * nz, cudaMemcpyDeviceToDevice,
+                                     s));
+        }
+        return CSC_OK;
+    };
+    const csc_opts saved = h->opts;
+    const int L = h->L;
+    int ncand = 0;
+    double best_ms = 1e300, default_ms = -1.0;
+    int best_w = 0, best_u = 0, best_c = 0;
+    auto trial = [&](int w, int u, double *ms) -> int {
+        h->opts.segments = 0;
+        h->opts.segment_width = w;
+        h->opts.updates_per_visit = u;
+        h->plan_ok = false;
+        csc_stats st;
+        int rc = csc_solve(h, tol, max_updates, nullptr, nullptr, &st);
+        if (rc < 0)
+            return rc;
+        ncand++;
+        *ms = rc == CSC_OK ? st.solve_ms : 1e300;  // a candidate that did not converge loses
+        if (*ms < best_ms) {
+            best_ms = *ms;
+            best_w = w;
+            best_u = u;
+            best_c = st.phases;
+        }
+        return restore();
+    };
+    // stage 1: segment width (and with it the number of phases) at the given u
+    const int u0 = saved.updates_per_visit ? saved.updates_per_visit : 24;
+    const int widths[] = {std::max(1, L - 1), std::max(1, 2 * L - 2), std::max(1, 3 * L - 3),
+                          std::max(1, 4 * L - 4), std::max(1, 6 * L - 6)};
+    int rc = CSC_OK;
+    for (int i = 0; i < 5 && rc == CSC_OK; i++) {
+        if (i > 0 && widths[i] == widths[i - 1])
+            continue;
+        double ms;
+        rc = trial(widths[i], u0, &ms);
+        if (rc == CSC_OK && widths[i] == std::max(1, 2 * L - 2))
+            default_ms = ms;
+    }
+    // stage 2: updates per visit at the chosen width
+    const int w1 = best_w;
+    const int us[] = {8, 24, 64, 0};
+    for (int i = 0; i < 4 && rc == CSC_OK; i++) {
+        if (us[i] == u0)
+            continue;
+        double ms;
+        rc = trial(w1, us[i], &ms);
+    }
+    if (rc != CSC_OK) {
+        h->opts = saved;
+        h->plan_ok = false;
+        return rc;
+    }
+    h->opts = saved;
+    h->opts.segments = 0;
+    h->opts.segment_width = best_w;
+    h->opts.updates_per_visit = best_u;
+    h->plan_ok = false;
+    if (out) {
+        out->segment_width = best_w;
+        out->updates_per_visit = best_u;
+        out->phases = best_c;
+        out->candidates = ncand;
+        out->best_ms = best_ms;
+        out->default_ms = default_ms;
+    }
+    return CSC_OK;
 }
 
 int csc_kernel_launches(csc_handle_t h, int64_t *out)

@@ -108,28 +108,34 @@ __host__ __device__ __forceinline__ int interval_of(const int64_t *a, int n, int
     return lo;
 }
 
-// Signals of a batch: n signals concatenated in time; signal i owns samples
-// [a[i], a[i+1]) and its valid activation columns [a[i], a[i+1] - L + 1).
-// The L-1 columns [a[i+1] - L + 1, a[i+1]) straddle two signals: they belong
-// to no segment and stay 0, which makes the batch exactly n separate problems
-// (a valid column of signal i and one of signal i+1 are at least L apart).
-struct SignalView {
-    const int64_t *a;   // [n+1]
-    const float *lam;   // [n]
-    int n;
+// One problem of a batch: its own activation arrays, row-major [K][ld] (atom
+// k's row at r + k * ld), valid columns [0, Tz), samples X [P][ldx] with
+// T = Tz + L - 1 of them, and its segments [seg0, seg0 + nseg) of the plan.
+// The arrays of different problems never overlap, so every kernel is a set of
+// independent per-problem computations.  A batch handle points the entries
+// into one concatenation (ld = the concatenation's width); a server points
+// them into separate allocations (ld = Tz).
+struct SigDesc {
+    float *r;            // r = beta - ||D_k||^2 Z
+    float *Z;
+    const float *beta0;  // D~ * X
+    const float *X;
+    int64_t ld, ldx, Tz;
+    int seg0, nseg;
+    float lam;
+    double lam_d;
 };
 
 // Parameters of one phase launch (see kernel_phase.cu).
 struct PhaseParams {
-    float *r;                  // r = beta - n Z, [K][Tz]
-    float *Z;                  // [K][Tz]
+    const SigDesc *sig;        // problems of the batch
+    const int *seg_sig;        // [M] problem of each segment
     const float *C;            // DtD [K][K][W2]
     const float *Ct;           // DtD by lag: Ct[(k0 * W2 + s) * Kp + k] = DtD[k0][k][s], 0 for k >= K
     const float *norms;        // [K]
     unsigned char *dirty;      // [M] segment needs a visit
-    const int64_t *seg_s;      // [M] first column of each segment
+    const int64_t *seg_s;      // [M] first column of each segment (in its problem)
     const int64_t *seg_e;      // [M] one past its last column
-    const float *seg_lam;      // [M] lambda of the segment's signal
     const int *phase_list;     // segments of this phase (grid = their count)
     long long *upd;            // [kPhaseRing] updates per phase launch
     double *dec;               // [kPhaseRing] objective decrease per phase launch
@@ -137,7 +143,6 @@ struct PhaseParams {
     long long *total;          // updates applied in this solve
     long long *visits;         // segment visits that applied updates
     int *done;                 // set once a full sweep applied nothing
-    int64_t Tz;
     long long max_updates;
     int M, c, p, K, Kp, L;  // Kp = K rounded up to a multiple of 4
     int g;        // launch index (monotone within a solve)
@@ -171,46 +176,52 @@ cudaError_t launch_coef_by_lag(const float *C, int K, int L, float *Ct, cudaStre
 cudaError_t launch_dtx(const float *D, const float *X, int K, int P, int L, int64_t T,
                        float *beta0, unsigned int *absmax_bits, double *x2sum, cudaStream_t s);
 
+// Reduction / output tiles of a batch: tile b covers columns (or samples)
+// [start[b], start[b] + width) of problem sig[b], clipped to the problem.
+struct Tiles {
+    const int *sig;
+    const int64_t *start;
+    int64_t n;
+};
+constexpr int kResyncCols = 64;  // columns per resync tile
+constexpr int kTile = 256;       // samples per objective tile, columns per absmax tile
+
 // Re-synchronisation of r with its definition, r = D~*X - sum_{l,t'} S Z
 // (beta0 = D~*X), accumulated in double-float and rounded once to float, and
-// the optimality report over the valid columns of every signal.  red[0..4]
-// receive (as non-negative double bit patterns for atomicMax): the drift
-// max |r_old - r_new|, zero_excess, nonzero_gap, max_delta_z, and the largest
-// coord_step change on the float state.  With dirty != NULL, also marks
-// dirty[m] = 1 for every segment m (bounds seg_s, M entries) that holds a
-// coordinate whose coord_step change on the new state is >= tol_mark.
-cudaError_t launch_resync(const float *beta0, float *r, const float *Z, const float *C,
-                          const float *norms, int K, int L, int64_t Tz, SignalView sig,
-                          int write_r, unsigned long long *red, unsigned char *dirty,
-                          const int64_t *seg_s, int M, float tol_mark, cudaStream_t s);
+// the optimality report over the valid columns of every problem (tiles of
+// kResyncCols columns).  red[0..4] receive (as non-negative double bit
+// patterns for atomicMax): the drift max |r_old - r_new|, zero_excess,
+// nonzero_gap, max_delta_z, and the largest coord_step change on the float
+// state; with red_stride > 0, problem i reduces into red[i * red_stride + q]
+// instead.  With dirty != NULL, also marks dirty[m] = 1 for every segment m
+// (bounds seg_s, local to the problem) that holds a coordinate whose
+// coord_step change on the new state is >= tol_mark.
+cudaError_t launch_resync(const SigDesc *sig, Tiles tiles, const float *C, const float *norms,
+                          int K, int L, int write_r, unsigned long long *red, int red_stride,
+                          unsigned char *dirty, const int64_t *seg_s, float tol_mark,
+                          cudaStream_t s);
 
-// out = r + n Z (beta of Sec. 2.1) in float.
+// out = r + n Z (beta of Sec. 2.1) in float, over one [K][ld] array.
 cudaError_t launch_beta_from_r(const float *r, const float *Z, const float *norms, int K,
                                int64_t Tz, float *out, cudaStream_t s);
 
-// Reduction tiles: kTile consecutive samples of one signal.
-constexpr int kTile = 256;
+// FP64 objective E_i(Z) (Eq. sparse_code) of every problem into out[i] (tiles
+// of kTile samples, partials[2b..2b+1] for tile b; tile_off[i] = first tile of
+// problem i, n+1 entries).  Zalt != NULL replaces each problem's Z by
+// Zalt + (its Z - Zbase) (same layout, another array).
+cudaError_t launch_objective(const float *D, const SigDesc *sig, int n, Tiles tiles,
+                             const int64_t *tile_off, int K, int P, int L, const float *Zbase,
+                             const float *Zalt, double *partials, double *out, cudaStream_t s);
 
-// FP64 objective E_i(Z) (Eq. sparse_code) of every signal into out[i]: tile b
-// covers samples [tile_s[b], min(tile_s[b] + kTile, a[tile_sig[b] + 1])) and
-// its partial sums land in partials[2b..2b+1]; tile_off[i] = first tile of
-// signal i (n+1 entries, device).  lam_d: lambda per signal in double.
-cudaError_t launch_objective(const float *D, const float *X, const float *Z, int K, int P, int L,
-                             int64_t T, SignalView sig, const double *lam_d,
-                             const int64_t *tile_s, const int *tile_sig, int64_t ntiles,
-                             const int64_t *tile_off, double *partials, double *out,
-                             cudaStream_t s);
+// The same for one problem described on the host, with no tables: consecutive
+// tiles, partials holds 2 * ceil(T / kTile) doubles; out[0] = E.
+cudaError_t launch_objective_single(const float *D, const SigDesc &one, int K, int P, int L,
+                                    double *partials, double *out, cudaStream_t s);
 
-// The same for one signal [0, T) with a scalar lambda and no tables: tiles are
-// consecutive and partials holds 2 * ceil(T / kTile) doubles; out[0] = E.
-cudaError_t launch_objective_single(const float *D, const float *X, const float *Z, int K, int P,
-                                    int L, int64_t T, double lambda, double *partials,
-                                    double *out, cudaStream_t s);
-
-// max |beta0| over the valid columns of each signal (out: float bits, zeroed).
-cudaError_t launch_signal_absmax(const float *beta0, int K, int L, int64_t Tz, SignalView sig,
-                                 const int64_t *tile_s, const int *tile_sig, int64_t ntiles,
-                                 unsigned int *out, cudaStream_t s);
+// max |beta0| over the valid columns of each problem (tiles of kTile columns;
+// out: float bits, zeroed by the caller).
+cudaError_t launch_signal_absmax(const SigDesc *sig, Tiles tiles, int K, unsigned int *out,
+                                 cudaStream_t s);
 
 cudaError_t launch_stamp(unsigned long long *out, cudaStream_t s);
 

@@ -146,14 +146,19 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseP
 
     const int K = KFIX ? KT : pp.K, L = pp.L, W2 = 2 * L - 1;
     const int Kp = KFIX ? KPC : pp.Kp;
-    const int64_t Tz = pp.Tz;
+    // the segment's problem: its arrays, row stride, width and lambda
+    const SigDesc *sdp = pp.sig + pp.seg_sig[m];
+    float *const gr = sdp->r;
+    float *const gz = sdp->Z;
+    const int64_t ld = sdp->ld, Tz = sdp->Tz;
+    const int seg_lo = sdp->seg0, seg_hi = sdp->seg0 + sdp->nseg;
     const int64_t s = pp.seg_s[m], e = pp.seg_e[m];
     const int w = (int)(e - s);
     // blockDim == MAXT, a power of two >= 2L-1 (see phase_config)
     constexpr int B = MAXT;
     constexpr int nwarps = B >> 5;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const float lam = pp.seg_lam[m], tol = pp.tol;
+    const float lam = sdp->lam, tol = pp.tol;
 
     const Layout lay(K, pp.w_max, SMEM);
     unsigned long long *ckey = reinterpret_cast<unsigned long long *>(smem_raw + lay.key);
@@ -172,7 +177,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseP
 
     // own segment: element (k, jj = t - s) at rs[jj * cst + k * kst]
     //   staged (SMEM): column-major [jj][k], cst = K|1, kst = 1
-    //   in place:      the global [k][Tz] arrays, cst = 1, kst = Tz
+    //   in place:      the problem's [k][ld] arrays, cst = 1, kst = ld
     float *rs;
     float *zs;
     Idx cst, kst;
@@ -182,18 +187,18 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseP
         cst = (Idx)(K | 1);
         kst = 1;
         for (int k = 0; k < K; k++) {
-            const float *rsrc = pp.r + (int64_t)k * Tz + s;
-            const float *zsrc = pp.Z + (int64_t)k * Tz + s;
+            const float *rsrc = gr + (int64_t)k * ld + s;
+            const float *zsrc = gz + (int64_t)k * ld + s;
             for (int jj = tid; jj < w; jj += B) {
                 rs[jj * cst + k] = rsrc[jj];
                 zs[jj * cst + k] = zsrc[jj];
             }
         }
     } else {
-        rs = pp.r + s;
-        zs = pp.Z + s;
+        rs = gr + s;
+        zs = gz + s;
         cst = 1;
-        kst = (Idx)Tz;
+        kst = (Idx)ld;
     }
     for (int k = tid; k < K; k += B) {
         nrm[k] = pp.norms[k];
@@ -346,12 +351,12 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseP
             // batch), then apply
             const float *Ck = pp.Ct + ((int64_t)k0 * W2 + off) * Kp;
             float *rcol = rs + jj * cst;
-            float *rg = pp.r + t;  // an idle neighbour's column (no other block touches it)
+            float *rg = gr + t;  // an idle neighbour's column (no other block touches it)
             auto apply = [&](int k, float cv) {
                 if (own)
                     rcol[k * kst] = fmaf(-cv, delta, rcol[k * kst]);
                 else
-                    atomicAdd(rg + (int64_t)k * Tz, -cv * delta);
+                    atomicAdd(rg + (int64_t)k * ld, -cv * delta);
             };
             if constexpr (KFIX) {
                 // all K coefficients in one round trip (KPC/4 vector loads)
@@ -383,7 +388,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseP
                 } else {
 #pragma unroll
                     for (int k = 0; k < KT; k++)
-                        atomicAdd(rg + (int64_t)k * Tz, -cv[k] * delta);
+                        atomicAdd(rg + (int64_t)k * ld, -cv[k] * delta);
                 }
             } else {
                 for (int kb = 0; kb < K; kb += kCoefBatch) {
@@ -412,8 +417,8 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseP
     // ---- write back, spill bookkeeping, trace ---------------------------
     if (SMEM && nupd > 0) {
         for (int k = 0; k < K; k++) {
-            float *rdst = pp.r + (int64_t)k * Tz + s;
-            float *zdst = pp.Z + (int64_t)k * Tz + s;
+            float *rdst = gr + (int64_t)k * ld + s;
+            float *zdst = gz + (int64_t)k * ld + s;
             for (int jj = tid; jj < w; jj += B) {
                 rdst[jj] = rs[jj * cst + k];
                 zdst[jj] = zs[jj * cst + k];
@@ -434,11 +439,10 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseP
         if (nupd > 0) {
             // neighbours whose r changed: segments meeting [tmin-L+1, tmax+L-1]
             const int64_t lo = tmin - (L - 1), hi = tmax + (L - 1);
-            // (segments are ordered by position; those of another signal never
-            //  meet the range, the straddling columns keep them L apart)
-            for (int mm = m - 1; mm >= 0 && pp.seg_e[mm] > lo; mm--)
+            // (a problem's segments are consecutive and ordered by position)
+            for (int mm = m - 1; mm >= seg_lo && pp.seg_e[mm] > lo; mm--)
                 pp.dirty[mm] = 1;
-            for (int mm = m + 1; mm < pp.M && pp.seg_s[mm] <= hi; mm++)
+            for (int mm = m + 1; mm < seg_hi && pp.seg_s[mm] <= hi; mm++)
                 pp.dirty[mm] = 1;
             const int slot = pp.g & (kPhaseRing - 1);
             atomicAdd(reinterpret_cast<unsigned long long *>(&pp.upd[slot]),

@@ -1,6 +1,7 @@
 // The re-synchronisation of the solver state r = beta - n Z with its
 // definition (Sec. 2.1), the objective E(Z) of Eq. sparse_code from the
-// explicit residual (FP64, one value per signal), and per-signal lambda_max.
+// explicit residual (FP64, one value per problem), and per-problem lambda_max.
+// Blocks work on tiles of one problem each (SigDesc, Tiles).
 //
 // Both exploit that Z is sparse: a block gathers the nonzeros of Z that can
 // reach its tile (compacted in a fixed order, so results are deterministic)
@@ -16,14 +17,14 @@ constexpr int kChunk = 64;  // Z columns scanned per compaction round
 
 struct NZ {
     int k;
-    int t;  // absolute column index (Tz < 2^31 is checked by csc_init)
+    int t;  // column index in its problem (Tz < 2^31 is checked at init)
     float z;
 };
 
 // Ordered compaction of the nonzeros of Z[:, c0:c1) (k-major) into list.
 // Returns the count (same value in every thread).  Block-wide barriers; each
 // thread takes 4 consecutive elements per round (two barriers per 4*blockDim).
-__device__ int compact_nonzeros(const float *__restrict__ Z, int K, int64_t Tz, int64_t c0,
+__device__ int compact_nonzeros(const float *__restrict__ Z, int K, int64_t ld, int64_t c0,
                                 int64_t c1, NZ *list, int *warp_counts)
 {
     const int tid = threadIdx.x, B = blockDim.x, lane = tid & 31, warp = tid >> 5,
@@ -39,7 +40,7 @@ __device__ int compact_nonzeros(const float *__restrict__ Z, int K, int64_t Tz, 
             const int i = r0 + 4 * tid + q;
             z[q] = 0.f;
             if (i < n)
-                z[q] = Z[(int64_t)(i / width) * Tz + c0 + i % width];
+                z[q] = Z[(int64_t)(i / width) * ld + c0 + i % width];
             cnt += z[q] != 0.f;
         }
         // inclusive warp scan of the counts
@@ -88,26 +89,27 @@ __device__ __forceinline__ void df_add_prod(float &hi, float &lo, float a, float
     lo = __fadd_rn(lo, __fadd_rn(se, pe));
 }
 
-constexpr int kResyncCols = 64;   // output columns per block
 constexpr int kResyncThreads = 256;
 constexpr int kResyncGroups = kResyncThreads / kResyncCols;  // atom groups
 
 template <int KPT>
 __global__ void __launch_bounds__(kResyncThreads)
-    resync_kernel(const float *__restrict__ beta0, float *__restrict__ rr,
-                  const float *__restrict__ Z, const float *__restrict__ C,
-                  const float *__restrict__ norms, int K, int L, int64_t Tz, SignalView sig,
-                  int write_r, unsigned long long *__restrict__ red,
-                  unsigned char *__restrict__ dirty, const int64_t *__restrict__ seg_s, int M,
+    resync_kernel(const SigDesc *__restrict__ sigs, Tiles tiles, const float *__restrict__ C,
+                  const float *__restrict__ norms, int K, int L, int write_r,
+                  unsigned long long *__restrict__ red, int red_stride,
+                  unsigned char *__restrict__ dirty, const int64_t *__restrict__ seg_s,
                   float tol_mark)
 {
     __shared__ NZ list[32 * kChunk];
     __shared__ int warp_counts[32];
     __shared__ float bred[5][kResyncThreads / 32];
+    const int isig = tiles.sig[blockIdx.x];
+    const SigDesc sd = sigs[isig];
+    const int64_t Tz = sd.Tz, ld = sd.ld;
     const int W2 = 2 * L - 1;
     const int tid = threadIdx.x;
     const int col = tid % kResyncCols, grp = tid / kResyncCols;
-    const int64_t c0 = (int64_t)blockIdx.x * kResyncCols;
+    const int64_t c0 = tiles.start[blockIdx.x];
     const int64_t t = c0 + col;
     float acc_hi[KPT], acc_lo[KPT];
 #pragma unroll
@@ -122,7 +124,7 @@ __global__ void __launch_bounds__(kResyncThreads)
     const int chunk = (32 * kChunk) / K < kChunk ? (32 * kChunk) / K : kChunk;
     for (int64_t a = lo; a < hi; a += chunk) {
         const int64_t b = a + chunk < hi ? a + chunk : hi;
-        const int n = compact_nonzeros(Z, K, Tz, a, b, list, warp_counts);
+        const int n = compact_nonzeros(sd.Z, K, ld, a, b, list, warp_counts);
         if (t < Tz) {
             for (int i = 0; i < n; i++) {
                 const NZ e = list[i];
@@ -142,35 +144,26 @@ __global__ void __launch_bounds__(kResyncThreads)
     }
 
     float drift = 0.f, zex = 0.f, nzg = 0.f, all = 0.f, dz32 = 0.f;
-    // the column's signal: valid columns are [a_i, a_{i+1} - L + 1)
-    bool valid = false;
-    float lam = 0.f;
-    if (t < Tz) {
-        const int i = interval_of(sig.a, sig.n, t);
-        valid = t <= sig.a[i + 1] - L;
-        lam = sig.lam[i];
-    }
+    const float lam = sd.lam;
     if (t < Tz) {
 #pragma unroll
         for (int q = 0; q < KPT; q++) {
             const int k = grp + q * kResyncGroups;
             if (k >= K)
                 continue;
-            const int64_t ix = (int64_t)k * Tz + t;
+            const int64_t ix = (int64_t)k * ld + t;
             // r = beta0 - (hi + lo), finished with TwoSum so that only the final
             // float rounding remains
-            const float b0 = beta0[ix], ah = acc_hi[q], al = acc_lo[q];
+            const float b0 = sd.beta0[ix], ah = acc_hi[q], al = acc_lo[q];
             const float sm = __fsub_rn(b0, ah);
             const float bv = __fsub_rn(sm, b0);
             const float er = __fadd_rn(__fsub_rn(b0, __fsub_rn(sm, bv)), __fsub_rn(-ah, bv));
             const float r32 = __fadd_rn(sm, __fsub_rn(er, al));
-            const float rold = rr[ix];
+            const float rold = sd.r[ix];
             if (write_r)
-                rr[ix] = r32;
-            if (!valid)
-                continue;  // a straddling column: frozen at 0, not part of any problem
+                sd.r[ix] = r32;
             drift = fmaxf(drift, fabsf(rold - r32));
-            const float z = Z[ix];
+            const float z = sd.Z[ix];
             const float n = norms[k], rn = __frcp_rn(n);
             // optimality in the r form (Theorem A.1): z = 0 needs |beta| = |r| <= lam;
             // otherwise |Z' - z| with Z' from Eq. pb_coord, without cancellation
@@ -189,8 +182,8 @@ __global__ void __launch_bounds__(kResyncThreads)
             float zn, d32;
             coord_step(write_r ? r32 : rold, z, n, rn, lam, &zn, &d32);
             dz32 = fmaxf(dz32, fabsf(d32));
-            if (dirty && fabsf(d32) >= tol_mark)
-                dirty[interval_of(seg_s, M, t)] = 1;  // segments cover every valid column
+            if (dirty && sd.nseg > 0 && fabsf(d32) >= tol_mark)
+                dirty[sd.seg0 + interval_of(seg_s + sd.seg0, sd.nseg, t)] = 1;
         }
     }
     // block reduce (max) and one atomic per block and quantity
@@ -215,32 +208,32 @@ __global__ void __launch_bounds__(kResyncThreads)
         for (int w = 0; w < kResyncThreads / 32; w++)
             for (int q = 0; q < 5; q++)
                 v[q] = fmaxf(v[q], bred[q][w]);
+        unsigned long long *rd = red + (int64_t)isig * red_stride;
         for (int q = 0; q < 5; q++)
-            atomicMax(&red[q], (unsigned long long)__double_as_longlong((double)v[q]));
+            atomicMax(&rd[q], (unsigned long long)__double_as_longlong((double)v[q]));
     }
 }
 
 constexpr int kObjP = 8;  // channels accumulated per pass
 
-// Tile b (kTile samples of one signal): partials[2b] = sum over its samples of
+// Tile b (kTile samples of one problem): partials[2b] = sum over its samples of
 // sum_p R[p][t]^2 with R = X - sum_k Z_k * D_k ((Z*D)[t] = sum_tau Z[t-tau] D[tau],
-// Sec. 2), partials[2b+1] = sum of |Z| over its columns.
+// Sec. 2), partials[2b+1] = sum of |Z| over its columns.  Without tables
+// (sigs == NULL) the problem is `one` and tile b starts at b * kTile.
 __global__ void __launch_bounds__(kTile)
-    objective_kernel(const float *__restrict__ D, const float *__restrict__ X,
-                     const float *__restrict__ Z, int K, int P, int L, int64_t T,
-                     SignalView sig, const int64_t *__restrict__ tile_s,
-                     const int *__restrict__ tile_sig, double *__restrict__ partials)
+    objective_kernel(const float *__restrict__ D, const SigDesc *__restrict__ sigs, SigDesc one,
+                     Tiles tiles, int K, int P, int L, const float *Zbase, const float *Zalt,
+                     double *__restrict__ partials)
 {
     __shared__ NZ list[32 * kChunk];
     __shared__ int warp_counts[32];
     __shared__ double bsum[2][kTile / 32];
-    const int64_t Tz = T - L + 1;
+    const SigDesc sd = sigs ? sigs[tiles.sig[blockIdx.x]] : one;
+    const float *Z = Zalt ? Zalt + (sd.Z - Zbase) : sd.Z;
+    const int64_t Tz = sd.Tz, ld = sd.ld, T = Tz + L - 1;
     const int tid = threadIdx.x;
-    // without tile tables: one signal [0, T) cut into consecutive tiles
-    const int64_t c0 = tile_s ? tile_s[blockIdx.x] : (int64_t)blockIdx.x * kTile;
-    const int i_sig = tile_sig ? tile_sig[blockIdx.x] : 0;
-    const int64_t end = sig.a ? sig.a[i_sig + 1] : T;
-    const int64_t c1 = c0 + kTile < end ? c0 + kTile : end;
+    const int64_t c0 = sigs ? tiles.start[blockIdx.x] : (int64_t)blockIdx.x * kTile;
+    const int64_t c1 = c0 + kTile < T ? c0 + kTile : T;
     const int64_t t = c0 + tid;
     double sq = 0.0, l1 = 0.0;
     // Z columns that reach samples [c0, c1): [c0-(L-1), c1) within [0,Tz)
@@ -256,7 +249,7 @@ __global__ void __launch_bounds__(kTile)
         }
         for (int64_t a = lo; a < hi; a += chunk) {
             const int64_t b = a + chunk < hi ? a + chunk : hi;
-            const int n = compact_nonzeros(Z, K, Tz, a, b, list, warp_counts);
+            const int n = compact_nonzeros(Z, K, ld, a, b, list, warp_counts);
             if (t < c1) {
                 for (int i = 0; i < n; i++) {
                     const NZ e = list[i];
@@ -278,7 +271,7 @@ __global__ void __launch_bounds__(kTile)
 #pragma unroll
             for (int q = 0; q < kObjP; q++)
                 if (p0 + q < P) {
-                    const double r = (double)X[(int64_t)(p0 + q) * T + t] -
+                    const double r = (double)sd.X[(int64_t)(p0 + q) * sd.ldx + t] -
                                      ((double)acc_hi[q] + (double)acc_lo[q]);
                     sq += r * r;
                 }
@@ -304,11 +297,11 @@ __global__ void __launch_bounds__(kTile)
     }
 }
 
-// Block i: fixed-order sum of signal i's tile partials, E_i = sq/2 + lam_i * l1
-// (without tables: the one signal owns all ntiles tiles and lam0 is its lambda).
+// Block i: fixed-order sum of problem i's tile partials, E_i = sq/2 + lam_i * l1
+// (without tables: the one problem owns all ntiles tiles).
 __global__ void objective_final_kernel(const double *__restrict__ partials,
                                        const int64_t *__restrict__ tile_off, int64_t ntiles,
-                                       const double *__restrict__ lam, double lam0,
+                                       const SigDesc *__restrict__ sigs, double lam0,
                                        double *__restrict__ out)
 {
     __shared__ double s[2][256];
@@ -330,21 +323,21 @@ __global__ void objective_final_kernel(const double *__restrict__ partials,
         __syncthreads();
     }
     if (threadIdx.x == 0)
-        out[i] = 0.5 * s[0][0] + (lam ? lam[i] : lam0) * s[1][0];
+        out[i] = 0.5 * s[0][0] + (sigs ? sigs[i].lam_d : lam0) * s[1][0];
 }
 
-// max |beta0| over tile b's valid columns, into out[signal] (float bits).
+// max |beta0| over tile b's columns, into out[problem] (float bits).
 __global__ void __launch_bounds__(kTile)
-    signal_absmax_kernel(const float *__restrict__ beta0, int K, int L, int64_t Tz,
-                         SignalView sig, const int64_t *__restrict__ tile_s,
-                         const int *__restrict__ tile_sig, unsigned int *__restrict__ out)
+    signal_absmax_kernel(const SigDesc *__restrict__ sigs, Tiles tiles, int K,
+                         unsigned int *__restrict__ out)
 {
-    const int i = tile_sig[blockIdx.x];
-    const int64_t t = tile_s[blockIdx.x] + threadIdx.x;
+    const int i = tiles.sig[blockIdx.x];
+    const SigDesc sd = sigs[i];
+    const int64_t t = tiles.start[blockIdx.x] + threadIdx.x;
     float m = 0.f;
-    if (t <= sig.a[i + 1] - L && t < Tz)
+    if (t < sd.Tz)
         for (int k = 0; k < K; k++)
-            m = fmaxf(m, fabsf(beta0[(int64_t)k * Tz + t]));
+            m = fmaxf(m, fabsf(sd.beta0[(int64_t)k * sd.ld + t]));
     for (int off = 16; off > 0; off >>= 1)
         m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
     if ((threadIdx.x & 31) == 0)
@@ -362,28 +355,29 @@ __global__ void beta_from_r_kernel(const float *__restrict__ r, const float *__r
 }
 
 template <int KPT>
-cudaError_t resync_launch(const float *beta0, float *r, const float *Z, const float *C,
-                          const float *norms, int K, int L, int64_t Tz, SignalView sig,
-                          int write_r, unsigned long long *red, unsigned char *dirty,
-                          const int64_t *seg_s, int M, float tol_mark, cudaStream_t s)
+cudaError_t resync_launch(const SigDesc *sig, Tiles tiles, const float *C, const float *norms,
+                          int K, int L, int write_r, unsigned long long *red, int red_stride,
+                          unsigned char *dirty, const int64_t *seg_s, float tol_mark,
+                          cudaStream_t s)
 {
-    const unsigned grid = (unsigned)((Tz + kResyncCols - 1) / kResyncCols);
-    resync_kernel<KPT><<<grid, kResyncThreads, 0, s>>>(beta0, r, Z, C, norms, K, L, Tz, sig,
-                                                       write_r, red, dirty, seg_s, M, tol_mark);
+    resync_kernel<KPT><<<(unsigned)tiles.n, kResyncThreads, 0, s>>>(
+        sig, tiles, C, norms, K, L, write_r, red, red_stride, dirty, seg_s, tol_mark);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_resync(const float *beta0, float *r, const float *Z, const float *C,
-                          const float *norms, int K, int L, int64_t Tz, SignalView sig,
-                          int write_r, unsigned long long *red, unsigned char *dirty,
-                          const int64_t *seg_s, int M, float tol_mark, cudaStream_t s)
+cudaError_t launch_resync(const SigDesc *sig, Tiles tiles, const float *C, const float *norms,
+                          int K, int L, int write_r, unsigned long long *red, int red_stride,
+                          unsigned char *dirty, const int64_t *seg_s, float tol_mark,
+                          cudaStream_t s)
 {
+    if (tiles.n <= 0)
+        return cudaSuccess;
     const int kpt = (K + kResyncGroups - 1) / kResyncGroups;
-#define CSC_RESYNC(N)                                                                        \
-    return resync_launch<N>(beta0, r, Z, C, norms, K, L, Tz, sig, write_r, red, dirty, seg_s, \
-                            M, tol_mark, s)
+#define CSC_RESYNC(N) \
+    return resync_launch<N>(sig, tiles, C, norms, K, L, write_r, red, red_stride, dirty, seg_s, \
+                            tol_mark, s)
     if (kpt <= 2)
         CSC_RESYNC(2);
     if (kpt <= 8)
@@ -406,46 +400,40 @@ cudaError_t launch_beta_from_r(const float *r, const float *Z, const float *norm
     return cudaGetLastError();
 }
 
-cudaError_t launch_objective(const float *D, const float *X, const float *Z, int K, int P, int L,
-                             int64_t T, SignalView sig, const double *lam_d,
-                             const int64_t *tile_s, const int *tile_sig, int64_t ntiles,
-                             const int64_t *tile_off, double *partials, double *out,
-                             cudaStream_t s)
+cudaError_t launch_objective(const float *D, const SigDesc *sig, int n, Tiles tiles,
+                             const int64_t *tile_off, int K, int P, int L, const float *Zbase,
+                             const float *Zalt, double *partials, double *out, cudaStream_t s)
 {
-    if (ntiles <= 0)
+    if (tiles.n <= 0)
         return cudaSuccess;
-    objective_kernel<<<(unsigned)ntiles, kTile, 0, s>>>(D, X, Z, K, P, L, T, sig, tile_s,
-                                                        tile_sig, partials);
+    objective_kernel<<<(unsigned)tiles.n, kTile, 0, s>>>(D, sig, SigDesc{}, tiles, K, P, L, Zbase,
+                                                         Zalt, partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
-    objective_final_kernel<<<sig.n, 256, 0, s>>>(partials, tile_off, ntiles, lam_d, 0.0, out);
+    objective_final_kernel<<<n, 256, 0, s>>>(partials, tile_off, tiles.n, sig, 0.0, out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_objective_single(const float *D, const float *X, const float *Z, int K, int P,
-                                    int L, int64_t T, double lambda, double *partials,
-                                    double *out, cudaStream_t s)
+cudaError_t launch_objective_single(const float *D, const SigDesc &one, int K, int P, int L,
+                                    double *partials, double *out, cudaStream_t s)
 {
-    const int64_t ntiles = (T + kTile - 1) / kTile;
-    const SignalView one{nullptr, nullptr, 1};
-    objective_kernel<<<(unsigned)ntiles, kTile, 0, s>>>(D, X, Z, K, P, L, T, one, nullptr,
-                                                        nullptr, partials);
+    const int64_t ntiles = (one.Tz + L - 1 + kTile - 1) / kTile;
+    objective_kernel<<<(unsigned)ntiles, kTile, 0, s>>>(D, nullptr, one, Tiles{nullptr, nullptr, 0},
+                                                        K, P, L, nullptr, nullptr, partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
-    objective_final_kernel<<<1, 256, 0, s>>>(partials, nullptr, ntiles, nullptr, lambda, out);
+    objective_final_kernel<<<1, 256, 0, s>>>(partials, nullptr, ntiles, nullptr, one.lam_d, out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_signal_absmax(const float *beta0, int K, int L, int64_t Tz, SignalView sig,
-                                 const int64_t *tile_s, const int *tile_sig, int64_t ntiles,
-                                 unsigned int *out, cudaStream_t s)
+cudaError_t launch_signal_absmax(const SigDesc *sig, Tiles tiles, int K, unsigned int *out,
+                                 cudaStream_t s)
 {
-    if (ntiles <= 0)
+    if (tiles.n <= 0)
         return cudaSuccess;
-    signal_absmax_kernel<<<(unsigned)ntiles, kTile, 0, s>>>(beta0, K, L, Tz, sig, tile_s,
-                                                            tile_sig, out);
+    signal_absmax_kernel<<<(unsigned)tiles.n, kTile, 0, s>>>(sig, tiles, K, out);
     return cudaGetLastError();
 }
 

@@ -93,7 +93,15 @@ extern "C" int csc_objective_noalloc(const float *D, int K, int P, int L, const 
     cudaStream_t s = (cudaStream_t)stream;
     const bool out_on_device = device_resident(E_out);
     double *out = out_on_device ? E_out : scratch + 2 * kNoAllocMaxBlocks;
-    e = csc::launch_objective_single(D, X, Z, K, P, L, T, lambda, scratch, out, s);
+    csc::SigDesc one{};
+    one.Z = const_cast<float *>(Z);
+    one.X = X;
+    one.ld = T - L + 1;
+    one.ldx = T;
+    one.Tz = T - L + 1;
+    one.lam = (float)lambda;
+    one.lam_d = lambda;
+    e = csc::launch_objective_single(D, one, K, P, L, scratch, out, s);
     if (e != cudaSuccess)
         return csc_record_error(CSC_ECUDA, "csc_objective_noalloc: launch failed: %s",
                                 cudaGetErrorString(e));

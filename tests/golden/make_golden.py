@@ -6,7 +6,12 @@ E* = E(Z*) reached by the oracle's phase-schedule locally greedy CD at
 eps = 1e-10, and a hash of the generated inputs so a reader can tell when
 the generator no longer reproduces them.
 
-    python tests/golden/make_golden.py            # all entries
+    python tests/golden/make_golden.py            # all single-signal entries
+    python tests/golden/make_golden.py --batch    # the 512-signal batch (8 processes)
+
+The batch entries (optimum_batch.json) hold, per signal of the batch
+workload, lambda_i = 0.1 * lambda_max_i and E*_i, plus one hash over all
+signals' inputs.
 """
 import hashlib
 import json
@@ -34,7 +39,69 @@ def input_hash(pb) -> str:
     return h.hexdigest()[:16]
 
 
+OUT_BATCH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "optimum_batch.json")
+BATCH = ("batch_P7_K25_L64_n512_T10000_500000", 0)
+
+
+def _batch_entry(i):
+    name, seed = BATCH
+    T = synth.batch_lengths(synth.BATCH_WORKLOADS[name]["n"],
+                            synth.BATCH_WORKLOADS[name]["T_min"],
+                            synth.BATCH_WORKLOADS[name]["T_max"], seed)
+    pb = synth.batch_signal(name, seed, i, int(T[i]))
+    lmax = oracle.lambda_max(pb.D, pb.X)
+    lam = 0.1 * lmax
+    M = max(1, pb.Tz // (2 * pb.L - 2))
+    r = oracle.locally_greedy_cd(pb.D, pb.X, lam, 1e-10, M=M, mode="phase")
+    assert r["converged"]
+    E = oracle.objective(pb.D, pb.X, r["Z"], lam)
+    h = hashlib.sha256()
+    h.update(pb.X.tobytes())
+    return {"i": i, "T": int(T[i]), "lambda": lam, "lambda_max": lmax, "E_star": E,
+            "updates": r["n_updates"], "nnz": int(np.count_nonzero(r["Z"])),
+            "x_sha256": h.hexdigest()}
+
+
+def batch_hash(D, x_hashes) -> str:
+    h = hashlib.sha256()
+    h.update(D.tobytes())
+    for x in x_hashes:
+        h.update(x.encode())
+    return h.hexdigest()[:16]
+
+
+def main_batch(workers: int = 8):
+    import multiprocessing as mp
+    name, seed = BATCH
+    n = synth.BATCH_WORKLOADS[name]["n"]
+    t = time.time()
+    # longest first so the pool's tail is short
+    T = synth.batch_lengths(n, synth.BATCH_WORKLOADS[name]["T_min"],
+                            synth.BATCH_WORKLOADS[name]["T_max"], seed)
+    order = [int(i) for i in np.argsort(-T)]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        rows = {}
+        for r in pool.imap_unordered(_batch_entry, order):
+            rows[r["i"]] = r
+            if len(rows) % 32 == 0:
+                print(f"{len(rows)}/{n} {time.time() - t:.0f}s", flush=True)
+    rows = [rows[i] for i in range(n)]
+    D = synth.make_dictionary(synth.BATCH_WORKLOADS[name]["K"], synth.BATCH_WORKLOADS[name]["P"],
+                              synth.BATCH_WORKLOADS[name]["L"], seed)
+    out = {"workload": name, "seed": seed, "eps": 1e-10,
+           "oracle": "phase schedule, M = max(1, floor(Tz / (2L - 2))) per signal",
+           "input_sha256_16": batch_hash(D, [r["x_sha256"] for r in rows]),
+           "T": [r["T"] for r in rows], "lambda": [r["lambda"] for r in rows],
+           "lambda_max": [r["lambda_max"] for r in rows], "E_star": [r["E_star"] for r in rows],
+           "updates": [r["updates"] for r in rows], "nnz": [r["nnz"] for r in rows]}
+    with open(OUT_BATCH, "w") as f:
+        json.dump(out, f, indent=0)
+    print(f"done in {time.time() - t:.0f}s", flush=True)
+
+
 def main():
+    if "--batch" in sys.argv[1:]:
+        return main_batch()
     res = {}
     for name, seed, M in ENTRIES:
         t = time.time()

@@ -258,3 +258,50 @@ def test_batch_full_size_sampled(capi):
                    for i in range(len(T))])
     assert np.all(Es < E0)
     assert not torch.any(Zd[:, torch.from_numpy(batch.straddle_mask(T, L)).cuda()])
+
+
+def test_autotune_restores_state_and_keeps_parity(capi, long_refs):
+    D, Xs, lams, refs = long_refs
+    X, T = batch.pack(Xs)
+    K, L = D.shape[0], D.shape[2]
+    Tz = int(T.sum()) - L + 1
+    h = capi.csc_setup(cuda(D))
+    try:
+        capi.csc_init_batch(h, cuda(X), T, lams)
+        E0 = capi.csc_objective(h, np.zeros((K, Tz), np.float32))
+        r = capi.csc_autotune(h, 1e-6)
+        assert r["candidates"] >= 5
+        assert r["segment_width"] in (L - 1, 2 * L - 2, 3 * L - 3, 4 * L - 4, 6 * L - 6)
+        assert r["updates_per_visit"] in (8, 24, 64, 0)
+        assert r["phases"] >= 1 and 0 < r["best_ms"] <= r["default_ms"]
+        # the tuner left the problem at its starting point: the next solve is a
+        # cold start (objective trace starts at E(0)) under the chosen options
+        Z = np.zeros((K, Tz), np.float32)
+        status, E, st = capi.csc_solve(h, 1e-6, 1 << 40, Z)
+        tr = capi.csc_get_trace(h)
+        Es = capi.csc_get_objectives(h, len(Xs))
+    finally:
+        capi.csc_destroy(h)
+    assert abs(tr["E_start"] - E0) <= 1e-9 * E0
+    assert st["phases"] == r["phases"]
+    check_batch(dict(Z=Z, T=T, E=E, Es=Es, stats=st, status=status), D, Xs, lams, refs)
+
+
+def test_autotune_from_warm_start(capi, short_refs):
+    D, Xs, lams, lmax, refs = short_refs
+    X, T = batch.pack(Xs)
+    L = D.shape[2]
+    Z0 = batch.pack_Z([Zr.astype(np.float32) * 0.9 for Zr, _ in refs], L)
+    h = capi.csc_setup(cuda(D))
+    try:
+        capi.csc_init_batch(h, cuda(X), T, lams, cuda(Z0))
+        E0 = capi.csc_objective(h, Z0)
+        capi.csc_autotune(h, 1e-6)
+        Z = np.zeros_like(Z0)
+        status, E, st = capi.csc_solve(h, 1e-6, 1 << 40, Z)
+        tr = capi.csc_get_trace(h)
+        Es = capi.csc_get_objectives(h, len(Xs))
+    finally:
+        capi.csc_destroy(h)
+    assert abs(tr["E_start"] - E0) <= 1e-12 * E0
+    check_batch(dict(Z=Z, T=T, E=E, Es=Es, stats=st, status=status), D, Xs, lams, refs)
