@@ -203,8 +203,10 @@ struct csc_handle_s {
     int *d_seg_sig = nullptr;
     int *d_phase_list = nullptr;
     size_t cap_seg_s = 0, cap_seg_e = 0, cap_seg_sig = 0, cap_phase = 0;
-    unsigned char *dirty = nullptr;
-    size_t cap_dirty = 0;
+    unsigned char *dirty = nullptr, *touched = nullptr;
+    size_t cap_dirty = 0, cap_touched = 0;
+    float *tile_rep = nullptr;  // stored resync report per resync tile
+    size_t cap_tile_rep = 0;
 
     float *tmpZ = nullptr, *tmpB = nullptr;
     size_t cap_tmpZ = 0, cap_tmpB = 0;
@@ -278,6 +280,8 @@ int build_plan(csc_handle_t h)
     CSC_CUDA(upload(&h->d_sig, &h->cap_sig, h->sigs, s));
     CSC_CUDA(upload(&h->d_phase_list, &h->cap_phase, list, s));
     CSC_CUDA(grow(&h->dirty, &h->cap_dirty, (size_t)M));
+    CSC_CUDA(grow(&h->touched, &h->cap_touched, (size_t)M));
+    CSC_CUDA(grow(&h->tile_rep, &h->cap_tile_rep, 5 * (size_t)h->nrtiles));
     // the host vectors must outlive the asynchronous copies
     CSC_CUDA(cudaStreamSynchronize(s));
     h->M = M;
@@ -366,7 +370,8 @@ int csc_destroy(csc_handle_t h)
                     h->r,          h->beta0,      h->Z,          h->partials,   h->dirty,
                     h->tmpZ,       h->tmpB,       h->sc,         h->d_sig,      h->d_tile_s,
                     h->d_tile_off, h->d_tile_sig, h->d_rtile_s,  h->d_rtile_sig, h->d_E,
-                    h->d_lmax,     h->d_seg_s,    h->d_seg_e,    h->d_seg_sig,  h->d_phase_list};
+                    h->d_lmax,     h->d_seg_s,    h->d_seg_e,    h->d_seg_sig,  h->d_phase_list,
+                    h->touched,    h->tile_rep};
     for (void *p : bufs)
         cudaFree(p);
     if (h->poll)
@@ -538,7 +543,7 @@ int csc_init_batch(csc_handle_t h, const float *X, const int64_t *T, int n, cons
                                        sizeof(float) * (h->L - 1), h->K, s));
         CSC_CUDA(cudaMemsetAsync(h->sc->red, 0, sizeof(h->sc->red), s));
         CSC_CUDA(launch_resync(h->d_sig, h->resync_tiles(), h->C, h->norms, h->K, h->L, 1,
-                               h->sc->red, 0, nullptr, nullptr, 0.f, s));
+                               h->sc->red, 0, nullptr, nullptr, 0.f, nullptr, nullptr, s));
     } else {
         CSC_CUDA(cudaMemsetAsync(h->Z, 0, sizeof(float) * nz, s));
         CSC_CUDA(cudaMemcpyAsync(h->r, h->beta0, sizeof(float) * nz, cudaMemcpyDeviceToDevice, s));
@@ -643,6 +648,8 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
     }
 
     CSC_CUDA(cudaMemsetAsync(h->dirty, 1, (size_t)M, s));
+    // the first resync of the solve recomputes every tile
+    CSC_CUDA(cudaMemsetAsync(h->touched, 1, (size_t)M, s));
     CSC_CUDA(cudaMemsetAsync(sc, 0, offsetof(Scratch, lmax_bits), s));
     CSC_CUDA(cudaMemsetAsync(sc->red, 0, sizeof(sc->red), s));
     CSC_CUDA(cudaEventRecord(h->ev0, s));
@@ -663,6 +670,7 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
     pp.Kp = coef_pad(h->K);
     pp.norms = h->norms;
     pp.dirty = h->dirty;
+    pp.touched = h->touched;
     pp.seg_s = h->d_seg_s;
     pp.seg_e = h->d_seg_e;
     pp.sig = h->d_sig;
@@ -756,7 +764,9 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
         // coordinate at or above the inner tolerance
         CSC_CUDA(cudaMemsetAsync(h->dirty, 0, (size_t)M, s));
         CSC_CUDA(launch_resync(h->d_sig, h->resync_tiles(), h->C, h->norms, h->K, h->L, 1,
-                               sc->red, 0, h->dirty, h->d_seg_s, pp.tol, s));
+                               sc->red, 0, h->dirty, h->d_seg_s, pp.tol, h->touched, h->tile_rep,
+                               s));
+        CSC_CUDA(cudaMemsetAsync(h->touched, 0, (size_t)M, s));
         h->launches += 1;
         unsigned long long red[8];
         CSC_CUDA(cudaMemcpyAsync(red, sc->red, sizeof red, cudaMemcpyDeviceToHost, s));
@@ -776,7 +786,7 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
         // optimality report against a fresh r, leaving r unchanged
         CSC_CUDA(cudaMemsetAsync(sc->red, 0, sizeof(sc->red), s));
         CSC_CUDA(launch_resync(h->d_sig, h->resync_tiles(), h->C, h->norms, h->K, h->L, 0,
-                               sc->red, 0, nullptr, nullptr, 0.f, s));
+                               sc->red, 0, nullptr, h->d_seg_s, 0.f, h->touched, h->tile_rep, s));
         h->launches += 1;
     }
     CSC_CUDA(cudaEventRecord(h->ev1, s));

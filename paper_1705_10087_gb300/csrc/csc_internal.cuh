@@ -134,6 +134,7 @@ struct PhaseParams {
     const float *Ct;           // DtD by lag: Ct[(k0 * W2 + s) * Kp + k] = DtD[k0][k][s], 0 for k >= K
     const float *norms;        // [K]
     unsigned char *dirty;      // [M] segment needs a visit
+    unsigned char *touched;    // [M] r changed in the segment since the last resync
     const int64_t *seg_s;      // [M] first column of each segment (in its problem)
     const int64_t *seg_e;      // [M] one past its last column
     const int *phase_list;     // segments of this phase (grid = their count)
@@ -196,10 +197,14 @@ constexpr int kTile = 256;       // samples per objective tile, columns per absm
 // instead.  With dirty != NULL, also marks dirty[m] = 1 for every segment m
 // (bounds seg_s, local to the problem) that holds a coordinate whose
 // coord_step change on the new state is >= tol_mark.
+// With touched != NULL (per segment: r changed there since r was last exact)
+// a tile whose columns meet no touched segment is not recomputed: its r is
+// already exact, and its report values are the ones stored in rep[5 b..5 b+4]
+// when it was last computed (every computed tile stores them when rep != NULL).
 cudaError_t launch_resync(const SigDesc *sig, Tiles tiles, const float *C, const float *norms,
                           int K, int L, int write_r, unsigned long long *red, int red_stride,
                           unsigned char *dirty, const int64_t *seg_s, float tol_mark,
-                          cudaStream_t s);
+                          const unsigned char *touched, float *rep, cudaStream_t s);
 
 // out = r + n Z (beta of Sec. 2.1) in float, over one [K][ld] array.
 cudaError_t launch_beta_from_r(const float *r, const float *Z, const float *norms, int K,

@@ -439,11 +439,17 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseP
         if (nupd > 0) {
             // neighbours whose r changed: segments meeting [tmin-L+1, tmax+L-1]
             const int64_t lo = tmin - (L - 1), hi = tmax + (L - 1);
-            // (a problem's segments are consecutive and ordered by position)
-            for (int mm = m - 1; mm >= seg_lo && pp.seg_e[mm] > lo; mm--)
+            // (a problem's segments are consecutive and ordered by position);
+            // they and this segment are also touched: r changed there
+            for (int mm = m - 1; mm >= seg_lo && pp.seg_e[mm] > lo; mm--) {
                 pp.dirty[mm] = 1;
-            for (int mm = m + 1; mm < seg_hi && pp.seg_s[mm] <= hi; mm++)
+                pp.touched[mm] = 1;
+            }
+            for (int mm = m + 1; mm < seg_hi && pp.seg_s[mm] <= hi; mm++) {
                 pp.dirty[mm] = 1;
+                pp.touched[mm] = 1;
+            }
+            pp.touched[m] = 1;
             const int slot = pp.g & (kPhaseRing - 1);
             atomicAdd(reinterpret_cast<unsigned long long *>(&pp.upd[slot]),
                       (unsigned long long)nupd);

@@ -98,7 +98,8 @@ __global__ void __launch_bounds__(kResyncThreads)
                   const float *__restrict__ norms, int K, int L, int write_r,
                   unsigned long long *__restrict__ red, int red_stride,
                   unsigned char *__restrict__ dirty, const int64_t *__restrict__ seg_s,
-                  float tol_mark)
+                  float tol_mark, const unsigned char *__restrict__ touched,
+                  float *__restrict__ rep)
 {
     __shared__ NZ list[32 * kChunk];
     __shared__ int warp_counts[32];
@@ -111,6 +112,28 @@ __global__ void __launch_bounds__(kResyncThreads)
     const int col = tid % kResyncCols, grp = tid / kResyncCols;
     const int64_t c0 = tiles.start[blockIdx.x];
     const int64_t t = c0 + col;
+    float drift = 0.f, zex = 0.f, nzg = 0.f, all = 0.f, dz32 = 0.f;
+    // r changed on this tile's columns only where an update window reached
+    // them, and every window marks the segments it covers as touched
+    bool need = true;
+    if (touched && rep && sd.nseg > 0) {
+        const int64_t ce = c0 + kResyncCols < Tz ? c0 + kResyncCols : Tz;
+        const int64_t *ss = seg_s + sd.seg0;
+        need = false;
+        for (int j = interval_of(ss, sd.nseg, c0); j < sd.nseg && ss[j] < ce; j++)
+            if (touched[sd.seg0 + j]) {
+                need = true;
+                break;
+            }
+    }
+    if (!need) {
+        if (tid == 0) {  // the stored report of the unchanged tile (drift 0)
+            zex = rep[5 * blockIdx.x + 1];
+            nzg = rep[5 * blockIdx.x + 2];
+            all = rep[5 * blockIdx.x + 3];
+            dz32 = rep[5 * blockIdx.x + 4];
+        }
+    } else {
     float acc_hi[KPT], acc_lo[KPT];
 #pragma unroll
     for (int i = 0; i < KPT; i++) {
@@ -143,7 +166,6 @@ __global__ void __launch_bounds__(kResyncThreads)
         __syncthreads();
     }
 
-    float drift = 0.f, zex = 0.f, nzg = 0.f, all = 0.f, dz32 = 0.f;
     const float lam = sd.lam;
     if (t < Tz) {
 #pragma unroll
@@ -186,6 +208,7 @@ __global__ void __launch_bounds__(kResyncThreads)
                 dirty[sd.seg0 + interval_of(seg_s + sd.seg0, sd.nseg, t)] = 1;
         }
     }
+    }  // need
     // block reduce (max) and one atomic per block and quantity
     for (int off = 16; off > 0; off >>= 1) {
         drift = fmaxf(drift, __shfl_xor_sync(0xffffffffu, drift, off));
@@ -208,6 +231,9 @@ __global__ void __launch_bounds__(kResyncThreads)
         for (int w = 0; w < kResyncThreads / 32; w++)
             for (int q = 0; q < 5; q++)
                 v[q] = fmaxf(v[q], bred[q][w]);
+        if (need && rep)
+            for (int q = 0; q < 5; q++)
+                rep[5 * blockIdx.x + q] = v[q];
         unsigned long long *rd = red + (int64_t)isig * red_stride;
         for (int q = 0; q < 5; q++)
             atomicMax(&rd[q], (unsigned long long)__double_as_longlong((double)v[q]));
@@ -358,10 +384,10 @@ template <int KPT>
 cudaError_t resync_launch(const SigDesc *sig, Tiles tiles, const float *C, const float *norms,
                           int K, int L, int write_r, unsigned long long *red, int red_stride,
                           unsigned char *dirty, const int64_t *seg_s, float tol_mark,
-                          cudaStream_t s)
+                          const unsigned char *touched, float *rep, cudaStream_t s)
 {
     resync_kernel<KPT><<<(unsigned)tiles.n, kResyncThreads, 0, s>>>(
-        sig, tiles, C, norms, K, L, write_r, red, red_stride, dirty, seg_s, tol_mark);
+        sig, tiles, C, norms, K, L, write_r, red, red_stride, dirty, seg_s, tol_mark, touched, rep);
     return cudaGetLastError();
 }
 
@@ -370,14 +396,14 @@ cudaError_t resync_launch(const SigDesc *sig, Tiles tiles, const float *C, const
 cudaError_t launch_resync(const SigDesc *sig, Tiles tiles, const float *C, const float *norms,
                           int K, int L, int write_r, unsigned long long *red, int red_stride,
                           unsigned char *dirty, const int64_t *seg_s, float tol_mark,
-                          cudaStream_t s)
+                          const unsigned char *touched, float *rep, cudaStream_t s)
 {
     if (tiles.n <= 0)
         return cudaSuccess;
     const int kpt = (K + kResyncGroups - 1) / kResyncGroups;
 #define CSC_RESYNC(N) \
     return resync_launch<N>(sig, tiles, C, norms, K, L, write_r, red, red_stride, dirty, seg_s, \
-                            tol_mark, s)
+                            tol_mark, touched, rep, s)
     if (kpt <= 2)
         CSC_RESYNC(2);
     if (kpt <= 8)
