@@ -98,6 +98,9 @@ typedef struct csc_stats {
     int64_t phase_launches;   /* phase-kernel launches issued */
     int64_t visits;           /* segment visits that applied at least one update */
     int64_t kernel_launches;  /* all kernels this call launched */
+    int64_t drift_resyncs;    /* resyncs that interrupted a CD round still running after
+                                 32 sweeps (float32 drift on strongly coupled atoms);
+                                 they do not count towards max_resyncs */
 } csc_stats;
 
 /* Fill *o with the defaults (all zero / -1 as documented above). */

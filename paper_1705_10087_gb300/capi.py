@@ -38,7 +38,8 @@ class csc_stats(ctypes.Structure):
                 ("kkt_zero_excess", ctypes.c_double), ("kkt_nonzero_gap", ctypes.c_double),
                 ("max_delta_z", ctypes.c_double), ("solve_ms", ctypes.c_double),
                 ("phase_ms", ctypes.c_double), ("phase_launches", ctypes.c_int64),
-                ("visits", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
+                ("visits", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("drift_resyncs", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -51,6 +52,30 @@ class csc_tune_result(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class csc_server_opts(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("sweeps_per_step", ctypes.c_int32),
+                ("max_resyncs", ctypes.c_int32), ("max_active", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
+
+
+class csc_request_info(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("dict", ctypes.c_int32), ("T", ctypes.c_int64),
+                ("lambda_", ctypes.c_double), ("lambda_max", ctypes.c_double),
+                ("objective", ctypes.c_double), ("max_delta_z", ctypes.c_double),
+                ("resyncs", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("rounds", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        d = {name: getattr(self, name) for name, _ in self._fields_}
+        d["lambda"] = d.pop("lambda_")
+        return d
+
+
+CSC_REQ_QUEUED, CSC_REQ_ACTIVE, CSC_REQ_DONE = 0, 1, 2
 
 
 class CscError(RuntimeError):
@@ -101,13 +126,29 @@ def load(path: str | None = None):
     lib.csc_lambda_max_batch.argtypes = [_vp, _vp]
     lib.csc_get_objectives.argtypes = [_vp, _vp]
     lib.csc_autotune.argtypes = [_vp, ctypes.c_double, _i64, ctypes.POINTER(csc_tune_result)]
+    lib.csc_server_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(csc_server_opts)]
+    lib.csc_server_add_dictionary.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.POINTER(ctypes.c_int)]
+    lib.csc_server_submit.argtypes = [_vp, ctypes.c_int, _vp, _i64, ctypes.c_double,
+                                      ctypes.c_double, ctypes.POINTER(_i64)]
+    lib.csc_server_step.argtypes = [_vp, ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.csc_server_info.argtypes = [_vp, _i64, ctypes.POINTER(csc_request_info)]
+    lib.csc_server_fetch.argtypes = [_vp, _i64, _vp, ctypes.POINTER(csc_request_info)]
+    lib.csc_server_memory.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                                      ctypes.POINTER(_i64)]
+    lib.csc_server_kernel_launches.argtypes = [_vp, ctypes.POINTER(_i64)]
+    lib.csc_server_destroy.argtypes = [_vp]
     lib.csc_last_error_string.argtypes = []
     lib.csc_last_error_string.restype = ctypes.c_char_p
     for name in ("csc_setup", "csc_init", "csc_solve", "csc_destroy", "csc_lambda_max",
                  "csc_get_beta", "csc_get_dtd", "csc_objective", "csc_get_trace", "csc_plan",
                  "csc_kernel_launches", "csc_objective_noalloc", "csc_init_batch",
                  "csc_set_lambda", "csc_lambda_max_batch", "csc_get_objectives",
-                 "csc_autotune"):
+                 "csc_autotune", "csc_server_create", "csc_server_add_dictionary",
+                 "csc_server_submit", "csc_server_step", "csc_server_info", "csc_server_fetch",
+                 "csc_server_memory", "csc_server_kernel_launches", "csc_server_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     if path == _build.LIB:
         _lib = lib
@@ -285,3 +326,66 @@ def csc_plan(Tz: int, L: int, M: int = 0):
     starts = np.zeros(Mo.value + 1, np.int64)
     _check(load().csc_plan(int(Tz), int(L), Mo.value, None, None, starts.ctypes.data))
     return Mo.value, c.value, starts
+
+
+# ------------------------------------------------------------------ server
+
+def csc_server_create(hbm_budget_bytes: int = 0, sweeps_per_step: int = 0,
+                      max_resyncs: int = -1, max_active: int = 0):
+    o = csc_server_opts()
+    o.hbm_budget_bytes, o.sweeps_per_step = hbm_budget_bytes, sweeps_per_step
+    o.max_resyncs, o.max_active = max_resyncs, max_active
+    s = _vp()
+    _check(load().csc_server_create(ctypes.byref(s), ctypes.byref(o)))
+    return s
+
+
+def csc_server_add_dictionary(s, D, segment_width: int = 0, updates_per_visit: int = 0) -> int:
+    K, P, L = (int(x) for x in D.shape)
+    d = ctypes.c_int(0)
+    _check(load().csc_server_add_dictionary(s, _ptr(D), K, P, L, segment_width,
+                                            updates_per_visit, ctypes.byref(d)))
+    return d.value
+
+
+def csc_server_submit(s, dict_id: int, X, lam: float, tol: float) -> int:
+    """lam > 0: absolute lambda; lam < 0: |lam| * lambda_max of X."""
+    r = _i64(0)
+    _check(load().csc_server_submit(s, int(dict_id), _ptr(X), int(X.shape[1]), float(lam),
+                                    float(tol), ctypes.byref(r)))
+    return r.value
+
+
+def csc_server_step(s):
+    """One scheduling round -> (active, queued, finished in this round)."""
+    a, q, d = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().csc_server_step(s, ctypes.byref(a), ctypes.byref(q), ctypes.byref(d)))
+    return a.value, q.value, d.value
+
+
+def csc_server_info(s, req: int) -> dict:
+    info = csc_request_info()
+    _check(load().csc_server_info(s, int(req), ctypes.byref(info)))
+    return info.as_dict()
+
+
+def csc_server_fetch(s, req: int, Z_out=None) -> dict:
+    info = csc_request_info()
+    _check(load().csc_server_fetch(s, int(req), _ptr(Z_out, True), ctypes.byref(info)))
+    return info.as_dict()
+
+
+def csc_server_memory(s):
+    a, b, c = _i64(0), _i64(0), _i64(0)
+    _check(load().csc_server_memory(s, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return {"pool_bytes": a.value, "in_use": b.value, "peak": c.value}
+
+
+def csc_server_kernel_launches(s) -> int:
+    v = _i64(0)
+    _check(load().csc_server_kernel_launches(s, ctypes.byref(v)))
+    return v.value
+
+
+def csc_server_destroy(s) -> None:
+    _check(load().csc_server_destroy(s))

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "csc_internal.cuh"
+#include "host_util.cuh"
 
 using namespace csc;
 
@@ -67,32 +68,6 @@ struct Poll {
     int pad;
 };
 
-bool is_device_pointer(const void *p)
-{
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
-cudaError_t copy_in(void *dst, const void *src, size_t bytes, cudaStream_t s)
-{
-    return cudaMemcpyAsync(dst, src, bytes,
-                           is_device_pointer(src) ? cudaMemcpyDeviceToDevice
-                                                  : cudaMemcpyHostToDevice,
-                           s);
-}
-
-cudaError_t copy_out(void *dst, const void *src, size_t bytes, cudaStream_t s)
-{
-    return cudaMemcpyAsync(dst, src, bytes,
-                           is_device_pointer(dst) ? cudaMemcpyDeviceToDevice
-                                                  : cudaMemcpyDeviceToHost,
-                           s);
-}
-
 // Phases of the schedule for one signal: co-active segments m, m' (m == m'
 // mod c) must leave at least 2L-2 samples between them, (c-1) w_min >= 2L-2.
 int phase_count_host(int64_t Tz, int M, int L)
@@ -120,30 +95,6 @@ int auto_segments(int64_t Tz, int L)
     if (M > (1 << 30))
         M = 1 << 30;
     return (int)M;
-}
-
-template <class T>
-cudaError_t grow(T **p, size_t *cap, size_t n)
-{
-    if (*cap >= n && *p)
-        return cudaSuccess;
-    if (*p)
-        cudaFree(*p);
-    *p = nullptr;
-    *cap = 0;
-    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), sizeof(T) * (n ? n : 1));
-    if (e == cudaSuccess)
-        *cap = n;
-    return e;
-}
-
-template <class T>
-cudaError_t upload(T **p, size_t *cap, const std::vector<T> &v, cudaStream_t s)
-{
-    cudaError_t e = grow(p, cap, v.size());
-    if (e != cudaSuccess)
-        return e;
-    return cudaMemcpyAsync(*p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s);
 }
 
 }  // namespace
@@ -690,18 +641,22 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
     // CD runs to tol/2 and a resync accepts at tol: coordinates left just under
     // the inner tolerance then stay under tol after the exact refresh, instead
     // of bouncing back above it round after round
-    pp.tol = (float)(max_resyncs > 0 ? 0.5 * tol : tol);
+    const float tol_inner = (float)(max_resyncs > 0 ? 0.5 * tol : tol);
+    for (SigDesc &d : h->sigs)
+        d.tol = tol_inner;
+    CSC_CUDA(upload(&h->d_sig, &h->cap_sig, h->sigs, s));
     pp.w_max = h->w_max;
 
     int status = CSC_OK;
     bool converged = false, report_fresh = false;
     int resyncs = 0;
+    int64_t drift_resyncs = 0;
     double drift = 0.0, phase_ms = 0.0;
     int64_t g = 0, effective = 0, phase_launches = 0;
     for (;;) {
         const int64_t g_round = g;
         CSC_CUDA(cudaMemsetAsync(&sc->done, 0, sizeof(int), s));
-        bool round_done = false;
+        bool round_done = false, forced = false;
         for (;;) {
             int nb = 0;  // launches in this poll batch
             for (int i = 0; i < S; i++)
@@ -750,28 +705,39 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
                 status = CSC_NOT_CONVERGED;
                 break;
             }
+            if (max_resyncs > 0 && g - g_round >= (int64_t)kDriftSweeps * c) {
+                forced = true;
+                break;
+            }
         }
-        if (!round_done) {
+        if (!round_done && !forced) {
             effective += g - g_round;
             break;
         }
-        if (resyncs >= max_resyncs) {
+        if (forced)
+            effective += g - g_round;
+        if (round_done && resyncs >= max_resyncs) {
             converged = true;
             break;
         }
         CSC_CUDA(cudaMemsetAsync(sc->red, 0, sizeof(sc->red), s));
         // segments come back dirty only where the refreshed state has a
-        // coordinate at or above the inner tolerance
-        CSC_CUDA(cudaMemsetAsync(h->dirty, 0, (size_t)M, s));
+        // coordinate at or above the inner tolerance (a round cut short keeps
+        // the segments it still had to visit)
+        if (round_done)
+            CSC_CUDA(cudaMemsetAsync(h->dirty, 0, (size_t)M, s));
         CSC_CUDA(launch_resync(h->d_sig, h->resync_tiles(), h->C, h->norms, h->K, h->L, 1,
-                               sc->red, 0, h->dirty, h->d_seg_s, pp.tol, h->touched, h->tile_rep,
+                               sc->red, 0, h->dirty, h->d_seg_s, tol_inner, h->touched, h->tile_rep,
                                s));
         CSC_CUDA(cudaMemsetAsync(h->touched, 0, (size_t)M, s));
         h->launches += 1;
         unsigned long long red[8];
         CSC_CUDA(cudaMemcpyAsync(red, sc->red, sizeof red, cudaMemcpyDeviceToHost, s));
         CSC_CUDA(cudaStreamSynchronize(s));
-        resyncs++;
+        if (round_done)
+            resyncs++;
+        else
+            drift_resyncs++;
         double d0, dz32;
         std::memcpy(&d0, &red[0], sizeof d0);
         std::memcpy(&dz32, &red[4], sizeof dz32);
@@ -831,6 +797,7 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
         stats->phase_launches = phase_launches;
         stats->visits = visits;
         stats->kernel_launches = h->launches - launches0;
+        stats->drift_resyncs = drift_resyncs;
     }
     return status != CSC_OK ? status : (converged ? CSC_OK : CSC_NOT_CONVERGED);
 }

@@ -14,6 +14,11 @@ namespace csc {
 constexpr int kMaxL = 512;
 constexpr int kPhaseRing = 1 << 16;      // per-phase trace slots (ring)
 constexpr int kDefaultMaxVisit = 1 << 20;  // cap on updates per segment visit
+// A CD round that has not settled after this many sweeps is interrupted by a
+// resync: on strongly coupled atoms float32 rounding in the incremental
+// updates of r can otherwise keep driving updates that the exact r would not
+// make (a cycle that never lowers E).
+constexpr int kDriftSweeps = 32;
 constexpr int kMaxSmem = 226 * 1024;     // dynamic shared memory per block (227 KB on sm_103a, less static)
 
 // Segment m of M over [0,Tz) (Sec. 2.2, 0-based): [floor(m*Tz/M), floor((m+1)*Tz/M)).
@@ -123,6 +128,7 @@ struct SigDesc {
     int64_t ld, ldx, Tz;
     int seg0, nseg;
     float lam;
+    float tol;  // CD stopping threshold of the problem (|Delta Z| below it: converged)
     double lam_d;
 };
 
@@ -149,7 +155,6 @@ struct PhaseParams {
     int g;        // launch index (monotone within a solve)
     int g_round;  // first launch index of the current CD round
     int u;        // cap on updates per visit
-    float tol;
     int w_max;  // widest segment (shared-memory layout)
 };
 
@@ -196,7 +201,8 @@ constexpr int kTile = 256;       // samples per objective tile, columns per absm
 // state; with red_stride > 0, problem i reduces into red[i * red_stride + q]
 // instead.  With dirty != NULL, also marks dirty[m] = 1 for every segment m
 // (bounds seg_s, local to the problem) that holds a coordinate whose
-// coord_step change on the new state is >= tol_mark.
+// coord_step change on the new state is >= tol_mark (tol_mark < 0: the
+// problem's own tol).
 // With touched != NULL (per segment: r changed there since r was last exact)
 // a tile whose columns meet no touched segment is not recomputed: its r is
 // already exact, and its report values are the ones stored in rep[5 b..5 b+4]

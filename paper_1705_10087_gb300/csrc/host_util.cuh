@@ -1,0 +1,61 @@
+// Host-side helpers shared by the C ABI translation units: pointer-kind
+// detection, copies in either direction and growable device buffers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+namespace csc {
+
+inline bool is_device_pointer(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+inline cudaError_t copy_in(void *dst, const void *src, size_t bytes, cudaStream_t s)
+{
+    return cudaMemcpyAsync(dst, src, bytes,
+                           is_device_pointer(src) ? cudaMemcpyDeviceToDevice
+                                                  : cudaMemcpyHostToDevice,
+                           s);
+}
+
+inline cudaError_t copy_out(void *dst, const void *src, size_t bytes, cudaStream_t s)
+{
+    return cudaMemcpyAsync(dst, src, bytes,
+                           is_device_pointer(dst) ? cudaMemcpyDeviceToDevice
+                                                  : cudaMemcpyDeviceToHost,
+                           s);
+}
+
+template <class T>
+cudaError_t grow(T **p, size_t *cap, size_t n)
+{
+    if (*cap >= n && *p)
+        return cudaSuccess;
+    if (*p)
+        cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), sizeof(T) * (n ? n : 1));
+    if (e == cudaSuccess)
+        *cap = n;
+    return e;
+}
+
+template <class T>
+cudaError_t upload(T **p, size_t *cap, const std::vector<T> &v, cudaStream_t s)
+{
+    cudaError_t e = grow(p, cap, v.size());
+    if (e != cudaSuccess)
+        return e;
+    return cudaMemcpyAsync(*p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s);
+}
+
+}  // namespace csc

@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseP
     constexpr int B = MAXT;
     constexpr int nwarps = B >> 5;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const float lam = sdp->lam, tol = pp.tol;
+    const float lam = sdp->lam, tol = sdp->tol;
 
     const Layout lay(K, pp.w_max, SMEM);
     unsigned long long *ckey = reinterpret_cast<unsigned long long *>(smem_raw + lay.key);

@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(kResyncThreads)
             float zn, d32;
             coord_step(write_r ? r32 : rold, z, n, rn, lam, &zn, &d32);
             dz32 = fmaxf(dz32, fabsf(d32));
-            if (dirty && sd.nseg > 0 && fabsf(d32) >= tol_mark)
+            if (dirty && sd.nseg > 0 && fabsf(d32) >= (tol_mark < 0.f ? sd.tol : tol_mark))
                 dirty[sd.seg0 + interval_of(seg_s + sd.seg0, sd.nseg, t)] = 1;
         }
     }

@@ -254,6 +254,53 @@ def make_batch(name: str, seed: int = 0, n: int | None = None, T_max: int | None
     return [batch_signal(*a) for a in args]
 
 
+# Request streams: Poisson arrivals of signals with log-uniform lengths, each
+# for one of several resident dictionaries (K, L, P) drawn uniformly.
+SERVE_WORKLOADS = {
+    "serve_4dict_poisson200_T5000_2000000": dict(
+        rate=200.0, T_min=5_000, T_max=2_000_000, rho=0.005, sigma=0.1, lambda_frac=0.1,
+        tol=1e-4, budget_bytes=40 << 30,
+        dicts=((25, 64, 1), (25, 128, 7), (64, 64, 7), (64, 128, 1))),  # (K, L, P)
+}
+
+
+def serve_sources(name: str, seed: int = 0, T_source: int | None = None, workers: int = 0):
+    """One long synthetic recording per dictionary of a request stream: a list
+    of Problems (dictionary of seed (seed << 8) + j, T_source samples, default
+    the longest request).  Requests are windows of these recordings."""
+    w = SERVE_WORKLOADS[name]
+    T = int(T_source if T_source is not None else w["T_max"])
+    args = [(K, P, L, T, w["rho"], w["sigma"], (seed << 8) + j)
+            for j, (K, L, P) in enumerate(w["dicts"])]
+    if workers > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(min(workers, len(args))) as pool:
+            return pool.map(_serve_source_args, args)
+    return [_serve_source_args(a) for a in args]
+
+
+def _serve_source_args(a):
+    K, P, L, T, rho, sigma, s = a
+    return make_problem(K=K, P=P, L=L, T=T, rho=rho, sigma=sigma, seed=s, support="gaps")
+
+
+def serve_schedule(name: str, n: int, seed: int = 0, T_max: int | None = None) -> dict:
+    """The first n requests of a stream: arrival times (s, Poisson process at
+    the stream's rate), dictionary index (uniform), length (log-uniform on
+    [T_min, T_max]) and window offset into the dictionary's recording (uniform)."""
+    w = SERVE_WORKLOADS[name]
+    T_max = int(T_max if T_max is not None else w["T_max"])
+    T_min = min(int(w["T_min"]), T_max)
+    gaps = -np.log(uniform(seed, 20, n)) / w["rate"]
+    dict_idx = np.minimum((uniform(seed, 21, n) * len(w["dicts"])).astype(np.int64),
+                          len(w["dicts"]) - 1)
+    u = uniform(seed, 22, n)
+    T = np.floor(np.exp(np.log(T_min) + u * (np.log(T_max) - np.log(T_min)))).astype(np.int64)
+    T = np.clip(T, T_min, T_max)
+    frac = uniform(seed, 23, n)
+    return {"arrival": np.cumsum(gaps), "dict": dict_idx, "T": T, "offset_frac": frac}
+
+
 def make_workload(name: str, seed: int = 0, T: int | None = None) -> Problem:
     """Problem for a named workload; T may be overridden for reduced-size cases."""
     w = WORKLOADS[name]
