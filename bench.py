@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the 512-signal batched-vs-plain comparison")
+    ap.add_argument("--no-serve", action="store_true", help="skip the request-stream leg")
+    ap.add_argument("--serve-requests", type=int, default=400)
     return ap.parse_args()
 
 
@@ -274,7 +276,7 @@ def batch_leg(args, capi, torch):
     out = {"workload": BATCH, "signals": n, "samples": int(T.sum()), "P": 7, "K": K, "L": L,
            "updates_per_visit": u, "segment_width": wseg, "autotune": tune, "gen_s": gen_s,
            "gap_target": 1e-4, "E_star": "FP64 oracle per signal (stored)"}
-    grid = (1e-3, 3e-4, 1e-4, 3e-5, 1e-5, 3e-6, 1e-6)
+    grid = (1e-1, 3e-2, 1e-2, 3e-3, 1e-3, 3e-4, 1e-4, 1e-5, 1e-6)
     for name, fn in (("batched", batched), ("plain", plain)):
         fn(grid[0])  # warm-up (module load, allocations)
         res = None
@@ -294,6 +296,37 @@ def batch_leg(args, capi, torch):
                                       out["batched"]["time_to_gap"]["ms"])
     out["speedup_converged"] = (out["plain"]["converged_tol_1e-6_ms"] /
                                 out["batched"]["converged_tol_1e-6_ms"])
+    return out
+
+
+def serve_leg(args, capi, torch):
+    """The request stream (Poisson arrivals at 200 req/s, lengths log-uniform in
+    [5e3, 2e6], four resident dictionaries, 40 GB pool, tol 1e-3, which meets
+    the 1e-4 objective-gap target on the oracle-checked samples) replayed in
+    real time through the serving engine: the first N requests at the offered
+    rate, and the same requests at a tenth of it."""
+    from paper_1705_10087_gb300 import serve, synth
+    name = serve.WORKLOAD
+    w = synth.SERVE_WORKLOADS[name]
+    n = args.serve_requests
+    sch = synth.serve_schedule(name, n, seed=0)
+    sources = synth.serve_sources(name, seed=0, T_source=int(sch["T"].max()),
+                                  workers=min(4, os.cpu_count() or 1))
+    out = {"workload": name, "requests": n, "tol": w["tol"], "lambda": "0.1*lambda_max",
+           "budget_bytes": w["budget_bytes"], "dictionaries_KLP": [list(d) for d in w["dicts"]]}
+    for label, rate in (("offered", w["rate"]), ("tenth", w["rate"] / 10)):
+        r = serve.run_stream(capi, torch, n, seed=0, rate=rate, sources=sources)
+        out[label] = {k: r[k] for k in ("offered_rate_req_s", "offered_samples_s", "wall_s",
+                                         "throughput_req_s", "throughput_samples_s", "p50_ms",
+                                         "p99_ms", "mean_ms", "max_ms", "converged", "steps",
+                                         "gpu_launches", "pool_peak_bytes")}
+        # per dictionary p50 / p99
+        lat = r["latency_ms"]
+        out[label]["per_dictionary"] = {
+            str(j): {"n": int((sch["dict"] == j).sum()),
+                     "p50_ms": float(np.percentile(lat[sch["dict"] == j], 50)),
+                     "p99_ms": float(np.percentile(lat[sch["dict"] == j], 99))}
+            for j in range(len(w["dicts"])) if (sch["dict"] == j).any()}
     return out
 
 
@@ -527,6 +560,8 @@ def main():
         line["segment_sweep"] = sweep
     if world == 1 and not args.no_batch:
         line["batch"] = batch_leg(args, capi, torch)
+    if world == 1 and not args.no_serve:
+        line["serve"] = serve_leg(args, capi, torch)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(pb, lam, args.tol, args.segments,
                                             args.updates_per_visit)

@@ -13,7 +13,9 @@
  *   - Each csc_server_step (a scheduling round) admits queued requests, in
  *     submission order per dictionary, while their device state fits in the
  *     device-memory budget (one pool allocated at creation: the server never
- *     allocates beyond it), runs a fixed number of CD sweeps over ALL active
+ *     allocates beyond it; while other dictionaries have requests waiting, a
+ *     dictionary holds at most its fair share, pool / dictionaries), runs a
+ *     fixed number of CD sweeps over ALL active
  *     requests of each dictionary in the same phase launches (every request
  *     is cut into its own segments, Sec. 2.2; the dictionaries' launches run
  *     on separate streams and overlap on the device), re-synchronises and

@@ -1,10 +1,10 @@
 // Serving engine (include/csc_server.h): resident dictionaries, a device
 // memory pool that bounds admission, and continuous batching of requests.
 //
-// Every dictionary is a group with its own stream.  A scheduling round
-// (csc_server_step) goes through the groups stage by stage, issuing one
-// stage's GPU work for all groups before waiting on any of them, so the
-// groups' kernels overlap on the device:
+// Every dictionary is a group with its own stream and moves through these
+// stages on its own: csc_server_step advances each group whose previous stage
+// has completed (an event query, no waiting), so the groups' kernels overlap
+// on the device and a slow dictionary never holds back a fast one:
 //   1. admission: queued requests (per group, in submission order) get a pool
 //      block while the pool has room; X is copied in, beta0 = D~ * X (the
 //      same dtx kernel as csc_init) with lambda_max, r = beta0, Z = 0;
@@ -184,9 +184,15 @@ __global__ void count_dirty_kernel(const unsigned char *__restrict__ dirty,
     }
 }
 
+// What a group's stream is working on; the group moves to the next stage
+// when the event recorded after that work has completed.
+enum Stage { kIdle, kAdmitting, kSweeping, kResyncing, kFinishing };
+
 struct Group {
     int K = 0, P = 0, L = 0, w = 0, u = 0;
     cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    Stage stage = kIdle;
     float *D = nullptr, *C = nullptr, *Ct = nullptr, *norms = nullptr;
     std::deque<int64_t> queue;    // submission order
     std::vector<int64_t> active;  // admission order; index = problem index of the plan
@@ -197,6 +203,7 @@ struct Group {
     std::vector<int> seg_sig, list;
     int phase_off[3] = {0, 0, 0};
     int M = 0, w_max = 1;
+    size_t held = 0;  // pool bytes of its admitted, not yet fetched requests
     SigDesc *d_sig = nullptr, *d_sub = nullptr;
     int64_t *d_seg_s = nullptr, *d_seg_e = nullptr;
     int *d_seg_sig = nullptr, *d_list = nullptr;
@@ -237,6 +244,7 @@ struct csc_server_s {
     int64_t next_id = 1;
     int64_t launches = 0;
     double t0 = 0.0;
+    cudaStream_t copy_st = nullptr;  // result copies
 };
 
 namespace {
@@ -271,17 +279,28 @@ size_t request_bytes(const Group &g, int64_t T)
 }
 
 // Stage 1 for one group: admit queued requests while the pool has room.
+// Fair share: while another dictionary has requests waiting, a group may hold
+// at most pool / (number of groups), so a dictionary whose requests are slow
+// to converge cannot take the whole pool from the others.
 int admit(csc_server_t s, Group &g, double t)
 {
     g.admitted.clear();
+    bool others_waiting = false;
+    for (const Group &o : s->groups)
+        if (&o != &g && !o.queue.empty())
+            others_waiting = true;
+    const size_t share = s->pool.size / std::max<size_t>(1, s->groups.size());
     while (!g.queue.empty()) {
         if (s->opts.max_active > 0 && (int)g.active.size() >= s->opts.max_active)
             break;
         Request &q = s->reqs[g.queue.front()];
+        if (others_waiting && g.held > 0 && g.held + align_up(q.bytes) > share)
+            break;
         size_t off;
         if (!s->pool.alloc(q.bytes, &off))
             break;  // first come, first served: later requests wait behind it
         q.off = off;
+        g.held += align_up(q.bytes);
         char *b = s->pool.base + off;
         q.hdr = reinterpret_cast<ReqHeader *>(b);
         b += align_up(sizeof(ReqHeader));
@@ -323,7 +342,6 @@ int finish_admit(csc_server_t s, Group &g)
 {
     if (g.admitted.empty())
         return CSC_OK;
-    SRV_CUDA(cudaStreamSynchronize(g.st));
     for (size_t j = 0; j < g.admitted.size(); j++) {
         Request &q = s->reqs[g.admitted[j]];
         std::vector<float>().swap(q.Xh);  // the copy has completed
@@ -462,7 +480,6 @@ int resync_ended(csc_server_t s, Group &g)
     const int n = (int)g.active.size();
     if (n == 0)
         return CSC_OK;
-    SRV_CUDA(cudaStreamSynchronize(g.st));
     g.t_sig.clear();
     g.t_start.clear();
     const int S = s->opts.sweeps_per_step > 0 ? s->opts.sweeps_per_step : 4;
@@ -508,7 +525,6 @@ int objective_finished(csc_server_t s, Group &g)
     g.finished.clear();
     if (g.ended.empty())
         return CSC_OK;
-    SRV_CUDA(cudaStreamSynchronize(g.st));
     const int max_resyncs = s->opts.max_resyncs < 0 ? 3 : s->opts.max_resyncs;
     for (size_t e = 0; e < g.ended.size(); e++) {
         const int i = g.ended[e];
@@ -560,7 +576,6 @@ int retire(csc_server_t s, Group &g, double t, int *n_done)
 {
     if (g.finished.empty())
         return CSC_OK;
-    SRV_CUDA(cudaStreamSynchronize(g.st));
     std::vector<char> gone(g.active.size(), 0);
     for (size_t j = 0; j < g.finished.size(); j++) {
         const int i = g.finished[j];
@@ -592,8 +607,73 @@ void release_group(Group &g)
     cudaFreeHost(g.h_red);
     cudaFreeHost(g.h_E);
     cudaFreeHost(g.h_lmax);
+    if (g.ev)
+        cudaEventDestroy(g.ev);
     if (g.st)
         cudaStreamDestroy(g.st);
+}
+
+// Advances one group through as many stages as have completed, issuing the
+// next stage's work without waiting for it.  Returns CSC_OK; *moved is set
+// when the group changed stage.
+int advance(csc_server_t s, Group &g, int *n_done, bool *moved)
+{
+    for (;;) {
+        if (g.stage != kIdle) {
+            const cudaError_t q = cudaEventQuery(g.ev);
+            if (q == cudaErrorNotReady)
+                return CSC_OK;
+            SRV_CUDA(q);
+            *moved = true;
+        }
+        switch (g.stage) {
+        case kIdle:
+            SRV_TRY(admit(s, g, now_s() - s->t0));
+            if (!g.admitted.empty()) {
+                SRV_CUDA(cudaEventRecord(g.ev, g.st));
+                g.stage = kAdmitting;
+                *moved = true;
+                continue;
+            }
+            if (g.active.empty())
+                return CSC_OK;  // nothing to do
+            *moved = true;
+            SRV_TRY(rebuild(s, g));
+            SRV_TRY(run_sweeps(s, g));
+            SRV_CUDA(cudaEventRecord(g.ev, g.st));
+            g.stage = kSweeping;
+            return CSC_OK;
+        case kAdmitting:
+            SRV_TRY(finish_admit(s, g));
+            SRV_TRY(rebuild(s, g));
+            SRV_TRY(run_sweeps(s, g));
+            SRV_CUDA(cudaEventRecord(g.ev, g.st));
+            g.stage = kSweeping;
+            return CSC_OK;
+        case kSweeping:
+            SRV_TRY(resync_ended(s, g));
+            if (g.ended.empty()) {
+                g.stage = kIdle;
+                continue;
+            }
+            SRV_CUDA(cudaEventRecord(g.ev, g.st));
+            g.stage = kResyncing;
+            continue;
+        case kResyncing:
+            SRV_TRY(objective_finished(s, g));
+            if (g.finished.empty()) {
+                g.stage = kIdle;
+                continue;
+            }
+            SRV_CUDA(cudaEventRecord(g.ev, g.st));
+            g.stage = kFinishing;
+            continue;
+        case kFinishing:
+            SRV_TRY(retire(s, g, now_s() - s->t0, n_done));
+            g.stage = kIdle;
+            continue;
+        }
+    }
 }
 
 }  // namespace
@@ -630,6 +710,12 @@ int csc_server_create(csc_server_t *sp, const csc_server_opts *opts)
                                 (long long)o.hbm_budget_bytes, cudaGetErrorString(e));
     }
     s->pool.init(static_cast<char *>(base), (size_t)o.hbm_budget_bytes);
+    e = cudaStreamCreateWithFlags(&s->copy_st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaFree(base);
+        delete s;
+        return csc_record_error(CSC_ECUDA, "csc_server_create: %s", cudaGetErrorString(e));
+    }
     s->t0 = now_s();
     *sp = s;
     return CSC_OK;
@@ -660,6 +746,7 @@ int csc_server_add_dictionary(csc_server_t s, const float *D, int K, int P, int 
     g.u = updates_per_visit ? updates_per_visit : 24;
     auto body = [&]() -> int {
         SRV_CUDA(cudaStreamCreateWithFlags(&g.st, cudaStreamNonBlocking));
+        SRV_CUDA(cudaEventCreateWithFlags(&g.ev, cudaEventDisableTiming));
         size_t cap = 0;
         SRV_CUDA(grow(&g.D, &cap, (size_t)K * P * L));
         cap = 0;
@@ -732,22 +819,25 @@ int csc_server_step(csc_server_t s, int *n_active, int *n_queued, int *n_done)
         return csc_record_error(CSC_EINVAL, "csc_server_step: null server");
     cudaSetDevice(s->device);
     int done = 0;
-    const double t = now_s() - s->t0;
-    for (Group &g : s->groups)
-        SRV_TRY(admit(s, g, t));
-    for (Group &g : s->groups)
-        SRV_TRY(finish_admit(s, g));
-    for (Group &g : s->groups) {
-        SRV_TRY(rebuild(s, g));
-        SRV_TRY(run_sweeps(s, g));
+    // every group advances on its own: a dictionary whose rounds are slow does
+    // not hold back the others; if no group could move, wait for the first
+    // busy one and try again
+    for (int attempt = 0; attempt < 2; attempt++) {
+        bool moved = false;
+        for (Group &g : s->groups)
+            SRV_TRY(advance(s, g, &done, &moved));
+        if (moved)
+            break;
+        Group *busy = nullptr;
+        for (Group &g : s->groups)
+            if (g.stage != kIdle) {
+                busy = &g;
+                break;
+            }
+        if (!busy)
+            break;
+        SRV_CUDA(cudaEventSynchronize(busy->ev));
     }
-    for (Group &g : s->groups)
-        SRV_TRY(resync_ended(s, g));
-    for (Group &g : s->groups)
-        SRV_TRY(objective_finished(s, g));
-    const double t1 = now_s() - s->t0;
-    for (Group &g : s->groups)
-        SRV_TRY(retire(s, g, t1, &done));
     int na = 0, nq = 0;
     for (const Group &g : s->groups) {
         na += (int)g.active.size();
@@ -802,18 +892,19 @@ int csc_server_fetch(csc_server_t s, int64_t request, float *Z_out, csc_request_
                                 (long long)request);
     cudaSetDevice(s->device);
     const Group &g = s->groups[q.dict];
+    // the request left its group's active set in a completed round, so no
+    // kernel in flight touches its block: copy on the server's own stream,
+    // without waiting for the group's running work
     if (Z_out) {
-        SRV_CUDA(copy_out(Z_out, q.Z, sizeof(float) * g.K * q.Tz, g.st));
-        SRV_CUDA(cudaStreamSynchronize(g.st));
+        SRV_CUDA(copy_out(Z_out, q.Z, sizeof(float) * g.K * q.Tz, s->copy_st));
+        SRV_CUDA(cudaStreamSynchronize(s->copy_st));
     }
     if (info)
         SRV_TRY(csc_server_info(s, request, info));
     if (info)
         info->device_bytes = 0;
-    // nothing of this group that could still read the block is in flight:
-    // the request left the active set in a completed round
-    SRV_CUDA(cudaStreamSynchronize(g.st));
     s->pool.release(q.off, q.bytes);
+    s->groups[q.dict].held -= align_up(q.bytes);
     s->reqs.erase(it);
     return CSC_OK;
 }
@@ -848,6 +939,10 @@ int csc_server_destroy(csc_server_t s)
         if (g.st)
             cudaStreamSynchronize(g.st);
         release_group(g);
+    }
+    if (s->copy_st) {
+        cudaStreamSynchronize(s->copy_st);
+        cudaStreamDestroy(s->copy_st);
     }
     cudaFree(s->pool.base);
     delete s;

@@ -259,7 +259,7 @@ def make_batch(name: str, seed: int = 0, n: int | None = None, T_max: int | None
 SERVE_WORKLOADS = {
     "serve_4dict_poisson200_T5000_2000000": dict(
         rate=200.0, T_min=5_000, T_max=2_000_000, rho=0.005, sigma=0.1, lambda_frac=0.1,
-        tol=1e-4, budget_bytes=40 << 30,
+        tol=1e-3, budget_bytes=40 << 30,
         dicts=((25, 64, 1), (25, 128, 7), (64, 64, 7), (64, 128, 1))),  # (K, L, P)
 }
 
