@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--updates-per-visit", type=int, default=24)
     ap.add_argument("--no-sweep", action="store_true", help="skip the segment-count sweep")
     ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--init-mode", type=int, default=0,
+                    help="beta0 kernel: 0 FP32 compensated, 1 tensor cores (split BF16)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the 512-signal batched-vs-plain comparison")
@@ -408,7 +410,7 @@ def main():
     X = torch.from_numpy(pb.X).cuda()
     Z = torch.zeros((pb.K, pb.Tz), dtype=torch.float32, device="cuda")
     opts = capi.make_opts(segments=args.segments, updates_per_visit=args.updates_per_visit,
-                          time_kernels=1)
+                          time_kernels=1, init_mode=args.init_mode)
     h = capi.csc_setup(D, opts)
     if g is not None:
         lam = g["lambda"]
@@ -536,7 +538,7 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "P": 7, "K": 25, "L": 64, "T": 200_000,
                    "segments": args.segments, "updates_per_visit": args.updates_per_visit,
-                   "phases": sts[-1]["phases"], "tol": args.tol,
+                   "phases": sts[-1]["phases"], "tol": args.tol, "init_mode": args.init_mode,
                    "lambda": "0.1*lambda_max", "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world}, one signal per GPU"},
         "time_to_gap_ms": ttg,

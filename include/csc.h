@@ -78,7 +78,13 @@ typedef struct csc_opts {
                                   the problem is a batch: each signal gets
                                   max(1, floor(Tz_i / width)) segments.  0 = 2L-2, the
                                   narrowest width that needs only 2 phases */
-    int32_t reserved[1];       /* must be zero */
+    int32_t init_mode;         /* beta0 = D~ * X in csc_init: 1 = tensor cores, X and D
+                                  split into three BF16 terms, six products accumulated
+                                  in FP32 (FP32-grade); 2 = tensor cores, one BF16 product
+                                  (only to measure its error); 3 = FP32 CUDA cores with
+                                  compensated sums; 0 = automatic: mode 1 where two of its
+                                  CTAs fit on an SM (shared memory grows with P * L), else
+                                  mode 3.  Modes 1-2 need K <= 64; other sizes use mode 3 */
 } csc_opts;
 
 typedef struct csc_stats {

@@ -59,6 +59,7 @@ struct Scratch {
     unsigned long long red[8];
     double obj[2];
     double x2;  // sum X^2 of the last csc_init
+    int tc_err;  // a bounded wait of the tensor-core beta0 kernel gave up
 };
 
 // Host mirror of what the solve loop polls (pinned).
@@ -352,7 +353,7 @@ int csc_setup(csc_handle_t *hp, const float *D, int K, int P, int L, const csc_o
         o = *opts;
         if (o.segments < 0 || o.updates_per_visit < 0 || o.max_resyncs < -1 ||
             o.sweeps_per_poll < 0 || o.max_sweeps < 0 || o.time_kernels < 0 ||
-            o.time_kernels > 1 || o.segment_width < 0 || o.reserved[0])
+            o.time_kernels > 1 || o.segment_width < 0 || o.init_mode < 0 || o.init_mode > 3)
             return fail(CSC_EINVAL, "csc_setup: invalid options");
     }
     csc_handle_t h = *hp;
@@ -480,8 +481,9 @@ int csc_init_batch(csc_handle_t h, const float *X, const int64_t *T, int n, cons
     CSC_CUDA(copy_in(h->X, X, sizeof(float) * h->P * Ttot, s));
     CSC_CUDA(cudaMemsetAsync(&h->sc->lmax_bits, 0, sizeof(unsigned), s));
     CSC_CUDA(cudaMemsetAsync(&h->sc->x2, 0, sizeof(double), s));
-    CSC_CUDA(launch_dtx(h->D, h->X, h->K, h->P, h->L, Ttot, h->beta0, &h->sc->lmax_bits,
-                        &h->sc->x2, s));
+    CSC_CUDA(cudaMemsetAsync(&h->sc->tc_err, 0, sizeof(int), s));
+    CSC_CUDA(launch_dtx_any(h->D, h->X, h->K, h->P, h->L, Ttot, h->opts.init_mode, h->beta0,
+                            &h->sc->lmax_bits, &h->sc->x2, &h->sc->tc_err, s));
     CSC_CUDA(cudaMemsetAsync(h->d_lmax, 0, sizeof(unsigned) * n, s));
     CSC_CUDA(launch_signal_absmax(h->d_sig, h->obj_tiles(), h->K, h->d_lmax, s));
     h->launches += 2;
@@ -500,9 +502,13 @@ int csc_init_batch(csc_handle_t h, const float *X, const int64_t *T, int n, cons
         CSC_CUDA(cudaMemcpyAsync(h->r, h->beta0, sizeof(float) * nz, cudaMemcpyDeviceToDevice, s));
     }
     std::vector<unsigned> bits(n);
+    int tc_err = 0;
     CSC_CUDA(cudaMemcpyAsync(bits.data(), h->d_lmax, sizeof(unsigned) * n, cudaMemcpyDeviceToHost,
                              s));
+    CSC_CUDA(cudaMemcpyAsync(&tc_err, &h->sc->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     CSC_CUDA(cudaStreamSynchronize(s));
+    if (tc_err)
+        return fail(CSC_ETIMEOUT, "csc_init: the tensor-core beta0 kernel gave up waiting");
     for (int i = 0; i < n; i++) {
         float v;
         std::memcpy(&v, &bits[i], sizeof v);

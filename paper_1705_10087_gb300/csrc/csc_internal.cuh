@@ -192,6 +192,26 @@ struct Tiles {
 constexpr int kResyncCols = 64;  // columns per resync tile
 constexpr int kTile = 256;       // samples per objective tile, columns per absmax tile
 
+// beta0 = D~ * X on the tensor cores (kernel_dtx_tc.cu): mode 1 = three-term
+// BF16 split of X and D with six FP32-accumulated products (FP32-grade),
+// mode 2 = one BF16 product.  Needs K <= 64 and dtx_tc_smem(K,P,L) <= kMaxSmem
+// (cudaErrorNotSupported otherwise).  *err is set when a bounded wait gave up.
+size_t dtx_tc_smem(int K, int P, int L);
+// The beta0 kernel used by default: the tensor cores (mode 1) where at least
+// two CTAs fit on an SM (measured faster: P = 1, L = 200, T = 5e6 in 1.11 ms
+// against 2.06 ms for the FP32 kernel), else the FP32 kernel.
+inline bool dtx_tc_preferred(int K, int P, int L)
+{
+    return K <= 64 && dtx_tc_smem(K, P, L) <= (size_t)kMaxSmem / 2;
+}
+// beta0 with init_mode 0 (automatic), 1 or 2 (tensor cores), 3 (FP32 kernel).
+cudaError_t launch_dtx_any(const float *D, const float *X, int K, int P, int L, int64_t T,
+                           int init_mode, float *beta0, unsigned int *absmax_bits, double *x2sum,
+                           int *err, cudaStream_t s);
+cudaError_t launch_dtx_tc(const float *D, const float *X, int K, int P, int L, int64_t T,
+                          int mode, float *beta0, unsigned int *absmax_bits, double *x2sum,
+                          int *err, cudaStream_t s);
+
 // Re-synchronisation of r with its definition, r = D~*X - sum_{l,t'} S Z
 // (beta0 = D~*X), accumulated in double-float and rounded once to float, and
 // the optimality report over the valid columns of every problem (tiles of

@@ -1,0 +1,406 @@
+// beta0 = D~ * X (Alg. 1 initialisation) on the 5th-generation tensor cores.
+//
+// As a matrix product, beta0^T [Tz x K] = A [Tz x J] B [J x K] with the
+// contraction index j = (p, tau), J = P * L16 (L padded to a multiple of 16),
+// A[t][j] = X[p][t + tau] (a Hankel matrix per channel) and B[j][k] = D[k][p][tau].
+// One CTA computes 128 consecutive t (the MMA's M) for all atoms (N = 32 or
+// 64 >= K) with tcgen05.mma (kind::f16, BF16 operands, FP32 accumulator in
+// tensor memory), one instruction per 16 contraction indices.
+//
+// Precision: every X and D value is split into three BF16 terms,
+// x = x_h + x_m + x_l (each term the BF16 rounding of what the previous ones
+// left, so the split is exact to 2^-24 |x|), and the six products whose
+// magnitude is at least 2^-16 of the leading one (hh, hm, mh, hl, lh, mm) are
+// accumulated in FP32.  The dropped ones (ml, lm, ll) are below 2^-24 of it,
+// so the result has the accuracy of an FP32 computation; with only the hh
+// product (mode 2) it is a plain BF16 product, kept to measure that error.
+//
+// Operand layouts (no swizzle; a core matrix is 8 rows of 16 bytes):
+//   A, MN-major (t contiguous): core matrix (m8, j8) holds rows j = 8 j8 + r,
+//     each row X[p][t0 + 8 (m8 + j8) + r + 0..7].  It depends on m8 + j8 only,
+//     so one run of 16 + L16/8 core matrices per channel and split serves the
+//     whole tile, with equal leading and stride byte offsets (128 B): moving
+//     one core matrix along M or along K is the same step in memory.
+//   B, K-major (j contiguous): per 16-wide contraction step, N/8 x 2 core
+//     matrices, K-adjacent at 128 B, N-adjacent at 256 B; row k of core matrix
+//     (n8, j8) holds D[k = 8 n8 + r][p][tau = 16 s + 8 j8 + 0..7 - p L16].
+// The accumulator lives in tensor memory (N columns of 32-bit, lane = t); each
+// of the 4 warps reads its 32 lanes with tcgen05.ld and writes beta0[k][t]
+// coalesced along t.
+//
+// Waits are bounded: a wait that gives up sets *err and the kernel stops
+// issuing work; tensor memory is always released.
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "csc_internal.cuh"
+
+namespace csc {
+
+namespace {
+
+constexpr int kTcM = 128;        // time rows per tile
+constexpr int kTcThreads = 128;  // 4 warps: one per 32 TMEM lanes
+constexpr int kSplits = 3;
+constexpr unsigned kWaitLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// tcgen05 shared-memory matrix descriptor: start address, leading and stride
+// byte offsets (16-byte units), descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t mma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo & 0x3FFFFu) >> 4) << 16;
+    d |= (uint64_t)((sbo & 0x3FFFFu) >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, A
+// MN-major, B K-major, shape M x N.
+__host__ __device__ constexpr uint32_t mma_idesc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void fence_before_sync()
+{
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after_sync()
+{
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// 32 consecutive 32-bit columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; i++)
+        v[i] = __uint_as_float(r[i]);
+}
+
+// The three BF16 terms of x.
+__device__ __forceinline__ void split3(float x, __nv_bfloat16 &h, __nv_bfloat16 &m,
+                                       __nv_bfloat16 &l)
+{
+    h = __float2bfloat16_rn(x);
+    const float r1 = x - __bfloat162float(h);
+    m = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(m);
+    l = __float2bfloat16_rn(r2);
+}
+
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b)
+{
+    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+struct TcLayout {
+    int L16, NQ, nsteps, xw;
+    size_t a_off, b_off, x_off, bar_off, total;
+    __host__ __device__ TcLayout(int P, int L, int N)
+    {
+        L16 = (L + 15) & ~15;
+        NQ = kTcM / 8 + L16 / 8;
+        nsteps = P * L16 / 16;
+        xw = kTcM + L16 + 8;  // staged samples per channel
+        size_t o = 0;
+        a_off = o;
+        o += (size_t)kSplits * P * NQ * 128;
+        b_off = o;
+        o += (size_t)kSplits * nsteps * (N / 8) * 256;
+        x_off = o;
+        o += (size_t)P * xw * 4;
+        o = (o + 15) & ~(size_t)15;
+        bar_off = o;
+        o += 16;
+        total = o;
+    }
+};
+
+template <int N>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    dtx_tc_kernel(const float *__restrict__ D, const float *__restrict__ X, int K, int P, int L,
+                  long long T, int mode, float *__restrict__ beta0,
+                  unsigned int *__restrict__ absmax_bits, double *__restrict__ x2sum,
+                  int *__restrict__ err)
+{
+    extern __shared__ __align__(128) unsigned char sm[];
+    __shared__ uint32_t s_taddr;
+    const TcLayout lay(P, L, N);
+    unsigned char *As = sm + lay.a_off;
+    unsigned char *Bs = sm + lay.b_off;
+    float *xs = reinterpret_cast<float *>(sm + lay.x_off);
+    const uint32_t bar = smem_u32(sm + lay.bar_off);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long Tz = T - L + 1;
+    const long long ntiles = (Tz + kTcM - 1) / kTcM;
+
+    // ---- tensor memory (N columns) and the MMA-completion barrier ----------
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&s_taddr)),
+                     "r"(N)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // ---- B: the three BF16 terms of D, per contraction step -----------------
+    // element (sigma, s, n8, j8, r, e): D[k = 8 n8 + r][p][tau], j = 16 s + 8 j8 + e
+    const int rows_b = lay.nsteps * (N / 8) * 2 * 8;  // 16-byte rows per split
+    for (int i = tid; i < rows_b; i += kTcThreads) {
+        const int r = i & 7, j8 = (i >> 3) & 1, n8 = (i >> 4) % (N / 8), s = (i >> 4) / (N / 8);
+        const int k = 8 * n8 + r;
+        uint32_t w[kSplits][4];
+#pragma unroll
+        for (int e2 = 0; e2 < 4; e2++) {
+            __nv_bfloat16 h[2], m[2], l[2];
+#pragma unroll
+            for (int q = 0; q < 2; q++) {
+                const int j = 16 * s + 8 * j8 + 2 * e2 + q;
+                const int p = j / lay.L16, tau = j % lay.L16;
+                const float v = (k < K && tau < L) ? D[((long long)k * P + p) * L + tau] : 0.f;
+                split3(v, h[q], m[q], l[q]);
+            }
+            w[0][e2] = pack2(h[0], h[1]);
+            w[1][e2] = pack2(m[0], m[1]);
+            w[2][e2] = pack2(l[0], l[1]);
+        }
+        const size_t off = (((size_t)s * (N / 8) + n8) * 2 + j8) * 128 + (size_t)r * 16;
+#pragma unroll
+        for (int sg = 0; sg < kSplits; sg++)
+            *reinterpret_cast<uint4 *>(Bs + (size_t)sg * lay.nsteps * (N / 8) * 256 + off) =
+                make_uint4(w[sg][0], w[sg][1], w[sg][2], w[sg][3]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t taddr = s_taddr;
+    const uint32_t idesc = mma_idesc(kTcM, N);
+    const uint32_t a_base = smem_u32(As), b_base = smem_u32(Bs);
+
+    float amax = 0.f;
+    double x2 = 0.0;
+    uint32_t phase = 0;
+    bool ok = true;
+    for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const long long t0 = tile * kTcM;
+        const bool last = tile == ntiles - 1;
+        // ---- stage X[p][t0 .. t0 + xw) (0 beyond T) and sum X^2 over own samples
+        for (int i = tid; i < P * lay.xw; i += kTcThreads) {
+            const int p = i / lay.xw, jx = i % lay.xw;
+            const long long t = t0 + jx;
+            const float v = t < T ? X[(long long)p * T + t] : 0.f;
+            xs[i] = v;
+            if (t < T && (jx < kTcM || (last && jx < kTcM + L)))
+                x2 += (double)v * (double)v;
+        }
+        __syncthreads();
+        // ---- A: row (sigma, p, q, r) = split sigma of X[p][t0 + 8 q + r + 0..7]
+        const int rows_a = P * lay.NQ * 8;
+        for (int i = tid; i < rows_a; i += kTcThreads) {
+            const int r = i & 7, q = (i >> 3) % lay.NQ, p = (i >> 3) / lay.NQ;
+            const float *src = xs + (size_t)p * lay.xw + 8 * q + r;
+            uint32_t w[kSplits][4];
+#pragma unroll
+            for (int e2 = 0; e2 < 4; e2++) {
+                __nv_bfloat16 h[2], m[2], l[2];
+                split3(src[2 * e2], h[0], m[0], l[0]);
+                split3(src[2 * e2 + 1], h[1], m[1], l[1]);
+                w[0][e2] = pack2(h[0], h[1]);
+                w[1][e2] = pack2(m[0], m[1]);
+                w[2][e2] = pack2(l[0], l[1]);
+            }
+            const size_t off = ((size_t)p * lay.NQ + q) * 128 + (size_t)r * 16;
+#pragma unroll
+            for (int sg = 0; sg < kSplits; sg++)
+                *reinterpret_cast<uint4 *>(As + (size_t)sg * P * lay.NQ * 128 + off) =
+                    make_uint4(w[sg][0], w[sg][1], w[sg][2], w[sg][3]);
+        }
+        // make the generic-proxy stores visible to the tensor cores
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        fence_before_sync();
+        __syncthreads();
+        fence_after_sync();
+        if (tid == 0) {
+            // products hh, hm, mh, hl, lh, mm (mode 2: hh only)
+            const int pa[6] = {0, 0, 1, 0, 2, 1}, pb[6] = {0, 1, 0, 2, 0, 1};
+            const int nprod = mode == 2 ? 1 : 6;
+            uint32_t acc = 0;
+            for (int s = 0; s < lay.nsteps; s++) {
+                const int p = (16 * s) / lay.L16, q0 = ((16 * s) % lay.L16) / 8;
+                for (int u = nprod - 1; u >= 0; u--) {  // small terms first
+                    const uint32_t aa = a_base + (uint32_t)((((size_t)pa[u] * P + p) * lay.NQ + q0) * 128);
+                    const uint32_t ba = b_base + (uint32_t)(((size_t)pb[u] * lay.nsteps + s) * (N / 8) * 256);
+                    mma_bf16(taddr, mma_desc(aa, 128, 128), mma_desc(ba, 128, 256), idesc, acc);
+                    acc = 1;
+                }
+            }
+            mma_commit(bar);
+        }
+        // ---- wait for the products (bounded), then read the accumulator ----
+        unsigned n = 0;
+        while (!mbar_try_wait(bar, phase))
+            if (++n >= kWaitLimit) {
+                ok = false;
+                break;
+            }
+        phase ^= 1u;
+        if (!ok) {
+            if (tid == 0)
+                atomicExch(err, 1);
+            break;
+        }
+        fence_after_sync();
+        const long long t = t0 + 32 * warp + lane;
+        const uint32_t lane_addr = taddr + ((uint32_t)(32 * warp) << 16);
+#pragma unroll
+        for (int c = 0; c < N; c += 32) {
+            float v[32];
+            tmem_ld32(lane_addr + (uint32_t)c, v);
+            if (t < Tz) {
+#pragma unroll
+                for (int i = 0; i < 32; i++) {
+                    const int k = c + i;
+                    if (k < K) {
+                        beta0[(long long)k * Tz + t] = v[i];
+                        amax = fmaxf(amax, fabsf(v[i]));
+                    }
+                }
+            }
+        }
+        // all lanes read before the next tile's products overwrite the accumulator
+        fence_before_sync();
+        __syncthreads();
+        fence_after_sync();
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+        x2 += __shfl_xor_sync(0xffffffffu, x2, off);
+    }
+    if (lane == 0) {
+        atomicMax(absmax_bits, __float_as_uint(amax));
+        atomicAdd(x2sum, x2);
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(N)
+                     : "memory");
+}
+
+}  // namespace
+
+size_t dtx_tc_smem(int K, int P, int L)
+{
+    const int N = K <= 32 ? 32 : 64;
+    return TcLayout(P, L, N).total;
+}
+
+cudaError_t launch_dtx_tc(const float *D, const float *X, int K, int P, int L, int64_t T,
+                          int mode, float *beta0, unsigned int *absmax_bits, double *x2sum,
+                          int *err, cudaStream_t s)
+{
+    if (K > 64)
+        return cudaErrorNotSupported;
+    const size_t smem = dtx_tc_smem(K, P, L);
+    if (smem > (size_t)kMaxSmem)
+        return cudaErrorNotSupported;
+    const int64_t Tz = T - L + 1;
+    const int64_t ntiles = (Tz + kTcM - 1) / kTcM;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    auto go = [&](auto kern) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (e != cudaSuccess)
+            return e;
+        // four CTAs per SM where they fit (their latencies overlap; more wait
+        // for a slot): at N <= 64 tensor-memory columns each, the CTAs resident
+        // on an SM never ask for more than its 512 columns unless eight or more
+        // of them fit, and then N = 32 (K <= 32) keeps them at 512
+        const int64_t cap = (int64_t)nsm * 4;
+        const unsigned grid = (unsigned)(ntiles < cap ? ntiles : cap);
+        kern<<<grid, kTcThreads, smem, s>>>(D, X, K, P, L, (long long)T, mode, beta0, absmax_bits,
+                                           x2sum, err);
+        return cudaGetLastError();
+    };
+    return K <= 32 ? go(dtx_tc_kernel<32>) : go(dtx_tc_kernel<64>);
+}
+
+cudaError_t launch_dtx_any(const float *D, const float *X, int K, int P, int L, int64_t T,
+                           int init_mode, float *beta0, unsigned int *absmax_bits, double *x2sum,
+                           int *err, cudaStream_t s)
+{
+    int mode = init_mode;
+    if (mode == 0)
+        mode = dtx_tc_preferred(K, P, L) ? 1 : 3;
+    if (mode == 1 || mode == 2) {
+        const cudaError_t e =
+            launch_dtx_tc(D, X, K, P, L, T, mode, beta0, absmax_bits, x2sum, err, s);
+        if (e != cudaErrorNotSupported)
+            return e;
+        cudaGetLastError();
+    }
+    return launch_dtx(D, X, K, P, L, T, beta0, absmax_bits, x2sum, s);
+}
+
+}  // namespace csc

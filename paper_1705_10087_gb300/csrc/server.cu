@@ -125,7 +125,7 @@ private:
 // First bytes of a request's pool block.
 struct ReqHeader {
     unsigned int lmax_bits;
-    unsigned int pad;
+    int tc_err;  // the tensor-core beta0 kernel gave up waiting
     double x2;
 };
 
@@ -266,7 +266,7 @@ int host_buffers(Group &g, size_t n)
     SRV_CUDA(cudaHostAlloc(&g.h_cnt, sizeof(int) * m, cudaHostAllocDefault));
     SRV_CUDA(cudaHostAlloc(&g.h_red, sizeof(unsigned long long) * kRed * m, cudaHostAllocDefault));
     SRV_CUDA(cudaHostAlloc(&g.h_E, sizeof(double) * m, cudaHostAllocDefault));
-    SRV_CUDA(cudaHostAlloc(&g.h_lmax, sizeof(unsigned int) * m, cudaHostAllocDefault));
+    SRV_CUDA(cudaHostAlloc(&g.h_lmax, 2 * sizeof(unsigned int) * m, cudaHostAllocDefault));
     g.cap_h = m;
     return CSC_OK;
 }
@@ -315,8 +315,8 @@ int admit(csc_server_t s, Group &g, double t)
         SRV_CUDA(cudaMemcpyAsync(q.X, q.Xh.data(), sizeof(float) * g.P * q.T,
                                  cudaMemcpyHostToDevice, g.st));
         SRV_CUDA(cudaMemsetAsync(q.hdr, 0, sizeof(ReqHeader), g.st));
-        SRV_CUDA(launch_dtx(g.D, q.X, g.K, g.P, g.L, q.T, q.beta0, &q.hdr->lmax_bits, &q.hdr->x2,
-                            g.st));
+        SRV_CUDA(launch_dtx_any(g.D, q.X, g.K, g.P, g.L, q.T, 0, q.beta0, &q.hdr->lmax_bits,
+                                &q.hdr->x2, &q.hdr->tc_err, g.st));
         s->launches += 1;
         SRV_CUDA(cudaMemcpyAsync(q.r, q.beta0, nz, cudaMemcpyDeviceToDevice, g.st));
         SRV_CUDA(cudaMemsetAsync(q.Z, 0, nz, g.st));
@@ -332,7 +332,7 @@ int admit(csc_server_t s, Group &g, double t)
     SRV_TRY(host_buffers(g, g.admitted.size()));
     for (size_t j = 0; j < g.admitted.size(); j++) {
         Request &q = s->reqs[g.admitted[j]];
-        SRV_CUDA(cudaMemcpyAsync(&g.h_lmax[j], &q.hdr->lmax_bits, sizeof(unsigned int),
+        SRV_CUDA(cudaMemcpyAsync(&g.h_lmax[2 * j], &q.hdr->lmax_bits, 2 * sizeof(unsigned int),
                                  cudaMemcpyDeviceToHost, g.st));
     }
     return CSC_OK;
@@ -345,8 +345,11 @@ int finish_admit(csc_server_t s, Group &g)
     for (size_t j = 0; j < g.admitted.size(); j++) {
         Request &q = s->reqs[g.admitted[j]];
         std::vector<float>().swap(q.Xh);  // the copy has completed
+        if (g.h_lmax[2 * j + 1])
+            return csc_record_error(CSC_ETIMEOUT,
+                                    "csc_server_step: the tensor-core beta0 kernel gave up waiting");
         float v;
-        std::memcpy(&v, &g.h_lmax[j], sizeof v);
+        std::memcpy(&v, &g.h_lmax[2 * j], sizeof v);
         q.lmax = v;
         q.lam = q.lam_spec > 0.0 ? q.lam_spec : -q.lam_spec * q.lmax;
         if (!(q.lam > 0.0))

@@ -125,8 +125,10 @@ def test_dtd_and_norms_elementwise(capi):
 @pytest.mark.parametrize("K,P,L,T", [(5, 1, 16, 2000), (25, 7, 64, 20_000), (3, 2, 5, 5),
                                      (25, 1, 200, 3001), (1, 1, 1, 700)])
 def test_dtx_elementwise(capi, K, P, L, T):
+    # the FP32 CUDA-core kernel (init_mode 3); the tensor-core kernel has its own
+    # bound in tests/test_gpu_dtx_tc.py
     pb = synth.make_problem(K=K, P=P, L=L, T=T, rho=0.01, sigma=0.1, seed=2)
-    h = capi.csc_setup(cuda(pb.D))
+    h = capi.csc_setup(cuda(pb.D), capi.make_opts(init_mode=3))
     capi.csc_init(h, cuda(pb.X), 1.0)
     beta = torch.zeros((K, pb.Tz), dtype=torch.float32, device="cuda")
     capi.csc_get_beta(h, beta)
