@@ -1,7 +1,8 @@
 """Command line: solve one synthetic workload on the GPU through the C ABI.
 
     python -m paper_1705_10087_gb300.cli --workload long_P7_K25_L64_T200000 \
-        --segments 1024 --updates-per-visit 24 [--seed 0] [--tol 1e-6] [--repeat 1]
+        --segments 1024 --updates-per-visit 24 [--seed 0] [--tol 1e-6] [--repeat 1] \
+        [--init-mode 0]
 
 Prints one JSON line per solve with the solver statistics.  Inputs come from
 paper_1705_10087_gb300.synth; lambda = 0.1 * lambda_max as computed by the
@@ -23,6 +24,7 @@ def main(argv=None) -> None:
     ap.add_argument("--updates-per-visit", type=int, default=0)
     ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--init-mode", type=int, default=0)
     a = ap.parse_args(argv)
 
     import torch
@@ -35,13 +37,13 @@ def main(argv=None) -> None:
     D = torch.from_numpy(pb.D).cuda()
     X = torch.from_numpy(pb.X).cuda()
     Z = torch.zeros((pb.K, pb.Tz), dtype=torch.float32, device="cuda")
-    h = capi.csc_setup(D, capi.make_opts(segments=a.segments,
+    h = capi.csc_setup(D, capi.make_opts(segments=a.segments, init_mode=a.init_mode,
                                          updates_per_visit=a.updates_per_visit))
     try:
         capi.csc_init(h, X, 1.0)
         lam = 0.1 * capi.csc_lambda_max(h)
         for _ in range(a.repeat):
-            capi.csc_setup(D, capi.make_opts(segments=a.segments,
+            capi.csc_setup(D, capi.make_opts(segments=a.segments, init_mode=a.init_mode,
                                              updates_per_visit=a.updates_per_visit), handle=h)
             capi.csc_init(h, X, lam)
             status, E, st = capi.csc_solve(h, tol, 1 << 40, Z)
