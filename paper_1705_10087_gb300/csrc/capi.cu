@@ -60,6 +60,7 @@ struct Scratch {
     double obj[2];
     double x2;  // sum X^2 of the last csc_init
     int tc_err;  // a bounded wait of the tensor-core beta0 kernel gave up
+    int qhead[2];  // drain launches: next queue entry, queue length
 };
 
 // Host mirror of what the solve loop polls (pinned).
@@ -157,6 +158,8 @@ struct csc_handle_s {
     size_t cap_seg_s = 0, cap_seg_e = 0, cap_seg_sig = 0, cap_phase = 0;
     unsigned char *dirty = nullptr, *touched = nullptr;
     size_t cap_dirty = 0, cap_touched = 0;
+    int *d_queue = nullptr;  // drain launches: the phase's segments to visit
+    size_t cap_queue = 0;
     float *tile_rep = nullptr;  // stored resync report per resync tile
     size_t cap_tile_rep = 0;
 
@@ -233,6 +236,12 @@ int build_plan(csc_handle_t h)
     CSC_CUDA(upload(&h->d_phase_list, &h->cap_phase, list, s));
     CSC_CUDA(grow(&h->dirty, &h->cap_dirty, (size_t)M));
     CSC_CUDA(grow(&h->touched, &h->cap_touched, (size_t)M));
+    {
+        int most = 0;
+        for (int p = 0; p < c; p++)
+            most = std::max(most, off[p + 1] - off[p]);
+        CSC_CUDA(grow(&h->d_queue, &h->cap_queue, (size_t)most));
+    }
     CSC_CUDA(grow(&h->tile_rep, &h->cap_tile_rep, 5 * (size_t)h->nrtiles));
     // the host vectors must outlive the asynchronous copies
     CSC_CUDA(cudaStreamSynchronize(s));
@@ -323,7 +332,7 @@ int csc_destroy(csc_handle_t h)
                     h->tmpZ,       h->tmpB,       h->sc,         h->d_sig,      h->d_tile_s,
                     h->d_tile_off, h->d_tile_sig, h->d_rtile_s,  h->d_rtile_sig, h->d_E,
                     h->d_lmax,     h->d_seg_s,    h->d_seg_e,    h->d_seg_sig,  h->d_phase_list,
-                    h->touched,    h->tile_rep};
+                    h->touched,    h->tile_rep,   h->d_queue};
     for (void *p : bufs)
         cudaFree(p);
     if (h->poll)
@@ -628,6 +637,12 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
     pp.norms = h->norms;
     pp.dirty = h->dirty;
     pp.touched = h->touched;
+    pp.qhead = sc->qhead;
+    pp.qlen = sc->qhead + 1;
+    pp.queue = h->d_queue;
+    // phases with many more segments than resident blocks are drained from a
+    // queue of the segments that need a visit by persistent blocks
+    const int resident = phase_resident_blocks(cfg, h->K);
     pp.seg_s = h->d_seg_s;
     pp.seg_e = h->d_seg_e;
     pp.sig = h->d_sig;
@@ -679,7 +694,13 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
                     pp.phase_list = h->d_phase_list + h->phase_off[p];
                     if (timed)
                         CSC_CUDA(cudaEventRecord(h->kev[2 * nb], s));
-                    CSC_CUDA(launch_phase(pp, cfg, h->phase_off[p + 1] - h->phase_off[p], s));
+                    const int cnt = h->phase_off[p + 1] - h->phase_off[p];
+                    if (cnt > 4 * resident) {
+                        CSC_CUDA(launch_phase_drain(pp, cfg, cnt, resident, s));
+                        h->launches += 1;  // the compaction (the drain counts below)
+                    } else {
+                        CSC_CUDA(launch_phase(pp, cfg, cnt, s));
+                    }
                     if (timed)
                         CSC_CUDA(cudaEventRecord(h->kev[2 * nb + 1], s));
                     nb++;

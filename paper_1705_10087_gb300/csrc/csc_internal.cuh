@@ -156,6 +156,11 @@ struct PhaseParams {
     int g_round;  // first launch index of the current CD round
     int u;        // cap on updates per visit
     int w_max;  // widest segment (shared-memory layout)
+    // queue of the phase's segments that need a visit (drain launches):
+    // qhead[0] = next entry to take, qhead[1] = queue length
+    int *qhead;
+    const int *qlen;
+    int *queue;
 };
 
 struct PhaseConfig {
@@ -169,6 +174,14 @@ PhaseConfig phase_config(int K, int L, int w_max);
 // active = number of segments in pp.phase_list (the grid size).
 cudaError_t launch_phase(const PhaseParams &pp, const PhaseConfig &cfg, int active,
                          cudaStream_t s);
+// Blocks of the phase kernel that are resident at once on the whole GPU.
+int phase_resident_blocks(const PhaseConfig &cfg, int K);
+// The same phase as launch_phase, for phase lists much longer than the
+// resident blocks: the segments of pp.phase_list[0..active) that need a visit
+// are compacted into pp.queue and min(resident, active) persistent blocks
+// drain it (three stream operations: reset, compaction, drain).
+cudaError_t launch_phase_drain(const PhaseParams &pp, const PhaseConfig &cfg, int active,
+                               int resident, cudaStream_t s);
 
 cudaError_t launch_dtd(const float *D, int K, int P, int L, float *C, float *norms,
                        cudaStream_t s);

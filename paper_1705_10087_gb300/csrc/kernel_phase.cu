@@ -100,14 +100,12 @@ struct Layout {
     __host__ __device__ static size_t up(size_t x) { return (x + 15) & ~(size_t)15; }
 };
 
-// MAXT: the block size the instantiation is launched with.  Blocks of 128
-// threads (atoms up to 64 samples) are compiled for 5 resident blocks per SM,
-// so that the several hundred co-active segments of a phase fit in one wave;
-// larger blocks get the full register file.  KT > 0 fixes K at compile time
-// (loops over atoms unroll, tile offsets become immediates); KT = 0 reads K
-// from the parameters.
+// KT > 0 fixes K at compile time (loops over atoms unroll, tile offsets
+// become immediates); KT = 0 reads K from the parameters.
+// One visit of segment m by the whole block (uniform control flow: every
+// early exit is decided by thread 0 and broadcast).
 template <bool SMEM, int MAXT, int KT>
-__global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseParams pp)
+__device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m)
 {
     using Idx = typename std::conditional<SMEM, int, int64_t>::type;
     constexpr bool KFIX = KT > 0;
@@ -118,7 +116,6 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseP
 
     // ---- early exits, decided by one thread so the block stays uniform ----
     // (total is being incremented by other blocks of this launch)
-    const int m = pp.phase_list[blockIdx.x];  // a segment of this phase
     if (threadIdx.x == 0) {
         int go = 1;
         if (*(volatile int *)pp.done) {
@@ -131,8 +128,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseP
             for (int j = pp.g - pp.c; j < pp.g; j++)
                 sum += *(volatile long long *)&pp.upd[j & (kPhaseRing - 1)];
             if (sum == 0) {
-                if (blockIdx.x == 0)
-                    *(volatile int *)pp.done = pp.g + 1;
+                *(volatile int *)pp.done = pp.g + 1;  // same value from every block
                 go = 0;
             }
         }
@@ -461,6 +457,73 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseP
     }
 }
 
+// MAXT: the block size the instantiation is launched with.  Blocks of 128
+// threads (atoms up to 64 samples) are compiled for 5 resident blocks per SM,
+// so that the several hundred co-active segments of a phase fit in one wave;
+// larger blocks get the full register file.
+// One block per segment of the phase list.
+template <bool SMEM, int MAXT, int KT>
+__global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseParams pp)
+{
+    visit_segment<SMEM, MAXT, KT>(pp, pp.phase_list[blockIdx.x]);
+}
+
+// Persistent form: a grid of resident blocks drains the queue of this phase's
+// segments that need a visit (built by compact_phase_kernel), so a phase with
+// few dirty segments among very many costs its work, not a block per segment.
+template <bool SMEM, int MAXT, int KT>
+__global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_drain_kernel(PhaseParams pp)
+{
+    __shared__ int s_idx;
+    const int n = *pp.qlen;
+    // an empty queue visits nothing, so the test for a full sweep without
+    // updates (made at the start of every visit) is also made here once
+    if (blockIdx.x == 0 && threadIdx.x == 0 && pp.g - pp.g_round >= pp.c &&
+        !*(volatile int *)pp.done) {
+        long long sum = 0;
+        for (int j = pp.g - pp.c; j < pp.g; j++)
+            sum += *(volatile long long *)&pp.upd[j & (kPhaseRing - 1)];
+        if (sum == 0)
+            *(volatile int *)pp.done = pp.g + 1;
+    }
+    for (;;) {
+        if (threadIdx.x == 0)
+            s_idx = atomicAdd(pp.qhead, 1);
+        __syncthreads();
+        const int idx = s_idx;
+        __syncthreads();  // every thread has read s_idx before it is overwritten
+        if (idx >= n)
+            break;
+        visit_segment<SMEM, MAXT, KT>(pp, pp.queue[idx]);
+        __syncthreads();  // the next visit re-uses the shared memory
+    }
+}
+
+// The segments of a phase list that need a visit, in any order (co-active
+// segments are independent, so the order of their visits changes nothing).
+__global__ void compact_phase_kernel(const int *__restrict__ list, int count,
+                                     const unsigned char *__restrict__ dirty,
+                                     int *__restrict__ queue, int *__restrict__ qlen)
+{
+    const int lane = threadIdx.x & 31;
+    for (int i0 = blockIdx.x * blockDim.x; i0 < count; i0 += gridDim.x * blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        int m = 0;
+        bool want = false;
+        if (i < count) {
+            m = list[i];
+            want = dirty[m] != 0;
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, want);
+        int base = 0;
+        if (lane == 0 && mask)
+            base = atomicAdd(qlen, __popc(mask));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (want)
+            queue[base + __popc(mask & ((1u << lane) - 1u))] = m;
+    }
+}
+
 }  // namespace
 
 PhaseConfig phase_config(int K, int L, int wmax)
@@ -476,38 +539,108 @@ PhaseConfig phase_config(int K, int L, int wmax)
     return cfg;
 }
 
+namespace {
+
+// Calls f with the phase-kernel instantiation (template) matching cfg and K.
+template <template <bool, int, int> class Sel, class F>
+cudaError_t dispatch(const PhaseConfig &cfg, int K, F &&f)
+{
+    const bool k25 = K == 25;  // the workloads' atom count: compiled with K fixed
+    if (cfg.block == 128) {
+        if (k25)
+            return cfg.tile_in_smem ? f(Sel<true, 128, 25>::fn()) : f(Sel<false, 128, 25>::fn());
+        return cfg.tile_in_smem ? f(Sel<true, 128, 0>::fn()) : f(Sel<false, 128, 0>::fn());
+    }
+    if (cfg.block == 512) {
+        if (k25)
+            return cfg.tile_in_smem ? f(Sel<true, 512, 25>::fn()) : f(Sel<false, 512, 25>::fn());
+        return cfg.tile_in_smem ? f(Sel<true, 512, 0>::fn()) : f(Sel<false, 512, 0>::fn());
+    }
+    return cfg.tile_in_smem ? f(Sel<true, 1024, 0>::fn()) : f(Sel<false, 1024, 0>::fn());
+}
+
+template <bool A, int B, int C>
+struct PerSegment {
+    static auto fn() { return phase_kernel<A, B, C>; }
+};
+template <bool A, int B, int C>
+struct Drain {
+    static auto fn() { return phase_drain_kernel<A, B, C>; }
+};
+
+cudaError_t check(const PhaseParams &pp, const PhaseConfig &cfg)
+{
+    if (cfg.smem > (size_t)kMaxSmem)
+        return cudaErrorInvalidConfiguration;
+    if (cfg.block < 2 * pp.L - 1)
+        return cudaErrorInvalidConfiguration;  // each window column needs its own thread
+    return cudaSuccess;
+}
+
+}  // namespace
+
 cudaError_t launch_phase(const PhaseParams &pp, const PhaseConfig &cfg, int active,
                          cudaStream_t s)
 {
     if (active == 0)
         return cudaSuccess;
-    if (cfg.smem > (size_t)kMaxSmem)
-        return cudaErrorInvalidConfiguration;
-    if (cfg.block < 2 * pp.L - 1)
-        return cudaErrorInvalidConfiguration;  // each window column needs its own thread
-    auto go = [&](auto kern) -> cudaError_t {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = check(pp, cfg);
+    if (e != cudaSuccess)
+        return e;
+    e = dispatch<PerSegment>(cfg, pp.K, [&](auto kern) -> cudaError_t {
+        cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)cfg.smem);
-        if (e != cudaSuccess)
-            return e;
+        if (r != cudaSuccess)
+            return r;
         kern<<<active, cfg.block, cfg.smem, s>>>(pp);
         return cudaSuccess;
-    };
-    cudaError_t e;
-    const bool k25 = pp.K == 25;  // the workloads' atom count: compiled with K fixed
-    if (cfg.block == 128) {
-        if (k25)
-            e = cfg.tile_in_smem ? go(phase_kernel<true, 128, 25>) : go(phase_kernel<false, 128, 25>);
-        else
-            e = cfg.tile_in_smem ? go(phase_kernel<true, 128, 0>) : go(phase_kernel<false, 128, 0>);
-    } else if (cfg.block == 512) {
-        if (k25)
-            e = cfg.tile_in_smem ? go(phase_kernel<true, 512, 25>) : go(phase_kernel<false, 512, 25>);
-        else
-            e = cfg.tile_in_smem ? go(phase_kernel<true, 512, 0>) : go(phase_kernel<false, 512, 0>);
-    } else {
-        e = cfg.tile_in_smem ? go(phase_kernel<true, 1024, 0>) : go(phase_kernel<false, 1024, 0>);
-    }
+    });
+    if (e != cudaSuccess)
+        return e;
+    return cudaGetLastError();
+}
+
+int phase_resident_blocks(const PhaseConfig &cfg, int K)
+{
+    int per_sm = 1, dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    dispatch<Drain>(cfg, K, [&](auto kern) -> cudaError_t {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, cfg.block, cfg.smem);
+        return cudaSuccess;
+    });
+    cudaGetLastError();
+    return nsm * (per_sm < 1 ? 1 : per_sm);
+}
+
+cudaError_t launch_phase_drain(const PhaseParams &pp, const PhaseConfig &cfg, int active,
+                               int resident, cudaStream_t s)
+{
+    if (active == 0)
+        return cudaSuccess;
+    cudaError_t e = check(pp, cfg);
+    if (e != cudaSuccess)
+        return e;
+    // queue length and head (two adjacent ints) start at 0
+    e = cudaMemsetAsync(pp.qhead, 0, 2 * sizeof(int), s);
+    if (e != cudaSuccess)
+        return e;
+    const int cb = 256;
+    const int cg = (active + cb - 1) / cb < 4096 ? (active + cb - 1) / cb : 4096;
+    compact_phase_kernel<<<cg, cb, 0, s>>>(pp.phase_list, active, pp.dirty, pp.queue, pp.qhead + 1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    const int grid = resident < active ? resident : active;
+    e = dispatch<Drain>(cfg, pp.K, [&](auto kern) -> cudaError_t {
+        cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)cfg.smem);
+        if (r != cudaSuccess)
+            return r;
+        kern<<<grid, cfg.block, cfg.smem, s>>>(pp);
+        return cudaSuccess;
+    });
     if (e != cudaSuccess)
         return e;
     return cudaGetLastError();

@@ -159,7 +159,7 @@ struct PhaseScratch {
     long long total;
     long long visits;
     int done;
-    int pad;
+    int qhead[2];  // drain launches: next queue entry, queue length
 };
 
 // Number of segments of problem i that still need a visit.
@@ -206,7 +206,7 @@ struct Group {
     size_t held = 0;  // pool bytes of its admitted, not yet fetched requests
     SigDesc *d_sig = nullptr, *d_sub = nullptr;
     int64_t *d_seg_s = nullptr, *d_seg_e = nullptr;
-    int *d_seg_sig = nullptr, *d_list = nullptr;
+    int *d_seg_sig = nullptr, *d_list = nullptr, *d_queue = nullptr;
     unsigned char *dirty = nullptr, *touched = nullptr;
     int *d_cnt = nullptr;
     unsigned long long *d_red = nullptr;
@@ -215,7 +215,7 @@ struct Group {
     int64_t *d_tstart = nullptr, *d_toff = nullptr;
     size_t cap_sig = 0, cap_sub = 0, cap_seg_s = 0, cap_seg_e = 0, cap_seg_sig = 0, cap_list = 0,
            cap_dirty = 0, cap_touched = 0, cap_cnt = 0, cap_red = 0, cap_E = 0, cap_partials = 0,
-           cap_tsig = 0, cap_tstart = 0, cap_toff = 0;
+           cap_tsig = 0, cap_tstart = 0, cap_toff = 0, cap_queue = 0;
     PhaseScratch *ps = nullptr;
     // pinned host mirrors
     int *h_cnt = nullptr;
@@ -415,6 +415,8 @@ int rebuild(csc_server_t s, Group &g)
     SRV_CUDA(upload(&g.d_list, &g.cap_list, g.list, g.st));
     SRV_CUDA(grow(&g.dirty, &g.cap_dirty, (size_t)g.M));
     SRV_CUDA(grow(&g.touched, &g.cap_touched, (size_t)g.M));
+    SRV_CUDA(grow(&g.d_queue, &g.cap_queue,
+                  (size_t)std::max(g.phase_off[1] - g.phase_off[0], g.phase_off[2] - g.phase_off[1])));
     SRV_CUDA(grow(&g.d_cnt, &g.cap_cnt, (size_t)n));
     SRV_CUDA(grow(&g.d_red, &g.cap_red, (size_t)n * kRed));
     SRV_CUDA(grow(&g.d_E, &g.cap_E, (size_t)n));
@@ -459,14 +461,24 @@ int run_sweeps(csc_server_t s, Group &g)
     pp.u = g.u;
     pp.w_max = g.w_max;
     pp.g_round = 0;
+    pp.qhead = g.ps->qhead;
+    pp.qlen = g.ps->qhead + 1;
+    pp.queue = g.d_queue;
+    const int resident = phase_resident_blocks(cfg, g.K);
     int gi = 0;
     for (int i = 0; i < S; i++)
         for (int p = 0; p < c; p++) {
             pp.p = p;
             pp.g = gi++;
             pp.phase_list = g.d_list + g.phase_off[p];
-            SRV_CUDA(launch_phase(pp, cfg, g.phase_off[p + 1] - g.phase_off[p], g.st));
-            s->launches += 1;
+            const int cnt = g.phase_off[p + 1] - g.phase_off[p];
+            if (cnt > 4 * resident) {
+                SRV_CUDA(launch_phase_drain(pp, cfg, cnt, resident, g.st));
+                s->launches += 2;
+            } else {
+                SRV_CUDA(launch_phase(pp, cfg, cnt, g.st));
+                s->launches += 1;
+            }
         }
     count_dirty_kernel<<<n, 256, 0, g.st>>>(g.dirty, g.d_sig, g.d_cnt);
     SRV_CUDA(cudaGetLastError());
@@ -603,7 +615,7 @@ void release_group(Group &g)
     void *bufs[] = {g.D,       g.C,       g.Ct,       g.norms,   g.d_sig,    g.d_sub,
                     g.d_seg_s, g.d_seg_e, g.d_seg_sig, g.d_list, g.dirty,    g.touched,
                     g.d_cnt,   g.d_red,   g.d_E,      g.d_partials, g.d_tsig, g.d_tstart,
-                    g.d_toff,  g.ps};
+                    g.d_toff,  g.ps,      g.d_queue};
     for (void *p : bufs)
         cudaFree(p);
     cudaFreeHost(g.h_cnt);

@@ -107,3 +107,50 @@ def test_solve_from_tensor_core_beta0_parity(capi):
     assert np.abs(Z - Zr).max() <= 1e-4 * np.abs(Zr).max()
     big = (np.abs(Z) >= 1e-6) | (np.abs(Zr) >= 1e-6)
     assert np.all(np.sign(Z[big]) == np.sign(Zr[big]))
+
+
+def test_very_long_recording_full_size_sampled(capi):
+    """The very long recording (P=1, K=25, L=200, T=5e6) at full size, as the
+    default options run it (tensor-core beta0): beta0 on sampled windows
+    against the oracle's correlation, the solution's optimality on sampled
+    windows from the oracle's fresh FP64 beta (which needs Z only within L-1
+    of the window), and the library's objective against the oracle's."""
+    pb = synth.make_workload("verylong_P1_K25_L200_T5000000", seed=0)
+    K, L, Tz = pb.K, pb.L, pb.Tz
+    D, X = cuda(pb.D), cuda(pb.X)
+    h = capi.csc_setup(D, capi.make_opts(updates_per_visit=24))
+    try:
+        capi.csc_init(h, X, 1.0)
+        lam = 0.1 * capi.csc_lambda_max(h)
+        capi.csc_init(h, X, lam)
+        b0 = torch.zeros((K, Tz), dtype=torch.float32, device="cuda")
+        capi.csc_get_beta(h, b0)
+        Zd = torch.zeros((K, Tz), dtype=torch.float32, device="cuda")
+        status, E, st = capi.csc_solve(h, 1e-6, 1 << 40, Zd)
+    finally:
+        capi.csc_destroy(h)
+    assert status == 0 and st["converged"] == 1
+    b0 = b0.cpu().numpy()
+    Z = Zd.cpu().numpy()
+    n = oracle.norms(pb.D)
+    steps = pb.P * ((L + 15) // 16)
+    for a in (0, 1_234_567, 3_000_001, Tz - 1000):
+        b = min(a + 1000, Tz)
+        want = oracle.dtx(pb.D, pb.X[:, a:b + L - 1])
+        bound = oracle.dtx(np.abs(pb.D), np.abs(pb.X[:, a:b + L - 1]))
+        err = np.abs(b0[:, a:b] - want)
+        allowed = (4 * steps + 16) * U * bound + 2 * U * np.abs(want)
+        assert np.all(err <= allowed)
+        # fresh beta on the window [a, b): Z on [a-L+1, b+L-1), X on [a-L+1, b+2L-2)
+        lo = max(0, a - L + 1)
+        zw = Z[:, lo:min(Tz, b + L - 1)]
+        xw = pb.X[:, lo:min(pb.T, lo + zw.shape[1] + L - 1)]
+        beta_w = oracle.beta_fresh(pb.D, xw, zw)[:, a - lo:b - lo]
+        k = oracle.kkt(beta_w, Z[:, a:b], n, lam)
+        # the solve is optimal for its own beta0: against the exact problem the
+        # coordinate gaps may also carry beta0's error (divided by ||D_k||^2 = 1)
+        slack = float(allowed.max())
+        assert k["zero_excess"] <= 1e-6 * lam + slack, k
+        assert k["max_delta_z"] <= 2e-6 + slack, k
+    Eo = oracle.objective(pb.D, pb.X, Z, lam)
+    assert abs(E - Eo) <= 1e-9 * Eo
