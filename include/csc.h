@@ -85,6 +85,10 @@ typedef struct csc_opts {
                                   compensated sums; 0 = automatic: mode 1 where two of its
                                   CTAs fit on an SM (shared memory grows with P * L), else
                                   mode 3.  Modes 1-2 need K <= 64; other sizes use mode 3 */
+    int32_t launch_mode;       /* 0 = each poll batch (sweeps_per_poll sweeps of the c phases)
+                                  is replayed from a CUDA graph captured once per handle
+                                  and plan; 1 = direct kernel launches.  Same results */
+    int32_t reserved[1];       /* must be zero */
 } csc_opts;
 
 typedef struct csc_stats {

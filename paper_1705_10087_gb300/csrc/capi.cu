@@ -61,6 +61,7 @@ struct Scratch {
     double x2;  // sum X^2 of the last csc_init
     int tc_err;  // a bounded wait of the tensor-core beta0 kernel gave up
     int qhead[2];  // drain launches: next queue entry, queue length
+    int gctr[2];   // graph replays: launch index of the next launch, first index of the round
 };
 
 // Host mirror of what the solve loop polls (pinned).
@@ -160,6 +161,11 @@ struct csc_handle_s {
     size_t cap_dirty = 0, cap_touched = 0;
     int *d_queue = nullptr;  // drain launches: the phase's segments to visit
     size_t cap_queue = 0;
+    // the poll batch (S sweeps of c phases) captured as a CUDA graph, and what
+    // it was captured for
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<unsigned char> gkey;
+    cudaStream_t cap_stream = nullptr;  // captures happen here (not on a legacy stream)
     float *tile_rep = nullptr;  // stored resync report per resync tile
     size_t cap_tile_rep = 0;
 
@@ -270,6 +276,94 @@ int objectives(csc_handle_t h, const float *Zd, double *sum)
     return CSC_OK;
 }
 
+template <class T>
+void append_bytes(std::vector<unsigned char> &v, const T &x)
+{
+    const unsigned char *b = reinterpret_cast<const unsigned char *>(&x);
+    v.insert(v.end(), b, b + sizeof(T));
+}
+
+// One poll batch, S sweeps of the c phases, as direct launches with the given
+// launch indices (gp.g_dev == NULL) or, while capturing, with indices offset
+// from the device counters.
+int issue_batch(csc_handle_t h, PhaseParams gp, const PhaseConfig &cfg, int S, int resident,
+                int64_t g0, int64_t g_round, cudaStream_t s)
+{
+    const int c = h->c;
+    for (int i = 0; i < S; i++)
+        for (int p = 0; p < c; p++) {
+            const int64_t g = g0 + (int64_t)i * c + p;
+            gp.p = p;
+            gp.g = (int)g;
+            gp.g_round = (int)g_round;
+            gp.phase_list = h->d_phase_list + h->phase_off[p];
+            const int cnt = h->phase_off[p + 1] - h->phase_off[p];
+            if (cnt > 4 * resident) {
+                CSC_CUDA(launch_phase_drain(gp, cfg, cnt, resident, s));
+                h->launches += 2;
+            } else {
+                CSC_CUDA(launch_phase(gp, cfg, cnt, s));
+                h->launches += 1;
+            }
+        }
+    return CSC_OK;
+}
+
+// The graph of one poll batch for these parameters, captured on first use and
+// re-used while nothing it depends on changes (same buffers, plan, options).
+int batch_graph(csc_handle_t h, const PhaseParams &pp, const PhaseConfig &cfg, int S,
+                int resident, int *gctr, cudaGraphExec_t *out)
+{
+    PhaseParams gp = pp;
+    gp.g_dev = gctr;
+    gp.g_round_dev = gctr + 1;
+    gp.g = 0;
+    gp.g_round = 0;
+    gp.p = 0;
+    gp.phase_list = nullptr;
+    std::vector<unsigned char> key;
+    append_bytes(key, gp);
+    append_bytes(key, cfg.block);
+    append_bytes(key, cfg.smem);
+    append_bytes(key, cfg.tile_in_smem);
+    append_bytes(key, S);
+    append_bytes(key, resident);
+    append_bytes(key, h->c);
+    for (int o : h->phase_off)
+        append_bytes(key, o);
+    if (h->gexec && key == h->gkey) {
+        *out = h->gexec;
+        return CSC_OK;
+    }
+    if (h->gexec) {
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+        h->gkey.clear();
+    }
+    const int64_t launches = h->launches;
+    if (!h->cap_stream)
+        CSC_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t s = h->cap_stream;
+    CSC_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    int rc = issue_batch(h, gp, cfg, S, resident, 0, 0, s);
+    cudaError_t e = cudaSuccess;
+    if (rc == CSC_OK)
+        e = launch_add_int(gctr, S * h->c, s);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(s, &graph);
+    h->launches = launches;  // captured, not launched
+    if (rc != CSC_OK)
+        return rc;
+    CSC_CUDA(e);
+    CSC_CUDA(ee);
+    e = cudaGraphInstantiate(&h->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    CSC_CUDA(e);
+    h->gkey = key;
+    *out = h->gexec;
+    return CSC_OK;
+}
+
 int set_lambdas(csc_handle_t h, const double *lambda)
 {
     for (int i = 0; i < h->n; i++)
@@ -344,6 +438,10 @@ int csc_destroy(csc_handle_t h)
     for (int i = 0; i < h->n_kev; i++)
         cudaEventDestroy(h->kev[i]);
     delete[] h->kev;
+    if (h->gexec)
+        cudaGraphExecDestroy(h->gexec);
+    if (h->cap_stream)
+        cudaStreamDestroy(h->cap_stream);
     delete h;
     return CSC_OK;
 }
@@ -362,7 +460,8 @@ int csc_setup(csc_handle_t *hp, const float *D, int K, int P, int L, const csc_o
         o = *opts;
         if (o.segments < 0 || o.updates_per_visit < 0 || o.max_resyncs < -1 ||
             o.sweeps_per_poll < 0 || o.max_sweeps < 0 || o.time_kernels < 0 ||
-            o.time_kernels > 1 || o.segment_width < 0 || o.init_mode < 0 || o.init_mode > 3)
+            o.time_kernels > 1 || o.segment_width < 0 || o.init_mode < 0 || o.init_mode > 3 ||
+            o.launch_mode < 0 || o.launch_mode > 1 || o.reserved[0])
             return fail(CSC_EINVAL, "csc_setup: invalid options");
     }
     csc_handle_t h = *hp;
@@ -630,7 +729,7 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
     }
     h->z_is_zero = false;
 
-    PhaseParams pp;
+    PhaseParams pp{};
     pp.C = h->C;
     pp.Ct = h->Ct;
     pp.Kp = coef_pad(h->K);
@@ -674,49 +773,82 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
     int64_t drift_resyncs = 0;
     double drift = 0.0, phase_ms = 0.0;
     int64_t g = 0, effective = 0, phase_launches = 0;
+    // a poll batch is replayed from a CUDA graph (launch indices from device
+    // counters) while its indices stay inside the trace ring
+    cudaGraphExec_t gexec = nullptr;
+    if (h->opts.launch_mode == 0) {
+        int rc = batch_graph(h, pp, cfg, S, resident, sc->gctr, &gexec);
+        if (rc != CSC_OK)
+            return rc;
+        CSC_CUDA(launch_set_int(sc->gctr, 0, s));
+        h->launches += 1;
+    }
     for (;;) {
         const int64_t g_round = g;
         CSC_CUDA(cudaMemsetAsync(&sc->done, 0, sizeof(int), s));
+        if (gexec) {
+            CSC_CUDA(launch_set_int(sc->gctr + 1, (int)g_round, s));
+            h->launches += 1;
+        }
         bool round_done = false, forced = false;
         for (;;) {
             int nb = 0;  // launches in this poll batch
-            for (int i = 0; i < S; i++)
-                for (int p = 0; p < c; p++) {
-                    if (g >= kPhaseRing) {
-                        const int slot = (int)(g & (kPhaseRing - 1));
-                        CSC_CUDA(cudaMemsetAsync(&sc->upd[slot], 0, sizeof(long long), s));
-                        CSC_CUDA(cudaMemsetAsync(&sc->dec[slot], 0, sizeof(double), s));
-                        CSC_CUDA(cudaMemsetAsync(&sc->tend[slot], 0, sizeof(unsigned long long), s));
+            const bool graphed = gexec && g + (int64_t)S * c <= kPhaseRing;
+            if (graphed) {
+                if (timed)
+                    CSC_CUDA(cudaEventRecord(h->kev[0], s));
+                CSC_CUDA(cudaGraphLaunch(gexec, s));
+                if (timed)
+                    CSC_CUDA(cudaEventRecord(h->kev[1], s));
+                h->launches += 1;  // the counter advance
+                for (int p = 0; p < c; p++)
+                    h->launches += S * ((h->phase_off[p + 1] - h->phase_off[p] > 4 * resident) ? 2 : 1);
+                nb = S * c;
+                g += nb;
+            } else {
+                for (int i = 0; i < S; i++)
+                    for (int p = 0; p < c; p++) {
+                        if (g >= kPhaseRing) {
+                            const int slot = (int)(g & (kPhaseRing - 1));
+                            CSC_CUDA(cudaMemsetAsync(&sc->upd[slot], 0, sizeof(long long), s));
+                            CSC_CUDA(cudaMemsetAsync(&sc->dec[slot], 0, sizeof(double), s));
+                            CSC_CUDA(cudaMemsetAsync(&sc->tend[slot], 0, sizeof(unsigned long long), s));
+                        }
+                        if (timed)
+                            CSC_CUDA(cudaEventRecord(h->kev[2 * nb], s));
+                        pp.phase_list = nullptr;
+                        // one launch: S = 1 sweep restricted to phase p
+                        PhaseParams one = pp;
+                        one.p = p;
+                        one.g = (int)g;
+                        one.g_round = (int)g_round;
+                        one.phase_list = h->d_phase_list + h->phase_off[p];
+                        const int cnt = h->phase_off[p + 1] - h->phase_off[p];
+                        if (cnt > 4 * resident) {
+                            CSC_CUDA(launch_phase_drain(one, cfg, cnt, resident, s));
+                            h->launches += 2;
+                        } else {
+                            CSC_CUDA(launch_phase(one, cfg, cnt, s));
+                            h->launches += 1;
+                        }
+                        if (timed)
+                            CSC_CUDA(cudaEventRecord(h->kev[2 * nb + 1], s));
+                        nb++;
+                        g++;
                     }
-                    pp.p = p;
-                    pp.g = (int)g;
-                    pp.g_round = (int)g_round;
-                    pp.phase_list = h->d_phase_list + h->phase_off[p];
-                    if (timed)
-                        CSC_CUDA(cudaEventRecord(h->kev[2 * nb], s));
-                    const int cnt = h->phase_off[p + 1] - h->phase_off[p];
-                    if (cnt > 4 * resident) {
-                        CSC_CUDA(launch_phase_drain(pp, cfg, cnt, resident, s));
-                        h->launches += 1;  // the compaction (the drain counts below)
-                    } else {
-                        CSC_CUDA(launch_phase(pp, cfg, cnt, s));
-                    }
-                    if (timed)
-                        CSC_CUDA(cudaEventRecord(h->kev[2 * nb + 1], s));
-                    nb++;
-                    g++;
-                }
+            }
             phase_launches += nb;
-            h->launches += nb;
             CSC_CUDA(cudaMemcpyAsync(h->poll, &sc->total, sizeof(long long) + sizeof(int),
                                      cudaMemcpyDeviceToHost, s));
             CSC_CUDA(cudaStreamSynchronize(s));
-            if (timed)
-                for (int i = 0; i < nb; i++) {
+            if (timed) {
+                const int pairs = graphed ? 1 : nb;
+                for (int i = 0; i < pairs; i++) {
                     float ms = 0.f;
                     CSC_CUDA(cudaEventElapsedTime(&ms, h->kev[2 * i], h->kev[2 * i + 1]));
                     phase_ms += ms;
                 }
+            }
             if (h->poll->total >= max_updates && !h->poll->done) {
                 status = CSC_NOT_CONVERGED;
                 break;

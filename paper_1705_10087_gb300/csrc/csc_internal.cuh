@@ -152,8 +152,10 @@ struct PhaseParams {
     int *done;                 // set once a full sweep applied nothing
     long long max_updates;
     int M, c, p, K, Kp, L;  // Kp = K rounded up to a multiple of 4
-    int g;        // launch index (monotone within a solve)
-    int g_round;  // first launch index of the current CD round
+    int g;        // launch index (monotone within a solve); with g_dev, offset from *g_dev
+    int g_round;  // first launch index of the current CD round (or *g_round_dev)
+    const int *g_dev;        // NULL, or the launch index of the first launch of a graph replay
+    const int *g_round_dev;  // NULL, or the first launch index of the round
     int u;        // cap on updates per visit
     int w_max;  // widest segment (shared-memory layout)
     // queue of the phase's segments that need a visit (drain launches):
@@ -174,6 +176,9 @@ PhaseConfig phase_config(int K, int L, int w_max);
 // active = number of segments in pp.phase_list (the grid size).
 cudaError_t launch_phase(const PhaseParams &pp, const PhaseConfig &cfg, int active,
                          cudaStream_t s);
+// Device counters for launches replayed from a CUDA graph: *p = v; *p += v.
+cudaError_t launch_set_int(int *p, int v, cudaStream_t s);
+cudaError_t launch_add_int(int *p, int v, cudaStream_t s);
 // Blocks of the phase kernel that are resident at once on the whole GPU.
 int phase_resident_blocks(const PhaseConfig &cfg, int K);
 // The same phase as launch_phase, for phase lists much longer than the

@@ -105,7 +105,8 @@ struct Layout {
 // One visit of segment m by the whole block (uniform control flow: every
 // early exit is decided by thread 0 and broadcast).
 template <bool SMEM, int MAXT, int KT>
-__device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m)
+__device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m, const int g,
+                                              const int g_round)
 {
     using Idx = typename std::conditional<SMEM, int, int64_t>::type;
     constexpr bool KFIX = KT > 0;
@@ -122,13 +123,13 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
             go = 0;
         } else if (*(volatile long long *)pp.total >= pp.max_updates) {
             go = 0;  // out of budget: not a converged sweep, so done stays unset
-        } else if (pp.g - pp.g_round >= pp.c) {
+        } else if (g - g_round >= pp.c) {
             // a full sweep (the previous c launches of this round) applied nothing
             long long sum = 0;
-            for (int j = pp.g - pp.c; j < pp.g; j++)
+            for (int j = g - pp.c; j < g; j++)
                 sum += *(volatile long long *)&pp.upd[j & (kPhaseRing - 1)];
             if (sum == 0) {
-                *(volatile int *)pp.done = pp.g + 1;  // same value from every block
+                *(volatile int *)pp.done = g + 1;  // same value from every block
                 go = 0;
             }
         }
@@ -446,7 +447,7 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
                 pp.touched[mm] = 1;
             }
             pp.touched[m] = 1;
-            const int slot = pp.g & (kPhaseRing - 1);
+            const int slot = g & (kPhaseRing - 1);
             atomicAdd(reinterpret_cast<unsigned long long *>(&pp.upd[slot]),
                       (unsigned long long)nupd);
             atomicAdd(reinterpret_cast<unsigned long long *>(pp.total), (unsigned long long)nupd);
@@ -457,6 +458,17 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
     }
 }
 
+// Launch index and first index of the round: from the parameters, or, for
+// launches replayed from a CUDA graph, offsets from counters in device memory.
+__device__ __forceinline__ int launch_index(const PhaseParams &pp)
+{
+    return pp.g_dev ? *pp.g_dev + pp.g : pp.g;
+}
+__device__ __forceinline__ int round_index(const PhaseParams &pp)
+{
+    return pp.g_round_dev ? *pp.g_round_dev : pp.g_round;
+}
+
 // MAXT: the block size the instantiation is launched with.  Blocks of 128
 // threads (atoms up to 64 samples) are compiled for 5 resident blocks per SM,
 // so that the several hundred co-active segments of a phase fit in one wave;
@@ -465,7 +477,8 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
 template <bool SMEM, int MAXT, int KT>
 __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseParams pp)
 {
-    visit_segment<SMEM, MAXT, KT>(pp, pp.phase_list[blockIdx.x]);
+    visit_segment<SMEM, MAXT, KT>(pp, pp.phase_list[blockIdx.x], launch_index(pp),
+                                  round_index(pp));
 }
 
 // Persistent form: a grid of resident blocks drains the queue of this phase's
@@ -476,15 +489,16 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_drain_kernel(
 {
     __shared__ int s_idx;
     const int n = *pp.qlen;
+    const int g = launch_index(pp), g_round = round_index(pp);
     // an empty queue visits nothing, so the test for a full sweep without
     // updates (made at the start of every visit) is also made here once
-    if (blockIdx.x == 0 && threadIdx.x == 0 && pp.g - pp.g_round >= pp.c &&
+    if (blockIdx.x == 0 && threadIdx.x == 0 && g - g_round >= pp.c &&
         !*(volatile int *)pp.done) {
         long long sum = 0;
-        for (int j = pp.g - pp.c; j < pp.g; j++)
+        for (int j = g - pp.c; j < g; j++)
             sum += *(volatile long long *)&pp.upd[j & (kPhaseRing - 1)];
         if (sum == 0)
-            *(volatile int *)pp.done = pp.g + 1;
+            *(volatile int *)pp.done = g + 1;
     }
     for (;;) {
         if (threadIdx.x == 0)
@@ -494,7 +508,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_drain_kernel(
         __syncthreads();  // every thread has read s_idx before it is overwritten
         if (idx >= n)
             break;
-        visit_segment<SMEM, MAXT, KT>(pp, pp.queue[idx]);
+        visit_segment<SMEM, MAXT, KT>(pp, pp.queue[idx], g, g_round);
         __syncthreads();  // the next visit re-uses the shared memory
     }
 }
@@ -524,7 +538,28 @@ __global__ void compact_phase_kernel(const int *__restrict__ list, int count,
     }
 }
 
+__global__ void set_int_kernel(int *p, int v)
+{
+    *p = v;
+}
+__global__ void add_int_kernel(int *p, int v)
+{
+    *p += v;
+}
+
 }  // namespace
+
+cudaError_t launch_set_int(int *p, int v, cudaStream_t s)
+{
+    set_int_kernel<<<1, 1, 0, s>>>(p, v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_int(int *p, int v, cudaStream_t s)
+{
+    add_int_kernel<<<1, 1, 0, s>>>(p, v);
+    return cudaGetLastError();
+}
 
 PhaseConfig phase_config(int K, int L, int wmax)
 {

@@ -71,7 +71,7 @@ def test_argument_validation_needs_no_device(lib):
     assert lib.csc_setup(ctypes.byref(h), D.ctypes.data, 2, 1, 513, None, None) == capi.CSC_EINVAL
     assert lib.csc_setup(ctypes.byref(h), None, 2, 1, 4, None, None) == capi.CSC_EINVAL
     o = capi.make_opts()
-    o.init_mode = 7
+    o.launch_mode = 7
     assert lib.csc_setup(ctypes.byref(h), D.ctypes.data, 2, 1, 4, ctypes.byref(o),
                          None) == capi.CSC_EINVAL
     assert lib.csc_init(None, D.ctypes.data, 10, 1.0, None) == capi.CSC_EINVAL

@@ -48,11 +48,13 @@ def oracle_solution(D, X, lam):
     return ref["Z"], oracle.objective(D, X, ref["Z"], lam)
 
 
-def solve_batch(capi, D, Xs, lams, tol=1e-6, width=0, u=0, Z0=None, host=False):
+def solve_batch(capi, D, Xs, lams, tol=1e-6, width=0, u=0, Z0=None, host=False,
+                launch_mode=0):
     X, T = batch.pack(Xs)
     K, L = D.shape[0], D.shape[2]
     h = capi.csc_setup(D if host else cuda(D),
-                       capi.make_opts(segment_width=width, updates_per_visit=u))
+                       capi.make_opts(segment_width=width, updates_per_visit=u,
+                                      launch_mode=launch_mode))
     try:
         capi.csc_init_batch(h, X if host else cuda(X), T, lams,
                             None if Z0 is None else (Z0 if host else cuda(Z0)))
@@ -305,3 +307,32 @@ def test_autotune_from_warm_start(capi, short_refs):
         capi.csc_destroy(h)
     assert abs(tr["E_start"] - E0) <= 1e-12 * E0
     check_batch(dict(Z=Z, T=T, E=E, Es=Es, stats=st, status=status), D, Xs, lams, refs)
+
+
+def test_graph_replay_equals_direct_launches(capi, long_refs):
+    # poll batches replayed from a captured CUDA graph (launch indices from
+    # device counters) compute exactly what direct launches compute
+    D, Xs, lams, refs = long_refs
+    a = solve_batch(capi, D, Xs, lams, u=24, launch_mode=0)
+    b = solve_batch(capi, D, Xs, lams, u=24, launch_mode=1)
+    assert np.array_equal(a["Z"], b["Z"])
+    assert a["E"] == b["E"]
+    for k in ("updates", "sweeps", "resyncs", "visits"):
+        assert a["stats"][k] == b["stats"][k], k
+    check_batch(a, D, Xs, lams, refs)
+
+
+def test_graph_is_captured_once_per_plan(capi, long_refs):
+    D, Xs, lams, refs = long_refs
+    X, T = batch.pack(Xs)
+    h = capi.csc_setup(cuda(D), capi.make_opts(updates_per_visit=24))
+    try:
+        launches = []
+        for _ in range(3):
+            capi.csc_init_batch(h, cuda(X), T, lams)
+            status, E, st = capi.csc_solve(h, 1e-6)
+            assert status == 0
+            launches.append(st["kernel_launches"])
+    finally:
+        capi.csc_destroy(h)
+    assert launches[0] == launches[1] == launches[2]
