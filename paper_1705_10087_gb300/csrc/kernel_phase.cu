@@ -285,7 +285,7 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
     // (no barrier needed: each thread reads back only its own columns)
 
     int buf = 0, nupd = 0;
-    double decrease = 0.0;
+    float decrease = 0.f;  // this thread's updates of the visit (at most u terms)
     int64_t tmin = Tz, tmax = -1;
     bool capped = false;
     for (int it = 0;; it++) {
@@ -339,9 +339,9 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
             if (t == t0) {
                 // Prop. A.1 from the owner's r before this update touches it:
                 // E(Z) - E(Z') = dZ (r - n dZ / 2) + lam (|z| - |u|), dZ = u - z
-                const double n = nrm[k0], d = delta, u = znew, z = (double)znew - d;
-                const double r0 = rs[jj * cst + k0 * kst];
-                decrease += d * (r0 - 0.5 * n * d) + (double)lam * (fabs(z) - fabs(u));
+                const float n = nrm[k0], d = delta, u = znew, z = znew - delta;
+                const float r0 = rs[jj * cst + k0 * kst];
+                decrease += d * (r0 - 0.5f * n * d) + lam * (fabsf(z) - fabsf(u));
             }
             // the K coefficients S_{k,k0}[t-t0] of this lag are contiguous in Ct:
             // fetch them first (independent vector loads, one L2 round trip per
@@ -426,12 +426,12 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
     for (int o = 16; o > 0; o >>= 1)
         decrease += __shfl_xor_sync(kFull, decrease, o);
     if (lane == 0)
-        s_dec[warp] = decrease;
+        s_dec[warp] = (double)decrease;
     __syncthreads();
     if (tid == 0) {
-        decrease = 0.0;
+        double dsum = 0.0;
         for (int i = 0; i < nwarps; i++)
-            decrease += s_dec[i];
+            dsum += s_dec[i];
         pp.dirty[m] = capped ? 1 : 0;
         if (nupd > 0) {
             // neighbours whose r changed: segments meeting [tmin-L+1, tmax+L-1]
@@ -452,7 +452,7 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
                       (unsigned long long)nupd);
             atomicAdd(reinterpret_cast<unsigned long long *>(pp.total), (unsigned long long)nupd);
             atomicAdd(reinterpret_cast<unsigned long long *>(pp.visits), 1ull);
-            atomicAdd(&pp.dec[slot], decrease);
+            atomicAdd(&pp.dec[slot], dsum);
             atomicMax(&pp.tend[slot], globaltimer_ns());
         }
     }
