@@ -206,24 +206,25 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
     // best coordinate of own column jj from its r values (registers) and the
     // mask of entries that can move: z != 0 or |r| > lam (all others have
     // Z' = Sh(r, lam)/n = 0 = z exactly); compile-time K only
+    // Only the set bits of need are visited (their r, z and norms re-read from
+    // shared memory): an unrolled, predicated loop over all K atoms would issue
+    // every atom's instructions whether its bit is set or not.
     auto col_finish = [&](int jj, const float (&rv)[KT > 0 ? KT : 1], unsigned need) {
+        (void)rv;
         float best = -1.f, bz = 0.f, bdz = 0.f;
         int bk = 0;
-        if (need) {
-            const float *zc = zs + jj * cst;
-#pragma unroll
-            for (int k = 0; k < (KT > 0 ? KT : 1); k++) {
-                if ((need >> k) & 1u) {
-                    float zn, d;
-                    coord_step(rv[k], zc[k * kst], nrm[k], rnrm[k], lam, &zn, &d);
-                    const float ad = fabsf(d);
-                    if (ad > best) {
-                        best = ad;
-                        bk = k;
-                        bz = zn;
-                        bdz = d;
-                    }
-                }
+        const float *rc = rs + jj * cst;
+        const float *zc = zs + jj * cst;
+        for (unsigned rest = need; rest; rest &= rest - 1u) {
+            const int k = __ffs(rest) - 1;
+            float zn, d;
+            coord_step(rc[k * kst], zc[k * kst], nrm[k], rnrm[k], lam, &zn, &d);
+            const float ad = fabsf(d);
+            if (ad > best) {
+                best = ad;
+                bk = k;
+                bz = zn;
+                bdz = d;
             }
         }
         // segment-local flat index: same order as k * Tz + t inside the segment
