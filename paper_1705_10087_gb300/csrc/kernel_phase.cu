@@ -72,8 +72,8 @@ struct Layout {
         o = up(o + 4 * (size_t)w);
         ck = o;
         o = up(o + 4 * (size_t)w);
-        zm = o;  // per column: bit k set when Z_k[t] != 0 (compile-time K <= 32)
-        o = up(o + 4 * (size_t)w);
+        zm = o;  // per column: bit k set when Z_k[t] != 0 (compile-time K <= 64)
+        o = up(o + 8 * (size_t)w);
         slot_z = o;
         o = up(o + 4 * 64);
         slot_d = o;
@@ -163,8 +163,10 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
     float *cz = reinterpret_cast<float *>(smem_raw + lay.cz);
     float *cd = reinterpret_cast<float *>(smem_raw + lay.cd);
     int *ck = reinterpret_cast<int *>(smem_raw + lay.ck);
-    unsigned *zmask = reinterpret_cast<unsigned *>(smem_raw + lay.zm);
-    static_assert(KT <= 32, "the nonzero mask of a column holds 32 atoms");
+    // one bit per atom of a column: 32 or 64 bits
+    using Mask = typename std::conditional<(KT > 32), unsigned long long, unsigned>::type;
+    static_assert(KT <= 64, "the masks of a column hold 64 atoms");
+    Mask *zmask = reinterpret_cast<Mask *>(smem_raw + lay.zm);
     float *slot_z = reinterpret_cast<float *>(smem_raw + lay.slot_z);
     float *slot_d = reinterpret_cast<float *>(smem_raw + lay.slot_d);
     int *slot_k = reinterpret_cast<int *>(smem_raw + lay.slot_k);
@@ -209,14 +211,13 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
     // Only the set bits of need are visited (their r, z and norms re-read from
     // shared memory): an unrolled, predicated loop over all K atoms would issue
     // every atom's instructions whether its bit is set or not.
-    auto col_finish = [&](int jj, const float (&rv)[KT > 0 ? KT : 1], unsigned need) {
-        (void)rv;
+    auto col_finish = [&](int jj, Mask need) {
         float best = -1.f, bz = 0.f, bdz = 0.f;
         int bk = 0;
         const float *rc = rs + jj * cst;
         const float *zc = zs + jj * cst;
-        for (unsigned rest = need; rest; rest &= rest - 1u) {
-            const int k = __ffs(rest) - 1;
+        for (Mask rest = need; rest; rest &= rest - 1) {
+            const int k = (sizeof(Mask) == 8 ? __ffsll((long long)rest) : __ffs((int)rest)) - 1;
             float zn, d;
             coord_step(rc[k * kst], zc[k * kst], nrm[k], rnrm[k], lam, &zn, &d);
             const float ad = fabsf(d);
@@ -258,16 +259,14 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
             }
         };
         if constexpr (KFIX) {
-            float rv[KT];
-            unsigned need = 0, zb = 0;
+            Mask need = 0, zb = 0;
 #pragma unroll
             for (int k = 0; k < KT; k++) {
-                rv[k] = rc[k * kst];
-                zb |= (zc[k * kst] != 0.f ? 1u : 0u) << k;
-                need |= (fabsf(rv[k]) > lam ? 1u : 0u) << k;
+                zb |= (Mask)(zc[k * kst] != 0.f ? 1 : 0) << k;
+                need |= (Mask)(fabsf(rc[k * kst]) > lam ? 1 : 0) << k;
             }
             zmask[jj] = zb;
-            col_finish(jj, rv, need | zb);
+            col_finish(jj, need | zb);
             return;
         } else {
 #pragma unroll 5
@@ -371,18 +370,17 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
                     // apply and screen in registers, then evaluate the movable entries
                     if (t == t0) {
                         zs[jj * cst + k0 * kst] = znew;
-                        zmask[jj] = znew != 0.f ? (zmask[jj] | (1u << k0)) : (zmask[jj] & ~(1u << k0));
+                        const Mask bit = (Mask)1 << k0;
+                        zmask[jj] = znew != 0.f ? (zmask[jj] | bit) : (zmask[jj] & ~bit);
                     }
-                    float rv[KT];
-                    unsigned need = 0;
+                    Mask need = 0;
 #pragma unroll
                     for (int k = 0; k < KT; k++) {
                         const float r = fmaf(-cv[k], delta, rcol[k * kst]);
                         rcol[k * kst] = r;
-                        rv[k] = r;
-                        need |= (fabsf(r) > lam ? 1u : 0u) << k;
+                        need |= (Mask)(fabsf(r) > lam ? 1 : 0) << k;
                     }
-                    col_finish(jj, rv, need | zmask[jj]);
+                    col_finish(jj, need | zmask[jj]);
                 } else {
 #pragma unroll
                     for (int k = 0; k < KT; k++)
@@ -581,15 +579,19 @@ namespace {
 template <template <bool, int, int> class Sel, class F>
 cudaError_t dispatch(const PhaseConfig &cfg, int K, F &&f)
 {
-    const bool k25 = K == 25;  // the workloads' atom count: compiled with K fixed
+    // the workloads' atom counts (25 and 64) are compiled with K fixed
     if (cfg.block == 128) {
-        if (k25)
+        if (K == 25)
             return cfg.tile_in_smem ? f(Sel<true, 128, 25>::fn()) : f(Sel<false, 128, 25>::fn());
+        if (K == 64)
+            return cfg.tile_in_smem ? f(Sel<true, 128, 64>::fn()) : f(Sel<false, 128, 64>::fn());
         return cfg.tile_in_smem ? f(Sel<true, 128, 0>::fn()) : f(Sel<false, 128, 0>::fn());
     }
     if (cfg.block == 512) {
-        if (k25)
+        if (K == 25)
             return cfg.tile_in_smem ? f(Sel<true, 512, 25>::fn()) : f(Sel<false, 512, 25>::fn());
+        if (K == 64)
+            return cfg.tile_in_smem ? f(Sel<true, 512, 64>::fn()) : f(Sel<false, 512, 64>::fn());
         return cfg.tile_in_smem ? f(Sel<true, 512, 0>::fn()) : f(Sel<false, 512, 0>::fn());
     }
     return cfg.tile_in_smem ? f(Sel<true, 1024, 0>::fn()) : f(Sel<false, 1024, 0>::fn());
