@@ -299,13 +299,16 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
                 myj = jj;
             }
         }
+        // the candidate's values are read while the warp reduction runs
+        const float my_z = cz[myj], my_d = cd[myj];
+        const int my_k = ck[myj];
         const unsigned long long wm = warp_max_u64(my);
         const unsigned win = __ballot_sync(kFull, my == wm);
         if (lane == __ffs(win) - 1) {
             slot_key[buf * 32 + warp] = wm;
-            slot_z[buf * 32 + warp] = cz[myj];
-            slot_d[buf * 32 + warp] = cd[myj];
-            slot_k[buf * 32 + warp] = ck[myj];
+            slot_z[buf * 32 + warp] = my_z;
+            slot_d[buf * 32 + warp] = my_d;
+            slot_k[buf * 32 + warp] = my_k;
             slot_j[buf * 32 + warp] = myj;
         }
         __syncthreads();
