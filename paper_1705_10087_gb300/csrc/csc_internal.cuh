@@ -27,6 +27,13 @@ __host__ __device__ __forceinline__ int64_t seg_start(int64_t Tz, int M, int64_t
     return m * Tz / M;
 }
 
+// The segment holding column t under that cut: the m with
+// seg_start(m) <= t < seg_start(m+1), m = floor(((t+1) M - 1) / Tz).
+__host__ __device__ __forceinline__ int segment_of(int64_t Tz, int M, int64_t t)
+{
+    return (int)(((t + 1) * (int64_t)M - 1) / Tz);
+}
+
 // Soft thresholding Sh(u, lam) = sign(u) max(|u| - lam, 0) (Sec. 2.1).
 __device__ __forceinline__ float soft_f(float u, float lam)
 {

@@ -107,6 +107,9 @@ __global__ void __launch_bounds__(kResyncThreads)
     const int isig = tiles.sig[blockIdx.x];
     const SigDesc sd = sigs[isig];
     const int64_t Tz = sd.Tz, ld = sd.ld;
+    float *__restrict__ const rr = sd.r;
+    const float *__restrict__ const zz = sd.Z;
+    const float *__restrict__ const b0p = sd.beta0;
     const int W2 = 2 * L - 1;
     const int tid = threadIdx.x;
     const int col = tid % kResyncCols, grp = tid / kResyncCols;
@@ -117,10 +120,11 @@ __global__ void __launch_bounds__(kResyncThreads)
     // them, and every window marks the segments it covers as touched
     bool need = true;
     if (touched && rep && sd.nseg > 0) {
+        // the problem's segments are the equal cut of seg_start
         const int64_t ce = c0 + kResyncCols < Tz ? c0 + kResyncCols : Tz;
-        const int64_t *ss = seg_s + sd.seg0;
+        const int j1 = segment_of(Tz, sd.nseg, ce - 1);
         need = false;
-        for (int j = interval_of(ss, sd.nseg, c0); j < sd.nseg && ss[j] < ce; j++)
+        for (int j = segment_of(Tz, sd.nseg, c0); j <= j1; j++)
             if (touched[sd.seg0 + j]) {
                 need = true;
                 break;
@@ -147,7 +151,7 @@ __global__ void __launch_bounds__(kResyncThreads)
     const int chunk = (32 * kChunk) / K < kChunk ? (32 * kChunk) / K : kChunk;
     for (int64_t a = lo; a < hi; a += chunk) {
         const int64_t b = a + chunk < hi ? a + chunk : hi;
-        const int n = compact_nonzeros(sd.Z, K, ld, a, b, list, warp_counts);
+        const int n = compact_nonzeros(zz, K, ld, a, b, list, warp_counts);
         if (t < Tz) {
             for (int i = 0; i < n; i++) {
                 const NZ e = list[i];
@@ -176,16 +180,16 @@ __global__ void __launch_bounds__(kResyncThreads)
             const int64_t ix = (int64_t)k * ld + t;
             // r = beta0 - (hi + lo), finished with TwoSum so that only the final
             // float rounding remains
-            const float b0 = sd.beta0[ix], ah = acc_hi[q], al = acc_lo[q];
+            const float b0 = b0p[ix], ah = acc_hi[q], al = acc_lo[q];
             const float sm = __fsub_rn(b0, ah);
             const float bv = __fsub_rn(sm, b0);
             const float er = __fadd_rn(__fsub_rn(b0, __fsub_rn(sm, bv)), __fsub_rn(-ah, bv));
             const float r32 = __fadd_rn(sm, __fsub_rn(er, al));
-            const float rold = sd.r[ix];
+            const float rold = rr[ix];
             if (write_r)
-                sd.r[ix] = r32;
+                rr[ix] = r32;
             drift = fmaxf(drift, fabsf(rold - r32));
-            const float z = sd.Z[ix];
+            const float z = zz[ix];
             const float n = norms[k], rn = __frcp_rn(n);
             // optimality in the r form (Theorem A.1): z = 0 needs |beta| = |r| <= lam;
             // otherwise |Z' - z| with Z' from Eq. pb_coord, without cancellation
@@ -205,7 +209,7 @@ __global__ void __launch_bounds__(kResyncThreads)
             coord_step(write_r ? r32 : rold, z, n, rn, lam, &zn, &d32);
             dz32 = fmaxf(dz32, fabsf(d32));
             if (dirty && sd.nseg > 0 && fabsf(d32) >= (tol_mark < 0.f ? sd.tol : tol_mark))
-                dirty[sd.seg0 + interval_of(seg_s + sd.seg0, sd.nseg, t)] = 1;
+                dirty[sd.seg0 + segment_of(Tz, sd.nseg, t)] = 1;
         }
     }
     }  // need

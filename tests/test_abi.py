@@ -84,3 +84,16 @@ def test_default_opts(lib):
     o = capi.csc_opts()
     lib.csc_default_opts(ctypes.byref(o))
     assert (o.segments, o.updates_per_visit, o.max_resyncs) == (0, 0, -1)
+
+
+@pytest.mark.parametrize("Tz,L,M", [(199_937, 64, 1024), (1985, 16, 10), (7, 3, 7), (50, 1, 9),
+                                    (4_999_801, 200, 12_500), (1, 5, 1)])
+def test_segment_of_closed_form(lib, Tz, L, M):
+    # the kernels find a column's segment as floor(((t+1) M - 1) / Tz): the
+    # inverse of the plan's starts floor(m Tz / M)
+    _, _, starts = capi.csc_plan(Tz, L, M)
+    t = np.unique(np.concatenate([np.arange(min(Tz, 3000)), starts[1:-1], starts[1:-1] - 1,
+                                  np.array([Tz - 1])]))
+    t = t[(t >= 0) & (t < Tz)]
+    m = ((t + 1) * M - 1) // Tz
+    assert np.all(starts[m] <= t) and np.all(t < starts[m + 1])
