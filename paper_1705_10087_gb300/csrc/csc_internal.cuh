@@ -214,7 +214,7 @@ struct Tiles {
     const int64_t *start;
     int64_t n;
 };
-constexpr int kResyncCols = 64;  // columns per resync tile
+constexpr int kResyncCols = 32;  // columns per resync tile
 constexpr int kTile = 256;       // samples per objective tile, columns per absmax tile
 
 // beta0 = D~ * X on the tensor cores (kernel_dtx_tc.cu): mode 1 = three-term

@@ -410,12 +410,18 @@ cudaError_t launch_resync(const SigDesc *sig, Tiles tiles, const float *C, const
                             tol_mark, touched, rep, s)
     if (kpt <= 2)
         CSC_RESYNC(2);
+    if (kpt <= 4)
+        CSC_RESYNC(4);
     if (kpt <= 8)
         CSC_RESYNC(8);
     if (kpt <= 16)
         CSC_RESYNC(16);
+    if (kpt <= 32)
+        CSC_RESYNC(32);
     if (kpt <= 64)
         CSC_RESYNC(64);
+    if (kpt <= 128)
+        CSC_RESYNC(128);
 #undef CSC_RESYNC
     return cudaErrorInvalidValue;
 }
