@@ -151,6 +151,11 @@ struct csc_handle_s {
 
     // segment plan (rebuilt when the signals, lambdas or segment options change)
     bool plan_ok = false;
+    // what the current plan and tile tables were built for (re-used when a
+    // csc_setup / csc_init repeats the same signal lengths and options)
+    std::vector<int64_t> plan_a, tiles_a;
+    int plan_L = -1, plan_segments = -1, plan_width = -1, tiles_L = -1;
+    std::vector<int> plan_seg0, plan_nseg;
     int M = 0, c = 0, w_max = 0;
     std::vector<int> phase_off;  // [c+1] into the phase list
     int64_t *d_seg_s = nullptr, *d_seg_e = nullptr;
@@ -195,6 +200,17 @@ int build_plan(csc_handle_t h)
         return CSC_OK;
     cudaStream_t s = h->stream;
     const int L = h->L;
+    if (h->M > 0 && h->plan_a == h->a && h->plan_L == L &&
+        h->plan_segments == h->opts.segments && h->plan_width == h->opts.segment_width) {
+        // same signals and options: the device tables are still those of this plan
+        for (int i = 0; i < h->n; i++) {
+            h->sigs[i].seg0 = h->plan_seg0[i];
+            h->sigs[i].nseg = h->plan_nseg[i];
+        }
+        CSC_CUDA(upload(&h->d_sig, &h->cap_sig, h->sigs, s));
+        h->plan_ok = true;
+        return CSC_OK;
+    }
     std::vector<int64_t> seg_s, seg_e;
     std::vector<int> seg_sig;
     std::vector<int> local;
@@ -255,6 +271,16 @@ int build_plan(csc_handle_t h)
     h->c = c;
     h->w_max = w_max;
     h->phase_off = off;
+    h->plan_a = h->a;
+    h->plan_L = L;
+    h->plan_segments = h->opts.segments;
+    h->plan_width = h->opts.segment_width;
+    h->plan_seg0.resize(h->n);
+    h->plan_nseg.resize(h->n);
+    for (int i = 0; i < h->n; i++) {
+        h->plan_seg0[i] = h->sigs[i].seg0;
+        h->plan_nseg[i] = h->sigs[i].nseg;
+    }
     h->plan_ok = true;
     return CSC_OK;
 }
@@ -374,8 +400,8 @@ int set_lambdas(csc_handle_t h, const double *lambda)
         h->sigs[i].lam = (float)h->lam[i];
         h->sigs[i].lam_d = h->lam[i];
     }
+    // (a copy from pageable memory has read the host array when it returns)
     CSC_CUDA(upload(&h->d_sig, &h->cap_sig, h->sigs, h->stream));
-    CSC_CUDA(cudaStreamSynchronize(h->stream));
     return CSC_OK;
 }
 
@@ -573,11 +599,15 @@ int csc_init_batch(csc_handle_t h, const float *X, const int64_t *T, int n, cons
     h->nrtiles = (int64_t)rtile_s.size();
     h->E_sig.assign(n, 0.0);
     h->lmax.assign(n, 0.0);
-    CSC_CUDA(upload(&h->d_tile_s, &h->cap_tile_s, tile_s, s));
-    CSC_CUDA(upload(&h->d_tile_sig, &h->cap_tile_sig, tile_sig, s));
-    CSC_CUDA(upload(&h->d_tile_off, &h->cap_tile_off, h->tile_off, s));
-    CSC_CUDA(upload(&h->d_rtile_s, &h->cap_rtile_s, rtile_s, s));
-    CSC_CUDA(upload(&h->d_rtile_sig, &h->cap_rtile_sig, rtile_sig, s));
+    if (h->tiles_a != h->a || h->tiles_L != h->L) {
+        CSC_CUDA(upload(&h->d_tile_s, &h->cap_tile_s, tile_s, s));
+        CSC_CUDA(upload(&h->d_tile_sig, &h->cap_tile_sig, tile_sig, s));
+        CSC_CUDA(upload(&h->d_tile_off, &h->cap_tile_off, h->tile_off, s));
+        CSC_CUDA(upload(&h->d_rtile_s, &h->cap_rtile_s, rtile_s, s));
+        CSC_CUDA(upload(&h->d_rtile_sig, &h->cap_rtile_sig, rtile_sig, s));
+        h->tiles_a = h->a;
+        h->tiles_L = h->L;
+    }
     CSC_CUDA(grow(&h->d_E, &h->cap_E, (size_t)n));
     CSC_CUDA(grow(&h->d_lmax, &h->cap_lmax, (size_t)n));
     CSC_CUDA(grow(&h->partials, &h->cap_partials, 2 * (size_t)h->ntiles));
