@@ -171,6 +171,20 @@ def phase_traffic():
     return float(fields["dram_bytes_per_launch"])
 
 
+def over_ranks(dist, device, elapsed, units):
+    """Whole-job figures of N independent replicas: the slowest rank's elapsed
+    time (max over ranks) and the units all ranks processed (sum); without a
+    process group, this rank's own."""
+    if dist is None:
+        return float(elapsed), float(units)
+    import torch
+    t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def time_to_gap_ms(trace, init_ms, E_star, rel=1e-4):
     E = trace["E_start"] - np.cumsum(trace["decrease"])
     ok = np.nonzero((E - E_star) <= rel * E_star)[0]
@@ -475,14 +489,7 @@ def main():
     achieved = alg_bytes / (phase_ms * 1e-3) / 1e9 if phase_ms > 0 else None
     peak, peak_kind = peaks()
 
-    if world > 1:
-        t = torch.tensor([tot_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        u = torch.tensor([updates], dtype=torch.float64, device="cuda")
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        tot_ms_max, updates_all = float(t.item()), float(u.item())
-    else:
-        tot_ms_max, updates_all = tot_ms, float(updates)
+    tot_ms_max, updates_all = over_ranks(dist if world > 1 else None, "cuda", tot_ms, updates)
 
     ttg = time_to_gap_ms(trace, init_ms[-1], g["E_star"]) if g else None
 
@@ -519,14 +526,8 @@ def main():
                             "rel_gap_final": (E - g["E_star"]) / g["E_star"] if g else None}
             sweep[str(M)] = best
     capi.csc_destroy(h)
-    if world > 1:
-        t = torch.tensor([e2e_t], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        u = torch.tensor([e2e_u], dtype=torch.float64, device="cuda")
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        e2e_value = float(u.item()) / float(t.item())
-    else:
-        e2e_value = e2e_u / e2e_t
+    e2e_t_max, e2e_u_all = over_ranks(dist if world > 1 else None, "cuda", e2e_t, e2e_u)
+    e2e_value = e2e_u_all / e2e_t_max
 
     if rank != 0:
         dist.destroy_process_group() if world > 1 else None
