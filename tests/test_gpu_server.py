@@ -216,3 +216,37 @@ def test_stream_driver_small(capi):
         # the stream stops at max |Delta Z| < 1e-3; its accuracy target is a
         # relative objective gap of at most 1e-4
         assert -1e-9 <= (E - Er) / Er <= 1e-4
+
+
+def test_server_fair_share_while_others_wait(capi):
+    # dictionary 0 queues more than the whole pool; dictionary 1 queues one
+    # request: while dictionary 1 waits, dictionary 0 may hold at most half
+    Ds = dictionaries()
+    D0, D1 = Ds[0], Ds[1]
+    T = 40_000
+    per0 = 4 * (D0.shape[1] * T + 3 * D0.shape[0] * (T - D0.shape[2] + 1)) + 4096
+    budget = int(4.5 * per0)
+    srv = capi.csc_server_create(hbm_budget_bytes=budget)
+    try:
+        d0 = capi.csc_server_add_dictionary(srv, D0)
+        d1 = capi.csc_server_add_dictionary(srv, D1)
+        a = [capi.csc_server_submit(srv, d0, problem(D0, T, seed=800 + i).X, -0.1, 1e-3)
+             for i in range(6)]
+        b = capi.csc_server_submit(srv, d1, problem(D1, 5000, seed=810).X, -0.1, 1e-3)
+        capi.csc_server_step(srv)
+        held0 = sum(capi.csc_server_info(srv, r)["device_bytes"] for r in a)
+        assert capi.csc_server_info(srv, b)["state"] != capi.CSC_REQ_QUEUED
+        assert held0 <= budget // 2
+        # finished requests release their memory when fetched
+        left = a + [b]
+        for _ in range(100_000):
+            if not left:
+                break
+            capi.csc_server_step(srv)
+            for r in list(left):
+                if capi.csc_server_info(srv, r)["state"] == capi.CSC_REQ_DONE:
+                    assert capi.csc_server_fetch(srv, r)["converged"] == 1
+                    left.remove(r)
+        assert not left
+    finally:
+        capi.csc_server_destroy(srv)
