@@ -277,18 +277,29 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         __syncthreads();
         fence_after_sync();
         if (tid == 0) {
-            // products hh, hm, mh, hl, lh, mm (mode 2: hh only)
-            const int pa[6] = {0, 0, 1, 0, 2, 1}, pb[6] = {0, 1, 0, 2, 0, 1};
-            const int nprod = mode == 2 ? 1 : 6;
+            // products hh, hm, mh, hl, lh, mm (mode 2: hh only), small terms first.
+            // Descriptors differ only in their start address (16-byte units in
+            // the low 14 bits, smem addresses < 256 KB): base descriptors plus
+            // offsets.
+            const uint64_t ad0 = mma_desc(a_base, 128, 128), bd0 = mma_desc(b_base, 128, 256);
+            const uint32_t a_split = (uint32_t)(P * lay.NQ * 128) >> 4;
+            const uint32_t b_split = (uint32_t)(lay.nsteps * (N / 8) * 256) >> 4;
             uint32_t acc = 0;
             for (int s = 0; s < lay.nsteps; s++) {
                 const int p = (16 * s) / lay.L16, q0 = ((16 * s) % lay.L16) / 8;
-                for (int u = nprod - 1; u >= 0; u--) {  // small terms first
-                    const uint32_t aa = a_base + (uint32_t)((((size_t)pa[u] * P + p) * lay.NQ + q0) * 128);
-                    const uint32_t ba = b_base + (uint32_t)(((size_t)pb[u] * lay.nsteps + s) * (N / 8) * 256);
-                    mma_bf16(taddr, mma_desc(aa, 128, 128), mma_desc(ba, 128, 256), idesc, acc);
-                    acc = 1;
+                const uint64_t a_s = ad0 + ((uint32_t)((p * lay.NQ + q0) * 128) >> 4);
+                const uint64_t b_s = bd0 + ((uint32_t)(s * (N / 8) * 256) >> 4);
+                if (mode == 2) {
+                    mma_bf16(taddr, a_s, b_s, idesc, acc);
+                } else {
+                    mma_bf16(taddr, a_s + 1 * a_split, b_s + 1 * b_split, idesc, acc);  // mm
+                    mma_bf16(taddr, a_s + 2 * a_split, b_s, idesc, 1u);                 // lh
+                    mma_bf16(taddr, a_s, b_s + 2 * b_split, idesc, 1u);                 // hl
+                    mma_bf16(taddr, a_s + 1 * a_split, b_s, idesc, 1u);                 // mh
+                    mma_bf16(taddr, a_s, b_s + 1 * b_split, idesc, 1u);                 // hm
+                    mma_bf16(taddr, a_s, b_s, idesc, 1u);                               // hh
                 }
+                acc = 1;
             }
             mma_commit(bar);
         }
