@@ -156,14 +156,14 @@ struct TcLayout {
         xw = kTcM + L16 + 8;  // staged samples per channel
         size_t o = 0;
         a_off = o;
-        o += (size_t)kSplits * P * NQ * 128;
+        o += 2 * (size_t)kSplits * P * NQ * 128;  // two operand buffers
         b_off = o;
         o += (size_t)kSplits * nsteps * (N / 8) * 256;
         x_off = o;
         o += (size_t)P * xw * 4;
         o = (o + 15) & ~(size_t)15;
         bar_off = o;
-        o += 16;
+        o += 16;  // two mbarriers
         total = o;
     }
 };
@@ -186,16 +186,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const long long Tz = T - L + 1;
     const long long ntiles = (Tz + kTcM - 1) / kTcM;
 
-    // ---- tensor memory (N columns) and the MMA-completion barrier ----------
+    // ---- tensor memory (two accumulators of N columns) and two barriers ------
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&s_taddr)),
-                     "r"(N)
+                     "r"(2 * N)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar + 8) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // ---- B: the three BF16 terms of D, per contraction step -----------------
@@ -231,26 +232,29 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     fence_after_sync();
     const uint32_t taddr = s_taddr;
     const uint32_t idesc = mma_idesc(kTcM, N);
+    const size_t a_bytes = (size_t)kSplits * P * lay.NQ * 128;  // one operand buffer
     const uint32_t a_base = smem_u32(As), b_base = smem_u32(Bs);
 
     float amax = 0.f;
     double x2 = 0.0;
-    uint32_t phase = 0;
+    uint32_t phase0 = 0u, phase1 = 0u;  // expected parity of each barrier
     bool ok = true;
-    for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+
+    // stage X of a tile, sum X^2 over its own samples, build its operand run in buffer buf
+    auto build = [&](long long tile, int buf) {
         const long long t0 = tile * kTcM;
         const bool last = tile == ntiles - 1;
-        // ---- stage X[p][t0 .. t0 + xw) (0 beyond T) and sum X^2 over own samples
         for (int i = tid; i < P * lay.xw; i += kTcThreads) {
             const int p = i / lay.xw, jx = i % lay.xw;
             const long long t = t0 + jx;
             const float v = t < T ? X[(long long)p * T + t] : 0.f;
             xs[i] = v;
-            if (t < T && (jx < kTcM || (last && jx < kTcM + L)))
+            if (t < T && (jx < kTcM || last))
                 x2 += (double)v * (double)v;
         }
         __syncthreads();
-        // ---- A: row (sigma, p, q, r) = split sigma of X[p][t0 + 8 q + r + 0..7]
+        // row (sigma, p, q, r) = split sigma of X[p][t0 + 8 q + r + 0..7]
+        unsigned char *Ab = As + (size_t)buf * a_bytes;
         const int rows_a = P * lay.NQ * 8;
         for (int i = tid; i < rows_a; i += kTcThreads) {
             const int r = i & 7, q = (i >> 3) % lay.NQ, p = (i >> 3) / lay.NQ;
@@ -268,57 +272,57 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const size_t off = ((size_t)p * lay.NQ + q) * 128 + (size_t)r * 16;
 #pragma unroll
             for (int sg = 0; sg < kSplits; sg++)
-                *reinterpret_cast<uint4 *>(As + (size_t)sg * P * lay.NQ * 128 + off) =
+                *reinterpret_cast<uint4 *>(Ab + (size_t)sg * P * lay.NQ * 128 + off) =
                     make_uint4(w[sg][0], w[sg][1], w[sg][2], w[sg][3]);
         }
         // make the generic-proxy stores visible to the tensor cores
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        fence_before_sync();
-        __syncthreads();
-        fence_after_sync();
-        if (tid == 0) {
-            // products hh, hm, mh, hl, lh, mm (mode 2: hh only), small terms first.
-            // Descriptors differ only in their start address (16-byte units in
-            // the low 14 bits, smem addresses < 256 KB): base descriptors plus
-            // offsets.
-            const uint64_t ad0 = mma_desc(a_base, 128, 128), bd0 = mma_desc(b_base, 128, 256);
-            const uint32_t a_split = (uint32_t)(P * lay.NQ * 128) >> 4;
-            const uint32_t b_split = (uint32_t)(lay.nsteps * (N / 8) * 256) >> 4;
-            uint32_t acc = 0;
-            for (int s = 0; s < lay.nsteps; s++) {
-                const int p = (16 * s) / lay.L16, q0 = ((16 * s) % lay.L16) / 8;
-                const uint64_t a_s = ad0 + ((uint32_t)((p * lay.NQ + q0) * 128) >> 4);
-                const uint64_t b_s = bd0 + ((uint32_t)(s * (N / 8) * 256) >> 4);
-                if (mode == 2) {
-                    mma_bf16(taddr, a_s, b_s, idesc, acc);
-                } else {
-                    mma_bf16(taddr, a_s + 1 * a_split, b_s + 1 * b_split, idesc, acc);  // mm
-                    mma_bf16(taddr, a_s + 2 * a_split, b_s, idesc, 1u);                 // lh
-                    mma_bf16(taddr, a_s, b_s + 2 * b_split, idesc, 1u);                 // hl
-                    mma_bf16(taddr, a_s + 1 * a_split, b_s, idesc, 1u);                 // mh
-                    mma_bf16(taddr, a_s, b_s + 1 * b_split, idesc, 1u);                 // hm
-                    mma_bf16(taddr, a_s, b_s, idesc, 1u);                               // hh
-                }
-                acc = 1;
+    };
+    // the products of the tile in buffer buf into accumulator buf (thread 0)
+    auto issue = [&](int buf) {
+        if (tid != 0)
+            return;
+        // products hh, hm, mh, hl, lh, mm (mode 2: hh only), small terms first.
+        // Descriptors differ only in their start address (16-byte units in the
+        // low 14 bits, smem addresses < 256 KB): base descriptors plus offsets.
+        const uint32_t d_acc = taddr + (uint32_t)(buf * N);
+        const uint64_t ad0 = mma_desc(a_base + (uint32_t)(buf * a_bytes), 128, 128);
+        const uint64_t bd0 = mma_desc(b_base, 128, 256);
+        const uint32_t a_split = (uint32_t)(P * lay.NQ * 128) >> 4;
+        const uint32_t b_split = (uint32_t)(lay.nsteps * (N / 8) * 256) >> 4;
+        uint32_t acc = 0;
+        for (int s = 0; s < lay.nsteps; s++) {
+            const int p = (16 * s) / lay.L16, q0 = ((16 * s) % lay.L16) / 8;
+            const uint64_t a_s = ad0 + ((uint32_t)((p * lay.NQ + q0) * 128) >> 4);
+            const uint64_t b_s = bd0 + ((uint32_t)(s * (N / 8) * 256) >> 4);
+            if (mode == 2) {
+                mma_bf16(d_acc, a_s, b_s, idesc, acc);
+            } else {
+                mma_bf16(d_acc, a_s + 1 * a_split, b_s + 1 * b_split, idesc, acc);  // mm
+                mma_bf16(d_acc, a_s + 2 * a_split, b_s, idesc, 1u);                 // lh
+                mma_bf16(d_acc, a_s, b_s + 2 * b_split, idesc, 1u);                 // hl
+                mma_bf16(d_acc, a_s + 1 * a_split, b_s, idesc, 1u);                 // mh
+                mma_bf16(d_acc, a_s, b_s + 1 * b_split, idesc, 1u);                 // hm
+                mma_bf16(d_acc, a_s, b_s, idesc, 1u);                               // hh
             }
-            mma_commit(bar);
+            acc = 1;
         }
-        // ---- wait for the products (bounded), then read the accumulator ----
+        mma_commit(bar + 8u * (uint32_t)buf);
+    };
+    // bounded wait for the products into accumulator buf
+    auto wait = [&](int buf) -> bool {
+        uint32_t &ph = buf ? phase1 : phase0;
         unsigned n = 0;
-        while (!mbar_try_wait(bar, phase))
-            if (++n >= kWaitLimit) {
-                ok = false;
-                break;
-            }
-        phase ^= 1u;
-        if (!ok) {
-            if (tid == 0)
-                atomicExch(err, 1);
-            break;
-        }
-        fence_after_sync();
-        const long long t = t0 + 32 * warp + lane;
-        const uint32_t lane_addr = taddr + ((uint32_t)(32 * warp) << 16);
+        while (!mbar_try_wait(bar + 8u * (uint32_t)buf, ph))
+            if (++n >= kWaitLimit)
+                return false;
+        ph ^= 1u;
+        return true;
+    };
+    // accumulator buf -> beta0 columns of the tile
+    auto epilogue = [&](long long tile, int buf) {
+        const long long t = tile * kTcM + 32 * warp + lane;
+        const uint32_t lane_addr = taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)(buf * N);
 #pragma unroll
         for (int c = 0; c < N; c += 32) {
             float v[32];
@@ -334,10 +338,33 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
             }
         }
-        // all lanes read before the next tile's products overwrite the accumulator
+    };
+
+    // Two-stage pipeline over this CTA's tiles: the operands of tile i are
+    // built, and the accumulator of tile i-1 read out, while the products of
+    // the neighbouring tile run on the tensor cores.
+    const long long cnt = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    for (long long i = 0; i <= cnt && cnt > 0; i++) {
+        if (i < cnt)
+            build(blockIdx.x + i * gridDim.x, (int)(i & 1));
+        // operands of tile i visible; every thread has read accumulator (i & 1)
+        // (tile i-2) before it is overwritten
         fence_before_sync();
         __syncthreads();
         fence_after_sync();
+        if (i > 0) {
+            ok = wait((int)((i - 1) & 1));
+            if (!ok) {
+                if (tid == 0)
+                    atomicExch(err, 1);
+                break;
+            }
+            fence_after_sync();
+        }
+        if (i < cnt)
+            issue((int)(i & 1));
+        if (i > 0)
+            epilogue(blockIdx.x + (i - 1) * gridDim.x, (int)((i - 1) & 1));
     }
     for (int off = 16; off > 0; off >>= 1) {
         amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
@@ -351,7 +378,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     __syncthreads();
     fence_after_sync();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(N)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr),
+                     "r"(2 * N)
                      : "memory");
 }
 
