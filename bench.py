@@ -303,8 +303,9 @@ def batch_leg(args, capi, torch):
                 res = {"tol": tol, "ms": ms, "max_rel_gap": gap, "updates": ups,
                        "updates_per_s": ups / (ms * 1e-3), "status": status}
                 break
-        ms6, Es6, ups6, st6 = fn(1e-6) if res is None or res["tol"] != 1e-6 else (
-            res["ms"], None, res["updates"], res["status"])
+        ms6, Es6, ups6, st6 = min((fn(1e-6) for _ in range(2)), key=lambda r: r[0]) \
+            if res is None or res["tol"] != 1e-6 else (res["ms"], None, res["updates"],
+                                                         res["status"])
         out[name] = {"time_to_gap": res, "converged_tol_1e-6_ms": ms6,
                      "converged_updates": ups6}
     if out["batched"]["time_to_gap"] and out["plain"]["time_to_gap"]:

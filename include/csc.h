@@ -86,8 +86,9 @@ typedef struct csc_opts {
                                   CTAs fit on an SM (shared memory grows with P * L), else
                                   mode 3.  Modes 1-2 need K <= 64; other sizes use mode 3 */
     int32_t launch_mode;       /* 0 = each poll batch (sweeps_per_poll sweeps of the c phases)
-                                  is replayed from a CUDA graph captured once per handle
-                                  and plan; 1 = direct kernel launches.  Same results */
+                                  is replayed from a CUDA graph, captured the second time a
+                                  plan is solved (a plan solved once runs direct launches);
+                                  1 = direct kernel launches.  Same results */
     int32_t reserved[1];       /* must be zero */
 } csc_opts;
 

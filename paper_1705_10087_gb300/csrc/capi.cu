@@ -169,7 +169,7 @@ struct csc_handle_s {
     // the poll batch (S sweeps of c phases) captured as a CUDA graph, and what
     // it was captured for
     cudaGraphExec_t gexec = nullptr;
-    std::vector<unsigned char> gkey;
+    std::vector<unsigned char> gkey, gkey_seen;
     cudaStream_t cap_stream = nullptr;  // captures happen here (not on a legacy stream)
     float *tile_rep = nullptr;  // stored resync report per resync tile
     size_t cap_tile_rep = 0;
@@ -359,6 +359,13 @@ int batch_graph(csc_handle_t h, const PhaseParams &pp, const PhaseConfig &cfg, i
         append_bytes(key, o);
     if (h->gexec && key == h->gkey) {
         *out = h->gexec;
+        return CSC_OK;
+    }
+    // a plan is captured the second time it is solved: a one-off plan (a new
+    // signal length every solve) runs direct launches and pays no capture
+    if (key != h->gkey_seen) {
+        h->gkey_seen = key;
+        *out = nullptr;
         return CSC_OK;
     }
     if (h->gexec) {
@@ -810,8 +817,10 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
         int rc = batch_graph(h, pp, cfg, S, resident, sc->gctr, &gexec);
         if (rc != CSC_OK)
             return rc;
-        CSC_CUDA(launch_set_int(sc->gctr, 0, s));
-        h->launches += 1;
+        if (gexec) {
+            CSC_CUDA(launch_set_int(sc->gctr, 0, s));
+            h->launches += 1;
+        }
     }
     for (;;) {
         const int64_t g_round = g;

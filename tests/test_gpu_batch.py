@@ -323,16 +323,20 @@ def test_graph_replay_equals_direct_launches(capi, long_refs):
 
 
 def test_graph_is_captured_once_per_plan(capi, long_refs):
+    # the first solve of a plan runs direct launches, the second captures the
+    # graph, later ones replay it; every solve computes the same
     D, Xs, lams, refs = long_refs
     X, T = batch.pack(Xs)
     h = capi.csc_setup(cuda(D), capi.make_opts(updates_per_visit=24))
     try:
-        launches = []
-        for _ in range(3):
+        launches, Es = [], []
+        for _ in range(4):
             capi.csc_init_batch(h, cuda(X), T, lams)
             status, E, st = capi.csc_solve(h, 1e-6)
             assert status == 0
             launches.append(st["kernel_launches"])
+            Es.append(E)
     finally:
         capi.csc_destroy(h)
-    assert launches[0] == launches[1] == launches[2]
+    assert Es[0] == Es[1] == Es[2] == Es[3]
+    assert launches[1] == launches[2] == launches[3]
