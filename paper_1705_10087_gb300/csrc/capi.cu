@@ -641,7 +641,7 @@ int csc_init_batch(csc_handle_t h, const float *X, const int64_t *T, int n, cons
                                        sizeof(float) * (h->L - 1), h->K, s));
         CSC_CUDA(cudaMemsetAsync(h->sc->red, 0, sizeof(h->sc->red), s));
         CSC_CUDA(launch_resync(h->d_sig, h->resync_tiles(), h->C, h->norms, h->K, h->L, 1,
-                               h->sc->red, 0, nullptr, nullptr, 0.f, nullptr, nullptr, s));
+                               h->sc->red, 0, nullptr, 0.f, nullptr, nullptr, s));
     } else {
         CSC_CUDA(cudaMemsetAsync(h->Z, 0, sizeof(float) * nz, s));
         CSC_CUDA(cudaMemcpyAsync(h->r, h->beta0, sizeof(float) * nz, cudaMemcpyDeviceToDevice, s));
@@ -925,7 +925,7 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
         if (round_done)
             CSC_CUDA(cudaMemsetAsync(h->dirty, 0, (size_t)M, s));
         CSC_CUDA(launch_resync(h->d_sig, h->resync_tiles(), h->C, h->norms, h->K, h->L, 1,
-                               sc->red, 0, h->dirty, h->d_seg_s, tol_inner, h->touched, h->tile_rep,
+                               sc->red, 0, h->dirty, tol_inner, h->touched, h->tile_rep,
                                s));
         CSC_CUDA(cudaMemsetAsync(h->touched, 0, (size_t)M, s));
         h->launches += 1;
@@ -950,7 +950,7 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
         // optimality report against a fresh r, leaving r unchanged
         CSC_CUDA(cudaMemsetAsync(sc->red, 0, sizeof(sc->red), s));
         CSC_CUDA(launch_resync(h->d_sig, h->resync_tiles(), h->C, h->norms, h->K, h->L, 0,
-                               sc->red, 0, nullptr, h->d_seg_s, 0.f, h->touched, h->tile_rep, s));
+                               sc->red, 0, nullptr, 0.f, h->touched, h->tile_rep, s));
         h->launches += 1;
     }
     CSC_CUDA(cudaEventRecord(h->ev1, s));

@@ -105,21 +105,6 @@ struct KahanF {
     __device__ __forceinline__ float value() const { return __fsub_rn(s, c); }
 };
 
-// Index of the interval holding x in a sorted array of n+1 boundaries:
-// the largest i in [0, n) with a[i] <= x (a[0] <= x < a[n] assumed).
-__host__ __device__ __forceinline__ int interval_of(const int64_t *a, int n, int64_t x)
-{
-    int lo = 0, hi = n;  // a[lo] <= x < a[hi]
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (a[mid] <= x)
-            lo = mid;
-        else
-            hi = mid;
-    }
-    return lo;
-}
-
 // One problem of a batch: its own activation arrays, row-major [K][ld] (atom
 // k's row at r + k * ld), valid columns [0, Tz), samples X [P][ldx] with
 // T = Tz + L - 1 of them, and its segments [seg0, seg0 + nseg) of the plan.
@@ -245,17 +230,17 @@ cudaError_t launch_dtx_tc(const float *D, const float *X, int K, int P, int L, i
 // nonzero_gap, max_delta_z, and the largest coord_step change on the float
 // state; with red_stride > 0, problem i reduces into red[i * red_stride + q]
 // instead.  With dirty != NULL, also marks dirty[m] = 1 for every segment m
-// (bounds seg_s, local to the problem) that holds a coordinate whose
-// coord_step change on the new state is >= tol_mark (tol_mark < 0: the
-// problem's own tol).
+// (the problem's segments are the equal cut of seg_start, found with
+// segment_of) that holds a coordinate whose coord_step change on the new state
+// is >= tol_mark (tol_mark < 0: the problem's own tol).
 // With touched != NULL (per segment: r changed there since r was last exact)
 // a tile whose columns meet no touched segment is not recomputed: its r is
 // already exact, and its report values are the ones stored in rep[5 b..5 b+4]
 // when it was last computed (every computed tile stores them when rep != NULL).
 cudaError_t launch_resync(const SigDesc *sig, Tiles tiles, const float *C, const float *norms,
                           int K, int L, int write_r, unsigned long long *red, int red_stride,
-                          unsigned char *dirty, const int64_t *seg_s, float tol_mark,
-                          const unsigned char *touched, float *rep, cudaStream_t s);
+                          unsigned char *dirty, float tol_mark, const unsigned char *touched,
+                          float *rep, cudaStream_t s);
 
 // out = r + n Z (beta of Sec. 2.1) in float, over one [K][ld] array.
 cudaError_t launch_beta_from_r(const float *r, const float *Z, const float *norms, int K,

@@ -97,9 +97,8 @@ __global__ void __launch_bounds__(kResyncThreads)
     resync_kernel(const SigDesc *__restrict__ sigs, Tiles tiles, const float *__restrict__ C,
                   const float *__restrict__ norms, int K, int L, int write_r,
                   unsigned long long *__restrict__ red, int red_stride,
-                  unsigned char *__restrict__ dirty, const int64_t *__restrict__ seg_s,
-                  float tol_mark, const unsigned char *__restrict__ touched,
-                  float *__restrict__ rep)
+                  unsigned char *__restrict__ dirty, float tol_mark,
+                  const unsigned char *__restrict__ touched, float *__restrict__ rep)
 {
     __shared__ NZ list[32 * kChunk];
     __shared__ int warp_counts[32];
@@ -387,11 +386,11 @@ __global__ void beta_from_r_kernel(const float *__restrict__ r, const float *__r
 template <int KPT>
 cudaError_t resync_launch(const SigDesc *sig, Tiles tiles, const float *C, const float *norms,
                           int K, int L, int write_r, unsigned long long *red, int red_stride,
-                          unsigned char *dirty, const int64_t *seg_s, float tol_mark,
-                          const unsigned char *touched, float *rep, cudaStream_t s)
+                          unsigned char *dirty, float tol_mark, const unsigned char *touched,
+                          float *rep, cudaStream_t s)
 {
     resync_kernel<KPT><<<(unsigned)tiles.n, kResyncThreads, 0, s>>>(
-        sig, tiles, C, norms, K, L, write_r, red, red_stride, dirty, seg_s, tol_mark, touched, rep);
+        sig, tiles, C, norms, K, L, write_r, red, red_stride, dirty, tol_mark, touched, rep);
     return cudaGetLastError();
 }
 
@@ -399,14 +398,14 @@ cudaError_t resync_launch(const SigDesc *sig, Tiles tiles, const float *C, const
 
 cudaError_t launch_resync(const SigDesc *sig, Tiles tiles, const float *C, const float *norms,
                           int K, int L, int write_r, unsigned long long *red, int red_stride,
-                          unsigned char *dirty, const int64_t *seg_s, float tol_mark,
-                          const unsigned char *touched, float *rep, cudaStream_t s)
+                          unsigned char *dirty, float tol_mark, const unsigned char *touched,
+                          float *rep, cudaStream_t s)
 {
     if (tiles.n <= 0)
         return cudaSuccess;
     const int kpt = (K + kResyncGroups - 1) / kResyncGroups;
 #define CSC_RESYNC(N) \
-    return resync_launch<N>(sig, tiles, C, norms, K, L, write_r, red, red_stride, dirty, seg_s, \
+    return resync_launch<N>(sig, tiles, C, norms, K, L, write_r, red, red_stride, dirty, \
                             tol_mark, touched, rep, s)
     if (kpt <= 2)
         CSC_RESYNC(2);

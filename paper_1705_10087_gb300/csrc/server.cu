@@ -525,7 +525,7 @@ int resync_ended(csc_server_t s, Group &g)
     SRV_CUDA(cudaMemsetAsync(g.d_red, 0, sizeof(unsigned long long) * kRed * n, g.st));
     const Tiles tiles{g.d_tsig, g.d_tstart, (int64_t)g.t_sig.size()};
     SRV_CUDA(launch_resync(g.d_sig, tiles, g.C, g.norms, g.K, g.L, 1, g.d_red, kRed, g.dirty,
-                           g.d_seg_s, -1.f, nullptr, nullptr, g.st));
+                           -1.f, nullptr, nullptr, g.st));
     count_dirty_kernel<<<n, 256, 0, g.st>>>(g.dirty, g.d_sig, g.d_cnt);
     SRV_CUDA(cudaGetLastError());
     s->launches += 2;
