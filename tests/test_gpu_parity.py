@@ -182,11 +182,12 @@ def test_long_signal_reduced_parity(capi, long_small, M, u):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("M", LONG["segments"])
-def test_long_signal_full_size_parity(capi, long_full, M):
-    # the full long-signal workload, in the launch configuration the benchmark times
+@pytest.mark.parametrize("M,u", [(M, 0) for M in LONG["segments"]] + [(1024, 24)])
+def test_long_signal_full_size_parity(capi, long_full, M, u):
+    # the full long-signal workload over the segment sweep, and in the launch
+    # configuration the benchmark times (M = 1024, 24 updates per visit)
     pb, lam, ref, Er = long_full
-    r = gpu_solve(capi, pb, lam, LONG["tol"], M=M)
+    r = gpu_solve(capi, pb, lam, LONG["tol"], M=M, u=u)
     assert r["status"] == 0, r["stats"]
     assert_parity(r["Z"], r["E"], ref["Z"], Er)
     st = r["stats"]
