@@ -101,6 +101,10 @@ int csc_server_submit(csc_server_t s, int dict, const float *X, int64_t T, doubl
 /* One scheduling round (see above).  Receives the counts after the round. */
 int csc_server_step(csc_server_t s, int *n_active, int *n_queued, int *n_done);
 
+/* Completion queue: up to cap ids of requests that finished (DONE) since the
+ * previous call, in finishing order, into requests[]; *n receives the count. */
+int csc_server_completed(csc_server_t s, int64_t *requests, int cap, int *n);
+
 /* State and statistics of a request (any state). */
 int csc_server_info(csc_server_t s, int64_t request, csc_request_info *info);
 

@@ -136,6 +136,7 @@ def load(path: str | None = None):
     lib.csc_server_step.argtypes = [_vp, ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.csc_server_info.argtypes = [_vp, _i64, ctypes.POINTER(csc_request_info)]
+    lib.csc_server_completed.argtypes = [_vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     lib.csc_server_fetch.argtypes = [_vp, _i64, _vp, ctypes.POINTER(csc_request_info)]
     lib.csc_server_memory.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
                                       ctypes.POINTER(_i64)]
@@ -149,6 +150,7 @@ def load(path: str | None = None):
                  "csc_set_lambda", "csc_lambda_max_batch", "csc_get_objectives",
                  "csc_autotune", "csc_server_create", "csc_server_add_dictionary",
                  "csc_server_submit", "csc_server_step", "csc_server_info", "csc_server_fetch",
+                 "csc_server_completed",
                  "csc_server_memory", "csc_server_kernel_launches", "csc_server_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     if path == _build.LIB:
@@ -363,6 +365,14 @@ def csc_server_step(s):
     a, q, d = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
     _check(load().csc_server_step(s, ctypes.byref(a), ctypes.byref(q), ctypes.byref(d)))
     return a.value, q.value, d.value
+
+
+def csc_server_completed(s, cap: int = 4096) -> list:
+    """Ids of the requests that finished since the previous call."""
+    buf = np.zeros(cap, np.int64)
+    n = ctypes.c_int(0)
+    _check(load().csc_server_completed(s, buf.ctypes.data, cap, ctypes.byref(n)))
+    return [int(x) for x in buf[:n.value]]
 
 
 def csc_server_info(s, req: int) -> dict:

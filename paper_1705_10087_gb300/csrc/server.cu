@@ -242,6 +242,7 @@ struct csc_server_s {
     std::vector<Group> groups;
     std::unordered_map<int64_t, Request> reqs;
     int64_t next_id = 1;
+    std::deque<int64_t> completed;  // finished requests not yet reported by csc_server_completed
     int64_t launches = 0;
     double t0 = 0.0;
     cudaStream_t copy_st = nullptr;  // result copies
@@ -598,6 +599,7 @@ int retire(csc_server_t s, Group &g, double t, int *n_done)
         q.E = g.h_E[j];
         q.state = CSC_REQ_DONE;
         q.t_done = t;
+        s->completed.push_back(q.id);
         gone[i] = 1;
         (*n_done)++;
     }
@@ -864,6 +866,19 @@ int csc_server_step(csc_server_t s, int *n_active, int *n_queued, int *n_done)
         *n_queued = nq;
     if (n_done)
         *n_done = done;
+    return CSC_OK;
+}
+
+int csc_server_completed(csc_server_t s, int64_t *requests, int cap, int *n)
+{
+    if (!s || !n || cap < 0 || (cap > 0 && !requests))
+        return csc_record_error(CSC_EINVAL, "csc_server_completed: bad arguments");
+    int k = 0;
+    while (k < cap && !s->completed.empty()) {
+        requests[k++] = s->completed.front();
+        s->completed.pop_front();
+    }
+    *n = k;
     return CSC_OK;
 }
 

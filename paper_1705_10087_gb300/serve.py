@@ -70,9 +70,7 @@ def run_stream(capi, torch, n_requests: int, seed: int = 0, rate: float | None =
             steps += 1
             if ndone:
                 t_seen = time.perf_counter() - t0
-                for rid in list(ids):
-                    if capi.csc_server_info(srv, rid)["state"] != capi.CSC_REQ_DONE:
-                        continue
+                for rid in capi.csc_server_completed(srv):
                     i = ids.pop(rid)
                     pb = sources[int(sch["dict"][i])]
                     nzc = pb.K * (int(sch["T"][i]) - pb.L + 1)

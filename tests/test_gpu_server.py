@@ -141,20 +141,31 @@ def test_server_admission_respects_budget(capi):
         d = capi.csc_server_add_dictionary(srv, D)
         pbs = [problem(D, T, seed=700 + i) for i in range(5)]
         ids = [capi.csc_server_submit(srv, d, pb.X, -0.1, 1e-6) for pb in pbs]
+        submitted = list(ids)
+        reported = []
         seen_active = 0
         for _ in range(100_000):
             a, q, n = capi.csc_server_step(srv)
             seen_active = max(seen_active, a)
             mem = capi.csc_server_memory(srv)
             assert mem["in_use"] <= budget
-            for rid in ids:
+            # the completion queue reports each finished request once
+            done = capi.csc_server_completed(srv, cap=1)
+            done += capi.csc_server_completed(srv)
+            for rid in done:
+                assert capi.csc_server_info(srv, rid)["state"] == capi.CSC_REQ_DONE
+                reported.append(rid)
+            for rid in list(ids):
                 if capi.csc_server_info(srv, rid)["state"] == capi.CSC_REQ_DONE:
+                    assert rid in reported
                     Z, info = fetch(capi, srv, rid, K, T - L + 1)
                     ids.remove(rid)
                     break
             if not ids:
                 break
         assert not ids
+        assert sorted(reported) == sorted(submitted) and len(set(reported)) == len(reported)
+        assert capi.csc_server_completed(srv) == []
         assert seen_active == 2
         assert capi.csc_server_memory(srv)["in_use"] == 0
     finally:
