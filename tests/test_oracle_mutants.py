@@ -25,6 +25,8 @@ PINS = [
     pins.test_matches_fista_optimum,
     pins.test_matches_exhaustive_lasso,
     pins.test_kkt_at_solution,
+    pins.test_segments_partition_and_phases_are_disjoint,
+    pins.test_single_segment_equals_greedy_trajectory,
 ]
 
 MUTANTS = {
@@ -45,6 +47,13 @@ MUTANTS = {
         "acc += (double)D[((i64)k * P + p) * L + tau] * (double)X[(i64)p * T + t + tau];",
         "acc += (double)D[((i64)k * P + p) * L + tau] * (double)X[(i64)p * T + t + L - 1 - tau];"),
     "threshold_not_shrunk": ("double a = fabs(u) - lam;", "double a = fabs(u) - 0.5 * lam;"),
+    "segment_start_truncated": ("return (i64)m * Tz / M;", "return (i64)m * (Tz / M);"),
+    "phase_count_one_short": ("i64 c = 1 + (need + wmin - 1) / wmin;",
+                              "i64 c = (need + wmin - 1) / wmin;"),
+    "argmax_keeps_first_coordinate": ("if (d > best) {", "if (d > best && best < 0.0) {"),
+    "schedule_skips_last_segment": ("for (int m = p; m < M && !stop; m += c)",
+                                    "for (int m = p; m < M - 1 && !stop; m += c)"),
+    "random_never_picks_last_segment": ("% (uint64_t)M);", "% (uint64_t)(M > 1 ? M - 1 : 1));"),
 }
 
 
