@@ -278,6 +278,20 @@ int csc_plan(int64_t Tz, int L, int M, int *M_out, int *phases, int64_t *starts)
 int csc_objective_noalloc(const float *D, int K, int P, int L, const float *X, int64_t T,
                           const float *Z, double lambda, double *E_out, void *stream);
 
+/*
+ * Failure detection check.  Every device-side wait of this library (the
+ * tensor-core beta0 kernel's mbarrier waits) is a bounded poll: when it gives
+ * up, the kernel sets an error flag, stops issuing work, waits (bounded) for
+ * the work already issued, releases tensor memory and returns, and the call
+ * returns CSC_ETIMEOUT with the device still usable.  This entry runs that
+ * wait in a one-warp kernel on an mbarrier that nothing arrives at, limited to
+ * `polls` polls (1 .. 2^22), on the current device and the legacy default
+ * stream (synchronous).  Expected result: CSC_ETIMEOUT (the wait gave up and
+ * the kernel returned).  CSC_OK would mean the barrier completed; CSC_EINVAL
+ * for polls out of range; CSC_ECUDA / CSC_ENOMEM on a CUDA error.
+ */
+int csc_check_wait_timeout(int64_t polls);
+
 /* Number of kernels launched through this handle since it was created. */
 int csc_kernel_launches(csc_handle_t h, int64_t *out);
 

@@ -120,6 +120,7 @@ def load(path: str | None = None):
     lib.csc_plan.argtypes = [_i64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                              ctypes.POINTER(ctypes.c_int), _vp]
     lib.csc_kernel_launches.argtypes = [_vp, ctypes.POINTER(_i64)]
+    lib.csc_check_wait_timeout.argtypes = [_i64]
     lib.csc_objective_noalloc.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp,
                                           _i64, _vp, ctypes.c_double, _vp, _vp]
     lib.csc_init_batch.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, _vp]
@@ -150,7 +151,7 @@ def load(path: str | None = None):
                  "csc_set_lambda", "csc_lambda_max_batch", "csc_get_objectives",
                  "csc_autotune", "csc_server_create", "csc_server_add_dictionary",
                  "csc_server_submit", "csc_server_step", "csc_server_info", "csc_server_fetch",
-                 "csc_server_completed",
+                 "csc_server_completed", "csc_check_wait_timeout",
                  "csc_server_memory", "csc_server_kernel_launches", "csc_server_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     if path == _build.LIB:
@@ -320,6 +321,11 @@ def csc_kernel_launches(h) -> int:
     v = _i64(0)
     _check(load().csc_kernel_launches(h, ctypes.byref(v)))
     return v.value
+
+
+def csc_check_wait_timeout(polls: int) -> int:
+    """Raw status of the bounded-wait check (CSC_ETIMEOUT expected), no raise."""
+    return int(load().csc_check_wait_timeout(int(polls)))
 
 
 def csc_plan(Tz: int, L: int, M: int = 0):

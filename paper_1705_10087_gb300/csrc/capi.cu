@@ -1100,6 +1100,27 @@ int csc_autotune(csc_handle_t h, double tol, int64_t max_updates, csc_tune_resul
     return CSC_OK;
 }
 
+int csc_check_wait_timeout(int64_t polls)
+{
+    if (polls < 1 || polls > (int64_t)1 << 22)
+        return fail(CSC_EINVAL, "csc_check_wait_timeout: polls must be in [1, 2^22]");
+    int *d = nullptr;
+    CSC_CUDA(cudaMalloc(&d, sizeof(int)));
+    int gave_up = 0;
+    cudaError_t e = cudaMemset(d, 0, sizeof(int));
+    if (e == cudaSuccess)
+        e = launch_wait_selftest((unsigned)polls, d, 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(&gave_up, d, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess)
+        return fail(CSC_ECUDA, "csc_check_wait_timeout: %s", cudaGetErrorString(e));
+    if (gave_up)
+        return fail(CSC_ETIMEOUT, "csc_check_wait_timeout: the bounded wait gave up after %lld polls",
+                    (long long)polls);
+    return CSC_OK;
+}
+
 int csc_kernel_launches(csc_handle_t h, int64_t *out)
 {
     if (!h || !out)

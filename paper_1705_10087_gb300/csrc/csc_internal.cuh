@@ -218,6 +218,9 @@ inline bool dtx_tc_preferred(int K, int P, int L)
 cudaError_t launch_dtx_any(const float *D, const float *X, int K, int P, int L, int64_t T,
                            int init_mode, float *beta0, unsigned int *absmax_bits, double *x2sum,
                            int *err, cudaStream_t s);
+// One warp waits, bounded by `limit` polls, on an mbarrier nothing arrives
+// at, and sets *gave_up when the wait gives up.
+cudaError_t launch_wait_selftest(unsigned limit, int *gave_up, cudaStream_t s);
 cudaError_t launch_dtx_tc(const float *D, const float *X, int K, int P, int L, int64_t T,
                           int mode, float *beta0, unsigned int *absmax_bits, double *x2sum,
                           int *err, cudaStream_t s);

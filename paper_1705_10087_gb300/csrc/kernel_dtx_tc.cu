@@ -28,8 +28,9 @@
 // of the 4 warps reads its 32 lanes with tcgen05.ld and writes beta0[k][t]
 // coalesced along t.
 //
-// Waits are bounded: a wait that gives up sets *err and the kernel stops
-// issuing work; tensor memory is always released.
+// Waits are bounded: a wait that gives up sets *err, the block stops issuing
+// work, waits (again bounded) for the products already issued and releases
+// tensor memory.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -97,6 +98,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
         : "r"(bar), "r"(parity)
         : "memory");
     return ok != 0;
+}
+
+// True once phase `parity` of the barrier has completed; false after `limit`
+// unsuccessful polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, unsigned limit)
+{
+    for (unsigned n = 0; n < limit; n++)
+        if (mbar_try_wait(bar, parity))
+            return true;
+    return false;
 }
 
 __device__ __forceinline__ void fence_before_sync()
@@ -238,7 +249,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     float amax = 0.f;
     double x2 = 0.0;
     uint32_t phase0 = 0u, phase1 = 0u;  // expected parity of each barrier
-    bool ok = true;
 
     // stage X of a tile, sum X^2 over its own samples, build its operand run in buffer buf
     auto build = [&](long long tile, int buf) {
@@ -309,16 +319,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         mma_commit(bar + 8u * (uint32_t)buf);
     };
-    // bounded wait for the products into accumulator buf
-    auto wait = [&](int buf) -> bool {
-        uint32_t &ph = buf ? phase1 : phase0;
-        unsigned n = 0;
-        while (!mbar_try_wait(bar + 8u * (uint32_t)buf, ph))
-            if (++n >= kWaitLimit)
-                return false;
-        ph ^= 1u;
-        return true;
-    };
     // accumulator buf -> beta0 columns of the tile
     auto epilogue = [&](long long tile, int buf) {
         const long long t = tile * kTcM + 32 * warp + lane;
@@ -353,12 +353,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         __syncthreads();
         fence_after_sync();
         if (i > 0) {
-            ok = wait((int)((i - 1) & 1));
-            if (!ok) {
+            // bounded wait for the products of tile i-1; giving up is the
+            // block's decision, so every thread leaves the loop together
+            const uint32_t b = (uint32_t)((i - 1) & 1);
+            uint32_t &ph = b ? phase1 : phase0;
+            const bool got = mbar_wait_bounded(bar + 8u * b, ph, kWaitLimit);
+            if (__syncthreads_or(!got)) {
                 if (tid == 0)
                     atomicExch(err, 1);
+                // those products still write accumulator b: let them finish
+                // (again bounded) before tensor memory is released
+                if (!got)
+                    mbar_wait_bounded(bar + 8u * b, ph, kWaitLimit);
                 break;
             }
+            ph ^= 1u;
             fence_after_sync();
         }
         if (i < cnt)
@@ -383,7 +392,30 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                      : "memory");
 }
 
+// Failure-detection check of the bounded wait: one warp waits, with the
+// wait the kernel above uses, on an mbarrier that nothing arrives at.  The
+// wait gives up after `limit` polls, *gave_up is set, and the kernel returns.
+__global__ void wait_selftest_kernel(unsigned limit, int *gave_up)
+{
+    __shared__ __align__(8) unsigned long long mb;
+    const uint32_t bar = smem_u32(&mb);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool got = mbar_wait_bounded(bar, 0u, limit);
+    if (__syncthreads_or(!got) && threadIdx.x == 0)
+        atomicExch(gave_up, 1);
+}
+
 }  // namespace
+
+cudaError_t launch_wait_selftest(unsigned limit, int *gave_up, cudaStream_t s)
+{
+    wait_selftest_kernel<<<1, 32, 0, s>>>(limit, gave_up);
+    return cudaGetLastError();
+}
 
 size_t dtx_tc_smem(int K, int P, int L)
 {

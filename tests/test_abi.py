@@ -78,6 +78,9 @@ def test_argument_validation_needs_no_device(lib):
     assert lib.csc_solve(None, 1e-6, 10, None, None, None) == capi.CSC_EINVAL
     assert lib.csc_destroy(None) == capi.CSC_OK
     assert "csc_solve" in capi.csc_last_error_string()
+    for polls in (0, -1, (1 << 22) + 1):
+        assert lib.csc_check_wait_timeout(polls) == capi.CSC_EINVAL
+    assert "polls" in capi.csc_last_error_string()
 
 
 def test_default_opts(lib):
