@@ -102,7 +102,11 @@ int csc_server_submit(csc_server_t s, int dict, const float *X, int64_t T, doubl
 int csc_server_step(csc_server_t s, int *n_active, int *n_queued, int *n_done);
 
 /* Completion queue: up to cap ids of requests that finished (DONE) since the
- * previous call, in finishing order, into requests[]; *n receives the count. */
+ * previous call, in finishing order, into requests[]; *n receives the count
+ * (ids beyond cap stay queued for the next call).  Every finished request is
+ * reported exactly once, also when it was fetched before it was reported;
+ * the queue keeps 8 bytes per finished request until it is read.
+ * cap = 0 with requests = NULL only reads nothing (returns *n = 0). */
 int csc_server_completed(csc_server_t s, int64_t *requests, int cap, int *n);
 
 /* State and statistics of a request (any state). */

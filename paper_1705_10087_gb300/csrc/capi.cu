@@ -482,6 +482,7 @@ int csc_destroy(csc_handle_t h)
 int csc_setup(csc_handle_t *hp, const float *D, int K, int P, int L, const csc_opts *opts,
               void *stream)
 {
+    csc::TraceRange trace_("csc_setup");
     if (!hp || !D)
         return fail(CSC_EINVAL, "csc_setup: null handle pointer or D");
     if (K < 1 || K > 256 || P < 1 || L < 1 || L > kMaxL)
@@ -549,6 +550,7 @@ int csc_setup(csc_handle_t *hp, const float *D, int K, int P, int L, const csc_o
 int csc_init_batch(csc_handle_t h, const float *X, const int64_t *T, int n, const double *lambda,
                    const float *Z0)
 {
+    csc::TraceRange trace_("csc_init");
     if (!h || !X || !T || !lambda)
         return fail(CSC_EINVAL, "csc_init: null argument");
     if (n < 1)
@@ -712,6 +714,7 @@ int csc_get_objectives(csc_handle_t h, double *out)
 int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, double *objective,
               csc_stats *stats)
 {
+    csc::TraceRange trace_("csc_solve");
     if (!h)
         return fail(CSC_EINVAL, "csc_solve: null handle");
     if (!h->initialized)
@@ -1002,6 +1005,7 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
 
 int csc_autotune(csc_handle_t h, double tol, int64_t max_updates, csc_tune_result *out)
 {
+    csc::TraceRange trace_("csc_autotune");
     if (!h)
         return fail(CSC_EINVAL, "csc_autotune: null handle");
     if (!h->initialized)
@@ -1166,6 +1170,7 @@ int csc_get_dtd(csc_handle_t h, float *dtd_out, float *norms_out)
 
 int csc_objective(csc_handle_t h, const float *Z, double *out)
 {
+    csc::TraceRange trace_("csc_objective");
     if (!h || !Z || !out)
         return fail(CSC_EINVAL, "csc_objective: null argument");
     if (!h->initialized)

@@ -1,12 +1,23 @@
 // Host-side helpers shared by the C ABI translation units: pointer-kind
-// detection, copies in either direction and growable device buffers.
+// detection, copies in either direction, growable device buffers and NVTX
+// ranges.
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <vector>
 
 namespace csc {
+
+// NVTX range over a scope: names an entry point's host span in a profiler's
+// timeline (a no-op unless a profiler is attached).
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 
 inline bool is_device_pointer(const void *p)
 {

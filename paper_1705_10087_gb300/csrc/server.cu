@@ -741,6 +741,7 @@ int csc_server_create(csc_server_t *sp, const csc_server_opts *opts)
 int csc_server_add_dictionary(csc_server_t s, const float *D, int K, int P, int L,
                               int32_t segment_width, int32_t updates_per_visit, int *dict)
 {
+    csc::TraceRange trace_("csc_server_add_dictionary");
     if (!s || !D || !dict)
         return csc_record_error(CSC_EINVAL, "csc_server_add_dictionary: null argument");
     if (K < 1 || K > 256 || P < 1 || L < 1 || L > kMaxL)
@@ -793,6 +794,7 @@ int csc_server_add_dictionary(csc_server_t s, const float *D, int K, int P, int 
 int csc_server_submit(csc_server_t s, int dict, const float *X, int64_t T, double lambda,
                       double tol, int64_t *request)
 {
+    csc::TraceRange trace_("csc_server_submit");
     if (!s || !X || !request)
         return csc_record_error(CSC_EINVAL, "csc_server_submit: null argument");
     if (dict < 0 || dict >= (int)s->groups.size())
@@ -832,6 +834,7 @@ int csc_server_submit(csc_server_t s, int dict, const float *X, int64_t T, doubl
 
 int csc_server_step(csc_server_t s, int *n_active, int *n_queued, int *n_done)
 {
+    csc::TraceRange trace_("csc_server_step");
     if (!s)
         return csc_record_error(CSC_EINVAL, "csc_server_step: null server");
     cudaSetDevice(s->device);
@@ -910,6 +913,7 @@ int csc_server_info(csc_server_t s, int64_t request, csc_request_info *info)
 
 int csc_server_fetch(csc_server_t s, int64_t request, float *Z_out, csc_request_info *info)
 {
+    csc::TraceRange trace_("csc_server_fetch");
     if (!s)
         return csc_record_error(CSC_EINVAL, "csc_server_fetch: null server");
     auto it = s->reqs.find(request);
