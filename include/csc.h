@@ -236,6 +236,20 @@ int csc_get_dtd(csc_handle_t h, float *dtd_out, float *norms_out);
 int csc_objective(csc_handle_t h, const float *Z, double *out);
 
 /*
+ * Optimality report of an arbitrary Z [K][Tz] (host or device, the layout of
+ * csc_solve's Z_out) for the handle's X and lambda, by coordinate-wise
+ * optimality (Theorem A.1): with beta = D~ * (X - sum_l Z_l * D_l) + ||D_k||^2 Z_k
+ * recomputed from Z (double-float accumulation from the stored D~ * X,
+ * rounded once to float32),
+ *   out[0] = max over Z_k[t] == 0 of |beta_k[t]| - lambda   (floored at 0)
+ *   out[1] = max over Z_k[t] != 0 of |Z_k[t] - Sh(beta_k[t], lambda)/||D_k||^2|
+ *   out[2] = max over all coordinates of the same gap (max |Delta Z|)
+ * out: three doubles, host memory; for a batch, the maxima over its signals.
+ * The handle's state (beta, Z, flags) is not changed.
+ */
+int csc_kkt(csc_handle_t h, const float *Z, double *out);
+
+/*
  * Per-phase trace of the last csc_solve: for phase launch g (0-based, in
  * launch order) the updates it applied, the objective decrease it achieved
  * (sum of Prop. A.1 cost variations, FP64) and the device time in ns of the

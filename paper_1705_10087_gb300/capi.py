@@ -115,6 +115,7 @@ def load(path: str | None = None):
     lib.csc_get_beta.argtypes = [_vp, _vp]
     lib.csc_get_dtd.argtypes = [_vp, _vp, _vp]
     lib.csc_objective.argtypes = [_vp, _vp, ctypes.POINTER(ctypes.c_double)]
+    lib.csc_kkt.argtypes = [_vp, _vp, _vp]
     lib.csc_get_trace.argtypes = [_vp, _i64, _vp, _vp, _vp, ctypes.POINTER(_i64),
                                   ctypes.POINTER(ctypes.c_double)]
     lib.csc_plan.argtypes = [_i64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -285,6 +286,14 @@ def csc_objective(h, Z) -> float:
     v = ctypes.c_double(0.0)
     _check(load().csc_objective(h, _ptr(Z), ctypes.byref(v)))
     return v.value
+
+
+def csc_kkt(h, Z) -> dict:
+    """Optimality report of Z (Theorem A.1) for the handle's X and lambda."""
+    out = np.zeros(3, np.float64)
+    _check(load().csc_kkt(h, _ptr(Z), out.ctypes.data))
+    return {"zero_excess": float(out[0]), "nonzero_gap": float(out[1]),
+            "max_delta_z": float(out[2])}
 
 
 def csc_get_trace(h, cap: int = 1 << 16) -> dict:

@@ -133,6 +133,8 @@ struct csc_handle_s {
     std::vector<SigDesc> sigs;      // [n] descriptors of the signals
     SigDesc *d_sig = nullptr;
     size_t cap_sig = 0;
+    SigDesc *d_sig_alt = nullptr;   // [n] the same over a caller's Z (csc_kkt)
+    size_t cap_sig_alt = 0;
     // objective / absmax tiles (kTile samples) and resync tiles (kResyncCols columns)
     std::vector<int64_t> tile_off;  // [n+1] first objective tile of each signal
     int64_t ntiles = 0, nrtiles = 0;
@@ -459,7 +461,7 @@ int csc_destroy(csc_handle_t h)
                     h->tmpZ,       h->tmpB,       h->sc,         h->d_sig,      h->d_tile_s,
                     h->d_tile_off, h->d_tile_sig, h->d_rtile_s,  h->d_rtile_sig, h->d_E,
                     h->d_lmax,     h->d_seg_s,    h->d_seg_e,    h->d_seg_sig,  h->d_phase_list,
-                    h->touched,    h->tile_rep,   h->d_queue};
+                    h->touched,    h->tile_rep,   h->d_queue,    h->d_sig_alt};
     for (void *p : bufs)
         cudaFree(p);
     if (h->poll)
@@ -1185,6 +1187,44 @@ int csc_objective(csc_handle_t h, const float *Z, double *out)
         Zd = h->tmpZ;
     }
     return objectives(h, Zd, out);
+}
+
+int csc_kkt(csc_handle_t h, const float *Z, double *out)
+{
+    csc::TraceRange trace_("csc_kkt");
+    if (!h || !Z || !out)
+        return fail(CSC_EINVAL, "csc_kkt: null argument");
+    if (!h->initialized)
+        return fail(CSC_ESTATE, "csc_kkt: call csc_init first");
+    cudaSetDevice(h->device);
+    cudaStream_t s = h->stream;
+    const size_t nz = (size_t)h->K * h->Tz;
+    const float *Zd = Z;
+    if (!is_device_pointer(Z)) {
+        CSC_CUDA(grow(&h->tmpZ, &h->cap_tmpZ, nz));
+        CSC_CUDA(cudaMemcpyAsync(h->tmpZ, Z, sizeof(float) * nz, cudaMemcpyHostToDevice, s));
+        Zd = h->tmpZ;
+    }
+    // the problems' descriptors with Z moved to the caller's array (same
+    // layout as the handle's Z); r is only read (write_r = 0), and no segment
+    // flags or stored tile reports are used or changed
+    std::vector<SigDesc> alt(h->sigs);
+    for (SigDesc &d : alt)
+        d.Z = const_cast<float *>(Zd) + (d.Z - h->Z);
+    CSC_CUDA(upload(&h->d_sig_alt, &h->cap_sig_alt, alt, s));
+    CSC_CUDA(cudaMemsetAsync(h->sc->red, 0, sizeof(h->sc->red), s));
+    CSC_CUDA(launch_resync(h->d_sig_alt, h->resync_tiles(), h->C, h->norms, h->K, h->L, 0,
+                           h->sc->red, 0, nullptr, 0.f, nullptr, nullptr, s));
+    h->launches += 1;
+    unsigned long long red[8];
+    CSC_CUDA(cudaMemcpyAsync(red, h->sc->red, sizeof red, cudaMemcpyDeviceToHost, s));
+    CSC_CUDA(cudaStreamSynchronize(s));
+    double v[5];
+    std::memcpy(v, red, sizeof v);
+    out[0] = v[1];
+    out[1] = v[2];
+    out[2] = v[3];
+    return CSC_OK;
 }
 
 int csc_get_trace(csc_handle_t h, int64_t cap, int64_t *updates, double *decrease,

@@ -75,6 +75,8 @@ def test_argument_validation_needs_no_device(lib):
     assert lib.csc_setup(ctypes.byref(h), D.ctypes.data, 2, 1, 4, ctypes.byref(o),
                          None) == capi.CSC_EINVAL
     assert lib.csc_init(None, D.ctypes.data, 10, 1.0, None) == capi.CSC_EINVAL
+    assert lib.csc_kkt(None, D.ctypes.data, D.ctypes.data) == capi.CSC_EINVAL
+    assert "csc_kkt" in capi.csc_last_error_string()
     assert lib.csc_solve(None, 1e-6, 10, None, None, None) == capi.CSC_EINVAL
     assert lib.csc_destroy(None) == capi.CSC_OK
     assert "csc_solve" in capi.csc_last_error_string()

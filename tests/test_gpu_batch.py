@@ -115,6 +115,37 @@ def test_batch_short_signals_match_oracle(capi, short_refs):
     np.testing.assert_allclose(res["lmax"], lmax, rtol=1e-5)
 
 
+def test_kkt_report_of_a_batch(capi, short_refs):
+    """csc_kkt over a batch: each signal against its own lambda and its own
+    columns of the packed Z; the maxima over the signals of the oracle's FP64
+    report per signal."""
+    D, Xs, lams, lmax, refs = short_refs
+    X, T = batch.pack(Xs)
+    L = D.shape[2]
+    Zp = batch.pack_Z([Zr.astype(np.float32) for Zr, _ in refs], L)
+    rng = np.random.default_rng(5)
+    mask = rng.random(Zp.shape) < 0.02
+    mask[:, batch.straddle_mask(T, L)] = False
+    Zp[mask] += rng.standard_normal(int(mask.sum())).astype(np.float32)
+    h = capi.csc_setup(cuda(D))
+    try:
+        capi.csc_init_batch(h, cuda(X), T, lams)
+        got = capi.csc_kkt(h, cuda(Zp))
+    finally:
+        capi.csc_destroy(h)
+    n = oracle.norms(D)
+    want = {"zero_excess": 0.0, "nonzero_gap": 0.0, "max_delta_z": 0.0}
+    scale = 0.0
+    for Xi, lam, Zi in zip(Xs, lams, batch.unpack_Z(Zp, T, L)):
+        B = oracle.beta_fresh(D, Xi, Zi)
+        r = oracle.kkt(B, Zi, n, lam)
+        for key in want:
+            want[key] = max(want[key], r[key])
+        scale = max(scale, float(np.abs(B).max()))
+    for key in want:
+        assert abs(got[key] - want[key]) <= 1e-5 * scale, (key, got[key], want[key])
+
+
 def test_batch_host_pointers(capi, short_refs):
     D, Xs, lams, lmax, refs = short_refs
     res = solve_batch(capi, D, Xs, lams, host=True)

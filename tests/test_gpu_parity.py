@@ -278,6 +278,48 @@ def test_warm_start_from_optimum(capi, short):
     assert_parity(r["Z"], r["E"], ref["Z"], Er)
 
 
+def test_kkt_report_of_any_Z(capi, long_small):
+    """csc_kkt: the optimality report (Theorem A.1) of a caller's Z against the
+    oracle's FP64 report of the same Z, on host and device pointers; of the
+    solve's own Z it is the report the solve returned, and it leaves the
+    handle's state alone."""
+    pb, lam, ref, Er = long_small
+    h = capi.csc_setup(cuda(pb.D), capi.make_opts(segments=64))
+    try:
+        capi.csc_init(h, cuda(pb.X), lam)
+        Zd = torch.zeros((pb.K, pb.Tz), dtype=torch.float32, device="cuda")
+        status, E, st = capi.csc_solve(h, 1e-7, 1 << 40, Zd)
+        b_before = torch.zeros_like(Zd)
+        capi.csc_get_beta(h, b_before)
+        own = capi.csc_kkt(h, Zd)
+        Z = Zd.cpu().numpy()
+        rng = np.random.default_rng(3)
+        Zp = Z.copy()
+        mask = rng.random(Z.shape) < 0.01
+        Zp[mask] += rng.standard_normal(int(mask.sum())).astype(np.float32)
+        pert = capi.csc_kkt(h, Zp)
+        again = capi.csc_kkt(h, Zd)
+        b_after = torch.zeros_like(Zd)
+        capi.csc_get_beta(h, b_after)
+    finally:
+        capi.csc_destroy(h)
+    assert status == 0
+    assert torch.equal(b_before, b_after)
+    assert again == own
+    for key, sk in (("zero_excess", "kkt_zero_excess"), ("nonzero_gap", "kkt_nonzero_gap"),
+                    ("max_delta_z", "max_delta_z")):
+        assert own[key] == pytest.approx(st[sk], rel=1e-6, abs=1e-12)
+    n = oracle.norms(pb.D)
+    for Zc, got in ((Z, own), (Zp, pert)):
+        B = oracle.beta_fresh(pb.D, pb.X, Zc)
+        want = oracle.kkt(B, Zc, n, lam)
+        # beta in float32 from an FP64-accurate residual and the FP32 D~*X
+        tol = 1e-5 * float(np.abs(B).max())
+        for key in want:
+            assert abs(got[key] - want[key]) <= tol, (key, got[key], want[key])
+    assert pert["max_delta_z"] > 1e3 * max(own["max_delta_z"], 1e-9)
+
+
 def test_invalid_arguments_raise(capi):
     D = cuda(synth.make_dictionary(3, 1, 8, seed=0))
     h = capi.csc_setup(D)
