@@ -62,3 +62,19 @@ def test_replicas_solve_distinct_seeds():
     a = synth.make_workload("short_P1_K5_L16_T2000", seed=0)
     b = synth.make_workload("short_P1_K5_L16_T2000", seed=1)
     assert a.X.shape == b.X.shape and not (a.X == b.X).all()
+
+
+def test_time_to_gap_from_the_objective_trace():
+    # E after each launch = E_start - cumulative decrease; the first launch at
+    # which (E - E*) <= 1e-4 E* gives the time, from the last time stamp up to it
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    tr = {"E_start": 10.0, "decrease": np.array([5.0, 3.0, 0.99995, 0.0, 1e-5]),
+          "t_ns": np.array([1_000_000, 2_000_000, 3_000_000, -1, 5_000_000])}
+    assert bench.time_to_gap_ms(tr, 0.5, 1.0) == pytest.approx(3.5)
+    # reached at a launch without a time stamp: the last stamped launch before it
+    tr2 = dict(tr, t_ns=np.array([1_000_000, 2_000_000, -1, -1, 5_000_000]))
+    assert bench.time_to_gap_ms(tr2, 0.0, 1.0) == pytest.approx(2.0)
+    # never within the gap
+    assert bench.time_to_gap_ms(tr, 0.5, 1.0, rel=1e-6) is None
