@@ -27,6 +27,7 @@ PINS = [
     pins.test_kkt_at_solution,
     pins.test_segments_partition_and_phases_are_disjoint,
     pins.test_single_segment_equals_greedy_trajectory,
+    pins.test_kkt_report_at_zero_and_after_one_coordinate,
 ]
 
 MUTANTS = {
@@ -54,6 +55,9 @@ MUTANTS = {
     "schedule_skips_last_segment": ("for (int m = p; m < M && !stop; m += c)",
                                     "for (int m = p; m < M - 1 && !stop; m += c)"),
     "random_never_picks_last_segment": ("% (uint64_t)M);", "% (uint64_t)(M > 1 ? M - 1 : 1));"),
+    "kkt_branches_swapped": ("if (z == 0.0) {\n                double e = fabs(b) - lam;",
+                             "if (z != 0.0) {\n                double e = fabs(b) - lam;"),
+    "kkt_excess_without_abs": ("double e = fabs(b) - lam;", "double e = b - lam;"),
 }
 
 

@@ -227,6 +227,33 @@ def test_kkt_at_solution():
 
 # ---------------------------------------------- Alg. 3 / phase schedule
 
+def test_kkt_report_at_zero_and_after_one_coordinate():
+    # Theorem A.1 at Z = 0: beta = D~*X, so the excess over the zero coordinates
+    # is lambda_max - lambda, there is no nonzero gap, and the largest |Delta Z|
+    # is the step Alg. 1 takes first; flipping X flips beta, not the report.
+    pb = tiny()
+    n = npref.norms(pb.D)
+    lmax = float(np.abs(npref.dtx_fft(pb.D, pb.X)).max())
+    lam = 0.5 * lmax
+    Z0 = np.zeros((pb.K, pb.Tz))
+    first = oracle.greedy_cd(pb.D, pb.X, lam, 1e-12, max_updates=1, trace=1)
+    z1 = float(first["trace"]["z_new"][0])
+    assert z1 != 0.0
+    for X in (pb.X, -pb.X):
+        rep = oracle.kkt(oracle.beta_fresh(pb.D, X, Z0), Z0, n, lam)
+        assert rep["zero_excess"] == pytest.approx(lmax - lam, rel=1e-12)
+        assert rep["nonzero_gap"] == 0.0
+        assert rep["max_delta_z"] == pytest.approx(abs(z1), rel=1e-12)
+    # that coordinate alone set to 3x its optimum: beta there excludes its own
+    # contribution, so its gap is |3 z1 - z1| and it is the only nonzero
+    k, t = int(first["trace"]["k"][0]), int(first["trace"]["t"][0])
+    Z1 = Z0.copy()
+    Z1[k, t] = 3.0 * z1
+    rep = oracle.kkt(oracle.beta_fresh(pb.D, pb.X, Z1), Z1, n, lam)
+    assert rep["nonzero_gap"] == pytest.approx(2.0 * abs(z1), rel=1e-10)
+    assert rep["max_delta_z"] >= rep["nonzero_gap"]
+
+
 def test_single_segment_equals_greedy_trajectory():
     # M = 1: the locally greedy argmax is the global one (Alg. 3 -> Alg. 1)
     pb = tiny(K=3, P=2, L=6, T=90, seed=17)
