@@ -28,6 +28,7 @@ PINS = [
     pins.test_segments_partition_and_phases_are_disjoint,
     pins.test_single_segment_equals_greedy_trajectory,
     pins.test_kkt_report_at_zero_and_after_one_coordinate,
+    pins.test_one_update_per_sweep_reaches_greedy_optimum,
 ]
 
 MUTANTS = {
@@ -58,6 +59,10 @@ MUTANTS = {
     "kkt_branches_swapped": ("if (z == 0.0) {\n                double e = fabs(b) - lam;",
                              "if (z != 0.0) {\n                double e = fabs(b) - lam;"),
     "kkt_excess_without_abs": ("double e = fabs(b) - lam;", "double e = b - lam;"),
+    "l1_without_abs": ("l1 += fabs(Z[i]);", "l1 += Z[i];"),
+    "norm_not_squared": ("                s += d * d;", "                s += fabs(d);"),
+    "schedule_stops_with_one_update_left": ("if (!stop && in_sweep == 0) {",
+                                            "if (!stop && in_sweep <= 1) {"),
 }
 
 

@@ -282,6 +282,18 @@ def test_locally_greedy_reaches_greedy_optimum(M, u):
         assert oracle.objective(pb.D, pb.X, r["Z"], lam) == pytest.approx(Eg, rel=1e-13)
 
 
+def test_one_update_per_sweep_reaches_greedy_optimum():
+    # Theorem conv_dcp with the slowest schedule: one segment, one update per
+    # visit, so every sweep applies a single update until none is left
+    pb = tiny(K=3, P=2, L=6, T=60, seed=29)
+    lam = 0.1 * oracle.lambda_max(pb.D, pb.X)
+    g = oracle.greedy_cd(pb.D, pb.X, lam, 1e-13, max_updates=CAP)
+    r = oracle.locally_greedy_cd(pb.D, pb.X, lam, 1e-13, M=1, mode="phase",
+                                 updates_per_visit=1, max_updates=CAP)
+    assert r["converged"] and r["sweeps"] == r["n_updates"] + 1
+    np.testing.assert_allclose(r["Z"], g["Z"], atol=1e-10)
+
+
 def test_segments_partition_and_phases_are_disjoint():
     # Sec. 2.2 segments; co-active segments' update windows [s-L+1, e+L-1) never meet
     rng = np.random.default_rng(0)
