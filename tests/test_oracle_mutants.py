@@ -63,6 +63,8 @@ MUTANTS = {
     "norm_not_squared": ("                s += d * d;", "                s += fabs(d);"),
     "schedule_stops_with_one_update_left": ("if (!stop && in_sweep == 0) {",
                                             "if (!stop && in_sweep <= 1) {"),
+    "random_mode_trusts_stale_dz": ("if (local_argmax(&s, 0, Tz, &kk, &tt, &zz) < eps) {",
+                                    "if (local_argmax(&s, 0, Tz, &kk, &tt, &zz) < eps || 1) {"),
 }
 
 
