@@ -55,7 +55,9 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true", help="skip the segment-count sweep")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--init-mode", type=int, default=0,
-                    help="beta0 kernel: 0 FP32 compensated, 1 tensor cores (split BF16)")
+                    help="beta0 kernel: 0 automatic (tensor cores where their tile needs at "
+                         "most half the shared memory, else FP32), 1 tensor cores (split BF16), "
+                         "2 one BF16 product, 3 FP32 compensated")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the 512-signal batched-vs-plain comparison")
