@@ -152,7 +152,7 @@ def load(path: str | None = None):
                  "csc_set_lambda", "csc_lambda_max_batch", "csc_get_objectives",
                  "csc_autotune", "csc_server_create", "csc_server_add_dictionary",
                  "csc_server_submit", "csc_server_step", "csc_server_info", "csc_server_fetch",
-                 "csc_server_completed", "csc_check_wait_timeout",
+                 "csc_server_completed", "csc_check_wait_timeout", "csc_kkt",
                  "csc_server_memory", "csc_server_kernel_launches", "csc_server_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     if path == _build.LIB:
@@ -195,11 +195,17 @@ def _stream(stream):
     return torch.cuda.current_stream().cuda_stream
 
 
+def csc_default_opts() -> csc_opts:
+    """The library's default options (every field as include/csc.h documents)."""
+    o = csc_opts()
+    load().csc_default_opts(ctypes.byref(o))
+    return o
+
+
 def make_opts(segments: int = 0, updates_per_visit: int = 0, max_resyncs: int = -1,
               sweeps_per_poll: int = 0, max_sweeps: int = 0, time_kernels: int = 0,
               segment_width: int = 0, init_mode: int = 0, launch_mode: int = 0) -> csc_opts:
-    o = csc_opts()
-    load().csc_default_opts(ctypes.byref(o))
+    o = csc_default_opts()
     o.segments, o.updates_per_visit = segments, updates_per_visit
     o.max_resyncs, o.sweeps_per_poll, o.max_sweeps = max_resyncs, sweeps_per_poll, max_sweeps
     o.time_kernels, o.segment_width, o.init_mode = time_kernels, segment_width, init_mode

@@ -102,3 +102,17 @@ def test_segment_of_closed_form(lib, Tz, L, M):
     t = t[(t >= 0) & (t < Tz)]
     m = ((t + 1) * M - 1) // Tz
     assert np.all(starts[m] <= t) and np.all(t < starts[m + 1])
+
+
+def test_binding_has_every_declared_function(lib):
+    # the Python binding keeps the C names: one wrapper per declared entry point
+    names = set()
+    for h in ("csc.h", "csc_server.h"):
+        src = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                                "include", h)).read()
+        names |= set(re.findall(r"^\s*(?:int|void|const char \*)\s*\**\s*(csc_\w+)\s*\(",
+                                src, re.M))
+    assert len(names) >= 30
+    assert sorted(n for n in names if not callable(getattr(capi, n, None))) == []
+    o = capi.csc_default_opts()
+    assert (o.segments, o.updates_per_visit, o.max_resyncs) == (0, 0, -1)
