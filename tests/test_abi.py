@@ -106,13 +106,27 @@ def test_segment_of_closed_form(lib, Tz, L, M):
 
 def test_binding_has_every_declared_function(lib):
     # the Python binding keeps the C names: one wrapper per declared entry point
-    names = set()
-    for h in ("csc.h", "csc_server.h"):
-        src = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
-                                "include", h)).read()
-        names |= set(re.findall(r"^\s*(?:int|void|const char \*)\s*\**\s*(csc_\w+)\s*\(",
-                                src, re.M))
+    names = declared_functions()
     assert len(names) >= 30
     assert sorted(n for n in names if not callable(getattr(capi, n, None))) == []
     o = capi.csc_default_opts()
     assert (o.segments, o.updates_per_visit, o.max_resyncs) == (0, 0, -1)
+
+
+def test_plain_c99_caller(lib, tmp_path):
+    # include/*.h must be usable from C, not only C++: tests/c_abi_check.c is
+    # compiled as C99 with warnings as errors, linked against libcsc.so and run
+    # (host-only entry points and argument validation need no GPU)
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    libdir = os.path.dirname(build.LIB)
+    exe = tmp_path / "c_abi_check"
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                           "-I", os.path.join(root, "include"),
+                           os.path.join(root, "tests", "c_abi_check.c"), "-L", libdir, "-lcsc",
+                           "-Wl,-rpath," + libdir, "-o", str(exe)])
+    res = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert res.returncode == 0 and res.stdout.strip() == "ok", res.stdout + res.stderr
