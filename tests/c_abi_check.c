@@ -5,6 +5,7 @@
  * the host-only entry points and of argument validation.  Exit status 0 on
  * success; the first failed check is printed.
  */
+#include <stddef.h>
 #include <stdint.h>
 #include <stdio.h>
 #include <string.h>
@@ -20,7 +21,44 @@
         }                                                         \
     } while (0)
 
-int main(void)
+/* "layout": one line per struct, its size then the offset of every field in
+ * declaration order, for the binding's ctypes mirrors to be compared with */
+#define OFF(T, f) (unsigned)offsetof(T, f)
+static void print_layouts(void)
+{
+    printf("csc_opts %u %u %u %u %u %u %u %u %u %u %u\n", (unsigned)sizeof(csc_opts),
+           OFF(csc_opts, segments), OFF(csc_opts, updates_per_visit),
+           OFF(csc_opts, max_resyncs), OFF(csc_opts, sweeps_per_poll),
+           OFF(csc_opts, max_sweeps), OFF(csc_opts, time_kernels),
+           OFF(csc_opts, segment_width), OFF(csc_opts, init_mode), OFF(csc_opts, launch_mode),
+           OFF(csc_opts, reserved));
+    printf("csc_stats %u %u %u %u %u %u %u %u %u %u %u %u %u %u %u %u %u %u\n",
+           (unsigned)sizeof(csc_stats), OFF(csc_stats, updates), OFF(csc_stats, sweeps),
+           OFF(csc_stats, segments), OFF(csc_stats, phases), OFF(csc_stats, resyncs),
+           OFF(csc_stats, converged), OFF(csc_stats, objective), OFF(csc_stats, max_drift),
+           OFF(csc_stats, kkt_zero_excess), OFF(csc_stats, kkt_nonzero_gap),
+           OFF(csc_stats, max_delta_z), OFF(csc_stats, solve_ms), OFF(csc_stats, phase_ms),
+           OFF(csc_stats, phase_launches), OFF(csc_stats, visits),
+           OFF(csc_stats, kernel_launches), OFF(csc_stats, drift_resyncs));
+    printf("csc_tune_result %u %u %u %u %u %u %u\n", (unsigned)sizeof(csc_tune_result),
+           OFF(csc_tune_result, segment_width), OFF(csc_tune_result, updates_per_visit),
+           OFF(csc_tune_result, phases), OFF(csc_tune_result, candidates),
+           OFF(csc_tune_result, best_ms), OFF(csc_tune_result, default_ms));
+    printf("csc_server_opts %u %u %u %u %u %u\n", (unsigned)sizeof(csc_server_opts),
+           OFF(csc_server_opts, hbm_budget_bytes), OFF(csc_server_opts, sweeps_per_step),
+           OFF(csc_server_opts, max_resyncs), OFF(csc_server_opts, max_active),
+           OFF(csc_server_opts, reserved));
+    printf("csc_request_info %u %u %u %u %u %u %u %u %u %u %u %u %u %u %u\n",
+           (unsigned)sizeof(csc_request_info), OFF(csc_request_info, state),
+           OFF(csc_request_info, dict), OFF(csc_request_info, T), OFF(csc_request_info, lambda),
+           OFF(csc_request_info, lambda_max), OFF(csc_request_info, objective),
+           OFF(csc_request_info, max_delta_z), OFF(csc_request_info, resyncs),
+           OFF(csc_request_info, converged), OFF(csc_request_info, rounds),
+           OFF(csc_request_info, device_bytes), OFF(csc_request_info, t_submit),
+           OFF(csc_request_info, t_admit), OFF(csc_request_info, t_done));
+}
+
+int main(int argc, char **argv)
 {
     csc_opts o;
     csc_handle_t h = NULL;
@@ -30,6 +68,10 @@ int main(void)
     float D[2 * 1 * 4];
     double out[3];
 
+    if (argc > 1 && strcmp(argv[1], "layout") == 0) {
+        print_layouts();
+        return 0;
+    }
     memset(&o, 0x7f, sizeof o);
     csc_default_opts(&o);
     CHECK(o.segments == 0 && o.updates_per_visit == 0 && o.max_resyncs == -1);

@@ -130,3 +130,12 @@ def test_plain_c99_caller(lib, tmp_path):
                            "-Wl,-rpath," + libdir, "-o", str(exe)])
     res = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert res.returncode == 0 and res.stdout.strip() == "ok", res.stdout + res.stderr
+    # the binding's ctypes structures have the C layout: size and every offset
+    res = subprocess.run([str(exe), "layout"], capture_output=True, text=True, timeout=120)
+    assert res.returncode == 0, res.stdout + res.stderr
+    for line in res.stdout.strip().splitlines():
+        name, size, *offs = line.split()
+        cls = getattr(capi, name)
+        fields = [f for f, _ in cls._fields_]
+        assert ctypes.sizeof(cls) == int(size), name
+        assert [getattr(cls, f).offset for f in fields] == [int(x) for x in offs], name
