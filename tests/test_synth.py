@@ -1,5 +1,6 @@
 """The seeded input generator: definition, determinism and the recipe of Sec. 4."""
 import numpy as np
+import pytest
 
 from paper_1705_10087_gb300 import synth
 from tests import npref
@@ -77,3 +78,29 @@ def test_gaps_support_problem():
     assert abs(nz - 0.01 * N) < 5 * np.sqrt(0.01 * N)
     amp = pb.Z_true[pb.Z_true != 0]
     assert abs(amp.std() - 1.0) < 0.05 and abs(amp.mean()) < 0.05
+
+
+def test_request_stream_schedule_law():
+    # Poisson arrivals at 200 req/s (exponential gaps: mean 1/rate, CV 1),
+    # dictionary uniform over four, length log-uniform on [5e3, 2e6]
+    name = "serve_4dict_poisson200_T5000_2000000"
+    n = 40_000
+    s = synth.serve_schedule(name, n, seed=0)
+    gaps = np.diff(np.concatenate([[0.0], s["arrival"]]))
+    assert np.all(gaps > 0)
+    assert gaps.mean() == pytest.approx(1 / 200, rel=0.02)
+    assert gaps.std() / gaps.mean() == pytest.approx(1.0, abs=0.03)
+    counts = np.bincount(s["dict"], minlength=4)
+    assert counts.shape == (4,) and np.all(np.abs(counts / n - 0.25) < 0.01)
+    assert s["T"].min() >= 5_000 and s["T"].max() <= 2_000_000
+    u = (np.log(s["T"]) - np.log(5_000)) / (np.log(2_000_000) - np.log(5_000))
+    assert u.mean() == pytest.approx(0.5, abs=0.01)
+    assert np.median(s["T"]) == pytest.approx(1e5, rel=0.05)
+    assert np.all((s["offset_frac"] >= 0) & (s["offset_frac"] < 1))
+    # the same seed gives the same stream; a shorter prefix is a prefix
+    s2 = synth.serve_schedule(name, 100, seed=0)
+    assert np.array_equal(s2["arrival"], s["arrival"][:100])
+    assert np.array_equal(s2["T"], s["T"][:100])
+    # T_max caps lengths without changing arrivals or dictionaries
+    s3 = synth.serve_schedule(name, 100, seed=0, T_max=20_000)
+    assert s3["T"].max() <= 20_000 and np.array_equal(s3["dict"], s2["dict"])
