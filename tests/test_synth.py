@@ -104,3 +104,19 @@ def test_request_stream_schedule_law():
     # T_max caps lengths without changing arrivals or dictionaries
     s3 = synth.serve_schedule(name, 100, seed=0, T_max=20_000)
     assert s3["T"].max() <= 20_000 and np.array_equal(s3["dict"], s2["dict"])
+
+
+def test_stream_sources_same_with_worker_processes():
+    # one recording per dictionary, (K, L, P) as the stream names them; the
+    # spawned worker pool yields exactly the serial result
+    name = "serve_4dict_poisson200_T5000_2000000"
+    a = synth.serve_sources(name, seed=1, T_source=3000)
+    b = synth.serve_sources(name, seed=1, T_source=3000, workers=2)
+    assert [(pb.K, pb.L, pb.P) for pb in a] == [tuple(d) for d in
+                                               synth.SERVE_WORKLOADS[name]["dicts"]]
+    for x, y in zip(a, b):
+        assert np.array_equal(x.D, y.D) and np.array_equal(x.X, y.X)
+        assert x.X.shape == (x.P, 3000)
+        # unit-norm atoms (Sec. 4 recipe)
+        assert np.allclose(np.sqrt((x.D.astype(np.float64) ** 2).sum(axis=(1, 2))), 1.0,
+                           atol=1e-6)
