@@ -139,3 +139,10 @@ def test_plain_c99_caller(lib, tmp_path):
         fields = [f for f, _ in cls._fields_]
         assert ctypes.sizeof(cls) == int(size), name
         assert [getattr(cls, f).offset for f in fields] == [int(x) for x in offs], name
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    # no CPU path: without the built library the binding raises instead of
+    # falling back to anything
+    with pytest.raises(OSError, match="not built"):
+        capi.load(str(tmp_path / "libcsc.so"))
