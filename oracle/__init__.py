@@ -41,12 +41,15 @@ _lp = ctypes.POINTER(ctypes.c_longlong)
 
 
 def build(force: bool = False) -> str:
-    """Compile csc_oracle.c into liboracle.so (plain gcc, no FMA contraction)."""
+    """Compile csc_oracle.c into liboracle.so (plain gcc, no FMA contraction),
+    and the 2-D variant's oracle (csc2d.py) with it."""
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + ".%d.tmp" % os.getpid()
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-std=c11", "-fPIC", "-shared",
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _SO)
+    from . import csc2d
+    csc2d.build(force)
     return _SO
 
 

@@ -142,3 +142,80 @@ def brute_force_lasso(A, x, lam):
         if E < best[1]:
             best = (z, E)
     return best
+
+
+# ------------------------------------------------- 2-D (scipy.signal routines)
+
+def _signal():
+    import scipy.signal
+    return scipy.signal
+
+
+def crosscorr2d(D):
+    """S[k,l,a,b] = sum_p correlate(D_l[p], D_k[p], 'full')[a, b] (scipy.signal)."""
+    sig = _signal()
+    K, P, h, w = D.shape
+    D = D.astype(np.float64)
+    S = np.zeros((K, K, 2 * h - 1, 2 * w - 1))
+    for k in range(K):
+        for l in range(K):
+            for p in range(P):
+                S[k, l] += sig.correlate(D[l, p], D[k, p], mode="full", method="direct")
+    return S
+
+
+def dtx2d(D, X):
+    """beta0[k,i,j] = sum_p sum_{u,v} D[k,p,u,v] X[p,i+u,j+v] (scipy 'valid' correlation)."""
+    sig = _signal()
+    K, P, h, w = D.shape
+    out = None
+    for k in range(K):
+        acc = sum(sig.correlate(X[p].astype(np.float64), D[k, p].astype(np.float64),
+                                mode="valid", method="direct") for p in range(P))
+        if out is None:
+            out = np.zeros((K,) + acc.shape)
+        out[k] = acc
+    return out
+
+
+def residual2d(D, X, Z):
+    """X - sum_k Z_k * D_k with scipy's full 2-D convolution (size H x W)."""
+    sig = _signal()
+    K, P, h, w = D.shape
+    R = X.astype(np.float64).copy()
+    for k in range(K):
+        for p in range(P):
+            R[p] -= sig.convolve2d(Z[k].astype(np.float64), D[k, p].astype(np.float64),
+                                   mode="full")
+    return R
+
+
+def objective2d(D, X, Z, lam):
+    R = residual2d(D, X, Z)
+    return 0.5 * float((R * R).sum()) + lam * float(np.abs(Z).sum())
+
+
+def norms2d(D):
+    return (D.astype(np.float64) ** 2).sum(axis=(1, 2, 3))
+
+
+def beta_fresh2d(D, X, Z):
+    n = norms2d(D)
+    return dtx2d(D, residual2d(D, X, Z)) + n[:, None, None] * Z
+
+
+def operator2d(D, H, W):
+    """Dense matrix of Z -> vec(sum_k Z_k * D_k), shape (P*H*W, K*Hz*Wz)."""
+    sig = _signal()
+    K, P, h, w = D.shape
+    Hz, Wz = H - h + 1, W - w + 1
+    A = np.zeros((P * H * W, K * Hz * Wz))
+    for k in range(K):
+        for i in range(Hz):
+            for j in range(Wz):
+                e = np.zeros((Hz, Wz))
+                e[i, j] = 1.0
+                A[:, (k * Hz + i) * Wz + j] = np.concatenate(
+                    [sig.convolve2d(e, D[k, p].astype(np.float64), mode="full").ravel()
+                     for p in range(P)])
+    return A
