@@ -20,6 +20,7 @@ PINS = [
     pins.test_beta_fresh_matches_definition,
     pins.test_greedy_beta_update_matches_fresh_residual,
     pins.test_band_schedule_border_updates_match_fresh_residual,
+    pins.test_each_update_lowers_E_by_prop_A1,
     pins.test_one_row_image_is_the_1d_problem,
     pins.test_transposed_problem_has_transposed_optimum,
     pins.test_matches_fista_optimum,
@@ -47,6 +48,8 @@ MUTANTS = {
     "phase_count_one_short": ("i64 c = 1 + (need + hmin - 1) / hmin;",
                               "i64 c = (need + hmin - 1) / hmin;"),
     "objective_half_dropped": ("return 0.5 * sq + lam * l1;", "return sq + lam * l1;"),
+    "threshold_not_shrunk": ("double a = fabs(u) - lam;", "double a = fabs(u) - 0.5 * lam;"),
+    "argmax_keeps_first_coordinate": ("if (d > best) {", "if (d > best && best < 0.0) {"),
 }
 
 

@@ -96,6 +96,31 @@ def test_band_schedule_border_updates_match_fresh_residual():
                                           updates_per_visit=2, max_updates=q), D, X, 40)
 
 
+def test_each_update_lowers_E_by_prop_A1():
+    # Prop. A.1 in 2-D: E(Z) - E(Z1) = n/2 (z^2 - u^2) - beta (z - u) + lam (|z| - |u|) >= 0,
+    # and the new value is the 1-D minimiser Sh(beta, lam) / n
+    D, X = tiny2d(seed=21)
+    lam = 0.1 * csc2d.lambda_max(D, X)
+    r = csc2d.greedy_cd(D, X, lam, 1e-10, trace=10_000, max_updates=CAP)
+    tr = r["trace"]
+    n = npref.norms2d(D)
+    Z = np.zeros_like(r["Z"])
+    E = npref.objective2d(D, X, Z, lam)
+    for q in range(len(tr["k"])):
+        k, i, j = int(tr["k"][q]), int(tr["i"][q]), int(tr["j"][q])
+        z, u = tr["z_old"][q], tr["z_new"][q]
+        assert Z[k, i, j] == z
+        b = npref.beta_fresh2d(D, X, Z)[k, i, j]
+        e = n[k] / 2 * (z * z - u * u) - b * (z - u) + lam * (abs(z) - abs(u))
+        assert u == pytest.approx(npref.soft(b, lam) / n[k], abs=1e-12)
+        Z[k, i, j] = u
+        E1 = npref.objective2d(D, X, Z, lam)
+        assert E - E1 == pytest.approx(e, abs=1e-10 * max(1.0, E))
+        assert E1 <= E + 1e-12 * E
+        E = E1
+    np.testing.assert_array_equal(Z, r["Z"])
+
+
 def test_lambda_above_lambda_max_gives_zero():
     D, X = tiny2d()
     lmax = float(np.abs(npref.dtx2d(D, X)).max())
