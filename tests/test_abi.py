@@ -146,3 +146,14 @@ def test_missing_library_fails_loudly(tmp_path):
     # falling back to anything
     with pytest.raises(OSError, match="not built"):
         capi.load(str(tmp_path / "libcsc.so"))
+
+
+@pytest.mark.parametrize("Hz,h,M", [(200, 11, 10), (64, 17, 4), (7, 3, 7), (1000, 8, 0),
+                                    (513, 1, 9)])
+def test_plan_gives_the_band_schedule_of_the_2d_oracle(lib, Hz, h, M):
+    # the 2-D variant cuts rows as the 1-D path cuts time: csc_plan over the
+    # Hz rows with atom height h is the 2-D oracle's band schedule
+    from oracle import csc2d
+    Mo, c, starts = capi.csc_plan(Hz, h, M)
+    assert c == csc2d.phase_count(Hz, Mo, h)
+    assert [int(x) for x in starts] == [csc2d.band_start(Hz, Mo, m) for m in range(Mo + 1)]
