@@ -192,6 +192,44 @@ def make_problem(K: int, P: int, L: int, T: int, rho: float, sigma: float,
     return Problem(D=D, Z_true=Z, X=X.astype(np.float32), seed=seed, rho=rho, sigma=sigma)
 
 
+@dataclasses.dataclass
+class Problem2D:
+    """One synthetic image problem (the 2-D variant, images cut into row bands).
+    D[K,P,h,w], Z_true[K,H-h+1,W-w+1], X[P,H,W], all float32."""
+    D: np.ndarray
+    Z_true: np.ndarray
+    X: np.ndarray
+    seed: int
+    rho: float
+    sigma: float
+
+
+def make_problem2d(K: int, P: int, h: int, w: int, H: int, W: int, rho: float, sigma: float,
+                   seed: int) -> Problem2D:
+    """The Sec. 4 recipe on images: K unit-norm Gaussian atoms [P, h, w], Z
+    Bernoulli(rho)-Gaussian over every coordinate (one uniform each), X = sum_k
+    Z_k * D_k (2-D, "valid" placement: activation (i, j) covers rows i..i+h-1
+    and columns j..j+w-1) plus N(0, sigma^2) noise, summed in float64 and
+    rounded once to float32.  The paper has no image workload; this one only
+    carries its law over to two dimensions."""
+    if H < h or W < w:
+        raise ValueError("the image must be at least as large as the atoms")
+    D = normal(seed, 11, K * P * h * w).reshape(K, P, h, w)
+    D /= np.sqrt((D * D).sum(axis=(1, 2, 3), keepdims=True))
+    D = D.astype(np.float32)
+    Hz, Wz = H - h + 1, W - w + 1
+    nz = np.flatnonzero(uniform(seed, 13, K * Hz * Wz) < rho)
+    Z = np.zeros(K * Hz * Wz, np.float32)
+    Z[nz] = normal_at(seed, 14, nz).astype(np.float32)
+    Z = Z.reshape(K, Hz, Wz)
+    X = np.zeros((P, H, W), np.float64)
+    ks, iz, jz = np.nonzero(Z)
+    for k, i, j in zip(ks, iz, jz):
+        X[:, i:i + h, j:j + w] += float(Z[k, i, j]) * D[k].astype(np.float64)
+    X += sigma * normal(seed, 15, P * H * W).reshape(P, H, W)
+    return Problem2D(D=D, Z_true=Z, X=X.astype(np.float32), seed=seed, rho=rho, sigma=sigma)
+
+
 # Workloads, named by what they are (shapes from the paper's Sec. 4 setting,
 # scaled as stated).  "segments" lists the segment counts M exercised.
 WORKLOADS = {

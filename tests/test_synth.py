@@ -120,3 +120,20 @@ def test_stream_sources_same_with_worker_processes():
         # unit-norm atoms (Sec. 4 recipe)
         assert np.allclose(np.sqrt((x.D.astype(np.float64) ** 2).sum(axis=(1, 2))), 1.0,
                            atol=1e-6)
+
+
+def test_image_problem_recipe():
+    # unit-norm atoms, Bernoulli(rho) support, and X minus the model is the
+    # noise: the 2-D oracle's residual at Z_true has the noise's spread
+    from oracle import csc2d
+    pb = synth.make_problem2d(K=4, P=2, h=5, w=4, H=60, W=50, rho=0.01, sigma=0.1, seed=3)
+    assert pb.D.dtype == np.float32 and pb.X.shape == (2, 60, 50)
+    assert np.allclose(np.sqrt((pb.D.astype(np.float64) ** 2).sum(axis=(1, 2, 3))), 1.0,
+                       atol=1e-6)
+    assert pb.Z_true.shape == (4, 56, 47)
+    dens = np.count_nonzero(pb.Z_true) / pb.Z_true.size
+    assert 0.005 < dens < 0.02
+    R = csc2d.residual(pb.D, pb.X, pb.Z_true)
+    assert R.std() == pytest.approx(0.1, rel=0.05) and abs(R.mean()) < 0.01
+    again = synth.make_problem2d(K=4, P=2, h=5, w=4, H=60, W=50, rho=0.01, sigma=0.1, seed=3)
+    assert np.array_equal(again.X, pb.X) and np.array_equal(again.Z_true, pb.Z_true)
