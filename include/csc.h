@@ -33,13 +33,17 @@
  * ownership of every array it passes; the library copies what it keeps.
  *
  * Errors: every entry point returns an int status.  CSC_OK (0) is success;
- * CSC_NOT_CONVERGED (1) means max_updates or the sweep limit was reached
- * (Z and the objective are still valid).  Negative values are errors; the
+ * CSC_NOT_CONVERGED (1) means max_updates or the sweep limit was reached, or
+ * the exact check after the last resync allowed still found a coordinate
+ * with |Delta Z| >= tol (Z and the objective are still valid).  Negative values are errors; the
  * text of the last error of the calling thread is csc_last_error_string().
  * No C++ exception crosses this boundary.
  *
  * Threads and streams: a handle is used by one host thread at a time; all of
- * its GPU work is ordered on the stream given to csc_setup.  Calls that read
+ * its GPU work is ordered on the stream given to csc_setup.  A handle lives
+ * on the device that was current at its first csc_setup; every call on it
+ * switches to that device and restores the caller's current device before
+ * returning.  Calls that read
  * results back (csc_solve, the getters) synchronise that stream.
  */
 #ifndef CSC_H
@@ -66,9 +70,14 @@ typedef struct csc_opts {
                                   segment_width).  Batches always use segment_width */
     int32_t updates_per_visit; /* u: updates a segment may apply per phase; 0 = until local
                                   convergence (bounded internally by 2^20) */
-    int32_t max_resyncs;       /* FP64 beta re-synchronisations after the FP32 loop settles;
-                                  CD resumes after a resync that finds |Delta Z| >= tol.
-                                  -1 = default (3); 0 = none */
+    int32_t max_resyncs;       /* exact re-synchronisations of beta (double-float
+                                  accumulation from D~*X) after the float32 loop settles;
+                                  CD resumes after one that finds |Delta Z| >= tol.  When
+                                  the loop settles again after the last one allowed, one
+                                  more exact refresh decides the status: CSC_OK if it finds
+                                  every |Delta Z| below tol, else CSC_NOT_CONVERGED.
+                                  -1 = default (3); 0 = none (the status is then the float32
+                                  loop's own test; stats.max_delta_z reports the exact one) */
     int32_t sweeps_per_poll;   /* sweeps enqueued between two host convergence polls;
                                   0 = default (4) */
     int32_t max_sweeps;        /* 0 = default (1,000,000) */
@@ -97,12 +106,17 @@ typedef struct csc_stats {
     int64_t sweeps;           /* full sweeps (c phases) launched */
     int32_t segments;         /* M used */
     int32_t phases;           /* c used */
-    int32_t resyncs;          /* FP64 re-synchronisations performed */
-    int32_t converged;        /* 1 if stopped because a sweep applied no update */
+    int32_t resyncs;          /* exact re-synchronisations performed after the loop settled
+                                 (including the final refresh that decides the status) */
+    int32_t converged;        /* 1 if a sweep applied no update and the exact check on the
+                                 refreshed state found every |Delta Z| below tol */
     double objective;         /* E(Z) in FP64 from the explicit residual */
-    double max_drift;         /* max |beta_fp32 - beta_fp64| seen at a resync */
-    double kkt_zero_excess;   /* max over Z == 0 of |beta| - lambda (FP64 beta) */
-    double kkt_nonzero_gap;   /* max over Z != 0 of |Z - Sh(beta,lambda)/n| (FP64 beta) */
+    double max_drift;         /* max |beta_float32 - beta_exact| seen at a resync */
+    /* The optimality report of the returned Z: beta recomputed from Z with
+     * double-float accumulation (about 48 bits) from D~*X and rounded once to
+     * float32; the gaps below are then evaluated in float32. */
+    double kkt_zero_excess;   /* max over Z == 0 of |beta| - lambda (floored at 0) */
+    double kkt_nonzero_gap;   /* max over Z != 0 of |Z - Sh(beta,lambda)/n| */
     double max_delta_z;       /* max over all coordinates of |Z - Sh(beta,lambda)/n| */
     double solve_ms;          /* device time from the first phase to the last resync */
     double phase_ms;          /* summed duration of the phase launches (time_kernels = 1) */
@@ -144,11 +158,13 @@ int csc_init(csc_handle_t h, const float *X, int64_t T, double lambda, const flo
 
 /*
  * Steps a3-a7: phase-scheduled locally greedy CD until a full sweep applies
- * no update with |Delta Z| >= tol, then an FP64 resync of beta and a final
- * FP64 objective / optimality check.  A coordinate counts as converged when
- * its |Delta Z| computed in FP32 is below max(tol, 2^-21 |beta| / ||D_k||^2):
- * smaller changes are under the resolution of the float32 state (a few ulps
- * of beta) and chasing them only accumulates rounding drift.
+ * no update with |Delta Z| >= tol, then an exact resync of beta (double-float
+ * accumulation, see max_resyncs) and a final FP64 objective and optimality
+ * report.  The solver keeps r = beta - ||D_k||^2 Z in float32; a coordinate
+ * counts as converged when its change computed in float32 is below
+ * max(tol, 2^-21 |r| / ||D_k||^2 + 2^-22 |Z|): smaller changes are under the
+ * resolution of the float32 state (a few ulps of r/n and of Z) and chasing
+ * them only accumulates rounding drift.
  *   tol          > 0 (the paper's epsilon)
  *   max_updates  > 0, cap on applied updates (checked between phases)
  *   Z_out        NULL or [K][T-L+1] float32, host or device, caller-owned
@@ -281,13 +297,17 @@ int csc_plan(int64_t Tz, int L, int M, int *M_out, int *phases, int64_t *starts)
  *   D [K][P][L], X [P][T], Z [K][T-L+1]  float32 DEVICE arrays, caller-owned
  *   lambda >= 0;  E_out: one double, host or device memory
  *   stream  cudaStream_t (NULL = legacy default stream)
+ * D, X and Z must be memory of the current device (or managed memory); a
+ * device E_out likewise.  The binding checks that X is [P][T] and Z is
+ * [K][T-L+1]; this entry point cannot, so wrong sizes read out of bounds.
  * Scratch: a static device array of 1 MiB that every GPU loading this library
  * keeps until process exit; it limits T to 16,777,216 samples (larger T gives
- * CSC_EINVAL).  The first call on a device looks up that array's address
- * (cudaGetSymbolAddress, with the device current); make that first call
- * before any stream capture.  All calls share the array: calls whose GPU
- * work may overlap (other streams, other threads) race and must be ordered
- * by the caller.  With a host E_out the call synchronises the stream.
+ * CSC_EINVAL).  Each call looks up that array's address on the current device
+ * (cudaGetSymbolAddress); the first call on a device also loads the module
+ * there, so make that first call before any stream capture.  All calls share
+ * the array: calls whose GPU work may overlap (other streams, other threads)
+ * race and must be ordered by the caller.  With a host E_out the call
+ * synchronises the stream.
  */
 int csc_objective_noalloc(const float *D, int K, int P, int L, const float *X, int64_t T,
                           const float *Z, double lambda, double *E_out, void *stream);

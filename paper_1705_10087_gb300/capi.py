@@ -188,6 +188,41 @@ def _ptr(a, writable: bool = False):
     raise TypeError(f"unsupported array type {type(a)!r}")
 
 
+class Handle(_vp):
+    """A csc handle (an opaque C pointer) that remembers the sizes (K, P, L) of
+    its dictionary, so that the binding can check array shapes before it
+    passes their pointers on."""
+    K = P = L = None
+    Tz = None  # columns of the current problem (set by csc_init / csc_init_batch)
+
+
+def _shape(a):
+    return tuple(int(x) for x in a.shape)
+
+
+def _device_of(a):
+    """("cuda", index) for a CUDA tensor, ("cpu", None) for anything else."""
+    dev = getattr(a, "device", None)
+    if dev is not None and getattr(dev, "type", "cpu") == "cuda":
+        return ("cuda", dev.index)
+    return ("cpu", None)
+
+
+def _check_signal(h, X, what: str = "X"):
+    if len(X.shape) != 2:
+        raise ValueError(f"{what} must be [P, T]")
+    if h is not None and getattr(h, "P", None) is not None and int(X.shape[0]) != h.P:
+        raise ValueError(f"{what} has {int(X.shape[0])} channels, the dictionary {h.P}")
+
+
+def _check_z(h, Z, Tz: int, what: str = "Z"):
+    if Z is None or h is None or getattr(h, "K", None) is None:
+        return
+    if int(np.prod(_shape(Z))) != h.K * Tz:
+        raise ValueError(f"{what} must hold K * Tz = {h.K} * {Tz} values, got shape "
+                         f"{_shape(Z)}")
+
+
 def _stream(stream):
     if stream is not None:
         return stream if isinstance(stream, int) else stream.cuda_stream
@@ -215,15 +250,24 @@ def make_opts(segments: int = 0, updates_per_visit: int = 0, max_resyncs: int = 
 
 def csc_setup(D, opts: csc_opts | None = None, stream=None, handle=None):
     """D [K,P,L] float32 -> handle (a ctypes c_void_p); re-uses ``handle`` if given."""
+    if len(D.shape) != 3:
+        raise ValueError("D must be [K, P, L]")
     K, P, L = (int(x) for x in D.shape)
-    h = handle if handle is not None else _vp()
+    h = handle if handle is not None else Handle()
     _check(load().csc_setup(ctypes.byref(h), _ptr(D), K, P, L,
                             ctypes.byref(opts) if opts is not None else None, _stream(stream)))
+    if isinstance(h, Handle):
+        h.K, h.P, h.L, h.Tz = K, P, L, None  # a new setup invalidates the problem
     return h
 
 
 def csc_init(h, X, lam: float, Z0=None) -> None:
+    _check_signal(h, X)
+    if getattr(h, "L", None) is not None:
+        _check_z(h, Z0, int(X.shape[1]) - h.L + 1, "Z0")
     _check(load().csc_init(h, _ptr(X), int(X.shape[1]), float(lam), _ptr(Z0)))
+    if isinstance(h, Handle) and h.L is not None:
+        h.Tz = int(X.shape[1]) - h.L + 1
 
 
 def csc_init_batch(h, X, T, lam, Z0=None) -> None:
@@ -232,10 +276,15 @@ def csc_init_batch(h, X, T, lam, Z0=None) -> None:
     la = np.ascontiguousarray(np.asarray(lam, dtype=np.float64).reshape(-1))
     if la.shape != Ta.shape:
         raise ValueError("T and lam need one entry per signal")
+    _check_signal(h, X)
     if int(Ta.sum()) != int(X.shape[1]):
         raise ValueError("X must hold sum(T) samples per channel")
+    if getattr(h, "L", None) is not None:
+        _check_z(h, Z0, int(Ta.sum()) - h.L + 1, "Z0")
     _check(load().csc_init_batch(h, _ptr(X), Ta.ctypes.data, int(Ta.size), la.ctypes.data,
                                  _ptr(Z0)))
+    if isinstance(h, Handle) and h.L is not None:
+        h.Tz = int(Ta.sum()) - h.L + 1
 
 
 def csc_set_lambda(h, lam) -> None:
@@ -263,6 +312,8 @@ def csc_autotune(h, tol: float, max_updates: int = 1 << 62) -> dict:
 
 def csc_solve(h, tol: float, max_updates: int = 1 << 62, Z_out=None):
     """Returns (status, objective, stats dict)."""
+    if getattr(h, "Tz", None) is not None:
+        _check_z(h, Z_out, h.Tz, "Z_out")
     obj = ctypes.c_double(0.0)
     st = csc_stats()
     status = _check(load().csc_solve(h, float(tol), int(max_updates), _ptr(Z_out, True),
@@ -281,6 +332,8 @@ def csc_lambda_max(h) -> float:
 
 
 def csc_get_beta(h, out) -> None:
+    if getattr(h, "Tz", None) is not None:
+        _check_z(h, out, h.Tz, "beta_out")
     _check(load().csc_get_beta(h, _ptr(out, True)))
 
 
@@ -289,6 +342,8 @@ def csc_get_dtd(h, dtd_out=None, norms_out=None) -> None:
 
 
 def csc_objective(h, Z) -> float:
+    if getattr(h, "Tz", None) is not None:
+        _check_z(h, Z, h.Tz)
     v = ctypes.c_double(0.0)
     _check(load().csc_objective(h, _ptr(Z), ctypes.byref(v)))
     return v.value
@@ -296,6 +351,8 @@ def csc_objective(h, Z) -> float:
 
 def csc_kkt(h, Z) -> dict:
     """Optimality report of Z (Theorem A.1) for the handle's X and lambda."""
+    if getattr(h, "Tz", None) is not None:
+        _check_z(h, Z, h.Tz)
     out = np.zeros(3, np.float64)
     _check(load().csc_kkt(h, _ptr(Z), out.ctypes.data))
     return {"zero_excess": float(out[0]), "nonzero_gap": float(out[1]),
@@ -318,7 +375,19 @@ def csc_get_trace(h, cap: int = 1 << 16) -> dict:
 def csc_objective_noalloc(D, X, Z, lam: float, out=None, stream=None) -> float:
     """E(Z) through the allocation-free entry point; D, X, Z must be CUDA tensors.
     ``out`` may be a one-element float64 CUDA tensor to receive E on the device."""
+    if len(D.shape) != 3:
+        raise ValueError("D must be [K, P, L]")
     K, P, L = (int(x) for x in D.shape)
+    if _shape(X)[:1] != (P,) or len(X.shape) != 2:
+        raise ValueError(f"X must be [P={P}, T], got shape {_shape(X)}")
+    T = int(X.shape[1])
+    if T < L:
+        raise ValueError(f"X has T = {T} < L = {L} samples")
+    if _shape(Z) != (K, T - L + 1):
+        raise ValueError(f"Z must be [K={K}, T-L+1={T - L + 1}], got shape {_shape(Z)}")
+    devs = {_device_of(a) for a in (D, X, Z) + (() if out is None else (out,))}
+    if len(devs) != 1 or next(iter(devs))[0] != "cuda":
+        raise ValueError("D, X, Z (and out) must be CUDA tensors on one device")
     if out is None:
         v = ctypes.c_double(0.0)
         _check(load().csc_objective_noalloc(_ptr(D), K, P, L, _ptr(X), int(X.shape[1]), _ptr(Z),

@@ -45,6 +45,14 @@ int fail(int code, const char *fmt, ...)
                         __LINE__);                                                       \
     } while (0)
 
+// Switches to the handle's device for the rest of the calling scope (the
+// caller's device is restored on return) and fails if the switch fails.
+#define CSC_ON_DEVICE(dev)                                                               \
+    csc::DeviceGuard dev_guard_(dev);                                                    \
+    if (dev_guard_.err != cudaSuccess)                                                   \
+        return fail(CSC_ECUDA, "cudaSetDevice(%d) failed: %s", (int)(dev),                \
+                    cudaGetErrorString(dev_guard_.err))
+
 // Small device-side state of a handle (one allocation).
 struct Scratch {
     long long upd[kPhaseRing];
@@ -453,7 +461,7 @@ int csc_destroy(csc_handle_t h)
 {
     if (!h)
         return CSC_OK;
-    cudaSetDevice(h->device);
+    CSC_ON_DEVICE(h->device);
     if (h->stream)
         cudaStreamSynchronize(h->stream);
     void *bufs[] = {h->D,          h->C,          h->Ct,         h->norms,      h->X,
@@ -512,7 +520,14 @@ int csc_setup(csc_handle_t *hp, const float *D, int K, int P, int L, const csc_o
             return fail(CSC_ECUDA, "csc_setup: no CUDA device");
         }
     }
-    cudaSetDevice(h->device);
+    const int dev = h->device;
+    csc::DeviceGuard dev_guard_(dev);
+    if (dev_guard_.err != cudaSuccess) {
+        if (fresh)
+            delete h;
+        return fail(CSC_ECUDA, "csc_setup: cudaSetDevice(%d) failed: %s", dev,
+                    cudaGetErrorString(dev_guard_.err));
+    }
     h->stream = (cudaStream_t)stream;
     h->opts = o;
     h->K = K;
@@ -566,7 +581,7 @@ int csc_init_batch(csc_handle_t h, const float *X, const int64_t *T, int n, cons
     const int64_t Tz = Ttot - h->L + 1;
     if (Tz >= ((int64_t)1 << 31) - 1)
         return fail(CSC_EINVAL, "csc_init: T - L + 1 must be below 2^31 - 1 columns");
-    cudaSetDevice(h->device);
+    CSC_ON_DEVICE(h->device);
     h->initialized = false;
     h->plan_ok = false;
     cudaStream_t s = h->stream;
@@ -679,7 +694,7 @@ int csc_set_lambda(csc_handle_t h, const double *lambda)
         return fail(CSC_EINVAL, "csc_set_lambda: null argument");
     if (!h->initialized)
         return fail(CSC_ESTATE, "csc_set_lambda: call csc_init first");
-    cudaSetDevice(h->device);
+    CSC_ON_DEVICE(h->device);
     return set_lambdas(h, lambda);
 }
 
@@ -723,7 +738,7 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
         return fail(CSC_ESTATE, "csc_solve: call csc_init first");
     if (!(tol > 0.0) || max_updates < 1)
         return fail(CSC_EINVAL, "csc_solve: need tol > 0 and max_updates >= 1");
-    cudaSetDevice(h->device);
+    CSC_ON_DEVICE(h->device);
     cudaStream_t s = h->stream;
     const int64_t Tz = h->Tz;
     {
@@ -919,19 +934,22 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
         }
         if (forced)
             effective += g - g_round;
-        if (round_done && resyncs >= max_resyncs) {
-            converged = true;
+        // the loop settled after the last resync allowed: one more exact
+        // refresh decides the status (no further CD round follows it)
+        const bool last = round_done && resyncs >= max_resyncs;
+        if (last && max_resyncs == 0) {
+            converged = true;  // no resync requested: the float32 loop's own test
             break;
         }
         CSC_CUDA(cudaMemsetAsync(sc->red, 0, sizeof(sc->red), s));
         // segments come back dirty only where the refreshed state has a
         // coordinate at or above the inner tolerance (a round cut short keeps
         // the segments it still had to visit)
-        if (round_done)
+        if (round_done && !last)
             CSC_CUDA(cudaMemsetAsync(h->dirty, 0, (size_t)M, s));
         CSC_CUDA(launch_resync(h->d_sig, h->resync_tiles(), h->C, h->norms, h->K, h->L, 1,
-                               sc->red, 0, h->dirty, tol_inner, h->touched, h->tile_rep,
-                               s));
+                               sc->red, 0, last ? nullptr : h->dirty, tol_inner, h->touched,
+                               h->tile_rep, s));
         CSC_CUDA(cudaMemsetAsync(h->touched, 0, (size_t)M, s));
         h->launches += 1;
         unsigned long long red[8];
@@ -945,8 +963,10 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
         std::memcpy(&d0, &red[0], sizeof d0);
         std::memcpy(&dz32, &red[4], sizeof dz32);
         drift = d0 > drift ? d0 : drift;
-        if (dz32 < tol) {
-            converged = true;
+        if (dz32 < tol || last) {
+            // the exact check: every coordinate's change on the refreshed state
+            // is below tol, or (after the last resync allowed) it is not
+            converged = dz32 < tol;
             report_fresh = true;
             break;
         }
@@ -1014,7 +1034,7 @@ int csc_autotune(csc_handle_t h, double tol, int64_t max_updates, csc_tune_resul
         return fail(CSC_ESTATE, "csc_autotune: call csc_init first");
     if (!(tol > 0.0) || max_updates < 1)
         return fail(CSC_EINVAL, "csc_autotune: need tol > 0 and max_updates >= 1");
-    cudaSetDevice(h->device);
+    CSC_ON_DEVICE(h->device);
     cudaStream_t s = h->stream;
     const size_t nz = (size_t)h->K * h->Tz;
     // the starting point every candidate solves from
@@ -1141,7 +1161,7 @@ int csc_get_beta(csc_handle_t h, float *beta_out)
         return fail(CSC_EINVAL, "csc_get_beta: null argument");
     if (!h->initialized)
         return fail(CSC_ESTATE, "csc_get_beta: call csc_init first");
-    cudaSetDevice(h->device);
+    CSC_ON_DEVICE(h->device);
     const size_t nz = (size_t)h->K * h->Tz;
     // beta = r + ||D_k||^2 Z (the kernels keep r)
     if (is_device_pointer(beta_out)) {
@@ -1161,7 +1181,7 @@ int csc_get_dtd(csc_handle_t h, float *dtd_out, float *norms_out)
 {
     if (!h)
         return fail(CSC_EINVAL, "csc_get_dtd: null handle");
-    cudaSetDevice(h->device);
+    CSC_ON_DEVICE(h->device);
     if (dtd_out)
         CSC_CUDA(copy_out(dtd_out, h->C, sizeof(float) * h->K * h->K * (2 * h->L - 1), h->stream));
     if (norms_out)
@@ -1177,7 +1197,7 @@ int csc_objective(csc_handle_t h, const float *Z, double *out)
         return fail(CSC_EINVAL, "csc_objective: null argument");
     if (!h->initialized)
         return fail(CSC_ESTATE, "csc_objective: call csc_init first");
-    cudaSetDevice(h->device);
+    CSC_ON_DEVICE(h->device);
     cudaStream_t s = h->stream;
     const size_t nz = (size_t)h->K * h->Tz;
     const float *Zd = Z;
@@ -1196,7 +1216,7 @@ int csc_kkt(csc_handle_t h, const float *Z, double *out)
         return fail(CSC_EINVAL, "csc_kkt: null argument");
     if (!h->initialized)
         return fail(CSC_ESTATE, "csc_kkt: call csc_init first");
-    cudaSetDevice(h->device);
+    CSC_ON_DEVICE(h->device);
     cudaStream_t s = h->stream;
     const size_t nz = (size_t)h->K * h->Tz;
     const float *Zd = Z;
@@ -1232,7 +1252,7 @@ int csc_get_trace(csc_handle_t h, int64_t cap, int64_t *updates, double *decreas
 {
     if (!h || cap < 0 || (cap > 0 && (!updates || !decrease || !t_ns)))
         return fail(CSC_EINVAL, "csc_get_trace: bad arguments");
-    cudaSetDevice(h->device);
+    CSC_ON_DEVICE(h->device);
     const int64_t g = h->g_used < kPhaseRing ? h->g_used : kPhaseRing;
     const int64_t m = cap < g ? cap : g;
     if (n)

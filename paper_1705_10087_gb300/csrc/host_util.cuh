@@ -19,6 +19,34 @@ struct TraceRange {
     TraceRange &operator=(const TraceRange &) = delete;
 };
 
+// Makes a handle's device current for the scope of an entry point and puts
+// the caller's current device back when the scope ends, so that no call of
+// this library changes which device is current for the calling thread.
+// err holds the result of the switch (checked by the caller).
+struct DeviceGuard {
+    int prev = -1;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+        }
+        if (prev != dev)
+            err = cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        if (err == cudaSuccess && prev >= 0) {
+            int cur = -1;
+            if (cudaGetDevice(&cur) == cudaSuccess && cur != prev)
+                cudaSetDevice(prev);
+        }
+    }
+    DeviceGuard(const DeviceGuard &) = delete;
+    DeviceGuard &operator=(const DeviceGuard &) = delete;
+};
+
 inline bool is_device_pointer(const void *p)
 {
     cudaPointerAttributes a;

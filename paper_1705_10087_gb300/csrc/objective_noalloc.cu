@@ -15,30 +15,28 @@
 // threads without ordering) race on it and must be serialised by the caller.
 // Each call overwrites every entry it later reads, so nothing is cleared.
 #include <cstring>
-#include <mutex>
 
 #include "csc_internal.cuh"
 
 namespace {
 
 constexpr int kNoAllocMaxBlocks = 1 << 16;
-constexpr int kNoAllocMaxDevices = 64;
 
 // [0, 2*kNoAllocMaxBlocks): per-block (sum of squared residuals, sum |Z|);
 // the extra entry receives E when the caller's output is in host memory.
 static __device__ __align__(256) double g_partials[2 * kNoAllocMaxBlocks + 2];
 
-std::mutex g_setup_mutex;
-double *g_partials_addr[kNoAllocMaxDevices] = {};
-
-bool device_resident(const void *p)
+// Device memory of device `dev` (the current one), or managed memory.
+bool device_resident(const void *p, int dev)
 {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged)
+        return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -65,33 +63,33 @@ extern "C" int csc_objective_noalloc(const float *D, int K, int P, int L, const 
                                 "csc_objective_noalloc: T = %lld exceeds the static scratch "
                                 "limit of %d samples",
                                 (long long)T, kNoAllocMaxBlocks * csc::kTile);
-    if (!device_resident(D) || !device_resident(X) || !device_resident(Z))
-        return csc_record_error(CSC_EINVAL,
-                                "csc_objective_noalloc: D, X and Z must be device memory");
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices)
+    if (e != cudaSuccess)
         return csc_record_error(CSC_ECUDA, "csc_objective_noalloc: no usable current device");
+    if (!device_resident(D, dev) || !device_resident(X, dev) || !device_resident(Z, dev))
+        return csc_record_error(CSC_EINVAL,
+                                "csc_objective_noalloc: D, X and Z must be memory of the "
+                                "current device (%d)",
+                                dev);
 
-    // One-time set-up per device, with that device current: the host-side
-    // name g_partials is not a device address, so look the address up.
-    double *scratch;
+    // The host-side name g_partials is not a device address: look the array
+    // up on the current device.  This is done on every call (a host-side
+    // query), so the address stays right after a context of the device was
+    // torn down and created again.
+    double *scratch = nullptr;
     {
-        std::lock_guard<std::mutex> lock(g_setup_mutex);
-        if (!g_partials_addr[dev]) {
-            void *p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_partials);
-            if (e != cudaSuccess || !p)
-                return csc_record_error(CSC_ECUDA,
-                                        "csc_objective_noalloc: cudaGetSymbolAddress failed: %s",
-                                        cudaGetErrorString(e));
-            g_partials_addr[dev] = static_cast<double *>(p);
-        }
-        scratch = g_partials_addr[dev];
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_partials);
+        if (e != cudaSuccess || !p)
+            return csc_record_error(CSC_ECUDA,
+                                    "csc_objective_noalloc: cudaGetSymbolAddress failed: %s",
+                                    cudaGetErrorString(e));
+        scratch = static_cast<double *>(p);
     }
 
     cudaStream_t s = (cudaStream_t)stream;
-    const bool out_on_device = device_resident(E_out);
+    const bool out_on_device = device_resident(E_out, dev);
     double *out = out_on_device ? E_out : scratch + 2 * kNoAllocMaxBlocks;
     csc::SigDesc one{};
     one.Z = const_cast<float *>(Z);

@@ -696,7 +696,10 @@ int csc_server_add_dictionary(csc_server_t s, const float *D, int K, int P, int 
                                 wmin);
     if (updates_per_visit < 0)
         return csc_record_error(CSC_EINVAL, "csc_server_add_dictionary: updates_per_visit < 0");
-    cudaSetDevice(s->device);
+    csc::DeviceGuard dev_guard_(s->device);
+    if (dev_guard_.err != cudaSuccess)
+        return csc_record_error(CSC_ECUDA, "cudaSetDevice(%d) failed: %s", s->device,
+                                cudaGetErrorString(dev_guard_.err));
     s->groups.emplace_back();
     Group &g = s->groups.back();
     g.K = K;
@@ -760,7 +763,10 @@ int csc_server_submit(csc_server_t s, int dict, const float *X, int64_t T, doubl
                                 "whole pool (%zu)",
                                 q.bytes, s->pool.size);
     q.Xh.resize((size_t)g.P * T);
-    cudaSetDevice(s->device);
+    csc::DeviceGuard dev_guard_(s->device);
+    if (dev_guard_.err != cudaSuccess)
+        return csc_record_error(CSC_ECUDA, "cudaSetDevice(%d) failed: %s", s->device,
+                                cudaGetErrorString(dev_guard_.err));
     if (is_device_pointer(X)) {
         SRV_CUDA(cudaMemcpy(q.Xh.data(), X, sizeof(float) * g.P * T, cudaMemcpyDeviceToHost));
     } else {
@@ -779,7 +785,10 @@ int csc_server_step(csc_server_t s, int *n_active, int *n_queued, int *n_done)
     csc::TraceRange trace_("csc_server_step");
     if (!s)
         return csc_record_error(CSC_EINVAL, "csc_server_step: null server");
-    cudaSetDevice(s->device);
+    csc::DeviceGuard dev_guard_(s->device);
+    if (dev_guard_.err != cudaSuccess)
+        return csc_record_error(CSC_ECUDA, "cudaSetDevice(%d) failed: %s", s->device,
+                                cudaGetErrorString(dev_guard_.err));
     int done = 0;
     // every group advances on its own: a dictionary whose rounds are slow does
     // not hold back the others; if no group could move, wait for the first
@@ -866,7 +875,10 @@ int csc_server_fetch(csc_server_t s, int64_t request, float *Z_out, csc_request_
     if (q.state != CSC_REQ_DONE)
         return csc_record_error(CSC_ESTATE, "csc_server_fetch: request %lld is not done",
                                 (long long)request);
-    cudaSetDevice(s->device);
+    csc::DeviceGuard dev_guard_(s->device);
+    if (dev_guard_.err != cudaSuccess)
+        return csc_record_error(CSC_ECUDA, "cudaSetDevice(%d) failed: %s", s->device,
+                                cudaGetErrorString(dev_guard_.err));
     const Group &g = s->groups[q.dict];
     // the request left its group's active set in a completed round, so no
     // kernel in flight touches its block: copy on the server's own stream,
@@ -910,7 +922,10 @@ int csc_server_destroy(csc_server_t s)
 {
     if (!s)
         return CSC_OK;
-    cudaSetDevice(s->device);
+    csc::DeviceGuard dev_guard_(s->device);
+    if (dev_guard_.err != cudaSuccess)
+        return csc_record_error(CSC_ECUDA, "cudaSetDevice(%d) failed: %s", s->device,
+                                cudaGetErrorString(dev_guard_.err));
     for (Group &g : s->groups) {
         if (g.st)
             cudaStreamSynchronize(g.st);

@@ -157,3 +157,34 @@ def test_plan_gives_the_band_schedule_of_the_2d_oracle(lib, Hz, h, M):
     Mo, c, starts = capi.csc_plan(Hz, h, M)
     assert c == csc2d.phase_count(Hz, Mo, h)
     assert [int(x) for x in starts] == [csc2d.band_start(Hz, Mo, m) for m in range(Mo + 1)]
+
+
+def test_binding_refuses_mismatched_shapes_before_any_call(lib):
+    """The C entry points take raw pointers and cannot see array sizes; the
+    binding checks shapes first, so a wrong array never reaches a kernel."""
+    D = np.zeros((2, 3, 4), np.float32)
+    X = np.zeros((3, 64), np.float32)
+    Z = np.zeros((2, 61), np.float32)
+    with pytest.raises(ValueError):  # Z one column short
+        capi.csc_objective_noalloc(D, X, Z[:, :60].copy(), 0.1)
+    with pytest.raises(ValueError):  # X with the wrong channel count
+        capi.csc_objective_noalloc(D, np.zeros((2, 64), np.float32), Z, 0.1)
+    with pytest.raises(ValueError):  # host arrays (the entry point needs device memory)
+        capi.csc_objective_noalloc(D, X, Z, 0.1)
+    h = capi.Handle()
+    h.K, h.P, h.L = 2, 3, 4
+    with pytest.raises(ValueError):
+        capi.csc_init(h, np.zeros((2, 64), np.float32), 0.1)
+    with pytest.raises(ValueError):  # warm start of the wrong size
+        capi.csc_init(h, X, 0.1, Z0=np.zeros((2, 60), np.float32))
+    with pytest.raises(ValueError):
+        capi.csc_init_batch(h, np.zeros((1, 64), np.float32), [64], [0.1])
+    h.Tz = 61
+    with pytest.raises(ValueError):
+        capi.csc_solve(h, 1e-6, 10, np.zeros((2, 60), np.float32))
+    with pytest.raises(ValueError):
+        capi.csc_objective(h, np.zeros((3, 61), np.float32))
+    with pytest.raises(ValueError):
+        capi.csc_kkt(h, np.zeros((2, 62), np.float32))
+    with pytest.raises(ValueError):
+        capi.csc_get_beta(h, np.zeros((2, 60), np.float32))
