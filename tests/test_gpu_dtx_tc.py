@@ -154,3 +154,48 @@ def test_very_long_recording_full_size_sampled(capi):
         assert k["max_delta_z"] <= 2e-6 + slack, k
     Eo = oracle.objective(pb.D, pb.X, Z, lam)
     assert abs(E - Eo) <= 1e-9 * Eo
+
+
+def test_very_long_recording_full_size_parity(capi):
+    """The very long recording at full size (K x Tz = 25 x 4,999,801 coordinates)
+    with the default options (tensor-core beta0, automatic segments) against
+    the oracle's optimum stored by tests/golden/make_golden.py --verylong
+    (phase-schedule locally greedy CD at eps = 1e-10): relative objective gap
+    <= 1e-5, ||Z - Z*||_inf <= 1e-4 ||Z*||_inf and the same support outside
+    |z| < 1e-6, over every coordinate (compared on the device)."""
+    import hashlib
+    import json
+    import os
+    gdir = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    name = "verylong_P1_K25_L200_T5000000"
+    with open(os.path.join(gdir, "optimum.json")) as f:
+        g = json.load(f)[f"{name}/seed0"]
+    pb = synth.make_workload(name, seed=0)
+    hsh = hashlib.sha256()
+    hsh.update(pb.D.tobytes())
+    hsh.update(pb.X.tobytes())
+    assert hsh.hexdigest()[:16] == g["input_sha256_16"], "generator drifted from the stored inputs"
+    zs = np.load(os.path.join(gdir, g["zstar"]))
+    K, Tz = pb.K, pb.Tz
+    assert tuple(zs["shape"]) == (K, Tz)
+    lam = g["lambda"]
+    h = capi.csc_setup(cuda(pb.D), capi.make_opts(updates_per_visit=24))
+    try:
+        capi.csc_init(h, cuda(pb.X), lam)
+        Zd = torch.zeros((K, Tz), dtype=torch.float32, device="cuda")
+        status, E, st = capi.csc_solve(h, 1e-6, 1 << 40, Zd)
+    finally:
+        capi.csc_destroy(h)
+    assert status == 0 and st["converged"] == 1, st
+    gap = (E - g["E_star"]) / g["E_star"]
+    assert -1e-9 <= gap <= 1e-5, gap
+    idx = torch.from_numpy(zs["index"]).cuda()
+    zstar = torch.zeros(K * Tz, dtype=torch.float32, device="cuda")
+    zstar[idx] = torch.from_numpy(zs["value"]).cuda()
+    zg = Zd.view(-1)
+    zinf = float(zstar.abs().max())
+    assert zinf == pytest.approx(g["zinf"], rel=1e-6)
+    assert float((zg - zstar).abs().max()) <= 1e-4 * zinf
+    big = (zg.abs() >= 1e-6) | (zstar.abs() >= 1e-6)
+    mismatched = int((torch.sign(zg[big]) != torch.sign(zstar[big])).sum())
+    assert mismatched == 0, mismatched
