@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the 512-signal batched-vs-plain comparison")
     ap.add_argument("--no-serve", action="store_true", help="skip the request-stream leg")
+    ap.add_argument("--no-verylong", action="store_true",
+                    help="skip the very long recording (T = 5e6) leg")
     ap.add_argument("--serve-requests", type=int, default=400)
     return ap.parse_args()
 
@@ -349,6 +351,71 @@ def serve_leg(args, capi, torch):
     return out
 
 
+VERYLONG = "verylong_P1_K25_L200_T5000000"
+
+
+def verylong_leg(args, capi, torch):
+    """The very long recording (P=1, K=25, L=200, T=5e6, about 1.4 h at 1 kHz)
+    with the default options (tensor-core beta0, segments of 2L-2 columns,
+    u = 24), tol 1e-6.  Per run: csc_setup + csc_init + csc_solve timed with
+    CUDA events; the beta0 kernel alone by the library's own event pair
+    (csc_init_time); time to a 1e-4 relative gap against the oracle's E*
+    stored by tests/golden/make_golden.py --verylong.  The state (beta0, r,
+    Z: 1.5 GB) is far larger than L2."""
+    from paper_1705_10087_gb300 import synth
+    pb = synth.make_workload(VERYLONG, seed=0)
+    try:
+        with open(GOLDEN) as f:
+            g = json.load(f).get(f"{VERYLONG}/seed0")
+    except OSError:
+        g = None
+    if g is not None and g.get("input_sha256_16") != input_hash(pb):
+        g = None
+    stream = torch.cuda.current_stream()
+    D = torch.from_numpy(pb.D).cuda()
+    X = torch.from_numpy(pb.X).cuda()
+    Z = torch.zeros((pb.K, pb.Tz), dtype=torch.float32, device="cuda")
+    opts = capi.make_opts(updates_per_visit=24, time_kernels=1)
+    h = capi.csc_setup(D, opts)
+    if g is not None:
+        lam = g["lambda"]
+    else:
+        capi.csc_init(h, X, 1.0)
+        lam = 0.1 * capi.csc_lambda_max(h)
+    runs = []
+    for i in range(4):  # the first run warms up
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        capi.csc_setup(D, opts, handle=h)
+        capi.csc_init(h, X, lam)
+        ev[1].record(stream)
+        status, E, st = capi.csc_solve(h, args.tol, 1 << 40, Z)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        b0 = capi.csc_init_time(h)
+        tr = capi.csc_get_trace(h)
+        init_ms = ev[0].elapsed_time(ev[1])
+        if i > 0:
+            runs.append({"step_ms": ev[0].elapsed_time(ev[2]), "init_ms": init_ms,
+                         "beta0_kernel_ms": b0, "solve_ms": st["solve_ms"],
+                         "updates": st["updates"], "status": status, "resyncs": st["resyncs"],
+                         "time_to_gap_ms": time_to_gap_ms(tr, init_ms, g["E_star"]) if g else None,
+                         "rel_gap_final": (E - g["E_star"]) / g["E_star"] if g else None})
+    capi.csc_destroy(h)
+    best = min(runs, key=lambda r: r["step_ms"])
+    peak, kind = peaks()
+    # beta0 kernel: X read once, beta0 and the cold-start r written
+    b0_bytes = 4.0 * pb.P * pb.T + 2 * 4.0 * pb.K * pb.Tz
+    b0_gbs = b0_bytes / (best["beta0_kernel_ms"] * 1e-3) / 1e9 if best["beta0_kernel_ms"] > 0 else None
+    return {"workload": VERYLONG, "P": pb.P, "K": pb.K, "L": pb.L, "T": pb.T, "tol": args.tol,
+            "lambda": "0.1*lambda_max", "runs": len(runs), **best,
+            "updates_per_s": best["updates"] / (best["step_ms"] * 1e-3),
+            "solve_updates_per_s": best["updates"] / (best["solve_ms"] * 1e-3),
+            "beta0_roofline": {"bound": "hbm", "bytes": b0_bytes, "achieved_gbs": b0_gbs,
+                               "peak_gbs": peak, "peak_kind": kind,
+                               "frac": b0_gbs / peak if b0_gbs else None}}
+
+
 def cpu_baseline(pb, lam, tol, M, u):
     """The FP64 oracle as it stands (single thread), on the full problem."""
     import oracle
@@ -358,6 +425,23 @@ def cpu_baseline(pb, lam, tol, M, u):
     return {"value": r["n_updates"] / dt, "unit": "updates/s", "cores": 1, "kind": "oracle",
             "sample": f"full solve (DtD, D~*X, phase-schedule CD to max|dZ|<{tol:g}) of seed 0, "
                       f"M={M}, u={u}: {r['n_updates']} updates in {dt:.2f} s"}
+
+
+def cpu_baseline_multicore(pb, lam, tol, M, u):
+    """The same phase-schedule solve with the segments of a phase spread over
+    all host cores (oracle/csc_baseline_omp.c: identical results to the
+    oracle, the CPU analogue of DICOD)."""
+    from oracle import baseline_omp
+    cores = os.cpu_count() or 1
+    t = time.perf_counter()
+    r = baseline_omp.phase_cd(pb.D, pb.X, lam, tol, M, u, threads=cores)
+    dt = time.perf_counter() - t
+    return {"value": r["n_updates"] / dt, "unit": "updates/s", "cores": r["threads"],
+            "kind": "oracle phase schedule, OpenMP over the segments of a phase",
+            "solve_s": dt,
+            "sample": f"full solve (DtD, D~*X, phase-schedule CD to max|dZ|<{tol:g}) of seed 0, "
+                      f"M={M}, u={u}: {r['n_updates']} updates in {dt:.2f} s on "
+                      f"{r['threads']} threads"}
 
 
 def run_reference(args):
@@ -397,6 +481,94 @@ def run_reference(args):
                 "d2h_bytes_per_step": 0}}))
 
 
+def sharded_main(args, torch, dist, world, rank):
+    """N > 1: one signal of N x 200,000 samples (the long workload's recipe,
+    seed 0) cut into N shards, one per rank, solved by DICOD's protocol
+    (paper_1705_10087_gb300/shard.py): per phase each rank runs its segments
+    and exchanges its [K][L-1] halo with its neighbours over NCCL (device
+    buffers); a sweep without update on any rank ends a round; exact resyncs
+    and the objective are reduced over ranks.  Per-rank work is fixed as N
+    grows (weak scaling); value = updates of all ranks / slowest rank's time."""
+    from paper_1705_10087_gb300 import build, capi, shard, synth
+    build.build()
+    capi.load()
+    T1 = synth.WORKLOADS[WORKLOAD]["T"]
+    pb = synth.make_workload(WORKLOAD, seed=0, T=world * T1)
+    M = args.segments * world
+    plan = capi.csc_shard_plan_make(pb.T, pb.L, M, world, rank)
+    a0, n0 = plan["x_first"], plan["x_count"]
+    Xw = torch.from_numpy(np.ascontiguousarray(pb.X[:, a0:a0 + n0])).cuda()
+    D = torch.from_numpy(pb.D).cuda()
+    opts = capi.make_opts(updates_per_visit=args.updates_per_visit, init_mode=args.init_mode)
+    h = capi.csc_setup(D, opts)
+    comm = shard.TorchComm(dist, device="cuda")
+    capi.csc_shard_init(h, plan, Xw, 1.0)
+    lam = 0.1 * comm.max(capi.csc_lambda_max(h))  # lambda_max over the whole signal
+    make = lambda shape: torch.zeros(shape, dtype=torch.float32, device="cuda")  # noqa: E731
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step():
+        capi.csc_setup(D, opts, handle=h)
+        capi.csc_shard_init(h, plan, Xw, lam)
+        return shard.solve(shard.CapiShard(capi, h, plan), comm, pb.K, plan, args.tol, make=make)
+
+    for _ in range(args.warmup):
+        step()
+        flush.zero_()
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tot_ms, ups = 0.0, 0
+    res = None
+    for _ in range(args.steps):
+        flush.zero_()
+        ev0.record(stream)
+        res = step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        tot_ms += ev0.elapsed_time(ev1)
+        ups += capi.csc_shard_updates(h)  # this rank's updates of the step
+    dist.barrier()
+    torch.cuda.synchronize()
+    t_max, u_all = over_ranks(dist, "cuda", tot_ms, ups)
+    # end to end: host (pinned) samples in, host Z out, through the same calls
+    Xh = torch.from_numpy(np.ascontiguousarray(pb.X[:, a0:a0 + n0])).pin_memory()
+    Zh = torch.zeros((pb.K, plan["col_count"]), dtype=torch.float32).pin_memory()
+    e_t, e_u = 0.0, 0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        capi.csc_setup(D, opts, handle=h)
+        capi.csc_shard_init(h, plan, Xh, lam)
+        shard.solve(shard.CapiShard(capi, h, plan), comm, pb.K, plan, args.tol, make=make)
+        capi.csc_shard_get_z(h, Zh)
+        e_t += time.perf_counter() - t0
+        e_u += capi.csc_shard_updates(h)
+    e_tmax, e_uall = over_ranks(dist, "cuda", e_t, e_u)
+    capi.csc_destroy(h)
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": u_all / (t_max * 1e-3), "unit": "updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD} per rank: one signal of {world} x {T1} samples "
+                                   f"in {world} shards", "P": pb.P, "K": pb.K, "L": pb.L,
+                       "T": pb.T, "segments": M, "updates_per_visit": args.updates_per_visit,
+                       "tol": args.tol, "lambda": "0.1*lambda_max",
+                       "l2": "flushed between steps (256 MB write)",
+                       "parallelism": f"shards x{world}: halo exchange per phase over NCCL"},
+            "converged": bool(res["converged"]), "sweeps": res["sweeps"],
+            "resyncs": res["resyncs"], "objective": res["E"],
+            "e2e": {"value": e_uall / e_tmax, "unit": "updates/s",
+                    "h2d_bytes_per_step": int(4 * pb.P * n0),
+                    "d2h_bytes_per_step": int(4 * pb.K * plan["col_count"])}}))
+    dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -413,6 +585,7 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        return sharded_main(args, torch, dist, world, rank)
 
     from paper_1705_10087_gb300 import build, capi, synth
     build.build()
@@ -564,6 +737,8 @@ def main():
     }
     if sweep:
         line["segment_sweep"] = sweep
+    if world == 1 and not args.no_verylong:
+        line["verylong"] = verylong_leg(args, capi, torch)
     if world == 1 and not args.no_batch:
         line["batch"] = batch_leg(args, capi, torch)
     if world == 1 and not args.no_serve:
@@ -571,6 +746,8 @@ def main():
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(pb, lam, args.tol, args.segments,
                                             args.updates_per_visit)
+        line["cpu_baseline_multicore"] = cpu_baseline_multicore(
+            pb, lam, args.tol, args.segments, args.updates_per_visit)
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

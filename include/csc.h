@@ -326,6 +326,11 @@ int csc_objective_noalloc(const float *D, int K, int P, int L, const float *X, i
  */
 int csc_check_wait_timeout(int64_t polls);
 
+/* Device time in ms of the beta0 kernel (D~ * X) of the last csc_init,
+ * measured with a CUDA event pair on the handle's stream when the handle's
+ * opts.time_kernels is 1; -1 otherwise. */
+int csc_init_time(csc_handle_t h, double *beta0_ms);
+
 /* Number of kernels launched through this handle since it was created. */
 int csc_kernel_launches(csc_handle_t h, int64_t *out);
 

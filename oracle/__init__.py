@@ -48,8 +48,9 @@ def build(force: bool = False) -> str:
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-std=c11", "-fPIC", "-shared",
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _SO)
-    from . import csc2d
+    from . import baseline_omp, csc2d
     csc2d.build(force)
+    baseline_omp.build(force)
     return _SO
 
 

@@ -79,6 +79,19 @@ class csc_request_info(ctypes.Structure):
 CSC_REQ_QUEUED, CSC_REQ_ACTIVE, CSC_REQ_DONE = 0, 1, 2
 
 
+class csc_shard_plan(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int64), ("Tz", ctypes.c_int64), ("L", ctypes.c_int32),
+                ("M", ctypes.c_int32), ("phases", ctypes.c_int32), ("world", ctypes.c_int32),
+                ("rank", ctypes.c_int32), ("seg_first", ctypes.c_int32),
+                ("seg_count", ctypes.c_int32), ("col_first", ctypes.c_int64),
+                ("col_count", ctypes.c_int64), ("halo_left", ctypes.c_int64),
+                ("halo_right", ctypes.c_int64), ("x_first", ctypes.c_int64),
+                ("x_count", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 class CscError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"csc error {status}: {message}")
@@ -121,6 +134,7 @@ def load(path: str | None = None):
     lib.csc_plan.argtypes = [_i64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                              ctypes.POINTER(ctypes.c_int), _vp]
     lib.csc_kernel_launches.argtypes = [_vp, ctypes.POINTER(_i64)]
+    lib.csc_init_time.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
     lib.csc_check_wait_timeout.argtypes = [_i64]
     lib.csc_objective_noalloc.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp,
                                           _i64, _vp, ctypes.c_double, _vp, _vp]
@@ -144,16 +158,31 @@ def load(path: str | None = None):
                                       ctypes.POINTER(_i64)]
     lib.csc_server_kernel_launches.argtypes = [_vp, ctypes.POINTER(_i64)]
     lib.csc_server_destroy.argtypes = [_vp]
+    lib.csc_shard_plan_make.argtypes = [_i64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.POINTER(csc_shard_plan)]
+    lib.csc_shard_init.argtypes = [_vp, ctypes.POINTER(csc_shard_plan), _vp, ctypes.c_double]
+    lib.csc_shard_phase.argtypes = [_vp, ctypes.c_int, ctypes.c_double]
+    for name in ("csc_shard_halo_out", "csc_shard_halo_in", "csc_shard_z_out",
+                 "csc_shard_z_in"):
+        getattr(lib, name).argtypes = [_vp, _vp, _vp]
+    lib.csc_shard_updates.argtypes = [_vp, ctypes.POINTER(_i64)]
+    lib.csc_shard_resync.argtypes = [_vp, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    lib.csc_shard_objective.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
+    lib.csc_shard_get_z.argtypes = [_vp, _vp]
     lib.csc_last_error_string.argtypes = []
     lib.csc_last_error_string.restype = ctypes.c_char_p
     for name in ("csc_setup", "csc_init", "csc_solve", "csc_destroy", "csc_lambda_max",
                  "csc_get_beta", "csc_get_dtd", "csc_objective", "csc_get_trace", "csc_plan",
-                 "csc_kernel_launches", "csc_objective_noalloc", "csc_init_batch",
+                 "csc_kernel_launches", "csc_init_time", "csc_objective_noalloc", "csc_init_batch",
                  "csc_set_lambda", "csc_lambda_max_batch", "csc_get_objectives",
                  "csc_autotune", "csc_server_create", "csc_server_add_dictionary",
                  "csc_server_submit", "csc_server_step", "csc_server_info", "csc_server_fetch",
                  "csc_server_completed", "csc_check_wait_timeout", "csc_kkt",
-                 "csc_server_memory", "csc_server_kernel_launches", "csc_server_destroy"):
+                 "csc_server_memory", "csc_server_kernel_launches", "csc_server_destroy",
+                 "csc_shard_plan_make", "csc_shard_init", "csc_shard_phase",
+                 "csc_shard_halo_out", "csc_shard_halo_in", "csc_shard_z_out",
+                 "csc_shard_z_in", "csc_shard_updates", "csc_shard_resync",
+                 "csc_shard_objective", "csc_shard_get_z"):
         getattr(lib, name).restype = ctypes.c_int
     if path == _build.LIB:
         _lib = lib
@@ -401,6 +430,13 @@ def csc_objective_noalloc(D, X, Z, lam: float, out=None, stream=None) -> float:
     return float(out.item())
 
 
+def csc_init_time(h) -> float:
+    """Device ms of the last csc_init's beta0 kernel (opts.time_kernels = 1), else -1."""
+    v = ctypes.c_double(0.0)
+    _check(load().csc_init_time(h, ctypes.byref(v)))
+    return v.value
+
+
 def csc_kernel_launches(h) -> int:
     v = _i64(0)
     _check(load().csc_kernel_launches(h, ctypes.byref(v)))
@@ -491,3 +527,93 @@ def csc_server_kernel_launches(s) -> int:
 
 def csc_server_destroy(s) -> None:
     _check(load().csc_server_destroy(s))
+
+
+# ------------------------------------------------------------------ shards
+
+def csc_shard_plan_make(T: int, L: int, M: int, world: int, rank: int) -> dict:
+    """Host-only plan of rank `rank` of `world` (include/csc_shard.h)."""
+    p = csc_shard_plan()
+    _check(load().csc_shard_plan_make(int(T), int(L), int(M), int(world), int(rank),
+                                      ctypes.byref(p)))
+    return p.as_dict()
+
+
+def _plan_struct(plan: dict) -> csc_shard_plan:
+    p = csc_shard_plan()
+    for name, _ in p._fields_:
+        setattr(p, name, int(plan[name]))
+    return p
+
+
+def _check_block(h, a, width: int, what: str):
+    if width == 0 or a is None:
+        return
+    if getattr(h, "K", None) is not None and _shape(a) != (h.K, width):
+        raise ValueError(f"{what} must be [K={h.K}, {width}], got shape {_shape(a)}")
+
+
+def csc_shard_init(h, plan: dict, X, lam: float) -> None:
+    """X: this rank's samples [P, plan['x_count']]."""
+    _check_signal(h, X)
+    if int(X.shape[1]) != int(plan["x_count"]):
+        raise ValueError(f"X must hold x_count = {plan['x_count']} samples per channel")
+    p = _plan_struct(plan)
+    _check(load().csc_shard_init(h, ctypes.byref(p), _ptr(X), float(lam)))
+    if isinstance(h, Handle):
+        h.Tz = None
+        h.shard = dict(plan)
+
+
+def csc_shard_phase(h, p: int, tol: float) -> None:
+    _check(load().csc_shard_phase(h, int(p), float(tol)))
+
+
+def _blocks(h, name, a, b):
+    sh = getattr(h, "shard", None)
+    if sh is not None:
+        _check_block(h, a, int(sh["halo_left"]), f"{name} left block")
+        _check_block(h, b, int(sh["halo_right"]), f"{name} right block")
+    return _ptr(a, True) if a is not None else None, _ptr(b, True) if b is not None else None
+
+
+def csc_shard_halo_out(h, to_left, to_right) -> None:
+    _check(load().csc_shard_halo_out(h, *_blocks(h, "halo_out", to_left, to_right)))
+
+
+def csc_shard_halo_in(h, from_left, from_right) -> None:
+    _check(load().csc_shard_halo_in(h, *_blocks(h, "halo_in", from_left, from_right)))
+
+
+def csc_shard_z_out(h, to_left, to_right) -> None:
+    _check(load().csc_shard_z_out(h, *_blocks(h, "z_out", to_left, to_right)))
+
+
+def csc_shard_z_in(h, from_left, from_right) -> None:
+    _check(load().csc_shard_z_in(h, *_blocks(h, "z_in", from_left, from_right)))
+
+
+def csc_shard_updates(h) -> int:
+    v = _i64(0)
+    _check(load().csc_shard_updates(h, ctypes.byref(v)))
+    return v.value
+
+
+def csc_shard_resync(h, tol: float) -> float:
+    v = ctypes.c_double(0.0)
+    _check(load().csc_shard_resync(h, float(tol), ctypes.byref(v)))
+    return v.value
+
+
+def csc_shard_objective(h) -> float:
+    v = ctypes.c_double(0.0)
+    _check(load().csc_shard_objective(h, ctypes.byref(v)))
+    return v.value
+
+
+def csc_shard_get_z(h, out) -> None:
+    sh = getattr(h, "shard", None)
+    if sh is not None and getattr(h, "K", None) is not None:
+        if int(np.prod(_shape(out))) != h.K * int(sh["col_count"]):
+            raise ValueError("Z_out must hold K * col_count values")
+    _check(load().csc_shard_get_z(h, _ptr(out, True)))

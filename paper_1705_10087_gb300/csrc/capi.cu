@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "csc_internal.cuh"
+#include "handle.cuh"
 #include "host_util.cuh"
 
 using namespace csc;
@@ -52,32 +53,6 @@ int fail(int code, const char *fmt, ...)
     if (dev_guard_.err != cudaSuccess)                                                   \
         return fail(CSC_ECUDA, "cudaSetDevice(%d) failed: %s", (int)(dev),                \
                     cudaGetErrorString(dev_guard_.err))
-
-// Small device-side state of a handle (one allocation).
-struct Scratch {
-    long long upd[kPhaseRing];
-    double dec[kPhaseRing];
-    unsigned long long tend[kPhaseRing];
-    long long total;
-    int done;
-    int pad;
-    long long visits;
-    unsigned int lmax_bits;
-    unsigned long long tstart;
-    unsigned long long red[8];
-    double obj[2];
-    double x2;  // sum X^2 of the last csc_init
-    int tc_err;  // a bounded wait of the tensor-core beta0 kernel gave up
-    int qhead[2];  // drain launches: next queue entry, queue length
-    int gctr[2];   // graph replays: launch index of the next launch, first index of the round
-};
-
-// Host mirror of what the solve loop polls (pinned).
-struct Poll {
-    long long total;
-    int done;
-    int pad;
-};
 
 // Phases of the schedule for one signal: co-active segments m, m' (m == m'
 // mod c) must leave at least 2L-2 samples between them, (c-1) w_min >= 2L-2.
@@ -121,85 +96,6 @@ int csc_record_error(int code, const char *fmt, ...)
     g_err = buf;
     return code;
 }
-
-struct csc_handle_s {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    csc_opts opts{};
-    int K = 0, P = 0, L = 0;
-    float *D = nullptr, *C = nullptr, *Ct = nullptr, *norms = nullptr;
-    size_t cap_D = 0, cap_C = 0, cap_Ct = 0, cap_n = 0;
-
-    // problem: n signals concatenated in time, T samples, Tz = T - L + 1 columns
-    bool initialized = false;
-    int64_t T = 0, Tz = 0;
-    int n = 0;
-    std::vector<int64_t> a;         // [n+1] sample starts
-    std::vector<double> lam;        // [n]
-    std::vector<double> lmax;       // [n]
-    std::vector<double> E_sig;      // [n] objectives of the last solve / csc_objective
-    std::vector<SigDesc> sigs;      // [n] descriptors of the signals
-    SigDesc *d_sig = nullptr;
-    size_t cap_sig = 0;
-    SigDesc *d_sig_alt = nullptr;   // [n] the same over a caller's Z (csc_kkt)
-    size_t cap_sig_alt = 0;
-    // objective / absmax tiles (kTile samples) and resync tiles (kResyncCols columns)
-    std::vector<int64_t> tile_off;  // [n+1] first objective tile of each signal
-    int64_t ntiles = 0, nrtiles = 0;
-    int64_t *d_tile_s = nullptr, *d_tile_off = nullptr, *d_rtile_s = nullptr;
-    int *d_tile_sig = nullptr, *d_rtile_sig = nullptr;
-    size_t cap_rtile_s = 0, cap_rtile_sig = 0;
-    double *d_E = nullptr;
-    unsigned int *d_lmax = nullptr;
-    size_t cap_tile_s = 0, cap_tile_off = 0, cap_tile_sig = 0, cap_E = 0, cap_lmax = 0;
-
-    // r = beta - ||D_k||^2 Z, the form of beta the kernels keep (csc_internal.cuh)
-    float *X = nullptr, *r = nullptr, *beta0 = nullptr, *Z = nullptr;
-    size_t cap_X = 0, cap_r = 0, cap_beta0 = 0, cap_Z = 0;
-    double *partials = nullptr;
-    size_t cap_partials = 0;
-
-    // segment plan (rebuilt when the signals, lambdas or segment options change)
-    bool plan_ok = false;
-    // what the current plan and tile tables were built for (re-used when a
-    // csc_setup / csc_init repeats the same signal lengths and options)
-    std::vector<int64_t> plan_a, tiles_a;
-    int plan_L = -1, plan_segments = -1, plan_width = -1, tiles_L = -1;
-    std::vector<int> plan_seg0, plan_nseg;
-    int M = 0, c = 0, w_max = 0;
-    std::vector<int> phase_off;  // [c+1] into the phase list
-    int64_t *d_seg_s = nullptr, *d_seg_e = nullptr;
-    int *d_seg_sig = nullptr;
-    int *d_phase_list = nullptr;
-    size_t cap_seg_s = 0, cap_seg_e = 0, cap_seg_sig = 0, cap_phase = 0;
-    unsigned char *dirty = nullptr, *touched = nullptr;
-    size_t cap_dirty = 0, cap_touched = 0;
-    int *d_queue = nullptr;  // drain launches: the phase's segments to visit
-    size_t cap_queue = 0;
-    // the poll batch (S sweeps of c phases) captured as a CUDA graph, and what
-    // it was captured for
-    cudaGraphExec_t gexec = nullptr;
-    std::vector<unsigned char> gkey, gkey_seen;
-    cudaStream_t cap_stream = nullptr;  // captures happen here (not on a legacy stream)
-    float *tile_rep = nullptr;  // stored resync report per resync tile
-    size_t cap_tile_rep = 0;
-
-    float *tmpZ = nullptr, *tmpB = nullptr;
-    size_t cap_tmpZ = 0, cap_tmpB = 0;
-    Scratch *sc = nullptr;
-    Poll *poll = nullptr;  // pinned
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    cudaEvent_t *kev = nullptr;  // per-launch timing events (2 per launch of a poll batch)
-    int n_kev = 0;
-    int64_t launches = 0;        // kernels launched through this handle
-    bool z_is_zero = false;      // Z == 0 since csc_init: E(Z) = sum X^2 / 2 is known
-    // last solve
-    int64_t g_used = 0;
-    double E_start = 0.0;
-
-    Tiles obj_tiles() const { return Tiles{d_tile_sig, d_tile_s, ntiles}; }
-    Tiles resync_tiles() const { return Tiles{d_rtile_sig, d_rtile_s, nrtiles}; }
-};
 
 namespace {
 
@@ -469,7 +365,10 @@ int csc_destroy(csc_handle_t h)
                     h->tmpZ,       h->tmpB,       h->sc,         h->d_sig,      h->d_tile_s,
                     h->d_tile_off, h->d_tile_sig, h->d_rtile_s,  h->d_rtile_sig, h->d_E,
                     h->d_lmax,     h->d_seg_s,    h->d_seg_e,    h->d_seg_sig,  h->d_phase_list,
-                    h->touched,    h->tile_rep,   h->d_queue,    h->d_sig_alt};
+                    h->touched,    h->tile_rep,   h->d_queue,    h->d_sig_alt,
+                    h->nz_count,   h->nz_ent,     h->shard.d_rt_sig, h->shard.d_ot_sig,
+                    h->shard.d_rt_s, h->shard.d_rt_e, h->shard.d_ot_s, h->shard.d_ot_e,
+                    h->shard.d_ot_off, h->shard.stage};
     for (void *p : bufs)
         cudaFree(p);
     if (h->poll)
@@ -478,6 +377,10 @@ int csc_destroy(csc_handle_t h)
         cudaEventDestroy(h->ev0);
     if (h->ev1)
         cudaEventDestroy(h->ev1);
+    if (h->ev_i0)
+        cudaEventDestroy(h->ev_i0);
+    if (h->ev_i1)
+        cudaEventDestroy(h->ev_i1);
     for (int i = 0; i < h->n_kev; i++)
         cudaEventDestroy(h->kev[i]);
     delete[] h->kev;
@@ -535,6 +438,7 @@ int csc_setup(csc_handle_t *hp, const float *D, int K, int P, int L, const csc_o
     h->L = L;
     h->initialized = false;
     h->plan_ok = false;
+    h->shard.on = false;
     auto body = [&]() -> int {
         CSC_CUDA(grow(&h->D, &h->cap_D, (size_t)K * P * L));
         CSC_CUDA(grow(&h->C, &h->cap_C, (size_t)K * K * (2 * L - 1)));
@@ -581,6 +485,7 @@ int csc_init_batch(csc_handle_t h, const float *X, const int64_t *T, int n, cons
     const int64_t Tz = Ttot - h->L + 1;
     if (Tz >= ((int64_t)1 << 31) - 1)
         return fail(CSC_EINVAL, "csc_init: T - L + 1 must be below 2^31 - 1 columns");
+    h->shard.on = false;  // csc_shard_init sets it again after this
     CSC_ON_DEVICE(h->device);
     h->initialized = false;
     h->plan_ok = false;
@@ -637,6 +542,8 @@ int csc_init_batch(csc_handle_t h, const float *X, const int64_t *T, int n, cons
     CSC_CUDA(grow(&h->d_E, &h->cap_E, (size_t)n));
     CSC_CUDA(grow(&h->d_lmax, &h->cap_lmax, (size_t)n));
     CSC_CUDA(grow(&h->partials, &h->cap_partials, 2 * (size_t)h->ntiles));
+    CSC_CUDA(grow(&h->nz_count, &h->cap_nz_count, (size_t)h->nrtiles));
+    CSC_CUDA(grow(&h->nz_ent, &h->cap_nz_ent, (size_t)h->nrtiles * kNzCap));
     {
         int rc = set_lambdas(h, lambda);  // uploads the descriptors; waits for the uploads
         if (rc != CSC_OK)
@@ -646,13 +553,29 @@ int csc_init_batch(csc_handle_t h, const float *X, const int64_t *T, int n, cons
     CSC_CUDA(cudaMemsetAsync(&h->sc->lmax_bits, 0, sizeof(unsigned), s));
     CSC_CUDA(cudaMemsetAsync(&h->sc->x2, 0, sizeof(double), s));
     CSC_CUDA(cudaMemsetAsync(&h->sc->tc_err, 0, sizeof(int), s));
+    const bool timed = h->opts.time_kernels != 0;
+    if (timed && !h->ev_i0) {
+        CSC_CUDA(cudaEventCreate(&h->ev_i0));
+        CSC_CUDA(cudaEventCreate(&h->ev_i1));
+    }
+    if (timed)
+        CSC_CUDA(cudaEventRecord(h->ev_i0, s));
+    // a cold start (Z = 0) has r = beta0: the kernel writes both
     CSC_CUDA(launch_dtx_any(h->D, h->X, h->K, h->P, h->L, Ttot, h->opts.init_mode, h->beta0,
-                            &h->sc->lmax_bits, &h->sc->x2, &h->sc->tc_err, s));
-    CSC_CUDA(cudaMemsetAsync(h->d_lmax, 0, sizeof(unsigned) * n, s));
-    CSC_CUDA(launch_signal_absmax(h->d_sig, h->obj_tiles(), h->K, h->d_lmax, s));
-    h->launches += 2;
-    if (Z0) {
+                            Z0 ? nullptr : h->r, &h->sc->lmax_bits, &h->sc->x2, &h->sc->tc_err,
+                            s));
+    if (timed)
+        CSC_CUDA(cudaEventRecord(h->ev_i1, s));
+    h->launches += 1;
+    if (n > 1) {
+        // per-signal maxima (the kernel's maximum also covers the columns
+        // between signals, which belong to no problem)
+        CSC_CUDA(cudaMemsetAsync(h->d_lmax, 0, sizeof(unsigned) * n, s));
+        CSC_CUDA(launch_signal_absmax(h->d_sig, h->obj_tiles(), h->K, h->d_lmax, s));
         h->launches += 1;
+    }
+    if (Z0) {
+        h->launches += 2;  // bucket lists + resync
         CSC_CUDA(copy_in(h->Z, Z0, sizeof(float) * nz, s));
         // the columns between signals belong to no problem: 0
         for (int i = 0; i + 1 < n; i++)
@@ -660,15 +583,14 @@ int csc_init_batch(csc_handle_t h, const float *X, const int64_t *T, int n, cons
                                        sizeof(float) * (h->L - 1), h->K, s));
         CSC_CUDA(cudaMemsetAsync(h->sc->red, 0, sizeof(h->sc->red), s));
         CSC_CUDA(launch_resync(h->d_sig, h->resync_tiles(), h->C, h->norms, h->K, h->L, 1,
-                               h->sc->red, 0, nullptr, 0.f, nullptr, nullptr, s));
+                               h->sc->red, 0, nullptr, 0.f, nullptr, nullptr, h->nz_lists(), s));
     } else {
         CSC_CUDA(cudaMemsetAsync(h->Z, 0, sizeof(float) * nz, s));
-        CSC_CUDA(cudaMemcpyAsync(h->r, h->beta0, sizeof(float) * nz, cudaMemcpyDeviceToDevice, s));
     }
     std::vector<unsigned> bits(n);
     int tc_err = 0;
-    CSC_CUDA(cudaMemcpyAsync(bits.data(), h->d_lmax, sizeof(unsigned) * n, cudaMemcpyDeviceToHost,
-                             s));
+    CSC_CUDA(cudaMemcpyAsync(bits.data(), n > 1 ? h->d_lmax : &h->sc->lmax_bits,
+                             sizeof(unsigned) * n, cudaMemcpyDeviceToHost, s));
     CSC_CUDA(cudaMemcpyAsync(&tc_err, &h->sc->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     CSC_CUDA(cudaStreamSynchronize(s));
     if (tc_err)
@@ -677,6 +599,12 @@ int csc_init_batch(csc_handle_t h, const float *X, const int64_t *T, int n, cons
         float v;
         std::memcpy(&v, &bits[i], sizeof v);
         h->lmax[i] = v;
+    }
+    h->init_ms = -1.0;
+    if (timed) {
+        float ms = 0.f;
+        CSC_CUDA(cudaEventElapsedTime(&ms, h->ev_i0, h->ev_i1));
+        h->init_ms = ms;
     }
     h->z_is_zero = Z0 == nullptr;
     h->initialized = true;
@@ -738,6 +666,8 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
         return fail(CSC_ESTATE, "csc_solve: call csc_init first");
     if (!(tol > 0.0) || max_updates < 1)
         return fail(CSC_EINVAL, "csc_solve: need tol > 0 and max_updates >= 1");
+    if (h->shard.on)
+        return fail(CSC_ESTATE, "csc_solve: the handle holds a shard (use the csc_shard_* calls)");
     CSC_ON_DEVICE(h->device);
     cudaStream_t s = h->stream;
     const int64_t Tz = h->Tz;
@@ -949,9 +879,9 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
             CSC_CUDA(cudaMemsetAsync(h->dirty, 0, (size_t)M, s));
         CSC_CUDA(launch_resync(h->d_sig, h->resync_tiles(), h->C, h->norms, h->K, h->L, 1,
                                sc->red, 0, last ? nullptr : h->dirty, tol_inner, h->touched,
-                               h->tile_rep, s));
+                               h->tile_rep, h->nz_lists(), s));
         CSC_CUDA(cudaMemsetAsync(h->touched, 0, (size_t)M, s));
-        h->launches += 1;
+        h->launches += 2;
         unsigned long long red[8];
         CSC_CUDA(cudaMemcpyAsync(red, sc->red, sizeof red, cudaMemcpyDeviceToHost, s));
         CSC_CUDA(cudaStreamSynchronize(s));
@@ -975,8 +905,8 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
         // optimality report against a fresh r, leaving r unchanged
         CSC_CUDA(cudaMemsetAsync(sc->red, 0, sizeof(sc->red), s));
         CSC_CUDA(launch_resync(h->d_sig, h->resync_tiles(), h->C, h->norms, h->K, h->L, 0,
-                               sc->red, 0, nullptr, 0.f, h->touched, h->tile_rep, s));
-        h->launches += 1;
+                               sc->red, 0, nullptr, 0.f, h->touched, h->tile_rep, h->nz_lists(), s));
+        h->launches += 2;
     }
     CSC_CUDA(cudaEventRecord(h->ev1, s));
     double E = 0.0;
@@ -1147,6 +1077,16 @@ int csc_check_wait_timeout(int64_t polls)
     return CSC_OK;
 }
 
+int csc_init_time(csc_handle_t h, double *beta0_ms)
+{
+    if (!h || !beta0_ms)
+        return fail(CSC_EINVAL, "csc_init_time: null argument");
+    if (!h->initialized)
+        return fail(CSC_ESTATE, "csc_init_time: call csc_init first");
+    *beta0_ms = h->init_ms;
+    return CSC_OK;
+}
+
 int csc_kernel_launches(csc_handle_t h, int64_t *out)
 {
     if (!h || !out)
@@ -1234,8 +1174,8 @@ int csc_kkt(csc_handle_t h, const float *Z, double *out)
     CSC_CUDA(upload(&h->d_sig_alt, &h->cap_sig_alt, alt, s));
     CSC_CUDA(cudaMemsetAsync(h->sc->red, 0, sizeof(h->sc->red), s));
     CSC_CUDA(launch_resync(h->d_sig_alt, h->resync_tiles(), h->C, h->norms, h->K, h->L, 0,
-                           h->sc->red, 0, nullptr, 0.f, nullptr, nullptr, s));
-    h->launches += 1;
+                           h->sc->red, 0, nullptr, 0.f, nullptr, nullptr, h->nz_lists(), s));
+    h->launches += 2;
     unsigned long long red[8];
     CSC_CUDA(cudaMemcpyAsync(red, h->sc->red, sizeof red, cudaMemcpyDeviceToHost, s));
     CSC_CUDA(cudaStreamSynchronize(s));

@@ -1,0 +1,831 @@
+// The 2-D variant (include/csc2d.h): images cut into row bands.
+//
+// The paper's conclusion names images cut along one direction as the way to
+// keep the 1-D analysis: a band of rows has a neighbour above and one below,
+// exactly as a 1-D segment has one on each side.  Every definition is that of
+// Sec. 2.1 with 2-D lags.  With image X[P][H][W], atoms D[K][P][h][w] and
+// activations Z[K][Hz][Wz] (Hz = H-h+1, Wz = W-w+1, "valid" placement):
+//   beta0_k[i][j]  = sum_{p,u,v} D[k][p][u][v] X[p][i+u][j+v]            (Alg. 1 init)
+//   C[k][k0][a][b] = sum_{p,u,v} D[k][p][u][v] D[k0][p][u+a-h+1][v+b-w+1] (S of Eq. beta_up)
+// and the solver keeps r = beta - ||D_k||^2 Z as in 1-D (csc_internal.cuh):
+// an update dZ of Z_k0[i0][j0] changes r_k[i][j] by -C[k][k0][i-i0+h-1][j-j0+w-1] dZ
+// for every (k, i, j) of the (2h-1) x (2w-1) window, own coordinate included.
+//
+// Bands: band m of M covers rows [floor(m Hz / M), floor((m+1) Hz / M)) and
+// all columns; bands m == p (mod c) run in phase p, with (c-1) times the
+// narrowest band at least 2h-2 rows, so that co-active bands' windows never
+// meet and each phase equals a sequential run of its bands.  One thread
+// block per active band: it keeps, per position (i, j) of its band, the best
+// coordinate over k as a 64-bit key (|Delta Z| bits, ~flat index; ties to the
+// lowest (k Hz + i) Wz + j) in shared memory, and repeats block argmax ->
+// update -> re-evaluation of the window's positions, writing the window rows
+// outside its band (idle neighbours) with atomicAdd.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "csc2d.h"
+#include "csc_internal.cuh"
+#include "host_util.cuh"
+
+using namespace csc;
+
+int csc_record_error(int code, const char *fmt, ...);
+
+namespace {
+
+#define C2_CUDA(expr)                                                                        \
+    do {                                                                                     \
+        cudaError_t e_ = (expr);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return csc_record_error(e_ == cudaErrorMemoryAllocation ? CSC_ENOMEM : CSC_ECUDA, \
+                                    "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_),   \
+                                    __FILE__, __LINE__);                                     \
+    } while (0)
+
+constexpr int kB2 = 256;        // threads of a band block
+constexpr int kMaxK2 = 64;      // atoms (one bit each in a 64-bit mask)
+constexpr int kMaxWin = 4096;   // (2h-1)(2w-1) window positions
+constexpr int kTile2 = 32;      // columns per resync / objective tile
+constexpr int kList2 = 2048;    // nonzeros gathered per round
+
+struct Dims {
+    int K, P, h, w;
+    int64_t H, W, Hz, Wz;
+};
+
+// ---------------------------------------------------------------- setup
+
+// C (by lag, float4 groups of atoms): Ct[((k0 * KQ + q) * A + lag) * 4 + e] =
+// C[k = 4q+e][k0][a][b], lag = a (2w-1) + b, A = (2h-1)(2w-1).  FP64 sums.
+__global__ void dtd2d_kernel(const float *__restrict__ D, Dims d, int KQ, float *__restrict__ Ct,
+                             float *__restrict__ norms)
+{
+    const int H2 = 2 * d.h - 1, W2 = 2 * d.w - 1, A = H2 * W2;
+    const int64_t n = (int64_t)d.K * KQ * A * 4;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int e = (int)(i & 3);
+        const int64_t rest = i >> 2;
+        const int lag = (int)(rest % A);
+        const int64_t kq = rest / A;
+        const int q = (int)(kq % KQ), k0 = (int)(kq / KQ);
+        const int k = 4 * q + e;
+        double acc = 0.0;
+        if (k < d.K) {
+            const int da = lag / W2 - (d.h - 1), db = lag % W2 - (d.w - 1);
+            for (int p = 0; p < d.P; p++)
+                for (int u = 0; u < d.h; u++) {
+                    const int u2 = u + da;
+                    if (u2 < 0 || u2 >= d.h)
+                        continue;
+                    for (int v = 0; v < d.w; v++) {
+                        const int v2 = v + db;
+                        if (v2 < 0 || v2 >= d.w)
+                            continue;
+                        acc += (double)D[(((int64_t)k * d.P + p) * d.h + u) * d.w + v] *
+                               (double)D[(((int64_t)k0 * d.P + p) * d.h + u2) * d.w + v2];
+                    }
+                }
+            if (k == k0 && lag == (d.h - 1) * W2 + (d.w - 1))
+                norms[k] = (float)acc;
+        }
+        Ct[i] = (float)acc;
+    }
+}
+
+// beta0 (and r = beta0 for Z = 0) in FP64 sums rounded once; max |beta0| and
+// sum X^2 (E(0) = sum X^2 / 2).
+__global__ void dtx2d_kernel(const float *__restrict__ D, const float *__restrict__ X, Dims d,
+                             float *__restrict__ beta0, float *__restrict__ r,
+                             unsigned *__restrict__ absmax, double *__restrict__ x2)
+{
+    const int64_t n = (int64_t)d.K * d.Hz * d.Wz;
+    float amax = 0.f;
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n;
+         o += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = o % d.Wz, i = (o / d.Wz) % d.Hz;
+        const int k = (int)(o / (d.Wz * d.Hz));
+        double acc = 0.0;
+        for (int p = 0; p < d.P; p++)
+            for (int u = 0; u < d.h; u++) {
+                const float *xr = X + ((int64_t)p * d.H + i + u) * d.W + j;
+                const float *dr = D + (((int64_t)k * d.P + p) * d.h + u) * d.w;
+                for (int v = 0; v < d.w; v++)
+                    acc += (double)dr[v] * (double)xr[v];
+            }
+        beta0[o] = (float)acc;
+        r[o] = (float)acc;
+        amax = fmaxf(amax, fabsf((float)acc));
+    }
+    double s = 0.0;
+    const int64_t nx = (int64_t)d.P * d.H * d.W;
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < nx;
+         o += (int64_t)gridDim.x * blockDim.x)
+        s += (double)X[o] * (double)X[o];
+    for (int off = 16; off > 0; off >>= 1) {
+        amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+        s += __shfl_xor_sync(0xffffffffu, s, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(absmax, __float_as_uint(amax));
+        atomicAdd(x2, s);
+    }
+}
+
+// ---------------------------------------------------------------- phase
+
+struct BandParams {
+    float *r, *Z;
+    const float *Ct, *norms;
+    const int64_t *band_s;   // [M+1] first row of each band
+    const int *list;         // bands of this phase
+    unsigned char *dirty;    // [M]
+    long long *upd;          // [1] updates of this launch's sweep counter
+    double *dec;             // [1] objective decrease (Prop. A.1)
+    Dims d;
+    int M, KQ, u;
+    float lam, tol;
+};
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
+{
+    unsigned hi = (unsigned)(v >> 32);
+    const unsigned hmax = __reduce_max_sync(0xffffffffu, hi);
+    unsigned lo = hi == hmax ? (unsigned)v : 0u;
+    const unsigned lmax = __reduce_max_sync(0xffffffffu, lo);
+    return ((unsigned long long)hmax << 32) | lmax;
+}
+
+// One visit of a band per block (a block of the phase's list).
+__global__ void __launch_bounds__(kB2) band_kernel(BandParams bp)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ unsigned long long s_key[kB2 / 32];
+    __shared__ float s_z[kB2 / 32], s_d[kB2 / 32];
+    __shared__ int s_k[kB2 / 32], s_pos[kB2 / 32];
+    __shared__ float s_nrm[kMaxK2], s_rn[kMaxK2];
+    __shared__ double s_dec[kB2 / 32];
+    const int m = bp.list[blockIdx.x];
+    if (!bp.dirty[m])
+        return;  // uniform: every thread reads the same flag
+    const Dims d = bp.d;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t i_lo = bp.band_s[m], i_hi = bp.band_s[m + 1];
+    const int64_t Wz = d.Wz, HWz = d.Hz * d.Wz;
+    const int npos = (int)((i_hi - i_lo) * Wz);
+    unsigned long long *key = reinterpret_cast<unsigned long long *>(sm);
+    float *cz = reinterpret_cast<float *>(key + npos);
+    float *cd = cz + npos;
+    int *ck = reinterpret_cast<int *>(cd + npos);
+    const int K = d.K, H2 = 2 * d.h - 1, W2 = 2 * d.w - 1, A = H2 * W2;
+    const float lam = bp.lam;
+    for (int k = tid; k < K; k += kB2) {
+        s_nrm[k] = bp.norms[k];
+        s_rn[k] = __frcp_rn(bp.norms[k]);
+    }
+    __syncthreads();
+    // best coordinate of band position pos (row i_lo + pos / Wz, column pos % Wz)
+    auto eval = [&](int pos) {
+        const int64_t e = (i_lo + pos / Wz) * Wz + pos % Wz;
+        float best = -1.f, bz = 0.f, bd = 0.f;
+        int bk = 0;
+        for (int k = 0; k < K; k++) {
+            const float r = bp.r[k * HWz + e], z = bp.Z[k * HWz + e];
+            if (z == 0.f && fabsf(r) <= lam)
+                continue;
+            float zn, dd;
+            coord_step(r, z, s_nrm[k], s_rn[k], lam, &zn, &dd);
+            if (fabsf(dd) > best) {
+                best = fabsf(dd);
+                bk = k;
+                bz = zn;
+                bd = dd;
+            }
+        }
+        // flat index within the band, same order as (k Hz + i) Wz + j
+        const unsigned flat = (unsigned)bk * (unsigned)npos + (unsigned)pos;
+        key[pos] = best > 0.f ? ((unsigned long long)__float_as_uint(best) << 32) | (unsigned)(~flat)
+                              : 0ull;
+        cz[pos] = bz;
+        cd[pos] = bd;
+        ck[pos] = bk;
+    };
+    for (int pos = tid; pos < npos; pos += kB2)
+        eval(pos);
+    int nupd = 0;
+    int64_t imin = i_hi, imax = i_lo - 1;
+    float decrease = 0.f;
+    bool capped = false;
+    for (int it = 0;; it++) {
+        unsigned long long my = 0ull;
+        int mp = 0;
+        for (int pos = tid; pos < npos; pos += kB2)
+            if (key[pos] > my) {
+                my = key[pos];
+                mp = pos;
+            }
+        const unsigned long long wm = warp_max_u64(my);
+        const unsigned win = __ballot_sync(0xffffffffu, my == wm);
+        if (lane == __ffs(win) - 1) {
+            s_key[warp] = wm;
+            s_z[warp] = cz[mp];
+            s_d[warp] = cd[mp];
+            s_k[warp] = ck[mp];
+            s_pos[warp] = mp;
+        }
+        __syncthreads();
+        unsigned long long bk = 0ull;
+        int bw = 0;
+        for (int q = 0; q < kB2 / 32; q++)
+            if (s_key[q] > bk) {
+                bk = s_key[q];
+                bw = q;
+            }
+        const float adz = __uint_as_float((unsigned)(bk >> 32));
+        if (!(adz >= bp.tol))
+            break;
+        if (it >= bp.u) {
+            capped = true;
+            break;
+        }
+        const float znew = s_z[bw], delta = s_d[bw];
+        const int k0 = s_k[bw], pos0 = s_pos[bw];
+        const int64_t i0 = i_lo + pos0 / Wz, j0 = pos0 % Wz;
+        const int64_t e0 = i0 * Wz + j0;
+        if (tid == 0) {
+            // Prop. A.1 from r before this update: dZ (r - n dZ / 2) + lam (|z| - |u|)
+            const float n = s_nrm[k0], z = znew - delta;
+            const float r0 = bp.r[k0 * HWz + e0];
+            decrease += delta * (r0 - 0.5f * n * delta) + lam * (fabsf(z) - fabsf(znew));
+        }
+        __syncthreads();  // r0 read before any thread changes it
+        // Eq. beta_up (r form) on the window, K coefficients per position
+        const float4 *Ct4 = reinterpret_cast<const float4 *>(bp.Ct);
+        for (int lag = tid; lag < A; lag += kB2) {
+            const int64_t i = i0 + lag / W2 - (d.h - 1), j = j0 + lag % W2 - (d.w - 1);
+            if (i < 0 || i >= d.Hz || j < 0 || j >= Wz)
+                continue;
+            const bool own = i >= i_lo && i < i_hi;
+            float *rp = bp.r + i * Wz + j;
+            for (int q = 0; q < bp.KQ; q++) {
+                const float4 c = __ldg(Ct4 + ((int64_t)k0 * bp.KQ + q) * A + lag);
+                const float cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    const int k = 4 * q + e;
+                    if (k >= K)
+                        break;
+                    if (own)
+                        rp[k * HWz] = fmaf(-cv[e], delta, rp[k * HWz]);
+                    else
+                        atomicAdd(rp + k * HWz, -cv[e] * delta);
+                }
+            }
+        }
+        if (tid == 0)
+            bp.Z[k0 * HWz + e0] = znew;
+        __syncthreads();
+        // re-evaluate this thread's positions inside the window
+        for (int pos = tid; pos < npos; pos += kB2) {
+            const int64_t i = i_lo + pos / Wz, j = pos % Wz;
+            if (i >= i0 - (d.h - 1) && i <= i0 + (d.h - 1) && j >= j0 - (d.w - 1) &&
+                j <= j0 + (d.w - 1))
+                eval(pos);
+        }
+        nupd++;
+        imin = i0 < imin ? i0 : imin;
+        imax = i0 > imax ? i0 : imax;
+    }
+    for (int off = 16; off > 0; off >>= 1)
+        decrease += __shfl_xor_sync(0xffffffffu, decrease, off);
+    if (lane == 0)
+        s_dec[warp] = (double)decrease;
+    __syncthreads();
+    if (tid == 0) {
+        double dsum = 0.0;
+        for (int q = 0; q < kB2 / 32; q++)
+            dsum += s_dec[q];
+        bp.dirty[m] = capped ? 1 : 0;
+        if (nupd > 0) {
+            // bands whose rows the windows reached need a visit again
+            const int64_t lo = imin - (d.h - 1), hi = imax + (d.h - 1);
+            for (int mm = m - 1; mm >= 0 && bp.band_s[mm + 1] > lo; mm--)
+                bp.dirty[mm] = 1;
+            for (int mm = m + 1; mm < bp.M && bp.band_s[mm] <= hi; mm++)
+                bp.dirty[mm] = 1;
+            atomicAdd(reinterpret_cast<unsigned long long *>(bp.upd), (unsigned long long)nupd);
+            atomicAdd(bp.dec, dsum);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- exact checks
+
+// Nonzeros of Z in rows [r0, r1) x columns [c0, c1) (at most kList2
+// elements: the callers cut their regions into column chunks that fit), in
+// (k, row, column) order, compacted into list; returns the count (the same
+// in every thread).  Block-wide barriers.
+struct NZ2 {
+    int k;
+    int i, j;
+    float z;
+};
+
+__device__ int compact2(const float *__restrict__ Z, const Dims &d, int64_t r0, int64_t r1,
+                        int64_t c0, int64_t c1, NZ2 *list, int *wc)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int64_t rows = r1 - r0, cols = c1 - c0;
+    const int64_t n = (int64_t)d.K * rows * cols;
+    int base = 0;
+    for (int64_t a = 0; a < n; a += blockDim.x) {
+        const int64_t i = a + tid;
+        float z = 0.f;
+        int k = 0;
+        int64_t ii = 0, jj = 0;
+        if (i < n) {
+            k = (int)(i / (rows * cols));
+            ii = r0 + (i / cols) % rows;
+            jj = c0 + i % cols;
+            z = Z[((int64_t)k * d.Hz + ii) * d.Wz + jj];
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, z != 0.f);
+        if (lane == 0)
+            wc[warp] = __popc(mask);
+        __syncthreads();
+        int off = base, tot = base;
+        for (int q = 0; q < nw; q++) {
+            off += q < warp ? wc[q] : 0;
+            tot += wc[q];
+        }
+        if (z != 0.f)
+            list[off + __popc(mask & ((1u << lane) - 1u))] = NZ2{k, (int)ii, (int)jj, z};
+        __syncthreads();
+        base = tot;
+    }
+    return base;
+}
+
+// r = beta0 - sum C Z (FP64 sums) on one row and kTile2 columns per block
+// (threads: 32 columns x 8 atom groups), and the optimality report as in 1-D:
+// red[0] drift, red[3] max |Delta Z| (no floor), red[4] the coordinate step on
+// the refreshed state (with the float32 floor); write_r = 0 leaves r alone.
+__global__ void __launch_bounds__(256)
+    resync2d_kernel(const float *__restrict__ beta0, float *__restrict__ r,
+                    const float *__restrict__ Z, const float *__restrict__ Ct,
+                    const float *__restrict__ norms, Dims d, int KQ, float lam, int write_r,
+                    unsigned long long *__restrict__ red)
+{
+    __shared__ NZ2 list[kList2];
+    __shared__ int wc[8];
+    __shared__ float bred[3][8];
+    const int tid = threadIdx.x, col = tid & 31, grp = tid >> 5;
+    const int64_t ntc = (d.Wz + kTile2 - 1) / kTile2;
+    const int64_t i = blockIdx.x / ntc, j0 = (blockIdx.x % ntc) * kTile2, j = j0 + col;
+    const int H2 = 2 * d.h - 1, W2 = 2 * d.w - 1, A = H2 * W2;
+    const int64_t r0 = max((int64_t)0, i - (d.h - 1)), r1 = min(d.Hz, i + d.h);
+    const int64_t c0 = max((int64_t)0, j0 - (d.w - 1)), c1 = min(d.Wz, j0 + kTile2 + d.w - 1);
+    constexpr int kPer = (kMaxK2 + 7) / 8;
+    double acc[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; q++)
+        acc[q] = 0.0;
+    // the region's columns in chunks whose K x rows x chunk elements fit the list
+    const int64_t chunk = max((int64_t)1, (int64_t)kList2 / ((int64_t)d.K * (r1 - r0)));
+    for (int64_t ca = c0; ca < c1; ca += chunk) {
+        const int64_t cb = ca + chunk < c1 ? ca + chunk : c1;
+        const int n = compact2(Z, d, r0, r1, ca, cb, list, wc);
+        if (j < d.Wz) {
+            for (int q = 0; q < n; q++) {
+                const NZ2 e = list[q];
+                const int a = (int)(i - e.i) + (d.h - 1), b = (int)(j - e.j) + (d.w - 1);
+                if (a < 0 || a >= H2 || b < 0 || b >= W2)
+                    continue;
+                const int lag = a * W2 + b;
+#pragma unroll
+                for (int t = 0; t < kPer; t++) {
+                    const int k = grp + 8 * t;
+                    if (k < d.K)
+                        acc[t] += (double)__ldg(Ct + ((((int64_t)e.k * KQ + (k >> 2)) * A + lag) << 2) +
+                                                (k & 3)) *
+                                  (double)e.z;
+                }
+            }
+        }
+        __syncthreads();  // the list is rewritten by the next chunk
+    }
+    float drift = 0.f, all = 0.f, dz32 = 0.f;
+    if (j < d.Wz) {
+#pragma unroll
+        for (int t = 0; t < kPer; t++) {
+            const int k = grp + 8 * t;
+            if (k >= d.K)
+                continue;
+            const int64_t o = ((int64_t)k * d.Hz + i) * d.Wz + j;
+            const float rn = (float)((double)beta0[o] - acc[t]);
+            const float rold = r[o];
+            if (write_r)
+                r[o] = rn;
+            drift = fmaxf(drift, fabsf(rold - rn));
+            const float z = Z[o], nk = norms[k], rnk = __frcp_rn(nk);
+            float gap;
+            if (z == 0.f) {
+                gap = soft_f(rn, lam) * rnk;
+            } else {
+                const float sg = z > 0.f ? 1.f : -1.f;
+                const float b = fmaf(nk, z, rn);
+                gap = b * sg > lam ? (rn - lam * sg) * rnk : soft_f(b, lam) * rnk - z;
+            }
+            all = fmaxf(all, fabsf(gap));
+            float zn, dd;
+            coord_step(rn, z, nk, rnk, lam, &zn, &dd);
+            dz32 = fmaxf(dz32, fabsf(dd));
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        drift = fmaxf(drift, __shfl_xor_sync(0xffffffffu, drift, off));
+        all = fmaxf(all, __shfl_xor_sync(0xffffffffu, all, off));
+        dz32 = fmaxf(dz32, __shfl_xor_sync(0xffffffffu, dz32, off));
+    }
+    if (col == 0) {
+        bred[0][grp] = drift;
+        bred[1][grp] = all;
+        bred[2][grp] = dz32;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        float v[3] = {0.f, 0.f, 0.f};
+        for (int g = 0; g < 8; g++)
+            for (int q = 0; q < 3; q++)
+                v[q] = fmaxf(v[q], bred[q][g]);
+        atomicMax(&red[0], (unsigned long long)__double_as_longlong((double)v[0]));
+        atomicMax(&red[3], (unsigned long long)__double_as_longlong((double)v[1]));
+        atomicMax(&red[4], (unsigned long long)__double_as_longlong((double)v[2]));
+    }
+}
+
+// Residual of one image row and kTile2 columns (all channels) per block, FP64:
+// partial[2b] = sum over its pixels of R^2, partial[2b+1] = sum |Z| over the
+// block's own activation positions (rows < Hz, columns < Wz).
+__global__ void __launch_bounds__(256)
+    objective2d_kernel(const float *__restrict__ D, const float *__restrict__ X,
+                       const float *__restrict__ Z, Dims d, double *__restrict__ partial)
+{
+    __shared__ NZ2 list[kList2];
+    __shared__ int wc[8];
+    __shared__ double bsum[2][8];
+    const int tid = threadIdx.x, col = tid & 31, grp = tid >> 5;
+    const int64_t ntc = (d.W + kTile2 - 1) / kTile2;
+    const int64_t y = blockIdx.x / ntc, x0 = (blockIdx.x % ntc) * kTile2, x = x0 + col;
+    // activations reaching pixel (y, x): rows [y-h+1, y], columns [x-w+1, x]
+    const int64_t r0 = max((int64_t)0, y - (d.h - 1)), r1 = min(d.Hz, y + 1);
+    const int64_t c0 = max((int64_t)0, x0 - (d.w - 1)), c1 = min(d.Wz, x0 + kTile2);
+    double sq = 0.0, l1 = 0.0;
+    constexpr int kPm = 8;  // channels per thread group pass (P up to 64)
+    double acc[kPm];
+#pragma unroll
+    for (int t = 0; t < kPm; t++)
+        acc[t] = 0.0;
+    if (r0 < r1 && c0 < c1) {
+        const int64_t chunk = max((int64_t)1, (int64_t)kList2 / ((int64_t)d.K * (r1 - r0)));
+        for (int64_t ca = c0; ca < c1; ca += chunk) {
+            const int64_t cb = ca + chunk < c1 ? ca + chunk : c1;
+            const int n = compact2(Z, d, r0, r1, ca, cb, list, wc);
+            if (x < d.W)
+                for (int q = 0; q < n; q++) {
+                    const NZ2 e = list[q];
+                    const int64_t u = y - e.i, v = x - e.j;
+                    if (u < 0 || u >= d.h || v < 0 || v >= d.w)
+                        continue;
+#pragma unroll
+                    for (int t = 0; t < kPm; t++) {
+                        const int p = grp + 8 * t;
+                        if (p < d.P)
+                            acc[t] += (double)__ldg(D + (((int64_t)e.k * d.P + p) * d.h + u) * d.w + v) *
+                                      (double)e.z;
+                    }
+                }
+            __syncthreads();
+        }
+    }
+    if (x < d.W)
+#pragma unroll
+        for (int t = 0; t < kPm; t++) {
+            const int p = grp + 8 * t;
+            if (p < d.P) {
+                const double rr = (double)X[((int64_t)p * d.H + y) * d.W + x] - acc[t];
+                sq += rr * rr;
+            }
+        }
+    // |Z| of this block's own positions (row y, columns [x0, x0+32)), once
+    if (grp == 0 && y < d.Hz && x < d.Wz)
+        for (int k = 0; k < d.K; k++)
+            l1 += fabs((double)Z[((int64_t)k * d.Hz + y) * d.Wz + x]);
+    for (int off = 16; off > 0; off >>= 1) {
+        sq += __shfl_xor_sync(0xffffffffu, sq, off);
+        l1 += __shfl_xor_sync(0xffffffffu, l1, off);
+    }
+    if (col == 0) {
+        bsum[0][grp] = sq;
+        bsum[1][grp] = l1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double a = 0.0, b = 0.0;
+        for (int g = 0; g < 8; g++) {
+            a += bsum[0][g];
+            b += bsum[1][g];
+        }
+        partial[2 * blockIdx.x] = a;
+        partial[2 * blockIdx.x + 1] = b;
+    }
+}
+
+__global__ void sum_partials_kernel(const double *__restrict__ partial, int64_t n, double lam,
+                                    double *__restrict__ out)
+{
+    __shared__ double s[2][256];
+    double a = 0.0, b = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        a += partial[2 * i];
+        b += partial[2 * i + 1];
+    }
+    s[0][threadIdx.x] = a;
+    s[1][threadIdx.x] = b;
+    __syncthreads();
+    for (int hh = blockDim.x / 2; hh > 0; hh >>= 1) {
+        if ((int)threadIdx.x < hh) {
+            s[0][threadIdx.x] += s[0][threadIdx.x + hh];
+            s[1][threadIdx.x] += s[1][threadIdx.x + hh];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        out[0] = 0.5 * s[0][0] + lam * s[1][0];
+}
+
+int phases2(int64_t Hz, int M, int h)
+{
+    if (M <= 1)
+        return 1;
+    const int64_t hmin = Hz / M;
+    const int64_t need = 2 * (int64_t)h - 2;
+    const int64_t c = 1 + (need + hmin - 1) / hmin;
+    return (int)(c > M ? M : c);
+}
+
+int auto_bands(int64_t Hz, int h)
+{
+    const int64_t bh = std::max<int64_t>(1, 2 * (int64_t)h - 2);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(Hz / bh, 1 << 20));
+}
+
+struct Dev2 {
+    float *D = nullptr, *X = nullptr, *Ct = nullptr, *norms = nullptr, *beta0 = nullptr,
+          *r = nullptr, *Z = nullptr;
+    int64_t *band_s = nullptr;
+    int *list = nullptr;
+    unsigned char *dirty = nullptr;
+    long long *upd = nullptr;
+    double *dec = nullptr, *x2 = nullptr, *partial = nullptr, *E = nullptr;
+    unsigned *amax = nullptr;
+    unsigned long long *red = nullptr;
+    ~Dev2()
+    {
+        void *p[] = {D, X, Ct, norms, beta0, r, Z, band_s, list, dirty, upd, dec, x2, partial, E,
+                     amax, red};
+        for (void *q : p)
+            cudaFree(q);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+int csc2d_plan(int64_t Hz, int h, int M, int *M_out, int *phases, int64_t *starts)
+{
+    if (Hz < 1 || h < 1 || M < 0)
+        return csc_record_error(CSC_EINVAL, "csc2d_plan: need Hz >= 1, h >= 1, M >= 0");
+    if (M == 0)
+        M = auto_bands(Hz, h);
+    if (M > Hz)
+        return csc_record_error(CSC_EINVAL, "csc2d_plan: M = %d exceeds Hz = %lld", M,
+                                (long long)Hz);
+    if (M_out)
+        *M_out = M;
+    if (phases)
+        *phases = phases2(Hz, M, h);
+    if (starts)
+        for (int m = 0; m <= M; m++)
+            starts[m] = (int64_t)m * Hz / M;
+    return CSC_OK;
+}
+
+int csc2d_solve(const float *D, int K, int P, int h, int w, const float *X, int64_t H, int64_t W,
+                double lambda, double tol, int64_t max_updates, int M, int updates_per_visit,
+                float *Z_out, double *objective, csc2d_stats *stats, void *stream)
+{
+    csc::TraceRange trace_("csc2d_solve");
+    if (!D || !X)
+        return csc_record_error(CSC_EINVAL, "csc2d_solve: null D or X");
+    if (K < 1 || K > kMaxK2 || P < 1 || h < 1 || w < 1 || (2 * h - 1) * (2 * w - 1) > kMaxWin ||
+        H < h || W < w)
+        return csc_record_error(CSC_EINVAL,
+                                "csc2d_solve: need 1 <= K <= %d, P >= 1, 1 <= h <= H, 1 <= w <= W, "
+                                "(2h-1)(2w-1) <= %d",
+                                kMaxK2, kMaxWin);
+    if (!(lambda > 0.0) || !(tol > 0.0) || max_updates < 1 || updates_per_visit < 0)
+        return csc_record_error(CSC_EINVAL, "csc2d_solve: need lambda > 0, tol > 0, "
+                                            "max_updates >= 1, updates_per_visit >= 0");
+    Dims d{K, P, h, w, H, W, H - h + 1, W - w + 1};
+    if (d.K * d.Hz * d.Wz >= ((int64_t)1 << 31) || d.Hz * d.Wz >= ((int64_t)1 << 31) / 64)
+        return csc_record_error(CSC_EINVAL, "csc2d_solve: image too large (flat indices)");
+    int Mb = 0, c = 0;
+    int rc = csc2d_plan(d.Hz, h, M, &Mb, &c, nullptr);
+    if (rc != CSC_OK)
+        return rc;
+    std::vector<int64_t> bs(Mb + 1);
+    for (int m = 0; m <= Mb; m++)
+        bs[m] = (int64_t)m * d.Hz / Mb;
+    int64_t hmax = 0;
+    for (int m = 0; m < Mb; m++)
+        hmax = std::max(hmax, bs[m + 1] - bs[m]);
+    const size_t smem = (size_t)hmax * d.Wz * 20;
+    if (smem > (size_t)kMaxSmem)
+        return csc_record_error(CSC_EINVAL,
+                                "csc2d_solve: a band of %lld x %lld positions needs %zu bytes of "
+                                "shared memory (more bands, or a narrower image)",
+                                (long long)hmax, (long long)d.Wz, smem);
+    // the exact checks gather the nonzeros of (2h-1) rows x K atoms one column
+    // chunk at a time: one column must fit the list; the objective's
+    // channels are spread over 8 thread groups, at most 8 passes each
+    if ((int64_t)K * (2 * h - 1) > kList2 || P > 64)
+        return csc_record_error(CSC_EINVAL, "csc2d_solve: need K (2h-1) <= %d and P <= 64",
+                                kList2);
+    int dev = 0;
+    C2_CUDA(cudaGetDevice(&dev));
+    cudaStream_t s = (cudaStream_t)stream;
+    Dev2 g;
+    const int KQ = (K + 3) / 4;
+    const int64_t nz = (int64_t)K * d.Hz * d.Wz;
+    const int A = (2 * h - 1) * (2 * w - 1);
+    C2_CUDA(cudaMalloc(&g.D, sizeof(float) * K * P * h * w));
+    C2_CUDA(cudaMalloc(&g.X, sizeof(float) * P * H * W));
+    C2_CUDA(cudaMalloc(&g.Ct, sizeof(float) * K * KQ * 4 * A));
+    C2_CUDA(cudaMalloc(&g.norms, sizeof(float) * K));
+    C2_CUDA(cudaMalloc(&g.beta0, sizeof(float) * nz));
+    C2_CUDA(cudaMalloc(&g.r, sizeof(float) * nz));
+    C2_CUDA(cudaMalloc(&g.Z, sizeof(float) * nz));
+    C2_CUDA(cudaMalloc(&g.band_s, sizeof(int64_t) * (Mb + 1)));
+    C2_CUDA(cudaMalloc(&g.list, sizeof(int) * Mb));
+    C2_CUDA(cudaMalloc(&g.dirty, Mb));
+    C2_CUDA(cudaMalloc(&g.upd, sizeof(long long)));
+    C2_CUDA(cudaMalloc(&g.dec, sizeof(double)));
+    C2_CUDA(cudaMalloc(&g.x2, sizeof(double)));
+    C2_CUDA(cudaMalloc(&g.amax, sizeof(unsigned)));
+    C2_CUDA(cudaMalloc(&g.red, sizeof(unsigned long long) * 8));
+    C2_CUDA(cudaMalloc(&g.E, sizeof(double)));
+    const int64_t ntile_o = H * ((W + kTile2 - 1) / kTile2);
+    C2_CUDA(cudaMalloc(&g.partial, sizeof(double) * 2 * ntile_o));
+    int64_t launches = 0;
+    C2_CUDA(copy_in(g.D, D, sizeof(float) * K * P * h * w, s));
+    C2_CUDA(copy_in(g.X, X, sizeof(float) * P * H * W, s));
+    // phase lists: bands m == p (mod c), consecutive in the device list
+    std::vector<int> list;
+    std::vector<int> off(c + 1, 0);
+    for (int p = 0; p < c; p++) {
+        off[p] = (int)list.size();
+        for (int m = p; m < Mb; m += c)
+            list.push_back(m);
+    }
+    off[c] = (int)list.size();
+    C2_CUDA(cudaMemcpyAsync(g.band_s, bs.data(), sizeof(int64_t) * (Mb + 1),
+                            cudaMemcpyHostToDevice, s));
+    C2_CUDA(cudaMemcpyAsync(g.list, list.data(), sizeof(int) * Mb, cudaMemcpyHostToDevice, s));
+    C2_CUDA(cudaMemsetAsync(g.amax, 0, sizeof(unsigned), s));
+    C2_CUDA(cudaMemsetAsync(g.x2, 0, sizeof(double), s));
+    C2_CUDA(cudaMemsetAsync(g.Z, 0, sizeof(float) * nz, s));
+    C2_CUDA(cudaMemsetAsync(g.dirty, 1, Mb, s));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    C2_CUDA(cudaEventCreate(&e0));
+    C2_CUDA(cudaEventCreate(&e1));
+    C2_CUDA(cudaEventRecord(e0, s));
+    {
+        const int64_t n = (int64_t)K * KQ * 4 * A;
+        dtd2d_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(g.D, d, KQ,
+                                                                                       g.Ct, g.norms);
+        C2_CUDA(cudaGetLastError());
+        dtx2d_kernel<<<(unsigned)std::min<int64_t>((nz + 255) / 256, 152 * 16), 256, 0, s>>>(
+            g.D, g.X, d, g.beta0, g.r, g.amax, g.x2);
+        C2_CUDA(cudaGetLastError());
+        launches += 2;
+    }
+    C2_CUDA(cudaFuncSetAttribute(band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    BandParams bp;
+    bp.r = g.r;
+    bp.Z = g.Z;
+    bp.Ct = g.Ct;
+    bp.norms = g.norms;
+    bp.band_s = g.band_s;
+    bp.dirty = g.dirty;
+    bp.upd = g.upd;
+    bp.dec = g.dec;
+    bp.d = d;
+    bp.M = Mb;
+    bp.KQ = KQ;
+    bp.u = updates_per_visit > 0 ? updates_per_visit : kDefaultMaxVisit;
+    bp.lam = (float)lambda;
+    const int max_resyncs = 3;
+    bp.tol = (float)(0.5 * tol);  // CD to tol/2, the exact check accepts at tol
+    int64_t updates = 0, sweeps = 0;
+    int resyncs = 0;
+    bool converged = false;
+    const int64_t ntc = (d.Wz + kTile2 - 1) / kTile2;
+    const unsigned rgrid = (unsigned)(d.Hz * ntc);
+    double dz32 = 0.0, all = 0.0;
+    for (;;) {
+        bool settled = false;
+        for (;;) {
+            C2_CUDA(cudaMemsetAsync(g.upd, 0, sizeof(long long), s));
+            for (int p = 0; p < c; p++) {
+                const int cnt = off[p + 1] - off[p];
+                if (cnt == 0)
+                    continue;
+                bp.list = g.list + off[p];
+                band_kernel<<<cnt, kB2, smem, s>>>(bp);
+                C2_CUDA(cudaGetLastError());
+                launches++;
+            }
+            long long u = 0;
+            C2_CUDA(cudaMemcpyAsync(&u, g.upd, sizeof u, cudaMemcpyDeviceToHost, s));
+            C2_CUDA(cudaStreamSynchronize(s));
+            sweeps++;
+            updates += u;
+            if (u == 0) {
+                settled = true;
+                break;
+            }
+            if (updates >= max_updates || sweeps >= 1000000)
+                break;
+        }
+        // exact refresh of r from Z and the report
+        C2_CUDA(cudaMemsetAsync(g.red, 0, sizeof(unsigned long long) * 8, s));
+        resync2d_kernel<<<rgrid, 256, 0, s>>>(g.beta0, g.r, g.Z, g.Ct, g.norms, d, KQ,
+                                              (float)lambda, 1, g.red);
+        C2_CUDA(cudaGetLastError());
+        launches++;
+        unsigned long long red[8];
+        C2_CUDA(cudaMemcpyAsync(red, g.red, sizeof red, cudaMemcpyDeviceToHost, s));
+        C2_CUDA(cudaStreamSynchronize(s));
+        std::memcpy(&dz32, &red[4], sizeof dz32);
+        std::memcpy(&all, &red[3], sizeof all);
+        if (!settled)
+            break;  // max_updates or the sweep limit
+        resyncs++;
+        if (dz32 < tol) {
+            converged = true;
+            break;
+        }
+        if (resyncs > max_resyncs)
+            break;
+        C2_CUDA(cudaMemsetAsync(g.dirty, 1, Mb, s));
+    }
+    C2_CUDA(cudaEventRecord(e1, s));
+    const unsigned ogrid = (unsigned)ntile_o;
+    objective2d_kernel<<<ogrid, 256, 0, s>>>(g.D, g.X, g.Z, d, g.partial);
+    C2_CUDA(cudaGetLastError());
+    sum_partials_kernel<<<1, 256, 0, s>>>(g.partial, ntile_o, lambda, g.E);
+    C2_CUDA(cudaGetLastError());
+    launches += 2;
+    double E = 0.0;
+    C2_CUDA(cudaMemcpyAsync(&E, g.E, sizeof E, cudaMemcpyDeviceToHost, s));
+    if (Z_out)
+        C2_CUDA(copy_out(Z_out, g.Z, sizeof(float) * nz, s));
+    C2_CUDA(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    C2_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (objective)
+        *objective = E;
+    if (stats) {
+        stats->updates = updates;
+        stats->sweeps = sweeps;
+        stats->bands = Mb;
+        stats->phases = c;
+        stats->resyncs = resyncs;
+        stats->converged = converged ? 1 : 0;
+        stats->objective = E;
+        stats->max_delta_z = all;
+        stats->solve_ms = ms;
+        stats->kernel_launches = launches;
+    }
+    (void)dev;
+    return converged ? CSC_OK : CSC_NOT_CONVERGED;
+}
+
+}  // extern "C"

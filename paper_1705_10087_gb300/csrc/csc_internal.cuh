@@ -129,7 +129,8 @@ struct PhaseParams {
     const SigDesc *sig;        // problems of the batch
     const int *seg_sig;        // [M] problem of each segment
     const float *C;            // DtD [K][K][W2]
-    const float *Ct;           // DtD by lag: Ct[(k0 * W2 + s) * Kp + k] = DtD[k0][k][s], 0 for k >= K
+    const float *Ct;           // DtD by lag, float4 groups of atoms:
+                               // Ct[((k0 * Kp/4 + k/4) * W2 + s) * 4 + k%4] = DtD[k0][k][s], 0 for k >= K
     const float *norms;        // [K]
     unsigned char *dirty;      // [M] segment needs a visit
     unsigned char *touched;    // [M] r changed in the segment since the last resync
@@ -182,22 +183,28 @@ cudaError_t launch_phase_drain(const PhaseParams &pp, const PhaseConfig &cfg, in
 
 cudaError_t launch_dtd(const float *D, int K, int P, int L, float *C, float *norms,
                        cudaStream_t s);
-// Ct[(k0 * W2 + s) * Kp + k] = C[(k0 * K + k) * W2 + s] (zero for k >= K): the K
-// coefficients an update of atom k0 applies at one lag are contiguous.
+// Ct[((k0 * Kp/4 + q) * W2 + s) * 4 + e] = C[(k0 * K + 4 q + e) * W2 + s] (zero for
+// 4 q + e >= K): the K coefficients an update of atom k0 applies at lag s are
+// Kp/4 float4 words, one per group q, and consecutive lags' words are adjacent.
 __host__ __device__ __forceinline__ int coef_pad(int K) { return (K + 3) & ~3; }
 cudaError_t launch_coef_by_lag(const float *C, int K, int L, float *Ct, cudaStream_t s);
 
 // beta0 = D~ * X, max |beta0| into *absmax_bits, and sum X^2 added to *x2sum
-// (so E(0) = x2sum / 2).
+// (so E(0) = x2sum / 2).  r_out != NULL receives a second copy of beta0 (the
+// state r of a cold start, Z = 0).
 cudaError_t launch_dtx(const float *D, const float *X, int K, int P, int L, int64_t T,
-                       float *beta0, unsigned int *absmax_bits, double *x2sum, cudaStream_t s);
+                       float *beta0, float *r_out, unsigned int *absmax_bits, double *x2sum,
+                       cudaStream_t s);
 
 // Reduction / output tiles of a batch: tile b covers columns (or samples)
-// [start[b], start[b] + width) of problem sig[b], clipped to the problem.
+// [start[b], start[b] + width) of problem sig[b], clipped to the problem and,
+// when end != NULL, to end[b] (a shard computes only the columns it owns; the
+// columns beyond end[b] are still read as neighbours).
 struct Tiles {
     const int *sig;
     const int64_t *start;
     int64_t n;
+    const int64_t *end = nullptr;
 };
 constexpr int kResyncCols = 32;  // columns per resync tile
 constexpr int kTile = 256;       // samples per objective tile, columns per absmax tile
@@ -207,23 +214,33 @@ constexpr int kTile = 256;       // samples per objective tile, columns per absm
 // mode 2 = one BF16 product.  Needs K <= 64 and dtx_tc_smem(K,P,L) <= kMaxSmem
 // (cudaErrorNotSupported otherwise).  *err is set when a bounded wait gave up.
 size_t dtx_tc_smem(int K, int P, int L);
-// The beta0 kernel used by default: the tensor cores (mode 1) where at least
-// two CTAs fit on an SM (measured faster: P = 1, L = 200, T = 5e6 in 1.11 ms
-// against 2.06 ms for the FP32 kernel), else the FP32 kernel.
+// The beta0 kernel used by default: the tensor cores (mode 1) wherever one
+// CTA fits on an SM, else the FP32 kernel.
 inline bool dtx_tc_preferred(int K, int P, int L)
 {
-    return K <= 64 && dtx_tc_smem(K, P, L) <= (size_t)kMaxSmem / 2;
+    return K <= 64 && dtx_tc_smem(K, P, L) <= (size_t)kMaxSmem;
 }
 // beta0 with init_mode 0 (automatic), 1 or 2 (tensor cores), 3 (FP32 kernel).
 cudaError_t launch_dtx_any(const float *D, const float *X, int K, int P, int L, int64_t T,
-                           int init_mode, float *beta0, unsigned int *absmax_bits, double *x2sum,
-                           int *err, cudaStream_t s);
+                           int init_mode, float *beta0, float *r_out, unsigned int *absmax_bits,
+                           double *x2sum, int *err, cudaStream_t s);
 // One warp waits, bounded by `limit` polls, on an mbarrier nothing arrives
 // at, and sets *gave_up when the wait gives up.
 cudaError_t launch_wait_selftest(unsigned limit, int *gave_up, cudaStream_t s);
 cudaError_t launch_dtx_tc(const float *D, const float *X, int K, int P, int L, int64_t T,
-                          int mode, float *beta0, unsigned int *absmax_bits, double *x2sum,
-                          int *err, cudaStream_t s);
+                          int mode, float *beta0, float *r_out, unsigned int *absmax_bits,
+                          double *x2sum, int *err, cudaStream_t s);
+
+// Nonzeros of Z per resync tile ("bucket": the tile's kResyncCols columns),
+// rebuilt at each resync where Z may have changed.  Bucket b holds
+// min(count[b], kNzCap) entries ent[b * kNzCap + i] = (k * kResyncCols + j,
+// bits of Z_k[start + j]) in (k, j) order; count[b] > kNzCap means the bucket
+// overflowed and a tile that needs it scans Z itself.
+constexpr int kNzCap = 64;
+struct NzLists {
+    int *count;  // [tiles]
+    uint2 *ent;  // [tiles * kNzCap]
+};
 
 // Re-synchronisation of r with its definition, r = D~*X - sum_{l,t'} S Z
 // (beta0 = D~*X), accumulated in double-float and rounded once to float, and
@@ -240,10 +257,15 @@ cudaError_t launch_dtx_tc(const float *D, const float *X, int K, int P, int L, i
 // a tile whose columns meet no touched segment is not recomputed: its r is
 // already exact, and its report values are the ones stored in rep[5 b..5 b+4]
 // when it was last computed (every computed tile stores them when rep != NULL).
+// With lists.count != NULL the nonzeros of Z are first listed per tile (a
+// tile's bucket is rebuilt unless touched says its Z did not change since the
+// previous resync over the same tiles) and each tile reads the lists of the
+// tiles within L-1 columns instead of scanning Z; the tiles of a problem must
+// be consecutive in the table and in column order (both tables are).
 cudaError_t launch_resync(const SigDesc *sig, Tiles tiles, const float *C, const float *norms,
                           int K, int L, int write_r, unsigned long long *red, int red_stride,
                           unsigned char *dirty, float tol_mark, const unsigned char *touched,
-                          float *rep, cudaStream_t s);
+                          float *rep, NzLists lists, cudaStream_t s);
 
 // out = r + n Z (beta of Sec. 2.1) in float, over one [K][ld] array.
 cudaError_t launch_beta_from_r(const float *r, const float *Z, const float *norms, int K,

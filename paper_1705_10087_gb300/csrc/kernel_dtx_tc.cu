@@ -158,20 +158,20 @@ __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b)
 
 struct TcLayout {
     int L16, NQ, nsteps, xw;
-    size_t a_off, b_off, x_off, bar_off, total;
+    size_t a_off, b_off, pl_off, bar_off, total;
     __host__ __device__ TcLayout(int P, int L, int N)
     {
         L16 = (L + 15) & ~15;
         NQ = kTcM / 8 + L16 / 8;
         nsteps = P * L16 / 16;
-        xw = kTcM + L16 + 8;  // staged samples per channel
+        xw = kTcM + L16 + 8;  // staged samples per channel: 8 (NQ + 1)
         size_t o = 0;
         a_off = o;
         o += 2 * (size_t)kSplits * P * NQ * 128;  // two operand buffers
         b_off = o;
         o += (size_t)kSplits * nsteps * (N / 8) * 256;
-        x_off = o;
-        o += (size_t)P * xw * 4;
+        pl_off = o;  // the three BF16 terms of the staged samples, [split][p][xw]
+        o += (size_t)kSplits * P * xw * 2;
         o = (o + 15) & ~(size_t)15;
         bar_off = o;
         o += 16;  // two mbarriers
@@ -182,7 +182,7 @@ struct TcLayout {
 template <int N>
 __global__ void __launch_bounds__(kTcThreads, 1)
     dtx_tc_kernel(const float *__restrict__ D, const float *__restrict__ X, int K, int P, int L,
-                  long long T, int mode, float *__restrict__ beta0,
+                  long long T, int mode, float *__restrict__ beta0, float *__restrict__ r_out,
                   unsigned int *__restrict__ absmax_bits, double *__restrict__ x2sum,
                   int *__restrict__ err)
 {
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const TcLayout lay(P, L, N);
     unsigned char *As = sm + lay.a_off;
     unsigned char *Bs = sm + lay.b_off;
-    float *xs = reinterpret_cast<float *>(sm + lay.x_off);
+    uint32_t *pl = reinterpret_cast<uint32_t *>(sm + lay.pl_off);  // BF16 pairs
     const uint32_t bar = smem_u32(sm + lay.bar_off);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long Tz = T - L + 1;
@@ -250,40 +250,81 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     double x2 = 0.0;
     uint32_t phase0 = 0u, phase1 = 0u;  // expected parity of each barrier
 
-    // stage X of a tile, sum X^2 over its own samples, build its operand run in buffer buf
+    // Stage X of a tile (sum X^2 over its own samples), split every sample
+    // once into its three BF16 terms (planes [split][p][xw], pairs of samples
+    // per 32-bit word), then build the tile's operand runs in buffer buf.
+    const int half = lay.xw / 2;  // words per plane row
+    // The samples of a tile are loaded into registers one iteration ahead
+    // (prefetch), so that their latency overlaps the previous tile's
+    // epilogue: a thread holds pairs i = tid + q * kTcThreads, q < kPairs.
+    constexpr int kPairs = 8;
+    const bool prefetched = P * half <= kPairs * kTcThreads;
+    float2 xr[kPairs];
+    auto load_x = [&](long long tile) {
+        const long long t0 = tile * kTcM;
+#pragma unroll
+        for (int q = 0; q < kPairs; q++) {
+            const int i = tid + q * kTcThreads;
+            float2 v = make_float2(0.f, 0.f);
+            if (i < P * half) {
+                const int p = i / half, j2 = i % half;
+                const long long t = t0 + 2 * j2;
+                const float *xp = X + (long long)p * T + t;
+                v.x = t < T ? xp[0] : 0.f;
+                v.y = t + 1 < T ? xp[1] : 0.f;
+            }
+            xr[q] = v;
+        }
+    };
+    auto put_pair = [&](int i, float v0, float v1, bool own) {
+        const int p = i / half, j2 = i % half;
+        if (own || 2 * j2 < kTcM)
+            x2 += (double)v0 * (double)v0 + (double)v1 * (double)v1;
+        __nv_bfloat16 h0, m0, l0, h1, m1, l1;
+        split3(v0, h0, m0, l0);
+        split3(v1, h1, m1, l1);
+        pl[(0 * P + p) * half + j2] = pack2(h0, h1);
+        pl[(1 * P + p) * half + j2] = pack2(m0, m1);
+        pl[(2 * P + p) * half + j2] = pack2(l0, l1);
+    };
     auto build = [&](long long tile, int buf) {
         const long long t0 = tile * kTcM;
         const bool last = tile == ntiles - 1;
-        for (int i = tid; i < P * lay.xw; i += kTcThreads) {
-            const int p = i / lay.xw, jx = i % lay.xw;
-            const long long t = t0 + jx;
-            const float v = t < T ? X[(long long)p * T + t] : 0.f;
-            xs[i] = v;
-            if (t < T && (jx < kTcM || last))
-                x2 += (double)v * (double)v;
+        if (prefetched) {
+#pragma unroll
+            for (int q = 0; q < kPairs; q++) {
+                const int i = tid + q * kTcThreads;
+                if (i < P * half)
+                    put_pair(i, xr[q].x, xr[q].y, last);
+            }
+        } else {
+            for (int i = tid; i < P * half; i += kTcThreads) {
+                const int p = i / half, j2 = i % half;
+                const long long t = t0 + 2 * j2;
+                const float *xp = X + (long long)p * T + t;
+                put_pair(i, t < T ? xp[0] : 0.f, t + 1 < T ? xp[1] : 0.f, last);
+            }
         }
         __syncthreads();
-        // row (sigma, p, q, r) = split sigma of X[p][t0 + 8 q + r + 0..7]
+        // row (sigma, p, q, r) = split sigma of X[p][t0 + 8 q + r + 0..7]: the
+        // BF16 words 4 q + r/2 .. 4 q + r/2 + 4 of the plane, shifted by 16 bits
+        // when r is odd.  r = tid & 7 is the same for all of a thread's rows, and
+        // the 8 lanes of one q write 128 contiguous bytes (no bank conflict).
         unsigned char *Ab = As + (size_t)buf * a_bytes;
         const int rows_a = P * lay.NQ * 8;
+        const int r = tid & 7, wa = r >> 1;
+        const unsigned sh = (unsigned)(r & 1) * 16u;
         for (int i = tid; i < rows_a; i += kTcThreads) {
-            const int r = i & 7, q = (i >> 3) % lay.NQ, p = (i >> 3) / lay.NQ;
-            const float *src = xs + (size_t)p * lay.xw + 8 * q + r;
-            uint32_t w[kSplits][4];
-#pragma unroll
-            for (int e2 = 0; e2 < 4; e2++) {
-                __nv_bfloat16 h[2], m[2], l[2];
-                split3(src[2 * e2], h[0], m[0], l[0]);
-                split3(src[2 * e2 + 1], h[1], m[1], l[1]);
-                w[0][e2] = pack2(h[0], h[1]);
-                w[1][e2] = pack2(m[0], m[1]);
-                w[2][e2] = pack2(l[0], l[1]);
-            }
+            const int q = (i >> 3) % lay.NQ, p = (i >> 3) / lay.NQ;
             const size_t off = ((size_t)p * lay.NQ + q) * 128 + (size_t)r * 16;
 #pragma unroll
-            for (int sg = 0; sg < kSplits; sg++)
+            for (int sg = 0; sg < kSplits; sg++) {
+                const uint32_t *w = pl + (size_t)(sg * P + p) * half + 4 * q + wa;
+                const uint32_t w0 = w[0], w1 = w[1], w2 = w[2], w3 = w[3], w4 = w[4];
                 *reinterpret_cast<uint4 *>(Ab + (size_t)sg * P * lay.NQ * 128 + off) =
-                    make_uint4(w[sg][0], w[sg][1], w[sg][2], w[sg][3]);
+                    make_uint4(__funnelshift_r(w0, w1, sh), __funnelshift_r(w1, w2, sh),
+                               __funnelshift_r(w2, w3, sh), __funnelshift_r(w3, w4, sh));
+            }
         }
         // make the generic-proxy stores visible to the tensor cores
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -333,6 +374,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     const int k = c + i;
                     if (k < K) {
                         beta0[(long long)k * Tz + t] = v[i];
+                        if (r_out)
+                            r_out[(long long)k * Tz + t] = v[i];
                         amax = fmaxf(amax, fabsf(v[i]));
                     }
                 }
@@ -344,9 +387,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // built, and the accumulator of tile i-1 read out, while the products of
     // the neighbouring tile run on the tensor cores.
     const long long cnt = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    if (prefetched && cnt > 0)
+        load_x(blockIdx.x);
     for (long long i = 0; i <= cnt && cnt > 0; i++) {
         if (i < cnt)
             build(blockIdx.x + i * gridDim.x, (int)(i & 1));
+        // the next tile's samples are in flight while this iteration's
+        // products run and the previous tile's accumulator is read out
+        if (prefetched && i + 1 < cnt)
+            load_x(blockIdx.x + (i + 1) * gridDim.x);
         // operands of tile i visible; every thread has read accumulator (i & 1)
         // (tile i-2) before it is overwritten
         fence_before_sync();
@@ -424,8 +473,8 @@ size_t dtx_tc_smem(int K, int P, int L)
 }
 
 cudaError_t launch_dtx_tc(const float *D, const float *X, int K, int P, int L, int64_t T,
-                          int mode, float *beta0, unsigned int *absmax_bits, double *x2sum,
-                          int *err, cudaStream_t s)
+                          int mode, float *beta0, float *r_out, unsigned int *absmax_bits,
+                          double *x2sum, int *err, cudaStream_t s)
 {
     if (K > 64)
         return cudaErrorNotSupported;
@@ -444,34 +493,38 @@ cudaError_t launch_dtx_tc(const float *D, const float *X, int K, int P, int L, i
             e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess)
             return e;
-        // four CTAs per SM where they fit (their latencies overlap; more wait
-        // for a slot): at N <= 64 tensor-memory columns each, the CTAs resident
-        // on an SM never ask for more than its 512 columns unless eight or more
-        // of them fit, and then N = 32 (K <= 32) keeps them at 512
-        const int64_t cap = (int64_t)nsm * 4;
+        // one wave of persistent CTAs: as many per SM as are resident at once
+        // (up to four; at N <= 64 tensor-memory columns each they never ask an
+        // SM for more than its 512 columns), each looping over its tiles
+        int per_sm = 1;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTcThreads, smem);
+        if (e != cudaSuccess)
+            return e;
+        per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
+        const int64_t cap = (int64_t)nsm * per_sm;
         const unsigned grid = (unsigned)(ntiles < cap ? ntiles : cap);
-        kern<<<grid, kTcThreads, smem, s>>>(D, X, K, P, L, (long long)T, mode, beta0, absmax_bits,
-                                           x2sum, err);
+        kern<<<grid, kTcThreads, smem, s>>>(D, X, K, P, L, (long long)T, mode, beta0, r_out,
+                                           absmax_bits, x2sum, err);
         return cudaGetLastError();
     };
     return K <= 32 ? go(dtx_tc_kernel<32>) : go(dtx_tc_kernel<64>);
 }
 
 cudaError_t launch_dtx_any(const float *D, const float *X, int K, int P, int L, int64_t T,
-                           int init_mode, float *beta0, unsigned int *absmax_bits, double *x2sum,
-                           int *err, cudaStream_t s)
+                           int init_mode, float *beta0, float *r_out, unsigned int *absmax_bits,
+                           double *x2sum, int *err, cudaStream_t s)
 {
     int mode = init_mode;
     if (mode == 0)
         mode = dtx_tc_preferred(K, P, L) ? 1 : 3;
     if (mode == 1 || mode == 2) {
         const cudaError_t e =
-            launch_dtx_tc(D, X, K, P, L, T, mode, beta0, absmax_bits, x2sum, err, s);
+            launch_dtx_tc(D, X, K, P, L, T, mode, beta0, r_out, absmax_bits, x2sum, err, s);
         if (e != cudaErrorNotSupported)
             return e;
         cudaGetLastError();
     }
-    return launch_dtx(D, X, K, P, L, T, beta0, absmax_bits, x2sum, s);
+    return launch_dtx(D, X, K, P, L, T, beta0, r_out, absmax_bits, x2sum, s);
 }
 
 }  // namespace csc

@@ -55,11 +55,25 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
     return ((unsigned long long)hmax << 32) | lmax;
 }
 
+// Column stride of the staged tiles for the compile-time-K kernels: a
+// multiple of 4 floats (16-byte aligned columns, 128-bit accesses) whose
+// quarter is odd, so that the 8 lanes of a 128-bit shared-memory phase, on
+// consecutive columns, cover all 32 banks.
+__host__ __device__ constexpr int vec_stride(int K)
+{
+    return (((K + 3) / 4) | 1) * 4;
+}
+// Whether phase_config picks a compile-time-K kernel (vector tile layout).
+__host__ __device__ inline bool vec_layout(int K, int block)
+{
+    return (K == 25 || K == 64) && block <= 512;
+}
+
 // Shared-memory layout of a block, in bytes from the start (16-byte aligned
 // pieces).  w = widest segment; with smem the segment's r and Z are staged.
 struct Layout {
     size_t key, slot_key, cz, cd, ck, zm, slot_z, slot_d, slot_k, slot_j, nrm, rnrm, r, z, total;
-    __host__ __device__ Layout(int K, int w, bool smem)
+    __host__ __device__ Layout(int K, int w, bool smem, bool vec)
     {
         size_t o = 0;
         key = o;
@@ -86,9 +100,10 @@ struct Layout {
         o = up(o + 4 * (size_t)K);
         rnrm = o;
         o = up(o + 4 * (size_t)K);
-        // staged tiles are column-major [jj][k] with an odd row length K|1, so that
-        // lanes on consecutive columns hit distinct banks
-        const size_t ks = (size_t)(K | 1);
+        // staged tiles are column-major [jj][k]: with an odd row length K|1 lanes on
+        // consecutive columns hit distinct banks (scalar accesses); the
+        // compile-time-K kernels use vec_stride(K) for 128-bit accesses
+        const size_t ks = vec ? (size_t)vec_stride(K) : (size_t)(K | 1);
         r = o;
         if (smem)
             o = up(o + 4 * ks * w);
@@ -157,7 +172,9 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float lam = sdp->lam, tol = sdp->tol;
 
-    const Layout lay(K, pp.w_max, SMEM);
+    constexpr int CST = vec_stride(KT);  // column stride of the vector layout (KFIX)
+    constexpr int KQ = (KT + 3) / 4;      // float4 groups holding the KT atoms
+    const Layout lay(K, pp.w_max, SMEM, KFIX);
     unsigned long long *ckey = reinterpret_cast<unsigned long long *>(smem_raw + lay.key);
     unsigned long long *slot_key = reinterpret_cast<unsigned long long *>(smem_raw + lay.slot_key);
     float *cz = reinterpret_cast<float *>(smem_raw + lay.cz);
@@ -183,16 +200,19 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
     if (SMEM) {
         rs = reinterpret_cast<float *>(smem_raw + lay.r);
         zs = reinterpret_cast<float *>(smem_raw + lay.z);
-        cst = (Idx)(K | 1);
+        cst = (Idx)(KFIX ? CST : (K | 1));
         kst = 1;
-        for (int k = 0; k < K; k++) {
-            const float *rsrc = gr + (int64_t)k * ld + s;
-            const float *zsrc = gz + (int64_t)k * ld + s;
-            for (int jj = tid; jj < w; jj += B) {
-                rs[jj * cst + k] = rsrc[jj];
-                zs[jj * cst + k] = zsrc[jj];
+        if constexpr (!KFIX) {
+            for (int k = 0; k < K; k++) {
+                const float *rsrc = gr + (int64_t)k * ld + s;
+                const float *zsrc = gz + (int64_t)k * ld + s;
+                for (int jj = tid; jj < w; jj += B) {
+                    rs[jj * cst + k] = rsrc[jj];
+                    zs[jj * cst + k] = zsrc[jj];
+                }
             }
         }
+        // (compile-time K: each thread stages its own columns below)
     } else {
         rs = gr + s;
         zs = gz + s;
@@ -280,8 +300,39 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
         cd[jj] = bdz;
         ck[jj] = bk;
     };
-    for (int jj = tid; jj < w; jj += B)
-        col_eval(jj);
+    if constexpr (SMEM && KFIX) {
+        // a column's KT values of r and of Z in one round trip of independent
+        // loads (coalesced across the threads, one atom row at a time), stored
+        // with 128-bit writes, screened from the registers
+        for (int jj = tid; jj < w; jj += B) {
+            Mask need = 0, zb = 0;
+            // r, then Z (one array's column in registers at a time)
+#pragma unroll
+            for (int a = 0; a < 2; a++) {
+                const float *src = (a == 0 ? gr : gz) + s + jj;
+                float v[4 * KQ];
+#pragma unroll
+                for (int k = 0; k < 4 * KQ; k++)
+                    v[k] = k < KT ? src[(int64_t)k * ld] : 0.f;
+                float4 *dst = reinterpret_cast<float4 *>((a == 0 ? rs : zs) + jj * CST);
+#pragma unroll
+                for (int q = 0; q < KQ; q++)
+                    dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+#pragma unroll
+                for (int k = 0; k < KT; k++) {
+                    if (a == 0)
+                        need |= (Mask)(fabsf(v[k]) > lam ? 1 : 0) << k;
+                    else
+                        zb |= (Mask)(v[k] != 0.f ? 1 : 0) << k;
+                }
+            }
+            zmask[jj] = zb;
+            col_finish(jj, need | zb);
+        }
+    } else {
+        for (int jj = tid; jj < w; jj += B)
+            col_eval(jj);
+    }
     // (no barrier needed: each thread reads back only its own columns)
 
     int buf = 0, nupd = 0;
@@ -346,10 +397,12 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
                 const float r0 = rs[jj * cst + k0 * kst];
                 decrease += d * (r0 - 0.5f * n * d) + lam * (fabsf(z) - fabsf(u));
             }
-            // the K coefficients S_{k,k0}[t-t0] of this lag are contiguous in Ct:
-            // fetch them first (independent vector loads, one L2 round trip per
-            // batch), then apply
-            const float *Ck = pp.Ct + ((int64_t)k0 * W2 + off) * Kp;
+            // the K coefficients S_{k,k0}[t-t0] of this lag: float4 group q of
+            // (k0, lag) at Ct4[(k0 * Kp/4 + q) * W2 + lag], so that the threads of a
+            // warp (consecutive lags) read consecutive 16-byte words; fetch them
+            // first (independent vector loads, one L2 round trip), then apply
+            const float4 *Ct4 = reinterpret_cast<const float4 *>(pp.Ct);
+            const int64_t cbase = (int64_t)k0 * (Kp / 4) * W2 + off;
             float *rcol = rs + jj * cst;
             float *rg = gr + t;  // an idle neighbour's column (no other block touches it)
             auto apply = [&](int k, float cv) {
@@ -363,7 +416,7 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
                 float cv[KPC];
 #pragma unroll
                 for (int q = 0; q < KPC / 4; q++) {
-                    const float4 v = __ldg(reinterpret_cast<const float4 *>(Ck) + q);
+                    const float4 v = __ldg(Ct4 + cbase + (int64_t)q * W2);
                     cv[4 * q] = v.x;
                     cv[4 * q + 1] = v.y;
                     cv[4 * q + 2] = v.z;
@@ -377,11 +430,31 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
                         zmask[jj] = znew != 0.f ? (zmask[jj] | bit) : (zmask[jj] & ~bit);
                     }
                     Mask need = 0;
+                    if constexpr (SMEM) {
+                        // 128-bit read-modify-write of the column (padded atoms stay 0:
+                        // their coefficients are 0)
+                        float4 *rc4 = reinterpret_cast<float4 *>(rcol);
 #pragma unroll
-                    for (int k = 0; k < KT; k++) {
-                        const float r = fmaf(-cv[k], delta, rcol[k * kst]);
-                        rcol[k * kst] = r;
-                        need |= (Mask)(fabsf(r) > lam ? 1 : 0) << k;
+                        for (int q = 0; q < KQ; q++) {
+                            float4 v = rc4[q];
+                            v.x = fmaf(-cv[4 * q], delta, v.x);
+                            v.y = fmaf(-cv[4 * q + 1], delta, v.y);
+                            v.z = fmaf(-cv[4 * q + 2], delta, v.z);
+                            v.w = fmaf(-cv[4 * q + 3], delta, v.w);
+                            rc4[q] = v;
+                            const float rr[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                            for (int e = 0; e < 4; e++)
+                                if (4 * q + e < KT)
+                                    need |= (Mask)(fabsf(rr[e]) > lam ? 1 : 0) << (4 * q + e);
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < KT; k++) {
+                            const float r = fmaf(-cv[k], delta, rcol[k * kst]);
+                            rcol[k * kst] = r;
+                            need |= (Mask)(fabsf(r) > lam ? 1 : 0) << k;
+                        }
                     }
                     col_finish(jj, need | zmask[jj]);
                 } else {
@@ -390,11 +463,15 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
                         atomicAdd(rg + (int64_t)k * ld, -cv[k] * delta);
                 }
             } else {
+                const float *Ct1 = pp.Ct;
                 for (int kb = 0; kb < K; kb += kCoefBatch) {
                     float cv[kCoefBatch];
 #pragma unroll
-                    for (int i = 0; i < kCoefBatch; i++)
-                        cv[i] = kb + i < K ? __ldg(Ck + kb + i) : 0.f;
+                    for (int i = 0; i < kCoefBatch; i++) {
+                        const int k = kb + i;
+                        cv[i] = k < K ? __ldg(Ct1 + ((cbase + (int64_t)(k >> 2) * W2) << 2) + (k & 3))
+                                      : 0.f;
+                    }
 #pragma unroll
                     for (int i = 0; i < kCoefBatch; i++)
                         if (kb + i < K)
@@ -415,12 +492,32 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
 
     // ---- write back, spill bookkeeping, trace ---------------------------
     if (SMEM && nupd > 0) {
-        for (int k = 0; k < K; k++) {
-            float *rdst = gr + (int64_t)k * ld + s;
-            float *zdst = gz + (int64_t)k * ld + s;
+        if constexpr (KFIX) {
+            // each thread writes back its own columns (128-bit shared reads;
+            // the global stores of one atom row are coalesced across threads)
             for (int jj = tid; jj < w; jj += B) {
-                rdst[jj] = rs[jj * cst + k];
-                zdst[jj] = zs[jj * cst + k];
+                const float4 *rc4 = reinterpret_cast<const float4 *>(rs + jj * CST);
+                const float4 *zc4 = reinterpret_cast<const float4 *>(zs + jj * CST);
+#pragma unroll
+                for (int q = 0; q < KQ; q++) {
+                    const float4 a = rc4[q], b = zc4[q];
+                    const float ra[4] = {a.x, a.y, a.z, a.w}, za[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+                    for (int e = 0; e < 4; e++)
+                        if (4 * q + e < KT) {
+                            gr[(int64_t)(4 * q + e) * ld + s + jj] = ra[e];
+                            gz[(int64_t)(4 * q + e) * ld + s + jj] = za[e];
+                        }
+                }
+            }
+        } else {
+            for (int k = 0; k < K; k++) {
+                float *rdst = gr + (int64_t)k * ld + s;
+                float *zdst = gz + (int64_t)k * ld + s;
+                for (int jj = tid; jj < w; jj += B) {
+                    rdst[jj] = rs[jj * cst + k];
+                    zdst[jj] = zs[jj * cst + k];
+                }
             }
         }
     }
@@ -566,13 +663,14 @@ cudaError_t launch_add_int(int *p, int v, cudaStream_t s)
 PhaseConfig phase_config(int K, int L, int wmax)
 {
     PhaseConfig cfg;
-    cfg.tile_in_smem = Layout(K, (int)wmax, true).total <= (size_t)kMaxSmem;
-    cfg.smem = Layout(K, (int)wmax, cfg.tile_in_smem).total;
     // An update touches the 2L-1 window columns: with at least that many threads
     // each of them goes to its own thread, however wide the segment; more threads
     // would idle in the update and only cost registers and occupancy.  The block
     // is a power of two (128, 512 or 1024) so that ownership is a mask.
     cfg.block = 2 * L - 1 <= 128 ? 128 : (2 * L - 1 <= 512 ? 512 : 1024);
+    const bool vec = vec_layout(K, cfg.block);
+    cfg.tile_in_smem = Layout(K, (int)wmax, true, vec).total <= (size_t)kMaxSmem;
+    cfg.smem = Layout(K, (int)wmax, cfg.tile_in_smem, vec).total;
     return cfg;
 }
 

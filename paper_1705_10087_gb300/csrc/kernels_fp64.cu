@@ -91,6 +91,58 @@ __device__ __forceinline__ void df_add_prod(float &hi, float &lo, float a, float
 
 constexpr int kResyncThreads = 256;
 constexpr int kResyncGroups = kResyncThreads / kResyncCols;  // atom groups
+constexpr int kListMax = 32 * kChunk;  // nonzeros a tile gathers from the lists at once
+
+// Whether r may have changed on the columns [c0, c0 + kResyncCols) of a
+// problem since the last resync: every update window marks the segments it
+// covers as touched, and every update marks its own segment.
+__device__ __forceinline__ bool tile_touched(const SigDesc &sd, int64_t c0,
+                                             const unsigned char *__restrict__ touched)
+{
+    if (!touched || sd.nseg <= 0)
+        return true;
+    // the problem's segments are the equal cut of seg_start
+    const int64_t ce = c0 + kResyncCols < sd.Tz ? c0 + kResyncCols : sd.Tz;
+    const int j1 = segment_of(sd.Tz, sd.nseg, ce - 1);
+    for (int j = segment_of(sd.Tz, sd.nseg, c0); j <= j1; j++)
+        if (touched[sd.seg0 + j])
+            return true;
+    return false;
+}
+
+// One warp per tile: the tile's nonzeros in (k, column) order (ballot
+// compaction over 32 columns, one coalesced row of Z per atom).
+__global__ void __launch_bounds__(256)
+    nz_bucket_kernel(const SigDesc *__restrict__ sigs, Tiles tiles, int K,
+                     const unsigned char *__restrict__ touched, NzLists lists)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (b >= tiles.n)
+        return;
+    const SigDesc sd = sigs[tiles.sig[b]];
+    const int64_t c0 = tiles.start[b];
+    // Z changed only in touched segments: the bucket of an untouched tile is
+    // the one built at the previous resync over the same Z
+    if (!tile_touched(sd, c0, touched))
+        return;
+    const int64_t t = c0 + lane;
+    const bool in = t < sd.Tz;
+    uint2 *__restrict__ out = lists.ent + b * kNzCap;
+    int base = 0;
+    for (int k = 0; k < K; k++) {
+        const float z = in ? sd.Z[(int64_t)k * sd.ld + t] : 0.f;
+        const unsigned m = __ballot_sync(0xffffffffu, z != 0.f);
+        if (z != 0.f) {
+            const int pos = base + __popc(m & ((1u << lane) - 1u));
+            if (pos < kNzCap)
+                out[pos] = make_uint2((unsigned)(k * kResyncCols + lane), __float_as_uint(z));
+        }
+        base += __popc(m);
+    }
+    if (lane == 0)
+        lists.count[b] = base;
+}
 
 template <int KPT>
 __global__ void __launch_bounds__(kResyncThreads)
@@ -98,11 +150,14 @@ __global__ void __launch_bounds__(kResyncThreads)
                   const float *__restrict__ norms, int K, int L, int write_r,
                   unsigned long long *__restrict__ red, int red_stride,
                   unsigned char *__restrict__ dirty, float tol_mark,
-                  const unsigned char *__restrict__ touched, float *__restrict__ rep)
+                  const unsigned char *__restrict__ touched, float *__restrict__ rep,
+                  NzLists lists)
 {
-    __shared__ NZ list[32 * kChunk];
+    __shared__ NZ list[kListMax];
     __shared__ int warp_counts[32];
     __shared__ float bred[5][kResyncThreads / 32];
+    __shared__ int s_off[2 * (kMaxL / kResyncCols) + 2];
+    __shared__ int s_ok;
     const int isig = tiles.sig[blockIdx.x];
     const SigDesc sd = sigs[isig];
     const int64_t Tz = sd.Tz, ld = sd.ld;
@@ -114,21 +169,12 @@ __global__ void __launch_bounds__(kResyncThreads)
     const int col = tid % kResyncCols, grp = tid / kResyncCols;
     const int64_t c0 = tiles.start[blockIdx.x];
     const int64_t t = c0 + col;
+    // columns this tile computes: [c0, tend)
+    const int64_t tend = tiles.end && tiles.end[blockIdx.x] < Tz ? tiles.end[blockIdx.x] : Tz;
     float drift = 0.f, zex = 0.f, nzg = 0.f, all = 0.f, dz32 = 0.f;
     // r changed on this tile's columns only where an update window reached
     // them, and every window marks the segments it covers as touched
-    bool need = true;
-    if (touched && rep && sd.nseg > 0) {
-        // the problem's segments are the equal cut of seg_start
-        const int64_t ce = c0 + kResyncCols < Tz ? c0 + kResyncCols : Tz;
-        const int j1 = segment_of(Tz, sd.nseg, ce - 1);
-        need = false;
-        for (int j = segment_of(Tz, sd.nseg, c0); j <= j1; j++)
-            if (touched[sd.seg0 + j]) {
-                need = true;
-                break;
-            }
-    }
+    const bool need = !(touched && rep) || tile_touched(sd, c0, touched);
     if (!need) {
         if (tid == 0) {  // the stored report of the unchanged tile (drift 0)
             zex = rep[5 * blockIdx.x + 1];
@@ -144,14 +190,59 @@ __global__ void __launch_bounds__(kResyncThreads)
         acc_lo[i] = 0.f;
     }
 
-    // nonzeros that reach [c0, c0+cols): Z columns in [c0-(L-1), c0+cols+(L-1))
+    // nonzeros that reach [c0, c0+cols): Z columns in [c0-(L-1), c0+cols+(L-1)),
+    // i.e. the buckets of the tiles b-R .. b+R of the same problem
+    const int R = (L - 1 + kResyncCols - 1) / kResyncCols;
+    bool listed = false;
+    if (lists.count) {
+        if (tid <= 2 * R) {
+            const int64_t bb = (int64_t)blockIdx.x - R + tid;
+            int cnt = 0;
+            if (bb >= 0 && bb < tiles.n && tiles.sig[bb] == isig &&
+                tiles.start[bb] == c0 + (int64_t)(tid - R) * kResyncCols)
+                cnt = lists.count[bb];
+            s_off[tid + 1] = cnt;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int acc = 0, ok = 1;
+            s_off[0] = 0;
+            for (int j = 1; j <= 2 * R + 1; j++) {
+                ok &= s_off[j] <= kNzCap;
+                acc += s_off[j];
+                s_off[j] = acc;
+            }
+            s_ok = ok && acc <= kListMax;
+        }
+        __syncthreads();
+        listed = s_ok != 0;
+    }
+    if (listed) {
+        // copy the 2R+1 buckets (in tile order) into the shared list
+        const int warp = tid >> 5, lane = tid & 31;
+        for (int j = warp; j <= 2 * R; j += kResyncThreads / 32) {
+            const int n0 = s_off[j], cnt = s_off[j + 1] - n0;
+            if (cnt == 0)
+                continue;
+            const int64_t bb = (int64_t)blockIdx.x - R + j;
+            const int64_t cb = c0 + (int64_t)(j - R) * kResyncCols;
+            const uint2 *src = lists.ent + bb * kNzCap;
+            for (int i = lane; i < cnt; i += 32) {
+                const uint2 v = src[i];
+                list[n0 + i] = NZ{(int)(v.x / kResyncCols), (int)(cb + v.x % kResyncCols),
+                                  __uint_as_float(v.y)};
+            }
+        }
+        __syncthreads();
+    }
     const int64_t lo = c0 - (L - 1) > 0 ? c0 - (L - 1) : 0;
     const int64_t hi = c0 + kResyncCols + (L - 1) < Tz ? c0 + kResyncCols + (L - 1) : Tz;
-    const int chunk = (32 * kChunk) / K < kChunk ? (32 * kChunk) / K : kChunk;
+    const int chunk = listed ? (int)(hi - lo)
+                             : ((32 * kChunk) / K < kChunk ? (32 * kChunk) / K : kChunk);
     for (int64_t a = lo; a < hi; a += chunk) {
         const int64_t b = a + chunk < hi ? a + chunk : hi;
-        const int n = compact_nonzeros(zz, K, ld, a, b, list, warp_counts);
-        if (t < Tz) {
+        const int n = listed ? s_off[2 * R + 1] : compact_nonzeros(zz, K, ld, a, b, list, warp_counts);
+        if (t < tend) {
             for (int i = 0; i < n; i++) {
                 const NZ e = list[i];
                 const int d = (int)(t - e.t) + (L - 1);
@@ -170,7 +261,7 @@ __global__ void __launch_bounds__(kResyncThreads)
     }
 
     const float lam = sd.lam;
-    if (t < Tz) {
+    if (t < tend) {
 #pragma unroll
         for (int q = 0; q < KPT; q++) {
             const int k = grp + q * kResyncGroups;
@@ -262,7 +353,9 @@ __global__ void __launch_bounds__(kTile)
     const int64_t Tz = sd.Tz, ld = sd.ld, T = Tz + L - 1;
     const int tid = threadIdx.x;
     const int64_t c0 = sigs ? tiles.start[blockIdx.x] : (int64_t)blockIdx.x * kTile;
-    const int64_t c1 = c0 + kTile < T ? c0 + kTile : T;
+    int64_t c1 = c0 + kTile < T ? c0 + kTile : T;
+    if (sigs && tiles.end && tiles.end[blockIdx.x] < c1)
+        c1 = tiles.end[blockIdx.x];
     const int64_t t = c0 + tid;
     double sq = 0.0, l1 = 0.0;
     // Z columns that reach samples [c0, c1): [c0-(L-1), c1) within [0,Tz)
@@ -387,10 +480,18 @@ template <int KPT>
 cudaError_t resync_launch(const SigDesc *sig, Tiles tiles, const float *C, const float *norms,
                           int K, int L, int write_r, unsigned long long *red, int red_stride,
                           unsigned char *dirty, float tol_mark, const unsigned char *touched,
-                          float *rep, cudaStream_t s)
+                          float *rep, NzLists lists, cudaStream_t s)
 {
+    if (lists.count) {
+        const int64_t blocks = (tiles.n + 7) / 8;
+        nz_bucket_kernel<<<(unsigned)blocks, 256, 0, s>>>(sig, tiles, K, touched, lists);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess)
+            return e;
+    }
     resync_kernel<KPT><<<(unsigned)tiles.n, kResyncThreads, 0, s>>>(
-        sig, tiles, C, norms, K, L, write_r, red, red_stride, dirty, tol_mark, touched, rep);
+        sig, tiles, C, norms, K, L, write_r, red, red_stride, dirty, tol_mark, touched, rep,
+        lists);
     return cudaGetLastError();
 }
 
@@ -399,14 +500,14 @@ cudaError_t resync_launch(const SigDesc *sig, Tiles tiles, const float *C, const
 cudaError_t launch_resync(const SigDesc *sig, Tiles tiles, const float *C, const float *norms,
                           int K, int L, int write_r, unsigned long long *red, int red_stride,
                           unsigned char *dirty, float tol_mark, const unsigned char *touched,
-                          float *rep, cudaStream_t s)
+                          float *rep, NzLists lists, cudaStream_t s)
 {
     if (tiles.n <= 0)
         return cudaSuccess;
     const int kpt = (K + kResyncGroups - 1) / kResyncGroups;
 #define CSC_RESYNC(N) \
     return resync_launch<N>(sig, tiles, C, norms, K, L, write_r, red, red_stride, dirty, \
-                            tol_mark, touched, rep, s)
+                            tol_mark, touched, rep, lists, s)
     if (kpt <= 2)
         CSC_RESYNC(2);
     if (kpt <= 4)

@@ -59,6 +59,7 @@ __global__ void __launch_bounds__(kDtxThreads) dtx_kernel(const float *__restric
                                                          const float *__restrict__ X, int K,
                                                          int P, int L, long long T,
                                                          float *__restrict__ beta0,
+                                                         float *__restrict__ r_out,
                                                          unsigned int *__restrict__ absmax_bits,
                                                          double *__restrict__ x2sum)
 {
@@ -129,6 +130,8 @@ __global__ void __launch_bounds__(kDtxThreads) dtx_kernel(const float *__restric
                 if (kk < nk) {
                     const float v = acc[kk][q].value();
                     beta0[(long long)(k0 + kk) * Tz + t] = v;
+                    if (r_out)
+                        r_out[(long long)(k0 + kk) * Tz + t] = v;
                     amax = fmaxf(amax, fabsf(v));
                 }
             }
@@ -146,17 +149,22 @@ __global__ void __launch_bounds__(kDtxThreads) dtx_kernel(const float *__restric
     }
 }
 
+// Ct[((k0 * Kp/4 + q) * W2 + s) * 4 + e] = C[k0][k = 4 q + e][s] (0 for k >= K):
+// for one updated atom k0 and lag s the K coefficients are Kp/4 float4 words,
+// and the words of consecutive lags are adjacent (coalesced across threads).
 __global__ void coef_by_lag_kernel(const float *__restrict__ C, int K, int L, int Kp,
                                    float *__restrict__ Ct)
 {
-    const int W2 = 2 * L - 1;
+    const int W2 = 2 * L - 1, KQ = Kp / 4;
     const long long n = (long long)K * W2 * Kp;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(i % Kp);
-        const long long ks = i / Kp;  // k0 * W2 + s
-        const int s = (int)(ks % W2);
-        const int k0 = (int)(ks / W2);
+        const int e = (int)(i & 3);
+        const long long rest = i >> 2;  // (k0 * KQ + q) * W2 + s
+        const int s = (int)(rest % W2);
+        const long long kq = rest / W2;
+        const int q = (int)(kq % KQ), k0 = (int)(kq / KQ);
+        const int k = 4 * q + e;
         Ct[i] = k < K ? C[((long long)k0 * K + k) * W2 + s] : 0.f;
     }
 }
@@ -180,7 +188,8 @@ cudaError_t launch_dtd(const float *D, int K, int P, int L, float *C, float *nor
 }
 
 cudaError_t launch_dtx(const float *D, const float *X, int K, int P, int L, int64_t T,
-                       float *beta0, unsigned int *absmax_bits, double *x2sum, cudaStream_t s)
+                       float *beta0, float *r_out, unsigned int *absmax_bits, double *x2sum,
+                       cudaStream_t s)
 {
     const int L8 = (L + 7) & ~7;
     const size_t smem =
@@ -193,7 +202,8 @@ cudaError_t launch_dtx(const float *D, const float *X, int K, int P, int L, int6
         return e;
     const int64_t Tz = T - L + 1;
     dim3 grid((unsigned)((Tz + kDtxTile - 1) / kDtxTile), (unsigned)((K + kDtxAtoms - 1) / kDtxAtoms));
-    dtx_kernel<<<grid, kDtxThreads, smem, s>>>(D, X, K, P, L, T, beta0, absmax_bits, x2sum);
+    dtx_kernel<<<grid, kDtxThreads, smem, s>>>(D, X, K, P, L, T, beta0, r_out, absmax_bits,
+                                               x2sum);
     return cudaGetLastError();
 }
 

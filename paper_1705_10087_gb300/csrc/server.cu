@@ -155,6 +155,9 @@ struct Group {
     double *d_E = nullptr, *d_partials = nullptr;
     int *d_tsig = nullptr;
     int64_t *d_tstart = nullptr, *d_toff = nullptr;
+    int *d_nzc = nullptr;  // nonzero lists per resync tile (kernels_fp64.cu)
+    uint2 *d_nze = nullptr;
+    size_t cap_nzc = 0, cap_nze = 0;
     size_t cap_sig = 0, cap_sub = 0, cap_seg_s = 0, cap_seg_e = 0, cap_seg_sig = 0, cap_list = 0,
            cap_dirty = 0, cap_touched = 0, cap_cnt = 0, cap_red = 0, cap_E = 0, cap_partials = 0,
            cap_tsig = 0, cap_tstart = 0, cap_toff = 0, cap_queue = 0;
@@ -258,10 +261,10 @@ int admit(csc_server_t s, Group &g, double t)
         SRV_CUDA(cudaMemcpyAsync(q.X, q.Xh.data(), sizeof(float) * g.P * q.T,
                                  cudaMemcpyHostToDevice, g.st));
         SRV_CUDA(cudaMemsetAsync(q.hdr, 0, sizeof(ReqHeader), g.st));
-        SRV_CUDA(launch_dtx_any(g.D, q.X, g.K, g.P, g.L, q.T, 0, q.beta0, &q.hdr->lmax_bits,
-                                &q.hdr->x2, &q.hdr->tc_err, g.st));
+        // Z = 0: r = beta0, written by the same kernel
+        SRV_CUDA(launch_dtx_any(g.D, q.X, g.K, g.P, g.L, q.T, 0, q.beta0, q.r,
+                                &q.hdr->lmax_bits, &q.hdr->x2, &q.hdr->tc_err, g.st));
         s->launches += 1;
-        SRV_CUDA(cudaMemcpyAsync(q.r, q.beta0, nz, cudaMemcpyDeviceToDevice, g.st));
         SRV_CUDA(cudaMemsetAsync(q.Z, 0, nz, g.st));
         q.state = CSC_REQ_ACTIVE;
         q.t_admit = t;
@@ -467,11 +470,13 @@ int resync_ended(csc_server_t s, Group &g)
     SRV_CUDA(upload(&g.d_tstart, &g.cap_tstart, g.t_start, g.st));
     SRV_CUDA(cudaMemsetAsync(g.d_red, 0, sizeof(unsigned long long) * kRed * n, g.st));
     const Tiles tiles{g.d_tsig, g.d_tstart, (int64_t)g.t_sig.size()};
+    SRV_CUDA(grow(&g.d_nzc, &g.cap_nzc, g.t_sig.size()));
+    SRV_CUDA(grow(&g.d_nze, &g.cap_nze, g.t_sig.size() * kNzCap));
     SRV_CUDA(launch_resync(g.d_sig, tiles, g.C, g.norms, g.K, g.L, 1, g.d_red, kRed, g.dirty,
-                           -1.f, nullptr, nullptr, g.st));
+                           -1.f, nullptr, nullptr, NzLists{g.d_nzc, g.d_nze}, g.st));
     count_dirty_kernel<<<n, 256, 0, g.st>>>(g.dirty, g.d_sig, g.d_cnt);
     SRV_CUDA(cudaGetLastError());
-    s->launches += 2;
+    s->launches += 3;  // bucket lists, resync, dirty count
     SRV_CUDA(cudaMemcpyAsync(g.h_red, g.d_red, sizeof(unsigned long long) * kRed * n,
                              cudaMemcpyDeviceToHost, g.st));
     return CSC_OK;
@@ -559,7 +564,7 @@ void release_group(Group &g)
     void *bufs[] = {g.D,       g.C,       g.Ct,       g.norms,   g.d_sig,    g.d_sub,
                     g.d_seg_s, g.d_seg_e, g.d_seg_sig, g.d_list, g.dirty,    g.touched,
                     g.d_cnt,   g.d_red,   g.d_E,      g.d_partials, g.d_tsig, g.d_tstart,
-                    g.d_toff,  g.ps,      g.d_queue};
+                    g.d_toff,  g.ps,      g.d_queue,  g.d_nzc,   g.d_nze};
     for (void *p : bufs)
         cudaFree(p);
     cudaFreeHost(g.h_cnt);

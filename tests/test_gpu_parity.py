@@ -45,6 +45,11 @@ def gpu_solve(capi, pb, lam, tol, M=0, u=0, max_updates=1 << 40, Z0=None, host=F
     h = capi.csc_setup(D, opts)
     try:
         capi.csc_init(h, X, lam, None if Z0 is None else (Z0 if host else cuda(Z0)))
+        beta0 = None
+        if Z0 is None:  # cold start: beta = r = D~*X as the library computed it
+            b = torch.zeros((pb.K, pb.Tz), dtype=torch.float32, device="cuda")
+            capi.csc_get_beta(h, b)
+            beta0 = b.cpu().numpy()
         Zo = np.zeros((pb.K, pb.Tz), np.float32) if host else torch.zeros(
             (pb.K, pb.Tz), dtype=torch.float32, device="cuda")
         status, E, st = capi.csc_solve(h, tol, max_updates, Zo)
@@ -56,7 +61,7 @@ def gpu_solve(capi, pb, lam, tol, M=0, u=0, max_updates=1 << 40, Z0=None, host=F
         capi.csc_destroy(h)
     Z = Zo if host else Zo.cpu().numpy()
     return dict(Z=Z, E=E, stats=st, status=status, beta=beta.cpu().numpy(), trace=trace,
-                lambda_max=lmax)
+                lambda_max=lmax, beta0=beta0)
 
 
 def assert_parity(Z, E, Zr, Er, tau=1e-6):
@@ -181,6 +186,17 @@ def test_long_signal_reduced_parity(capi, long_small, M, u):
     assert np.abs(r["beta"] - B).max() <= 1e-5
 
 
+_BETA0 = {}
+
+
+def _exact_beta0(pb):
+    """D~*X from the FP64 oracle (computed once per problem)."""
+    key = (pb.seed, pb.X.shape)
+    if key not in _BETA0:
+        _BETA0[key] = oracle.dtx(pb.D, pb.X)
+    return _BETA0[key]
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("M,u", [(M, 0) for M in LONG["segments"]] + [(1024, 24)])
 def test_long_signal_full_size_parity(capi, long_full, M, u):
@@ -192,9 +208,14 @@ def test_long_signal_full_size_parity(capi, long_full, M, u):
     assert_parity(r["Z"], r["E"], ref["Z"], Er)
     st = r["stats"]
     assert st["kkt_zero_excess"] <= 1e-5 and st["kkt_nonzero_gap"] <= 1e-5
-    # objective trace (Prop. A.1 per update) agrees with the final FP64 objective
+    # objective trace (Prop. A.1 per update, from E(0) = |X|^2 / 2) agrees with the
+    # final FP64 objective.  The decreases are those of the problem whose beta0
+    # is the one the library computed (the state r is exact for it after each
+    # resync), whose objective at Z is E(Z) - <Z, beta0_computed - D~*X>.
     tr = r["trace"]
-    assert tr["E_start"] - tr["decrease"].sum() == pytest.approx(r["E"], rel=1e-6)
+    offset = float(np.sum(r["Z"].astype(np.float64) *
+                          (r["beta0"].astype(np.float64) - _exact_beta0(pb))))
+    assert tr["E_start"] - tr["decrease"].sum() == pytest.approx(r["E"] - offset, rel=1e-6)
     assert tr["updates"].sum() == st["updates"]
 
 
