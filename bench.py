@@ -160,19 +160,27 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def phase_traffic():
-    """DRAM bytes per phase-kernel launch from the committed ncu summary, or None
+def phase_profile():
+    """Per-launch counters of the phase kernel from the committed ncu summary
+    (dram_bytes_per_launch, l2_bytes_per_launch, l2_throughput_pct), or {}
     when the kernel source changed since those counters were taken."""
     import hashlib
     try:
         text = open(os.path.join(ROOT, "profiles", f"phase_kernel_{WORKLOAD}.md")).read()
         src = open(os.path.join(ROOT, "paper_1705_10087_gb300", "csrc", "kernel_phase.cu"), "rb").read()
     except OSError:
-        return None
-    fields = dict(ln.split(":", 1) for ln in text.splitlines() if ln.startswith(("kernel_source", "dram_")))
+        return {}
+    fields = dict(ln.split(":", 1) for ln in text.splitlines()
+                  if ln.startswith(("kernel_source", "dram_", "l2_")))
     if fields.get("kernel_source_sha256_16", "").strip() != hashlib.sha256(src).hexdigest()[:16]:
-        return None
-    return float(fields["dram_bytes_per_launch"])
+        return {}
+    out = {}
+    for k in ("dram_bytes_per_launch", "l2_bytes_per_launch", "l2_throughput_pct"):
+        try:
+            out[k] = float(fields[k])
+        except (KeyError, ValueError):
+            pass
+    return out
 
 
 def over_ranks(dist, device, elapsed, units):
@@ -708,6 +716,9 @@ def main():
     if rank != 0:
         dist.destroy_process_group() if world > 1 else None
         return
+    clk_sum = clk.summary()
+    prof = phase_profile()
+    sm_mhz = clk_sum.get("sm_mhz") or 0.0
     line = {
         "metric": METRIC, "value": updates_all / (tot_ms_max * 1e-3), "unit": "updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -722,18 +733,33 @@ def main():
         "init_ms": statistics.mean(init_ms),
         "solve_ms": statistics.mean(s["solve_ms"] for s in sts),
         "updates_per_step": updates / args.steps,
+        # live device time of a step by part (CUDA events inside the library)
+        "breakdown_ms": {"setup_and_init": statistics.mean(init_ms),
+                         "phase_kernels": phase_ms / args.steps,
+                         "resyncs": sum(s["resync_ms"] for s in sts) / args.steps,
+                         "objective": sum(s["objective_ms"] for s in sts) / args.steps,
+                         "solve_total": statistics.mean(s["solve_ms"] for s in sts)},
         "sweeps": sts[-1]["sweeps"], "resyncs": sts[-1]["resyncs"],
         "rel_gap_final": (Es[-1] - g["E_star"]) / g["E_star"] if g else None,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak if achieved else None, "traffic": phase_traffic(),
+                     "frac": achieved / peak if achieved else None,
+                     "traffic": prof.get("dram_bytes_per_launch"),
                      "kernel": "phase_kernel", "peak_kind": peak_kind,
                      "avg_launch_us": 1e3 * phase_ms / phase_launches if phase_launches else None,
-                     "launches": phase_launches},
+                     "launches": phase_launches,
+                     # the state lives in L2: the level the data are served from
+                     "l2": {"bytes_per_launch": prof.get("l2_bytes_per_launch"),
+                            "throughput_pct_of_peak": prof.get("l2_throughput_pct"),
+                            "source": "ncu summary in profiles/ (null if the kernel changed)"},
+                     # latency: SM cycles of phase-kernel time per applied update
+                     # (all SMs together), phase time x median SM clock / updates
+                     "cycles_per_update": (phase_ms * 1e-3 * sm_mhz * 1e6 / updates
+                                           if updates and sm_mhz else None)},
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": "updates/s",
                 "h2d_bytes_per_step": int(pb.D.nbytes + pb.X.nbytes),
                 "d2h_bytes_per_step": int(pb.K * pb.Tz * 4 + 8)},
-        "clocks": clk.summary(),
+        "clocks": clk_sum,
     }
     if sweep:
         line["segment_sweep"] = sweep

@@ -126,6 +126,9 @@ typedef struct csc_stats {
     int64_t drift_resyncs;    /* resyncs that interrupted a CD round still running after
                                  32 sweeps (float32 drift on strongly coupled atoms);
                                  they do not count towards max_resyncs */
+    double resync_ms;         /* summed device time of the resyncs (nonzero lists + resync
+                                 kernel; time_kernels = 1, else 0) */
+    double objective_ms;      /* device time of the final objective (time_kernels = 1) */
 } csc_stats;
 
 /* Fill *o with the defaults (all zero / -1 as documented above). */

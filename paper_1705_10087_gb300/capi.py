@@ -40,7 +40,8 @@ class csc_stats(ctypes.Structure):
                 ("max_delta_z", ctypes.c_double), ("solve_ms", ctypes.c_double),
                 ("phase_ms", ctypes.c_double), ("phase_launches", ctypes.c_int64),
                 ("visits", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
-                ("drift_resyncs", ctypes.c_int64)]
+                ("drift_resyncs", ctypes.c_int64), ("resync_ms", ctypes.c_double),
+                ("objective_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -77,6 +78,17 @@ class csc_request_info(ctypes.Structure):
 
 
 CSC_REQ_QUEUED, CSC_REQ_ACTIVE, CSC_REQ_DONE = 0, 1, 2
+
+
+class csc2d_stats(ctypes.Structure):
+    _fields_ = [("updates", ctypes.c_int64), ("sweeps", ctypes.c_int64),
+                ("bands", ctypes.c_int32), ("phases", ctypes.c_int32),
+                ("resyncs", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("objective", ctypes.c_double), ("max_delta_z", ctypes.c_double),
+                ("solve_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class csc_shard_plan(ctypes.Structure):
@@ -169,6 +181,12 @@ def load(path: str | None = None):
     lib.csc_shard_resync.argtypes = [_vp, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
     lib.csc_shard_objective.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
     lib.csc_shard_get_z.argtypes = [_vp, _vp]
+    lib.csc2d_plan.argtypes = [_i64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                               ctypes.POINTER(ctypes.c_int), _vp]
+    lib.csc2d_solve.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp,
+                                _i64, _i64, ctypes.c_double, ctypes.c_double, _i64, ctypes.c_int,
+                                ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(csc2d_stats), _vp]
     lib.csc_last_error_string.argtypes = []
     lib.csc_last_error_string.restype = ctypes.c_char_p
     for name in ("csc_setup", "csc_init", "csc_solve", "csc_destroy", "csc_lambda_max",
@@ -182,7 +200,7 @@ def load(path: str | None = None):
                  "csc_shard_plan_make", "csc_shard_init", "csc_shard_phase",
                  "csc_shard_halo_out", "csc_shard_halo_in", "csc_shard_z_out",
                  "csc_shard_z_in", "csc_shard_updates", "csc_shard_resync",
-                 "csc_shard_objective", "csc_shard_get_z"):
+                 "csc_shard_objective", "csc_shard_get_z", "csc2d_plan", "csc2d_solve"):
         getattr(lib, name).restype = ctypes.c_int
     if path == _build.LIB:
         _lib = lib
@@ -617,3 +635,34 @@ def csc_shard_get_z(h, out) -> None:
         if int(np.prod(_shape(out))) != h.K * int(sh["col_count"]):
             raise ValueError("Z_out must hold K * col_count values")
     _check(load().csc_shard_get_z(h, _ptr(out, True)))
+
+
+# ------------------------------------------------------------------ images (2-D)
+
+def csc2d_plan(Hz: int, h: int, M: int = 0):
+    """Host-only band schedule: (M, phases, starts[M+1])."""
+    Mo, c = ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().csc2d_plan(int(Hz), int(h), int(M), ctypes.byref(Mo), ctypes.byref(c), None))
+    starts = np.zeros(Mo.value + 1, np.int64)
+    _check(load().csc2d_plan(int(Hz), int(h), Mo.value, None, None, starts.ctypes.data))
+    return Mo.value, c.value, starts
+
+
+def csc2d_solve(D, X, lam: float, tol: float, max_updates: int = 1 << 62, M: int = 0,
+                updates_per_visit: int = 0, Z_out=None, stream=None):
+    """D [K,P,h,w], X [P,H,W] -> (status, objective, stats dict)."""
+    if len(D.shape) != 4 or len(X.shape) != 3:
+        raise ValueError("D must be [K, P, h, w] and X [P, H, W]")
+    K, P, h, w = (int(x) for x in D.shape)
+    if int(X.shape[0]) != P:
+        raise ValueError(f"X has {int(X.shape[0])} channels, D {P}")
+    H, W = int(X.shape[1]), int(X.shape[2])
+    if Z_out is not None and int(np.prod(_shape(Z_out))) != K * (H - h + 1) * (W - w + 1):
+        raise ValueError("Z_out must hold K * (H-h+1) * (W-w+1) values")
+    obj = ctypes.c_double(0.0)
+    st = csc2d_stats()
+    status = _check(load().csc2d_solve(_ptr(D), K, P, h, w, _ptr(X), H, W, float(lam),
+                                       float(tol), int(max_updates), int(M),
+                                       int(updates_per_visit), _ptr(Z_out, True),
+                                       ctypes.byref(obj), ctypes.byref(st), _stream(stream)))
+    return status, obj.value, st.as_dict()

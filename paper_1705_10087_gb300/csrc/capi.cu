@@ -381,6 +381,10 @@ int csc_destroy(csc_handle_t h)
         cudaEventDestroy(h->ev_i0);
     if (h->ev_i1)
         cudaEventDestroy(h->ev_i1);
+    if (h->ev_r0)
+        cudaEventDestroy(h->ev_r0);
+    if (h->ev_r1)
+        cudaEventDestroy(h->ev_r1);
     for (int i = 0; i < h->n_kev; i++)
         cudaEventDestroy(h->kev[i]);
     delete[] h->kev;
@@ -699,6 +703,18 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
         }
     }
 
+    if (timed && !h->ev_r0) {
+        CSC_CUDA(cudaEventCreate(&h->ev_r0));
+        CSC_CUDA(cudaEventCreate(&h->ev_r1));
+    }
+    double resync_ms = 0.0, objective_ms = 0.0;
+    // device time between ev_r0 and ev_r1 (recorded around one resync or objective)
+    auto span_ms = [&](double *acc) -> int {
+        float ms = 0.f;
+        CSC_CUDA(cudaEventElapsedTime(&ms, h->ev_r0, h->ev_r1));
+        *acc += ms;
+        return CSC_OK;
+    };
     CSC_CUDA(cudaMemsetAsync(h->dirty, 1, (size_t)M, s));
     // the first resync of the solve recomputes every tile
     CSC_CUDA(cudaMemsetAsync(h->touched, 1, (size_t)M, s));
@@ -877,14 +893,23 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
         // the segments it still had to visit)
         if (round_done && !last)
             CSC_CUDA(cudaMemsetAsync(h->dirty, 0, (size_t)M, s));
+        if (timed)
+            CSC_CUDA(cudaEventRecord(h->ev_r0, s));
         CSC_CUDA(launch_resync(h->d_sig, h->resync_tiles(), h->C, h->norms, h->K, h->L, 1,
                                sc->red, 0, last ? nullptr : h->dirty, tol_inner, h->touched,
                                h->tile_rep, h->nz_lists(), s));
+        if (timed)
+            CSC_CUDA(cudaEventRecord(h->ev_r1, s));
         CSC_CUDA(cudaMemsetAsync(h->touched, 0, (size_t)M, s));
         h->launches += 2;
         unsigned long long red[8];
         CSC_CUDA(cudaMemcpyAsync(red, sc->red, sizeof red, cudaMemcpyDeviceToHost, s));
         CSC_CUDA(cudaStreamSynchronize(s));
+        if (timed) {
+            const int rc = span_ms(&resync_ms);
+            if (rc != CSC_OK)
+                return rc;
+        }
         if (round_done)
             resyncs++;
         else
@@ -904,16 +929,34 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
     if (!report_fresh) {
         // optimality report against a fresh r, leaving r unchanged
         CSC_CUDA(cudaMemsetAsync(sc->red, 0, sizeof(sc->red), s));
+        if (timed)
+            CSC_CUDA(cudaEventRecord(h->ev_r0, s));
         CSC_CUDA(launch_resync(h->d_sig, h->resync_tiles(), h->C, h->norms, h->K, h->L, 0,
                                sc->red, 0, nullptr, 0.f, h->touched, h->tile_rep, h->nz_lists(), s));
+        if (timed) {
+            CSC_CUDA(cudaEventRecord(h->ev_r1, s));
+            CSC_CUDA(cudaEventSynchronize(h->ev_r1));
+            const int rc = span_ms(&resync_ms);
+            if (rc != CSC_OK)
+                return rc;
+        }
         h->launches += 2;
     }
     CSC_CUDA(cudaEventRecord(h->ev1, s));
     double E = 0.0;
     {
-        int rc = objectives(h, h->Z, &E);
+        if (timed)
+            CSC_CUDA(cudaEventRecord(h->ev_r0, s));
+        int rc = objectives(h, h->Z, &E);  // (synchronises the stream)
         if (rc != CSC_OK)
             return rc;
+        if (timed) {
+            CSC_CUDA(cudaEventRecord(h->ev_r1, s));
+            CSC_CUDA(cudaEventSynchronize(h->ev_r1));
+            rc = span_ms(&objective_ms);
+            if (rc != CSC_OK)
+                return rc;
+        }
     }
     if (Z_out)
         CSC_CUDA(copy_out(Z_out, h->Z, sizeof(float) * h->K * Tz, s));
@@ -951,6 +994,8 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
         stats->visits = visits;
         stats->kernel_launches = h->launches - launches0;
         stats->drift_resyncs = drift_resyncs;
+        stats->resync_ms = resync_ms;
+        stats->objective_ms = objective_ms;
     }
     return status != CSC_OK ? status : (converged ? CSC_OK : CSC_NOT_CONVERGED);
 }

@@ -139,6 +139,7 @@ struct csc_handle_s {
     Poll *poll = nullptr;  // pinned
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEvent_t ev_i0 = nullptr, ev_i1 = nullptr;  // around the beta0 kernel (time_kernels)
+    cudaEvent_t ev_r0 = nullptr, ev_r1 = nullptr;  // around a resync / the objective
     double init_ms = -1.0;
     cudaEvent_t *kev = nullptr;  // per-launch timing events (2 per launch of a poll batch)
     int n_kev = 0;

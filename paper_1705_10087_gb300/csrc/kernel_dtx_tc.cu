@@ -44,6 +44,7 @@ constexpr int kTcM = 128;        // time rows per tile
 constexpr int kTcThreads = 128;  // 4 warps: one per 32 TMEM lanes
 constexpr int kSplits = 3;
 constexpr unsigned kWaitLimit = 1u << 22;
+constexpr int kMaxSteps = 128;  // P * L16 / 16 contraction steps (B alone then needs >= 96 KB)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -179,8 +180,11 @@ struct TcLayout {
     }
 };
 
+// At N = 32 three CTAs fit an SM's shared memory for short atoms (P = 1,
+// L = 200: 76 KB each); the register budget is set so that they also fit
+// its register file.
 template <int N>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(kTcThreads, N <= 32 ? 3 : 1)
     dtx_tc_kernel(const float *__restrict__ D, const float *__restrict__ X, int K, int P, int L,
                   long long T, int mode, float *__restrict__ beta0, float *__restrict__ r_out,
                   unsigned int *__restrict__ absmax_bits, double *__restrict__ x2sum,
@@ -188,6 +192,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 {
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ uint32_t s_taddr;
+    __shared__ uint32_t s_aoff[kMaxSteps];  // A descriptor offset of each contraction step
     const TcLayout lay(P, L, N);
     unsigned char *As = sm + lay.a_off;
     unsigned char *Bs = sm + lay.b_off;
@@ -209,6 +214,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar + 8) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int st = tid; st < lay.nsteps; st += kTcThreads) {
+        const int p = (16 * st) / lay.L16, q0 = ((16 * st) % lay.L16) / 8;
+        s_aoff[st] = (uint32_t)((p * lay.NQ + q0) * 128) >> 4;
     }
     // ---- B: the three BF16 terms of D, per contraction step -----------------
     // element (sigma, s, n8, j8, r, e): D[k = 8 n8 + r][p][tau], j = 16 s + 8 j8 + e
@@ -335,7 +344,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             return;
         // products hh, hm, mh, hl, lh, mm (mode 2: hh only), small terms first.
         // Descriptors differ only in their start address (16-byte units in the
-        // low 14 bits, smem addresses < 256 KB): base descriptors plus offsets.
+        // low 14 bits, smem addresses < 256 KB): base descriptors plus the
+        // per-step offsets tabulated at the start of the kernel.
         const uint32_t d_acc = taddr + (uint32_t)(buf * N);
         const uint64_t ad0 = mma_desc(a_base + (uint32_t)(buf * a_bytes), 128, 128);
         const uint64_t bd0 = mma_desc(b_base, 128, 256);
@@ -343,8 +353,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const uint32_t b_split = (uint32_t)(lay.nsteps * (N / 8) * 256) >> 4;
         uint32_t acc = 0;
         for (int s = 0; s < lay.nsteps; s++) {
-            const int p = (16 * s) / lay.L16, q0 = ((16 * s) % lay.L16) / 8;
-            const uint64_t a_s = ad0 + ((uint32_t)((p * lay.NQ + q0) * 128) >> 4);
+            const uint64_t a_s = ad0 + s_aoff[s];
             const uint64_t b_s = bd0 + ((uint32_t)(s * (N / 8) * 256) >> 4);
             if (mode == 2) {
                 mma_bf16(d_acc, a_s, b_s, idesc, acc);
@@ -479,7 +488,7 @@ cudaError_t launch_dtx_tc(const float *D, const float *X, int K, int P, int L, i
     if (K > 64)
         return cudaErrorNotSupported;
     const size_t smem = dtx_tc_smem(K, P, L);
-    if (smem > (size_t)kMaxSmem)
+    if (smem > (size_t)kMaxSmem || (size_t)P * ((L + 15) / 16) > (size_t)kMaxSteps)
         return cudaErrorNotSupported;
     const int64_t Tz = T - L + 1;
     const int64_t ntiles = (Tz + kTcM - 1) / kTcM;
@@ -493,13 +502,20 @@ cudaError_t launch_dtx_tc(const float *D, const float *X, int K, int P, int L, i
             e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess)
             return e;
-        // one wave of persistent CTAs: as many per SM as are resident at once
-        // (up to four; at N <= 64 tensor-memory columns each they never ask an
-        // SM for more than its 512 columns), each looping over its tiles
-        int per_sm = 1;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTcThreads, smem);
+        // one wave of persistent CTAs: as many per SM as its shared memory
+        // (1 KB reserved per block) and register file hold at once, up to four
+        // (at N <= 64 tensor-memory columns each they never ask an SM for more
+        // than its 512 columns), each looping over its tiles
+        int smem_sm = 0;
+        cudaFuncAttributes fa;
+        e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        if (e == cudaSuccess)
+            e = cudaFuncGetAttributes(&fa, kern);
         if (e != cudaSuccess)
             return e;
+        const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + 1024);
+        const int by_regs = 65536 / (fa.numRegs * kTcThreads > 0 ? fa.numRegs * kTcThreads : 1);
+        int per_sm = by_smem < by_regs ? by_smem : by_regs;
         per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
         const int64_t cap = (int64_t)nsm * per_sm;
         const unsigned grid = (unsigned)(ntiles < cap ? ntiles : cap);

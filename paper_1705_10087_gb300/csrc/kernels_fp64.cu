@@ -92,6 +92,7 @@ __device__ __forceinline__ void df_add_prod(float &hi, float &lo, float a, float
 constexpr int kResyncThreads = 256;
 constexpr int kResyncGroups = kResyncThreads / kResyncCols;  // atom groups
 constexpr int kListMax = 32 * kChunk;  // nonzeros a tile gathers from the lists at once
+constexpr int kGatherBatch = 4;        // nonzeros whose coefficients are loaded together
 
 // Whether r may have changed on the columns [c0, c0 + kResyncCols) of a
 // problem since the last resync: every update window marks the segments it
@@ -243,18 +244,34 @@ __global__ void __launch_bounds__(kResyncThreads)
         const int64_t b = a + chunk < hi ? a + chunk : hi;
         const int n = listed ? s_off[2 * R + 1] : compact_nonzeros(zz, K, ld, a, b, list, warp_counts);
         if (t < tend) {
-            for (int i = 0; i < n; i++) {
-                const NZ e = list[i];
-                const int d = (int)(t - e.t) + (L - 1);
-                if (d < 0 || d >= W2)
-                    continue;
-                const float *Cl = C + (int64_t)e.k * K * W2 + d;
+            // kGatherBatch nonzeros at a time: all their coefficients are loaded
+            // first (clamped to valid addresses), so that one L2 round trip
+            // serves the batch; a nonzero out of the window (or past n) adds
+            // the exact product 0 and leaves the sums unchanged
+            // (fewer at a time for many atoms per thread: registers)
+            constexpr int NB = KPT <= 8 ? kGatherBatch : (KPT <= 16 ? 2 : 1);
+            for (int i0 = 0; i0 < n; i0 += NB) {
+                float cv[NB][KPT], zv[NB];
 #pragma unroll
-                for (int q = 0; q < KPT; q++) {
-                    const int k = grp + q * kResyncGroups;
-                    if (k < K)
-                        df_add_prod(acc_hi[q], acc_lo[q], __ldg(Cl + (int64_t)k * W2), e.z);
+                for (int b = 0; b < NB; b++) {
+                    const int i = i0 + b < n ? i0 + b : n - 1;
+                    const NZ e = list[i];
+                    const int d = (int)(t - e.t) + (L - 1);
+                    const bool in = i0 + b < n && d >= 0 && d < W2;
+                    zv[b] = in ? e.z : 0.f;
+                    const float *Cl = C + (int64_t)e.k * K * W2 + (in ? d : 0);
+#pragma unroll
+                    for (int q = 0; q < KPT; q++) {
+                        const int k = grp + q * kResyncGroups;
+                        cv[b][q] = __ldg(Cl + (int64_t)(k < K ? k : K - 1) * W2);
+                    }
                 }
+#pragma unroll
+                for (int b = 0; b < NB; b++)
+#pragma unroll
+                    for (int q = 0; q < KPT; q++)
+                        if (zv[b] != 0.f)
+                            df_add_prod(acc_hi[q], acc_lo[q], cv[b][q], zv[b]);
             }
         }
         __syncthreads();
@@ -516,12 +533,8 @@ cudaError_t launch_resync(const SigDesc *sig, Tiles tiles, const float *C, const
         CSC_RESYNC(8);
     if (kpt <= 16)
         CSC_RESYNC(16);
-    if (kpt <= 32)
+    if (kpt <= 32)  // K <= 256 (csc_setup, the server)
         CSC_RESYNC(32);
-    if (kpt <= 64)
-        CSC_RESYNC(64);
-    if (kpt <= 128)
-        CSC_RESYNC(128);
 #undef CSC_RESYNC
     return cudaErrorInvalidValue;
 }

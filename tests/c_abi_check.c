@@ -11,7 +11,9 @@
 #include <string.h>
 
 #include "csc.h"
+#include "csc2d.h"
 #include "csc_server.h"
+#include "csc_shard.h"
 
 #define CHECK(c)                                                  \
     do {                                                          \
@@ -32,14 +34,28 @@ static void print_layouts(void)
            OFF(csc_opts, max_sweeps), OFF(csc_opts, time_kernels),
            OFF(csc_opts, segment_width), OFF(csc_opts, init_mode), OFF(csc_opts, launch_mode),
            OFF(csc_opts, reserved));
-    printf("csc_stats %u %u %u %u %u %u %u %u %u %u %u %u %u %u %u %u %u %u\n",
+    printf("csc_stats %u %u %u %u %u %u %u %u %u %u %u %u %u %u %u %u %u %u %u %u\n",
            (unsigned)sizeof(csc_stats), OFF(csc_stats, updates), OFF(csc_stats, sweeps),
            OFF(csc_stats, segments), OFF(csc_stats, phases), OFF(csc_stats, resyncs),
            OFF(csc_stats, converged), OFF(csc_stats, objective), OFF(csc_stats, max_drift),
            OFF(csc_stats, kkt_zero_excess), OFF(csc_stats, kkt_nonzero_gap),
            OFF(csc_stats, max_delta_z), OFF(csc_stats, solve_ms), OFF(csc_stats, phase_ms),
            OFF(csc_stats, phase_launches), OFF(csc_stats, visits),
-           OFF(csc_stats, kernel_launches), OFF(csc_stats, drift_resyncs));
+           OFF(csc_stats, kernel_launches), OFF(csc_stats, drift_resyncs),
+           OFF(csc_stats, resync_ms), OFF(csc_stats, objective_ms));
+    printf("csc_shard_plan %u %u %u %u %u %u %u %u %u %u %u %u %u %u %u %u\n",
+           (unsigned)sizeof(csc_shard_plan), OFF(csc_shard_plan, T), OFF(csc_shard_plan, Tz),
+           OFF(csc_shard_plan, L), OFF(csc_shard_plan, M), OFF(csc_shard_plan, phases),
+           OFF(csc_shard_plan, world), OFF(csc_shard_plan, rank), OFF(csc_shard_plan, seg_first),
+           OFF(csc_shard_plan, seg_count), OFF(csc_shard_plan, col_first),
+           OFF(csc_shard_plan, col_count), OFF(csc_shard_plan, halo_left),
+           OFF(csc_shard_plan, halo_right), OFF(csc_shard_plan, x_first),
+           OFF(csc_shard_plan, x_count));
+    printf("csc2d_stats %u %u %u %u %u %u %u %u %u %u %u\n", (unsigned)sizeof(csc2d_stats),
+           OFF(csc2d_stats, updates), OFF(csc2d_stats, sweeps), OFF(csc2d_stats, bands),
+           OFF(csc2d_stats, phases), OFF(csc2d_stats, resyncs), OFF(csc2d_stats, converged),
+           OFF(csc2d_stats, objective), OFF(csc2d_stats, max_delta_z), OFF(csc2d_stats, solve_ms),
+           OFF(csc2d_stats, kernel_launches));
     printf("csc_tune_result %u %u %u %u %u %u %u\n", (unsigned)sizeof(csc_tune_result),
            OFF(csc_tune_result, segment_width), OFF(csc_tune_result, updates_per_visit),
            OFF(csc_tune_result, phases), OFF(csc_tune_result, candidates),
@@ -96,6 +112,19 @@ int main(int argc, char **argv)
     CHECK(csc_destroy(NULL) == CSC_OK);
     CHECK(csc_server_step(srv, NULL, NULL, NULL) == CSC_EINVAL);
     CHECK(csc_server_destroy(NULL) == CSC_OK);
+
+    /* host-only plans of the sharded and the 2-D solves */
+    {
+        csc_shard_plan sp;
+        CHECK(csc_shard_plan_make(2000, 16, 10, 2, 1, &sp) == CSC_OK);
+        CHECK(sp.seg_first == 5 && sp.col_first == 5 * 1985 / 10 && sp.halo_left == 15);
+        CHECK(csc_shard_plan_make(2000, 16, 10, 11, 0, &sp) == CSC_EINVAL);
+        CHECK(csc_shard_phase(NULL, 0, 1e-6) == CSC_EINVAL);
+        CHECK(csc2d_plan(121, 8, 8, &M, &c, starts) == CSC_OK);
+        CHECK(M == 8 && c == 2 && starts[1] == 15);
+        CHECK(csc2d_solve(NULL, 1, 1, 2, 2, NULL, 4, 4, 0.1, 1e-6, 1, 0, 0, NULL, NULL, NULL,
+                          NULL) == CSC_EINVAL);
+    }
     printf("ok\n");
     return 0;
 }

@@ -356,3 +356,33 @@ def test_invalid_arguments_raise(capi):
             capi.csc_solve(h, 0.0)
     finally:
         capi.csc_destroy(h)
+
+
+def test_status_after_the_last_resync_is_the_exact_check(capi):
+    """After the last resync allowed, csc_solve's status is the exact check's:
+    with one resync allowed this problem's float32 loop settles twice while
+    the refreshed state still has a coordinate above tol, so the solve must
+    say CSC_NOT_CONVERGED (not a limit: few sweeps, few updates); with two
+    resyncs allowed the third refresh passes and the solve converges.  tol is
+    below the float32 floor, where only the refresh can tell."""
+    pb = synth.make_problem(K=25, P=7, L=64, T=20_000, rho=0.005, sigma=0.1, seed=1)
+    D, X = cuda(pb.D), cuda(pb.X)
+    tol, max_sweeps = 1e-9, 2000
+    out = {}
+    for mr in (1, 2):
+        h = capi.csc_setup(D, capi.make_opts(max_resyncs=mr, updates_per_visit=24,
+                                             max_sweeps=max_sweeps))
+        try:
+            capi.csc_init(h, X, 1.0)
+            lam = 0.1 * capi.csc_lambda_max(h)
+            capi.csc_init(h, X, lam)
+            out[mr] = capi.csc_solve(h, tol, 1 << 40)
+        finally:
+            capi.csc_destroy(h)
+    status, E, st = out[1]
+    assert status == capi.CSC_NOT_CONVERGED and st["converged"] == 0, st
+    assert st["resyncs"] == 2 and st["sweeps"] < max_sweeps, st  # the check, not a limit
+    assert st["max_delta_z"] >= tol
+    status2, E2, st2 = out[2]
+    assert status2 == capi.CSC_OK and st2["converged"] == 1, st2
+    assert E2 <= E * (1 + 1e-12)
