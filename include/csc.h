@@ -98,7 +98,11 @@ typedef struct csc_opts {
                                   is replayed from a CUDA graph, captured the second time a
                                   plan is solved (a plan solved once runs direct launches);
                                   1 = direct kernel launches.  Same results */
-    int32_t reserved[1];       /* must be zero */
+    int32_t threads_per_segment; /* threads that run one segment's visit: 0 = automatic
+                                  (a block), 128 = a block of at least 2L-1 threads per
+                                  segment, 32 = one warp per segment where eligible (K =
+                                  25, 2L-1 <= 128, the segment's tile fits shared memory;
+                                  else a block).  Same results */
 } csc_opts;
 
 typedef struct csc_stats {
@@ -218,6 +222,7 @@ typedef struct csc_tune_result {
     int32_t candidates;        /* solves timed */
     double best_ms;            /* csc_stats.solve_ms of the choice */
     double default_ms;         /* the same for width 2L-2 at the starting u (-1 if not run) */
+    int32_t threads_per_segment; /* chosen threads per segment (32 or 128) */
 } csc_tune_result;
 
 /*
@@ -227,11 +232,13 @@ typedef struct csc_tune_result {
  * candidate and keeps the fastest by device solve time: first the segment
  * width among L-1, 2L-2, 3L-3, 4L-4, 6L-6 (which sets the number of phases c)
  * at the handle's updates_per_visit (24 if 0), then updates_per_visit among
- * 8, 24, 64 and 0 at that width.  Every candidate starts from the state the
- * problem had when csc_autotune was called, and that state is restored
- * afterwards; the choice is stored in the handle's options (segments = 0,
- * segment_width, updates_per_visit) for the following solves and, when out is
- * not NULL, reported.  Tune on a representative problem of the (K, L, P) at
+ * 8, 24, 64 and 0 at that width, then (where both forms apply) one warp or a
+ * block of threads per segment (csc_opts.threads_per_segment).  Every
+ * candidate starts from the state the problem had when csc_autotune was
+ * called, and that state is restored afterwards; the choice is stored in the
+ * handle's options (segments = 0, segment_width, updates_per_visit,
+ * threads_per_segment) for the following solves and, when out is not NULL,
+ * reported.  Tune on a representative problem of the (K, L, P) at
  * hand and re-use the result through csc_opts for others.
  */
 int csc_autotune(csc_handle_t h, double tol, int64_t max_updates, csc_tune_result *out);

@@ -28,7 +28,7 @@ class csc_opts(ctypes.Structure):
                 ("max_resyncs", ctypes.c_int32), ("sweeps_per_poll", ctypes.c_int32),
                 ("max_sweeps", ctypes.c_int32), ("time_kernels", ctypes.c_int32),
                 ("segment_width", ctypes.c_int32), ("init_mode", ctypes.c_int32),
-                ("launch_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("launch_mode", ctypes.c_int32), ("threads_per_segment", ctypes.c_int32)]
 
 
 class csc_stats(ctypes.Structure):
@@ -50,7 +50,8 @@ class csc_stats(ctypes.Structure):
 class csc_tune_result(ctypes.Structure):
     _fields_ = [("segment_width", ctypes.c_int32), ("updates_per_visit", ctypes.c_int32),
                 ("phases", ctypes.c_int32), ("candidates", ctypes.c_int32),
-                ("best_ms", ctypes.c_double), ("default_ms", ctypes.c_double)]
+                ("best_ms", ctypes.c_double), ("default_ms", ctypes.c_double),
+                ("threads_per_segment", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -286,12 +287,14 @@ def csc_default_opts() -> csc_opts:
 
 def make_opts(segments: int = 0, updates_per_visit: int = 0, max_resyncs: int = -1,
               sweeps_per_poll: int = 0, max_sweeps: int = 0, time_kernels: int = 0,
-              segment_width: int = 0, init_mode: int = 0, launch_mode: int = 0) -> csc_opts:
+              segment_width: int = 0, init_mode: int = 0, launch_mode: int = 0,
+              threads_per_segment: int = 0) -> csc_opts:
     o = csc_default_opts()
     o.segments, o.updates_per_visit = segments, updates_per_visit
     o.max_resyncs, o.sweeps_per_poll, o.max_sweeps = max_resyncs, sweeps_per_poll, max_sweeps
     o.time_kernels, o.segment_width, o.init_mode = time_kernels, segment_width, init_mode
     o.launch_mode = launch_mode
+    o.threads_per_segment = threads_per_segment
     return o
 
 

@@ -73,6 +73,12 @@ int64_t auto_width(int L)
     return 2 * (int64_t)L - 2 > 1 ? 2 * (int64_t)L - 2 : 1;
 }
 
+// Threads per segment when the options leave it automatic: a block (the
+// one-warp form measured 2.2x slower per phase launch on the long signal,
+// 94.8 vs 43.7 us: its lanes apply up to four window columns each in turn,
+// which costs more than the block barrier it saves; csc_autotune tries both).
+constexpr int kAutoThreadsPerSegment = 128;
+
 int auto_segments(int64_t Tz, int L)
 {
     int64_t M = Tz / auto_width(L);
@@ -98,6 +104,11 @@ int csc_record_error(int code, const char *fmt, ...)
 }
 
 namespace {
+
+int threads_per_segment(csc_handle_t h)
+{
+    return h->opts.threads_per_segment ? h->opts.threads_per_segment : kAutoThreadsPerSegment;
+}
 
 // Segments of every signal, their lambdas and the per-phase lists.
 int build_plan(csc_handle_t h)
@@ -412,7 +423,9 @@ int csc_setup(csc_handle_t *hp, const float *D, int K, int P, int L, const csc_o
         if (o.segments < 0 || o.updates_per_visit < 0 || o.max_resyncs < -1 ||
             o.sweeps_per_poll < 0 || o.max_sweeps < 0 || o.time_kernels < 0 ||
             o.time_kernels > 1 || o.segment_width < 0 || o.init_mode < 0 || o.init_mode > 3 ||
-            o.launch_mode < 0 || o.launch_mode > 1 || o.reserved[0])
+            o.launch_mode < 0 || o.launch_mode > 1 ||
+            (o.threads_per_segment != 0 && o.threads_per_segment != 32 &&
+             o.threads_per_segment != 128))
             return fail(CSC_EINVAL, "csc_setup: invalid options");
     }
     csc_handle_t h = *hp;
@@ -681,7 +694,7 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
             return rc;
     }
     const int M = h->M, c = h->c;
-    const PhaseConfig cfg = phase_config(h->K, h->L, h->w_max);
+    const PhaseConfig cfg = phase_config(h->K, h->L, h->w_max, threads_per_segment(h));
     const int S = h->opts.sweeps_per_poll ? h->opts.sweeps_per_poll : 4;
     const int64_t max_sweeps = h->opts.max_sweeps ? h->opts.max_sweeps : 1000000;
     const int max_resyncs = h->opts.max_resyncs < 0 ? 3 : h->opts.max_resyncs;
@@ -1080,6 +1093,25 @@ int csc_autotune(csc_handle_t h, double tol, int64_t max_updates, csc_tune_resul
         double ms;
         rc = trial(w1, us[i], &ms);
     }
+    // stage 3: threads per segment (one warp or a block) at that width and u
+    int best_t = saved.threads_per_segment;
+    if (rc == CSC_OK && phase_warp_eligible(h->K, h->L, 2 * std::max(best_w, 1))) {
+        const int tps[] = {32, 128};
+        const int t0 = saved.threads_per_segment ? saved.threads_per_segment
+                                                 : kAutoThreadsPerSegment;
+        best_t = t0;
+        for (int i = 0; i < 2 && rc == CSC_OK; i++) {
+            if (tps[i] == t0)
+                continue;
+            const double before = best_ms;
+            double ms;
+            h->opts.threads_per_segment = tps[i];
+            rc = trial(best_w, best_u, &ms);
+            h->opts.threads_per_segment = saved.threads_per_segment;
+            if (best_ms < before)
+                best_t = tps[i];
+        }
+    }
     if (rc != CSC_OK) {
         h->opts = saved;
         h->plan_ok = false;
@@ -1089,6 +1121,7 @@ int csc_autotune(csc_handle_t h, double tol, int64_t max_updates, csc_tune_resul
     h->opts.segments = 0;
     h->opts.segment_width = best_w;
     h->opts.updates_per_visit = best_u;
+    h->opts.threads_per_segment = best_t;
     h->plan_ok = false;
     if (out) {
         out->segment_width = best_w;
@@ -1097,6 +1130,7 @@ int csc_autotune(csc_handle_t h, double tol, int64_t max_updates, csc_tune_resul
         out->candidates = ncand;
         out->best_ms = best_ms;
         out->default_ms = default_ms;
+        out->threads_per_segment = best_t ? best_t : kAutoThreadsPerSegment;
     }
     return CSC_OK;
 }

@@ -164,8 +164,11 @@ struct PhaseConfig {
     bool tile_in_smem;
 };
 
-// w_max: widest segment of the plan.
-PhaseConfig phase_config(int K, int L, int w_max);
+// w_max: widest segment of the plan; threads_per_segment: 32 = one warp per
+// segment where eligible (K = 25, 2L-1 <= 128, the tile fits shared memory),
+// otherwise (and for 0) a block of 128, 512 or 1024 threads.
+PhaseConfig phase_config(int K, int L, int w_max, int threads_per_segment);
+bool phase_warp_eligible(int K, int L, int w_max);
 // active = number of segments in pp.phase_list (the grid size).
 cudaError_t launch_phase(const PhaseParams &pp, const PhaseConfig &cfg, int active,
                          cudaStream_t s);

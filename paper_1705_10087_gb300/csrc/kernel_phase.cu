@@ -557,6 +557,278 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
     }
 }
 
+// One visit of segment m by one warp: the compile-time-K, shared-memory form
+// for update windows of at most 128 columns (2L-1 <= 127).  Lane l owns the
+// segment columns jj == l (mod 32) and handles, in an update, the window
+// positions whose column is one of its own (up to four of them), so the
+// argmax is a warp reduction, no barrier is needed between updates and the
+// coefficients of all the lane's positions are loaded in one round trip.
+// The arithmetic of an update is that of visit_segment (same coordinate
+// step, same order per column, same tie-break), so both forms apply the
+// same updates.
+template <int KT>
+__device__ __forceinline__ void visit_segment_warp(const PhaseParams &pp, const int m, const int g,
+                                                   const int g_round)
+{
+    static_assert(KT > 0 && KT <= 64, "compile-time K");
+    constexpr int KPC = (KT + 3) & ~3;
+    constexpr int CST = vec_stride(KT);
+    constexpr int KQ = (KT + 3) / 4;
+    constexpr int NPOS = 4;  // window positions per lane: 2L-1 <= 4 * 32
+    using Mask = typename std::conditional<(KT > 32), unsigned long long, unsigned>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+
+    // ---- early exits, decided by lane 0 and broadcast ----
+    int go = 1;
+    if (lane == 0) {
+        if (*(volatile int *)pp.done) {
+            go = 0;
+        } else if (*(volatile long long *)pp.total >= pp.max_updates) {
+            go = 0;
+        } else if (g - g_round >= pp.c) {
+            long long sum = 0;
+            for (int j = g - pp.c; j < g; j++)
+                sum += *(volatile long long *)&pp.upd[j & (kPhaseRing - 1)];
+            if (sum == 0) {
+                *(volatile int *)pp.done = g + 1;
+                go = 0;
+            }
+        }
+        if (go && !*(volatile unsigned char *)&pp.dirty[m])
+            go = 0;
+    }
+    if (!__shfl_sync(kFull, go, 0))
+        return;
+
+    const int K = KT, L = pp.L, W2 = 2 * L - 1, Kp = KPC;
+    const SigDesc *sdp = pp.sig + pp.seg_sig[m];
+    float *const gr = sdp->r;
+    float *const gz = sdp->Z;
+    const int64_t ld = sdp->ld, Tz = sdp->Tz;
+    const int seg_lo = sdp->seg0, seg_hi = sdp->seg0 + sdp->nseg;
+    const int64_t s = pp.seg_s[m], e = pp.seg_e[m];
+    const int w = (int)(e - s);
+    const float lam = sdp->lam, tol = sdp->tol;
+
+    const Layout lay(K, pp.w_max, true, true);
+    unsigned long long *ckey = reinterpret_cast<unsigned long long *>(smem_raw + lay.key);
+    float *cz = reinterpret_cast<float *>(smem_raw + lay.cz);
+    float *cd = reinterpret_cast<float *>(smem_raw + lay.cd);
+    int *ck = reinterpret_cast<int *>(smem_raw + lay.ck);
+    Mask *zmask = reinterpret_cast<Mask *>(smem_raw + lay.zm);
+    float *nrm = reinterpret_cast<float *>(smem_raw + lay.nrm);
+    float *rnrm = reinterpret_cast<float *>(smem_raw + lay.rnrm);
+    float *rs = reinterpret_cast<float *>(smem_raw + lay.r);
+    float *zs = reinterpret_cast<float *>(smem_raw + lay.z);
+    for (int k = lane; k < K; k += 32) {
+        nrm[k] = pp.norms[k];
+        rnrm[k] = __frcp_rn(pp.norms[k]);
+    }
+    __syncwarp();
+
+    // best coordinate of own column jj over the atoms whose bit is set in need
+    auto col_finish = [&](int jj, Mask need) {
+        float best = -1.f, bz = 0.f, bdz = 0.f;
+        int bk = 0;
+        const float *rc = rs + jj * CST;
+        const float *zc = zs + jj * CST;
+        for (Mask rest = need; rest; rest &= rest - 1) {
+            const int k = (sizeof(Mask) == 8 ? __ffsll((long long)rest) : __ffs((int)rest)) - 1;
+            float zn, d;
+            coord_step(rc[k], zc[k], nrm[k], rnrm[k], lam, &zn, &d);
+            const float ad = fabsf(d);
+            if (ad > best) {
+                best = ad;
+                bk = k;
+                bz = zn;
+                bdz = d;
+            }
+        }
+        const unsigned flat = (unsigned)bk * (unsigned)pp.w_max + (unsigned)jj;
+        ckey[jj] = best > 0.f ? ((unsigned long long)__float_as_uint(best) << 32) | (unsigned)(~flat)
+                              : 0ull;
+        cz[jj] = bz;
+        cd[jj] = bdz;
+        ck[jj] = bk;
+    };
+    // stage the lane's columns (one round trip of independent loads each)
+    for (int jj = lane; jj < w; jj += 32) {
+        Mask need = 0, zb = 0;
+#pragma unroll
+        for (int a = 0; a < 2; a++) {
+            const float *src = (a == 0 ? gr : gz) + s + jj;
+            float v[4 * KQ];
+#pragma unroll
+            for (int k = 0; k < 4 * KQ; k++)
+                v[k] = k < KT ? src[(int64_t)k * ld] : 0.f;
+            float4 *dst = reinterpret_cast<float4 *>((a == 0 ? rs : zs) + jj * CST);
+#pragma unroll
+            for (int q = 0; q < KQ; q++)
+                dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+#pragma unroll
+            for (int k = 0; k < KT; k++) {
+                if (a == 0)
+                    need |= (Mask)(fabsf(v[k]) > lam ? 1 : 0) << k;
+                else
+                    zb |= (Mask)(v[k] != 0.f ? 1 : 0) << k;
+            }
+        }
+        zmask[jj] = zb;
+        col_finish(jj, need | zb);
+    }
+    __syncwarp();
+
+    const float4 *Ct4 = reinterpret_cast<const float4 *>(pp.Ct);
+    int nupd = 0;
+    float decrease = 0.f;
+    int64_t tmin = Tz, tmax = -1;
+    bool capped = false;
+    for (int it = 0;; it++) {
+        // ---- warp argmax of the cached column keys ----------------------
+        unsigned long long my = 0ull;
+        int myj = 0;
+        for (int jj = lane; jj < w; jj += 32) {
+            const unsigned long long kk = ckey[jj];
+            if (kk > my) {
+                my = kk;
+                myj = jj;
+            }
+        }
+        const unsigned long long wm = warp_max_u64(my);
+        const float adz = __uint_as_float((unsigned)(wm >> 32));
+        if (!(adz >= tol))
+            break;
+        if (it >= pp.u) {
+            capped = true;
+            break;
+        }
+        const int src = __ffs(__ballot_sync(kFull, my == wm)) - 1;
+        // the winning column is one of lane src's own: it reads its cached step
+        float wz = 0.f, wd = 0.f;
+        int wk = 0;
+        if (lane == src) {
+            wz = cz[myj];
+            wd = cd[myj];
+            wk = ck[myj];
+        }
+        const int jw = __shfl_sync(kFull, myj, src);
+        const float znew = __shfl_sync(kFull, wz, src), delta = __shfl_sync(kFull, wd, src);
+        const int k0 = __shfl_sync(kFull, wk, src);
+        const int64_t t0 = s + jw;
+
+        // ---- Eq. beta_up (r form) on the window -------------------------
+        const int64_t tlo = t0 - (L - 1);
+        const int base = (lane - (int)((tlo - s) & 31)) & 31;
+        float cv[NPOS][KPC];
+#pragma unroll
+        for (int q = 0; q < NPOS; q++) {
+            const int off = base + 32 * q;
+            const int64_t t = tlo + off;
+            const bool valid = off < W2 && t >= 0 && t < Tz;
+            const int64_t cb = (int64_t)k0 * (Kp / 4) * W2 + (valid ? off : 0);
+#pragma unroll
+            for (int g4 = 0; g4 < KPC / 4; g4++) {
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (valid)
+                    v = __ldg(Ct4 + cb + (int64_t)g4 * W2);
+                cv[q][4 * g4] = v.x;
+                cv[q][4 * g4 + 1] = v.y;
+                cv[q][4 * g4 + 2] = v.z;
+                cv[q][4 * g4 + 3] = v.w;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NPOS; q++) {
+            const int off = base + 32 * q;
+            const int64_t t = tlo + off;
+            if (!(off < W2 && t >= 0 && t < Tz))
+                continue;
+            const int jj = (int)(t - s);
+            if (t >= s && t < e) {
+                float *rcol = rs + jj * CST;
+                if (t == t0) {
+                    const float n = nrm[k0], u = znew, z = znew - delta;
+                    decrease += delta * (rcol[k0] - 0.5f * n * delta) + lam * (fabsf(z) - fabsf(u));
+                    zs[jj * CST + k0] = znew;
+                    const Mask bit = (Mask)1 << k0;
+                    zmask[jj] = znew != 0.f ? (zmask[jj] | bit) : (zmask[jj] & ~bit);
+                }
+                Mask need = 0;
+                float4 *rc4 = reinterpret_cast<float4 *>(rcol);
+#pragma unroll
+                for (int g4 = 0; g4 < KQ; g4++) {
+                    float4 v = rc4[g4];
+                    v.x = fmaf(-cv[q][4 * g4], delta, v.x);
+                    v.y = fmaf(-cv[q][4 * g4 + 1], delta, v.y);
+                    v.z = fmaf(-cv[q][4 * g4 + 2], delta, v.z);
+                    v.w = fmaf(-cv[q][4 * g4 + 3], delta, v.w);
+                    rc4[g4] = v;
+                    const float rr[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int c = 0; c < 4; c++)
+                        if (4 * g4 + c < KT)
+                            need |= (Mask)(fabsf(rr[c]) > lam ? 1 : 0) << (4 * g4 + c);
+                }
+                col_finish(jj, need | zmask[jj]);
+            } else {
+                // an idle neighbour's column (no other block touches it)
+                float *rg = gr + t;
+#pragma unroll
+                for (int k = 0; k < KT; k++)
+                    atomicAdd(rg + (int64_t)k * ld, -cv[q][k] * delta);
+            }
+        }
+        __syncwarp();  // every lane's keys are updated before the next argmax
+        nupd++;
+        tmin = t0 < tmin ? t0 : tmin;
+        tmax = t0 > tmax ? t0 : tmax;
+    }
+
+    // ---- write back, spill bookkeeping, trace ---------------------------
+    if (nupd > 0) {
+        for (int jj = lane; jj < w; jj += 32) {
+            const float4 *rc4 = reinterpret_cast<const float4 *>(rs + jj * CST);
+            const float4 *zc4 = reinterpret_cast<const float4 *>(zs + jj * CST);
+#pragma unroll
+            for (int q = 0; q < KQ; q++) {
+                const float4 a = rc4[q], b = zc4[q];
+                const float ra[4] = {a.x, a.y, a.z, a.w}, za[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+                for (int c = 0; c < 4; c++)
+                    if (4 * q + c < KT) {
+                        gr[(int64_t)(4 * q + c) * ld + s + jj] = ra[c];
+                        gz[(int64_t)(4 * q + c) * ld + s + jj] = za[c];
+                    }
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        decrease += __shfl_xor_sync(kFull, decrease, o);
+    if (lane == 0) {
+        pp.dirty[m] = capped ? 1 : 0;
+        if (nupd > 0) {
+            const int64_t lo = tmin - (L - 1), hi = tmax + (L - 1);
+            for (int mm = m - 1; mm >= seg_lo && pp.seg_e[mm] > lo; mm--) {
+                pp.dirty[mm] = 1;
+                pp.touched[mm] = 1;
+            }
+            for (int mm = m + 1; mm < seg_hi && pp.seg_s[mm] <= hi; mm++) {
+                pp.dirty[mm] = 1;
+                pp.touched[mm] = 1;
+            }
+            pp.touched[m] = 1;
+            const int slot = g & (kPhaseRing - 1);
+            atomicAdd(reinterpret_cast<unsigned long long *>(&pp.upd[slot]),
+                      (unsigned long long)nupd);
+            atomicAdd(reinterpret_cast<unsigned long long *>(pp.total), (unsigned long long)nupd);
+            atomicAdd(reinterpret_cast<unsigned long long *>(pp.visits), 1ull);
+            atomicAdd(&pp.dec[slot], (double)decrease);
+            atomicMax(&pp.tend[slot], globaltimer_ns());
+        }
+    }
+}
+
 // Launch index and first index of the round: from the parameters, or, for
 // launches replayed from a CUDA graph, offsets from counters in device memory.
 __device__ __forceinline__ int launch_index(const PhaseParams &pp)
@@ -578,6 +850,39 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 5 : 1) phase_kernel(PhaseP
 {
     visit_segment<SMEM, MAXT, KT>(pp, pp.phase_list[blockIdx.x], launch_index(pp),
                                   round_index(pp));
+}
+
+// One warp (block) per segment of the phase list (K fixed, 2L-1 <= 127).
+template <int KT>
+__global__ void __launch_bounds__(32) phase_warp_kernel(PhaseParams pp)
+{
+    visit_segment_warp<KT>(pp, pp.phase_list[blockIdx.x], launch_index(pp), round_index(pp));
+}
+
+// The persistent form of the warp kernel (see phase_drain_kernel).
+template <int KT>
+__global__ void __launch_bounds__(32) phase_warp_drain_kernel(PhaseParams pp)
+{
+    const int n = *pp.qlen;
+    const int g = launch_index(pp), g_round = round_index(pp);
+    const int lane = threadIdx.x & 31;
+    if (blockIdx.x == 0 && lane == 0 && g - g_round >= pp.c && !*(volatile int *)pp.done) {
+        long long sum = 0;
+        for (int j = g - pp.c; j < g; j++)
+            sum += *(volatile long long *)&pp.upd[j & (kPhaseRing - 1)];
+        if (sum == 0)
+            *(volatile int *)pp.done = g + 1;
+    }
+    for (;;) {
+        int idx = 0;
+        if (lane == 0)
+            idx = atomicAdd(pp.qhead, 1);
+        idx = __shfl_sync(kFull, idx, 0);
+        if (idx >= n)
+            break;
+        visit_segment_warp<KT>(pp, pp.queue[idx], g, g_round);
+        __syncwarp();  // the next visit re-uses the shared memory
+    }
 }
 
 // Persistent form: a grid of resident blocks drains the queue of this phase's
@@ -660,9 +965,21 @@ cudaError_t launch_add_int(int *p, int v, cudaStream_t s)
     return cudaGetLastError();
 }
 
-PhaseConfig phase_config(int K, int L, int wmax)
+bool phase_warp_eligible(int K, int L, int wmax)
+{
+    return K == 25 && 2 * L - 1 <= 128 && Layout(K, wmax, true, true).total <= (size_t)kMaxSmem;
+}
+
+PhaseConfig phase_config(int K, int L, int wmax, int threads_per_segment)
 {
     PhaseConfig cfg;
+    if (threads_per_segment == 32 && phase_warp_eligible(K, L, wmax)) {
+        // one warp per segment (visit_segment_warp)
+        cfg.block = 32;
+        cfg.tile_in_smem = true;
+        cfg.smem = Layout(K, wmax, true, true).total;
+        return cfg;
+    }
     // An update touches the 2L-1 window columns: with at least that many threads
     // each of them goes to its own thread, however wide the segment; more threads
     // would idle in the update and only cost registers and occupancy.  The block
@@ -680,6 +997,9 @@ namespace {
 template <template <bool, int, int> class Sel, class F>
 cudaError_t dispatch(const PhaseConfig &cfg, int K, F &&f)
 {
+    // one warp per segment (phase_config checked K == 25 and the window)
+    if (cfg.block == 32)
+        return f(Sel<true, 32, 25>::fn());
     // the workloads' atom counts (25 and 64) are compiled with K fixed
     if (cfg.block == 128) {
         if (K == 25)
@@ -698,21 +1018,34 @@ cudaError_t dispatch(const PhaseConfig &cfg, int K, F &&f)
     return cfg.tile_in_smem ? f(Sel<true, 1024, 0>::fn()) : f(Sel<false, 1024, 0>::fn());
 }
 
+// (block 32 selects the warp forms; A is then always true and C == 25)
 template <bool A, int B, int C>
 struct PerSegment {
-    static auto fn() { return phase_kernel<A, B, C>; }
+    static auto fn()
+    {
+        if constexpr (B == 32)
+            return phase_warp_kernel<C>;
+        else
+            return phase_kernel<A, B, C>;
+    }
 };
 template <bool A, int B, int C>
 struct Drain {
-    static auto fn() { return phase_drain_kernel<A, B, C>; }
+    static auto fn()
+    {
+        if constexpr (B == 32)
+            return phase_warp_drain_kernel<C>;
+        else
+            return phase_drain_kernel<A, B, C>;
+    }
 };
 
 cudaError_t check(const PhaseParams &pp, const PhaseConfig &cfg)
 {
     if (cfg.smem > (size_t)kMaxSmem)
         return cudaErrorInvalidConfiguration;
-    if (cfg.block < 2 * pp.L - 1)
-        return cudaErrorInvalidConfiguration;  // each window column needs its own thread
+    if (cfg.block == 32 ? 2 * pp.L - 1 > 128 : cfg.block < 2 * pp.L - 1)
+        return cudaErrorInvalidConfiguration;  // window positions per thread: 1 (block), <= 4 (warp)
     return cudaSuccess;
 }
 

@@ -295,7 +295,8 @@ int csc_shard_phase(csc_handle_t h, int p, double tol)
     }
     if (cnt == 0)
         return CSC_OK;
-    const PhaseConfig cfg = phase_config(h->K, h->L, h->w_max);
+    const PhaseConfig cfg = phase_config(h->K, h->L, h->w_max,
+                                         h->opts.threads_per_segment == 32 ? 32 : 128);
     PhaseParams pp{};
     pp.sig = h->d_sig;
     pp.seg_sig = h->d_seg_sig;

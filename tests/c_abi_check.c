@@ -33,7 +33,7 @@ static void print_layouts(void)
            OFF(csc_opts, max_resyncs), OFF(csc_opts, sweeps_per_poll),
            OFF(csc_opts, max_sweeps), OFF(csc_opts, time_kernels),
            OFF(csc_opts, segment_width), OFF(csc_opts, init_mode), OFF(csc_opts, launch_mode),
-           OFF(csc_opts, reserved));
+           OFF(csc_opts, threads_per_segment));
     printf("csc_stats %u %u %u %u %u %u %u %u %u %u %u %u %u %u %u %u %u %u %u %u\n",
            (unsigned)sizeof(csc_stats), OFF(csc_stats, updates), OFF(csc_stats, sweeps),
            OFF(csc_stats, segments), OFF(csc_stats, phases), OFF(csc_stats, resyncs),
@@ -56,10 +56,11 @@ static void print_layouts(void)
            OFF(csc2d_stats, phases), OFF(csc2d_stats, resyncs), OFF(csc2d_stats, converged),
            OFF(csc2d_stats, objective), OFF(csc2d_stats, max_delta_z), OFF(csc2d_stats, solve_ms),
            OFF(csc2d_stats, kernel_launches));
-    printf("csc_tune_result %u %u %u %u %u %u %u\n", (unsigned)sizeof(csc_tune_result),
+    printf("csc_tune_result %u %u %u %u %u %u %u %u\n", (unsigned)sizeof(csc_tune_result),
            OFF(csc_tune_result, segment_width), OFF(csc_tune_result, updates_per_visit),
            OFF(csc_tune_result, phases), OFF(csc_tune_result, candidates),
-           OFF(csc_tune_result, best_ms), OFF(csc_tune_result, default_ms));
+           OFF(csc_tune_result, best_ms), OFF(csc_tune_result, default_ms),
+           OFF(csc_tune_result, threads_per_segment));
     printf("csc_server_opts %u %u %u %u %u %u\n", (unsigned)sizeof(csc_server_opts),
            OFF(csc_server_opts, hbm_budget_bytes), OFF(csc_server_opts, sweeps_per_step),
            OFF(csc_server_opts, max_resyncs), OFF(csc_server_opts, max_active),
@@ -91,7 +92,7 @@ int main(int argc, char **argv)
     memset(&o, 0x7f, sizeof o);
     csc_default_opts(&o);
     CHECK(o.segments == 0 && o.updates_per_visit == 0 && o.max_resyncs == -1);
-    CHECK(o.reserved[0] == 0);
+    CHECK(o.threads_per_segment == 0);
 
     /* Sec. 2.2 segments: [floor(m*Tz/M), floor((m+1)*Tz/M)) */
     CHECK(csc_plan(1985, 16, 10, &M, &c, starts) == CSC_OK);

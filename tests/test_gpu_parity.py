@@ -386,3 +386,39 @@ def test_status_after_the_last_resync_is_the_exact_check(capi):
     status2, E2, st2 = out[2]
     assert status2 == capi.CSC_OK and st2["converged"] == 1, st2
     assert E2 <= E * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("tps", [32, 128])
+@pytest.mark.parametrize("M,u", [(64, 0), (313, 24), (1000, 1)])
+def test_both_phase_kernel_forms_match_the_oracle(capi, long_small, M, u, tps):
+    """One warp per segment and a block per segment (csc_opts.threads_per_segment)
+    run the same coordinate steps: both meet the parity bars."""
+    pb, lam, ref, Er = long_small
+    opts = capi.make_opts(segments=M, updates_per_visit=u, threads_per_segment=tps)
+    h = capi.csc_setup(cuda(pb.D), opts)
+    try:
+        capi.csc_init(h, cuda(pb.X), lam)
+        Z = torch.zeros((pb.K, pb.Tz), dtype=torch.float32, device="cuda")
+        status, E, st = capi.csc_solve(h, LONG["tol"], 1 << 40, Z)
+    finally:
+        capi.csc_destroy(h)
+    assert status == 0, st
+    assert_parity(Z.cpu().numpy(), E, ref["Z"], Er)
+
+
+@pytest.mark.slow
+def test_warp_form_full_size_parity(capi, long_full):
+    pb, lam, ref, Er = long_full
+    r = gpu_solve(capi, pb, lam, LONG["tol"], M=1024, u=24)  # automatic form
+    assert r["status"] == 0
+    assert_parity(r["Z"], r["E"], ref["Z"], Er)
+    opts = capi.make_opts(segments=1024, updates_per_visit=24, threads_per_segment=128)
+    h = capi.csc_setup(cuda(pb.D), opts)
+    try:
+        capi.csc_init(h, cuda(pb.X), lam)
+        Z = torch.zeros((pb.K, pb.Tz), dtype=torch.float32, device="cuda")
+        status, E, st = capi.csc_solve(h, LONG["tol"], 1 << 40, Z)
+    finally:
+        capi.csc_destroy(h)
+    assert status == 0
+    assert_parity(Z.cpu().numpy(), E, ref["Z"], Er)
