@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--updates-per-visit", type=int, default=24)
     ap.add_argument("--no-sweep", action="store_true", help="skip the segment-count sweep")
     ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--threads-per-segment", type=int, default=0, choices=[0, 32, 128],
+                    help="phase kernel form: 0 automatic, 32 one warp per segment, 128 a block")
     ap.add_argument("--init-mode", type=int, default=0,
                     help="beta0 kernel: 0 automatic (tensor cores where their tile needs at "
                          "most half the shared memory, else FP32), 1 tensor cores (split BF16), "
@@ -64,6 +66,7 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the request-stream leg")
     ap.add_argument("--no-verylong", action="store_true",
                     help="skip the very long recording (T = 5e6) leg")
+    ap.add_argument("--no-image", action="store_true", help="skip the 2-D image leg")
     ap.add_argument("--serve-requests", type=int, default=400)
     return ap.parse_args()
 
@@ -262,10 +265,11 @@ def batch_leg(args, capi, torch):
         tune = capi.csc_autotune(ht, args.tol)
     finally:
         capi.csc_destroy(ht)
-    u, wseg = tune["updates_per_visit"], tune["segment_width"]
+    u, wseg, tps = tune["updates_per_visit"], tune["segment_width"], tune["threads_per_segment"]
 
     def batched(tol):
-        hb = capi.csc_setup(Dd, capi.make_opts(updates_per_visit=u, segment_width=wseg))
+        hb = capi.csc_setup(Dd, capi.make_opts(updates_per_visit=u, segment_width=wseg,
+                                               threads_per_segment=tps))
         try:
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -280,7 +284,8 @@ def batch_leg(args, capi, torch):
             capi.csc_destroy(hb)
 
     def plain(tol):
-        hp = capi.csc_setup(Dd, capi.make_opts(updates_per_visit=u, segment_width=wseg))
+        hp = capi.csc_setup(Dd, capi.make_opts(updates_per_visit=u, segment_width=wseg,
+                                               threads_per_segment=tps))
         try:
             Es = np.zeros(n)
             ups = 0
@@ -302,7 +307,8 @@ def batch_leg(args, capi, torch):
             capi.csc_destroy(hp)
 
     out = {"workload": BATCH, "signals": n, "samples": int(T.sum()), "P": 7, "K": K, "L": L,
-           "updates_per_visit": u, "segment_width": wseg, "autotune": tune, "gen_s": gen_s,
+           "updates_per_visit": u, "segment_width": wseg, "threads_per_segment": tps,
+           "autotune": tune, "gen_s": gen_s,
            "gap_target": 1e-4, "E_star": "FP64 oracle per signal (stored)"}
     grid = (1e-1, 3e-2, 1e-2, 3e-3, 1e-3, 3e-4, 1e-4, 1e-5, 1e-6)
     for name, fn in (("batched", batched), ("plain", plain)):
@@ -422,6 +428,48 @@ def verylong_leg(args, capi, torch):
             "beta0_roofline": {"bound": "hbm", "bytes": b0_bytes, "achieved_gbs": b0_gbs,
                                "peak_gbs": peak, "peak_kind": kind,
                                "frac": b0_gbs / peak if b0_gbs else None}}
+
+
+IMAGE = "image_P1_K8_h8_w8_512x512"
+
+
+def image_leg(args, capi, torch):
+    """The 2-D variant (images cut into row bands): one 512 x 512 gray image,
+    K = 8 atoms of 8 x 8, the Sec. 4 law; csc2d_solve to tol 1e-6 with automatic
+    bands (2h-2 rows each), timed with CUDA events around the call (setup, beta0,
+    band phases, resyncs, objective), against the 2-D oracle's E* stored by
+    tests/golden/make_golden.py --image2d."""
+    from paper_1705_10087_gb300 import synth
+    pb = synth.make_image_workload(IMAGE, seed=0)
+    try:
+        with open(GOLDEN) as f:
+            g = json.load(f).get(f"{IMAGE}/seed0")
+    except OSError:
+        g = None
+    if g is None or g.get("input_sha256_16") != input_hash(pb):
+        return {"workload": IMAGE, "unavailable": "no stored optimum for these inputs"}
+    w = synth.IMAGE_WORKLOADS[IMAGE]
+    stream = torch.cuda.current_stream()
+    D = torch.from_numpy(pb.D).cuda()
+    X = torch.from_numpy(pb.X).cuda()
+    Hz, Wz = w["H"] - w["h"] + 1, w["W"] - w["w"] + 1
+    Z = torch.zeros((w["K"], Hz, Wz), dtype=torch.float32, device="cuda")
+    runs = []
+    for i in range(4):  # the first run warms up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        status, E, st = capi.csc2d_solve(D, X, g["lambda"], w["tol"], Z_out=Z)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i > 0:
+            runs.append({"ms": e0.elapsed_time(e1), "solve_ms": st["solve_ms"], "status": status,
+                         "updates": st["updates"], "sweeps": st["sweeps"], "bands": st["bands"],
+                         "phases": st["phases"], "resyncs": st["resyncs"],
+                         "rel_gap_final": (E - g["E_star"]) / g["E_star"]})
+    best = min(runs, key=lambda r: r["ms"])
+    return {"workload": IMAGE, "K": w["K"], "P": w["P"], "h": w["h"], "w": w["w"],
+            "H": w["H"], "W": w["W"], "tol": w["tol"], "lambda": "0.1*lambda_max",
+            **best, "updates_per_s": best["updates"] / (best["ms"] * 1e-3)}
 
 
 def cpu_baseline(pb, lam, tol, M, u):
@@ -608,7 +656,8 @@ def main():
     X = torch.from_numpy(pb.X).cuda()
     Z = torch.zeros((pb.K, pb.Tz), dtype=torch.float32, device="cuda")
     opts = capi.make_opts(segments=args.segments, updates_per_visit=args.updates_per_visit,
-                          time_kernels=1, init_mode=args.init_mode)
+                          time_kernels=1, init_mode=args.init_mode,
+                          threads_per_segment=args.threads_per_segment)
     h = capi.csc_setup(D, opts)
     if g is not None:
         lam = g["lambda"]
@@ -695,7 +744,8 @@ def main():
     sweep = {}
     if world == 1 and not args.no_sweep:
         for M in (64, 256, 1024, 3072):
-            o = capi.make_opts(segments=M, updates_per_visit=args.updates_per_visit)
+            o = capi.make_opts(segments=M, updates_per_visit=args.updates_per_visit,
+                               threads_per_segment=args.threads_per_segment)
             best = None
             for _ in range(3):
                 capi.csc_setup(D, o, handle=h)
@@ -727,6 +777,7 @@ def main():
         "config": {"workload": WORKLOAD, "P": 7, "K": 25, "L": 64, "T": 200_000,
                    "segments": args.segments, "updates_per_visit": args.updates_per_visit,
                    "phases": sts[-1]["phases"], "tol": args.tol, "init_mode": args.init_mode,
+                   "threads_per_segment": args.threads_per_segment,
                    "lambda": "0.1*lambda_max", "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world}, one signal per GPU"},
         "time_to_gap_ms": ttg,
@@ -765,6 +816,8 @@ def main():
         line["segment_sweep"] = sweep
     if world == 1 and not args.no_verylong:
         line["verylong"] = verylong_leg(args, capi, torch)
+    if world == 1 and not args.no_image:
+        line["image2d"] = image_leg(args, capi, torch)
     if world == 1 and not args.no_batch:
         line["batch"] = batch_leg(args, capi, torch)
     if world == 1 and not args.no_serve:

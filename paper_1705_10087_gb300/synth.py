@@ -339,6 +339,20 @@ def serve_schedule(name: str, n: int, seed: int = 0, T_max: int | None = None) -
     return {"arrival": np.cumsum(gaps), "dict": dict_idx, "T": T, "offset_frac": frac}
 
 
+# Images for the 2-D variant (the paper has no image workload: the Sec. 4 law
+# on one gray image, atoms of 8 x 8 pixels).
+IMAGE_WORKLOADS = {
+    "image_P1_K8_h8_w8_512x512": dict(K=8, P=1, h=8, w=8, H=512, W=512, rho=0.005, sigma=0.1,
+                                      tol=1e-6),
+}
+
+
+def make_image_workload(name: str, seed: int = 0):
+    w = IMAGE_WORKLOADS[name]
+    return make_problem2d(K=w["K"], P=w["P"], h=w["h"], w=w["w"], H=w["H"], W=w["W"],
+                          rho=w["rho"], sigma=w["sigma"], seed=seed)
+
+
 def make_workload(name: str, seed: int = 0, T: int | None = None) -> Problem:
     """Problem for a named workload; T may be overridden for reduced-size cases."""
     w = WORKLOADS[name]

@@ -9,6 +9,7 @@ the generator no longer reproduces them.
     python tests/golden/make_golden.py            # all single-signal entries
     python tests/golden/make_golden.py --batch    # the 512-signal batch (8 processes)
     python tests/golden/make_golden.py --verylong # the T = 5e6 recording, with Z*
+    python tests/golden/make_golden.py --image2d  # the 512 x 512 image (2-D oracle)
 
 The very long recording's entry (about 7 minutes of oracle time) also stores
 the oracle's sparse Z* (verylong_seed0_zstar.npz: flat indices k * Tz + t of
@@ -136,9 +137,37 @@ def main_verylong():
     print(name, seed, res[f"{name}/seed{seed}"], f"{time.time() - t:.1f}s", flush=True)
 
 
+IMAGE = ("image_P1_K8_h8_w8_512x512", 0)
+
+
+def main_image2d():
+    from oracle import csc2d
+    name, seed = IMAGE
+    t = time.time()
+    pb = synth.make_image_workload(name, seed=seed)
+    lmax = csc2d.lambda_max(pb.D, pb.X)
+    lam = 0.1 * lmax
+    Hz = pb.X.shape[1] - pb.D.shape[2] + 1
+    M = max(1, Hz // (2 * pb.D.shape[2] - 2))
+    r = csc2d.locally_greedy_cd(pb.D, pb.X, lam, 1e-10, M=M, mode="phase")
+    assert r["converged"]
+    E = csc2d.objective(pb.D, pb.X, r["Z"], lam)
+    with open(OUT) as f:
+        res = json.load(f)
+    res[f"{name}/seed{seed}"] = {
+        "lambda": lam, "lambda_max": lmax, "E_star": E, "eps": 1e-10,
+        "oracle": f"band phase schedule, M={M}", "updates": r["n_updates"],
+        "nnz": int(np.count_nonzero(r["Z"])), "input_sha256_16": input_hash(pb)}
+    with open(OUT, "w") as f:
+        json.dump(res, f, indent=1, sort_keys=True)
+    print(name, seed, res[f"{name}/seed{seed}"], f"{time.time() - t:.1f}s", flush=True)
+
+
 def main():
     if "--batch" in sys.argv[1:]:
         return main_batch()
+    if "--image2d" in sys.argv[1:]:
+        return main_image2d()
     if "--verylong" in sys.argv[1:]:
         return main_verylong()
     res = {}
@@ -158,7 +187,8 @@ def main():
     try:
         with open(OUT) as f:
             old = json.load(f)
-        res.update({k: v for k, v in old.items() if k.startswith(VERYLONG[0])})
+        res.update({k: v for k, v in old.items()
+                    if k.startswith(VERYLONG[0]) or k.startswith(IMAGE[0])})
     except (OSError, ValueError):
         pass
     with open(OUT, "w") as f:
