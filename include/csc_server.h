@@ -82,9 +82,11 @@ int csc_server_create(csc_server_t *s, const csc_server_opts *opts);
 
 /*
  * Adds a resident dictionary D [K][P][L] (host or device; copied) and
- * returns its index.  segment_width (>= 2L-2, 0 = 2L-2) and
- * updates_per_visit (0 = 24) apply to all its requests; widths below 2L-2
- * are rejected so that every request runs in the same 2 phases.
+ * returns its index.  segment_width (>= 1, 0 = 2L-2) and updates_per_visit
+ * (0 = 24) apply to all its requests; every request of the dictionary runs in
+ * the same c = 1 + ceil((2L-2) / segment_width) phases (2 at the default
+ * width; narrower segments take less shared memory each, so more of them run
+ * at once).  CSC_EINVAL if sweeps_per_step x c exceeds 4096 launches.
  */
 int csc_server_add_dictionary(csc_server_t s, const float *D, int K, int P, int L,
                               int32_t segment_width, int32_t updates_per_visit, int *dict);

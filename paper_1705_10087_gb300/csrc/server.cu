@@ -57,6 +57,9 @@ namespace {
     } while (0)
 
 constexpr int kRed = 8;  // resync reduction slots per request
+// threads per segment of the phase launches: a block (the faster form, see
+// kAutoThreadsPerSegment in capi.cu)
+constexpr int kServerThreadsPerSegment = 128;
 
 double now_s()
 {
@@ -143,7 +146,8 @@ struct Group {
     std::vector<SigDesc> sigs;
     std::vector<int64_t> seg_s, seg_e;
     std::vector<int> seg_sig, list;
-    int phase_off[3] = {0, 0, 0};
+    int c = 2;                    // phases of the group's schedule
+    std::vector<int> phase_off;   // [c+1] into the phase list
     int M = 0, w_max = 1;
     size_t held = 0;  // pool bytes of its admitted, not yet fetched requests
     SigDesc *d_sig = nullptr, *d_sub = nullptr;
@@ -304,7 +308,9 @@ int finish_admit(csc_server_t s, Group &g)
     return CSC_OK;
 }
 
-// Stage 2: segments of every active request, two phases.
+// Stage 2: segments of every active request and the phase lists: c phases,
+// c = 1 + ceil((2L-2) / w) for segments of at least w columns (two for the
+// default width 2L-2).
 int rebuild(csc_server_t s, Group &g)
 {
     if (!g.stale)
@@ -344,14 +350,18 @@ int rebuild(csc_server_t s, Group &g)
     g.w_max = 1;
     for (int m = 0; m < g.M; m++)
         g.w_max = std::max<int>(g.w_max, (int)(g.seg_e[m] - g.seg_s[m]));
+    g.c = 1 + (int)((2 * (int64_t)g.L - 2 + g.w - 1) / g.w);
     g.list.clear();
-    for (int p = 0; p < 2; p++) {
+    g.phase_off.assign(g.c + 1, 0);
+    int most = 0;
+    for (int p = 0; p < g.c; p++) {
         g.phase_off[p] = (int)g.list.size();
         for (int m = 0; m < g.M; m++)
-            if (local[m] % 2 == p)
+            if (local[m] % g.c == p)
                 g.list.push_back(m);
+        most = std::max(most, (int)g.list.size() - g.phase_off[p]);
     }
-    g.phase_off[2] = (int)g.list.size();
+    g.phase_off[g.c] = (int)g.list.size();
     if (n == 0)
         return CSC_OK;
     SRV_CUDA(upload(&g.d_sig, &g.cap_sig, g.sigs, g.st));
@@ -361,8 +371,7 @@ int rebuild(csc_server_t s, Group &g)
     SRV_CUDA(upload(&g.d_list, &g.cap_list, g.list, g.st));
     SRV_CUDA(grow(&g.dirty, &g.cap_dirty, (size_t)g.M));
     SRV_CUDA(grow(&g.touched, &g.cap_touched, (size_t)g.M));
-    SRV_CUDA(grow(&g.d_queue, &g.cap_queue,
-                  (size_t)std::max(g.phase_off[1] - g.phase_off[0], g.phase_off[2] - g.phase_off[1])));
+    SRV_CUDA(grow(&g.d_queue, &g.cap_queue, (size_t)std::max(most, 1)));
     SRV_CUDA(grow(&g.d_cnt, &g.cap_cnt, (size_t)n));
     SRV_CUDA(grow(&g.d_red, &g.cap_red, (size_t)n * kRed));
     SRV_CUDA(grow(&g.d_E, &g.cap_E, (size_t)n));
@@ -372,15 +381,15 @@ int rebuild(csc_server_t s, Group &g)
     return CSC_OK;
 }
 
-// Stage 3: S sweeps of the two phases over the group's active requests.
+// Stage 3: S sweeps of the c phases over the group's active requests.
 int run_sweeps(csc_server_t s, Group &g)
 {
     const int n = (int)g.active.size();
     if (n == 0)
         return CSC_OK;
     const int S = s->opts.sweeps_per_step > 0 ? s->opts.sweeps_per_step : 4;
-    const int c = 2;
-    const PhaseConfig cfg = phase_config(g.K, g.L, g.w_max);
+    const int c = g.c;
+    const PhaseConfig cfg = phase_config(g.K, g.L, g.w_max, kServerThreadsPerSegment);
     SRV_CUDA(cudaMemsetAsync(g.ps, 0, sizeof(PhaseScratch), g.st));
     PhaseParams pp{};
     pp.sig = g.d_sig;
@@ -695,10 +704,20 @@ int csc_server_add_dictionary(csc_server_t s, const float *D, int K, int P, int 
         return csc_record_error(CSC_EINVAL, "csc_server_add_dictionary: bad sizes %d,%d,%d", K,
                                 P, L);
     const int wmin = std::max(1, 2 * L - 2);
-    if (segment_width != 0 && segment_width < wmin)
-        return csc_record_error(CSC_EINVAL,
-                                "csc_server_add_dictionary: segment_width must be >= 2L-2 = %d",
-                                wmin);
+    if (segment_width < 0)
+        return csc_record_error(CSC_EINVAL, "csc_server_add_dictionary: segment_width < 0");
+    {
+        // launches of one scheduling step (S sweeps of c phases) index the
+        // group's per-launch counters
+        const int w = segment_width ? segment_width : wmin;
+        const int S = s->opts.sweeps_per_step > 0 ? s->opts.sweeps_per_step : 4;
+        const int64_t c = 1 + (2 * (int64_t)L - 2 + w - 1) / w;
+        if (S * c > kMaxLaunches)
+            return csc_record_error(CSC_EINVAL,
+                                    "csc_server_add_dictionary: %lld phases x %d sweeps per step "
+                                    "exceed %d launches",
+                                    (long long)c, S, kMaxLaunches);
+    }
     if (updates_per_visit < 0)
         return csc_record_error(CSC_EINVAL, "csc_server_add_dictionary: updates_per_visit < 0");
     csc::DeviceGuard dev_guard_(s->device);

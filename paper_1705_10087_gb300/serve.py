@@ -26,7 +26,7 @@ WORKLOAD = "serve_4dict_poisson200_T5000_2000000"
 def run_stream(capi, torch, n_requests: int, seed: int = 0, rate: float | None = None,
                name: str = WORKLOAD, sources=None, T_max: int | None = None,
                budget_bytes: int | None = None, sweeps_per_step: int = 0,
-               keep_Z: bool = False, workers: int = 0) -> dict:
+               keep_Z: bool = False, workers: int = 0, segment_widths=None) -> dict:
     w = synth.SERVE_WORKLOADS[name]
     sch = synth.serve_schedule(name, n_requests, seed=seed, T_max=T_max)
     if rate is not None:
@@ -38,7 +38,9 @@ def run_stream(capi, torch, n_requests: int, seed: int = 0, rate: float | None =
     srv = capi.csc_server_create(hbm_budget_bytes=budget, sweeps_per_step=sweeps_per_step)
     out = {"requests": n_requests, "seed": seed, "budget_bytes": budget}
     try:
-        dicts = [capi.csc_server_add_dictionary(srv, pb.D) for pb in sources]
+        widths = list(segment_widths) if segment_widths is not None else [0] * len(sources)
+        dicts = [capi.csc_server_add_dictionary(srv, pb.D, segment_width=int(wd))
+                 for pb, wd in zip(sources, widths)]
         zmax = max(pb.K * (int(sch["T"].max()) - pb.L + 1) for pb in sources)
         zbuf = torch.empty(zmax, dtype=torch.float32).pin_memory()
         # request windows, cut before the clock starts

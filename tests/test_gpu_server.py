@@ -58,14 +58,18 @@ def fetch(capi, srv, rid, K, Tz):
     return Z, info
 
 
-@pytest.mark.parametrize("j", [0, 1, 2, 3])
-def test_server_requests_match_oracle(capi, j):
+@pytest.mark.parametrize("j,narrow", [(0, False), (1, False), (2, False), (3, False),
+                                      (1, True), (3, True)])
+def test_server_requests_match_oracle(capi, j, narrow):
     # each resident dictionary of the stream (K, L, P) with short requests,
-    # including T = L (one column) and T < 2L - 2 (one segment)
+    # including T = L (one column) and T < 2L - 2 (one segment); narrow: the
+    # dictionary's segments are L-1 wide, so its requests run in 3 phases
     Ds = dictionaries()
     srv = capi.csc_server_create(hbm_budget_bytes=1 << 30)
     try:
-        dicts = [capi.csc_server_add_dictionary(srv, D) for D in Ds]
+        dicts = [capi.csc_server_add_dictionary(
+            srv, D, segment_width=(D.shape[2] - 1 if narrow and i == j else 0))
+            for i, D in enumerate(Ds)]
         D = Ds[j]
         K, P, L = D.shape
         # (K, L, P) = (64, 128, 1) has strongly coupled atoms: the oracle needs

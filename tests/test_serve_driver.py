@@ -37,7 +37,7 @@ class FakeServer:
 
     def __init__(self, rounds=3):
         self.rounds = rounds
-        self.dicts, self.reqs, self.queue = [], {}, []
+        self.dicts, self.widths, self.reqs, self.queue = [], [], {}, []
         self.submitted, self.fetched = [], []
         self.next_id, self.launches, self.destroyed = 1, 0, False
         self.t_first_count = None  # the driver reads the counter just before its clock starts
@@ -46,8 +46,10 @@ class FakeServer:
         assert hbm_budget_bytes > 0
         return "srv"
 
-    def csc_server_add_dictionary(self, srv, D):
+    def csc_server_add_dictionary(self, srv, D, segment_width=0):
+        assert segment_width >= 0
         self.dicts.append(D.shape)
+        self.widths.append(segment_width)
         return len(self.dicts) - 1
 
     def csc_server_submit(self, srv, d, X, lam, tol):
@@ -127,3 +129,13 @@ def test_stream_driver_submits_on_time_and_fetches_each_request_once():
     assert out["steps"] == out["gpu_launches"] == fake.launches
     assert (out["pool_peak_bytes"], out["pool_bytes"]) == (123, 456)
     assert out["throughput_req_s"] == pytest.approx(n / out["wall_s"])
+    assert fake.widths == [0] * len(fake.dicts)              # the server's own widths
+
+
+def test_stream_driver_passes_each_dictionary_its_segment_width():
+    src = sources(1200)
+    widths = [0, 63, 0, 7][:len(src)]
+    fake = FakeServer(rounds=1)
+    serve.run_stream(fake, FakeTorch, 4, seed=1, rate=2000.0, sources=src, T_max=600,
+                     segment_widths=widths)
+    assert fake.widths == widths
