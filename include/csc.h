@@ -160,6 +160,12 @@ int csc_setup(csc_handle_t *h, const float *D, int K, int P, int L, const csc_op
  *           K*(T-L+1) < 2^32 - 1 (flat coordinate indices are 32-bit)
  *   lambda  > 0, absolute (not scaled)
  *   Z0      NULL (cold start) or [K][T-L+1] float32 warm start
+ * The call does not wait for its kernels (X and Z0 may be reused once it
+ * returns): lambda_max, the beta0 kernel's time and its status are read back
+ * by the first call that needs them (csc_lambda_max, csc_lambda_max_batch,
+ * csc_init_time, csc_solve, csc_objective, csc_kkt, csc_get_beta,
+ * csc_autotune), which returns CSC_ETIMEOUT if the tensor-core kernel's
+ * bounded wait gave up (the handle then needs a new csc_init).
  */
 int csc_init(csc_handle_t h, const float *X, int64_t T, double lambda, const float *Z0);
 

@@ -124,7 +124,7 @@ int build_plan(csc_handle_t h)
             h->sigs[i].seg0 = h->plan_seg0[i];
             h->sigs[i].nseg = h->plan_nseg[i];
         }
-        CSC_CUDA(upload(&h->d_sig, &h->cap_sig, h->sigs, s));
+        CSC_CUDA(push_sigs(h, s));
         h->plan_ok = true;
         return CSC_OK;
     }
@@ -171,7 +171,7 @@ int build_plan(csc_handle_t h)
     CSC_CUDA(upload(&h->d_seg_s, &h->cap_seg_s, seg_s, s));
     CSC_CUDA(upload(&h->d_seg_e, &h->cap_seg_e, seg_e, s));
     CSC_CUDA(upload(&h->d_seg_sig, &h->cap_seg_sig, seg_sig, s));
-    CSC_CUDA(upload(&h->d_sig, &h->cap_sig, h->sigs, s));
+    CSC_CUDA(push_sigs(h, s));
     CSC_CUDA(upload(&h->d_phase_list, &h->cap_phase, list, s));
     CSC_CUDA(grow(&h->dirty, &h->cap_dirty, (size_t)M));
     CSC_CUDA(grow(&h->touched, &h->cap_touched, (size_t)M));
@@ -314,7 +314,7 @@ int batch_graph(csc_handle_t h, const PhaseParams &pp, const PhaseConfig &cfg, i
     return CSC_OK;
 }
 
-int set_lambdas(csc_handle_t h, const double *lambda)
+int set_lambdas(csc_handle_t h, const double *lambda, bool push)
 {
     for (int i = 0; i < h->n; i++)
         if (!(lambda[i] > 0.0) || !std::isfinite(lambda[i]))
@@ -324,12 +324,38 @@ int set_lambdas(csc_handle_t h, const double *lambda)
         h->sigs[i].lam = (float)h->lam[i];
         h->sigs[i].lam_d = h->lam[i];
     }
-    // (a copy from pageable memory has read the host array when it returns)
-    CSC_CUDA(upload(&h->d_sig, &h->cap_sig, h->sigs, h->stream));
+    if (push)
+        CSC_CUDA(push_sigs(h, h->stream));
     return CSC_OK;
 }
 
 }  // namespace
+
+// Completes csc_init's asynchronous read-back: lambda_max per signal, the
+// beta0 kernel's time and its give-up flag (an error surfaces here).
+int finish_init(csc_handle_t h)
+{
+    if (!h->init_pending)
+        return CSC_OK;
+    CSC_CUDA(cudaEventSynchronize(h->ev_init));
+    h->init_pending = false;
+    if (h->init_pin[0]) {
+        h->initialized = false;
+        return fail(CSC_ETIMEOUT, "csc_init: the tensor-core beta0 kernel gave up waiting");
+    }
+    for (int i = 0; i < h->n; i++) {
+        float v;
+        std::memcpy(&v, &h->init_pin[1 + i], sizeof v);
+        h->lmax[i] = v;
+    }
+    h->init_ms = -1.0;
+    if (h->opts.time_kernels) {
+        float ms = 0.f;
+        CSC_CUDA(cudaEventElapsedTime(&ms, h->ev_i0, h->ev_i1));
+        h->init_ms = ms;
+    }
+    return CSC_OK;
+}
 
 extern "C" {
 
@@ -384,6 +410,12 @@ int csc_destroy(csc_handle_t h)
         cudaFree(p);
     if (h->poll)
         cudaFreeHost(h->poll);
+    if (h->init_pin)
+        cudaFreeHost(h->init_pin);
+    if (h->ev_init)
+        cudaEventDestroy(h->ev_init);
+    if (h->ev_copy)
+        cudaEventDestroy(h->ev_copy);
     if (h->ev0)
         cudaEventDestroy(h->ev0);
     if (h->ev1)
@@ -469,10 +501,15 @@ int csc_setup(csc_handle_t *hp, const float *D, int K, int P, int L, const csc_o
             CSC_CUDA(cudaEventCreate(&h->ev0));
         if (!h->ev1)
             CSC_CUDA(cudaEventCreate(&h->ev1));
+        if (!h->ev_copy)
+            CSC_CUDA(cudaEventCreateWithFlags(&h->ev_copy, cudaEventDisableTiming));
         CSC_CUDA(copy_in(h->D, D, sizeof(float) * K * P * L, h->stream));
+        CSC_CUDA(cudaEventRecord(h->ev_copy, h->stream));
         CSC_CUDA(launch_dtd(h->D, K, P, L, h->C, h->norms, h->stream));
         CSC_CUDA(launch_coef_by_lag(h->C, K, L, h->Ct, h->stream));
         h->launches += 2;
+        // D may be reused once this returns; the kernels run on
+        CSC_CUDA(cudaEventSynchronize(h->ev_copy));
         return CSC_OK;
     };
     int rc = body();
@@ -504,6 +541,11 @@ int csc_init_batch(csc_handle_t h, const float *X, const int64_t *T, int n, cons
         return fail(CSC_EINVAL, "csc_init: T - L + 1 must be below 2^31 - 1 columns");
     h->shard.on = false;  // csc_shard_init sets it again after this
     CSC_ON_DEVICE(h->device);
+    if (h->init_pending) {
+        // superseded by this call; its read-back buffer is about to be reused
+        CSC_CUDA(cudaEventSynchronize(h->ev_init));
+        h->init_pending = false;
+    }
     h->initialized = false;
     h->plan_ok = false;
     cudaStream_t s = h->stream;
@@ -518,8 +560,15 @@ int csc_init_batch(csc_handle_t h, const float *X, const int64_t *T, int n, cons
     CSC_CUDA(grow(&h->r, &h->cap_r, nz));
     CSC_CUDA(grow(&h->beta0, &h->cap_beta0, nz));
     CSC_CUDA(grow(&h->Z, &h->cap_Z, nz));
-    // descriptors into the concatenation and the tiles over each signal
+    // descriptors into the concatenation and the tiles over each signal (the
+    // stopping threshold of the previous solve is kept: unchanged descriptors
+    // are not uploaded again)
+    std::vector<float> tol_prev;
+    for (const SigDesc &d : h->sigs)
+        tol_prev.push_back(d.tol);
     h->sigs.assign(n, SigDesc{});
+    for (int i = 0; i < n && i < (int)tol_prev.size(); i++)
+        h->sigs[i].tol = tol_prev[i];
     std::vector<int64_t> tile_s, rtile_s;
     std::vector<int> tile_sig, rtile_sig;
     h->tile_off.assign(n + 1, 0);
@@ -562,11 +611,24 @@ int csc_init_batch(csc_handle_t h, const float *X, const int64_t *T, int n, cons
     CSC_CUDA(grow(&h->nz_count, &h->cap_nz_count, (size_t)h->nrtiles));
     CSC_CUDA(grow(&h->nz_ent, &h->cap_nz_ent, (size_t)h->nrtiles * kNzCap));
     {
-        int rc = set_lambdas(h, lambda);  // uploads the descriptors; waits for the uploads
+        int rc = set_lambdas(h, lambda, n > 1 || Z0 != nullptr);  // (only those need d_sig here)
         if (rc != CSC_OK)
             return rc;
     }
+    if (h->cap_init_pin < (size_t)n + 1) {
+        if (h->init_pin)
+            cudaFreeHost(h->init_pin);
+        h->init_pin = nullptr;
+        h->cap_init_pin = 0;
+        CSC_CUDA(cudaHostAlloc(&h->init_pin, sizeof(unsigned) * (n + 1), cudaHostAllocDefault));
+        h->cap_init_pin = (size_t)n + 1;
+    }
+    if (!h->ev_init)
+        CSC_CUDA(cudaEventCreateWithFlags(&h->ev_init, cudaEventDisableTiming));
+    if (!h->ev_copy)
+        CSC_CUDA(cudaEventCreateWithFlags(&h->ev_copy, cudaEventDisableTiming));
     CSC_CUDA(copy_in(h->X, X, sizeof(float) * h->P * Ttot, s));
+    CSC_CUDA(cudaEventRecord(h->ev_copy, s));  // the caller's X has been read
     CSC_CUDA(cudaMemsetAsync(&h->sc->lmax_bits, 0, sizeof(unsigned), s));
     CSC_CUDA(cudaMemsetAsync(&h->sc->x2, 0, sizeof(double), s));
     CSC_CUDA(cudaMemsetAsync(&h->sc->tc_err, 0, sizeof(int), s));
@@ -594,6 +656,7 @@ int csc_init_batch(csc_handle_t h, const float *X, const int64_t *T, int n, cons
     if (Z0) {
         h->launches += 2;  // bucket lists + resync
         CSC_CUDA(copy_in(h->Z, Z0, sizeof(float) * nz, s));
+        CSC_CUDA(cudaEventRecord(h->ev_copy, s));
         // the columns between signals belong to no problem: 0
         for (int i = 0; i + 1 < n; i++)
             CSC_CUDA(cudaMemset2DAsync(h->Z + h->a[i + 1] - h->L + 1, sizeof(float) * Tz, 0,
@@ -604,25 +667,16 @@ int csc_init_batch(csc_handle_t h, const float *X, const int64_t *T, int n, cons
     } else {
         CSC_CUDA(cudaMemsetAsync(h->Z, 0, sizeof(float) * nz, s));
     }
-    std::vector<unsigned> bits(n);
-    int tc_err = 0;
-    CSC_CUDA(cudaMemcpyAsync(bits.data(), n > 1 ? h->d_lmax : &h->sc->lmax_bits,
+    // read back without waiting (finish_init completes it): the stream goes
+    // on to the solve while beta0 is computed
+    CSC_CUDA(cudaMemcpyAsync(h->init_pin + 1, n > 1 ? h->d_lmax : &h->sc->lmax_bits,
                              sizeof(unsigned) * n, cudaMemcpyDeviceToHost, s));
-    CSC_CUDA(cudaMemcpyAsync(&tc_err, &h->sc->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CSC_CUDA(cudaStreamSynchronize(s));
-    if (tc_err)
-        return fail(CSC_ETIMEOUT, "csc_init: the tensor-core beta0 kernel gave up waiting");
-    for (int i = 0; i < n; i++) {
-        float v;
-        std::memcpy(&v, &bits[i], sizeof v);
-        h->lmax[i] = v;
-    }
-    h->init_ms = -1.0;
-    if (timed) {
-        float ms = 0.f;
-        CSC_CUDA(cudaEventElapsedTime(&ms, h->ev_i0, h->ev_i1));
-        h->init_ms = ms;
-    }
+    CSC_CUDA(cudaMemcpyAsync(h->init_pin, &h->sc->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CSC_CUDA(cudaEventRecord(h->ev_init, s));
+    h->init_pending = true;
+    // the inputs may be reused once this returns (a copy from pinned host
+    // memory is asynchronous): wait for the copies, not for the kernels
+    CSC_CUDA(cudaEventSynchronize(h->ev_copy));
     h->z_is_zero = Z0 == nullptr;
     h->initialized = true;
     return CSC_OK;
@@ -640,7 +694,7 @@ int csc_set_lambda(csc_handle_t h, const double *lambda)
     if (!h->initialized)
         return fail(CSC_ESTATE, "csc_set_lambda: call csc_init first");
     CSC_ON_DEVICE(h->device);
-    return set_lambdas(h, lambda);
+    return set_lambdas(h, lambda, true);
 }
 
 int csc_lambda_max(csc_handle_t h, double *out)
@@ -649,6 +703,9 @@ int csc_lambda_max(csc_handle_t h, double *out)
         return fail(CSC_EINVAL, "csc_lambda_max: null argument");
     if (!h->initialized)
         return fail(CSC_ESTATE, "csc_lambda_max: call csc_init first");
+    CSC_ON_DEVICE(h->device);
+    if (int rc = finish_init(h))
+        return rc;
     *out = *std::max_element(h->lmax.begin(), h->lmax.end());
     return CSC_OK;
 }
@@ -659,6 +716,9 @@ int csc_lambda_max_batch(csc_handle_t h, double *out)
         return fail(CSC_EINVAL, "csc_lambda_max_batch: null argument");
     if (!h->initialized)
         return fail(CSC_ESTATE, "csc_lambda_max_batch: call csc_init first");
+    CSC_ON_DEVICE(h->device);
+    if (int rc = finish_init(h))
+        return rc;
     std::copy(h->lmax.begin(), h->lmax.end(), out);
     return CSC_OK;
 }
@@ -780,7 +840,7 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
     const float tol_inner = (float)(max_resyncs > 0 ? 0.5 * tol : tol);
     for (SigDesc &d : h->sigs)
         d.tol = tol_inner;
-    CSC_CUDA(upload(&h->d_sig, &h->cap_sig, h->sigs, s));
+    CSC_CUDA(push_sigs(h, s));
     pp.w_max = h->w_max;
 
     int status = CSC_OK;
@@ -859,6 +919,8 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
             CSC_CUDA(cudaMemcpyAsync(h->poll, &sc->total, sizeof(long long) + sizeof(int),
                                      cudaMemcpyDeviceToHost, s));
             CSC_CUDA(cudaStreamSynchronize(s));
+            if (int rc = finish_init(h))  // (beta0 came before this poll in the stream)
+                return rc;
             if (timed) {
                 const int pairs = graphed ? 1 : nb;
                 for (int i = 0; i < pairs; i++) {
@@ -1023,6 +1085,8 @@ int csc_autotune(csc_handle_t h, double tol, int64_t max_updates, csc_tune_resul
     if (!(tol > 0.0) || max_updates < 1)
         return fail(CSC_EINVAL, "csc_autotune: need tol > 0 and max_updates >= 1");
     CSC_ON_DEVICE(h->device);
+    if (int rc = finish_init(h))
+        return rc;
     cudaStream_t s = h->stream;
     const size_t nz = (size_t)h->K * h->Tz;
     // the starting point every candidate solves from
@@ -1162,6 +1226,9 @@ int csc_init_time(csc_handle_t h, double *beta0_ms)
         return fail(CSC_EINVAL, "csc_init_time: null argument");
     if (!h->initialized)
         return fail(CSC_ESTATE, "csc_init_time: call csc_init first");
+    CSC_ON_DEVICE(h->device);
+    if (int rc = finish_init(h))
+        return rc;
     *beta0_ms = h->init_ms;
     return CSC_OK;
 }
@@ -1181,6 +1248,8 @@ int csc_get_beta(csc_handle_t h, float *beta_out)
     if (!h->initialized)
         return fail(CSC_ESTATE, "csc_get_beta: call csc_init first");
     CSC_ON_DEVICE(h->device);
+    if (int rc = finish_init(h))
+        return rc;
     const size_t nz = (size_t)h->K * h->Tz;
     // beta = r + ||D_k||^2 Z (the kernels keep r)
     if (is_device_pointer(beta_out)) {
@@ -1217,6 +1286,8 @@ int csc_objective(csc_handle_t h, const float *Z, double *out)
     if (!h->initialized)
         return fail(CSC_ESTATE, "csc_objective: call csc_init first");
     CSC_ON_DEVICE(h->device);
+    if (int rc = finish_init(h))
+        return rc;
     cudaStream_t s = h->stream;
     const size_t nz = (size_t)h->K * h->Tz;
     const float *Zd = Z;
@@ -1236,6 +1307,8 @@ int csc_kkt(csc_handle_t h, const float *Z, double *out)
     if (!h->initialized)
         return fail(CSC_ESTATE, "csc_kkt: call csc_init first");
     CSC_ON_DEVICE(h->device);
+    if (int rc = finish_init(h))
+        return rc;
     cudaStream_t s = h->stream;
     const size_t nz = (size_t)h->K * h->Tz;
     const float *Zd = Z;

@@ -7,9 +7,11 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 #include <vector>
 
 #include "csc_internal.cuh"
+#include "host_util.cuh"
 
 namespace csc {
 
@@ -85,6 +87,7 @@ struct csc_handle_s {
     std::vector<double> lmax;       // [n]
     std::vector<double> E_sig;      // [n] objectives of the last solve / csc_objective
     std::vector<SigDesc> sigs;      // [n] descriptors of the signals
+    std::vector<SigDesc> sigs_dev;  // what d_sig holds (see push_sigs)
     SigDesc *d_sig = nullptr;
     size_t cap_sig = 0;
     SigDesc *d_sig_alt = nullptr;   // [n] the same over a caller's Z (csc_kkt)
@@ -141,6 +144,14 @@ struct csc_handle_s {
     cudaEvent_t ev_i0 = nullptr, ev_i1 = nullptr;  // around the beta0 kernel (time_kernels)
     cudaEvent_t ev_r0 = nullptr, ev_r1 = nullptr;  // around a resync / the objective
     double init_ms = -1.0;
+    // csc_init's results, copied back without waiting: init_pin[0] = the
+    // tensor-core kernel's give-up flag, init_pin[1 + i] = max |beta0| bits of
+    // signal i (pinned; complete once ev_init has completed)
+    unsigned *init_pin = nullptr;
+    size_t cap_init_pin = 0;
+    cudaEvent_t ev_init = nullptr;
+    cudaEvent_t ev_copy = nullptr;  // after csc_init's copies of the caller's arrays
+    bool init_pending = false;
     cudaEvent_t *kev = nullptr;  // per-launch timing events (2 per launch of a poll batch)
     int n_kev = 0;
     int64_t launches = 0;        // kernels launched through this handle
@@ -154,3 +165,24 @@ struct csc_handle_s {
     Tiles resync_tiles() const { return Tiles{d_rtile_sig, d_rtile_s, nrtiles}; }
 };
 
+// Completes csc_init's asynchronous read-back (capi.cu): lambda_max per
+// signal, the beta0 kernel's time and its give-up flag; CSC_ETIMEOUT if the
+// tensor-core kernel gave up.  Every call that reads them calls it first.
+int finish_init(csc_handle_s *h);
+
+// d_sig <- h->sigs, skipped when the device copy already holds exactly these
+// descriptors: a copy from pageable memory waits for the stream, and repeated
+// solves of the same signals would otherwise stall the queue at every call.
+static_assert(sizeof(csc::SigDesc) == 80, "SigDesc has no padding (compared bytewise)");
+inline cudaError_t push_sigs(csc_handle_s *h, cudaStream_t s)
+{
+    if (h->d_sig && h->sigs_dev.size() == h->sigs.size() &&
+        std::memcmp(h->sigs_dev.data(), h->sigs.data(), sizeof(csc::SigDesc) * h->sigs.size()) == 0)
+        return cudaSuccess;
+    const cudaError_t e = csc::upload(&h->d_sig, &h->cap_sig, h->sigs, s);
+    if (e == cudaSuccess)
+        h->sigs_dev = h->sigs;
+    else
+        h->sigs_dev.clear();
+    return e;
+}

@@ -14,6 +14,7 @@ namespace csc {
 namespace {
 
 constexpr int kChunk = 64;  // Z columns scanned per compaction round
+constexpr int kBucketBatch = 8;  // atom rows of Z a warp loads at once when listing nonzeros
 
 struct NZ {
     int k;
@@ -89,6 +90,38 @@ __device__ __forceinline__ void df_add_prod(float &hi, float &lo, float a, float
     lo = __fadd_rn(lo, __fadd_rn(se, pe));
 }
 
+// (hi, lo) += a, a float (TwoSum; the rounding error is carried in lo)
+__device__ __forceinline__ void df_add(float &hi, float &lo, float a)
+{
+    const float s = __fadd_rn(hi, a);
+    const float bv = __fsub_rn(s, hi);
+    const float se = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(a, bv));
+    hi = s;
+    lo = __fadd_rn(lo, se);
+}
+
+// (hi, lo) += (bh, bl), both double-float
+__device__ __forceinline__ void df_add_df(float &hi, float &lo, float bh, float bl)
+{
+    df_add(hi, lo, bh);
+    lo = __fadd_rn(lo, bl);
+}
+
+// (sh, sl) += (x - (ah + al))^2 in double-float: the residual with TwoSum,
+// its square as rh^2 (exact error by fma) + 2 rh rl (rl^2 is below the
+// pair's precision)
+__device__ __forceinline__ void df_add_sq_residual(float &sh, float &sl, float x, float ah,
+                                                   float al)
+{
+    float rh = x, rl = 0.f;
+    df_add(rh, rl, -ah);
+    df_add(rh, rl, -al);
+    const float p = __fmul_rn(rh, rh);
+    const float q = __fmaf_rn(__fmul_rn(2.f, rh), rl, __fmaf_rn(rh, rh, -p));
+    df_add(sh, sl, p);
+    sl = __fadd_rn(sl, q);
+}
+
 constexpr int kResyncThreads = 256;
 constexpr int kResyncGroups = kResyncThreads / kResyncCols;  // atom groups
 constexpr int kListMax = 32 * kChunk;  // nonzeros a tile gathers from the lists at once
@@ -131,15 +164,24 @@ __global__ void __launch_bounds__(256)
     const bool in = t < sd.Tz;
     uint2 *__restrict__ out = lists.ent + b * kNzCap;
     int base = 0;
-    for (int k = 0; k < K; k++) {
-        const float z = in ? sd.Z[(int64_t)k * sd.ld + t] : 0.f;
-        const unsigned m = __ballot_sync(0xffffffffu, z != 0.f);
-        if (z != 0.f) {
-            const int pos = base + __popc(m & ((1u << lane) - 1u));
-            if (pos < kNzCap)
-                out[pos] = make_uint2((unsigned)(k * kResyncCols + lane), __float_as_uint(z));
+    for (int k0 = 0; k0 < K; k0 += kBucketBatch) {
+        // kBucketBatch rows loaded together: one memory round trip
+        float zv[kBucketBatch];
+#pragma unroll
+        for (int q = 0; q < kBucketBatch; q++)
+            zv[q] = in && k0 + q < K ? sd.Z[(int64_t)(k0 + q) * sd.ld + t] : 0.f;
+#pragma unroll
+        for (int q = 0; q < kBucketBatch; q++) {
+            const float z = zv[q];
+            const unsigned m = __ballot_sync(0xffffffffu, z != 0.f);
+            if (z != 0.f) {
+                const int pos = base + __popc(m & ((1u << lane) - 1u));
+                if (pos < kNzCap)
+                    out[pos] = make_uint2((unsigned)((k0 + q) * kResyncCols + lane),
+                                          __float_as_uint(z));
+            }
+            base += __popc(m);
         }
-        base += __popc(m);
     }
     if (lane == 0)
         lists.count[b] = base;
@@ -351,34 +393,97 @@ __global__ void __launch_bounds__(kResyncThreads)
     }
 }
 
-constexpr int kObjP = 8;  // channels accumulated per pass
+constexpr int kObjP = 8;    // channels accumulated per pass
+constexpr int kObjCap = 64;  // nonzeros of one 32-column bucket held in shared memory
+constexpr int kObjBuckets = kTile / 32 + (kMaxL - 1 + 31) / 32;
+
+// acc[q] += D[q L] z for the channels q < np of a pass (double-float)
+__device__ __forceinline__ void obj_add(float (&hi)[kObjP], float (&lo)[kObjP],
+                                        const float *__restrict__ Dk, int np, int L, float z)
+{
+#pragma unroll
+    for (int q = 0; q < kObjP; q++)
+        if (q < np)
+            df_add_prod(hi[q], lo[q], __ldg(Dk + q * L), z);
+}
 
 // Tile b (kTile samples of one problem): partials[2b] = sum over its samples of
 // sum_p R[p][t]^2 with R = X - sum_k Z_k * D_k ((Z*D)[t] = sum_tau Z[t-tau] D[tau],
 // Sec. 2), partials[2b+1] = sum of |Z| over its columns.  Without tables
 // (sigs == NULL) the problem is `one` and tile b starts at b * kTile.
-__global__ void __launch_bounds__(kTile)
+//
+// The Z columns that reach the tile, [c0 - 32 R, c0 + kTile) with R =
+// ceil((L-1)/32), are listed first in buckets of 32 columns (one warp per
+// bucket, a ballot per atom row: entries in (k, column) order).  Warp w's
+// samples [c0 + 32 w, c0 + 32 w + 32) are reached only by the columns of
+// buckets w .. w + R, so each thread walks R + 1 buckets.  A bucket with more
+// than kObjCap nonzeros is walked straight from Z in the same order.
+__global__ void __launch_bounds__(kTile, 5)
     objective_kernel(const float *__restrict__ D, const SigDesc *__restrict__ sigs, SigDesc one,
                      Tiles tiles, int K, int P, int L, const float *Zbase, const float *Zalt,
                      double *__restrict__ partials)
 {
-    __shared__ NZ list[32 * kChunk];
-    __shared__ int warp_counts[32];
+    __shared__ uint2 ent[kObjBuckets][kObjCap];
+    __shared__ int cnt[kObjBuckets];
     __shared__ double bsum[2][kTile / 32];
     const SigDesc sd = sigs ? sigs[tiles.sig[blockIdx.x]] : one;
     const float *Z = Zalt ? Zalt + (sd.Z - Zbase) : sd.Z;
     const int64_t Tz = sd.Tz, ld = sd.ld, T = Tz + L - 1;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t c0 = sigs ? tiles.start[blockIdx.x] : (int64_t)blockIdx.x * kTile;
     int64_t c1 = c0 + kTile < T ? c0 + kTile : T;
     if (sigs && tiles.end && tiles.end[blockIdx.x] < c1)
         c1 = tiles.end[blockIdx.x];
     const int64_t t = c0 + tid;
-    double sq = 0.0, l1 = 0.0;
-    // Z columns that reach samples [c0, c1): [c0-(L-1), c1) within [0,Tz)
-    const int64_t lo = c0 - (L - 1) > 0 ? c0 - (L - 1) : 0;
-    const int64_t hi = c1 < Tz ? c1 : Tz;
-    const int chunk = (32 * kChunk) / K < kChunk ? (32 * kChunk) / K : kChunk;
+    // Z columns that reach samples below c1 are below c1
+    const int64_t zhi = c1 < Tz ? c1 : Tz;
+    const int R = (L - 1 + 31) / 32;
+    const int64_t cb0 = c0 - 32 * (int64_t)R;  // bucket j: columns [cb0 + 32 j, cb0 + 32 j + 32)
+    const int nb = kTile / 32 + R;
+    for (int j = warp; j < nb; j += kTile / 32) {
+        const int64_t col = cb0 + 32 * (int64_t)j + lane;
+        const bool in = col >= 0 && col < zhi;
+        int base = 0;
+        for (int k0 = 0; k0 < K; k0 += kBucketBatch) {
+            // kBucketBatch rows loaded together: one memory round trip
+            float zv[kBucketBatch];
+#pragma unroll
+            for (int q = 0; q < kBucketBatch; q++)
+                zv[q] = in && k0 + q < K ? Z[(int64_t)(k0 + q) * ld + col] : 0.f;
+#pragma unroll
+            for (int q = 0; q < kBucketBatch; q++) {
+                const float z = zv[q];
+                const unsigned m = __ballot_sync(0xffffffffu, z != 0.f);
+                if (z != 0.f) {
+                    const int pos = base + __popc(m & ((1u << lane) - 1u));
+                    if (pos < kObjCap)
+                        ent[j][pos] = make_uint2((unsigned)((k0 + q) * 32 + lane), __float_as_uint(z));
+                }
+                base += __popc(m);
+            }
+        }
+        if (lane == 0)
+            cnt[j] = base;
+    }
+    __syncthreads();
+
+    // per thread: sum of squared residuals and of |Z| in double-float (the
+    // FP64 pipe is narrow: only the per-warp totals are taken to FP64)
+    float sq_h = 0.f, sq_l = 0.f, l1_h = 0.f, l1_l = 0.f;
+    // |Z| of the tile's own columns [c0 + 32 w, ...) (bucket R + w), once each
+    {
+        const int j = R + warp;
+        const int n = cnt[j];
+        if (n <= kObjCap) {
+            for (int i = lane; i < n; i += 32)
+                df_add(l1_h, l1_l, fabsf(__uint_as_float(ent[j][i].y)));
+        } else {
+            const int64_t col = cb0 + 32 * (int64_t)j + lane;
+            if (col >= 0 && col < zhi)
+                for (int k = 0; k < K; k++)
+                    df_add(l1_h, l1_l, fabsf(Z[(int64_t)k * ld + col]));
+        }
+    }
     for (int p0 = 0; p0 < P; p0 += kObjP) {
         float acc_hi[kObjP], acc_lo[kObjP];
 #pragma unroll
@@ -386,43 +491,49 @@ __global__ void __launch_bounds__(kTile)
             acc_hi[q] = 0.f;
             acc_lo[q] = 0.f;
         }
-        for (int64_t a = lo; a < hi; a += chunk) {
-            const int64_t b = a + chunk < hi ? a + chunk : hi;
-            const int n = compact_nonzeros(Z, K, ld, a, b, list, warp_counts);
-            if (t < c1) {
-                for (int i = 0; i < n; i++) {
-                    const NZ e = list[i];
-                    const int tau = (int)(t - e.t);
-                    if (tau < 0 || tau >= L)
-                        continue;
-                    if (tau == 0 && p0 == 0)
-                        l1 += fabs((double)e.z);  // each nonzero once, by the thread t = t'
-                    const float *Dk = D + (int64_t)e.k * P * L + tau;
-#pragma unroll
-                    for (int q = 0; q < kObjP; q++)
-                        if (p0 + q < P)
-                            df_add_prod(acc_hi[q], acc_lo[q], __ldg(Dk + (int64_t)(p0 + q) * L), e.z);
+        if (t < c1) {
+            for (int j = warp; j <= warp + R; j++) {
+                const int n = cnt[j];
+                const int64_t cbj = cb0 + 32 * (int64_t)j;
+                if (n <= kObjCap) {
+                    for (int i = 0; i < n; i++) {
+                        const uint2 v = ent[j][i];
+                        const int tau = (int)(t - (cbj + (v.x & 31u)));
+                        if (tau >= 0 && tau < L)
+                            obj_add(acc_hi, acc_lo, D + ((int)(v.x >> 5) * P + p0) * L + tau,
+                                    P - p0, L, __uint_as_float(v.y));
+                    }
+                } else {
+                    for (int k = 0; k < K; k++)
+                        for (int jj = 0; jj < 32; jj++) {
+                            const int64_t tp = cbj + jj;
+                            const int tau = (int)(t - tp);
+                            if (tp < 0 || tp >= zhi || tau < 0 || tau >= L)
+                                continue;
+                            const float z = Z[(int64_t)k * ld + tp];
+                            if (z != 0.f)
+                                obj_add(acc_hi, acc_lo, D + (k * P + p0) * L + tau, P - p0, L, z);
+                        }
                 }
             }
-            __syncthreads();
-        }
-        if (t < c1) {
 #pragma unroll
             for (int q = 0; q < kObjP; q++)
-                if (p0 + q < P) {
-                    const double r = (double)sd.X[(int64_t)(p0 + q) * sd.ldx + t] -
-                                     ((double)acc_hi[q] + (double)acc_lo[q]);
-                    sq += r * r;
-                }
+                if (p0 + q < P)
+                    df_add_sq_residual(sq_h, sq_l, sd.X[(int64_t)(p0 + q) * sd.ldx + t], acc_hi[q],
+                                       acc_lo[q]);
         }
     }
     for (int off = 16; off > 0; off >>= 1) {
-        sq += __shfl_xor_sync(0xffffffffu, sq, off);
-        l1 += __shfl_xor_sync(0xffffffffu, l1, off);
+        const float a = __shfl_xor_sync(0xffffffffu, sq_h, off);
+        const float b = __shfl_xor_sync(0xffffffffu, sq_l, off);
+        const float c = __shfl_xor_sync(0xffffffffu, l1_h, off);
+        const float e = __shfl_xor_sync(0xffffffffu, l1_l, off);
+        df_add_df(sq_h, sq_l, a, b);
+        df_add_df(l1_h, l1_l, c, e);
     }
-    if ((tid & 31) == 0) {
-        bsum[0][tid >> 5] = sq;
-        bsum[1][tid >> 5] = l1;
+    if (lane == 0) {
+        bsum[0][warp] = (double)sq_h + (double)sq_l;
+        bsum[1][warp] = (double)l1_h + (double)l1_l;
     }
     __syncthreads();
     if (tid == 0) {

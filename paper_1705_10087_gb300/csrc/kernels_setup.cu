@@ -12,34 +12,45 @@ namespace csc {
 namespace {
 
 // DtD[k0][k][s] = sum_p sum_tau D[k][p][tau] * D[k0][p][tau + s - (L-1)]
-// = S_{k,k0}[s-(L-1)] of Eq. beta_up (Sec. 2.1).  One thread per entry.
+// = S_{k,k0}[s-(L-1)] of Eq. beta_up (Sec. 2.1).  One block per pair (k0, k),
+// one thread per lag; with STAGE the two atoms are first copied to shared
+// memory (every thread of the block reads all of both).
+template <bool STAGE>
 __global__ void dtd_kernel(const float *__restrict__ D, int K, int P, int L,
                            float *__restrict__ C, float *__restrict__ norms)
 {
+    extern __shared__ float dsm[];  // STAGE: [2][P][L], atom k then atom k0
     const int W2 = 2 * L - 1;
-    const long long n = (long long)K * K * W2;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int s = (int)(idx % W2);
-        const int k = (int)((idx / W2) % K);
-        const int k0 = (int)(idx / ((long long)W2 * K));
+    const int k0 = blockIdx.x / K, k = blockIdx.x % K;
+    const int PL = P * L;
+    const float *da = D + (long long)k * PL, *db = D + (long long)k0 * PL;
+    if (STAGE) {
+        for (int i = threadIdx.x; i < PL; i += blockDim.x) {
+            dsm[i] = __ldg(da + i);
+            dsm[PL + i] = __ldg(db + i);
+        }
+        __syncthreads();
+        da = dsm;
+        db = dsm + PL;
+    }
+    for (int s = threadIdx.x; s < W2; s += blockDim.x) {
         const int lag = s - (L - 1);
         const int tlo = lag < 0 ? -lag : 0;
         const int thi = lag > 0 ? L - lag : L;
         KahanF acc;
         for (int p = 0; p < P; p++) {
-            const float *a = D + ((long long)k * P + p) * L;
-            const float *b = D + ((long long)k0 * P + p) * L + lag;
+            const float *a = da + p * L;
+            const float *b = db + p * L + lag;
             for (int t8 = tlo; t8 < thi; t8 += 8) {
                 float part = 0.f;
                 const int te = min(t8 + 8, thi);
                 for (int t = t8; t < te; t++)
-                    part = fmaf(__ldg(a + t), __ldg(b + t), part);
+                    part = fmaf(a[t], b[t], part);
                 acc.add(part);
             }
         }
         const float v = acc.value();
-        C[idx] = v;
+        C[((long long)k0 * K + k) * W2 + s] = v;
         if (k == k0 && lag == 0)
             norms[k] = v;
     }
@@ -179,11 +190,13 @@ __global__ void stamp_kernel(unsigned long long *out)
 cudaError_t launch_dtd(const float *D, int K, int P, int L, float *C, float *norms,
                        cudaStream_t s)
 {
-    const long long n = (long long)K * K * (2 * L - 1);
-    const int block = 256;
-    const long long grid = (n + block - 1) / block;
-    dtd_kernel<<<(unsigned)(grid < 65535 * 32 ? grid : 65535 * 32), block, 0, s>>>(D, K, P, L, C,
-                                                                                   norms);
+    const int W2 = 2 * L - 1;
+    const int block = W2 <= 128 ? 128 : (W2 <= 256 ? 256 : 512);
+    const size_t smem = 2 * sizeof(float) * (size_t)P * L;
+    if (smem <= 48 * 1024)
+        dtd_kernel<true><<<(unsigned)(K * K), block, smem, s>>>(D, K, P, L, C, norms);
+    else
+        dtd_kernel<false><<<(unsigned)(K * K), block, 0, s>>>(D, K, P, L, C, norms);
     return cudaGetLastError();
 }
 

@@ -223,7 +223,7 @@ int csc_shard_init(csc_handle_t h, const csc_shard_plan *plan, const float *X, d
     SH_CUDA(cudaMemsetAsync(h->touched, 1, (size_t)sh.seg_count, s));
     h->sigs[0].seg0 = 0;
     h->sigs[0].nseg = sh.seg_count;
-    SH_CUDA(upload(&h->d_sig, &h->cap_sig, h->sigs, s));
+    SH_CUDA(push_sigs(h, s));
     // resync tiles over the owned columns, objective tiles over the owned
     // samples (the last shard also owns the samples [Tz, T) of the signal)
     std::vector<int> rt_sig, ot_sig;
@@ -282,7 +282,7 @@ int csc_shard_phase(csc_handle_t h, int p, double tol)
     ShardState &sh = h->shard;
     if (h->sigs[0].tol != (float)tol) {
         h->sigs[0].tol = (float)tol;
-        SH_CUDA(upload(&h->d_sig, &h->cap_sig, h->sigs, s));
+        SH_CUDA(push_sigs(h, s));
         SH_CUDA(cudaStreamSynchronize(s));
     }
     const int cnt = h->phase_off[p + 1] - h->phase_off[p];
@@ -473,6 +473,8 @@ int csc_shard_resync(csc_handle_t h, double tol, double *max_dz)
     unsigned long long red[8];
     SH_CUDA(cudaMemcpyAsync(red, h->sc->red, sizeof red, cudaMemcpyDeviceToHost, s));
     SH_CUDA(cudaStreamSynchronize(s));
+    if (int rc = finish_init(h))  // (beta0 came before this resync in the stream)
+        return rc;
     double v[5];
     std::memcpy(v, red, sizeof v);
     max_dz[0] = v[4];

@@ -181,7 +181,14 @@ def test_server_argument_errors(capi):
     srv = capi.csc_server_create(hbm_budget_bytes=1 << 20)
     try:
         with pytest.raises(capi.CscError):
-            capi.csc_server_add_dictionary(srv, D, segment_width=10)   # < 2L - 2
+            capi.csc_server_add_dictionary(srv, D, segment_width=-1)   # negative width
+        s2 = capi.csc_server_create(hbm_budget_bytes=1 << 20, sweeps_per_step=200)
+        try:
+            with pytest.raises(capi.CscError):                         # 200 sweeps x 31 phases
+                capi.csc_server_add_dictionary(s2, D, segment_width=1)
+            capi.csc_server_add_dictionary(s2, D, segment_width=15)    # 200 x 3 launches
+        finally:
+            capi.csc_server_destroy(s2)
         d = capi.csc_server_add_dictionary(srv, D)
         X = np.ones((1, 100), np.float32)
         with pytest.raises(capi.CscError):
