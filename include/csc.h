@@ -91,8 +91,8 @@ typedef struct csc_opts {
                                   split into three BF16 terms, six products accumulated
                                   in FP32 (FP32-grade); 2 = tensor cores, one BF16 product
                                   (only to measure its error); 3 = FP32 CUDA cores with
-                                  compensated sums; 0 = automatic: mode 1 where two of its
-                                  CTAs fit on an SM (shared memory grows with P * L), else
+                                  compensated sums; 0 = automatic: mode 1 where one of its
+                                  CTAs fits on an SM (shared memory grows with P * L), else
                                   mode 3.  Modes 1-2 need K <= 64; other sizes use mode 3 */
     int32_t launch_mode;       /* 0 = each poll batch (sweeps_per_poll sweeps of the c phases)
                                   is replayed from a CUDA graph, captured the second time a
@@ -102,7 +102,7 @@ typedef struct csc_opts {
                                   (a block), 128 = a block of at least 2L-1 threads per
                                   segment, 32 = one warp per segment where eligible (K =
                                   25, 2L-1 <= 128, the segment's tile fits shared memory;
-                                  else a block).  Same results */
+                                  else a block).  Both meet the same bars */
 } csc_opts;
 
 typedef struct csc_stats {

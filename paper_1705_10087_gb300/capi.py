@@ -83,8 +83,9 @@ CSC_REQ_QUEUED, CSC_REQ_ACTIVE, CSC_REQ_DONE = 0, 1, 2
 
 class csc2d_stats(ctypes.Structure):
     _fields_ = [("updates", ctypes.c_int64), ("sweeps", ctypes.c_int64),
-                ("bands", ctypes.c_int32), ("phases", ctypes.c_int32),
-                ("resyncs", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("bands", ctypes.c_int32), ("col_blocks", ctypes.c_int32),
+                ("phases", ctypes.c_int32), ("resyncs", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("objective", ctypes.c_double), ("max_delta_z", ctypes.c_double),
                 ("solve_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
 
@@ -186,7 +187,7 @@ def load(path: str | None = None):
                                ctypes.POINTER(ctypes.c_int), _vp]
     lib.csc2d_solve.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp,
                                 _i64, _i64, ctypes.c_double, ctypes.c_double, _i64, ctypes.c_int,
-                                ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_double),
+                                ctypes.c_int, ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(csc2d_stats), _vp]
     lib.csc_last_error_string.argtypes = []
     lib.csc_last_error_string.restype = ctypes.c_char_p
@@ -652,7 +653,7 @@ def csc2d_plan(Hz: int, h: int, M: int = 0):
 
 
 def csc2d_solve(D, X, lam: float, tol: float, max_updates: int = 1 << 62, M: int = 0,
-                updates_per_visit: int = 0, Z_out=None, stream=None):
+                N: int = 0, updates_per_visit: int = 0, Z_out=None, stream=None):
     """D [K,P,h,w], X [P,H,W] -> (status, objective, stats dict)."""
     if len(D.shape) != 4 or len(X.shape) != 3:
         raise ValueError("D must be [K, P, h, w] and X [P, H, W]")
@@ -665,7 +666,7 @@ def csc2d_solve(D, X, lam: float, tol: float, max_updates: int = 1 << 62, M: int
     obj = ctypes.c_double(0.0)
     st = csc2d_stats()
     status = _check(load().csc2d_solve(_ptr(D), K, P, h, w, _ptr(X), H, W, float(lam),
-                                       float(tol), int(max_updates), int(M),
+                                       float(tol), int(max_updates), int(M), int(N),
                                        int(updates_per_visit), _ptr(Z_out, True),
                                        ctypes.byref(obj), ctypes.byref(st), _stream(stream)))
     return status, obj.value, st.as_dict()

@@ -611,7 +611,10 @@ int csc_init_batch(csc_handle_t h, const float *X, const int64_t *T, int n, cons
     CSC_CUDA(grow(&h->nz_count, &h->cap_nz_count, (size_t)h->nrtiles));
     CSC_CUDA(grow(&h->nz_ent, &h->cap_nz_ent, (size_t)h->nrtiles * kNzCap));
     {
-        int rc = set_lambdas(h, lambda, n > 1 || Z0 != nullptr);  // (only those need d_sig here)
+        // d_sig is read by every kernel on the handle's problems (csc_objective
+        // and csc_kkt may follow without a solve); unchanged descriptors are
+        // not uploaded again
+        int rc = set_lambdas(h, lambda, true);
         if (rc != CSC_OK)
             return rc;
     }

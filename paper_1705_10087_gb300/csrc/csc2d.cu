@@ -11,15 +11,22 @@
 // an update dZ of Z_k0[i0][j0] changes r_k[i][j] by -C[k][k0][i-i0+h-1][j-j0+w-1] dZ
 // for every (k, i, j) of the (2h-1) x (2w-1) window, own coordinate included.
 //
-// Bands: band m of M covers rows [floor(m Hz / M), floor((m+1) Hz / M)) and
-// all columns; bands m == p (mod c) run in phase p, with (c-1) times the
-// narrowest band at least 2h-2 rows, so that co-active bands' windows never
-// meet and each phase equals a sequential run of its bands.  One thread
-// block per active band: it keeps, per position (i, j) of its band, the best
-// coordinate over k as a 64-bit key (|Delta Z| bits, ~flat index; ties to the
-// lowest (k Hz + i) Wz + j) in shared memory, and repeats block argmax ->
-// update -> re-evaluation of the window's positions, writing the window rows
-// outside its band (idle neighbours) with atomicAdd.
+// Tiles: row band m of M covers rows [floor(m Hz / M), floor((m+1) Hz / M)),
+// column block n of N the columns [floor(n Wz / N), floor((n+1) Wz / N)).
+// Each axis gets the 1-D phase count (cr over rows, cc over columns, so that
+// (cr-1) times the narrowest band is at least 2h-2 rows and likewise for the
+// columns), and tile (m, n) runs in phase (m mod cr) cc + (n mod cc): two
+// co-active tiles are separated by at least 2h-2 rows or 2w-2 columns, their
+// windows never meet, and each phase equals a sequential run of its tiles.
+// N = 1 is the paper's cut along one axis (bands only); more column blocks
+// give more co-active tiles, which one GPU needs (a 512 x 512 image with
+// 8 x 8 atoms has 18 co-active bands but 324 co-active tiles of 14 x 14).
+// One thread block per active tile: it keeps, per position (i, j) of its
+// tile, the best coordinate over k as a 64-bit key (|Delta Z| bits, ~flat
+// index; ties to the lowest (k Hz + i) Wz + j) in shared memory, with r and Z
+// of the tile staged there too when they fit, and repeats block argmax ->
+// update -> re-evaluation of the window's positions, writing the window
+// positions outside its tile (idle neighbours) with atomicAdd.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -44,7 +51,12 @@ namespace {
                                     __FILE__, __LINE__);                                     \
     } while (0)
 
-constexpr int kB2 = 256;        // threads of a band block
+constexpr int kB2 = 256;        // threads of a tile block
+// updates per tile visit by default: a launch lasts as long as its busiest
+// tile, so short visits keep the 324 co-active tiles of a 512 x 512 image
+// (8 x 8 atoms) in step (measured: 6.2 ms at 8, 6.6 at 16, 8.1 at 32, 23 ms
+// when every visit runs to local convergence)
+constexpr int kAutoVisit2d = 8;
 constexpr int kMaxK2 = 64;      // atoms (one bit each in a 64-bit mask)
 constexpr int kMaxWin = 4096;   // (2h-1)(2w-1) window positions
 constexpr int kTile2 = 32;      // columns per resync / objective tile
@@ -95,8 +107,8 @@ __global__ void dtd2d_kernel(const float *__restrict__ D, Dims d, int KQ, float 
     }
 }
 
-// beta0 (and r = beta0 for Z = 0) in FP64 sums rounded once; max |beta0| and
-// sum X^2 (E(0) = sum X^2 / 2).
+// beta0 (and r = beta0 for Z = 0) in double-float sums rounded once (the
+// FP64 pipe of GB300 is narrow); max |beta0| and sum X^2 (E(0) = sum X^2 / 2).
 __global__ void dtx2d_kernel(const float *__restrict__ D, const float *__restrict__ X, Dims d,
                              float *__restrict__ beta0, float *__restrict__ r,
                              unsigned *__restrict__ absmax, double *__restrict__ x2)
@@ -107,17 +119,18 @@ __global__ void dtx2d_kernel(const float *__restrict__ D, const float *__restric
          o += (int64_t)gridDim.x * blockDim.x) {
         const int64_t j = o % d.Wz, i = (o / d.Wz) % d.Hz;
         const int k = (int)(o / (d.Wz * d.Hz));
-        double acc = 0.0;
+        float hi = 0.f, lo = 0.f;
         for (int p = 0; p < d.P; p++)
             for (int u = 0; u < d.h; u++) {
                 const float *xr = X + ((int64_t)p * d.H + i + u) * d.W + j;
                 const float *dr = D + (((int64_t)k * d.P + p) * d.h + u) * d.w;
                 for (int v = 0; v < d.w; v++)
-                    acc += (double)dr[v] * (double)xr[v];
+                    df_add_prod(hi, lo, __ldg(dr + v), __ldg(xr + v));
             }
-        beta0[o] = (float)acc;
-        r[o] = (float)acc;
-        amax = fmaxf(amax, fabsf((float)acc));
+        const float b = __fadd_rn(hi, lo);
+        beta0[o] = b;
+        r[o] = b;
+        amax = fmaxf(amax, fabsf(b));
     }
     double s = 0.0;
     const int64_t nx = (int64_t)d.P * d.H * d.W;
@@ -136,16 +149,18 @@ __global__ void dtx2d_kernel(const float *__restrict__ D, const float *__restric
 
 // ---------------------------------------------------------------- phase
 
-struct BandParams {
+struct TileParams {
     float *r, *Z;
     const float *Ct, *norms;
-    const int64_t *band_s;   // [M+1] first row of each band
-    const int *list;         // bands of this phase
-    unsigned char *dirty;    // [M]
-    long long *upd;          // [1] updates of this launch's sweep counter
+    const int64_t *row_s;    // [Mr+1] first row of each row band
+    const int64_t *col_s;    // [Mc+1] first column of each column block
+    const int *list;         // tiles of this phase, m * Mc + n
+    unsigned char *dirty;    // [Mr * Mc]
+    long long *upd;          // [1] updates of this sweep
     double *dec;             // [1] objective decrease (Prop. A.1)
     Dims d;
-    int M, KQ, u;
+    int Mr, Mc, KQ, u;
+    int max_pos;             // positions of the largest tile (shared-memory layout)
     float lam, tol;
 };
 
@@ -158,41 +173,98 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
     return ((unsigned long long)hmax << 32) | lmax;
 }
 
-// One visit of a band per block (a block of the phase's list).
-__global__ void __launch_bounds__(kB2) band_kernel(BandParams bp)
+// Shared-memory layout of a tile block (bytes, 16-aligned pieces): per
+// position its cached key, candidate Z', change and atom; with STAGE also r
+// and Z of the tile, position-major with an odd row of ks = K | 1 floats.
+struct TileLayout {
+    size_t key, cz, cd, ck, r, z, total;
+    __host__ __device__ TileLayout(int K, int npos, bool stage)
+    {
+        size_t o = 0;
+        key = o;
+        o = up(o + 8 * (size_t)npos);
+        cz = o;
+        o = up(o + 4 * (size_t)npos);
+        cd = o;
+        o = up(o + 4 * (size_t)npos);
+        ck = o;
+        o = up(o + 4 * (size_t)npos);
+        r = o;
+        if (stage)
+            o = up(o + 4 * (size_t)(K | 1) * npos);
+        z = o;
+        if (stage)
+            o = up(o + 4 * (size_t)(K | 1) * npos);
+        total = o;
+    }
+    __host__ __device__ static size_t up(size_t x) { return (x + 15) & ~(size_t)15; }
+};
+
+// One visit of a tile (row band m x column block n) per block.  Position
+// (i, j) belongs to the thread (slot(i, j) mod kB2), slot(i, j) = (i mod
+// (2h-1)) (2w-1) + (j mod (2w-1)): the (2h-1) x (2w-1) positions of an
+// update window have distinct slots, so the window's positions go to
+// distinct threads, and each position of the tile is only ever written, and
+// its key re-evaluated, by its owner (no barrier between an update and the
+// next argmax).  Positions of the window outside the tile belong to idle
+// neighbours of this phase: their r is changed with atomicAdd.
+template <bool STAGE>
+__global__ void __launch_bounds__(kB2) tile_kernel(TileParams tp)
 {
     extern __shared__ __align__(16) unsigned char sm[];
-    __shared__ unsigned long long s_key[kB2 / 32];
-    __shared__ float s_z[kB2 / 32], s_d[kB2 / 32];
-    __shared__ int s_k[kB2 / 32], s_pos[kB2 / 32];
+    __shared__ unsigned long long s_key[2][kB2 / 32];
+    __shared__ float s_z[2][kB2 / 32], s_d[2][kB2 / 32];
+    __shared__ int s_k[2][kB2 / 32], s_pos[2][kB2 / 32];
     __shared__ float s_nrm[kMaxK2], s_rn[kMaxK2];
     __shared__ double s_dec[kB2 / 32];
-    const int m = bp.list[blockIdx.x];
-    if (!bp.dirty[m])
+    const int tile = tp.list[blockIdx.x];
+    if (!tp.dirty[tile])
         return;  // uniform: every thread reads the same flag
-    const Dims d = bp.d;
+    const int m = tile / tp.Mc, n = tile % tp.Mc;
+    const Dims d = tp.d;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t i_lo = bp.band_s[m], i_hi = bp.band_s[m + 1];
+    const int64_t i_lo = tp.row_s[m], i_hi = tp.row_s[m + 1];
+    const int64_t j_lo = tp.col_s[n], j_hi = tp.col_s[n + 1];
+    const int tw = (int)(j_hi - j_lo);
+    const int npos = (int)(i_hi - i_lo) * tw;
     const int64_t Wz = d.Wz, HWz = d.Hz * d.Wz;
-    const int npos = (int)((i_hi - i_lo) * Wz);
-    unsigned long long *key = reinterpret_cast<unsigned long long *>(sm);
-    float *cz = reinterpret_cast<float *>(key + npos);
-    float *cd = cz + npos;
-    int *ck = reinterpret_cast<int *>(cd + npos);
-    const int K = d.K, H2 = 2 * d.h - 1, W2 = 2 * d.w - 1, A = H2 * W2;
-    const float lam = bp.lam;
+    const int K = d.K, ks = K | 1;
+    const int H2 = 2 * d.h - 1, W2 = 2 * d.w - 1, A = H2 * W2;
+    const TileLayout lay(K, tp.max_pos, STAGE);
+    unsigned long long *key = reinterpret_cast<unsigned long long *>(sm + lay.key);
+    float *cz = reinterpret_cast<float *>(sm + lay.cz);
+    float *cd = reinterpret_cast<float *>(sm + lay.cd);
+    int *ck = reinterpret_cast<int *>(sm + lay.ck);
+    float *rs = reinterpret_cast<float *>(sm + lay.r);
+    float *zs = reinterpret_cast<float *>(sm + lay.z);
+    const float lam = tp.lam;
     for (int k = tid; k < K; k += kB2) {
-        s_nrm[k] = bp.norms[k];
-        s_rn[k] = __frcp_rn(bp.norms[k]);
+        s_nrm[k] = tp.norms[k];
+        s_rn[k] = __frcp_rn(tp.norms[k]);
     }
+    // element k of tile position p = (i - i_lo) tw + (j - j_lo)
+    auto rref = [&](int p, int64_t i, int64_t j, int k) -> float & {
+        return STAGE ? rs[p * ks + k] : tp.r[k * HWz + i * Wz + j];
+    };
+    auto zref = [&](int p, int64_t i, int64_t j, int k) -> float & {
+        return STAGE ? zs[p * ks + k] : tp.Z[k * HWz + i * Wz + j];
+    };
+    if (STAGE)
+        for (int p = tid; p < npos; p += kB2) {
+            const int64_t i = i_lo + p / tw, j = j_lo + p % tw;
+            for (int k = 0; k < K; k++) {
+                rs[p * ks + k] = tp.r[k * HWz + i * Wz + j];
+                zs[p * ks + k] = tp.Z[k * HWz + i * Wz + j];
+            }
+        }
     __syncthreads();
-    // best coordinate of band position pos (row i_lo + pos / Wz, column pos % Wz)
-    auto eval = [&](int pos) {
-        const int64_t e = (i_lo + pos / Wz) * Wz + pos % Wz;
+    // best coordinate over k of position p, cached as a key (|dZ| bits, ~flat)
+    // with ties to the lowest (k, i, j), i.e. the lowest (k Hz + i) Wz + j
+    auto eval = [&](int p, int64_t i, int64_t j) {
         float best = -1.f, bz = 0.f, bd = 0.f;
         int bk = 0;
         for (int k = 0; k < K; k++) {
-            const float r = bp.r[k * HWz + e], z = bp.Z[k * HWz + e];
+            const float r = rref(p, i, j, k), z = zref(p, i, j, k);
             if (z == 0.f && fabsf(r) <= lam)
                 continue;
             float zn, dd;
@@ -204,99 +276,126 @@ __global__ void __launch_bounds__(kB2) band_kernel(BandParams bp)
                 bd = dd;
             }
         }
-        // flat index within the band, same order as (k Hz + i) Wz + j
-        const unsigned flat = (unsigned)bk * (unsigned)npos + (unsigned)pos;
-        key[pos] = best > 0.f ? ((unsigned long long)__float_as_uint(best) << 32) | (unsigned)(~flat)
-                              : 0ull;
-        cz[pos] = bz;
-        cd[pos] = bd;
-        ck[pos] = bk;
+        const unsigned flat = (unsigned)bk * (unsigned)npos + (unsigned)p;
+        key[p] = best > 0.f ? ((unsigned long long)__float_as_uint(best) << 32) | (unsigned)(~flat)
+                            : 0ull;
+        cz[p] = bz;
+        cd[p] = bd;
+        ck[p] = bk;
     };
-    for (int pos = tid; pos < npos; pos += kB2)
-        eval(pos);
+    // this thread's positions: slots q, q + kB2, ... < A; for slot (a, b) the
+    // rows i == a (mod H2) and columns j == b (mod W2) of the tile
+    auto first = [](int64_t lo, int res, int period) -> int64_t {
+        return lo + (((res - lo) % period) + period) % period;
+    };
+    for (int q = tid; q < A; q += kB2) {
+        const int a = q / W2, b = q % W2;
+        for (int64_t i = first(i_lo, a, H2); i < i_hi; i += H2)
+            for (int64_t j = first(j_lo, b, W2); j < j_hi; j += W2)
+                eval((int)(i - i_lo) * tw + (int)(j - j_lo), i, j);
+    }
     int nupd = 0;
-    int64_t imin = i_hi, imax = i_lo - 1;
+    int64_t imin = i_hi, imax = i_lo - 1, jmin = j_hi, jmax = j_lo - 1;
     float decrease = 0.f;
     bool capped = false;
+    const float4 *Ct4 = reinterpret_cast<const float4 *>(tp.Ct);
     for (int it = 0;; it++) {
+        const int buf = it & 1;
         unsigned long long my = 0ull;
         int mp = 0;
-        for (int pos = tid; pos < npos; pos += kB2)
-            if (key[pos] > my) {
-                my = key[pos];
-                mp = pos;
-            }
+        for (int q = tid; q < A; q += kB2) {
+            const int a = q / W2, b = q % W2;
+            for (int64_t i = first(i_lo, a, H2); i < i_hi; i += H2)
+                for (int64_t j = first(j_lo, b, W2); j < j_hi; j += W2) {
+                    const int p = (int)(i - i_lo) * tw + (int)(j - j_lo);
+                    if (key[p] > my) {
+                        my = key[p];
+                        mp = p;
+                    }
+                }
+        }
+        const float my_z = cz[mp], my_d = cd[mp];
+        const int my_k = ck[mp];
         const unsigned long long wm = warp_max_u64(my);
         const unsigned win = __ballot_sync(0xffffffffu, my == wm);
         if (lane == __ffs(win) - 1) {
-            s_key[warp] = wm;
-            s_z[warp] = cz[mp];
-            s_d[warp] = cd[mp];
-            s_k[warp] = ck[mp];
-            s_pos[warp] = mp;
+            s_key[buf][warp] = wm;
+            s_z[buf][warp] = my_z;
+            s_d[buf][warp] = my_d;
+            s_k[buf][warp] = my_k;
+            s_pos[buf][warp] = mp;
         }
         __syncthreads();
         unsigned long long bk = 0ull;
         int bw = 0;
         for (int q = 0; q < kB2 / 32; q++)
-            if (s_key[q] > bk) {
-                bk = s_key[q];
+            if (s_key[buf][q] > bk) {
+                bk = s_key[buf][q];
                 bw = q;
             }
         const float adz = __uint_as_float((unsigned)(bk >> 32));
-        if (!(adz >= bp.tol))
+        if (!(adz >= tp.tol))
             break;
-        if (it >= bp.u) {
+        if (it >= tp.u) {
             capped = true;
             break;
         }
-        const float znew = s_z[bw], delta = s_d[bw];
-        const int k0 = s_k[bw], pos0 = s_pos[bw];
-        const int64_t i0 = i_lo + pos0 / Wz, j0 = pos0 % Wz;
-        const int64_t e0 = i0 * Wz + j0;
-        if (tid == 0) {
-            // Prop. A.1 from r before this update: dZ (r - n dZ / 2) + lam (|z| - |u|)
-            const float n = s_nrm[k0], z = znew - delta;
-            const float r0 = bp.r[k0 * HWz + e0];
-            decrease += delta * (r0 - 0.5f * n * delta) + lam * (fabsf(z) - fabsf(znew));
-        }
-        __syncthreads();  // r0 read before any thread changes it
-        // Eq. beta_up (r form) on the window, K coefficients per position
-        const float4 *Ct4 = reinterpret_cast<const float4 *>(bp.Ct);
-        for (int lag = tid; lag < A; lag += kB2) {
-            const int64_t i = i0 + lag / W2 - (d.h - 1), j = j0 + lag % W2 - (d.w - 1);
+        const float znew = s_z[buf][bw], delta = s_d[buf][bw];
+        const int k0 = s_k[buf][bw], p0 = s_pos[buf][bw];
+        const int64_t i0 = i_lo + p0 / tw, j0 = j_lo + p0 % tw;
+        const int64_t ib = i0 - (d.h - 1), jb = j0 - (d.w - 1);
+        // Eq. beta_up (r form) on the window: slot q holds the window
+        // position (i, j) with i == a (mod H2), j == b (mod W2)
+        for (int q = tid; q < A; q += kB2) {
+            const int a = q / W2, b = q % W2;
+            const int64_t i = first(ib, a, H2), j = first(jb, b, W2);
             if (i < 0 || i >= d.Hz || j < 0 || j >= Wz)
                 continue;
-            const bool own = i >= i_lo && i < i_hi;
-            float *rp = bp.r + i * Wz + j;
-            for (int q = 0; q < bp.KQ; q++) {
-                const float4 c = __ldg(Ct4 + ((int64_t)k0 * bp.KQ + q) * A + lag);
+            const int lag = (int)(i - ib) * W2 + (int)(j - jb);
+            const bool own = i >= i_lo && i < i_hi && j >= j_lo && j < j_hi;
+            const int p = own ? (int)(i - i_lo) * tw + (int)(j - j_lo) : 0;
+            if (own && i == i0 && j == j0) {
+                // Prop. A.1 from the owner's r before this update touches it:
+                // dZ (r - n dZ / 2) + lam (|z| - |u|)
+                const float nk = s_nrm[k0], z = znew - delta;
+                const float r0 = rref(p, i, j, k0);
+                decrease += delta * (r0 - 0.5f * nk * delta) + lam * (fabsf(z) - fabsf(znew));
+                zref(p, i, j, k0) = znew;
+            }
+            for (int g = 0; g < tp.KQ; g++) {
+                const float4 c = __ldg(Ct4 + ((int64_t)k0 * tp.KQ + g) * A + lag);
                 const float cv[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
                 for (int e = 0; e < 4; e++) {
-                    const int k = 4 * q + e;
+                    const int k = 4 * g + e;
                     if (k >= K)
                         break;
-                    if (own)
-                        rp[k * HWz] = fmaf(-cv[e], delta, rp[k * HWz]);
-                    else
-                        atomicAdd(rp + k * HWz, -cv[e] * delta);
+                    if (own) {
+                        float &rv = rref(p, i, j, k);
+                        rv = fmaf(-cv[e], delta, rv);
+                    } else {
+                        atomicAdd(tp.r + k * HWz + i * Wz + j, -cv[e] * delta);
+                    }
                 }
             }
-        }
-        if (tid == 0)
-            bp.Z[k0 * HWz + e0] = znew;
-        __syncthreads();
-        // re-evaluate this thread's positions inside the window
-        for (int pos = tid; pos < npos; pos += kB2) {
-            const int64_t i = i_lo + pos / Wz, j = pos % Wz;
-            if (i >= i0 - (d.h - 1) && i <= i0 + (d.h - 1) && j >= j0 - (d.w - 1) &&
-                j <= j0 + (d.w - 1))
-                eval(pos);
+            if (own)
+                eval(p, i, j);
         }
         nupd++;
         imin = i0 < imin ? i0 : imin;
         imax = i0 > imax ? i0 : imax;
+        jmin = j0 < jmin ? j0 : jmin;
+        jmax = j0 > jmax ? j0 : jmax;
+    }
+    if (STAGE && nupd > 0) {
+        __syncthreads();  // every owner's last update is in shared memory
+        for (int p = tid; p < npos; p += kB2) {
+            const int64_t i = i_lo + p / tw, j = j_lo + p % tw;
+            for (int k = 0; k < K; k++) {
+                tp.r[k * HWz + i * Wz + j] = rs[p * ks + k];
+                tp.Z[k * HWz + i * Wz + j] = zs[p * ks + k];
+            }
+        }
     }
     for (int off = 16; off > 0; off >>= 1)
         decrease += __shfl_xor_sync(0xffffffffu, decrease, off);
@@ -307,16 +406,26 @@ __global__ void __launch_bounds__(kB2) band_kernel(BandParams bp)
         double dsum = 0.0;
         for (int q = 0; q < kB2 / 32; q++)
             dsum += s_dec[q];
-        bp.dirty[m] = capped ? 1 : 0;
+        tp.dirty[tile] = capped ? 1 : 0;
         if (nupd > 0) {
-            // bands whose rows the windows reached need a visit again
-            const int64_t lo = imin - (d.h - 1), hi = imax + (d.h - 1);
-            for (int mm = m - 1; mm >= 0 && bp.band_s[mm + 1] > lo; mm--)
-                bp.dirty[mm] = 1;
-            for (int mm = m + 1; mm < bp.M && bp.band_s[mm] <= hi; mm++)
-                bp.dirty[mm] = 1;
-            atomicAdd(reinterpret_cast<unsigned long long *>(bp.upd), (unsigned long long)nupd);
-            atomicAdd(bp.dec, dsum);
+            // tiles the windows reached need a visit again
+            const int64_t rlo = imin - (d.h - 1), rhi = imax + (d.h - 1);
+            const int64_t clo = jmin - (d.w - 1), chi = jmax + (d.w - 1);
+            int m0 = m, m1 = m, n0 = n, n1 = n;
+            while (m0 > 0 && tp.row_s[m0] > rlo)
+                m0--;
+            while (m1 + 1 < tp.Mr && tp.row_s[m1 + 1] <= rhi)
+                m1++;
+            while (n0 > 0 && tp.col_s[n0] > clo)
+                n0--;
+            while (n1 + 1 < tp.Mc && tp.col_s[n1 + 1] <= chi)
+                n1++;
+            for (int mm = m0; mm <= m1; mm++)
+                for (int nn = n0; nn <= n1; nn++)
+                    if (mm != m || nn != n)
+                        tp.dirty[mm * tp.Mc + nn] = 1;
+            atomicAdd(reinterpret_cast<unsigned long long *>(tp.upd), (unsigned long long)nupd);
+            atomicAdd(tp.dec, dsum);
         }
     }
 }
@@ -388,10 +497,12 @@ __global__ void __launch_bounds__(256)
     const int64_t r0 = max((int64_t)0, i - (d.h - 1)), r1 = min(d.Hz, i + d.h);
     const int64_t c0 = max((int64_t)0, j0 - (d.w - 1)), c1 = min(d.Wz, j0 + kTile2 + d.w - 1);
     constexpr int kPer = (kMaxK2 + 7) / 8;
-    double acc[kPer];
+    float acc_hi[kPer], acc_lo[kPer];  // double-float sums of C z
 #pragma unroll
-    for (int q = 0; q < kPer; q++)
-        acc[q] = 0.0;
+    for (int q = 0; q < kPer; q++) {
+        acc_hi[q] = 0.f;
+        acc_lo[q] = 0.f;
+    }
     // the region's columns in chunks whose K x rows x chunk elements fit the list
     const int64_t chunk = max((int64_t)1, (int64_t)kList2 / ((int64_t)d.K * (r1 - r0)));
     for (int64_t ca = c0; ca < c1; ca += chunk) {
@@ -408,9 +519,10 @@ __global__ void __launch_bounds__(256)
                 for (int t = 0; t < kPer; t++) {
                     const int k = grp + 8 * t;
                     if (k < d.K)
-                        acc[t] += (double)__ldg(Ct + ((((int64_t)e.k * KQ + (k >> 2)) * A + lag) << 2) +
-                                                (k & 3)) *
-                                  (double)e.z;
+                        df_add_prod(acc_hi[t], acc_lo[t],
+                                    __ldg(Ct + ((((int64_t)e.k * KQ + (k >> 2)) * A + lag) << 2) +
+                                          (k & 3)),
+                                    e.z);
                 }
             }
         }
@@ -424,7 +536,11 @@ __global__ void __launch_bounds__(256)
             if (k >= d.K)
                 continue;
             const int64_t o = ((int64_t)k * d.Hz + i) * d.Wz + j;
-            const float rn = (float)((double)beta0[o] - acc[t]);
+            // r = beta0 - (hi + lo), finished with TwoSum: one final rounding
+            float rn = beta0[o], rl = 0.f;
+            df_add(rn, rl, -acc_hi[t]);
+            df_add(rn, rl, -acc_lo[t]);
+            rn = __fadd_rn(rn, rl);
             const float rold = r[o];
             if (write_r)
                 r[o] = rn;
@@ -482,12 +598,15 @@ __global__ void __launch_bounds__(256)
     // activations reaching pixel (y, x): rows [y-h+1, y], columns [x-w+1, x]
     const int64_t r0 = max((int64_t)0, y - (d.h - 1)), r1 = min(d.Hz, y + 1);
     const int64_t c0 = max((int64_t)0, x0 - (d.w - 1)), c1 = min(d.Wz, x0 + kTile2);
-    double sq = 0.0, l1 = 0.0;
+    // double-float per thread (the FP64 pipe is narrow); FP64 per warp
+    float sq_h = 0.f, sq_l = 0.f, l1_h = 0.f, l1_l = 0.f;
     constexpr int kPm = 8;  // channels per thread group pass (P up to 64)
-    double acc[kPm];
+    float acc_hi[kPm], acc_lo[kPm];
 #pragma unroll
-    for (int t = 0; t < kPm; t++)
-        acc[t] = 0.0;
+    for (int t = 0; t < kPm; t++) {
+        acc_hi[t] = 0.f;
+        acc_lo[t] = 0.f;
+    }
     if (r0 < r1 && c0 < c1) {
         const int64_t chunk = max((int64_t)1, (int64_t)kList2 / ((int64_t)d.K * (r1 - r0)));
         for (int64_t ca = c0; ca < c1; ca += chunk) {
@@ -503,8 +622,9 @@ __global__ void __launch_bounds__(256)
                     for (int t = 0; t < kPm; t++) {
                         const int p = grp + 8 * t;
                         if (p < d.P)
-                            acc[t] += (double)__ldg(D + (((int64_t)e.k * d.P + p) * d.h + u) * d.w + v) *
-                                      (double)e.z;
+                            df_add_prod(acc_hi[t], acc_lo[t],
+                                        __ldg(D + (((int64_t)e.k * d.P + p) * d.h + u) * d.w + v),
+                                        e.z);
                     }
                 }
             __syncthreads();
@@ -514,22 +634,25 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int t = 0; t < kPm; t++) {
             const int p = grp + 8 * t;
-            if (p < d.P) {
-                const double rr = (double)X[((int64_t)p * d.H + y) * d.W + x] - acc[t];
-                sq += rr * rr;
-            }
+            if (p < d.P)
+                df_add_sq_residual(sq_h, sq_l, X[((int64_t)p * d.H + y) * d.W + x], acc_hi[t],
+                                   acc_lo[t]);
         }
     // |Z| of this block's own positions (row y, columns [x0, x0+32)), once
     if (grp == 0 && y < d.Hz && x < d.Wz)
         for (int k = 0; k < d.K; k++)
-            l1 += fabs((double)Z[((int64_t)k * d.Hz + y) * d.Wz + x]);
+            df_add(l1_h, l1_l, fabsf(Z[((int64_t)k * d.Hz + y) * d.Wz + x]));
     for (int off = 16; off > 0; off >>= 1) {
-        sq += __shfl_xor_sync(0xffffffffu, sq, off);
-        l1 += __shfl_xor_sync(0xffffffffu, l1, off);
+        const float a = __shfl_xor_sync(0xffffffffu, sq_h, off);
+        const float b = __shfl_xor_sync(0xffffffffu, sq_l, off);
+        const float c = __shfl_xor_sync(0xffffffffu, l1_h, off);
+        const float e = __shfl_xor_sync(0xffffffffu, l1_l, off);
+        df_add_df(sq_h, sq_l, a, b);
+        df_add_df(l1_h, l1_l, c, e);
     }
     if (col == 0) {
-        bsum[0][grp] = sq;
-        bsum[1][grp] = l1;
+        bsum[0][grp] = (double)sq_h + (double)sq_l;
+        bsum[1][grp] = (double)l1_h + (double)l1_l;
     }
     __syncthreads();
     if (tid == 0) {
@@ -585,7 +708,7 @@ int auto_bands(int64_t Hz, int h)
 struct Dev2 {
     float *D = nullptr, *X = nullptr, *Ct = nullptr, *norms = nullptr, *beta0 = nullptr,
           *r = nullptr, *Z = nullptr;
-    int64_t *band_s = nullptr;
+    int64_t *band_s = nullptr, *col_s = nullptr;
     int *list = nullptr;
     unsigned char *dirty = nullptr;
     long long *upd = nullptr;
@@ -594,8 +717,8 @@ struct Dev2 {
     unsigned long long *red = nullptr;
     ~Dev2()
     {
-        void *p[] = {D, X, Ct, norms, beta0, r, Z, band_s, list, dirty, upd, dec, x2, partial, E,
-                     amax, red};
+        void *p[] = {D, X, Ct, norms, beta0, r, Z, band_s, col_s, list, dirty, upd, dec, x2,
+                     partial, E, amax, red};
         for (void *q : p)
             cudaFree(q);
     }
@@ -625,8 +748,9 @@ int csc2d_plan(int64_t Hz, int h, int M, int *M_out, int *phases, int64_t *start
 }
 
 int csc2d_solve(const float *D, int K, int P, int h, int w, const float *X, int64_t H, int64_t W,
-                double lambda, double tol, int64_t max_updates, int M, int updates_per_visit,
-                float *Z_out, double *objective, csc2d_stats *stats, void *stream)
+                double lambda, double tol, int64_t max_updates, int M, int N,
+                int updates_per_visit, float *Z_out, double *objective, csc2d_stats *stats,
+                void *stream)
 {
     csc::TraceRange trace_("csc2d_solve");
     if (!D || !X)
@@ -637,28 +761,46 @@ int csc2d_solve(const float *D, int K, int P, int h, int w, const float *X, int6
                                 "csc2d_solve: need 1 <= K <= %d, P >= 1, 1 <= h <= H, 1 <= w <= W, "
                                 "(2h-1)(2w-1) <= %d",
                                 kMaxK2, kMaxWin);
-    if (!(lambda > 0.0) || !(tol > 0.0) || max_updates < 1 || updates_per_visit < 0)
+    if (!(lambda > 0.0) || !(tol > 0.0) || max_updates < 1 || updates_per_visit < 0 || N < 0)
         return csc_record_error(CSC_EINVAL, "csc2d_solve: need lambda > 0, tol > 0, "
-                                            "max_updates >= 1, updates_per_visit >= 0");
+                                            "max_updates >= 1, updates_per_visit >= 0, N >= 0");
     Dims d{K, P, h, w, H, W, H - h + 1, W - w + 1};
     if (d.K * d.Hz * d.Wz >= ((int64_t)1 << 31) || d.Hz * d.Wz >= ((int64_t)1 << 31) / 64)
         return csc_record_error(CSC_EINVAL, "csc2d_solve: image too large (flat indices)");
-    int Mb = 0, c = 0;
-    int rc = csc2d_plan(d.Hz, h, M, &Mb, &c, nullptr);
+    // row bands and column blocks: the same cut and phase count per axis
+    int Mb = 0, cr = 0, Nb = 0, cc = 0;
+    int rc = csc2d_plan(d.Hz, h, M, &Mb, &cr, nullptr);
     if (rc != CSC_OK)
         return rc;
-    std::vector<int64_t> bs(Mb + 1);
+    rc = csc2d_plan(d.Wz, w, N, &Nb, &cc, nullptr);
+    if (rc != CSC_OK)
+        return rc;
+    const int c = cr * cc;
+    const int64_t ntiles = (int64_t)Mb * Nb;
+    if (ntiles > (1 << 24))
+        return csc_record_error(CSC_EINVAL, "csc2d_solve: %lld tiles (at most 2^24)",
+                                (long long)ntiles);
+    std::vector<int64_t> bs(Mb + 1), cs(Nb + 1);
     for (int m = 0; m <= Mb; m++)
         bs[m] = (int64_t)m * d.Hz / Mb;
-    int64_t hmax = 0;
+    for (int q = 0; q <= Nb; q++)
+        cs[q] = (int64_t)q * d.Wz / Nb;
+    int64_t hmax = 0, wmax = 0;
     for (int m = 0; m < Mb; m++)
         hmax = std::max(hmax, bs[m + 1] - bs[m]);
-    const size_t smem = (size_t)hmax * d.Wz * 20;
+    for (int q = 0; q < Nb; q++)
+        wmax = std::max(wmax, cs[q + 1] - cs[q]);
+    const int64_t max_pos = hmax * wmax;
+    if (max_pos >= ((int64_t)1 << 31) / 64)
+        return csc_record_error(CSC_EINVAL, "csc2d_solve: tiles too large");
+    // a tile's r and Z are staged in shared memory when they fit
+    const bool stage = TileLayout(K, (int)max_pos, true).total <= (size_t)kMaxSmem;
+    const size_t smem = TileLayout(K, (int)max_pos, stage).total;
     if (smem > (size_t)kMaxSmem)
         return csc_record_error(CSC_EINVAL,
-                                "csc2d_solve: a band of %lld x %lld positions needs %zu bytes of "
-                                "shared memory (more bands, or a narrower image)",
-                                (long long)hmax, (long long)d.Wz, smem);
+                                "csc2d_solve: a tile of %lld x %lld positions needs %zu bytes of "
+                                "shared memory (more bands or column blocks)",
+                                (long long)hmax, (long long)wmax, smem);
     // the exact checks gather the nonzeros of (2h-1) rows x K atoms one column
     // chunk at a time: one column must fit the list; the objective's
     // channels are spread over 8 thread groups, at most 8 passes each
@@ -680,8 +822,9 @@ int csc2d_solve(const float *D, int K, int P, int h, int w, const float *X, int6
     C2_CUDA(cudaMalloc(&g.r, sizeof(float) * nz));
     C2_CUDA(cudaMalloc(&g.Z, sizeof(float) * nz));
     C2_CUDA(cudaMalloc(&g.band_s, sizeof(int64_t) * (Mb + 1)));
-    C2_CUDA(cudaMalloc(&g.list, sizeof(int) * Mb));
-    C2_CUDA(cudaMalloc(&g.dirty, Mb));
+    C2_CUDA(cudaMalloc(&g.col_s, sizeof(int64_t) * (Nb + 1)));
+    C2_CUDA(cudaMalloc(&g.list, sizeof(int) * ntiles));
+    C2_CUDA(cudaMalloc(&g.dirty, ntiles));
     C2_CUDA(cudaMalloc(&g.upd, sizeof(long long)));
     C2_CUDA(cudaMalloc(&g.dec, sizeof(double)));
     C2_CUDA(cudaMalloc(&g.x2, sizeof(double)));
@@ -693,22 +836,28 @@ int csc2d_solve(const float *D, int K, int P, int h, int w, const float *X, int6
     int64_t launches = 0;
     C2_CUDA(copy_in(g.D, D, sizeof(float) * K * P * h * w, s));
     C2_CUDA(copy_in(g.X, X, sizeof(float) * P * H * W, s));
-    // phase lists: bands m == p (mod c), consecutive in the device list
+    // phase lists: phase pr cc + pc holds the tiles (m, n) with m == pr (mod
+    // cr) and n == pc (mod cc), consecutive in the device list
     std::vector<int> list;
     std::vector<int> off(c + 1, 0);
-    for (int p = 0; p < c; p++) {
-        off[p] = (int)list.size();
-        for (int m = p; m < Mb; m += c)
-            list.push_back(m);
-    }
+    for (int pr = 0; pr < cr; pr++)
+        for (int pc = 0; pc < cc; pc++) {
+            off[pr * cc + pc] = (int)list.size();
+            for (int m = pr; m < Mb; m += cr)
+                for (int q = pc; q < Nb; q += cc)
+                    list.push_back(m * Nb + q);
+        }
     off[c] = (int)list.size();
     C2_CUDA(cudaMemcpyAsync(g.band_s, bs.data(), sizeof(int64_t) * (Mb + 1),
                             cudaMemcpyHostToDevice, s));
-    C2_CUDA(cudaMemcpyAsync(g.list, list.data(), sizeof(int) * Mb, cudaMemcpyHostToDevice, s));
+    C2_CUDA(cudaMemcpyAsync(g.col_s, cs.data(), sizeof(int64_t) * (Nb + 1),
+                            cudaMemcpyHostToDevice, s));
+    C2_CUDA(cudaMemcpyAsync(g.list, list.data(), sizeof(int) * ntiles, cudaMemcpyHostToDevice,
+                            s));
     C2_CUDA(cudaMemsetAsync(g.amax, 0, sizeof(unsigned), s));
     C2_CUDA(cudaMemsetAsync(g.x2, 0, sizeof(double), s));
     C2_CUDA(cudaMemsetAsync(g.Z, 0, sizeof(float) * nz, s));
-    C2_CUDA(cudaMemsetAsync(g.dirty, 1, Mb, s));
+    C2_CUDA(cudaMemsetAsync(g.dirty, 1, ntiles, s));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     C2_CUDA(cudaEventCreate(&e0));
     C2_CUDA(cudaEventCreate(&e1));
@@ -723,24 +872,28 @@ int csc2d_solve(const float *D, int K, int P, int h, int w, const float *X, int6
         C2_CUDA(cudaGetLastError());
         launches += 2;
     }
-    C2_CUDA(cudaFuncSetAttribute(band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    auto tile_fn = stage ? tile_kernel<true> : tile_kernel<false>;
+    C2_CUDA(cudaFuncSetAttribute(tile_fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
-    BandParams bp;
-    bp.r = g.r;
-    bp.Z = g.Z;
-    bp.Ct = g.Ct;
-    bp.norms = g.norms;
-    bp.band_s = g.band_s;
-    bp.dirty = g.dirty;
-    bp.upd = g.upd;
-    bp.dec = g.dec;
-    bp.d = d;
-    bp.M = Mb;
-    bp.KQ = KQ;
-    bp.u = updates_per_visit > 0 ? updates_per_visit : kDefaultMaxVisit;
-    bp.lam = (float)lambda;
+    TileParams tp;
+    tp.r = g.r;
+    tp.Z = g.Z;
+    tp.Ct = g.Ct;
+    tp.norms = g.norms;
+    tp.row_s = g.band_s;
+    tp.col_s = g.col_s;
+    tp.dirty = g.dirty;
+    tp.upd = g.upd;
+    tp.dec = g.dec;
+    tp.d = d;
+    tp.Mr = Mb;
+    tp.Mc = Nb;
+    tp.KQ = KQ;
+    tp.max_pos = (int)max_pos;
+    tp.u = updates_per_visit > 0 ? updates_per_visit : kAutoVisit2d;
+    tp.lam = (float)lambda;
     const int max_resyncs = 3;
-    bp.tol = (float)(0.5 * tol);  // CD to tol/2, the exact check accepts at tol
+    tp.tol = (float)(0.5 * tol);  // CD to tol/2, the exact check accepts at tol
     int64_t updates = 0, sweeps = 0;
     int resyncs = 0;
     bool converged = false;
@@ -755,8 +908,8 @@ int csc2d_solve(const float *D, int K, int P, int h, int w, const float *X, int6
                 const int cnt = off[p + 1] - off[p];
                 if (cnt == 0)
                     continue;
-                bp.list = g.list + off[p];
-                band_kernel<<<cnt, kB2, smem, s>>>(bp);
+                tp.list = g.list + off[p];
+                tile_fn<<<cnt, kB2, smem, s>>>(tp);
                 C2_CUDA(cudaGetLastError());
                 launches++;
             }
@@ -792,7 +945,7 @@ int csc2d_solve(const float *D, int K, int P, int h, int w, const float *X, int6
         }
         if (resyncs > max_resyncs)
             break;
-        C2_CUDA(cudaMemsetAsync(g.dirty, 1, Mb, s));
+        C2_CUDA(cudaMemsetAsync(g.dirty, 1, ntiles, s));
     }
     C2_CUDA(cudaEventRecord(e1, s));
     const unsigned ogrid = (unsigned)ntile_o;
@@ -816,6 +969,7 @@ int csc2d_solve(const float *D, int K, int P, int h, int w, const float *X, int6
         stats->updates = updates;
         stats->sweeps = sweeps;
         stats->bands = Mb;
+        stats->col_blocks = Nb;
         stats->phases = c;
         stats->resyncs = resyncs;
         stats->converged = converged ? 1 : 0;

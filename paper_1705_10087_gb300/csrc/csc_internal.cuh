@@ -83,6 +83,54 @@ __device__ __forceinline__ void coord_step(float r, float z, float n, float rn, 
     }
 }
 
+// Double-float accumulation (hi + lo, about 48 significant bits) of products
+// of floats, with error-free transformations: the rounding error of a*b is
+// fma(a, b, -p) (exact), that of hi + p is Knuth's TwoSum.  The _rn
+// intrinsics keep the compiler from contracting or reassociating them.  This
+// runs on the FP32 pipes, which GB300 has about 64 times more of than FP64.
+__device__ __forceinline__ void df_add_prod(float &hi, float &lo, float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    const float pe = __fmaf_rn(a, b, -p);
+    const float s = __fadd_rn(hi, p);
+    const float bv = __fsub_rn(s, hi);
+    const float se = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(p, bv));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(se, pe));
+}
+
+// (hi, lo) += a, a float (TwoSum; the rounding error is carried in lo)
+__device__ __forceinline__ void df_add(float &hi, float &lo, float a)
+{
+    const float s = __fadd_rn(hi, a);
+    const float bv = __fsub_rn(s, hi);
+    const float se = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(a, bv));
+    hi = s;
+    lo = __fadd_rn(lo, se);
+}
+
+// (hi, lo) += (bh, bl), both double-float
+__device__ __forceinline__ void df_add_df(float &hi, float &lo, float bh, float bl)
+{
+    df_add(hi, lo, bh);
+    lo = __fadd_rn(lo, bl);
+}
+
+// (sh, sl) += (x - (ah + al))^2 in double-float: the residual with TwoSum,
+// its square as rh^2 (exact error by fma) + 2 rh rl (rl^2 is below the
+// pair's precision)
+__device__ __forceinline__ void df_add_sq_residual(float &sh, float &sl, float x, float ah,
+                                                   float al)
+{
+    float rh = x, rl = 0.f;
+    df_add(rh, rl, -ah);
+    df_add(rh, rl, -al);
+    const float p = __fmul_rn(rh, rh);
+    const float q = __fmaf_rn(__fmul_rn(2.f, rh), rl, __fmaf_rn(rh, rh, -p));
+    df_add(sh, sl, p);
+    sl = __fadd_rn(sl, q);
+}
+
 __device__ __forceinline__ unsigned long long globaltimer_ns()
 {
     unsigned long long t;

@@ -72,7 +72,7 @@ __host__ __device__ inline bool vec_layout(int K, int block)
 // Shared-memory layout of a block, in bytes from the start (16-byte aligned
 // pieces).  w = widest segment; with smem the segment's r and Z are staged.
 struct Layout {
-    size_t key, slot_key, cz, cd, ck, zm, slot_z, slot_d, slot_k, slot_j, nrm, rnrm, r, z, total;
+    size_t key, slot_key, cz, cd, ck, zm, slot_v, nrm, rnrm, r, z, total;
     __host__ __device__ Layout(int K, int w, bool smem, bool vec)
     {
         size_t o = 0;
@@ -88,14 +88,8 @@ struct Layout {
         o = up(o + 4 * (size_t)w);
         zm = o;  // per column: bit k set when Z_k[t] != 0 (compile-time K <= 64)
         o = up(o + 8 * (size_t)w);
-        slot_z = o;
-        o = up(o + 4 * 64);
-        slot_d = o;
-        o = up(o + 4 * 64);
-        slot_k = o;
-        o = up(o + 4 * 64);
-        slot_j = o;
-        o = up(o + 4 * 64);
+        slot_v = o;  // per warp candidate: (Z', dZ, k, column) as one 16-byte word
+        o = up(o + 16 * 64);
         nrm = o;
         o = up(o + 4 * (size_t)K);
         rnrm = o;
@@ -184,10 +178,7 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
     using Mask = typename std::conditional<(KT > 32), unsigned long long, unsigned>::type;
     static_assert(KT <= 64, "the masks of a column hold 64 atoms");
     Mask *zmask = reinterpret_cast<Mask *>(smem_raw + lay.zm);
-    float *slot_z = reinterpret_cast<float *>(smem_raw + lay.slot_z);
-    float *slot_d = reinterpret_cast<float *>(smem_raw + lay.slot_d);
-    int *slot_k = reinterpret_cast<int *>(smem_raw + lay.slot_k);
-    int *slot_j = reinterpret_cast<int *>(smem_raw + lay.slot_j);
+    uint4 *slot_v = reinterpret_cast<uint4 *>(smem_raw + lay.slot_v);
     float *nrm = reinterpret_cast<float *>(smem_raw + lay.nrm);    // ||D_k||^2
     float *rnrm = reinterpret_cast<float *>(smem_raw + lay.rnrm);  // 1 / ||D_k||^2
 
@@ -236,16 +227,30 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
         int bk = 0;
         const float *rc = rs + jj * cst;
         const float *zc = zs + jj * cst;
-        for (Mask rest = need; rest; rest &= rest - 1) {
-            const int k = (sizeof(Mask) == 8 ? __ffsll((long long)rest) : __ffs((int)rest)) - 1;
-            float zn, d;
-            coord_step(rc[k * kst], zc[k * kst], nrm[k], rnrm[k], lam, &zn, &d);
-            const float ad = fabsf(d);
-            if (ad > best) {
-                best = ad;
-                bk = k;
-                bz = zn;
-                bdz = d;
+        // two set bits per round: their coordinate steps are independent, so
+        // their latencies overlap (lower atom first: ties go to the lower k)
+        for (Mask rest = need; rest;) {
+            const int k1 = (sizeof(Mask) == 8 ? __ffsll((long long)rest) : __ffs((int)rest)) - 1;
+            rest &= rest - 1;
+            const bool two = rest != 0;
+            const int k2 =
+                two ? (sizeof(Mask) == 8 ? __ffsll((long long)rest) : __ffs((int)rest)) - 1 : k1;
+            if (two)
+                rest &= rest - 1;
+            float zn1, d1, zn2, d2;
+            coord_step(rc[k1 * kst], zc[k1 * kst], nrm[k1], rnrm[k1], lam, &zn1, &d1);
+            coord_step(rc[k2 * kst], zc[k2 * kst], nrm[k2], rnrm[k2], lam, &zn2, &d2);
+            if (fabsf(d1) > best) {
+                best = fabsf(d1);
+                bk = k1;
+                bz = zn1;
+                bdz = d1;
+            }
+            if (two && fabsf(d2) > best) {
+                best = fabsf(d2);
+                bk = k2;
+                bz = zn2;
+                bdz = d2;
             }
         }
         // segment-local flat index: same order as k * Tz + t inside the segment
@@ -357,31 +362,51 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
         const unsigned win = __ballot_sync(kFull, my == wm);
         if (lane == __ffs(win) - 1) {
             slot_key[buf * 32 + warp] = wm;
-            slot_z[buf * 32 + warp] = my_z;
-            slot_d[buf * 32 + warp] = my_d;
-            slot_k[buf * 32 + warp] = my_k;
-            slot_j[buf * 32 + warp] = myj;
+            slot_v[buf * 32 + warp] =
+                make_uint4(__float_as_uint(my_z), __float_as_uint(my_d), (unsigned)my_k, (unsigned)myj);
         }
         __syncthreads();
+        // every warp's candidate in one round of independent loads (up to 4
+        // warps; wider blocks read the winner's values after the key scan)
+        constexpr int NV = nwarps <= 4 ? nwarps : 1;
+        unsigned long long kv[NV];
+        uint4 vv[NV];
+#pragma unroll
+        for (int i = 0; i < NV; i++) {
+            kv[i] = slot_key[buf * 32 + i];
+            vv[i] = slot_v[buf * 32 + i];
+        }
         unsigned long long bk = 0ull;
         int bw = 0;
-        for (int i = 0; i < nwarps; i++) {
-            const unsigned long long kk = slot_key[buf * 32 + i];
-            if (kk > bk) {
-                bk = kk;
-                bw = i;
+        uint4 bv = vv[0];
+        if constexpr (nwarps <= 4) {
+#pragma unroll
+            for (int i = 0; i < nwarps; i++)
+                if (kv[i] > bk) {
+                    bk = kv[i];
+                    bw = i;
+                    bv = vv[i];
+                }
+        } else {
+            for (int i = 0; i < nwarps; i++) {
+                const unsigned long long kk = slot_key[buf * 32 + i];
+                if (kk > bk) {
+                    bk = kk;
+                    bw = i;
+                }
             }
+            bv = slot_v[buf * 32 + bw];
         }
         const float adz = __uint_as_float((unsigned)(bk >> 32));
         if (!(adz >= tol))
             break;
-        if (it >= pp.u) {
+        if (nupd >= pp.u) {
             capped = true;
             break;
         }
-        const float znew = slot_z[buf * 32 + bw], delta = slot_d[buf * 32 + bw];
-        const int k0 = slot_k[buf * 32 + bw];
-        const int64_t t0 = s + slot_j[buf * 32 + bw];
+        const float znew = __uint_as_float(bv.x), delta = __uint_as_float(bv.y);
+        const int k0 = (int)bv.z;
+        const int64_t t0 = s + (int)bv.w;
 
         // ---- Eq. beta_up (r form) on the window -------------------------
         const int64_t tlo = t0 - (L - 1);

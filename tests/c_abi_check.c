@@ -51,10 +51,11 @@ static void print_layouts(void)
            OFF(csc_shard_plan, col_count), OFF(csc_shard_plan, halo_left),
            OFF(csc_shard_plan, halo_right), OFF(csc_shard_plan, x_first),
            OFF(csc_shard_plan, x_count));
-    printf("csc2d_stats %u %u %u %u %u %u %u %u %u %u %u\n", (unsigned)sizeof(csc2d_stats),
+    printf("csc2d_stats %u %u %u %u %u %u %u %u %u %u %u %u %u\n", (unsigned)sizeof(csc2d_stats),
            OFF(csc2d_stats, updates), OFF(csc2d_stats, sweeps), OFF(csc2d_stats, bands),
-           OFF(csc2d_stats, phases), OFF(csc2d_stats, resyncs), OFF(csc2d_stats, converged),
-           OFF(csc2d_stats, objective), OFF(csc2d_stats, max_delta_z), OFF(csc2d_stats, solve_ms),
+           OFF(csc2d_stats, col_blocks), OFF(csc2d_stats, phases), OFF(csc2d_stats, resyncs),
+           OFF(csc2d_stats, converged), OFF(csc2d_stats, reserved), OFF(csc2d_stats, objective),
+           OFF(csc2d_stats, max_delta_z), OFF(csc2d_stats, solve_ms),
            OFF(csc2d_stats, kernel_launches));
     printf("csc_tune_result %u %u %u %u %u %u %u %u\n", (unsigned)sizeof(csc_tune_result),
            OFF(csc_tune_result, segment_width), OFF(csc_tune_result, updates_per_visit),
@@ -123,7 +124,7 @@ int main(int argc, char **argv)
         CHECK(csc_shard_phase(NULL, 0, 1e-6) == CSC_EINVAL);
         CHECK(csc2d_plan(121, 8, 8, &M, &c, starts) == CSC_OK);
         CHECK(M == 8 && c == 2 && starts[1] == 15);
-        CHECK(csc2d_solve(NULL, 1, 1, 2, 2, NULL, 4, 4, 0.1, 1e-6, 1, 0, 0, NULL, NULL, NULL,
+        CHECK(csc2d_solve(NULL, 1, 1, 2, 2, NULL, 4, 4, 0.1, 1e-6, 1, 0, 0, 0, NULL, NULL, NULL,
                           NULL) == CSC_EINVAL);
     }
     printf("ok\n");

@@ -70,10 +70,12 @@ def test_argument_validation_needs_no_device(lib):
     assert lib.csc_setup(ctypes.byref(h), D.ctypes.data, 0, 1, 4, None, None) == capi.CSC_EINVAL
     assert lib.csc_setup(ctypes.byref(h), D.ctypes.data, 2, 1, 513, None, None) == capi.CSC_EINVAL
     assert lib.csc_setup(ctypes.byref(h), None, 2, 1, 4, None, None) == capi.CSC_EINVAL
-    o = capi.make_opts()
-    o.launch_mode = 7
-    assert lib.csc_setup(ctypes.byref(h), D.ctypes.data, 2, 1, 4, ctypes.byref(o),
-                         None) == capi.CSC_EINVAL
+    for field, bad in (("launch_mode", 7), ("threads_per_segment", 64), ("init_mode", 4),
+                       ("segment_width", -1)):
+        o = capi.make_opts()
+        setattr(o, field, bad)
+        assert lib.csc_setup(ctypes.byref(h), D.ctypes.data, 2, 1, 4, ctypes.byref(o),
+                             None) == capi.CSC_EINVAL, field
     assert lib.csc_init(None, D.ctypes.data, 10, 1.0, None) == capi.CSC_EINVAL
     assert lib.csc_kkt(None, D.ctypes.data, D.ctypes.data) == capi.CSC_EINVAL
     assert "csc_kkt" in capi.csc_last_error_string()

@@ -1,6 +1,7 @@
 """The 2-D variant on the GPU (csc2d_solve, include/csc2d.h) against the 2-D
-FP64 oracle (oracle/csc2d_oracle.c): images cut into row bands, run in the
-band phase schedule.  Same bars as the 1-D parity tests: relative objective
+FP64 oracle (oracle/csc2d_oracle.c): images cut into row bands (N = 1, the
+paper's one-axis cut) or into tiles of row bands x column blocks (N = 0),
+run in their phase schedules; the oracle runs the band schedule.  Same bars as the 1-D parity tests: relative objective
 gap <= 1e-5, ||Z - Z*||_inf <= 1e-4 ||Z*||_inf, identical support outside
 |z| < 1e-6, with Z* the oracle's band-schedule optimum at eps = 1e-10."""
 import numpy as np
@@ -60,18 +61,20 @@ def assert_parity(Z, E, Zr, Er):
 
 
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("u", [0, 8])
-def test_band_solve_matches_oracle(capi, refs, name, u):
+@pytest.mark.parametrize("u", [0, 3, 1 << 20])
+@pytest.mark.parametrize("N", [0, 1, 3])
+def test_tile_solve_matches_oracle(capi, refs, name, u, N):
     pb, lam, M, Zr, Er = refs[name]
     K, P, h, w = pb.D.shape
     Hz, Wz = pb.X.shape[1] - h + 1, pb.X.shape[2] - w + 1
     Z = torch.zeros((K, Hz, Wz), dtype=torch.float32, device="cuda")
     status, E, st = capi.csc2d_solve(torch.from_numpy(pb.D).cuda(),
-                                     torch.from_numpy(pb.X).cuda(), lam, 1e-6, M=M,
+                                     torch.from_numpy(pb.X).cuda(), lam, 1e-6, M=M, N=N,
                                      updates_per_visit=u, Z_out=Z)
     assert status == capi.CSC_OK and st["converged"] == 1, st
-    Mo, c, _ = capi.csc2d_plan(Hz, h, M)
-    assert (st["bands"], st["phases"]) == (Mo, c)
+    Mo, cr, _ = capi.csc2d_plan(Hz, h, M)
+    No, cc, _ = capi.csc2d_plan(Wz, w, N)
+    assert (st["bands"], st["col_blocks"], st["phases"]) == (Mo, No, cr * cc)
     assert_parity(Z.cpu().numpy(), E, Zr, Er)
     # the library's objective is E(Z) of the returned Z
     assert E == pytest.approx(csc2d.objective(pb.D, pb.X, Z.cpu().numpy(), lam), rel=1e-10)
@@ -99,3 +102,7 @@ def test_rejects_bad_arguments(capi):
         capi.csc2d_solve(D, X, -1.0, 1e-6)
     with pytest.raises(capi.CscError):
         capi.csc2d_solve(D, X, 0.1, 1e-6, M=9)  # more bands than rows (Hz = 8)
+    with pytest.raises(capi.CscError):
+        capi.csc2d_solve(D, X, 0.1, 1e-6, N=9)  # more column blocks than columns
+    with pytest.raises(capi.CscError):
+        capi.csc2d_solve(D, X, 0.1, 1e-6, N=-1)
