@@ -665,7 +665,7 @@ int csc_init_batch(csc_handle_t h, const float *X, const int64_t *T, int n, cons
             CSC_CUDA(cudaMemset2DAsync(h->Z + h->a[i + 1] - h->L + 1, sizeof(float) * Tz, 0,
                                        sizeof(float) * (h->L - 1), h->K, s));
         CSC_CUDA(cudaMemsetAsync(h->sc->red, 0, sizeof(h->sc->red), s));
-        CSC_CUDA(launch_resync(h->d_sig, h->resync_tiles(), h->C, h->norms, h->K, h->L, 1,
+        CSC_CUDA(launch_resync(h->d_sig, h->resync_tiles(), h->Ct, h->norms, h->K, h->L, 1,
                                h->sc->red, 0, nullptr, 0.f, nullptr, nullptr, h->nz_lists(), s));
     } else {
         CSC_CUDA(cudaMemsetAsync(h->Z, 0, sizeof(float) * nz, s));
@@ -973,7 +973,7 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
             CSC_CUDA(cudaMemsetAsync(h->dirty, 0, (size_t)M, s));
         if (timed)
             CSC_CUDA(cudaEventRecord(h->ev_r0, s));
-        CSC_CUDA(launch_resync(h->d_sig, h->resync_tiles(), h->C, h->norms, h->K, h->L, 1,
+        CSC_CUDA(launch_resync(h->d_sig, h->resync_tiles(), h->Ct, h->norms, h->K, h->L, 1,
                                sc->red, 0, last ? nullptr : h->dirty, tol_inner, h->touched,
                                h->tile_rep, h->nz_lists(), s));
         if (timed)
@@ -1009,7 +1009,7 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
         CSC_CUDA(cudaMemsetAsync(sc->red, 0, sizeof(sc->red), s));
         if (timed)
             CSC_CUDA(cudaEventRecord(h->ev_r0, s));
-        CSC_CUDA(launch_resync(h->d_sig, h->resync_tiles(), h->C, h->norms, h->K, h->L, 0,
+        CSC_CUDA(launch_resync(h->d_sig, h->resync_tiles(), h->Ct, h->norms, h->K, h->L, 0,
                                sc->red, 0, nullptr, 0.f, h->touched, h->tile_rep, h->nz_lists(), s));
         if (timed) {
             CSC_CUDA(cudaEventRecord(h->ev_r1, s));
@@ -1328,7 +1328,7 @@ int csc_kkt(csc_handle_t h, const float *Z, double *out)
         d.Z = const_cast<float *>(Zd) + (d.Z - h->Z);
     CSC_CUDA(upload(&h->d_sig_alt, &h->cap_sig_alt, alt, s));
     CSC_CUDA(cudaMemsetAsync(h->sc->red, 0, sizeof(h->sc->red), s));
-    CSC_CUDA(launch_resync(h->d_sig_alt, h->resync_tiles(), h->C, h->norms, h->K, h->L, 0,
+    CSC_CUDA(launch_resync(h->d_sig_alt, h->resync_tiles(), h->Ct, h->norms, h->K, h->L, 0,
                            h->sc->red, 0, nullptr, 0.f, nullptr, nullptr, h->nz_lists(), s));
     h->launches += 2;
     unsigned long long red[8];

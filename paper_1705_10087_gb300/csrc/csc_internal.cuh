@@ -313,7 +313,8 @@ struct NzLists {
 // previous resync over the same tiles) and each tile reads the lists of the
 // tiles within L-1 columns instead of scanning Z; the tiles of a problem must
 // be consecutive in the table and in column order (both tables are).
-cudaError_t launch_resync(const SigDesc *sig, Tiles tiles, const float *C, const float *norms,
+// Ct: the by-lag table of PhaseParams::Ct (float4 groups of atoms).
+cudaError_t launch_resync(const SigDesc *sig, Tiles tiles, const float *Ct, const float *norms,
                           int K, int L, int write_r, unsigned long long *red, int red_stride,
                           unsigned char *dirty, float tol_mark, const unsigned char *touched,
                           float *rep, NzLists lists, cudaStream_t s);

@@ -21,9 +21,17 @@
 //     so one run of 16 + L16/8 core matrices per channel and split serves the
 //     whole tile, with equal leading and stride byte offsets (128 B): moving
 //     one core matrix along M or along K is the same step in memory.
-//   B, K-major (j contiguous): per 16-wide contraction step, N/8 x 2 core
-//     matrices, K-adjacent at 128 B, N-adjacent at 256 B; row k of core matrix
-//     (n8, j8) holds D[k = 8 n8 + r][p][tau = 16 s + 8 j8 + 0..7 - p L16].
+//   B, K-major (j contiguous): per 16-wide contraction step, the three
+//     splits one after the other, each N/8 x 2 core matrices, K-adjacent at
+//     128 B, N-adjacent at 256 B; row k of core matrix (n8, j8) of split
+//     sigma holds term sigma of D[k = 8 n8 + r][p][tau = 16 s + 8 j8 + 0..7 -
+//     p L16].  The splits of a step are thus one operand of 3N rows.
+// Concatenated products (N = 32, "cat"): per step one M x 3N product of the
+// leading term of X with [D_h D_m D_l] (hh, hm, hl), one M x 2N product of its
+// middle term with [D_h D_m] (mh, mm) and one M x N product of its last term
+// with D_h (lh), into one accumulator of 3N columns: hh + mh + lh, hm + mm
+// and hl, summed in the epilogue.  The tensor cores read each A run three
+// times per step instead of six.
 // The accumulator lives in tensor memory (N columns of 32-bit, lane = t); each
 // of the 4 warps reads its 32 lanes with tcgen05.ld and writes beta0[k][t]
 // coalesced along t.
@@ -170,7 +178,7 @@ struct TcLayout {
         a_off = o;
         o += 2 * (size_t)kSplits * P * NQ * 128;  // two operand buffers
         b_off = o;
-        o += (size_t)kSplits * nsteps * (N / 8) * 256;
+        o += (size_t)kSplits * nsteps * (N / 8) * 256;  // [step][split][n8][j8][r]
         pl_off = o;  // the three BF16 terms of the staged samples, [split][p][xw]
         o += (size_t)kSplits * P * xw * 2;
         o = (o + 15) & ~(size_t)15;
@@ -183,12 +191,12 @@ struct TcLayout {
 // At N = 32 three CTAs fit an SM's shared memory for short atoms (P = 1,
 // L = 200: 76 KB each); the register budget is set so that they also fit
 // its register file.
-template <int N>
+template <int N, bool CAT>
 __global__ void __launch_bounds__(kTcThreads, N <= 32 ? 3 : 1)
     dtx_tc_kernel(const float *__restrict__ D, const float *__restrict__ X, int K, int P, int L,
-                  long long T, int mode, float *__restrict__ beta0, float *__restrict__ r_out,
-                  unsigned int *__restrict__ absmax_bits, double *__restrict__ x2sum,
-                  int *__restrict__ err)
+                  long long T, int mode, float *__restrict__ beta0,
+                  float *__restrict__ r_out, unsigned int *__restrict__ absmax_bits,
+                  double *__restrict__ x2sum, int *__restrict__ err)
 {
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ uint32_t s_taddr;
@@ -202,11 +210,15 @@ __global__ void __launch_bounds__(kTcThreads, N <= 32 ? 3 : 1)
     const long long Tz = T - L + 1;
     const long long ntiles = (Tz + kTcM - 1) / kTcM;
 
-    // ---- tensor memory (two accumulators of N columns) and two barriers ------
+    // ---- tensor memory (two accumulators of N, or 3N when cat, columns; the
+    // allocation is a power of two) and two barriers ---------------------------
+    static_assert(!CAT || N == 32, "concatenated products need N = 32 (3N + 3N <= 256 columns)");
+    constexpr int acc_cols = CAT ? 3 * N : N;
+    constexpr uint32_t tm_cols = CAT ? 256u : 2u * N;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&s_taddr)),
-                     "r"(2 * N)
+                     "r"(tm_cols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -240,11 +252,12 @@ __global__ void __launch_bounds__(kTcThreads, N <= 32 ? 3 : 1)
             w[1][e2] = pack2(m[0], m[1]);
             w[2][e2] = pack2(l[0], l[1]);
         }
-        const size_t off = (((size_t)s * (N / 8) + n8) * 2 + j8) * 128 + (size_t)r * 16;
 #pragma unroll
-        for (int sg = 0; sg < kSplits; sg++)
-            *reinterpret_cast<uint4 *>(Bs + (size_t)sg * lay.nsteps * (N / 8) * 256 + off) =
-                make_uint4(w[sg][0], w[sg][1], w[sg][2], w[sg][3]);
+        for (int sg = 0; sg < kSplits; sg++) {
+            const size_t off =
+                ((((size_t)s * kSplits + sg) * (N / 8) + n8) * 2 + j8) * 128 + (size_t)r * 16;
+            *reinterpret_cast<uint4 *>(Bs + off) = make_uint4(w[sg][0], w[sg][1], w[sg][2], w[sg][3]);
+        }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     fence_before_sync();
@@ -252,6 +265,7 @@ __global__ void __launch_bounds__(kTcThreads, N <= 32 ? 3 : 1)
     fence_after_sync();
     const uint32_t taddr = s_taddr;
     const uint32_t idesc = mma_idesc(kTcM, N);
+    const uint32_t idesc_cat2 = mma_idesc(kTcM, 2 * N), idesc_cat3 = mma_idesc(kTcM, 3 * N);
     const size_t a_bytes = (size_t)kSplits * P * lay.NQ * 128;  // one operand buffer
     const uint32_t a_base = smem_u32(As), b_base = smem_u32(Bs);
 
@@ -346,16 +360,21 @@ __global__ void __launch_bounds__(kTcThreads, N <= 32 ? 3 : 1)
         // Descriptors differ only in their start address (16-byte units in the
         // low 14 bits, smem addresses < 256 KB): base descriptors plus the
         // per-step offsets tabulated at the start of the kernel.
-        const uint32_t d_acc = taddr + (uint32_t)(buf * N);
+        const uint32_t d_acc = taddr + (uint32_t)(buf * acc_cols);
         const uint64_t ad0 = mma_desc(a_base + (uint32_t)(buf * a_bytes), 128, 128);
         const uint64_t bd0 = mma_desc(b_base, 128, 256);
         const uint32_t a_split = (uint32_t)(P * lay.NQ * 128) >> 4;
-        const uint32_t b_split = (uint32_t)(lay.nsteps * (N / 8) * 256) >> 4;
+        const uint32_t b_split = (uint32_t)((N / 8) * 256) >> 4;
         uint32_t acc = 0;
         for (int s = 0; s < lay.nsteps; s++) {
             const uint64_t a_s = ad0 + s_aoff[s];
-            const uint64_t b_s = bd0 + ((uint32_t)(s * (N / 8) * 256) >> 4);
-            if (mode == 2) {
+            const uint64_t b_s = bd0 + ((uint32_t)(s * kSplits * (N / 8) * 256) >> 4);
+            if constexpr (CAT) {
+                // hh|hm|hl (first: it covers all 3N columns), mh|mm, lh
+                mma_bf16(d_acc, a_s, b_s, idesc_cat3, acc);
+                mma_bf16(d_acc, a_s + 1 * a_split, b_s, idesc_cat2, 1u);
+                mma_bf16(d_acc, a_s + 2 * a_split, b_s, idesc, 1u);
+            } else if (mode == 2) {
                 mma_bf16(d_acc, a_s, b_s, idesc, acc);
             } else {
                 mma_bf16(d_acc, a_s + 1 * a_split, b_s + 1 * b_split, idesc, acc);  // mm
@@ -372,11 +391,26 @@ __global__ void __launch_bounds__(kTcThreads, N <= 32 ? 3 : 1)
     // accumulator buf -> beta0 columns of the tile
     auto epilogue = [&](long long tile, int buf) {
         const long long t = tile * kTcM + 32 * warp + lane;
-        const uint32_t lane_addr = taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)(buf * N);
+        const uint32_t lane_addr =
+            taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)(buf * acc_cols);
 #pragma unroll
         for (int c = 0; c < N; c += 32) {
             float v[32];
-            tmem_ld32(lane_addr + (uint32_t)c, v);
+            if constexpr (CAT) {
+                // hl + (hm + mm) + (hh + mh + lh), smallest first
+                float u[32];
+                tmem_ld32(lane_addr + (uint32_t)(2 * N + c), v);
+                tmem_ld32(lane_addr + (uint32_t)(N + c), u);
+#pragma unroll
+                for (int i = 0; i < 32; i++)
+                    v[i] += u[i];
+                tmem_ld32(lane_addr + (uint32_t)c, u);
+#pragma unroll
+                for (int i = 0; i < 32; i++)
+                    v[i] += u[i];
+            } else {
+                tmem_ld32(lane_addr + (uint32_t)c, v);
+            }
             if (t < Tz) {
 #pragma unroll
                 for (int i = 0; i < 32; i++) {
@@ -446,7 +480,7 @@ __global__ void __launch_bounds__(kTcThreads, N <= 32 ? 3 : 1)
     fence_after_sync();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr),
-                     "r"(2 * N)
+                     "r"(tm_cols)
                      : "memory");
 }
 
@@ -495,7 +529,8 @@ cudaError_t launch_dtx_tc(const float *D, const float *X, int K, int P, int L, i
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    auto go = [&](auto kern) -> cudaError_t {
+    // max_per_sm: tensor-memory columns allow at most 512 / (columns per CTA)
+    auto go = [&](auto kern, int max_per_sm) -> cudaError_t {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e == cudaSuccess)
@@ -516,14 +551,29 @@ cudaError_t launch_dtx_tc(const float *D, const float *X, int K, int P, int L, i
         const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + 1024);
         const int by_regs = 65536 / (fa.numRegs * kTcThreads > 0 ? fa.numRegs * kTcThreads : 1);
         int per_sm = by_smem < by_regs ? by_smem : by_regs;
-        per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
+        per_sm = per_sm < 1 ? 1 : (per_sm > max_per_sm ? max_per_sm : per_sm);
+        // concatenated products where at most two CTAs share an SM: their
+        // accumulators take 256 of its 512 tensor-memory columns each
         const int64_t cap = (int64_t)nsm * per_sm;
         const unsigned grid = (unsigned)(ntiles < cap ? ntiles : cap);
         kern<<<grid, kTcThreads, smem, s>>>(D, X, K, P, L, (long long)T, mode, beta0, r_out,
                                            absmax_bits, x2sum, err);
         return cudaGetLastError();
     };
-    return K <= 32 ? go(dtx_tc_kernel<32>) : go(dtx_tc_kernel<64>);
+    if (K > 32)
+        return go(dtx_tc_kernel<64, false>, 4);
+    // concatenated products where shared memory holds at most two CTAs per
+    // SM (their accumulators take 256 of its 512 tensor-memory columns each);
+    // a smaller tile keeps three or more CTAs with the six narrow products
+    int smem_sm = 0;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess)
+        e = cudaFuncGetAttributes(&fa, dtx_tc_kernel<32, true>);
+    if (e != cudaSuccess)
+        return e;
+    const bool cat = mode == 1 && smem_sm / (int)(smem + fa.sharedSizeBytes + 1024) <= 2;
+    return cat ? go(dtx_tc_kernel<32, true>, 2) : go(dtx_tc_kernel<32, false>, 4);
 }
 
 cudaError_t launch_dtx_any(const float *D, const float *X, int K, int P, int L, int64_t T,

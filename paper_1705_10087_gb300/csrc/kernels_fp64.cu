@@ -139,9 +139,74 @@ __global__ void __launch_bounds__(256)
         lists.count[b] = base;
 }
 
+// The refreshed r of coordinate (k, t) of problem sd from beta0 and the
+// double-float sum (ah, al) of its S Z terms, and its share of the report:
+// drift |r_old - r|, zero_excess, nonzero_gap, max |Delta Z| and the
+// coord_step change on the float state (marking its segment dirty when that
+// change is >= tol_mark, or the problem's tol when tol_mark < 0).
+// (b0, rold, z, n: beta0, r, Z of the coordinate and ||D_k||^2, already loaded)
+__device__ __forceinline__ void resync_finish_v(const SigDesc &sd, int64_t ix, int64_t t,
+                                                float b0, float rold, float z, float n,
+                                                float *__restrict__ rr, float ah, float al,
+                                                float lam, int write_r,
+                                                unsigned char *__restrict__ dirty, float tol_mark,
+                                                float &drift, float &zex, float &nzg, float &all,
+                                                float &dz32)
+{
+    const int64_t Tz = sd.Tz;
+    // r = beta0 - (hi + lo), finished with TwoSum so that only the final
+    // float rounding remains
+    const float sm = __fsub_rn(b0, ah);
+    const float bv = __fsub_rn(sm, b0);
+    const float er = __fadd_rn(__fsub_rn(b0, __fsub_rn(sm, bv)), __fsub_rn(-ah, bv));
+    const float r32 = __fadd_rn(sm, __fsub_rn(er, al));
+    if (write_r)
+        rr[ix] = r32;
+    drift = fmaxf(drift, fabsf(rold - r32));
+    const float rn = __frcp_rn(n);
+    // optimality in the r form (Theorem A.1): z = 0 needs |beta| = |r| <= lam;
+    // otherwise |Z' - z| with Z' from Eq. pb_coord, without cancellation
+    float gap;
+    if (z == 0.f) {
+        zex = fmaxf(zex, fabsf(r32) - lam);
+        gap = soft_f(r32, lam) * rn;
+    } else {
+        const float sg = z > 0.f ? 1.f : -1.f;
+        const float b = fmaf(n, z, r32);
+        gap = b * sg > lam ? (r32 - lam * sg) * rn : soft_f(b, lam) * rn - z;
+        nzg = fmaxf(nzg, fabsf(gap));
+    }
+    all = fmaxf(all, fabsf(gap));
+    // the phase kernel's own test on the float state it will see
+    float zn, d32;
+    coord_step(write_r ? r32 : rold, z, n, rn, lam, &zn, &d32);
+    dz32 = fmaxf(dz32, fabsf(d32));
+    if (dirty && sd.nseg > 0 && fabsf(d32) >= (tol_mark < 0.f ? sd.tol : tol_mark))
+        dirty[sd.seg0 + segment_of(Tz, sd.nseg, t)] = 1;
+}
+
+// resync_finish_v with its loads
+__device__ __forceinline__ void resync_finish(const SigDesc &sd, int k, int64_t t,
+                                              const float *__restrict__ b0p,
+                                              float *__restrict__ rr,
+                                              const float *__restrict__ zz,
+                                              const float *__restrict__ norms, float ah, float al,
+                                              float lam, int write_r,
+                                              unsigned char *__restrict__ dirty, float tol_mark,
+                                              float &drift, float &zex, float &nzg, float &all,
+                                              float &dz32)
+{
+    const int64_t ix = (int64_t)k * sd.ld + t;
+    resync_finish_v(sd, ix, t, b0p[ix], rr[ix], zz[ix], norms[k], rr, ah, al, lam, write_r, dirty,
+                    tol_mark, drift, zex, nzg, all, dz32);
+}
+
+// KPT = 4 NG atoms per thread: thread group g (of kResyncGroups) owns the
+// float4 groups of atoms g, g + kResyncGroups, ... of the by-lag table, so
+// each listed nonzero costs one 16-byte coefficient load per group.
 template <int KPT>
-__global__ void __launch_bounds__(kResyncThreads)
-    resync_kernel(const SigDesc *__restrict__ sigs, Tiles tiles, const float *__restrict__ C,
+__global__ void __launch_bounds__(kResyncThreads, KPT <= 4 ? 3 : 1)
+    resync_kernel(const SigDesc *__restrict__ sigs, Tiles tiles, const float *__restrict__ Ct,
                   const float *__restrict__ norms, int K, int L, int write_r,
                   unsigned long long *__restrict__ red, int red_stride,
                   unsigned char *__restrict__ dirty, float tol_mark,
@@ -238,14 +303,18 @@ __global__ void __launch_bounds__(kResyncThreads)
         const int64_t b = a + chunk < hi ? a + chunk : hi;
         const int n = listed ? s_off[2 * R + 1] : compact_nonzeros(zz, K, ld, a, b, list, warp_counts);
         if (t < tend) {
-            // kGatherBatch nonzeros at a time: all their coefficients are loaded
-            // first (clamped to valid addresses), so that one L2 round trip
-            // serves the batch; a nonzero out of the window (or past n) adds
-            // the exact product 0 and leaves the sums unchanged
+            // NB nonzeros at a time: all their coefficients are loaded first
+            // (one float4 per atom group, clamped to valid addresses), so that
+            // one L2 round trip serves the batch; a nonzero out of the window
+            // (or past n) adds the exact product 0 and leaves the sums unchanged
             // (fewer at a time for many atoms per thread: registers)
-            constexpr int NB = KPT <= 8 ? kGatherBatch : (KPT <= 16 ? 2 : 1);
+            constexpr int NG = KPT / 4;
+            constexpr int NB = NG == 1 ? 2 * kGatherBatch : (NG == 2 ? kGatherBatch : (NG <= 4 ? 2 : 1));
+            const int G = (K + 3) / 4;  // float4 groups of the table
+            const float4 *Ct4 = reinterpret_cast<const float4 *>(Ct);
             for (int i0 = 0; i0 < n; i0 += NB) {
-                float cv[NB][KPT], zv[NB];
+                float4 cv[NB][NG];
+                float zv[NB];
 #pragma unroll
                 for (int b = 0; b < NB; b++) {
                     const int i = i0 + b < n ? i0 + b : n - 1;
@@ -253,19 +322,24 @@ __global__ void __launch_bounds__(kResyncThreads)
                     const int d = (int)(t - e.t) + (L - 1);
                     const bool in = i0 + b < n && d >= 0 && d < W2;
                     zv[b] = in ? e.z : 0.f;
-                    const float *Cl = C + (int64_t)e.k * K * W2 + (in ? d : 0);
+                    const int64_t base = (int64_t)e.k * G * W2 + (in ? d : 0);
 #pragma unroll
-                    for (int q = 0; q < KPT; q++) {
-                        const int k = grp + q * kResyncGroups;
-                        cv[b][q] = __ldg(Cl + (int64_t)(k < K ? k : K - 1) * W2);
+                    for (int gi = 0; gi < NG; gi++) {
+                        const int g = grp + gi * kResyncGroups;
+                        cv[b][gi] = g < G ? __ldg(Ct4 + base + (int64_t)g * W2)
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
                     }
                 }
 #pragma unroll
                 for (int b = 0; b < NB; b++)
 #pragma unroll
-                    for (int q = 0; q < KPT; q++)
-                        if (zv[b] != 0.f)
-                            df_add_prod(acc_hi[q], acc_lo[q], cv[b][q], zv[b]);
+                    for (int gi = 0; gi < NG; gi++)
+                        if (zv[b] != 0.f) {
+                            df_add_prod(acc_hi[4 * gi], acc_lo[4 * gi], cv[b][gi].x, zv[b]);
+                            df_add_prod(acc_hi[4 * gi + 1], acc_lo[4 * gi + 1], cv[b][gi].y, zv[b]);
+                            df_add_prod(acc_hi[4 * gi + 2], acc_lo[4 * gi + 2], cv[b][gi].z, zv[b]);
+                            df_add_prod(acc_hi[4 * gi + 3], acc_lo[4 * gi + 3], cv[b][gi].w, zv[b]);
+                        }
             }
         }
         __syncthreads();
@@ -275,42 +349,11 @@ __global__ void __launch_bounds__(kResyncThreads)
     if (t < tend) {
 #pragma unroll
         for (int q = 0; q < KPT; q++) {
-            const int k = grp + q * kResyncGroups;
+            const int k = 4 * (grp + (q / 4) * kResyncGroups) + (q % 4);
             if (k >= K)
                 continue;
-            const int64_t ix = (int64_t)k * ld + t;
-            // r = beta0 - (hi + lo), finished with TwoSum so that only the final
-            // float rounding remains
-            const float b0 = b0p[ix], ah = acc_hi[q], al = acc_lo[q];
-            const float sm = __fsub_rn(b0, ah);
-            const float bv = __fsub_rn(sm, b0);
-            const float er = __fadd_rn(__fsub_rn(b0, __fsub_rn(sm, bv)), __fsub_rn(-ah, bv));
-            const float r32 = __fadd_rn(sm, __fsub_rn(er, al));
-            const float rold = rr[ix];
-            if (write_r)
-                rr[ix] = r32;
-            drift = fmaxf(drift, fabsf(rold - r32));
-            const float z = zz[ix];
-            const float n = norms[k], rn = __frcp_rn(n);
-            // optimality in the r form (Theorem A.1): z = 0 needs |beta| = |r| <= lam;
-            // otherwise |Z' - z| with Z' from Eq. pb_coord, without cancellation
-            float gap;
-            if (z == 0.f) {
-                zex = fmaxf(zex, fabsf(r32) - lam);
-                gap = soft_f(r32, lam) * rn;
-            } else {
-                const float sg = z > 0.f ? 1.f : -1.f;
-                const float b = fmaf(n, z, r32);
-                gap = b * sg > lam ? (r32 - lam * sg) * rn : soft_f(b, lam) * rn - z;
-                nzg = fmaxf(nzg, fabsf(gap));
-            }
-            all = fmaxf(all, fabsf(gap));
-            // the phase kernel's own test on the float state it will see
-            float zn, d32;
-            coord_step(write_r ? r32 : rold, z, n, rn, lam, &zn, &d32);
-            dz32 = fmaxf(dz32, fabsf(d32));
-            if (dirty && sd.nseg > 0 && fabsf(d32) >= (tol_mark < 0.f ? sd.tol : tol_mark))
-                dirty[sd.seg0 + segment_of(Tz, sd.nseg, t)] = 1;
+            resync_finish(sd, k, t, b0p, rr, zz, norms, acc_hi[q], acc_lo[q], lam, write_r, dirty,
+                          tol_mark, drift, zex, nzg, all, dz32);
         }
     }
     }  // need
@@ -339,6 +382,224 @@ __global__ void __launch_bounds__(kResyncThreads)
         if (need && rep)
             for (int q = 0; q < 5; q++)
                 rep[5 * blockIdx.x + q] = v[q];
+        unsigned long long *rd = red + (int64_t)isig * red_stride;
+        for (int q = 0; q < 5; q++)
+            atomicMax(&rd[q], (unsigned long long)__double_as_longlong((double)v[q]));
+    }
+}
+
+// The resync with a few warps per tile (lane = column): the tiles of a long
+// signal are many and each needs little arithmetic (a few nonzeros reach a
+// 32-column tile at the optimum), so what bounds a tile is its chain of
+// dependent memory round trips; small blocks keep many tiles in flight on an
+// SM and need no barrier before the final reduction.  Block = WPT warps of
+// one tile; warp q owns the float4 atom groups [q NG, (q+1) NG) of the
+// by-lag table, and each lane loads the coefficients of NB nonzeros, and the
+// state of its NG x 4 coordinates, in one round.  The nonzeros are read from
+// the buckets in the same order as resync_kernel (bucket, then (k, column)),
+// or, when a bucket overflowed or no lists are given, gathered from Z in that
+// same order with ballots: results are identical either way.  Needs 2R+1 <=
+// 32 buckets, R = ceil((L-1)/32) (L <= 481), and K <= 64 (at most 8 warps).
+template <int NG>
+__global__ void __launch_bounds__(256, 2)
+    resync_warp_kernel(const SigDesc *__restrict__ sigs, Tiles tiles, const float *__restrict__ Ct,
+                       const float *__restrict__ norms, int K, int L, int write_r,
+                       unsigned long long *__restrict__ red, int red_stride,
+                       unsigned char *__restrict__ dirty, float tol_mark,
+                       const unsigned char *__restrict__ touched, float *__restrict__ rep,
+                       NzLists lists)
+{
+    constexpr int KPT = 4 * NG;
+    constexpr int NB = NG == 1 ? 8 : 4;  // nonzeros whose coefficients are loaded together
+    constexpr unsigned kFullMask = 0xffffffffu;
+    __shared__ float bred[5][32];
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5, nwq = blockDim.x >> 5;
+    const int64_t b = blockIdx.x;
+    const int isig = tiles.sig[b];
+    const SigDesc sd = sigs[isig];
+    const int64_t Tz = sd.Tz, ld = sd.ld;
+    float *__restrict__ const rr = sd.r;
+    const float *__restrict__ const zz = sd.Z;
+    const float *__restrict__ const b0p = sd.beta0;
+    const int W2 = 2 * L - 1;
+    const int G = (K + 3) / 4;  // float4 groups of the table
+    const int g0 = wq * NG;     // this warp's first group
+    const int64_t c0 = tiles.start[b];
+    const int64_t t = c0 + lane;
+    const int64_t tend = tiles.end && tiles.end[b] < Tz ? tiles.end[b] : Tz;
+    const bool col_ok = t < tend;
+    float drift = 0.f, zex = 0.f, nzg = 0.f, all = 0.f, dz32 = 0.f;
+    const bool need = !(touched && rep) || tile_touched(sd, c0, touched);
+    if (!need) {
+        if (lane == 0 && wq == 0) {  // the stored report of the unchanged tile (drift 0)
+            zex = rep[5 * b + 1];
+            nzg = rep[5 * b + 2];
+            all = rep[5 * b + 3];
+            dz32 = rep[5 * b + 4];
+        }
+    } else {
+        // this lane's coordinates: its state first (one round trip for all)
+        float b0v[KPT], rov[KPT], zv[KPT], nv[KPT];
+#pragma unroll
+        for (int q = 0; q < KPT; q++) {
+            const int k = 4 * (g0 + q / 4) + (q % 4);
+            const bool ok = col_ok && k < K;
+            const int64_t ix = (int64_t)(ok ? k : 0) * ld + (ok ? t : 0);
+            b0v[q] = ok ? b0p[ix] : 0.f;
+            rov[q] = ok ? rr[ix] : 0.f;
+            zv[q] = ok ? zz[ix] : 0.f;
+            nv[q] = ok ? norms[k] : 1.f;
+        }
+        float acc_hi[KPT], acc_lo[KPT];
+#pragma unroll
+        for (int i = 0; i < KPT; i++) {
+            acc_hi[i] = 0.f;
+            acc_lo[i] = 0.f;
+        }
+        const float4 *Ct4 = reinterpret_cast<const float4 *>(Ct);
+        // NB nonzeros (k, column, z) at a time: loads first, then the sums; a
+        // nonzero out of this lane's window (z = 0 there) adds nothing
+        auto add_batch = [&](const int (&kk)[NB], const int64_t (&tc)[NB], const float (&z)[NB]) {
+            float4 cv[NB][NG];
+            float zz_[NB];
+#pragma unroll
+            for (int e = 0; e < NB; e++) {
+                const int d = (int)(t - tc[e]) + (L - 1);
+                const bool in = col_ok && z[e] != 0.f && d >= 0 && d < W2;
+                zz_[e] = in ? z[e] : 0.f;
+                const int64_t base = (int64_t)kk[e] * G * W2 + (in ? d : 0);
+#pragma unroll
+                for (int gi = 0; gi < NG; gi++)
+                    cv[e][gi] = in && g0 + gi < G ? __ldg(Ct4 + base + (int64_t)(g0 + gi) * W2)
+                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int e = 0; e < NB; e++)
+                if (zz_[e] != 0.f) {
+#pragma unroll
+                    for (int gi = 0; gi < NG; gi++) {
+                        df_add_prod(acc_hi[4 * gi], acc_lo[4 * gi], cv[e][gi].x, zz_[e]);
+                        df_add_prod(acc_hi[4 * gi + 1], acc_lo[4 * gi + 1], cv[e][gi].y, zz_[e]);
+                        df_add_prod(acc_hi[4 * gi + 2], acc_lo[4 * gi + 2], cv[e][gi].z, zz_[e]);
+                        df_add_prod(acc_hi[4 * gi + 3], acc_lo[4 * gi + 3], cv[e][gi].w, zz_[e]);
+                    }
+                }
+        };
+        // buckets b-R .. b+R of the same problem: lane j holds bucket b-R+j
+        const int R = (L - 1 + kResyncCols - 1) / kResyncCols;
+        int cnt = 0;
+        if (lists.count && lane <= 2 * R) {
+            const int64_t bb = b - R + lane;
+            const bool valid = bb >= 0 && bb < tiles.n && tiles.sig[bb] == isig &&
+                               tiles.start[bb] == c0 + (int64_t)(lane - R) * kResyncCols;
+            cnt = valid ? lists.count[bb] : 0;
+        }
+        const bool listed = lists.count && !__any_sync(kFullMask, cnt > kNzCap);
+        if (listed) {
+            // entries in bucket order: prefix of the counts over the lanes
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(kFullMask, incl, o);
+                if (lane >= o)
+                    incl += v;
+            }
+            const int total = __shfl_sync(kFullMask, incl, 31);
+            const int excl = incl - cnt;
+            for (int e0 = 0; e0 < total; e0 += 32) {
+                // lane l fetches entry e0 + l: its bucket j is the last one with
+                // excl_j <= e (empty buckets before it are passed over)
+                const int e = e0 + lane;
+                int j = 0;
+                for (int q = 0; q <= 2 * R; q++)
+                    if (e >= __shfl_sync(kFullMask, excl, q))
+                        j = q;
+                const int xj = __shfl_sync(kFullMask, excl, j);
+                const uint2 v = e < total ? lists.ent[(b - R + j) * kNzCap + (e - xj)]
+                                          : make_uint2(0u, 0u);
+                const int64_t cb = c0 + (int64_t)(j - R) * kResyncCols;
+                const int m = total - e0 < 32 ? total - e0 : 32;
+                for (int i0 = 0; i0 < m; i0 += NB) {
+                    int kk[NB];
+                    int64_t tc[NB];
+                    float z[NB];
+#pragma unroll
+                    for (int x = 0; x < NB; x++) {
+                        const int src = i0 + x < m ? i0 + x : 0;
+                        const unsigned vx = __shfl_sync(kFullMask, v.x, src);
+                        const float zx = __uint_as_float(__shfl_sync(kFullMask, v.y, src));
+                        kk[x] = (int)(vx / kResyncCols);
+                        tc[x] = __shfl_sync(kFullMask, cb, src) + (vx % kResyncCols);
+                        z[x] = i0 + x < m ? zx : 0.f;
+                    }
+                    add_batch(kk, tc, z);
+                }
+            }
+        } else {
+            // from Z itself, bucket by bucket, (k, column) order by ballots;
+            // every column of the problem counts here, also those no tile of
+            // the table computes (a shard's halo)
+            for (int q = 0; q <= 2 * R; q++) {
+                const int64_t cb = c0 + (int64_t)(q - R) * kResyncCols;
+                if (cb + kResyncCols <= 0 || cb >= Tz)
+                    continue;
+                const int64_t tq = cb + lane;
+                const bool in = tq >= 0 && tq < Tz;
+                for (int k = 0; k < K; k++) {
+                    const float zq = in ? zz[(int64_t)k * ld + tq] : 0.f;
+                    unsigned msk = __ballot_sync(kFullMask, zq != 0.f);
+                    while (msk) {
+                        int kk[NB];
+                        int64_t tc[NB];
+                        float z[NB];
+#pragma unroll
+                        for (int x = 0; x < NB; x++) {
+                            const int src = msk ? __ffs((int)msk) - 1 : 0;
+                            const float zx = __shfl_sync(kFullMask, zq, src);
+                            kk[x] = k;
+                            tc[x] = cb + src;
+                            z[x] = msk ? zx : 0.f;
+                            msk &= msk - 1;
+                        }
+                        add_batch(kk, tc, z);
+                    }
+                }
+            }
+        }
+        const float lam = sd.lam;
+        if (col_ok) {
+#pragma unroll
+            for (int q = 0; q < KPT; q++) {
+                const int k = 4 * (g0 + q / 4) + (q % 4);
+                if (k < K)
+                    resync_finish_v(sd, (int64_t)k * ld + t, t, b0v[q], rov[q], zv[q], nv[q], rr,
+                                    acc_hi[q], acc_lo[q], lam, write_r, dirty, tol_mark, drift,
+                                    zex, nzg, all, dz32);
+            }
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        drift = fmaxf(drift, __shfl_xor_sync(kFullMask, drift, off));
+        zex = fmaxf(zex, __shfl_xor_sync(kFullMask, zex, off));
+        nzg = fmaxf(nzg, __shfl_xor_sync(kFullMask, nzg, off));
+        all = fmaxf(all, __shfl_xor_sync(kFullMask, all, off));
+        dz32 = fmaxf(dz32, __shfl_xor_sync(kFullMask, dz32, off));
+    }
+    float v[5] = {drift, zex, nzg, all, dz32};
+    if (nwq > 1) {
+        if (lane == 0)
+            for (int q = 0; q < 5; q++)
+                bred[q][wq] = v[q];
+        __syncthreads();
+        if (wq == 0 && lane == 0)
+            for (int w = 1; w < nwq; w++)
+                for (int q = 0; q < 5; q++)
+                    v[q] = fmaxf(v[q], bred[q][w]);
+    }
+    if (wq == 0 && lane == 0) {
+        if (need && rep)
+            for (int q = 0; q < 5; q++)
+                rep[5 * b + q] = v[q];
         unsigned long long *rd = red + (int64_t)isig * red_stride;
         for (int q = 0; q < 5; q++)
             atomicMax(&rd[q], (unsigned long long)__double_as_longlong((double)v[q]));
@@ -557,7 +818,7 @@ __global__ void beta_from_r_kernel(const float *__restrict__ r, const float *__r
 }
 
 template <int KPT>
-cudaError_t resync_launch(const SigDesc *sig, Tiles tiles, const float *C, const float *norms,
+cudaError_t resync_launch(const SigDesc *sig, Tiles tiles, const float *Ct, const float *norms,
                           int K, int L, int write_r, unsigned long long *red, int red_stride,
                           unsigned char *dirty, float tol_mark, const unsigned char *touched,
                           float *rep, NzLists lists, cudaStream_t s)
@@ -570,33 +831,56 @@ cudaError_t resync_launch(const SigDesc *sig, Tiles tiles, const float *C, const
             return e;
     }
     resync_kernel<KPT><<<(unsigned)tiles.n, kResyncThreads, 0, s>>>(
-        sig, tiles, C, norms, K, L, write_r, red, red_stride, dirty, tol_mark, touched, rep,
+        sig, tiles, Ct, norms, K, L, write_r, red, red_stride, dirty, tol_mark, touched, rep,
         lists);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_resync(const SigDesc *sig, Tiles tiles, const float *C, const float *norms,
+cudaError_t launch_resync(const SigDesc *sig, Tiles tiles, const float *Ct, const float *norms,
                           int K, int L, int write_r, unsigned long long *red, int red_stride,
                           unsigned char *dirty, float tol_mark, const unsigned char *touched,
                           float *rep, NzLists lists, cudaStream_t s)
 {
     if (tiles.n <= 0)
         return cudaSuccess;
-    const int kpt = (K + kResyncGroups - 1) / kResyncGroups;
+    const int G = (K + 3) / 4;  // float4 groups of atoms
+    const int R = (L - 1 + kResyncCols - 1) / kResyncCols;
+    if (2 * R + 1 <= 32 && G <= 16) {
+        // a few warps per tile: NG groups per warp, ceil(G / NG) warps
+        const int ng = G <= 1 ? 1 : 2;
+        const int wpt = (G + ng - 1) / ng;
+        if (lists.count) {
+            const int64_t blocks = (tiles.n + 7) / 8;
+            nz_bucket_kernel<<<(unsigned)blocks, 256, 0, s>>>(sig, tiles, K, touched, lists);
+            const cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess)
+                return e;
+        }
+#define CSC_RESYNC_W(N) \
+    resync_warp_kernel<N><<<(unsigned)tiles.n, 32 * wpt, 0, s>>>(                            \
+        sig, tiles, Ct, norms, K, L, write_r, red, red_stride, dirty, tol_mark, touched, rep, \
+        lists);                                                                                \
+    return cudaGetLastError()
+        if (ng == 1) {
+            CSC_RESYNC_W(1);
+        }
+        CSC_RESYNC_W(2);
+#undef CSC_RESYNC_W
+    }
+    // float4 groups of atoms per thread group
+    const int ngb = (G + kResyncGroups - 1) / kResyncGroups;
 #define CSC_RESYNC(N) \
-    return resync_launch<N>(sig, tiles, C, norms, K, L, write_r, red, red_stride, dirty, \
+    return resync_launch<N>(sig, tiles, Ct, norms, K, L, write_r, red, red_stride, dirty, \
                             tol_mark, touched, rep, lists, s)
-    if (kpt <= 2)
-        CSC_RESYNC(2);
-    if (kpt <= 4)
+    if (ngb <= 1)
         CSC_RESYNC(4);
-    if (kpt <= 8)
+    if (ngb <= 2)
         CSC_RESYNC(8);
-    if (kpt <= 16)
+    if (ngb <= 4)
         CSC_RESYNC(16);
-    if (kpt <= 32)  // K <= 256 (csc_setup, the server)
+    if (ngb <= 8)  // K <= 256 (csc_setup, the server)
         CSC_RESYNC(32);
 #undef CSC_RESYNC
     return cudaErrorInvalidValue;

@@ -481,7 +481,7 @@ int resync_ended(csc_server_t s, Group &g)
     const Tiles tiles{g.d_tsig, g.d_tstart, (int64_t)g.t_sig.size()};
     SRV_CUDA(grow(&g.d_nzc, &g.cap_nzc, g.t_sig.size()));
     SRV_CUDA(grow(&g.d_nze, &g.cap_nze, g.t_sig.size() * kNzCap));
-    SRV_CUDA(launch_resync(g.d_sig, tiles, g.C, g.norms, g.K, g.L, 1, g.d_red, kRed, g.dirty,
+    SRV_CUDA(launch_resync(g.d_sig, tiles, g.Ct, g.norms, g.K, g.L, 1, g.d_red, kRed, g.dirty,
                            -1.f, nullptr, nullptr, NzLists{g.d_nzc, g.d_nze}, g.st));
     count_dirty_kernel<<<n, 256, 0, g.st>>>(g.dirty, g.d_sig, g.d_cnt);
     SRV_CUDA(cudaGetLastError());

@@ -465,7 +465,7 @@ int csc_shard_resync(csc_handle_t h, double tol, double *max_dz)
     Tiles tiles{sh.d_rt_sig, sh.d_rt_s, sh.n_rt, sh.d_rt_e};
     // the owned columns only (the halo keeps the changes still to send); the
     // nonzeros are gathered by scanning Z, halo columns included
-    SH_CUDA(launch_resync(h->d_sig, tiles, h->C, h->norms, h->K, h->L, 1, h->sc->red, 0, nullptr,
+    SH_CUDA(launch_resync(h->d_sig, tiles, h->Ct, h->norms, h->K, h->L, 1, h->sc->red, 0, nullptr,
                           0.f, nullptr, nullptr, NzLists{nullptr, nullptr}, s));
     h->launches += 1;
     // every owned segment is visited again in the next round
