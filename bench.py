@@ -675,6 +675,7 @@ def main():
         ev[2].record(stream)
         if status != capi.CSC_OK:
             raise RuntimeError(f"solve did not converge: {st}")
+        st["beta0_ms"] = capi.csc_init_time(h)  # (after the solve: no extra wait)
         return E, st
 
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)]
@@ -786,6 +787,7 @@ def main():
         "updates_per_step": updates / args.steps,
         # live device time of a step by part (CUDA events inside the library)
         "breakdown_ms": {"setup_and_init": statistics.mean(init_ms),
+                         "beta0_kernel": statistics.mean(s["beta0_ms"] for s in sts),
                          "phase_kernels": phase_ms / args.steps,
                          "resyncs": sum(s["resync_ms"] for s in sts) / args.steps,
                          "objective": sum(s["objective_ms"] for s in sts) / args.steps,

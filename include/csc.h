@@ -78,8 +78,8 @@ typedef struct csc_opts {
                                   every |Delta Z| below tol, else CSC_NOT_CONVERGED.
                                   -1 = default (3); 0 = none (the status is then the float32
                                   loop's own test; stats.max_delta_z reports the exact one) */
-    int32_t sweeps_per_poll;   /* sweeps enqueued between two host convergence polls;
-                                  0 = default (4) */
+    int32_t sweeps_per_poll;   /* sweeps between two convergence tests (a batch); 0 =
+                                  default (4) */
     int32_t max_sweeps;        /* 0 = default (1,000,000) */
     int32_t time_kernels;      /* 1 = time every phase launch with a CUDA event pair
                                   (csc_stats.phase_ms); 0 = off */
@@ -94,10 +94,11 @@ typedef struct csc_opts {
                                   compensated sums; 0 = automatic: mode 1 where one of its
                                   CTAs fits on an SM (shared memory grows with P * L), else
                                   mode 3.  Modes 1-2 need K <= 64; other sizes use mode 3 */
-    int32_t launch_mode;       /* 0 = each poll batch (sweeps_per_poll sweeps of the c phases)
-                                  is replayed from a CUDA graph, captured the second time a
-                                  plan is solved (a plan solved once runs direct launches);
-                                  1 = direct kernel launches.  Same results */
+    int32_t launch_mode;       /* 0 = each CD round runs as one CUDA graph, a while loop over
+                                  batches whose convergence test runs on the device (captured
+                                  the second time a plan is solved; a plan solved once runs
+                                  direct launches with a host wait per batch); 1 = direct
+                                  kernel launches.  Same results */
     int32_t threads_per_segment; /* threads that run one segment's visit: 0 = automatic
                                   (a block), 128 = a block of at least 2L-1 threads per
                                   segment, 32 = one warp per segment where eligible (K =

@@ -202,6 +202,37 @@ int build_plan(csc_handle_t h)
     return CSC_OK;
 }
 
+// Per-signal objectives of Zd into pinned h->E_pin, not waited for.
+int objectives_async(csc_handle_t h, const float *Zd)
+{
+    cudaStream_t s = h->stream;
+    if (h->cap_E_pin < (size_t)h->n) {
+        CSC_CUDA(cudaStreamSynchronize(s));  // (the old block may still be written)
+        if (h->E_pin)
+            cudaFreeHost(h->E_pin);
+        h->E_pin = nullptr;
+        h->cap_E_pin = 0;
+        CSC_CUDA(cudaHostAlloc(&h->E_pin, sizeof(double) * h->n, cudaHostAllocDefault));
+        h->cap_E_pin = (size_t)h->n;
+    }
+    CSC_CUDA(launch_objective(h->D, h->d_sig, h->n, h->obj_tiles(), h->d_tile_off, h->K, h->P,
+                              h->L, h->Z, Zd == h->Z ? nullptr : Zd, h->partials, h->d_E, s));
+    h->launches += 2;
+    CSC_CUDA(cudaMemcpyAsync(h->E_pin, h->d_E, sizeof(double) * h->n, cudaMemcpyDeviceToHost, s));
+    return CSC_OK;
+}
+
+// h->E_sig from E_pin (after the stream has been waited for), and their sum.
+double objectives_done(csc_handle_t h)
+{
+    double t = 0.0;
+    for (int i = 0; i < h->n; i++) {
+        h->E_sig[i] = h->E_pin[i];
+        t += h->E_pin[i];
+    }
+    return t;
+}
+
 // Per-signal objectives into h->E_sig (and their sum).
 int objectives(csc_handle_t h, const float *Zd, double *sum)
 {
@@ -252,8 +283,12 @@ int issue_batch(csc_handle_t h, PhaseParams gp, const PhaseConfig &cfg, int S, i
     return CSC_OK;
 }
 
-// The graph of one poll batch for these parameters, captured on first use and
-// re-used while nothing it depends on changes (same buffers, plan, options).
+// The graph of a CD round for these parameters: a while loop over poll
+// batches (S sweeps of the c phases), each ended by launch_round_step, which
+// stops the loop on the round's stopping rules (the limits in
+// Scratch::round_lim), so that the host waits once per round instead of once
+// per batch.  Captured the second time a plan is solved and re-used while
+// nothing it depends on changes (same buffers, plan, options).
 int batch_graph(csc_handle_t h, const PhaseParams &pp, const PhaseConfig &cfg, int S,
                 int resident, int *gctr, cudaGraphExec_t *out)
 {
@@ -294,18 +329,43 @@ int batch_graph(csc_handle_t h, const PhaseParams &pp, const PhaseConfig &cfg, i
     if (!h->cap_stream)
         CSC_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     cudaStream_t s = h->cap_stream;
-    CSC_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    int rc = issue_batch(h, gp, cfg, S, resident, 0, 0, s);
-    cudaError_t e = cudaSuccess;
-    if (rc == CSC_OK)
-        e = launch_add_int(gctr, S * h->c, s);
     cudaGraph_t graph = nullptr;
-    const cudaError_t ee = cudaStreamEndCapture(s, &graph);
+    CSC_CUDA(cudaGraphCreate(&graph, 0));
+    // while (cond) { one poll batch; launch_round_step }, cond = 1 at each launch
+    cudaGraphConditionalHandle cond;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&cond, graph, 1u, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    if (e == cudaSuccess)
+        e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+    int rc = CSC_OK;
+    if (e == cudaSuccess) {
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            rc = issue_batch(h, gp, cfg, S, resident, 0, 0, s);
+            cudaError_t e2 = cudaSuccess;
+            if (rc == CSC_OK)
+                e2 = launch_round_step(cond, gctr, S * h->c, &h->sc->done, &h->sc->total,
+                                       h->sc->round_lim, s);
+            cudaGraph_t captured = nullptr;
+            e = cudaStreamEndCapture(s, &captured);
+            if (e == cudaSuccess)
+                e = e2;
+        }
+    }
     h->launches = launches;  // captured, not launched
-    if (rc != CSC_OK)
-        return rc;
-    CSC_CUDA(e);
-    CSC_CUDA(ee);
+    if (rc != CSC_OK || e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        if (rc != CSC_OK)
+            return rc;
+        CSC_CUDA(e);
+    }
     e = cudaGraphInstantiate(&h->gexec, graph, 0);
     cudaGraphDestroy(graph);
     CSC_CUDA(e);
@@ -412,6 +472,10 @@ int csc_destroy(csc_handle_t h)
         cudaFreeHost(h->poll);
     if (h->init_pin)
         cudaFreeHost(h->init_pin);
+    if (h->fin)
+        cudaFreeHost(h->fin);
+    if (h->E_pin)
+        cudaFreeHost(h->E_pin);
     if (h->ev_init)
         cudaEventDestroy(h->ev_init);
     if (h->ev_copy)
@@ -497,6 +561,8 @@ int csc_setup(csc_handle_t *hp, const float *D, int K, int P, int L, const csc_o
             CSC_CUDA(cudaMalloc(&h->sc, sizeof(Scratch)));
         if (!h->poll)
             CSC_CUDA(cudaHostAlloc(&h->poll, sizeof(Poll), cudaHostAllocDefault));
+        if (!h->fin)
+            CSC_CUDA(cudaHostAlloc(&h->fin, sizeof(Fin), cudaHostAllocDefault));
         if (!h->ev0)
             CSC_CUDA(cudaEventCreate(&h->ev0));
         if (!h->ev1)
@@ -508,8 +574,10 @@ int csc_setup(csc_handle_t *hp, const float *D, int K, int P, int L, const csc_o
         CSC_CUDA(launch_dtd(h->D, K, P, L, h->C, h->norms, h->stream));
         CSC_CUDA(launch_coef_by_lag(h->C, K, L, h->Ct, h->stream));
         h->launches += 2;
-        // D may be reused once this returns; the kernels run on
-        CSC_CUDA(cudaEventSynchronize(h->ev_copy));
+        // D may be reused once this returns (a copy from pinned host memory
+        // is asynchronous: wait for it; the kernels run on)
+        if (is_pinned_host(D))
+            CSC_CUDA(cudaEventSynchronize(h->ev_copy));
         return CSC_OK;
     };
     int rc = body();
@@ -679,7 +747,8 @@ int csc_init_batch(csc_handle_t h, const float *X, const int64_t *T, int n, cons
     h->init_pending = true;
     // the inputs may be reused once this returns (a copy from pinned host
     // memory is asynchronous): wait for the copies, not for the kernels
-    CSC_CUDA(cudaEventSynchronize(h->ev_copy));
+    if (is_pinned_host(X) || (Z0 && is_pinned_host(Z0)))
+        CSC_CUDA(cudaEventSynchronize(h->ev_copy));
     h->z_is_zero = Z0 == nullptr;
     h->initialized = true;
     return CSC_OK;
@@ -876,16 +945,17 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
             int nb = 0;  // launches in this poll batch
             const bool graphed = gexec && g + (int64_t)S * c <= kPhaseRing;
             if (graphed) {
+                // the round runs on the device, batch after batch, until one of
+                // the stopping rules tested below holds (launch_round_step)
+                CSC_CUDA(launch_set_limits(sc->round_lim, max_updates,
+                                           max_resyncs > 0 ? (long long)kDriftSweeps * c : 0,
+                                           (long long)max_sweeps * c, kPhaseRing, s));
                 if (timed)
                     CSC_CUDA(cudaEventRecord(h->kev[0], s));
                 CSC_CUDA(cudaGraphLaunch(gexec, s));
                 if (timed)
                     CSC_CUDA(cudaEventRecord(h->kev[1], s));
-                h->launches += 1;  // the counter advance
-                for (int p = 0; p < c; p++)
-                    h->launches += S * ((h->phase_off[p + 1] - h->phase_off[p] > 4 * resident) ? 2 : 1);
-                nb = S * c;
-                g += nb;
+                h->launches += 1;
             } else {
                 for (int i = 0; i < S; i++)
                     for (int p = 0; p < c; p++) {
@@ -918,12 +988,25 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
                         g++;
                     }
             }
-            phase_launches += nb;
             CSC_CUDA(cudaMemcpyAsync(h->poll, &sc->total, sizeof(long long) + sizeof(int),
                                      cudaMemcpyDeviceToHost, s));
+            if (graphed)
+                CSC_CUDA(cudaMemcpyAsync(&h->poll->g_next, &sc->gctr[0], sizeof(int),
+                                         cudaMemcpyDeviceToHost, s));
             CSC_CUDA(cudaStreamSynchronize(s));
             if (int rc = finish_init(h))  // (beta0 came before this poll in the stream)
                 return rc;
+            if (graphed) {
+                // batches the device loop ran, each S sweeps of the c phases
+                // and one round_step launch
+                nb = (int)(h->poll->g_next - g);
+                g = h->poll->g_next;
+                int per_batch = 1;
+                for (int p = 0; p < c; p++)
+                    per_batch += S * ((h->phase_off[p + 1] - h->phase_off[p] > 4 * resident) ? 2 : 1);
+                h->launches += (int64_t)(nb / (S * c)) * per_batch;
+            }
+            phase_launches += nb;
             if (timed) {
                 const int pairs = graphed ? 1 : nb;
                 for (int i = 0; i < pairs; i++) {
@@ -1021,31 +1104,31 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
         h->launches += 2;
     }
     CSC_CUDA(cudaEventRecord(h->ev1, s));
-    double E = 0.0;
-    {
-        if (timed)
-            CSC_CUDA(cudaEventRecord(h->ev_r0, s));
-        int rc = objectives(h, h->Z, &E);  // (synchronises the stream)
-        if (rc != CSC_OK)
-            return rc;
-        if (timed) {
-            CSC_CUDA(cudaEventRecord(h->ev_r1, s));
-            CSC_CUDA(cudaEventSynchronize(h->ev_r1));
-            rc = span_ms(&objective_ms);
-            if (rc != CSC_OK)
-                return rc;
-        }
-    }
+    // the objective, the copy of Z and the counters, then one wait
+    if (timed)
+        CSC_CUDA(cudaEventRecord(h->ev_r0, s));
+    if (int rc = objectives_async(h, h->Z))
+        return rc;
+    if (timed)
+        CSC_CUDA(cudaEventRecord(h->ev_r1, s));
     if (Z_out)
         CSC_CUDA(copy_out(Z_out, h->Z, sizeof(float) * h->K * Tz, s));
-    unsigned long long red[8];
-    double x2 = 0.0;
-    long long total = 0, visits = 0;
-    CSC_CUDA(cudaMemcpyAsync(red, sc->red, sizeof red, cudaMemcpyDeviceToHost, s));
-    CSC_CUDA(cudaMemcpyAsync(&x2, &sc->x2, sizeof x2, cudaMemcpyDeviceToHost, s));
-    CSC_CUDA(cudaMemcpyAsync(&total, &sc->total, sizeof total, cudaMemcpyDeviceToHost, s));
-    CSC_CUDA(cudaMemcpyAsync(&visits, &sc->visits, sizeof visits, cudaMemcpyDeviceToHost, s));
+    Fin *fin = h->fin;
+    CSC_CUDA(cudaMemcpyAsync(fin->red, sc->red, sizeof fin->red, cudaMemcpyDeviceToHost, s));
+    CSC_CUDA(cudaMemcpyAsync(&fin->x2, &sc->x2, sizeof fin->x2, cudaMemcpyDeviceToHost, s));
+    CSC_CUDA(cudaMemcpyAsync(&fin->total, &sc->total, sizeof fin->total, cudaMemcpyDeviceToHost, s));
+    CSC_CUDA(cudaMemcpyAsync(&fin->visits, &sc->visits, sizeof fin->visits, cudaMemcpyDeviceToHost, s));
     CSC_CUDA(cudaStreamSynchronize(s));
+    const double E = objectives_done(h);
+    if (timed) {
+        const int rc = span_ms(&objective_ms);
+        if (rc != CSC_OK)
+            return rc;
+    }
+    unsigned long long red[8];
+    std::memcpy(red, fin->red, sizeof red);
+    const double x2 = fin->x2;
+    const long long total = fin->total, visits = fin->visits;
     float ms = 0.f;
     CSC_CUDA(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
     h->g_used = g;

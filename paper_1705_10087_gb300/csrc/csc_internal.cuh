@@ -223,6 +223,17 @@ cudaError_t launch_phase(const PhaseParams &pp, const PhaseConfig &cfg, int acti
 // Device counters for launches replayed from a CUDA graph: *p = v; *p += v.
 cudaError_t launch_set_int(int *p, int v, cudaStream_t s);
 cudaError_t launch_add_int(int *p, int v, cudaStream_t s);
+// The last node of a poll batch in the graph of a CD round (a while loop over
+// batches): gctr[0] += batch (the launch index of the next launch), then the
+// loop's condition is set to go on unless the round's sweep found nothing to
+// do (*done), the update budget is spent (*total >= lim[0]), the round reached
+// lim[1] > 0 launches (a drift resync is due), the solve reached lim[2]
+// launches (max_sweeps) or the next batch would pass lim[3] (the trace ring).
+cudaError_t launch_round_step(cudaGraphConditionalHandle cond, int *gctr, int batch,
+                              const int *done, const long long *total, const long long *lim,
+                              cudaStream_t s);
+cudaError_t launch_set_limits(long long *lim, long long max_updates, long long drift_launches,
+                              long long max_g, long long ring, cudaStream_t s);
 // Blocks of the phase kernel that are resident at once on the whole GPU.
 int phase_resident_blocks(const PhaseConfig &cfg, int K);
 // The same phase as launch_phase, for phase lists much longer than the

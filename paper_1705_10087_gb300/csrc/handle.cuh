@@ -32,13 +32,21 @@ struct Scratch {
     int tc_err;  // a bounded wait of the tensor-core beta0 kernel gave up
     int qhead[2];  // drain launches: next queue entry, queue length
     int gctr[2];   // graph replays: launch index of the next launch, first index of the round
+    long long round_lim[4];  // stopping rules of a CD round run as a graph (launch_round_step)
 };
 
 // Host mirror of what the solve loop polls (pinned).
 struct Poll {
     long long total;
     int done;
-    int pad;
+    int g_next;  // launch index after a CD round run as a graph (Scratch::gctr[0])
+};
+
+// What the end of a solve reads back, in one pinned block (one wait).
+struct Fin {
+    unsigned long long red[8];
+    double x2;
+    long long total, visits;
 };
 
 // The host-side segment plan of one shard (shard.cu); empty for ordinary handles.
@@ -64,6 +72,7 @@ struct ShardState {
 }  // namespace csc
 
 using csc::NzLists;
+using csc::Fin;
 using csc::Poll;
 using csc::Scratch;
 using csc::SigDesc;
@@ -140,6 +149,9 @@ struct csc_handle_s {
     size_t cap_tmpZ = 0, cap_tmpB = 0;
     Scratch *sc = nullptr;
     Poll *poll = nullptr;  // pinned
+    Fin *fin = nullptr;    // pinned
+    double *E_pin = nullptr;  // pinned, [n] objectives of the last solve
+    size_t cap_E_pin = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEvent_t ev_i0 = nullptr, ev_i1 = nullptr;  // around the beta0 kernel (time_kernels)
     cudaEvent_t ev_r0 = nullptr, ev_r1 = nullptr;  // around a resync / the objective

@@ -57,6 +57,18 @@ inline bool is_device_pointer(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Whether p is page-locked host memory: a cudaMemcpyAsync from it returns
+// before the copy has read it (from pageable memory it returns after staging).
+inline bool is_pinned_host(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
 inline cudaError_t copy_in(void *dst, const void *src, size_t bytes, cudaStream_t s)
 {
     return cudaMemcpyAsync(dst, src, bytes,
