@@ -434,11 +434,11 @@ IMAGE = "image_P1_K8_h8_w8_512x512"
 
 
 def image_leg(args, capi, torch):
-    """The 2-D variant (images cut into row bands): one 512 x 512 gray image,
-    K = 8 atoms of 8 x 8, the Sec. 4 law; csc2d_solve to tol 1e-6 with automatic
-    bands (2h-2 rows each), timed with CUDA events around the call (setup, beta0,
-    band phases, resyncs, objective), against the 2-D oracle's E* stored by
-    tests/golden/make_golden.py --image2d."""
+    """The 2-D variant: one 512 x 512 gray image, K = 8 atoms of 8 x 8, the Sec. 4
+    law; csc2d_solve to tol 1e-6 with automatic tiles (row bands of 2h-2 rows cut
+    into column blocks of 2w-2 columns), timed with CUDA events around the call
+    (setup, beta0, tile phases, resyncs, objective), against the 2-D oracle's E*
+    stored by tests/golden/make_golden.py --image2d."""
     from paper_1705_10087_gb300 import synth
     pb = synth.make_image_workload(IMAGE, seed=0)
     try:
@@ -464,7 +464,8 @@ def image_leg(args, capi, torch):
         if i > 0:
             runs.append({"ms": e0.elapsed_time(e1), "solve_ms": st["solve_ms"], "status": status,
                          "updates": st["updates"], "sweeps": st["sweeps"], "bands": st["bands"],
-                         "phases": st["phases"], "resyncs": st["resyncs"],
+                         "col_blocks": st["col_blocks"], "phases": st["phases"],
+                         "resyncs": st["resyncs"],
                          "rel_gap_final": (E - g["E_star"]) / g["E_star"]})
     best = min(runs, key=lambda r: r["ms"])
     return {"workload": IMAGE, "K": w["K"], "P": w["P"], "h": w["h"], "w": w["w"],

@@ -49,7 +49,7 @@ namespace csc {
 namespace {
 
 constexpr int kTcM = 128;        // time rows per tile
-constexpr int kTcThreads = 128;  // 4 warps: one per 32 TMEM lanes
+constexpr int kTcThreads = 128;  // 4 warps: one per 32 TMEM lanes (NT = 256: two per quarter)
 constexpr int kSplits = 3;
 constexpr unsigned kWaitLimit = 1u << 22;
 constexpr int kMaxSteps = 128;  // P * L16 / 16 contraction steps (B alone then needs >= 96 KB)
@@ -149,6 +149,23 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
         v[i] = __uint_as_float(r[i]);
 }
 
+// 16 consecutive 32-bit columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; i++)
+        v[i] = __uint_as_float(r[i]);
+}
+
 // The three BF16 terms of x.
 __device__ __forceinline__ void split3(float x, __nv_bfloat16 &h, __nv_bfloat16 &m,
                                        __nv_bfloat16 &l)
@@ -188,11 +205,14 @@ struct TcLayout {
     }
 };
 
-// At N = 32 three CTAs fit an SM's shared memory for short atoms (P = 1,
-// L = 200: 76 KB each); the register budget is set so that they also fit
-// its register file.
-template <int N, bool CAT>
-__global__ void __launch_bounds__(kTcThreads, N <= 32 ? 3 : 1)
+// NT threads: 128 (four warps, one per quarter of the TMEM lanes) where
+// several CTAs share an SM (at N = 32 three fit its shared memory for short
+// atoms, P = 1, L = 200: 76 KB each, and the register budget is set so that
+// they also fit its register file), or 256 where one CTA holds an SM (P = 7):
+// twice the warps to build operands and read accumulators, the read-out split
+// between two warps per lane quarter by column halves.
+template <int N, bool CAT, int NT>
+__global__ void __launch_bounds__(NT, NT == 128 && N <= 32 ? 3 : 1)
     dtx_tc_kernel(const float *__restrict__ D, const float *__restrict__ X, int K, int P, int L,
                   long long T, int mode, float *__restrict__ beta0,
                   float *__restrict__ r_out, unsigned int *__restrict__ absmax_bits,
@@ -227,14 +247,14 @@ __global__ void __launch_bounds__(kTcThreads, N <= 32 ? 3 : 1)
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar + 8) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int st = tid; st < lay.nsteps; st += kTcThreads) {
+    for (int st = tid; st < lay.nsteps; st += NT) {
         const int p = (16 * st) / lay.L16, q0 = ((16 * st) % lay.L16) / 8;
         s_aoff[st] = (uint32_t)((p * lay.NQ + q0) * 128) >> 4;
     }
     // ---- B: the three BF16 terms of D, per contraction step -----------------
     // element (sigma, s, n8, j8, r, e): D[k = 8 n8 + r][p][tau], j = 16 s + 8 j8 + e
     const int rows_b = lay.nsteps * (N / 8) * 2 * 8;  // 16-byte rows per split
-    for (int i = tid; i < rows_b; i += kTcThreads) {
+    for (int i = tid; i < rows_b; i += NT) {
         const int r = i & 7, j8 = (i >> 3) & 1, n8 = (i >> 4) % (N / 8), s = (i >> 4) / (N / 8);
         const int k = 8 * n8 + r;
         uint32_t w[kSplits][4];
@@ -279,15 +299,15 @@ __global__ void __launch_bounds__(kTcThreads, N <= 32 ? 3 : 1)
     const int half = lay.xw / 2;  // words per plane row
     // The samples of a tile are loaded into registers one iteration ahead
     // (prefetch), so that their latency overlaps the previous tile's
-    // epilogue: a thread holds pairs i = tid + q * kTcThreads, q < kPairs.
+    // epilogue: a thread holds pairs i = tid + q * NT, q < kPairs.
     constexpr int kPairs = 8;
-    const bool prefetched = P * half <= kPairs * kTcThreads;
+    const bool prefetched = P * half <= kPairs * NT;
     float2 xr[kPairs];
     auto load_x = [&](long long tile) {
         const long long t0 = tile * kTcM;
 #pragma unroll
         for (int q = 0; q < kPairs; q++) {
-            const int i = tid + q * kTcThreads;
+            const int i = tid + q * NT;
             float2 v = make_float2(0.f, 0.f);
             if (i < P * half) {
                 const int p = i / half, j2 = i % half;
@@ -316,12 +336,12 @@ __global__ void __launch_bounds__(kTcThreads, N <= 32 ? 3 : 1)
         if (prefetched) {
 #pragma unroll
             for (int q = 0; q < kPairs; q++) {
-                const int i = tid + q * kTcThreads;
+                const int i = tid + q * NT;
                 if (i < P * half)
                     put_pair(i, xr[q].x, xr[q].y, last);
             }
         } else {
-            for (int i = tid; i < P * half; i += kTcThreads) {
+            for (int i = tid; i < P * half; i += NT) {
                 const int p = i / half, j2 = i % half;
                 const long long t = t0 + 2 * j2;
                 const float *xp = X + (long long)p * T + t;
@@ -337,8 +357,9 @@ __global__ void __launch_bounds__(kTcThreads, N <= 32 ? 3 : 1)
         const int rows_a = P * lay.NQ * 8;
         const int r = tid & 7, wa = r >> 1;
         const unsigned sh = (unsigned)(r & 1) * 16u;
-        for (int i = tid; i < rows_a; i += kTcThreads) {
-            const int q = (i >> 3) % lay.NQ, p = (i >> 3) / lay.NQ;
+        // row group i >> 3 = p NQ + q, advanced by NT / 8 per row without a division
+        int q = (tid >> 3) % lay.NQ, p = (tid >> 3) / lay.NQ;
+        for (int i = tid; i < rows_a; i += NT) {
             const size_t off = ((size_t)p * lay.NQ + q) * 128 + (size_t)r * 16;
 #pragma unroll
             for (int sg = 0; sg < kSplits; sg++) {
@@ -347,6 +368,11 @@ __global__ void __launch_bounds__(kTcThreads, N <= 32 ? 3 : 1)
                 *reinterpret_cast<uint4 *>(Ab + (size_t)sg * P * lay.NQ * 128 + off) =
                     make_uint4(__funnelshift_r(w0, w1, sh), __funnelshift_r(w1, w2, sh),
                                __funnelshift_r(w2, w3, sh), __funnelshift_r(w3, w4, sh));
+            }
+            q += NT / 8;
+            while (q >= lay.NQ) {
+                q -= lay.NQ;
+                p++;
             }
         }
         // make the generic-proxy stores visible to the tensor cores
@@ -390,38 +416,65 @@ __global__ void __launch_bounds__(kTcThreads, N <= 32 ? 3 : 1)
     };
     // accumulator buf -> beta0 columns of the tile
     auto epilogue = [&](long long tile, int buf) {
-        const long long t = tile * kTcM + 32 * warp + lane;
+        // warp w reads lane quarter w % 4 and, with NT = 256, column half w / 4
+        constexpr int CW = N / (NT / 128);  // columns per warp
+        const int quarter = warp & 3, c_lo = (warp >> 2) * CW;
+        const long long t = tile * kTcM + 32 * quarter + lane;
         const uint32_t lane_addr =
-            taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)(buf * acc_cols);
+            taddr + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(buf * acc_cols);
+        auto put = [&](int k, float v) {
+            if (k < K) {
+                beta0[(long long)k * Tz + t] = v;
+                if (r_out)
+                    r_out[(long long)k * Tz + t] = v;
+                amax = fmaxf(amax, fabsf(v));
+            }
+        };
+        if constexpr (CW >= 32) {
 #pragma unroll
-        for (int c = 0; c < N; c += 32) {
-            float v[32];
+            for (int c = c_lo; c < c_lo + CW; c += 32) {
+                float v[32];
+                if constexpr (CAT) {
+                    // hl + (hm + mm) + (hh + mh + lh), smallest first
+                    float u[32];
+                    tmem_ld32(lane_addr + (uint32_t)(2 * N + c), v);
+                    tmem_ld32(lane_addr + (uint32_t)(N + c), u);
+#pragma unroll
+                    for (int i = 0; i < 32; i++)
+                        v[i] += u[i];
+                    tmem_ld32(lane_addr + (uint32_t)c, u);
+#pragma unroll
+                    for (int i = 0; i < 32; i++)
+                        v[i] += u[i];
+                } else {
+                    tmem_ld32(lane_addr + (uint32_t)c, v);
+                }
+                if (t < Tz) {
+#pragma unroll
+                    for (int i = 0; i < 32; i++)
+                        put(c + i, v[i]);
+                }
+            }
+        } else {
+            float v[16];
             if constexpr (CAT) {
-                // hl + (hm + mm) + (hh + mh + lh), smallest first
-                float u[32];
-                tmem_ld32(lane_addr + (uint32_t)(2 * N + c), v);
-                tmem_ld32(lane_addr + (uint32_t)(N + c), u);
+                float u[16];
+                tmem_ld16(lane_addr + (uint32_t)(2 * N + c_lo), v);
+                tmem_ld16(lane_addr + (uint32_t)(N + c_lo), u);
 #pragma unroll
-                for (int i = 0; i < 32; i++)
+                for (int i = 0; i < 16; i++)
                     v[i] += u[i];
-                tmem_ld32(lane_addr + (uint32_t)c, u);
+                tmem_ld16(lane_addr + (uint32_t)c_lo, u);
 #pragma unroll
-                for (int i = 0; i < 32; i++)
+                for (int i = 0; i < 16; i++)
                     v[i] += u[i];
             } else {
-                tmem_ld32(lane_addr + (uint32_t)c, v);
+                tmem_ld16(lane_addr + (uint32_t)c_lo, v);
             }
             if (t < Tz) {
 #pragma unroll
-                for (int i = 0; i < 32; i++) {
-                    const int k = c + i;
-                    if (k < K) {
-                        beta0[(long long)k * Tz + t] = v[i];
-                        if (r_out)
-                            r_out[(long long)k * Tz + t] = v[i];
-                        amax = fmaxf(amax, fabsf(v[i]));
-                    }
-                }
+                for (int i = 0; i < 16; i++)
+                    put(c_lo + i, v[i]);
             }
         }
     };
@@ -549,19 +602,18 @@ cudaError_t launch_dtx_tc(const float *D, const float *X, int K, int P, int L, i
         if (e != cudaSuccess)
             return e;
         const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + 1024);
-        const int by_regs = 65536 / (fa.numRegs * kTcThreads > 0 ? fa.numRegs * kTcThreads : 1);
+        const int nt = fa.maxThreadsPerBlock >= 256 ? 256 : 128;
+        const int by_regs = 65536 / (fa.numRegs * nt > 0 ? fa.numRegs * nt : 1);
         int per_sm = by_smem < by_regs ? by_smem : by_regs;
         per_sm = per_sm < 1 ? 1 : (per_sm > max_per_sm ? max_per_sm : per_sm);
         // concatenated products where at most two CTAs share an SM: their
         // accumulators take 256 of its 512 tensor-memory columns each
         const int64_t cap = (int64_t)nsm * per_sm;
         const unsigned grid = (unsigned)(ntiles < cap ? ntiles : cap);
-        kern<<<grid, kTcThreads, smem, s>>>(D, X, K, P, L, (long long)T, mode, beta0, r_out,
-                                           absmax_bits, x2sum, err);
+        kern<<<grid, nt, smem, s>>>(D, X, K, P, L, (long long)T, mode, beta0, r_out, absmax_bits,
+                                   x2sum, err);
         return cudaGetLastError();
     };
-    if (K > 32)
-        return go(dtx_tc_kernel<64, false>, 4);
     // concatenated products where shared memory holds at most two CTAs per
     // SM (their accumulators take 256 of its 512 tensor-memory columns each);
     // a smaller tile keeps three or more CTAs with the six narrow products
@@ -569,11 +621,19 @@ cudaError_t launch_dtx_tc(const float *D, const float *X, int K, int P, int L, i
     cudaFuncAttributes fa;
     cudaError_t e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     if (e == cudaSuccess)
-        e = cudaFuncGetAttributes(&fa, dtx_tc_kernel<32, true>);
+        e = cudaFuncGetAttributes(&fa, dtx_tc_kernel<32, true, 256>);
     if (e != cudaSuccess)
         return e;
-    const bool cat = mode == 1 && smem_sm / (int)(smem + fa.sharedSizeBytes + 1024) <= 2;
-    return cat ? go(dtx_tc_kernel<32, true>, 2) : go(dtx_tc_kernel<32, false>, 4);
+    const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + 1024);
+    if (K > 32)
+        return by_smem <= 1 ? go(dtx_tc_kernel<64, false, 256>, 1)
+                            : go(dtx_tc_kernel<64, false, 128>, 4);
+    // one CTA per SM: eight warps; two (cat) or more: four
+    if (by_smem <= 1)
+        return mode == 1 ? go(dtx_tc_kernel<32, true, 256>, 1) : go(dtx_tc_kernel<32, false, 256>, 1);
+    if (mode == 1 && by_smem <= 2)
+        return go(dtx_tc_kernel<32, true, 128>, 2);
+    return go(dtx_tc_kernel<32, false, 128>, 4);
 }
 
 cudaError_t launch_dtx_any(const float *D, const float *X, int K, int P, int L, int64_t T,

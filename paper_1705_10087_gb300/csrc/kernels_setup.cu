@@ -42,10 +42,12 @@ __global__ void dtd_kernel(const float *__restrict__ D, int K, int P, int L,
             const float *a = da + p * L;
             const float *b = db + p * L + lag;
             for (int t8 = tlo; t8 < thi; t8 += 8) {
+                // (unrolled with predicates: the loads of a chunk issue together)
                 float part = 0.f;
-                const int te = min(t8 + 8, thi);
-                for (int t = t8; t < te; t++)
-                    part = fmaf(a[t], b[t], part);
+#pragma unroll
+                for (int u = 0; u < 8; u++)
+                    if (t8 + u < thi)
+                        part = fmaf(a[t8 + u], b[t8 + u], part);
                 acc.add(part);
             }
         }
