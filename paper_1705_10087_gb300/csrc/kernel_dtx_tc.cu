@@ -26,15 +26,23 @@
 //     128 B, N-adjacent at 256 B; row k of core matrix (n8, j8) of split
 //     sigma holds term sigma of D[k = 8 n8 + r][p][tau = 16 s + 8 j8 + 0..7 -
 //     p L16].  The splits of a step are thus one operand of 3N rows.
-// Concatenated products (N = 32, "cat"): per step one M x 3N product of the
-// leading term of X with [D_h D_m D_l] (hh, hm, hl), one M x 2N product of its
-// middle term with [D_h D_m] (mh, mm) and one M x N product of its last term
-// with D_h (lh), into one accumulator of 3N columns: hh + mh + lh, hm + mm
-// and hl, summed in the epilogue.  The tensor cores read each A run three
-// times per step instead of six.
-// The accumulator lives in tensor memory (N columns of 32-bit, lane = t); each
-// of the 4 warps reads its 32 lanes with tcgen05.ld and writes beta0[k][t]
-// coalesced along t.
+// Concatenated products (N = 32, dtx_tc_ws_kernel): per step one M x 3N
+// product of the leading term of X with [D_h D_m D_l] (hh, hm, hl), one M x 2N
+// product of its middle term with [D_h D_m] (mh, mm) and one M x N product of
+// its last term with D_h (lh), into one accumulator of 3N columns: hh + mh +
+// lh, hm + mm and hl, summed in the epilogue.  The tensor cores read each A
+// run three times per step instead of six.  That kernel gives the issue of
+// the products a warp of its own; dtx_tc_kernel (N = 64, or the hh product
+// alone) issues them from thread 0 between the operand build and read-out.
+// The accumulator lives in tensor memory (32-bit columns, lane = t); the warp
+// of each lane quarter reads its 32 lanes with tcgen05.ld and writes
+// beta0[k][t] coalesced along t.
+//
+// What bounds the products: the tensor cores read the operands from shared
+// memory in this unswizzled layout (the Hankel runs of A overlap, which no
+// swizzled layout allows); at N = 32 a step reads 18 KB (A three times, B
+// once) for 0.4 M multiply-adds, so the operand reads, not the multipliers,
+// set the pace of the products.
 //
 // Waits are bounded: a wait that gives up sets *err, the block stops issuing
 // work, waits (again bounded) for the products already issued and releases
@@ -49,7 +57,6 @@ namespace csc {
 namespace {
 
 constexpr int kTcM = 128;        // time rows per tile
-constexpr int kTcThreads = 128;  // 4 warps: one per 32 TMEM lanes (NT = 256: two per quarter)
 constexpr int kSplits = 3;
 constexpr unsigned kWaitLimit = 1u << 22;
 constexpr int kMaxSteps = 128;  // P * L16 / 16 contraction steps (B alone then needs >= 96 KB)
@@ -205,13 +212,14 @@ struct TcLayout {
     }
 };
 
+// The six separate products (kind of mode 1 for K > 32, where N = 64 leaves
+// no room to concatenate) or the single hh product (mode 2), each thread
+// taking part in the operand build and the read-out and thread 0 issuing.
 // NT threads: 128 (four warps, one per quarter of the TMEM lanes) where
-// several CTAs share an SM (at N = 32 three fit its shared memory for short
-// atoms, P = 1, L = 200: 76 KB each, and the register budget is set so that
-// they also fit its register file), or 256 where one CTA holds an SM (P = 7):
-// twice the warps to build operands and read accumulators, the read-out split
-// between two warps per lane quarter by column halves.
-template <int N, bool CAT, int NT>
+// several CTAs share an SM, or 256 where one CTA holds an SM: twice the warps
+// to build operands and read accumulators, the read-out split between two
+// warps per lane quarter by column halves.
+template <int N, int NT>
 __global__ void __launch_bounds__(NT, NT == 128 && N <= 32 ? 3 : 1)
     dtx_tc_kernel(const float *__restrict__ D, const float *__restrict__ X, int K, int P, int L,
                   long long T, int mode, float *__restrict__ beta0,
@@ -230,11 +238,9 @@ __global__ void __launch_bounds__(NT, NT == 128 && N <= 32 ? 3 : 1)
     const long long Tz = T - L + 1;
     const long long ntiles = (Tz + kTcM - 1) / kTcM;
 
-    // ---- tensor memory (two accumulators of N, or 3N when cat, columns; the
-    // allocation is a power of two) and two barriers ---------------------------
-    static_assert(!CAT || N == 32, "concatenated products need N = 32 (3N + 3N <= 256 columns)");
-    constexpr int acc_cols = CAT ? 3 * N : N;
-    constexpr uint32_t tm_cols = CAT ? 256u : 2u * N;
+    // ---- tensor memory (two accumulators of N columns) and two barriers ----
+    constexpr int acc_cols = N;
+    constexpr uint32_t tm_cols = 2u * N;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&s_taddr)),
@@ -285,7 +291,6 @@ __global__ void __launch_bounds__(NT, NT == 128 && N <= 32 ? 3 : 1)
     fence_after_sync();
     const uint32_t taddr = s_taddr;
     const uint32_t idesc = mma_idesc(kTcM, N);
-    const uint32_t idesc_cat2 = mma_idesc(kTcM, 2 * N), idesc_cat3 = mma_idesc(kTcM, 3 * N);
     const size_t a_bytes = (size_t)kSplits * P * lay.NQ * 128;  // one operand buffer
     const uint32_t a_base = smem_u32(As), b_base = smem_u32(Bs);
 
@@ -395,12 +400,7 @@ __global__ void __launch_bounds__(NT, NT == 128 && N <= 32 ? 3 : 1)
         for (int s = 0; s < lay.nsteps; s++) {
             const uint64_t a_s = ad0 + s_aoff[s];
             const uint64_t b_s = bd0 + ((uint32_t)(s * kSplits * (N / 8) * 256) >> 4);
-            if constexpr (CAT) {
-                // hh|hm|hl (first: it covers all 3N columns), mh|mm, lh
-                mma_bf16(d_acc, a_s, b_s, idesc_cat3, acc);
-                mma_bf16(d_acc, a_s + 1 * a_split, b_s, idesc_cat2, 1u);
-                mma_bf16(d_acc, a_s + 2 * a_split, b_s, idesc, 1u);
-            } else if (mode == 2) {
+            if (mode == 2) {
                 mma_bf16(d_acc, a_s, b_s, idesc, acc);
             } else {
                 mma_bf16(d_acc, a_s + 1 * a_split, b_s + 1 * b_split, idesc, acc);  // mm
@@ -434,21 +434,7 @@ __global__ void __launch_bounds__(NT, NT == 128 && N <= 32 ? 3 : 1)
 #pragma unroll
             for (int c = c_lo; c < c_lo + CW; c += 32) {
                 float v[32];
-                if constexpr (CAT) {
-                    // hl + (hm + mm) + (hh + mh + lh), smallest first
-                    float u[32];
-                    tmem_ld32(lane_addr + (uint32_t)(2 * N + c), v);
-                    tmem_ld32(lane_addr + (uint32_t)(N + c), u);
-#pragma unroll
-                    for (int i = 0; i < 32; i++)
-                        v[i] += u[i];
-                    tmem_ld32(lane_addr + (uint32_t)c, u);
-#pragma unroll
-                    for (int i = 0; i < 32; i++)
-                        v[i] += u[i];
-                } else {
-                    tmem_ld32(lane_addr + (uint32_t)c, v);
-                }
+                tmem_ld32(lane_addr + (uint32_t)c, v);
                 if (t < Tz) {
 #pragma unroll
                     for (int i = 0; i < 32; i++)
@@ -457,20 +443,7 @@ __global__ void __launch_bounds__(NT, NT == 128 && N <= 32 ? 3 : 1)
             }
         } else {
             float v[16];
-            if constexpr (CAT) {
-                float u[16];
-                tmem_ld16(lane_addr + (uint32_t)(2 * N + c_lo), v);
-                tmem_ld16(lane_addr + (uint32_t)(N + c_lo), u);
-#pragma unroll
-                for (int i = 0; i < 16; i++)
-                    v[i] += u[i];
-                tmem_ld16(lane_addr + (uint32_t)c_lo, u);
-#pragma unroll
-                for (int i = 0; i < 16; i++)
-                    v[i] += u[i];
-            } else {
-                tmem_ld16(lane_addr + (uint32_t)c_lo, v);
-            }
+            tmem_ld16(lane_addr + (uint32_t)c_lo, v);
             if (t < Tz) {
 #pragma unroll
                 for (int i = 0; i < 16; i++)
@@ -532,6 +505,346 @@ __global__ void __launch_bounds__(NT, NT == 128 && N <= 32 ? 3 : 1)
     __syncthreads();
     fence_after_sync();
     if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr),
+                     "r"(tm_cols)
+                     : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Barrier 1 among the n worker threads (the issuing warp does not take part).
+__device__ __forceinline__ void workers_sync(int n)
+{
+    asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory");
+}
+
+// The same barrier, returning whether v was true in any of the n threads.
+__device__ __forceinline__ bool workers_any(bool v, int n)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(n)
+        : "memory");
+    return r != 0;
+}
+
+// Warp-specialised form of the concatenated products (N = 32): NW worker
+// warps build the operands of tile i and read the accumulator of tile i-1
+// out while one more warp issues the products, so that the issue of a tile's
+// P * L16 / 16 * 3 products by one thread no longer holds up the operand
+// build and the read-out.  The two sides meet only at mbarriers:
+//   full[b]  the operands of the tile in buffer b are written (one arrival
+//            per worker thread, after its proxy fence),
+//   done[b]  the products into accumulator b have finished (tcgen05.commit),
+//   free[b]  accumulator b has been read out (one arrival per worker thread).
+// Tile i of the CTA uses operand buffer and accumulator b = i & 1; its use
+// u = i >> 1 of them completes phase u of the three barriers of b, which is
+// waited for with parity u & 1.  The workers share barrier 1 (plane buffer
+// reuse, and the block's decision to give up after a wait ran out).
+template <int NW>
+__global__ void __launch_bounds__(32 * NW + 32, NW <= 4 ? 2 : 1)
+    dtx_tc_ws_kernel(const float *__restrict__ D, const float *__restrict__ X, int K, int P,
+                     int L, long long T, int /* mode: 1, the signature of dtx_tc_kernel */,
+                     float *__restrict__ beta0, float *__restrict__ r_out,
+                     unsigned int *__restrict__ absmax_bits, double *__restrict__ x2sum,
+                     int *__restrict__ err)
+{
+    constexpr int N = 32;
+    constexpr int NTW = 32 * NW;        // worker threads
+    constexpr int NTA = NTW + 32;       // with the issuing warp
+    constexpr int acc_cols = 3 * N;     // hh+mh+lh | hm+mm | hl
+    constexpr uint32_t tm_cols = 256u;  // two accumulators, rounded up to a power of two
+    extern __shared__ __align__(128) unsigned char sm[];
+    __shared__ uint32_t s_taddr;
+    __shared__ uint32_t s_aoff[kMaxSteps];
+    __shared__ __align__(8) unsigned long long s_bar[6];  // full[2], done[2], free[2]
+    const TcLayout lay(P, L, N);
+    unsigned char *As = sm + lay.a_off;
+    unsigned char *Bs = sm + lay.b_off;
+    uint32_t *pl = reinterpret_cast<uint32_t *>(sm + lay.pl_off);
+    const uint32_t full0 = smem_u32(&s_bar[0]), done0 = smem_u32(&s_bar[2]),
+                   free0 = smem_u32(&s_bar[4]);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long Tz = T - L + 1;
+    const long long ntiles = (Tz + kTcM - 1) / kTcM;
+
+    if (warp == NW) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&s_taddr)),
+                     "r"(tm_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int b = 0; b < 2; b++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(full0 + 8u * b), "r"(NTW)
+                         : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(done0 + 8u * b) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(free0 + 8u * b), "r"(NTW)
+                         : "memory");
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int st = tid; st < lay.nsteps; st += NTA) {
+        const int p = (16 * st) / lay.L16, q0 = ((16 * st) % lay.L16) / 8;
+        s_aoff[st] = (uint32_t)((p * lay.NQ + q0) * 128) >> 4;
+    }
+    // B: the three BF16 terms of D per contraction step, as in dtx_tc_kernel
+    const int rows_b = lay.nsteps * (N / 8) * 2 * 8;
+    for (int i = tid; i < rows_b; i += NTA) {
+        const int r = i & 7, j8 = (i >> 3) & 1, n8 = (i >> 4) % (N / 8), s = (i >> 4) / (N / 8);
+        const int k = 8 * n8 + r;
+        uint32_t w[kSplits][4];
+#pragma unroll
+        for (int e2 = 0; e2 < 4; e2++) {
+            __nv_bfloat16 h[2], m[2], l[2];
+#pragma unroll
+            for (int q = 0; q < 2; q++) {
+                const int j = 16 * s + 8 * j8 + 2 * e2 + q;
+                const int p = j / lay.L16, tau = j % lay.L16;
+                const float v = (k < K && tau < L) ? D[((long long)k * P + p) * L + tau] : 0.f;
+                split3(v, h[q], m[q], l[q]);
+            }
+            w[0][e2] = pack2(h[0], h[1]);
+            w[1][e2] = pack2(m[0], m[1]);
+            w[2][e2] = pack2(l[0], l[1]);
+        }
+#pragma unroll
+        for (int sg = 0; sg < kSplits; sg++) {
+            const size_t off =
+                ((((size_t)s * kSplits + sg) * (N / 8) + n8) * 2 + j8) * 128 + (size_t)r * 16;
+            *reinterpret_cast<uint4 *>(Bs + off) = make_uint4(w[sg][0], w[sg][1], w[sg][2], w[sg][3]);
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t taddr = s_taddr;
+    const size_t a_bytes = (size_t)kSplits * P * lay.NQ * 128;
+    const uint32_t a_base = smem_u32(As), b_base = smem_u32(Bs);
+    const long long cnt = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+    if (warp < NW) {
+        // ---------------- workers: operand build and read-out ----------------
+        float amax = 0.f;
+        float x2h = 0.f, x2l = 0.f;  // sum of X^2 over the CTA's own samples (double-float)
+        const int half = lay.xw / 2;
+        constexpr int kPairs = 4;  // P = 7 at L = 64, or P = 1 at L = 200, fit
+        const bool prefetched = P * half <= kPairs * NTW;
+        float2 xr[kPairs];
+        auto load_x = [&](long long tile) {
+            const long long t0 = tile * kTcM;
+#pragma unroll
+            for (int q = 0; q < kPairs; q++) {
+                const int i = tid + q * NTW;
+                float2 v = make_float2(0.f, 0.f);
+                if (i < P * half) {
+                    const int p = i / half, j2 = i % half;
+                    const long long t = t0 + 2 * j2;
+                    const float *xp = X + (long long)p * T + t;
+                    v.x = t < T ? xp[0] : 0.f;
+                    v.y = t + 1 < T ? xp[1] : 0.f;
+                }
+                xr[q] = v;
+            }
+        };
+        auto put_pair = [&](int i, float v0, float v1, bool own) {
+            const int p = i / half, j2 = i % half;
+            if (own || 2 * j2 < kTcM) {
+                df_add_prod(x2h, x2l, v0, v0);
+                df_add_prod(x2h, x2l, v1, v1);
+            }
+            __nv_bfloat16 h0, m0, l0, h1, m1, l1;
+            split3(v0, h0, m0, l0);
+            split3(v1, h1, m1, l1);
+            pl[(0 * P + p) * half + j2] = pack2(h0, h1);
+            pl[(1 * P + p) * half + j2] = pack2(m0, m1);
+            pl[(2 * P + p) * half + j2] = pack2(l0, l1);
+        };
+        // operand runs of a tile into buffer buf (the row layout of dtx_tc_kernel)
+        auto build = [&](long long tile, int buf) {
+            const long long t0 = tile * kTcM;
+            const bool last = tile == ntiles - 1;
+            if (prefetched) {
+#pragma unroll
+                for (int q = 0; q < kPairs; q++) {
+                    const int i = tid + q * NTW;
+                    if (i < P * half)
+                        put_pair(i, xr[q].x, xr[q].y, last);
+                }
+            } else {
+                for (int i = tid; i < P * half; i += NTW) {
+                    const int p = i / half, j2 = i % half;
+                    const long long t = t0 + 2 * j2;
+                    const float *xp = X + (long long)p * T + t;
+                    put_pair(i, t < T ? xp[0] : 0.f, t + 1 < T ? xp[1] : 0.f, last);
+                }
+            }
+            workers_sync(NTW);
+            unsigned char *Ab = As + (size_t)buf * a_bytes;
+            const int rows_a = P * lay.NQ * 8;
+            const int r = tid & 7, wa = r >> 1;
+            const unsigned sh = (unsigned)(r & 1) * 16u;
+            int q = (tid >> 3) % lay.NQ, p = (tid >> 3) / lay.NQ;
+            for (int i = tid; i < rows_a; i += NTW) {
+                const size_t off = ((size_t)p * lay.NQ + q) * 128 + (size_t)r * 16;
+#pragma unroll
+                for (int sg = 0; sg < kSplits; sg++) {
+                    const uint32_t *w = pl + (size_t)(sg * P + p) * half + 4 * q + wa;
+                    const uint32_t w0 = w[0], w1 = w[1], w2 = w[2], w3 = w[3], w4 = w[4];
+                    *reinterpret_cast<uint4 *>(Ab + (size_t)sg * P * lay.NQ * 128 + off) =
+                        make_uint4(__funnelshift_r(w0, w1, sh), __funnelshift_r(w1, w2, sh),
+                                   __funnelshift_r(w2, w3, sh), __funnelshift_r(w3, w4, sh));
+                }
+                q += NTW / 8;
+                while (q >= lay.NQ) {
+                    q -= lay.NQ;
+                    p++;
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        };
+        // accumulator buf (use parity par) -> beta0 columns of the tile; false
+        // if the wait for its products ran out
+        auto epilogue = [&](long long tile, int buf, uint32_t par) -> bool {
+            const bool got = mbar_wait_bounded(done0 + 8u * (uint32_t)buf, par, kWaitLimit);
+            if (got) {
+                fence_after_sync();
+                constexpr int CW = N / (NTW / 128);
+                const int quarter = warp & 3, c_lo = (warp >> 2) * CW;
+                const long long t = tile * kTcM + 32 * quarter + lane;
+                const uint32_t lane_addr =
+                    taddr + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(buf * acc_cols);
+                auto put = [&](int k, float v) {
+                    if (k < K) {
+                        beta0[(long long)k * Tz + t] = v;
+                        if (r_out)
+                            r_out[(long long)k * Tz + t] = v;
+                        amax = fmaxf(amax, fabsf(v));
+                    }
+                };
+                // 16 columns at a time: hl + (hm + mm) + (hh + mh + lh), smallest first
+#pragma unroll
+                for (int c = c_lo; c < c_lo + CW; c += 16) {
+                    float v[16], u[16];
+                    tmem_ld16(lane_addr + (uint32_t)(2 * N + c), v);
+                    tmem_ld16(lane_addr + (uint32_t)(N + c), u);
+#pragma unroll
+                    for (int i = 0; i < 16; i++)
+                        v[i] += u[i];
+                    tmem_ld16(lane_addr + (uint32_t)c, u);
+#pragma unroll
+                    for (int i = 0; i < 16; i++)
+                        v[i] += u[i];
+                    if (t < Tz) {
+#pragma unroll
+                        for (int i = 0; i < 16; i++)
+                            put(c + i, v[i]);
+                    }
+                }
+            }
+            fence_before_sync();
+            mbar_arrive(free0 + 8u * (uint32_t)buf);
+            return got;
+        };
+
+        if (prefetched && cnt > 0)
+            load_x(blockIdx.x);
+        bool gave_up = false;
+        for (long long i = 0; i < cnt; i++) {
+            const int b = (int)(i & 1);
+            build(blockIdx.x + i * gridDim.x, b);
+            mbar_arrive(full0 + 8u * (uint32_t)b);
+            // the next tile's samples are in flight while the products of tile i
+            // run and the accumulator of tile i-1 is read out
+            if (prefetched && i + 1 < cnt)
+                load_x(blockIdx.x + (i + 1) * gridDim.x);
+            bool got = true;
+            if (i > 0)
+                got = epilogue(blockIdx.x + (i - 1) * gridDim.x, (int)((i - 1) & 1),
+                               (uint32_t)(((i - 1) >> 1) & 1));
+            // every worker is done with the planes of tile i before the next
+            // tile's samples overwrite them; a wait that ran out stops all of them
+            if (workers_any(!got, NTW)) {
+                gave_up = true;
+                break;
+            }
+        }
+        if (!gave_up && cnt > 0 &&
+            !epilogue(blockIdx.x + (cnt - 1) * gridDim.x, (int)((cnt - 1) & 1),
+                      (uint32_t)(((cnt - 1) >> 1) & 1)))
+            gave_up = true;
+        if (gave_up)
+            atomicExch(err, 1);
+        double x2 = (double)x2h + (double)x2l;
+        for (int off = 16; off > 0; off >>= 1) {
+            amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+            x2 += __shfl_xor_sync(0xffffffffu, x2, off);
+        }
+        if (lane == 0) {
+            atomicMax(absmax_bits, __float_as_uint(amax));
+            atomicAdd(x2sum, x2);
+        }
+    } else {
+        // ---------------- issuing warp (lane 0 issues) -----------------------
+        const uint32_t idesc = mma_idesc(kTcM, N);
+        const uint32_t idesc_cat2 = mma_idesc(kTcM, 2 * N), idesc_cat3 = mma_idesc(kTcM, 3 * N);
+        const uint32_t a_split = (uint32_t)(P * lay.NQ * 128) >> 4;
+        const uint64_t bd0 = mma_desc(b_base, 128, 256);
+        long long issued = -1;
+        for (long long i = 0; i < cnt; i++) {
+            const int b = (int)(i & 1);
+            const uint32_t par = (uint32_t)((i >> 1) & 1);
+            bool ok = true;
+            if (lane == 0) {
+                ok = mbar_wait_bounded(full0 + 8u * (uint32_t)b, par, kWaitLimit);
+                // accumulator b was read out (tile i-2)
+                if (ok && i >= 2)
+                    ok = mbar_wait_bounded(free0 + 8u * (uint32_t)b, par ^ 1u, kWaitLimit);
+                if (ok) {
+                    fence_after_sync();
+                    const uint32_t d_acc = taddr + (uint32_t)(b * acc_cols);
+                    const uint64_t ad0 = mma_desc(a_base + (uint32_t)(b * a_bytes), 128, 128);
+                    for (int s = 0; s < lay.nsteps; s++) {
+                        const uint64_t a_s = ad0 + s_aoff[s];
+                        const uint64_t b_s = bd0 + ((uint32_t)(s * kSplits * (N / 8) * 256) >> 4);
+                        // hh|hm|hl (first: it covers all 3N columns), mh|mm, lh
+                        mma_bf16(d_acc, a_s, b_s, idesc_cat3, s > 0 ? 1u : 0u);
+                        mma_bf16(d_acc, a_s + 1 * a_split, b_s, idesc_cat2, 1u);
+                        mma_bf16(d_acc, a_s + 2 * a_split, b_s, idesc, 1u);
+                    }
+                    mma_commit(done0 + 8u * (uint32_t)b);
+                }
+            }
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) {
+                if (lane == 0)
+                    atomicExch(err, 1);
+                break;
+            }
+            issued = i;
+        }
+        // the last products issued (tcgen05.commit tracks all earlier ones) have
+        // finished before tensor memory is released
+        if (lane == 0 && issued >= 0 &&
+            !mbar_wait_bounded(done0 + 8u * (uint32_t)(issued & 1), (uint32_t)((issued >> 1) & 1),
+                               kWaitLimit))
+            atomicExch(err, 1);
+        __syncwarp();
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (warp == NW)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr),
                      "r"(tm_cols)
                      : "memory");
@@ -602,7 +915,8 @@ cudaError_t launch_dtx_tc(const float *D, const float *X, int K, int P, int L, i
         if (e != cudaSuccess)
             return e;
         const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + 1024);
-        const int nt = fa.maxThreadsPerBlock >= 256 ? 256 : 128;
+        // the block size the instantiation was compiled for (launch bounds)
+        const int nt = fa.maxThreadsPerBlock;
         const int by_regs = 65536 / (fa.numRegs * nt > 0 ? fa.numRegs * nt : 1);
         int per_sm = by_smem < by_regs ? by_smem : by_regs;
         per_sm = per_sm < 1 ? 1 : (per_sm > max_per_sm ? max_per_sm : per_sm);
@@ -614,26 +928,22 @@ cudaError_t launch_dtx_tc(const float *D, const float *X, int K, int P, int L, i
                                    x2sum, err);
         return cudaGetLastError();
     };
-    // concatenated products where shared memory holds at most two CTAs per
-    // SM (their accumulators take 256 of its 512 tensor-memory columns each);
-    // a smaller tile keeps three or more CTAs with the six narrow products
+    // mode 1 at N = 32: concatenated products with a warp of their own, one
+    // CTA per SM with eight worker warps or two with four (their accumulators
+    // take 256 of the SM's 512 tensor-memory columns each)
     int smem_sm = 0;
     cudaFuncAttributes fa;
     cudaError_t e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     if (e == cudaSuccess)
-        e = cudaFuncGetAttributes(&fa, dtx_tc_kernel<32, true, 256>);
+        e = cudaFuncGetAttributes(&fa, dtx_tc_ws_kernel<8>);
     if (e != cudaSuccess)
         return e;
     const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + 1024);
     if (K > 32)
-        return by_smem <= 1 ? go(dtx_tc_kernel<64, false, 256>, 1)
-                            : go(dtx_tc_kernel<64, false, 128>, 4);
-    // one CTA per SM: eight warps; two (cat) or more: four
-    if (by_smem <= 1)
-        return mode == 1 ? go(dtx_tc_kernel<32, true, 256>, 1) : go(dtx_tc_kernel<32, false, 256>, 1);
-    if (mode == 1 && by_smem <= 2)
-        return go(dtx_tc_kernel<32, true, 128>, 2);
-    return go(dtx_tc_kernel<32, false, 128>, 4);
+        return by_smem <= 1 ? go(dtx_tc_kernel<64, 256>, 1) : go(dtx_tc_kernel<64, 128>, 4);
+    if (mode == 1)
+        return by_smem <= 1 ? go(dtx_tc_ws_kernel<8>, 1) : go(dtx_tc_ws_kernel<4>, 2);
+    return by_smem <= 1 ? go(dtx_tc_kernel<32, 256>, 1) : go(dtx_tc_kernel<32, 128>, 4);
 }
 
 cudaError_t launch_dtx_any(const float *D, const float *X, int K, int P, int L, int64_t T,
