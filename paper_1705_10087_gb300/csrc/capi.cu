@@ -460,7 +460,8 @@ int csc_destroy(csc_handle_t h)
     void *bufs[] = {h->D,          h->C,          h->Ct,         h->norms,      h->X,
                     h->r,          h->beta0,      h->Z,          h->partials,   h->dirty,
                     h->tmpZ,       h->tmpB,       h->sc,         h->d_sig,      h->d_tile_s,
-                    h->d_tile_off, h->d_tile_sig, h->d_rtile_s,  h->d_rtile_sig, h->d_E,
+                    h->d_tile_off, h->d_tile_sig, h->d_rtile_s,  h->d_rtile_sig, h->d_rtile_off,
+                    h->d_E,
                     h->d_lmax,     h->d_seg_s,    h->d_seg_e,    h->d_seg_sig,  h->d_phase_list,
                     h->touched,    h->tile_rep,   h->d_queue,    h->d_sig_alt,
                     h->nz_count,   h->nz_ent,     h->shard.d_rt_sig, h->shard.d_ot_sig,
@@ -637,8 +638,10 @@ int csc_init_batch(csc_handle_t h, const float *X, const int64_t *T, int n, cons
     h->sigs.assign(n, SigDesc{});
     for (int i = 0; i < n && i < (int)tol_prev.size(); i++)
         h->sigs[i].tol = tol_prev[i];
-    std::vector<int64_t> tile_s, rtile_s;
-    std::vector<int> tile_sig, rtile_sig;
+    // tiles over each signal: the objective's (kTile samples) and the
+    // resync's (kResyncCols columns); the host keeps only the first tile of
+    // each signal, the device expands the tables from it
+    std::vector<int64_t> rtile_off(n + 1, 0);
     h->tile_off.assign(n + 1, 0);
     for (int i = 0; i < n; i++) {
         SigDesc &d = h->sigs[i];
@@ -649,27 +652,25 @@ int csc_init_batch(csc_handle_t h, const float *X, const int64_t *T, int n, cons
         d.ld = Tz;
         d.ldx = Ttot;
         d.Tz = T[i] - h->L + 1;
-        h->tile_off[i] = (int64_t)tile_s.size();
-        for (int64_t t = 0; t < T[i]; t += kTile) {
-            tile_s.push_back(t);
-            tile_sig.push_back(i);
-        }
-        for (int64_t t = 0; t < d.Tz; t += kResyncCols) {
-            rtile_s.push_back(t);
-            rtile_sig.push_back(i);
-        }
+        h->tile_off[i + 1] = h->tile_off[i] + (T[i] + kTile - 1) / kTile;
+        rtile_off[i + 1] = rtile_off[i] + (d.Tz + kResyncCols - 1) / kResyncCols;
     }
-    h->tile_off[n] = (int64_t)tile_s.size();
-    h->ntiles = (int64_t)tile_s.size();
-    h->nrtiles = (int64_t)rtile_s.size();
+    h->ntiles = h->tile_off[n];
+    h->nrtiles = rtile_off[n];
     h->E_sig.assign(n, 0.0);
     h->lmax.assign(n, 0.0);
     if (h->tiles_a != h->a || h->tiles_L != h->L) {
-        CSC_CUDA(upload(&h->d_tile_s, &h->cap_tile_s, tile_s, s));
-        CSC_CUDA(upload(&h->d_tile_sig, &h->cap_tile_sig, tile_sig, s));
         CSC_CUDA(upload(&h->d_tile_off, &h->cap_tile_off, h->tile_off, s));
-        CSC_CUDA(upload(&h->d_rtile_s, &h->cap_rtile_s, rtile_s, s));
-        CSC_CUDA(upload(&h->d_rtile_sig, &h->cap_rtile_sig, rtile_sig, s));
+        CSC_CUDA(upload(&h->d_rtile_off, &h->cap_rtile_off, rtile_off, s));
+        CSC_CUDA(grow(&h->d_tile_s, &h->cap_tile_s, (size_t)h->ntiles));
+        CSC_CUDA(grow(&h->d_tile_sig, &h->cap_tile_sig, (size_t)h->ntiles));
+        CSC_CUDA(grow(&h->d_rtile_s, &h->cap_rtile_s, (size_t)h->nrtiles));
+        CSC_CUDA(grow(&h->d_rtile_sig, &h->cap_rtile_sig, (size_t)h->nrtiles));
+        CSC_CUDA(launch_expand_tiles(h->d_tile_off, n, kTile, h->ntiles, h->d_tile_s,
+                                     h->d_tile_sig, s));
+        CSC_CUDA(launch_expand_tiles(h->d_rtile_off, n, kResyncCols, h->nrtiles, h->d_rtile_s,
+                                     h->d_rtile_sig, s));
+        h->launches += 2;
         h->tiles_a = h->a;
         h->tiles_L = h->L;
     }

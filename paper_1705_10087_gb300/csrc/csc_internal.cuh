@@ -254,6 +254,12 @@ cudaError_t launch_coef_by_lag(const float *C, int K, int L, float *Ct, cudaStre
 // beta0 = D~ * X, max |beta0| into *absmax_bits, and sum X^2 added to *x2sum
 // (so E(0) = x2sum / 2).  r_out != NULL receives a second copy of beta0 (the
 // state r of a cold start, Z = 0).
+// Tile table of a batch: tile i of the problems belongs to signal sig[i] =
+// the last j with off[j] <= i (off[n] = count, every signal has a tile) and
+// starts at column (i - off[sig[i]]) * width of that signal.
+cudaError_t launch_expand_tiles(const int64_t *off, int n, int width, int64_t count,
+                                int64_t *start, int *sig, cudaStream_t s);
+
 cudaError_t launch_dtx(const float *D, const float *X, int K, int P, int L, int64_t T,
                        float *beta0, float *r_out, unsigned int *absmax_bits, double *x2sum,
                        cudaStream_t s);

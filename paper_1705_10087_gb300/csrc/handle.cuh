@@ -104,9 +104,9 @@ struct csc_handle_s {
     // objective / absmax tiles (kTile samples) and resync tiles (kResyncCols columns)
     std::vector<int64_t> tile_off;  // [n+1] first objective tile of each signal
     int64_t ntiles = 0, nrtiles = 0;
-    int64_t *d_tile_s = nullptr, *d_tile_off = nullptr, *d_rtile_s = nullptr;
+    int64_t *d_tile_s = nullptr, *d_tile_off = nullptr, *d_rtile_s = nullptr, *d_rtile_off = nullptr;
     int *d_tile_sig = nullptr, *d_rtile_sig = nullptr;
-    size_t cap_rtile_s = 0, cap_rtile_sig = 0;
+    size_t cap_rtile_s = 0, cap_rtile_sig = 0, cap_rtile_off = 0;
     double *d_E = nullptr;
     unsigned int *d_lmax = nullptr;
     size_t cap_tile_s = 0, cap_tile_off = 0, cap_tile_sig = 0, cap_E = 0, cap_lmax = 0;

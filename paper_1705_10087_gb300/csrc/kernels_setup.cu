@@ -202,6 +202,41 @@ cudaError_t launch_dtd(const float *D, int K, int P, int L, float *C, float *nor
     return cudaGetLastError();
 }
 
+namespace {
+
+// one thread per tile: binary search of its signal in off[0..n]
+__global__ void expand_tiles_kernel(const int64_t *__restrict__ off, int n, int width,
+                                    int64_t count, int64_t *__restrict__ start,
+                                    int *__restrict__ sig)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = n;  // off[lo] <= i < off[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (off[mid] <= i)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        start[i] = (i - off[lo]) * width;
+        sig[i] = lo;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_expand_tiles(const int64_t *off, int n, int width, int64_t count,
+                                int64_t *start, int *sig, cudaStream_t s)
+{
+    if (count <= 0)
+        return cudaSuccess;
+    const int64_t blocks = (count + 255) / 256;
+    expand_tiles_kernel<<<(unsigned)(blocks < 8192 ? blocks : 8192), 256, 0, s>>>(off, n, width,
+                                                                                 count, start, sig);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_dtx(const float *D, const float *X, int K, int P, int L, int64_t T,
                        float *beta0, float *r_out, unsigned int *absmax_bits, double *x2sum,
                        cudaStream_t s)
