@@ -861,13 +861,13 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
         *acc += ms;
         return CSC_OK;
     };
-    CSC_CUDA(cudaMemsetAsync(h->dirty, 1, (size_t)M, s));
-    // the first resync of the solve recomputes every tile
-    CSC_CUDA(cudaMemsetAsync(h->touched, 1, (size_t)M, s));
-    CSC_CUDA(cudaMemsetAsync(sc, 0, offsetof(Scratch, lmax_bits), s));
-    CSC_CUDA(cudaMemsetAsync(sc->red, 0, sizeof(sc->red), s));
     CSC_CUDA(cudaEventRecord(h->ev0, s));
-    CSC_CUDA(launch_stamp(&sc->tstart, s));
+    // trace ring, counters and red zeroed (Scratch up to x2), every segment
+    // dirty and, so that the first resync of the solve recomputes every tile,
+    // touched; the start stamped
+    CSC_CUDA(launch_solve_begin(reinterpret_cast<unsigned long long *>(sc),
+                                (int64_t)(offsetof(Scratch, x2) / sizeof(unsigned long long)),
+                                h->dirty, h->touched, M, &sc->tstart, s));
     h->launches += 1;
     const bool cold = h->z_is_zero;
     double E0 = 0.0;
@@ -929,18 +929,16 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
         int rc = batch_graph(h, pp, cfg, S, resident, sc->gctr, &gexec);
         if (rc != CSC_OK)
             return rc;
-        if (gexec) {
-            CSC_CUDA(launch_set_int(sc->gctr, 0, s));
-            h->launches += 1;
-        }
+        // (the launch counter gctr[0] starts at 0: solve_begin)
     }
     for (;;) {
         const int64_t g_round = g;
-        CSC_CUDA(cudaMemsetAsync(&sc->done, 0, sizeof(int), s));
-        if (gexec) {
-            CSC_CUDA(launch_set_int(sc->gctr + 1, (int)g_round, s));
-            h->launches += 1;
-        }
+        // done cleared, the round's first launch index and the stopping rules
+        // tested on the device (launch_round_step) set
+        CSC_CUDA(launch_round_begin(&sc->done, sc->gctr, (int)g_round, sc->round_lim, max_updates,
+                                    max_resyncs > 0 ? (long long)kDriftSweeps * c : 0,
+                                    (long long)max_sweeps * c, kPhaseRing, s));
+        h->launches += 1;
         bool round_done = false, forced = false;
         for (;;) {
             int nb = 0;  // launches in this poll batch
@@ -948,15 +946,12 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
             if (graphed) {
                 // the round runs on the device, batch after batch, until one of
                 // the stopping rules tested below holds (launch_round_step)
-                CSC_CUDA(launch_set_limits(sc->round_lim, max_updates,
-                                           max_resyncs > 0 ? (long long)kDriftSweeps * c : 0,
-                                           (long long)max_sweeps * c, kPhaseRing, s));
                 if (timed)
                     CSC_CUDA(cudaEventRecord(h->kev[0], s));
                 CSC_CUDA(cudaGraphLaunch(gexec, s));
                 if (timed)
                     CSC_CUDA(cudaEventRecord(h->kev[1], s));
-                h->launches += 1;
+                // (the graph's launches are counted after the poll)
             } else {
                 for (int i = 0; i < S; i++)
                     for (int p = 0; p < c; p++) {
@@ -989,11 +984,8 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
                         g++;
                     }
             }
-            CSC_CUDA(cudaMemcpyAsync(h->poll, &sc->total, sizeof(long long) + sizeof(int),
-                                     cudaMemcpyDeviceToHost, s));
-            if (graphed)
-                CSC_CUDA(cudaMemcpyAsync(&h->poll->g_next, &sc->gctr[0], sizeof(int),
-                                         cudaMemcpyDeviceToHost, s));
+            // total, done and the next launch index in one copy
+            CSC_CUDA(cudaMemcpyAsync(h->poll, &sc->total, sizeof(Poll), cudaMemcpyDeviceToHost, s));
             CSC_CUDA(cudaStreamSynchronize(s));
             if (int rc = finish_init(h))  // (beta0 came before this poll in the stream)
                 return rc;
@@ -1115,10 +1107,7 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
     if (Z_out)
         CSC_CUDA(copy_out(Z_out, h->Z, sizeof(float) * h->K * Tz, s));
     Fin *fin = h->fin;
-    CSC_CUDA(cudaMemcpyAsync(fin->red, sc->red, sizeof fin->red, cudaMemcpyDeviceToHost, s));
-    CSC_CUDA(cudaMemcpyAsync(&fin->x2, &sc->x2, sizeof fin->x2, cudaMemcpyDeviceToHost, s));
-    CSC_CUDA(cudaMemcpyAsync(&fin->total, &sc->total, sizeof fin->total, cudaMemcpyDeviceToHost, s));
-    CSC_CUDA(cudaMemcpyAsync(&fin->visits, &sc->visits, sizeof fin->visits, cudaMemcpyDeviceToHost, s));
+    CSC_CUDA(cudaMemcpyAsync(fin, &sc->total, sizeof(Fin), cudaMemcpyDeviceToHost, s));
     CSC_CUDA(cudaStreamSynchronize(s));
     const double E = objectives_done(h);
     if (timed) {

@@ -220,9 +220,6 @@ bool phase_warp_eligible(int K, int L, int w_max);
 // active = number of segments in pp.phase_list (the grid size).
 cudaError_t launch_phase(const PhaseParams &pp, const PhaseConfig &cfg, int active,
                          cudaStream_t s);
-// Device counters for launches replayed from a CUDA graph: *p = v; *p += v.
-cudaError_t launch_set_int(int *p, int v, cudaStream_t s);
-cudaError_t launch_add_int(int *p, int v, cudaStream_t s);
 // The last node of a poll batch in the graph of a CD round (a while loop over
 // batches): gctr[0] += batch (the launch index of the next launch), then the
 // loop's condition is set to go on unless the round's sweep found nothing to
@@ -232,8 +229,16 @@ cudaError_t launch_add_int(int *p, int v, cudaStream_t s);
 cudaError_t launch_round_step(cudaGraphConditionalHandle cond, int *gctr, int batch,
                               const int *done, const long long *total, const long long *lim,
                               cudaStream_t s);
-cudaError_t launch_set_limits(long long *lim, long long max_updates, long long drift_launches,
-                              long long max_g, long long ring, cudaStream_t s);
+// Start of a CD round: *done = 0, gctr[1] = g_round and the stopping rules
+// lim = {max_updates, drift_launches, max_g, ring} tested by launch_round_step.
+cudaError_t launch_round_begin(int *done, int *gctr, int g_round, long long *lim,
+                               long long max_updates, long long drift_launches, long long max_g,
+                               long long ring, cudaStream_t s);
+// Start of a solve: zero[0 .. nwords) = 0, dirty[0 .. M) = touched[0 .. M) = 1
+// and *tstart = the global timer, in one launch.
+cudaError_t launch_solve_begin(unsigned long long *zero, int64_t nwords, unsigned char *dirty,
+                               unsigned char *touched, int64_t M, unsigned long long *tstart,
+                               cudaStream_t s);
 // Blocks of the phase kernel that are resident at once on the whole GPU.
 int phase_resident_blocks(const PhaseConfig &cfg, int K);
 // The same phase as launch_phase, for phase lists much longer than the
@@ -358,6 +363,5 @@ cudaError_t launch_objective_single(const float *D, const SigDesc &one, int K, i
 cudaError_t launch_signal_absmax(const SigDesc *sig, Tiles tiles, int K, unsigned int *out,
                                  cudaStream_t s);
 
-cudaError_t launch_stamp(unsigned long long *out, cudaStream_t s);
 
 }  // namespace csc

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstddef>
 #include <cstring>
 #include <vector>
 
@@ -20,34 +21,58 @@ struct Scratch {
     long long upd[kPhaseRing];
     double dec[kPhaseRing];
     unsigned long long tend[kPhaseRing];
+    // polled after a CD round (Poll mirrors total .. gctr[0]); zeroed at the
+    // start of a solve up to red (solve_begin)
     long long total;
     int done;
+    int gctr[2];   // graph replays: launch index of the next launch, first index of the round
     int pad;
     long long visits;
-    unsigned int lmax_bits;
-    unsigned long long tstart;
     unsigned long long red[8];
-    double obj[2];
     double x2;  // sum X^2 of the last csc_init
+    // (the end of a solve reads total .. x2 back in one copy: Fin)
+    unsigned int lmax_bits;
     int tc_err;  // a bounded wait of the tensor-core beta0 kernel gave up
+    unsigned long long tstart;
+    double obj[2];
     int qhead[2];  // drain launches: next queue entry, queue length
-    int gctr[2];   // graph replays: launch index of the next launch, first index of the round
     long long round_lim[4];  // stopping rules of a CD round run as a graph (launch_round_step)
 };
 
-// Host mirror of what the solve loop polls (pinned).
+// Host mirror of what the solve loop polls (pinned): Scratch::total .. gctr[0].
 struct Poll {
     long long total;
     int done;
     int g_next;  // launch index after a CD round run as a graph (Scratch::gctr[0])
 };
 
-// What the end of a solve reads back, in one pinned block (one wait).
+// What the end of a solve reads back, in one pinned block and one copy:
+// Scratch::total .. x2.
 struct Fin {
+    long long total;
+    int done;
+    int gctr[2];
+    int pad;
+    long long visits;
     unsigned long long red[8];
     double x2;
-    long long total, visits;
 };
+
+#define CSC_MIRRORS(S, f)                                                               \
+    static_assert(offsetof(S, f) == offsetof(Scratch, f) - offsetof(Scratch, total), \
+                  #S " mirrors Scratch")
+CSC_MIRRORS(Poll, total);
+CSC_MIRRORS(Poll, done);
+static_assert(offsetof(Poll, g_next) == offsetof(Scratch, gctr) - offsetof(Scratch, total),
+              "Poll mirrors Scratch");
+CSC_MIRRORS(Fin, done);
+CSC_MIRRORS(Fin, gctr);
+CSC_MIRRORS(Fin, visits);
+CSC_MIRRORS(Fin, red);
+CSC_MIRRORS(Fin, x2);
+static_assert(sizeof(Fin) == offsetof(Scratch, lmax_bits) - offsetof(Scratch, total),
+              "Fin mirrors Scratch");
+#undef CSC_MIRRORS
 
 // The host-side segment plan of one shard (shard.cu); empty for ordinary handles.
 struct ShardState {

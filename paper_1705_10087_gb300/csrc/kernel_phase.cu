@@ -967,28 +967,7 @@ __global__ void compact_phase_kernel(const int *__restrict__ list, int count,
     }
 }
 
-__global__ void set_int_kernel(int *p, int v)
-{
-    *p = v;
-}
-__global__ void add_int_kernel(int *p, int v)
-{
-    *p += v;
-}
-
 }  // namespace
-
-cudaError_t launch_set_int(int *p, int v, cudaStream_t s)
-{
-    set_int_kernel<<<1, 1, 0, s>>>(p, v);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_add_int(int *p, int v, cudaStream_t s)
-{
-    add_int_kernel<<<1, 1, 0, s>>>(p, v);
-    return cudaGetLastError();
-}
 
 bool phase_warp_eligible(int K, int L, int wmax)
 {

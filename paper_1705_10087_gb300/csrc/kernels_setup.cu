@@ -182,11 +182,6 @@ __global__ void coef_by_lag_kernel(const float *__restrict__ C, int K, int L, in
     }
 }
 
-__global__ void stamp_kernel(unsigned long long *out)
-{
-    *out = globaltimer_ns();
-}
-
 }  // namespace
 
 cudaError_t launch_dtd(const float *D, int K, int P, int L, float *C, float *norms,
@@ -263,12 +258,6 @@ cudaError_t launch_coef_by_lag(const float *C, int K, int L, float *Ct, cudaStre
     const long long grid = (n + 255) / 256;
     coef_by_lag_kernel<<<(unsigned)(grid < 65535 ? grid : 65535), 256, 0, s>>>(C, K, L,
                                                                             coef_pad(K), Ct);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_stamp(unsigned long long *out, cudaStream_t s)
-{
-    stamp_kernel<<<1, 1, 0, s>>>(out);
     return cudaGetLastError();
 }
 

@@ -258,7 +258,7 @@ int csc_shard_init(csc_handle_t h, const csc_shard_plan *plan, const float *X, d
     if (sh.hr > 0)
         SH_CUDA(cudaMemset2DAsync(h->r + own_hi, sizeof(float) * ld, 0, sizeof(float) * sh.hr,
                                   h->K, s));
-    SH_CUDA(cudaMemsetAsync(h->sc, 0, offsetof(Scratch, lmax_bits), s));
+    SH_CUDA(cudaMemsetAsync(h->sc, 0, offsetof(Scratch, red), s));  // trace ring, counters
     SH_CUDA(cudaStreamSynchronize(s));  // host tables outlive their uploads
     h->M = sh.seg_count;
     h->c = c;
