@@ -716,7 +716,10 @@ __global__ void __launch_bounds__(32 * NW + 32, NW <= 4 ? 2 : 1)
         // accumulator buf (use parity par) -> beta0 columns of the tile; false
         // if the wait for its products ran out
         auto epilogue = [&](long long tile, int buf, uint32_t par) -> bool {
-            const bool got = mbar_wait_bounded(done0 + 8u * (uint32_t)buf, par, kWaitLimit);
+            // the warp reads tensor memory together (tcgen05.ld is warp-wide):
+            // it reads only if every lane saw the products finish
+            const bool got = __all_sync(0xffffffffu, mbar_wait_bounded(done0 + 8u * (uint32_t)buf,
+                                                                      par, kWaitLimit));
             if (got) {
                 fence_after_sync();
                 constexpr int CW = N / (NTW / 128);

@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(256)
 // change is >= tol_mark, or the problem's tol when tol_mark < 0).
 // (b0, rold, z, n: beta0, r, Z of the coordinate and ||D_k||^2, already loaded)
 __device__ __forceinline__ void resync_finish_v(const SigDesc &sd, int64_t ix, int64_t t,
-                                                float b0, float rold, float z, float n,
+                                                float b0, float rold, float z, float n, float rn,
                                                 float *__restrict__ rr, float ah, float al,
                                                 float lam, int write_r,
                                                 unsigned char *__restrict__ dirty, float tol_mark,
@@ -163,7 +163,6 @@ __device__ __forceinline__ void resync_finish_v(const SigDesc &sd, int64_t ix, i
     if (write_r)
         rr[ix] = r32;
     drift = fmaxf(drift, fabsf(rold - r32));
-    const float rn = __frcp_rn(n);
     // optimality in the r form (Theorem A.1): z = 0 needs |beta| = |r| <= lam;
     // otherwise |Z' - z| with Z' from Eq. pb_coord, without cancellation
     float gap;
@@ -197,8 +196,9 @@ __device__ __forceinline__ void resync_finish(const SigDesc &sd, int k, int64_t 
                                               float &dz32)
 {
     const int64_t ix = (int64_t)k * sd.ld + t;
-    resync_finish_v(sd, ix, t, b0p[ix], rr[ix], zz[ix], norms[k], rr, ah, al, lam, write_r, dirty,
-                    tol_mark, drift, zex, nzg, all, dz32);
+    const float n = norms[k];
+    resync_finish_v(sd, ix, t, b0p[ix], rr[ix], zz[ix], n, __frcp_rn(n), rr, ah, al, lam, write_r,
+                    dirty, tol_mark, drift, zex, nzg, all, dz32);
 }
 
 // KPT = 4 NG atoms per thread: thread group g (of kResyncGroups) owns the
@@ -413,6 +413,7 @@ __global__ void __launch_bounds__(256, 2)
     constexpr int NB = NG == 1 ? 8 : 4;  // nonzeros whose coefficients are loaded together
     constexpr unsigned kFullMask = 0xffffffffu;
     __shared__ float bred[5][32];
+    __shared__ int s_need;
     const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5, nwq = blockDim.x >> 5;
     const int64_t b = blockIdx.x;
     const int isig = tiles.sig[b];
@@ -429,7 +430,12 @@ __global__ void __launch_bounds__(256, 2)
     const int64_t tend = tiles.end && tiles.end[b] < Tz ? tiles.end[b] : Tz;
     const bool col_ok = t < tend;
     float drift = 0.f, zex = 0.f, nzg = 0.f, all = 0.f, dz32 = 0.f;
-    const bool need = !(touched && rep) || tile_touched(sd, c0, touched);
+    // whether the tile must be recomputed: decided once per block (the
+    // segment range of the tile takes two 64-bit divisions)
+    if (threadIdx.x == 0)
+        s_need = !(touched && rep) || tile_touched(sd, c0, touched);
+    __syncthreads();
+    const bool need = s_need != 0;
     if (!need) {
         if (lane == 0 && wq == 0) {  // the stored report of the unchanged tile (drift 0)
             zex = rep[5 * b + 1];
@@ -440,6 +446,9 @@ __global__ void __launch_bounds__(256, 2)
     } else {
         // this lane's coordinates: its state first (one round trip for all)
         float b0v[KPT], rov[KPT], zv[KPT], nv[KPT];
+        // 1 / ||D_k||^2 of the warp's KPT atoms: lane q computes atom q's
+        const int kq = 4 * (g0 + (lane % KPT) / 4) + (lane % KPT) % 4;
+        const float rn_lane = __frcp_rn(kq < K ? norms[kq] : 1.f);
 #pragma unroll
         for (int q = 0; q < KPT; q++) {
             const int k = 4 * (g0 + q / 4) + (q % 4);
@@ -459,18 +468,19 @@ __global__ void __launch_bounds__(256, 2)
         const float4 *Ct4 = reinterpret_cast<const float4 *>(Ct);
         // NB nonzeros (k, column, z) at a time: loads first, then the sums; a
         // nonzero out of this lane's window (z = 0 there) adds nothing
-        auto add_batch = [&](const int (&kk)[NB], const int64_t (&tc)[NB], const float (&z)[NB]) {
+        // (column offsets relative to the tile start c0: 32-bit)
+        auto add_batch = [&](const int (&kk)[NB], const int (&tc)[NB], const float (&z)[NB]) {
             float4 cv[NB][NG];
             float zz_[NB];
 #pragma unroll
             for (int e = 0; e < NB; e++) {
-                const int d = (int)(t - tc[e]) + (L - 1);
+                const int d = lane - tc[e] + (L - 1);
                 const bool in = col_ok && z[e] != 0.f && d >= 0 && d < W2;
                 zz_[e] = in ? z[e] : 0.f;
-                const int64_t base = (int64_t)kk[e] * G * W2 + (in ? d : 0);
+                const int base = (kk[e] * G + g0) * W2 + (in ? d : 0);
 #pragma unroll
                 for (int gi = 0; gi < NG; gi++)
-                    cv[e][gi] = in && g0 + gi < G ? __ldg(Ct4 + base + (int64_t)(g0 + gi) * W2)
+                    cv[e][gi] = in && g0 + gi < G ? __ldg(Ct4 + base + gi * W2)
                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
             }
 #pragma unroll
@@ -517,19 +527,22 @@ __global__ void __launch_bounds__(256, 2)
                 const int xj = __shfl_sync(kFullMask, excl, j);
                 const uint2 v = e < total ? lists.ent[(b - R + j) * kNzCap + (e - xj)]
                                           : make_uint2(0u, 0u);
-                const int64_t cb = c0 + (int64_t)(j - R) * kResyncCols;
+                // atom and column offset from c0 in one word: k << 16 | (offset + 1024)
+                // (offsets lie in [-32 R, 32 R + 32), 2R + 1 <= 32)
+                const int off = (j - R) * kResyncCols + (int)(v.x % kResyncCols);
+                const unsigned pk = ((v.x / kResyncCols) << 16) | (unsigned)(off + 1024);
                 const int m = total - e0 < 32 ? total - e0 : 32;
                 for (int i0 = 0; i0 < m; i0 += NB) {
                     int kk[NB];
-                    int64_t tc[NB];
+                    int tc[NB];
                     float z[NB];
 #pragma unroll
                     for (int x = 0; x < NB; x++) {
                         const int src = i0 + x < m ? i0 + x : 0;
-                        const unsigned vx = __shfl_sync(kFullMask, v.x, src);
+                        const unsigned px = __shfl_sync(kFullMask, pk, src);
                         const float zx = __uint_as_float(__shfl_sync(kFullMask, v.y, src));
-                        kk[x] = (int)(vx / kResyncCols);
-                        tc[x] = __shfl_sync(kFullMask, cb, src) + (vx % kResyncCols);
+                        kk[x] = (int)(px >> 16);
+                        tc[x] = (int)(px & 0xffffu) - 1024;
                         z[x] = i0 + x < m ? zx : 0.f;
                     }
                     add_batch(kk, tc, z);
@@ -550,14 +563,14 @@ __global__ void __launch_bounds__(256, 2)
                     unsigned msk = __ballot_sync(kFullMask, zq != 0.f);
                     while (msk) {
                         int kk[NB];
-                        int64_t tc[NB];
+                        int tc[NB];
                         float z[NB];
 #pragma unroll
                         for (int x = 0; x < NB; x++) {
                             const int src = msk ? __ffs((int)msk) - 1 : 0;
                             const float zx = __shfl_sync(kFullMask, zq, src);
                             kk[x] = k;
-                            tc[x] = cb + src;
+                            tc[x] = (q - R) * kResyncCols + src;
                             z[x] = msk ? zx : 0.f;
                             msk &= msk - 1;
                         }
@@ -567,15 +580,16 @@ __global__ void __launch_bounds__(256, 2)
             }
         }
         const float lam = sd.lam;
-        if (col_ok) {
 #pragma unroll
-            for (int q = 0; q < KPT; q++) {
-                const int k = 4 * (g0 + q / 4) + (q % 4);
-                if (k < K)
-                    resync_finish_v(sd, (int64_t)k * ld + t, t, b0v[q], rov[q], zv[q], nv[q], rr,
-                                    acc_hi[q], acc_lo[q], lam, write_r, dirty, tol_mark, drift,
-                                    zex, nzg, all, dz32);
-            }
+        for (int q = 0; q < KPT; q++) {
+            const int k = 4 * (g0 + q / 4) + (q % 4);
+            // every lane takes part in the shuffle (col_ok differs across the
+            // lanes of a signal's last tile)
+            const float rn = __shfl_sync(kFullMask, rn_lane, q);
+            if (col_ok && k < K)
+                resync_finish_v(sd, (int64_t)k * ld + t, t, b0v[q], rov[q], zv[q], nv[q], rn, rr,
+                                acc_hi[q], acc_lo[q], lam, write_r, dirty, tol_mark, drift, zex,
+                                nzg, all, dz32);
         }
     }
     for (int off = 16; off > 0; off >>= 1) {
