@@ -17,9 +17,10 @@
 //   2. keeps, per owned column t, the best coordinate over k of
 //      |Delta Z_k[t]| = |Sh(beta_k[t], lambda)/||D_k||^2 - Z_k[t]| (Eq. pb_coord,
 //      evaluated from r by coord_step) as a 64-bit key
-//      (|Delta Z| bits << 32 | ~(k*w + t - s)): the max key is the largest
+//      (|Delta Z| bits << 32 | ~(k << 16 | t - s)): the max key is the largest
 //      |Delta Z| with ties to the lowest (k, t), i.e. the lowest k*Tz + t,
-//   3. repeats: block argmax (warp max + one barrier), stop if the best
+//   3. repeats: block argmax (warp max, a shared atomicMax per warp, one
+//      barrier; the key names the winner), stop if the best
 //      |Delta Z| < tol (Alg. 1 stopping rule) or after u updates, else
 //      Z_k0[t0] <- Z' and r_k[t] -= S_{k,k0}[t-t0] (Z' - Z_old) for every k
 //      and t in [t0-L+1, t0+L-1] (Eq. beta_up, sign fixed by the beta
@@ -72,24 +73,20 @@ __host__ __device__ inline bool vec_layout(int K, int block)
 // Shared-memory layout of a block, in bytes from the start (16-byte aligned
 // pieces).  w = widest segment; with smem the segment's r and Z are staged.
 struct Layout {
-    size_t key, slot_key, cz, cd, ck, zm, slot_v, nrm, rnrm, r, z, total;
+    size_t key, cz, cd, ck, zm, nrm, rnrm, r, z, total;
     __host__ __device__ Layout(int K, int w, bool smem, bool vec)
     {
         size_t o = 0;
         key = o;
         o = up(o + 8 * (size_t)w);
-        slot_key = o;
-        o = up(o + 8 * 64);
         cz = o;
         o = up(o + 4 * (size_t)w);
         cd = o;
         o = up(o + 4 * (size_t)w);
-        ck = o;
+        ck = o;  // the best atom of a column (the one-warp form's winner read)
         o = up(o + 4 * (size_t)w);
         zm = o;  // per column: bit k set when Z_k[t] != 0 (compile-time K <= 64)
         o = up(o + 8 * (size_t)w);
-        slot_v = o;  // per warp candidate: (Z', dZ, k, column) as one 16-byte word
-        o = up(o + 16 * 64);
         nrm = o;
         o = up(o + 4 * (size_t)K);
         rnrm = o;
@@ -123,6 +120,10 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_go;
     __shared__ double s_dec[32];
+    // the block's best key of update i is reduced into s_best[i & 3] (a 64-bit
+    // shared atomicMax per warp); slot (i + 2) & 3, last read in update i - 2,
+    // is cleared during update i
+    __shared__ unsigned long long s_best[4];
 
     // ---- early exits, decided by one thread so the block stays uniform ----
     // (total is being incremented by other blocks of this launch)
@@ -170,15 +171,12 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
     constexpr int KQ = (KT + 3) / 4;      // float4 groups holding the KT atoms
     const Layout lay(K, pp.w_max, SMEM, KFIX);
     unsigned long long *ckey = reinterpret_cast<unsigned long long *>(smem_raw + lay.key);
-    unsigned long long *slot_key = reinterpret_cast<unsigned long long *>(smem_raw + lay.slot_key);
     float *cz = reinterpret_cast<float *>(smem_raw + lay.cz);
     float *cd = reinterpret_cast<float *>(smem_raw + lay.cd);
-    int *ck = reinterpret_cast<int *>(smem_raw + lay.ck);
     // one bit per atom of a column: 32 or 64 bits
     using Mask = typename std::conditional<(KT > 32), unsigned long long, unsigned>::type;
     static_assert(KT <= 64, "the masks of a column hold 64 atoms");
     Mask *zmask = reinterpret_cast<Mask *>(smem_raw + lay.zm);
-    uint4 *slot_v = reinterpret_cast<uint4 *>(smem_raw + lay.slot_v);
     float *nrm = reinterpret_cast<float *>(smem_raw + lay.nrm);    // ||D_k||^2
     float *rnrm = reinterpret_cast<float *>(smem_raw + lay.rnrm);  // 1 / ||D_k||^2
 
@@ -214,6 +212,8 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
         nrm[k] = pp.norms[k];
         rnrm[k] = __frcp_rn(pp.norms[k]);
     }
+    if (tid < 4)
+        s_best[tid] = 0ull;
     __syncthreads();
 
     // best coordinate of own column jj from its r values (registers) and the
@@ -253,13 +253,13 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
                 bdz = d2;
             }
         }
-        // segment-local flat index: same order as k * Tz + t inside the segment
-        const unsigned flat = (unsigned)bk * (unsigned)pp.w_max + (unsigned)jj;
+        // segment-local index k << 16 | jj: same order as k * Tz + t inside the
+        // segment (jj < w_max < 2^16: the column caches live in shared memory)
+        const unsigned flat = ((unsigned)bk << 16) | (unsigned)jj;
         ckey[jj] = best > 0.f ? ((unsigned long long)__float_as_uint(best) << 32) | (unsigned)(~flat)
                               : 0ull;
         cz[jj] = bz;
         cd[jj] = bdz;
-        ck[jj] = bk;
     };
 
     // best coordinate of own column jj over k
@@ -298,12 +298,11 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
             for (int k = 0; k < K; k++)
                 visit(k);
         }
-        const unsigned flat = (unsigned)bk * (unsigned)pp.w_max + (unsigned)jj;
+        const unsigned flat = ((unsigned)bk << 16) | (unsigned)jj;
         ckey[jj] = best > 0.f ? ((unsigned long long)__float_as_uint(best) << 32) | (unsigned)(~flat)
                               : 0ull;
         cz[jj] = bz;
         cd[jj] = bdz;
-        ck[jj] = bk;
     };
     if constexpr (SMEM && KFIX) {
         // a column's KT values of r and of Z in one round trip of independent
@@ -340,63 +339,25 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
     }
     // (no barrier needed: each thread reads back only its own columns)
 
-    int buf = 0, nupd = 0;
+    int nupd = 0;
     float decrease = 0.f;  // this thread's updates of the visit (at most u terms)
     int64_t tmin = Tz, tmax = -1;
     bool capped = false;
     for (int it = 0;; it++) {
         // ---- block argmax of the cached column keys ----------------------
         unsigned long long my = 0ull;
-        int myj = 0;
         for (int jj = tid; jj < w; jj += B) {
             const unsigned long long kk = ckey[jj];
-            if (kk > my) {
+            if (kk > my)
                 my = kk;
-                myj = jj;
-            }
         }
-        // the candidate's values are read while the warp reduction runs
-        const float my_z = cz[myj], my_d = cd[myj];
-        const int my_k = ck[myj];
         const unsigned long long wm = warp_max_u64(my);
-        const unsigned win = __ballot_sync(kFull, my == wm);
-        if (lane == __ffs(win) - 1) {
-            slot_key[buf * 32 + warp] = wm;
-            slot_v[buf * 32 + warp] =
-                make_uint4(__float_as_uint(my_z), __float_as_uint(my_d), (unsigned)my_k, (unsigned)myj);
-        }
+        if (lane == 0 && wm != 0ull)
+            atomicMax(&s_best[it & 3], wm);
+        if (tid == 0)
+            s_best[(it + 2) & 3] = 0ull;
         __syncthreads();
-        // every warp's candidate in one round of independent loads (up to 4
-        // warps; wider blocks read the winner's values after the key scan)
-        constexpr int NV = nwarps <= 4 ? nwarps : 1;
-        unsigned long long kv[NV];
-        uint4 vv[NV];
-#pragma unroll
-        for (int i = 0; i < NV; i++) {
-            kv[i] = slot_key[buf * 32 + i];
-            vv[i] = slot_v[buf * 32 + i];
-        }
-        unsigned long long bk = 0ull;
-        int bw = 0;
-        uint4 bv = vv[0];
-        if constexpr (nwarps <= 4) {
-#pragma unroll
-            for (int i = 0; i < nwarps; i++)
-                if (kv[i] > bk) {
-                    bk = kv[i];
-                    bw = i;
-                    bv = vv[i];
-                }
-        } else {
-            for (int i = 0; i < nwarps; i++) {
-                const unsigned long long kk = slot_key[buf * 32 + i];
-                if (kk > bk) {
-                    bk = kk;
-                    bw = i;
-                }
-            }
-            bv = slot_v[buf * 32 + bw];
-        }
+        const unsigned long long bk = s_best[it & 3];
         const float adz = __uint_as_float((unsigned)(bk >> 32));
         if (!(adz >= tol))
             break;
@@ -404,9 +365,11 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
             capped = true;
             break;
         }
-        const float znew = __uint_as_float(bv.x), delta = __uint_as_float(bv.y);
-        const int k0 = (int)bv.z;
-        const int64_t t0 = s + (int)bv.w;
+        // the winner (k0, column) from its key; its step from the column caches
+        const unsigned flat = ~(unsigned)bk;
+        const int k0 = (int)(flat >> 16), jw = (int)(flat & 0xffffu);
+        const float znew = cz[jw], delta = cd[jw];
+        const int64_t t0 = s + jw;
 
         // ---- Eq. beta_up (r form) on the window -------------------------
         const int64_t tlo = t0 - (L - 1);
@@ -512,7 +475,6 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
         nupd++;
         tmin = t0 < tmin ? t0 : tmin;
         tmax = t0 > tmax ? t0 : tmax;
-        buf ^= 1;
     }
 
     // ---- write back, spill bookkeeping, trace ---------------------------
