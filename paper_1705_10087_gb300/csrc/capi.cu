@@ -202,8 +202,9 @@ int build_plan(csc_handle_t h)
     return CSC_OK;
 }
 
-// Per-signal objectives of Zd into pinned h->E_pin, not waited for.
-int objectives_async(csc_handle_t h, const float *Zd)
+// Per-signal objectives of Zd into pinned h->E_pin, not waited for;
+// lists_current: the resync bucket lists describe Zd (no change since).
+int objectives_async(csc_handle_t h, const float *Zd, bool lists_current)
 {
     cudaStream_t s = h->stream;
     if (h->cap_E_pin < (size_t)h->n) {
@@ -215,8 +216,11 @@ int objectives_async(csc_handle_t h, const float *Zd)
         CSC_CUDA(cudaHostAlloc(&h->E_pin, sizeof(double) * h->n, cudaHostAllocDefault));
         h->cap_E_pin = (size_t)h->n;
     }
+    const bool lists = lists_current && Zd == h->Z;
     CSC_CUDA(launch_objective(h->D, h->d_sig, h->n, h->obj_tiles(), h->d_tile_off, h->K, h->P,
-                              h->L, h->Z, Zd == h->Z ? nullptr : Zd, h->partials, h->d_E, s));
+                              h->L, h->Z, Zd == h->Z ? nullptr : Zd, h->partials, h->d_E, s,
+                              lists ? h->nz_lists() : NzLists{nullptr, nullptr},
+                              lists ? h->d_rtile_off : nullptr));
     h->launches += 2;
     CSC_CUDA(cudaMemcpyAsync(h->E_pin, h->d_E, sizeof(double) * h->n, cudaMemcpyDeviceToHost, s));
     return CSC_OK;
@@ -1100,7 +1104,8 @@ int csc_solve(csc_handle_t h, double tol, int64_t max_updates, float *Z_out, dou
     // the objective, the copy of Z and the counters, then one wait
     if (timed)
         CSC_CUDA(cudaEventRecord(h->ev_r0, s));
-    if (int rc = objectives_async(h, h->Z))
+    // (the last resync listed the nonzeros of this Z: the objective re-uses them)
+    if (int rc = objectives_async(h, h->Z, true))
         return rc;
     if (timed)
         CSC_CUDA(cudaEventRecord(h->ev_r1, s));

@@ -348,10 +348,14 @@ cudaError_t launch_beta_from_r(const float *r, const float *Z, const float *norm
 // FP64 objective E_i(Z) (Eq. sparse_code) of every problem into out[i] (tiles
 // of kTile samples, partials[2b..2b+1] for tile b; tile_off[i] = first tile of
 // problem i, n+1 entries).  Zalt != NULL replaces each problem's Z by
-// Zalt + (its Z - Zbase) (same layout, another array).
+// Zalt + (its Z - Zbase) (same layout, another array).  lists: the nonzero
+// buckets of the last resync, valid only if Z has not changed since (its
+// tiles start at rtile_off[i] for problem i); {NULL, NULL} lists Z here.
 cudaError_t launch_objective(const float *D, const SigDesc *sig, int n, Tiles tiles,
                              const int64_t *tile_off, int K, int P, int L, const float *Zbase,
-                             const float *Zalt, double *partials, double *out, cudaStream_t s);
+                             const float *Zalt, double *partials, double *out, cudaStream_t s,
+                             NzLists lists = NzLists{nullptr, nullptr},
+                             const int64_t *rtile_off = nullptr);
 
 // The same for one problem described on the host, with no tables: consecutive
 // tiles, partials holds 2 * ceil(T / kTile) doubles; out[0] = E.

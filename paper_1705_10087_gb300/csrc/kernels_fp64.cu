@@ -645,11 +645,16 @@ __device__ __forceinline__ void obj_add(float (&hi)[kObjP], float (&lo)[kObjP],
 // samples [c0 + 32 w, c0 + 32 w + 32) are reached only by the columns of
 // buckets w .. w + R, so each thread walks R + 1 buckets.  A bucket with more
 // than kObjCap nonzeros is walked straight from Z in the same order.
+// With lists (the buckets of the last resync, which saw this Z: same
+// entries in the same order) a bucket inside the problem is copied from the
+// resync tile starting at its first column, rtile_off[problem] + column / 32.
 __global__ void __launch_bounds__(kTile, 5)
     objective_kernel(const float *__restrict__ D, const SigDesc *__restrict__ sigs, SigDesc one,
                      Tiles tiles, int K, int P, int L, const float *Zbase, const float *Zalt,
-                     double *__restrict__ partials)
+                     double *__restrict__ partials, NzLists lists,
+                     const int64_t *__restrict__ rtile_off)
 {
+    static_assert(kObjCap == kNzCap && kResyncCols == 32, "resync buckets serve the objective");
     __shared__ uint2 ent[kObjBuckets][kObjCap];
     __shared__ int cnt[kObjBuckets];
     __shared__ double bsum[2][kTile / 32];
@@ -668,7 +673,18 @@ __global__ void __launch_bounds__(kTile, 5)
     const int64_t cb0 = c0 - 32 * (int64_t)R;  // bucket j: columns [cb0 + 32 j, cb0 + 32 j + 32)
     const int nb = kTile / 32 + R;
     for (int j = warp; j < nb; j += kTile / 32) {
-        const int64_t col = cb0 + 32 * (int64_t)j + lane;
+        const int64_t cbj = cb0 + 32 * (int64_t)j;
+        if (lists.count && cbj >= 0 && cbj < zhi) {
+            const int64_t rt = rtile_off[tiles.sig[blockIdx.x]] + cbj / kResyncCols;
+            const int n = lists.count[rt];
+            if (n <= kObjCap)
+                for (int i = lane; i < n; i += 32)
+                    ent[j][i] = lists.ent[rt * kNzCap + i];
+            if (lane == 0)
+                cnt[j] = n;
+            continue;
+        }
+        const int64_t col = cbj + lane;
         const bool in = col >= 0 && col < zhi;
         int base = 0;
         for (int k0 = 0; k0 < K; k0 += kBucketBatch) {
@@ -912,12 +928,13 @@ cudaError_t launch_beta_from_r(const float *r, const float *Z, const float *norm
 
 cudaError_t launch_objective(const float *D, const SigDesc *sig, int n, Tiles tiles,
                              const int64_t *tile_off, int K, int P, int L, const float *Zbase,
-                             const float *Zalt, double *partials, double *out, cudaStream_t s)
+                             const float *Zalt, double *partials, double *out, cudaStream_t s,
+                             NzLists lists, const int64_t *rtile_off)
 {
     if (tiles.n <= 0)
         return cudaSuccess;
     objective_kernel<<<(unsigned)tiles.n, kTile, 0, s>>>(D, sig, SigDesc{}, tiles, K, P, L, Zbase,
-                                                         Zalt, partials);
+                                                         Zalt, partials, lists, rtile_off);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
@@ -930,7 +947,8 @@ cudaError_t launch_objective_single(const float *D, const SigDesc &one, int K, i
 {
     const int64_t ntiles = (one.Tz + L - 1 + kTile - 1) / kTile;
     objective_kernel<<<(unsigned)ntiles, kTile, 0, s>>>(D, nullptr, one, Tiles{nullptr, nullptr, 0},
-                                                        K, P, L, nullptr, nullptr, partials);
+                                                        K, P, L, nullptr, nullptr, partials,
+                                                        NzLists{nullptr, nullptr}, nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
