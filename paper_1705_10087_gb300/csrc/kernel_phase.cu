@@ -26,7 +26,8 @@
 //      and t in [t0-L+1, t0+L-1] (Eq. beta_up, sign fixed by the beta
 //      definition, written for r); own columns are updated in shared memory
 //      and re-evaluated, the others (idle neighbours) by atomicAdd,
-//   4. writes its segment back, marks the neighbours it spilled into as
+//   4. writes its segment's r back (each new Z value went to global memory
+//      when it was applied), marks the neighbours it spilled into as
 //      dirty and adds its count and objective decrease (Prop. A.1) to the
 //      per-launch trace.
 // Thread i owns the segment columns jj == i (mod blockDim) and handles, in an
@@ -414,6 +415,8 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
                     // apply and screen in registers, then evaluate the movable entries
                     if (t == t0) {
                         zs[jj * cst + k0 * kst] = znew;
+                        if constexpr (SMEM)
+                            gz[(int64_t)k0 * ld + t0] = znew;  // (the write-back copies r only)
                         const Mask bit = (Mask)1 << k0;
                         zmask[jj] = znew != 0.f ? (zmask[jj] | bit) : (zmask[jj] & ~bit);
                     }
@@ -467,8 +470,11 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
                 }
             }
             if (!KFIX && own) {
-                if (t == t0)
+                if (t == t0) {
                     zs[jj * cst + k0 * kst] = znew;
+                    if constexpr (SMEM)
+                        gz[(int64_t)k0 * ld + t0] = znew;
+                }
                 col_eval(jj);
             }
         }
@@ -478,33 +484,29 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
     }
 
     // ---- write back, spill bookkeeping, trace ---------------------------
+    // (Z changed only at the updated coordinates, each written to global
+    // memory when it was applied: the write-back copies r)
     if (SMEM && nupd > 0) {
         if constexpr (KFIX) {
             // each thread writes back its own columns (128-bit shared reads;
             // the global stores of one atom row are coalesced across threads)
             for (int jj = tid; jj < w; jj += B) {
                 const float4 *rc4 = reinterpret_cast<const float4 *>(rs + jj * CST);
-                const float4 *zc4 = reinterpret_cast<const float4 *>(zs + jj * CST);
 #pragma unroll
                 for (int q = 0; q < KQ; q++) {
-                    const float4 a = rc4[q], b = zc4[q];
-                    const float ra[4] = {a.x, a.y, a.z, a.w}, za[4] = {b.x, b.y, b.z, b.w};
+                    const float4 a = rc4[q];
+                    const float ra[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
                     for (int e = 0; e < 4; e++)
-                        if (4 * q + e < KT) {
+                        if (4 * q + e < KT)
                             gr[(int64_t)(4 * q + e) * ld + s + jj] = ra[e];
-                            gz[(int64_t)(4 * q + e) * ld + s + jj] = za[e];
-                        }
                 }
             }
         } else {
             for (int k = 0; k < K; k++) {
                 float *rdst = gr + (int64_t)k * ld + s;
-                float *zdst = gz + (int64_t)k * ld + s;
-                for (int jj = tid; jj < w; jj += B) {
+                for (int jj = tid; jj < w; jj += B)
                     rdst[jj] = rs[jj * cst + k];
-                    zdst[jj] = zs[jj * cst + k];
-                }
             }
         }
     }
@@ -738,6 +740,7 @@ __device__ __forceinline__ void visit_segment_warp(const PhaseParams &pp, const 
                     const float n = nrm[k0], u = znew, z = znew - delta;
                     decrease += delta * (rcol[k0] - 0.5f * n * delta) + lam * (fabsf(z) - fabsf(u));
                     zs[jj * CST + k0] = znew;
+                    gz[(int64_t)k0 * ld + t0] = znew;  // (the write-back copies r only)
                     const Mask bit = (Mask)1 << k0;
                     zmask[jj] = znew != 0.f ? (zmask[jj] | bit) : (zmask[jj] & ~bit);
                 }
@@ -776,17 +779,14 @@ __device__ __forceinline__ void visit_segment_warp(const PhaseParams &pp, const 
     if (nupd > 0) {
         for (int jj = lane; jj < w; jj += 32) {
             const float4 *rc4 = reinterpret_cast<const float4 *>(rs + jj * CST);
-            const float4 *zc4 = reinterpret_cast<const float4 *>(zs + jj * CST);
 #pragma unroll
             for (int q = 0; q < KQ; q++) {
-                const float4 a = rc4[q], b = zc4[q];
-                const float ra[4] = {a.x, a.y, a.z, a.w}, za[4] = {b.x, b.y, b.z, b.w};
+                const float4 a = rc4[q];
+                const float ra[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
                 for (int c = 0; c < 4; c++)
-                    if (4 * q + c < KT) {
+                    if (4 * q + c < KT)
                         gr[(int64_t)(4 * q + c) * ld + s + jj] = ra[c];
-                        gz[(int64_t)(4 * q + c) * ld + s + jj] = za[c];
-                    }
             }
         }
     }
