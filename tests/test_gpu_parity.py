@@ -288,6 +288,26 @@ def test_deterministic(capi, long_small):
     np.testing.assert_array_equal(a["Z"], b["Z"])
 
 
+@pytest.mark.parametrize("T,M", [(20_000, 64), (5_131, 10)])
+def test_solve_objective_equals_a_fresh_one_bitwise(capi, T, M):
+    # the objective a solve returns is computed from the nonzero lists of its
+    # last resync; csc_objective on the same Z lists Z itself: the same sums in
+    # the same order, so the same double; both match the oracle's E of that Z
+    pb = synth.make_workload("long_P7_K25_L64_T200000", seed=2, T=T)
+    lam = 0.1 * oracle.lambda_max(pb.D, pb.X)
+    h = capi.csc_setup(cuda(pb.D), capi.make_opts(segments=M))
+    try:
+        capi.csc_init(h, cuda(pb.X), lam)
+        Z = torch.zeros((pb.K, pb.Tz), dtype=torch.float32, device="cuda")
+        status, E, st = capi.csc_solve(h, 1e-6, 1 << 40, Z)
+        assert status == capi.CSC_OK
+        assert capi.csc_objective(h, Z) == E
+    finally:
+        capi.csc_destroy(h)
+    Er = oracle.objective(pb.D, pb.X, Z.cpu().numpy().astype(np.float64), lam)
+    assert abs(E - Er) <= 1e-12 * abs(Er)
+
+
 def test_warm_start_from_optimum(capi, short):
     # csc_init with Z0: beta = D~*X - DtD Z0 + n Z0 in FP64 (the beta definition)
     pb, lam, ref, Er = short
