@@ -26,17 +26,17 @@
 //     128 B, N-adjacent at 256 B; row k of core matrix (n8, j8) of split
 //     sigma holds term sigma of D[k = 8 n8 + r][p][tau = 16 s + 8 j8 + 0..7 -
 //     p L16].  The splits of a step are thus one operand of 3N rows.
-// Concatenated products (N = 32, dtx_tc_ws_kernel): per step one M x 3N
-// product of the leading term of X with [D_h D_m D_l] (hh, hm, hl), one M x 2N
-// product of its middle term with [D_h D_m] (mh, mm) and one M x N product of
-// its last term with D_h (lh), into one accumulator of 3N columns: hh + mh +
-// lh, hm + mm and hl, summed in the epilogue.  The tensor cores read each A
-// run three times per step instead of six.  That kernel gives the issue of
-// the products a warp of its own; dtx_tc_kernel (N = 64, or the hh product
-// alone) issues them from thread 0 between the operand build and read-out.
-// The accumulator lives in tensor memory (32-bit columns, lane = t); the warp
-// of each lane quarter reads its 32 lanes with tcgen05.ld and writes
-// beta0[k][t] coalesced along t.
+// Concatenated products (N = 32): per step one M x 3N product of the leading
+// term of X with [D_h D_m D_l] (hh, hm, hl), one M x 2N product of its middle
+// term with [D_h D_m] (mh, mm) and one M x N product of its last term with D_h
+// (lh), into one accumulator of 3N columns: hh + mh + lh, hm + mm and hl,
+// summed in the epilogue.  The tensor cores read each A run three times per
+// step instead of six.  At N = 64 (K > 32) the six products go into one
+// accumulator of N columns (3N columns twice would exceed the 256 a CTA
+// allocates).  One warp issues the products while the others build operands
+// and read accumulators out (dtx_tc_ws_kernel).  The accumulator lives in
+// tensor memory (32-bit columns, lane = t); the warp of each lane quarter
+// reads its 32 lanes with tcgen05.ld and writes beta0[k][t] coalesced along t.
 //
 // What bounds the products: the tensor cores read the operands from shared
 // memory in this unswizzled layout (the Hankel runs of A overlap, which no
@@ -212,304 +212,6 @@ struct TcLayout {
     }
 };
 
-// The six separate products (kind of mode 1 for K > 32, where N = 64 leaves
-// no room to concatenate) or the single hh product (mode 2), each thread
-// taking part in the operand build and the read-out and thread 0 issuing.
-// NT threads: 128 (four warps, one per quarter of the TMEM lanes) where
-// several CTAs share an SM, or 256 where one CTA holds an SM: twice the warps
-// to build operands and read accumulators, the read-out split between two
-// warps per lane quarter by column halves.
-template <int N, int NT>
-__global__ void __launch_bounds__(NT, NT == 128 && N <= 32 ? 3 : 1)
-    dtx_tc_kernel(const float *__restrict__ D, const float *__restrict__ X, int K, int P, int L,
-                  long long T, int mode, float *__restrict__ beta0,
-                  float *__restrict__ r_out, unsigned int *__restrict__ absmax_bits,
-                  double *__restrict__ x2sum, int *__restrict__ err)
-{
-    extern __shared__ __align__(128) unsigned char sm[];
-    __shared__ uint32_t s_taddr;
-    __shared__ uint32_t s_aoff[kMaxSteps];  // A descriptor offset of each contraction step
-    const TcLayout lay(P, L, N);
-    unsigned char *As = sm + lay.a_off;
-    unsigned char *Bs = sm + lay.b_off;
-    uint32_t *pl = reinterpret_cast<uint32_t *>(sm + lay.pl_off);  // BF16 pairs
-    const uint32_t bar = smem_u32(sm + lay.bar_off);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const long long Tz = T - L + 1;
-    const long long ntiles = (Tz + kTcM - 1) / kTcM;
-
-    // ---- tensor memory (two accumulators of N columns) and two barriers ----
-    constexpr int acc_cols = N;
-    constexpr uint32_t tm_cols = 2u * N;
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         smem_u32(&s_taddr)),
-                     "r"(tm_cols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar + 8) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    for (int st = tid; st < lay.nsteps; st += NT) {
-        const int p = (16 * st) / lay.L16, q0 = ((16 * st) % lay.L16) / 8;
-        s_aoff[st] = (uint32_t)((p * lay.NQ + q0) * 128) >> 4;
-    }
-    // ---- B: the three BF16 terms of D, per contraction step -----------------
-    // element (sigma, s, n8, j8, r, e): D[k = 8 n8 + r][p][tau], j = 16 s + 8 j8 + e
-    const int rows_b = lay.nsteps * (N / 8) * 2 * 8;  // 16-byte rows per split
-    for (int i = tid; i < rows_b; i += NT) {
-        const int r = i & 7, j8 = (i >> 3) & 1, n8 = (i >> 4) % (N / 8), s = (i >> 4) / (N / 8);
-        const int k = 8 * n8 + r;
-        uint32_t w[kSplits][4];
-#pragma unroll
-        for (int e2 = 0; e2 < 4; e2++) {
-            __nv_bfloat16 h[2], m[2], l[2];
-#pragma unroll
-            for (int q = 0; q < 2; q++) {
-                const int j = 16 * s + 8 * j8 + 2 * e2 + q;
-                const int p = j / lay.L16, tau = j % lay.L16;
-                const float v = (k < K && tau < L) ? D[((long long)k * P + p) * L + tau] : 0.f;
-                split3(v, h[q], m[q], l[q]);
-            }
-            w[0][e2] = pack2(h[0], h[1]);
-            w[1][e2] = pack2(m[0], m[1]);
-            w[2][e2] = pack2(l[0], l[1]);
-        }
-#pragma unroll
-        for (int sg = 0; sg < kSplits; sg++) {
-            const size_t off =
-                ((((size_t)s * kSplits + sg) * (N / 8) + n8) * 2 + j8) * 128 + (size_t)r * 16;
-            *reinterpret_cast<uint4 *>(Bs + off) = make_uint4(w[sg][0], w[sg][1], w[sg][2], w[sg][3]);
-        }
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    fence_before_sync();
-    __syncthreads();
-    fence_after_sync();
-    const uint32_t taddr = s_taddr;
-    const uint32_t idesc = mma_idesc(kTcM, N);
-    const size_t a_bytes = (size_t)kSplits * P * lay.NQ * 128;  // one operand buffer
-    const uint32_t a_base = smem_u32(As), b_base = smem_u32(Bs);
-
-    float amax = 0.f;
-    double x2 = 0.0;
-    uint32_t phase0 = 0u, phase1 = 0u;  // expected parity of each barrier
-
-    // Stage X of a tile (sum X^2 over its own samples), split every sample
-    // once into its three BF16 terms (planes [split][p][xw], pairs of samples
-    // per 32-bit word), then build the tile's operand runs in buffer buf.
-    const int half = lay.xw / 2;  // words per plane row
-    // The samples of a tile are loaded into registers one iteration ahead
-    // (prefetch), so that their latency overlaps the previous tile's
-    // epilogue: a thread holds pairs i = tid + q * NT, q < kPairs.
-    constexpr int kPairs = 8;
-    const bool prefetched = P * half <= kPairs * NT;
-    float2 xr[kPairs];
-    auto load_x = [&](long long tile) {
-        const long long t0 = tile * kTcM;
-#pragma unroll
-        for (int q = 0; q < kPairs; q++) {
-            const int i = tid + q * NT;
-            float2 v = make_float2(0.f, 0.f);
-            if (i < P * half) {
-                const int p = i / half, j2 = i % half;
-                const long long t = t0 + 2 * j2;
-                const float *xp = X + (long long)p * T + t;
-                v.x = t < T ? xp[0] : 0.f;
-                v.y = t + 1 < T ? xp[1] : 0.f;
-            }
-            xr[q] = v;
-        }
-    };
-    auto put_pair = [&](int i, float v0, float v1, bool own) {
-        const int p = i / half, j2 = i % half;
-        if (own || 2 * j2 < kTcM)
-            x2 += (double)v0 * (double)v0 + (double)v1 * (double)v1;
-        __nv_bfloat16 h0, m0, l0, h1, m1, l1;
-        split3(v0, h0, m0, l0);
-        split3(v1, h1, m1, l1);
-        pl[(0 * P + p) * half + j2] = pack2(h0, h1);
-        pl[(1 * P + p) * half + j2] = pack2(m0, m1);
-        pl[(2 * P + p) * half + j2] = pack2(l0, l1);
-    };
-    auto build = [&](long long tile, int buf) {
-        const long long t0 = tile * kTcM;
-        const bool last = tile == ntiles - 1;
-        if (prefetched) {
-#pragma unroll
-            for (int q = 0; q < kPairs; q++) {
-                const int i = tid + q * NT;
-                if (i < P * half)
-                    put_pair(i, xr[q].x, xr[q].y, last);
-            }
-        } else {
-            for (int i = tid; i < P * half; i += NT) {
-                const int p = i / half, j2 = i % half;
-                const long long t = t0 + 2 * j2;
-                const float *xp = X + (long long)p * T + t;
-                put_pair(i, t < T ? xp[0] : 0.f, t + 1 < T ? xp[1] : 0.f, last);
-            }
-        }
-        __syncthreads();
-        // row (sigma, p, q, r) = split sigma of X[p][t0 + 8 q + r + 0..7]: the
-        // BF16 words 4 q + r/2 .. 4 q + r/2 + 4 of the plane, shifted by 16 bits
-        // when r is odd.  r = tid & 7 is the same for all of a thread's rows, and
-        // the 8 lanes of one q write 128 contiguous bytes (no bank conflict).
-        unsigned char *Ab = As + (size_t)buf * a_bytes;
-        const int rows_a = P * lay.NQ * 8;
-        const int r = tid & 7, wa = r >> 1;
-        const unsigned sh = (unsigned)(r & 1) * 16u;
-        // row group i >> 3 = p NQ + q, advanced by NT / 8 per row without a division
-        int q = (tid >> 3) % lay.NQ, p = (tid >> 3) / lay.NQ;
-        for (int i = tid; i < rows_a; i += NT) {
-            const size_t off = ((size_t)p * lay.NQ + q) * 128 + (size_t)r * 16;
-#pragma unroll
-            for (int sg = 0; sg < kSplits; sg++) {
-                const uint32_t *w = pl + (size_t)(sg * P + p) * half + 4 * q + wa;
-                const uint32_t w0 = w[0], w1 = w[1], w2 = w[2], w3 = w[3], w4 = w[4];
-                *reinterpret_cast<uint4 *>(Ab + (size_t)sg * P * lay.NQ * 128 + off) =
-                    make_uint4(__funnelshift_r(w0, w1, sh), __funnelshift_r(w1, w2, sh),
-                               __funnelshift_r(w2, w3, sh), __funnelshift_r(w3, w4, sh));
-            }
-            q += NT / 8;
-            while (q >= lay.NQ) {
-                q -= lay.NQ;
-                p++;
-            }
-        }
-        // make the generic-proxy stores visible to the tensor cores
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    };
-    // the products of the tile in buffer buf into accumulator buf (thread 0)
-    auto issue = [&](int buf) {
-        if (tid != 0)
-            return;
-        // products hh, hm, mh, hl, lh, mm (mode 2: hh only), small terms first.
-        // Descriptors differ only in their start address (16-byte units in the
-        // low 14 bits, smem addresses < 256 KB): base descriptors plus the
-        // per-step offsets tabulated at the start of the kernel.
-        const uint32_t d_acc = taddr + (uint32_t)(buf * acc_cols);
-        const uint64_t ad0 = mma_desc(a_base + (uint32_t)(buf * a_bytes), 128, 128);
-        const uint64_t bd0 = mma_desc(b_base, 128, 256);
-        const uint32_t a_split = (uint32_t)(P * lay.NQ * 128) >> 4;
-        const uint32_t b_split = (uint32_t)((N / 8) * 256) >> 4;
-        uint32_t acc = 0;
-        for (int s = 0; s < lay.nsteps; s++) {
-            const uint64_t a_s = ad0 + s_aoff[s];
-            const uint64_t b_s = bd0 + ((uint32_t)(s * kSplits * (N / 8) * 256) >> 4);
-            if (mode == 2) {
-                mma_bf16(d_acc, a_s, b_s, idesc, acc);
-            } else {
-                mma_bf16(d_acc, a_s + 1 * a_split, b_s + 1 * b_split, idesc, acc);  // mm
-                mma_bf16(d_acc, a_s + 2 * a_split, b_s, idesc, 1u);                 // lh
-                mma_bf16(d_acc, a_s, b_s + 2 * b_split, idesc, 1u);                 // hl
-                mma_bf16(d_acc, a_s + 1 * a_split, b_s, idesc, 1u);                 // mh
-                mma_bf16(d_acc, a_s, b_s + 1 * b_split, idesc, 1u);                 // hm
-                mma_bf16(d_acc, a_s, b_s, idesc, 1u);                               // hh
-            }
-            acc = 1;
-        }
-        mma_commit(bar + 8u * (uint32_t)buf);
-    };
-    // accumulator buf -> beta0 columns of the tile
-    auto epilogue = [&](long long tile, int buf) {
-        // warp w reads lane quarter w % 4 and, with NT = 256, column half w / 4
-        constexpr int CW = N / (NT / 128);  // columns per warp
-        const int quarter = warp & 3, c_lo = (warp >> 2) * CW;
-        const long long t = tile * kTcM + 32 * quarter + lane;
-        const uint32_t lane_addr =
-            taddr + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(buf * acc_cols);
-        auto put = [&](int k, float v) {
-            if (k < K) {
-                beta0[(long long)k * Tz + t] = v;
-                if (r_out)
-                    r_out[(long long)k * Tz + t] = v;
-                amax = fmaxf(amax, fabsf(v));
-            }
-        };
-        if constexpr (CW >= 32) {
-#pragma unroll
-            for (int c = c_lo; c < c_lo + CW; c += 32) {
-                float v[32];
-                tmem_ld32(lane_addr + (uint32_t)c, v);
-                if (t < Tz) {
-#pragma unroll
-                    for (int i = 0; i < 32; i++)
-                        put(c + i, v[i]);
-                }
-            }
-        } else {
-            float v[16];
-            tmem_ld16(lane_addr + (uint32_t)c_lo, v);
-            if (t < Tz) {
-#pragma unroll
-                for (int i = 0; i < 16; i++)
-                    put(c_lo + i, v[i]);
-            }
-        }
-    };
-
-    // Two-stage pipeline over this CTA's tiles: the operands of tile i are
-    // built, and the accumulator of tile i-1 read out, while the products of
-    // the neighbouring tile run on the tensor cores.
-    const long long cnt = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    if (prefetched && cnt > 0)
-        load_x(blockIdx.x);
-    for (long long i = 0; i <= cnt && cnt > 0; i++) {
-        if (i < cnt)
-            build(blockIdx.x + i * gridDim.x, (int)(i & 1));
-        // the next tile's samples are in flight while this iteration's
-        // products run and the previous tile's accumulator is read out
-        if (prefetched && i + 1 < cnt)
-            load_x(blockIdx.x + (i + 1) * gridDim.x);
-        // operands of tile i visible; every thread has read accumulator (i & 1)
-        // (tile i-2) before it is overwritten
-        fence_before_sync();
-        __syncthreads();
-        fence_after_sync();
-        if (i > 0) {
-            // bounded wait for the products of tile i-1; giving up is the
-            // block's decision, so every thread leaves the loop together
-            const uint32_t b = (uint32_t)((i - 1) & 1);
-            uint32_t &ph = b ? phase1 : phase0;
-            const bool got = mbar_wait_bounded(bar + 8u * b, ph, kWaitLimit);
-            if (__syncthreads_or(!got)) {
-                if (tid == 0)
-                    atomicExch(err, 1);
-                // those products still write accumulator b: let them finish
-                // (again bounded) before tensor memory is released
-                if (!got)
-                    mbar_wait_bounded(bar + 8u * b, ph, kWaitLimit);
-                break;
-            }
-            ph ^= 1u;
-            fence_after_sync();
-        }
-        if (i < cnt)
-            issue((int)(i & 1));
-        if (i > 0)
-            epilogue(blockIdx.x + (i - 1) * gridDim.x, (int)((i - 1) & 1));
-    }
-    for (int off = 16; off > 0; off >>= 1) {
-        amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
-        x2 += __shfl_xor_sync(0xffffffffu, x2, off);
-    }
-    if (lane == 0) {
-        atomicMax(absmax_bits, __float_as_uint(amax));
-        atomicAdd(x2sum, x2);
-    }
-    fence_before_sync();
-    __syncthreads();
-    fence_after_sync();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr),
-                     "r"(tm_cols)
-                     : "memory");
-}
-
 __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
@@ -536,11 +238,13 @@ __device__ __forceinline__ bool workers_any(bool v, int n)
     return r != 0;
 }
 
-// Warp-specialised form of the concatenated products (N = 32): NW worker
-// warps build the operands of tile i and read the accumulator of tile i-1
-// out while one more warp issues the products, so that the issue of a tile's
-// P * L16 / 16 * 3 products by one thread no longer holds up the operand
-// build and the read-out.  The two sides meet only at mbarriers:
+// NW worker warps build the operands of tile i and read the accumulator of
+// tile i-1 out while one more warp issues the products, so that the issue of
+// a tile's products by one thread does not hold up the operand build and the
+// read-out.  CAT (N = 32, mode 1): three concatenated products per step into
+// an accumulator of 3N columns; otherwise one accumulator of N columns with
+// the six products of mode 1 (N = 64, where 3N columns would not fit twice)
+// or the hh product alone (mode 2).  The two sides meet only at mbarriers:
 //   full[b]  the operands of the tile in buffer b are written (one arrival
 //            per worker thread, after its proxy fence),
 //   done[b]  the products into accumulator b have finished (tcgen05.commit),
@@ -549,19 +253,20 @@ __device__ __forceinline__ bool workers_any(bool v, int n)
 // u = i >> 1 of them completes phase u of the three barriers of b, which is
 // waited for with parity u & 1.  The workers share barrier 1 (plane buffer
 // reuse, and the block's decision to give up after a wait ran out).
-template <int NW>
+// (two CTAs per SM with four workers; the N = 64 form then keeps a few
+// values in local memory, and still runs faster than with one CTA per SM)
+template <int N, bool CAT, int NW>
 __global__ void __launch_bounds__(32 * NW + 32, NW <= 4 ? 2 : 1)
     dtx_tc_ws_kernel(const float *__restrict__ D, const float *__restrict__ X, int K, int P,
-                     int L, long long T, int /* mode: 1, the signature of dtx_tc_kernel */,
-                     float *__restrict__ beta0, float *__restrict__ r_out,
-                     unsigned int *__restrict__ absmax_bits, double *__restrict__ x2sum,
-                     int *__restrict__ err)
+                     int L, long long T, int mode, float *__restrict__ beta0,
+                     float *__restrict__ r_out, unsigned int *__restrict__ absmax_bits,
+                     double *__restrict__ x2sum, int *__restrict__ err)
 {
-    constexpr int N = 32;
-    constexpr int NTW = 32 * NW;        // worker threads
-    constexpr int NTA = NTW + 32;       // with the issuing warp
-    constexpr int acc_cols = 3 * N;     // hh+mh+lh | hm+mm | hl
-    constexpr uint32_t tm_cols = 256u;  // two accumulators, rounded up to a power of two
+    static_assert(!CAT || N == 32, "concatenated products need N = 32 (3N + 3N <= 256 columns)");
+    constexpr int NTW = 32 * NW;                   // worker threads
+    constexpr int NTA = NTW + 32;                  // with the issuing warp
+    constexpr int acc_cols = CAT ? 3 * N : N;      // CAT: hh+mh+lh | hm+mm | hl
+    constexpr uint32_t tm_cols = CAT ? 256u : 2u * N;  // two accumulators (a power of two)
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ uint32_t s_taddr;
     __shared__ uint32_t s_aoff[kMaxSteps];
@@ -597,7 +302,8 @@ __global__ void __launch_bounds__(32 * NW + 32, NW <= 4 ? 2 : 1)
         const int p = (16 * st) / lay.L16, q0 = ((16 * st) % lay.L16) / 8;
         s_aoff[st] = (uint32_t)((p * lay.NQ + q0) * 128) >> 4;
     }
-    // B: the three BF16 terms of D per contraction step, as in dtx_tc_kernel
+    // B: the three BF16 terms of D per contraction step.
+    // element (sigma, s, n8, j8, r, e): D[k = 8 n8 + r][p][tau], j = 16 s + 8 j8 + e
     const int rows_b = lay.nsteps * (N / 8) * 2 * 8;
     for (int i = tid; i < rows_b; i += NTA) {
         const int r = i & 7, j8 = (i >> 3) & 1, n8 = (i >> 4) % (N / 8), s = (i >> 4) / (N / 8);
@@ -670,7 +376,11 @@ __global__ void __launch_bounds__(32 * NW + 32, NW <= 4 ? 2 : 1)
             pl[(1 * P + p) * half + j2] = pack2(m0, m1);
             pl[(2 * P + p) * half + j2] = pack2(l0, l1);
         };
-        // operand runs of a tile into buffer buf (the row layout of dtx_tc_kernel)
+        // operand runs of a tile into buffer buf.  Row (sigma, p, q, r) = split
+        // sigma of X[p][t0 + 8 q + r + 0..7]: the BF16 words 4 q + r/2 .. 4 q +
+        // r/2 + 4 of the plane, shifted by 16 bits when r is odd.  r = tid & 7 is
+        // the same for all of a thread's rows, and the 8 lanes of one q write
+        // 128 contiguous bytes (no bank conflict).
         auto build = [&](long long tile, int buf) {
             const long long t0 = tile * kTcM;
             const bool last = tile == ntiles - 1;
@@ -735,19 +445,25 @@ __global__ void __launch_bounds__(32 * NW + 32, NW <= 4 ? 2 : 1)
                         amax = fmaxf(amax, fabsf(v));
                     }
                 };
-                // 16 columns at a time: hl + (hm + mm) + (hh + mh + lh), smallest first
+                // 16 columns at a time (CAT: hl + (hm + mm) + (hh + mh + lh),
+                // smallest first)
 #pragma unroll
                 for (int c = c_lo; c < c_lo + CW; c += 16) {
-                    float v[16], u[16];
-                    tmem_ld16(lane_addr + (uint32_t)(2 * N + c), v);
-                    tmem_ld16(lane_addr + (uint32_t)(N + c), u);
+                    float v[16];
+                    if constexpr (CAT) {
+                        float u[16];
+                        tmem_ld16(lane_addr + (uint32_t)(2 * N + c), v);
+                        tmem_ld16(lane_addr + (uint32_t)(N + c), u);
 #pragma unroll
-                    for (int i = 0; i < 16; i++)
-                        v[i] += u[i];
-                    tmem_ld16(lane_addr + (uint32_t)c, u);
+                        for (int i = 0; i < 16; i++)
+                            v[i] += u[i];
+                        tmem_ld16(lane_addr + (uint32_t)c, u);
 #pragma unroll
-                    for (int i = 0; i < 16; i++)
-                        v[i] += u[i];
+                        for (int i = 0; i < 16; i++)
+                            v[i] += u[i];
+                    } else {
+                        tmem_ld16(lane_addr + (uint32_t)c, v);
+                    }
                     if (t < Tz) {
 #pragma unroll
                         for (int i = 0; i < 16; i++)
@@ -802,6 +518,7 @@ __global__ void __launch_bounds__(32 * NW + 32, NW <= 4 ? 2 : 1)
         const uint32_t idesc = mma_idesc(kTcM, N);
         const uint32_t idesc_cat2 = mma_idesc(kTcM, 2 * N), idesc_cat3 = mma_idesc(kTcM, 3 * N);
         const uint32_t a_split = (uint32_t)(P * lay.NQ * 128) >> 4;
+        const uint32_t b_split = (uint32_t)((N / 8) * 256) >> 4;
         const uint64_t bd0 = mma_desc(b_base, 128, 256);
         long long issued = -1;
         for (long long i = 0; i < cnt; i++) {
@@ -820,10 +537,23 @@ __global__ void __launch_bounds__(32 * NW + 32, NW <= 4 ? 2 : 1)
                     for (int s = 0; s < lay.nsteps; s++) {
                         const uint64_t a_s = ad0 + s_aoff[s];
                         const uint64_t b_s = bd0 + ((uint32_t)(s * kSplits * (N / 8) * 256) >> 4);
-                        // hh|hm|hl (first: it covers all 3N columns), mh|mm, lh
-                        mma_bf16(d_acc, a_s, b_s, idesc_cat3, s > 0 ? 1u : 0u);
-                        mma_bf16(d_acc, a_s + 1 * a_split, b_s, idesc_cat2, 1u);
-                        mma_bf16(d_acc, a_s + 2 * a_split, b_s, idesc, 1u);
+                        const uint32_t acc = s > 0 ? 1u : 0u;
+                        if constexpr (CAT) {
+                            // hh|hm|hl (first: it covers all 3N columns), mh|mm, lh
+                            mma_bf16(d_acc, a_s, b_s, idesc_cat3, acc);
+                            mma_bf16(d_acc, a_s + 1 * a_split, b_s, idesc_cat2, 1u);
+                            mma_bf16(d_acc, a_s + 2 * a_split, b_s, idesc, 1u);
+                        } else if (mode == 2) {
+                            mma_bf16(d_acc, a_s, b_s, idesc, acc);  // hh
+                        } else {
+                            // mm, lh, hl, mh, hm, hh: small terms first
+                            mma_bf16(d_acc, a_s + 1 * a_split, b_s + 1 * b_split, idesc, acc);
+                            mma_bf16(d_acc, a_s + 2 * a_split, b_s, idesc, 1u);
+                            mma_bf16(d_acc, a_s, b_s + 2 * b_split, idesc, 1u);
+                            mma_bf16(d_acc, a_s + 1 * a_split, b_s, idesc, 1u);
+                            mma_bf16(d_acc, a_s, b_s + 1 * b_split, idesc, 1u);
+                            mma_bf16(d_acc, a_s, b_s, idesc, 1u);
+                        }
                     }
                     mma_commit(done0 + 8u * (uint32_t)b);
                 }
@@ -938,15 +668,17 @@ cudaError_t launch_dtx_tc(const float *D, const float *X, int K, int P, int L, i
     cudaFuncAttributes fa;
     cudaError_t e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     if (e == cudaSuccess)
-        e = cudaFuncGetAttributes(&fa, dtx_tc_ws_kernel<8>);
+        e = cudaFuncGetAttributes(&fa, dtx_tc_ws_kernel<32, true, 8>);
     if (e != cudaSuccess)
         return e;
     const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + 1024);
     if (K > 32)
-        return by_smem <= 1 ? go(dtx_tc_kernel<64, 256>, 1) : go(dtx_tc_kernel<64, 128>, 4);
+        return go(dtx_tc_ws_kernel<64, false, 4>, 2);
     if (mode == 1)
-        return by_smem <= 1 ? go(dtx_tc_ws_kernel<8>, 1) : go(dtx_tc_ws_kernel<4>, 2);
-    return by_smem <= 1 ? go(dtx_tc_kernel<32, 256>, 1) : go(dtx_tc_kernel<32, 128>, 4);
+        return by_smem <= 1 ? go(dtx_tc_ws_kernel<32, true, 8>, 1)
+                            : go(dtx_tc_ws_kernel<32, true, 4>, 2);
+    return by_smem <= 1 ? go(dtx_tc_ws_kernel<32, false, 8>, 1)
+                        : go(dtx_tc_ws_kernel<32, false, 4>, 2);
 }
 
 cudaError_t launch_dtx_any(const float *D, const float *X, int K, int P, int L, int64_t T,
