@@ -465,7 +465,7 @@ int csc_destroy(csc_handle_t h)
                     h->r,          h->beta0,      h->Z,          h->partials,   h->dirty,
                     h->tmpZ,       h->tmpB,       h->sc,         h->d_sig,      h->d_tile_s,
                     h->d_tile_off, h->d_tile_sig, h->d_rtile_s,  h->d_rtile_sig, h->d_rtile_off,
-                    h->d_E,
+                    h->d_sig_a,    h->d_E,
                     h->d_lmax,     h->d_seg_s,    h->d_seg_e,    h->d_seg_sig,  h->d_phase_list,
                     h->touched,    h->tile_rep,   h->d_queue,    h->d_sig_alt,
                     h->nz_count,   h->nz_ent,     h->shard.d_rt_sig, h->shard.d_ot_sig,
@@ -666,6 +666,7 @@ int csc_init_batch(csc_handle_t h, const float *X, const int64_t *T, int n, cons
     if (h->tiles_a != h->a || h->tiles_L != h->L) {
         CSC_CUDA(upload(&h->d_tile_off, &h->cap_tile_off, h->tile_off, s));
         CSC_CUDA(upload(&h->d_rtile_off, &h->cap_rtile_off, rtile_off, s));
+        CSC_CUDA(upload(&h->d_sig_a, &h->cap_sig_a, h->a, s));
         CSC_CUDA(grow(&h->d_tile_s, &h->cap_tile_s, (size_t)h->ntiles));
         CSC_CUDA(grow(&h->d_tile_sig, &h->cap_tile_sig, (size_t)h->ntiles));
         CSC_CUDA(grow(&h->d_rtile_s, &h->cap_rtile_s, (size_t)h->nrtiles));
@@ -705,27 +706,39 @@ int csc_init_batch(csc_handle_t h, const float *X, const int64_t *T, int n, cons
         CSC_CUDA(cudaEventCreateWithFlags(&h->ev_copy, cudaEventDisableTiming));
     CSC_CUDA(copy_in(h->X, X, sizeof(float) * h->P * Ttot, s));
     CSC_CUDA(cudaEventRecord(h->ev_copy, s));  // the caller's X has been read
-    CSC_CUDA(cudaMemsetAsync(&h->sc->lmax_bits, 0, sizeof(unsigned), s));
-    CSC_CUDA(cudaMemsetAsync(&h->sc->x2, 0, sizeof(double), s));
-    CSC_CUDA(cudaMemsetAsync(&h->sc->tc_err, 0, sizeof(int), s));
+    // x2, lmax_bits and tc_err (adjacent in Scratch) cleared in one memset
+    static_assert(offsetof(Scratch, lmax_bits) == offsetof(Scratch, x2) + sizeof(double) &&
+                      offsetof(Scratch, tc_err) == offsetof(Scratch, lmax_bits) + sizeof(unsigned),
+                  "x2, lmax_bits, tc_err adjacent");
+    CSC_CUDA(cudaMemsetAsync(&h->sc->x2, 0, offsetof(Scratch, tc_err) + sizeof(int) -
+                                              offsetof(Scratch, x2), s));
     const bool timed = h->opts.time_kernels != 0;
     if (timed && !h->ev_i0) {
         CSC_CUDA(cudaEventCreate(&h->ev_i0));
         CSC_CUDA(cudaEventCreate(&h->ev_i1));
     }
+    // a cold start (Z = 0) has r = beta0: the kernel writes both, and the
+    // tensor-core kernel also zeroes Z and, for a batch, takes the per-signal
+    // maxima (the kernel's overall maximum also covers the columns between
+    // signals, which belong to no problem)
+    Dtx0Extras ex;
+    if (!Z0)
+        ex.z_out = h->Z;
+    if (n > 1) {
+        CSC_CUDA(cudaMemsetAsync(h->d_lmax, 0, sizeof(unsigned) * n, s));
+        ex.a = h->d_sig_a;
+        ex.nsig = n;
+        ex.lmax = h->d_lmax;
+    }
     if (timed)
         CSC_CUDA(cudaEventRecord(h->ev_i0, s));
-    // a cold start (Z = 0) has r = beta0: the kernel writes both
     CSC_CUDA(launch_dtx_any(h->D, h->X, h->K, h->P, h->L, Ttot, h->opts.init_mode, h->beta0,
                             Z0 ? nullptr : h->r, &h->sc->lmax_bits, &h->sc->x2, &h->sc->tc_err,
-                            s));
+                            s, &ex));
     if (timed)
         CSC_CUDA(cudaEventRecord(h->ev_i1, s));
     h->launches += 1;
-    if (n > 1) {
-        // per-signal maxima (the kernel's maximum also covers the columns
-        // between signals, which belong to no problem)
-        CSC_CUDA(cudaMemsetAsync(h->d_lmax, 0, sizeof(unsigned) * n, s));
+    if (n > 1 && !ex.done) {
         CSC_CUDA(launch_signal_absmax(h->d_sig, h->obj_tiles(), h->K, h->d_lmax, s));
         h->launches += 1;
     }
@@ -740,7 +753,7 @@ int csc_init_batch(csc_handle_t h, const float *X, const int64_t *T, int n, cons
         CSC_CUDA(cudaMemsetAsync(h->sc->red, 0, sizeof(h->sc->red), s));
         CSC_CUDA(launch_resync(h->d_sig, h->resync_tiles(), h->Ct, h->norms, h->K, h->L, 1,
                                h->sc->red, 0, nullptr, 0.f, nullptr, nullptr, h->nz_lists(), s));
-    } else {
+    } else if (!ex.done) {
         CSC_CUDA(cudaMemsetAsync(h->Z, 0, sizeof(float) * nz, s));
     }
     // read back without waiting (finish_init completes it): the stream goes

@@ -293,16 +293,28 @@ inline bool dtx_tc_preferred(int K, int P, int L)
 {
     return K <= 64 && dtx_tc_smem(K, P, L) <= (size_t)kMaxSmem;
 }
+// What the tensor-core beta0 kernel can do besides beta0 and r, in the same
+// pass: z_out != NULL zeroes Z [K][Tz] (a cold start); lmax != NULL gathers the
+// maximum |beta0| of each of the nsig problems of a batch (float bits, zeroed
+// by the caller), problem i owning the columns [a[i], a[i+1] - L + 1).  done
+// is set when the kernel that ran did both (the FP32 kernel does neither).
+struct Dtx0Extras {
+    float *z_out = nullptr;
+    const int64_t *a = nullptr;  // [nsig + 1] first sample of each problem (device)
+    int nsig = 0;
+    unsigned int *lmax = nullptr;  // [nsig]
+    bool done = false;
+};
 // beta0 with init_mode 0 (automatic), 1 or 2 (tensor cores), 3 (FP32 kernel).
 cudaError_t launch_dtx_any(const float *D, const float *X, int K, int P, int L, int64_t T,
                            int init_mode, float *beta0, float *r_out, unsigned int *absmax_bits,
-                           double *x2sum, int *err, cudaStream_t s);
+                           double *x2sum, int *err, cudaStream_t s, Dtx0Extras *ex = nullptr);
 // One warp waits, bounded by `limit` polls, on an mbarrier nothing arrives
 // at, and sets *gave_up when the wait gives up.
 cudaError_t launch_wait_selftest(unsigned limit, int *gave_up, cudaStream_t s);
 cudaError_t launch_dtx_tc(const float *D, const float *X, int K, int P, int L, int64_t T,
                           int mode, float *beta0, float *r_out, unsigned int *absmax_bits,
-                          double *x2sum, int *err, cudaStream_t s);
+                          double *x2sum, int *err, cudaStream_t s, Dtx0Extras *ex = nullptr);
 
 // Nonzeros of Z per resync tile ("bucket": the tile's kResyncCols columns),
 // rebuilt at each resync where Z may have changed.  Bucket b holds

@@ -130,6 +130,8 @@ struct csc_handle_s {
     std::vector<int64_t> tile_off;  // [n+1] first objective tile of each signal
     int64_t ntiles = 0, nrtiles = 0;
     int64_t *d_tile_s = nullptr, *d_tile_off = nullptr, *d_rtile_s = nullptr, *d_rtile_off = nullptr;
+    int64_t *d_sig_a = nullptr;  // [n+1] first sample of each problem (a)
+    size_t cap_sig_a = 0;
     int *d_tile_sig = nullptr, *d_rtile_sig = nullptr;
     size_t cap_rtile_s = 0, cap_rtile_sig = 0, cap_rtile_off = 0;
     double *d_E = nullptr;

@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(32 * NW + 32, NW <= 4 ? 2 : 1)
     dtx_tc_ws_kernel(const float *__restrict__ D, const float *__restrict__ X, int K, int P,
                      int L, long long T, int mode, float *__restrict__ beta0,
                      float *__restrict__ r_out, unsigned int *__restrict__ absmax_bits,
-                     double *__restrict__ x2sum, int *__restrict__ err)
+                     double *__restrict__ x2sum, int *__restrict__ err, Dtx0Extras ex)
 {
     static_assert(!CAT || N == 32, "concatenated products need N = 32 (3N + 3N <= 256 columns)");
     constexpr int NTW = 32 * NW;                   // worker threads
@@ -437,12 +437,15 @@ __global__ void __launch_bounds__(32 * NW + 32, NW <= 4 ? 2 : 1)
                 const long long t = tile * kTcM + 32 * quarter + lane;
                 const uint32_t lane_addr =
                     taddr + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(buf * acc_cols);
+                float tmax = 0.f;  // this tile's largest |beta0| in the thread's column
                 auto put = [&](int k, float v) {
                     if (k < K) {
                         beta0[(long long)k * Tz + t] = v;
                         if (r_out)
                             r_out[(long long)k * Tz + t] = v;
-                        amax = fmaxf(amax, fabsf(v));
+                        if (ex.z_out)
+                            ex.z_out[(long long)k * Tz + t] = 0.f;
+                        tmax = fmaxf(tmax, fabsf(v));
                     }
                 };
                 // 16 columns at a time (CAT: hl + (hm + mm) + (hh + mh + lh),
@@ -468,6 +471,34 @@ __global__ void __launch_bounds__(32 * NW + 32, NW <= 4 ? 2 : 1)
 #pragma unroll
                         for (int i = 0; i < 16; i++)
                             put(c + i, v[i]);
+                    }
+                }
+                amax = fmaxf(amax, tmax);
+                if (ex.lmax) {
+                    // the problem of column t: the last i with a[i] <= t, if t
+                    // is one of its columns (the L - 1 after it belong to none)
+                    int sig = -1;
+                    if (t < Tz) {
+                        int lo = 0, hi = ex.nsig;  // a[lo] <= t < a[hi]
+                        while (hi - lo > 1) {
+                            const int mid = (lo + hi) >> 1;
+                            if (ex.a[mid] <= t)
+                                lo = mid;
+                            else
+                                hi = mid;
+                        }
+                        sig = t < ex.a[lo + 1] - L + 1 ? lo : -1;
+                    }
+                    // one atomic per warp where its 32 columns share a problem
+                    const int s0 = __shfl_sync(0xffffffffu, sig, 0);
+                    if (__all_sync(0xffffffffu, sig == s0)) {
+                        float m = tmax;
+                        for (int off = 16; off > 0; off >>= 1)
+                            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+                        if (lane == 0 && s0 >= 0)
+                            atomicMax(ex.lmax + s0, __float_as_uint(m));
+                    } else if (sig >= 0) {
+                        atomicMax(ex.lmax + sig, __float_as_uint(tmax));
                     }
                 }
             }
@@ -616,8 +647,9 @@ size_t dtx_tc_smem(int K, int P, int L)
 
 cudaError_t launch_dtx_tc(const float *D, const float *X, int K, int P, int L, int64_t T,
                           int mode, float *beta0, float *r_out, unsigned int *absmax_bits,
-                          double *x2sum, int *err, cudaStream_t s)
+                          double *x2sum, int *err, cudaStream_t s, Dtx0Extras *ex)
 {
+    const Dtx0Extras extras = ex ? *ex : Dtx0Extras{};
     if (K > 64)
         return cudaErrorNotSupported;
     const size_t smem = dtx_tc_smem(K, P, L);
@@ -658,8 +690,11 @@ cudaError_t launch_dtx_tc(const float *D, const float *X, int K, int P, int L, i
         const int64_t cap = (int64_t)nsm * per_sm;
         const unsigned grid = (unsigned)(ntiles < cap ? ntiles : cap);
         kern<<<grid, nt, smem, s>>>(D, X, K, P, L, (long long)T, mode, beta0, r_out, absmax_bits,
-                                   x2sum, err);
-        return cudaGetLastError();
+                                   x2sum, err, extras);
+        e = cudaGetLastError();
+        if (e == cudaSuccess && ex)
+            ex->done = true;
+        return e;
     };
     // mode 1 at N = 32: concatenated products with a warp of their own, one
     // CTA per SM with eight worker warps or two with four (their accumulators
@@ -683,14 +718,14 @@ cudaError_t launch_dtx_tc(const float *D, const float *X, int K, int P, int L, i
 
 cudaError_t launch_dtx_any(const float *D, const float *X, int K, int P, int L, int64_t T,
                            int init_mode, float *beta0, float *r_out, unsigned int *absmax_bits,
-                           double *x2sum, int *err, cudaStream_t s)
+                           double *x2sum, int *err, cudaStream_t s, Dtx0Extras *ex)
 {
     int mode = init_mode;
     if (mode == 0)
         mode = dtx_tc_preferred(K, P, L) ? 1 : 3;
     if (mode == 1 || mode == 2) {
         const cudaError_t e =
-            launch_dtx_tc(D, X, K, P, L, T, mode, beta0, r_out, absmax_bits, x2sum, err, s);
+            launch_dtx_tc(D, X, K, P, L, T, mode, beta0, r_out, absmax_bits, x2sum, err, s, ex);
         if (e != cudaErrorNotSupported)
             return e;
         cudaGetLastError();
