@@ -342,6 +342,7 @@ __global__ void __launch_bounds__(32 * NW + 32, NW <= 4 ? 2 : 1)
     if (warp < NW) {
         // ---------------- workers: operand build and read-out ----------------
         float amax = 0.f;
+        int sig_c = -1;  // the batch problem of this thread's column in its last tile
         float x2h = 0.f, x2l = 0.f;  // sum of X^2 over the CTA's own samples (double-float)
         const int half = lay.xw / 2;
         constexpr int kPairs = 4;  // P = 7 at L = 64, or P = 1 at L = 200, fit
@@ -476,18 +477,25 @@ __global__ void __launch_bounds__(32 * NW + 32, NW <= 4 ? 2 : 1)
                 amax = fmaxf(amax, tmax);
                 if (ex.lmax) {
                     // the problem of column t: the last i with a[i] <= t, if t
-                    // is one of its columns (the L - 1 after it belong to none)
+                    // is one of its columns (the L - 1 after it belong to none);
+                    // a thread's columns only grow from tile to tile, so the
+                    // search starts from the problem of its previous tile
                     int sig = -1;
                     if (t < Tz) {
-                        int lo = 0, hi = ex.nsig;  // a[lo] <= t < a[hi]
-                        while (hi - lo > 1) {
-                            const int mid = (lo + hi) >> 1;
-                            if (ex.a[mid] <= t)
-                                lo = mid;
-                            else
-                                hi = mid;
+                        if (sig_c < 0) {
+                            int lo = 0, hi = ex.nsig;  // a[lo] <= t < a[hi]
+                            while (hi - lo > 1) {
+                                const int mid = (lo + hi) >> 1;
+                                if (ex.a[mid] <= t)
+                                    lo = mid;
+                                else
+                                    hi = mid;
+                            }
+                            sig_c = lo;
                         }
-                        sig = t < ex.a[lo + 1] - L + 1 ? lo : -1;
+                        while (sig_c + 1 < ex.nsig && ex.a[sig_c + 1] <= t)
+                            sig_c++;
+                        sig = t < ex.a[sig_c + 1] - L + 1 ? sig_c : -1;
                     }
                     // one atomic per warp where its 32 columns share a problem
                     const int s0 = __shfl_sync(0xffffffffu, sig, 0);
