@@ -436,8 +436,9 @@ def verylong_leg(args, capi, torch):
                   "updates_per_s": tuned["updates"] / (tuned["step_ms"] * 1e-3)})
     capi.csc_destroy(h)
     peak, kind = peaks()
-    # beta0 kernel: X read once, beta0 and the cold-start r written
-    b0_bytes = 4.0 * pb.P * pb.T + 2 * 4.0 * pb.K * pb.Tz
+    # beta0 kernel: X read once; beta0, the cold-start r and the cold-start
+    # Z = 0 written
+    b0_bytes = 4.0 * pb.P * pb.T + 3 * 4.0 * pb.K * pb.Tz
     b0_gbs = b0_bytes / (best["beta0_kernel_ms"] * 1e-3) / 1e9 if best["beta0_kernel_ms"] > 0 else None
     return {"workload": VERYLONG, "P": pb.P, "K": pb.K, "L": pb.L, "T": pb.T, "tol": args.tol,
             "lambda": "0.1*lambda_max", "runs": nruns, **best, "autotuned": tuned,
