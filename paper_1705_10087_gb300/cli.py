@@ -3,10 +3,12 @@
     python -m paper_1705_10087_gb300.cli --workload long_P7_K25_L64_T200000 \
         --segments 1024 --updates-per-visit 24 [--seed 0] [--tol 1e-6] [--repeat 1] \
         [--init-mode 0]
+    python -m paper_1705_10087_gb300.cli --workload image_P1_K8_h8_w8_512x512
 
 Prints one JSON line per solve with the solver statistics.  Inputs come from
-paper_1705_10087_gb300.synth; lambda = 0.1 * lambda_max as computed by the
-library (csc_lambda_max).
+paper_1705_10087_gb300.synth; lambda = 0.1 * lambda_max, for signals as
+computed by the library (csc_lambda_max), for images from the cross-correlation
+D~ * X taken by torch on the GPU (input preparation, outside the solver).
 """
 from __future__ import annotations
 
@@ -17,7 +19,8 @@ import json
 def main(argv=None) -> None:
     from . import synth
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="long_P7_K25_L64_T200000", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--workload", default="long_P7_K25_L64_T200000",
+                    choices=sorted(synth.WORKLOADS) + sorted(synth.IMAGE_WORKLOADS))
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--T", type=int, default=None, help="override the signal length")
     ap.add_argument("--segments", type=int, default=0)
@@ -32,6 +35,8 @@ def main(argv=None) -> None:
     from . import build, capi
     build.build()
     capi.load()
+    if a.workload in synth.IMAGE_WORKLOADS:
+        return image(a, synth, capi, torch)
     pb = synth.make_workload(a.workload, seed=a.seed, T=a.T)
     tol = a.tol if a.tol is not None else synth.WORKLOADS[a.workload]["tol"]
     D = torch.from_numpy(pb.D).cuda()
@@ -51,6 +56,24 @@ def main(argv=None) -> None:
                               "status": status, "objective": E, **st}))
     finally:
         capi.csc_destroy(h)
+
+
+def image(a, synth, capi, torch) -> None:
+    """csc2d_solve on a synthetic image workload, automatic tiles."""
+    w = synth.IMAGE_WORKLOADS[a.workload]
+    pb = synth.make_image_workload(a.workload, seed=a.seed)
+    tol = a.tol if a.tol is not None else w["tol"]
+    D = torch.from_numpy(pb.D).cuda()
+    X = torch.from_numpy(pb.X).cuda()
+    # lambda_max = max |D~ * X| (Sec. 4); conv2d is the cross-correlation
+    lam = 0.1 * float(torch.nn.functional.conv2d(X[None].double(), D.double()).abs().max())
+    Z = torch.zeros((w["K"], w["H"] - w["h"] + 1, w["W"] - w["w"] + 1), dtype=torch.float32,
+                    device="cuda")
+    for _ in range(a.repeat):
+        status, E, st = capi.csc2d_solve(D, X, lam, tol, updates_per_visit=a.updates_per_visit,
+                                         Z_out=Z)
+        print(json.dumps({"workload": a.workload, "seed": a.seed, "lambda": lam,
+                          "status": status, "objective": E, **st}))
 
 
 if __name__ == "__main__":

@@ -23,10 +23,12 @@
 // 8 x 8 atoms has 18 co-active bands but 324 co-active tiles of 14 x 14).
 // One thread block per active tile: it keeps, per position (i, j) of its
 // tile, the best coordinate over k as a 64-bit key (|Delta Z| bits, ~flat
-// index; ties to the lowest (k Hz + i) Wz + j) in shared memory, with r and Z
-// of the tile staged there too when they fit, and repeats block argmax ->
-// update -> re-evaluation of the window's positions, writing the window
-// positions outside its tile (idle neighbours) with atomicAdd.
+// index and the sign of Delta Z; ties to the lowest (k Hz + i) Wz + j) in
+// shared memory, with r and Z of the tile staged there too when they fit, and
+// repeats block argmax (a shared atomicMax per warp, one barrier) -> update
+// -> re-evaluation of the window's positions, writing the window positions
+// outside its tile (idle neighbours) with atomicAdd and each new Z value to
+// global memory when it is applied.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -174,20 +176,16 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
 }
 
 // Shared-memory layout of a tile block (bytes, 16-aligned pieces): per
-// position its cached key, candidate Z', change and atom; with STAGE also r
+// position its cached key and candidate Z'; with STAGE also r
 // and Z of the tile, position-major with an odd row of ks = K | 1 floats.
 struct TileLayout {
-    size_t key, cz, cd, ck, r, z, total;
+    size_t key, cz, r, z, total;
     __host__ __device__ TileLayout(int K, int npos, bool stage)
     {
         size_t o = 0;
         key = o;
         o = up(o + 8 * (size_t)npos);
         cz = o;
-        o = up(o + 4 * (size_t)npos);
-        cd = o;
-        o = up(o + 4 * (size_t)npos);
-        ck = o;
         o = up(o + 4 * (size_t)npos);
         r = o;
         if (stage)
@@ -208,13 +206,16 @@ struct TileLayout {
 // its key re-evaluated, by its owner (no barrier between an update and the
 // next argmax).  Positions of the window outside the tile belong to idle
 // neighbours of this phase: their r is changed with atomicAdd.
+// (three blocks per SM: the 324 co-active tiles of a 512 x 512 image with
+// 8 x 8 atoms are resident at once, without spills)
 template <bool STAGE>
-__global__ void __launch_bounds__(kB2) tile_kernel(TileParams tp)
+__global__ void __launch_bounds__(kB2, 3) tile_kernel(TileParams tp)
 {
     extern __shared__ __align__(16) unsigned char sm[];
-    __shared__ unsigned long long s_key[2][kB2 / 32];
-    __shared__ float s_z[2][kB2 / 32], s_d[2][kB2 / 32];
-    __shared__ int s_k[2][kB2 / 32], s_pos[2][kB2 / 32];
+    // the block's best key of update i is reduced into s_best[i & 3] (a 64-bit
+    // shared atomicMax per warp); slot (i + 2) & 3, last read in update i - 2,
+    // is cleared during update i
+    __shared__ unsigned long long s_best[4];
     __shared__ float s_nrm[kMaxK2], s_rn[kMaxK2];
     __shared__ double s_dec[kB2 / 32];
     const int tile = tp.list[blockIdx.x];
@@ -233,8 +234,6 @@ __global__ void __launch_bounds__(kB2) tile_kernel(TileParams tp)
     const TileLayout lay(K, tp.max_pos, STAGE);
     unsigned long long *key = reinterpret_cast<unsigned long long *>(sm + lay.key);
     float *cz = reinterpret_cast<float *>(sm + lay.cz);
-    float *cd = reinterpret_cast<float *>(sm + lay.cd);
-    int *ck = reinterpret_cast<int *>(sm + lay.ck);
     float *rs = reinterpret_cast<float *>(sm + lay.r);
     float *zs = reinterpret_cast<float *>(sm + lay.z);
     const float lam = tp.lam;
@@ -242,6 +241,8 @@ __global__ void __launch_bounds__(kB2) tile_kernel(TileParams tp)
         s_nrm[k] = tp.norms[k];
         s_rn[k] = __frcp_rn(tp.norms[k]);
     }
+    if (tid < 4)
+        s_best[tid] = 0ull;
     // element k of tile position p = (i - i_lo) tw + (j - j_lo)
     auto rref = [&](int p, int64_t i, int64_t j, int k) -> float & {
         return STAGE ? rs[p * ks + k] : tp.r[k * HWz + i * Wz + j];
@@ -258,8 +259,10 @@ __global__ void __launch_bounds__(kB2) tile_kernel(TileParams tp)
             }
         }
     __syncthreads();
-    // best coordinate over k of position p, cached as a key (|dZ| bits, ~flat)
-    // with ties to the lowest (k, i, j), i.e. the lowest (k Hz + i) Wz + j
+    // best coordinate over k of position p, cached as a key (|dZ| bits,
+    // ~(flat << 1 | sign of dZ)), flat = k npos + p: ties go to the lowest
+    // (k, i, j), i.e. the lowest (k Hz + i) Wz + j, and the key alone gives dZ
+    // exactly (flat < 2^31: K npos < 2^31)
     auto eval = [&](int p, int64_t i, int64_t j) {
         float best = -1.f, bz = 0.f, bd = 0.f;
         int bk = 0;
@@ -276,12 +279,10 @@ __global__ void __launch_bounds__(kB2) tile_kernel(TileParams tp)
                 bd = dd;
             }
         }
-        const unsigned flat = (unsigned)bk * (unsigned)npos + (unsigned)p;
+        const unsigned flat = (((unsigned)bk * (unsigned)npos + (unsigned)p) << 1) | (bd < 0.f ? 1u : 0u);
         key[p] = best > 0.f ? ((unsigned long long)__float_as_uint(best) << 32) | (unsigned)(~flat)
                             : 0ull;
         cz[p] = bz;
-        cd[p] = bd;
-        ck[p] = bk;
     };
     // this thread's positions: slots q, q + kB2, ... < A; for slot (a, b) the
     // rows i == a (mod H2) and columns j == b (mod W2) of the tile
@@ -300,39 +301,22 @@ __global__ void __launch_bounds__(kB2) tile_kernel(TileParams tp)
     bool capped = false;
     const float4 *Ct4 = reinterpret_cast<const float4 *>(tp.Ct);
     for (int it = 0;; it++) {
-        const int buf = it & 1;
         unsigned long long my = 0ull;
-        int mp = 0;
         for (int q = tid; q < A; q += kB2) {
             const int a = q / W2, b = q % W2;
             for (int64_t i = first(i_lo, a, H2); i < i_hi; i += H2)
                 for (int64_t j = first(j_lo, b, W2); j < j_hi; j += W2) {
-                    const int p = (int)(i - i_lo) * tw + (int)(j - j_lo);
-                    if (key[p] > my) {
-                        my = key[p];
-                        mp = p;
-                    }
+                    const unsigned long long kk = key[(int)(i - i_lo) * tw + (int)(j - j_lo)];
+                    my = kk > my ? kk : my;
                 }
         }
-        const float my_z = cz[mp], my_d = cd[mp];
-        const int my_k = ck[mp];
         const unsigned long long wm = warp_max_u64(my);
-        const unsigned win = __ballot_sync(0xffffffffu, my == wm);
-        if (lane == __ffs(win) - 1) {
-            s_key[buf][warp] = wm;
-            s_z[buf][warp] = my_z;
-            s_d[buf][warp] = my_d;
-            s_k[buf][warp] = my_k;
-            s_pos[buf][warp] = mp;
-        }
+        if (lane == 0 && wm != 0ull)
+            atomicMax(&s_best[it & 3], wm);
+        if (tid == 0)
+            s_best[(it + 2) & 3] = 0ull;
         __syncthreads();
-        unsigned long long bk = 0ull;
-        int bw = 0;
-        for (int q = 0; q < kB2 / 32; q++)
-            if (s_key[buf][q] > bk) {
-                bk = s_key[buf][q];
-                bw = q;
-            }
+        const unsigned long long bk = s_best[it & 3];
         const float adz = __uint_as_float((unsigned)(bk >> 32));
         if (!(adz >= tp.tol))
             break;
@@ -340,8 +324,12 @@ __global__ void __launch_bounds__(kB2) tile_kernel(TileParams tp)
             capped = true;
             break;
         }
-        const float znew = s_z[buf][bw], delta = s_d[buf][bw];
-        const int k0 = s_k[buf][bw], p0 = s_pos[buf][bw];
+        // the winner and dZ = +-|dZ| from its key.  Only the position's owner
+        // reads Z' from the position cache: the owner rewrites that cache later
+        // in this update, and another thread's read would race it
+        const unsigned flat = ~(unsigned)bk;
+        const float delta = (flat & 1u) ? -adz : adz;
+        const int k0 = (int)((flat >> 1) / (unsigned)npos), p0 = (int)((flat >> 1) % (unsigned)npos);
         const int64_t i0 = i_lo + p0 / tw, j0 = j_lo + p0 % tw;
         const int64_t ib = i0 - (d.h - 1), jb = j0 - (d.w - 1);
         // Eq. beta_up (r form) on the window: slot q holds the window
@@ -357,10 +345,12 @@ __global__ void __launch_bounds__(kB2) tile_kernel(TileParams tp)
             if (own && i == i0 && j == j0) {
                 // Prop. A.1 from the owner's r before this update touches it:
                 // dZ (r - n dZ / 2) + lam (|z| - |u|)
-                const float nk = s_nrm[k0], z = znew - delta;
+                const float znew = cz[p], nk = s_nrm[k0], z = znew - delta;
                 const float r0 = rref(p, i, j, k0);
                 decrease += delta * (r0 - 0.5f * nk * delta) + lam * (fabsf(z) - fabsf(znew));
                 zref(p, i, j, k0) = znew;
+                if (STAGE)
+                    tp.Z[k0 * HWz + i * Wz + j] = znew;  // (the write-back copies r only)
             }
             for (int g = 0; g < tp.KQ; g++) {
                 const float4 c = __ldg(Ct4 + ((int64_t)k0 * tp.KQ + g) * A + lag);
@@ -391,10 +381,8 @@ __global__ void __launch_bounds__(kB2) tile_kernel(TileParams tp)
         __syncthreads();  // every owner's last update is in shared memory
         for (int p = tid; p < npos; p += kB2) {
             const int64_t i = i_lo + p / tw, j = j_lo + p % tw;
-            for (int k = 0; k < K; k++) {
+            for (int k = 0; k < K; k++)
                 tp.r[k * HWz + i * Wz + j] = rs[p * ks + k];
-                tp.Z[k * HWz + i * Wz + j] = zs[p * ks + k];
-            }
         }
     }
     for (int off = 16; off > 0; off >>= 1)

@@ -17,10 +17,11 @@
 //   2. keeps, per owned column t, the best coordinate over k of
 //      |Delta Z_k[t]| = |Sh(beta_k[t], lambda)/||D_k||^2 - Z_k[t]| (Eq. pb_coord,
 //      evaluated from r by coord_step) as a 64-bit key
-//      (|Delta Z| bits << 32 | ~(k << 16 | t - s)): the max key is the largest
-//      |Delta Z| with ties to the lowest (k, t), i.e. the lowest k*Tz + t,
+//      (|Delta Z| bits << 32 | ~(k << 17 | (t - s) << 1 | sign of Delta Z)):
+//      the max key is the largest |Delta Z| with ties to the lowest (k, t),
+//      i.e. the lowest k*Tz + t,
 //   3. repeats: block argmax (warp max, a shared atomicMax per warp, one
-//      barrier; the key names the winner), stop if the best
+//      barrier; the key names the winner and its Delta Z), stop if the best
 //      |Delta Z| < tol (Alg. 1 stopping rule) or after u updates, else
 //      Z_k0[t0] <- Z' and r_k[t] -= S_{k,k0}[t-t0] (Z' - Z_old) for every k
 //      and t in [t0-L+1, t0+L-1] (Eq. beta_up, sign fixed by the beta
@@ -82,9 +83,9 @@ struct Layout {
         o = up(o + 8 * (size_t)w);
         cz = o;
         o = up(o + 4 * (size_t)w);
-        cd = o;
+        cd = o;  // dZ and the best atom of a column (the one-warp form's winner read)
         o = up(o + 4 * (size_t)w);
-        ck = o;  // the best atom of a column (the one-warp form's winner read)
+        ck = o;
         o = up(o + 4 * (size_t)w);
         zm = o;  // per column: bit k set when Z_k[t] != 0 (compile-time K <= 64)
         o = up(o + 8 * (size_t)w);
@@ -172,8 +173,7 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
     constexpr int KQ = (KT + 3) / 4;      // float4 groups holding the KT atoms
     const Layout lay(K, pp.w_max, SMEM, KFIX);
     unsigned long long *ckey = reinterpret_cast<unsigned long long *>(smem_raw + lay.key);
-    float *cz = reinterpret_cast<float *>(smem_raw + lay.cz);
-    float *cd = reinterpret_cast<float *>(smem_raw + lay.cd);
+    float *cz = reinterpret_cast<float *>(smem_raw + lay.cz);  // Z' of a column's key
     // one bit per atom of a column: 32 or 64 bits
     using Mask = typename std::conditional<(KT > 32), unsigned long long, unsigned>::type;
     static_assert(KT <= 64, "the masks of a column hold 64 atoms");
@@ -254,13 +254,13 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
                 bdz = d2;
             }
         }
-        // segment-local index k << 16 | jj: same order as k * Tz + t inside the
-        // segment (jj < w_max < 2^16: the column caches live in shared memory)
-        const unsigned flat = ((unsigned)bk << 16) | (unsigned)jj;
+        // segment-local index k << 17 | jj << 1: same order as k * Tz + t inside
+        // the segment (jj < w_max < 2^16: the column caches live in shared
+        // memory); bit 0 is the sign of dZ, so the key alone gives dZ exactly
+        const unsigned flat = ((unsigned)bk << 17) | ((unsigned)jj << 1) | (bdz < 0.f ? 1u : 0u);
         ckey[jj] = best > 0.f ? ((unsigned long long)__float_as_uint(best) << 32) | (unsigned)(~flat)
                               : 0ull;
         cz[jj] = bz;
-        cd[jj] = bdz;
     };
 
     // best coordinate of own column jj over k
@@ -299,11 +299,10 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
             for (int k = 0; k < K; k++)
                 visit(k);
         }
-        const unsigned flat = ((unsigned)bk << 16) | (unsigned)jj;
+        const unsigned flat = ((unsigned)bk << 17) | ((unsigned)jj << 1) | (bdz < 0.f ? 1u : 0u);
         ckey[jj] = best > 0.f ? ((unsigned long long)__float_as_uint(best) << 32) | (unsigned)(~flat)
                               : 0ull;
         cz[jj] = bz;
-        cd[jj] = bdz;
     };
     if constexpr (SMEM && KFIX) {
         // a column's KT values of r and of Z in one round trip of independent
@@ -366,10 +365,13 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
             capped = true;
             break;
         }
-        // the winner (k0, column) from its key; its step from the column caches
+        // the winner (k0, column) and dZ = +-|dZ| from its key.  Only the
+        // column's owner reads Z' from the column cache: the owner rewrites that
+        // cache later in this update, and another thread's read would race it
         const unsigned flat = ~(unsigned)bk;
-        const int k0 = (int)(flat >> 16), jw = (int)(flat & 0xffffu);
-        const float znew = cz[jw], delta = cd[jw];
+        const int k0 = (int)(flat >> 17), jw = (int)((flat >> 1) & 0xffffu);
+        const float delta = (flat & 1u) ? -adz : adz;
+        float znew = 0.f;
         const int64_t t0 = s + jw;
 
         // ---- Eq. beta_up (r form) on the window -------------------------
@@ -380,6 +382,7 @@ __device__ __forceinline__ void visit_segment(const PhaseParams &pp, const int m
             const bool own = t >= s && t < e;
             const int jj = (int)(t - s);
             if (t == t0) {
+                znew = cz[jw];
                 // Prop. A.1 from the owner's r before this update touches it:
                 // E(Z) - E(Z') = dZ (r - n dZ / 2) + lam (|z| - |u|), dZ = u - z
                 const float n = nrm[k0], d = delta, u = znew, z = znew - delta;
