@@ -56,8 +56,8 @@ namespace {
 constexpr int kB2 = 256;        // threads of a tile block
 // updates per tile visit by default: a launch lasts as long as its busiest
 // tile, so short visits keep the 324 co-active tiles of a 512 x 512 image
-// (8 x 8 atoms) in step (measured: 6.2 ms at 8, 6.6 at 16, 8.1 at 32, 23 ms
-// when every visit runs to local convergence)
+// (8 x 8 atoms) in step (measured on an earlier build: 6.2 ms at 8, 6.6 at
+// 16, 8.1 at 32, 23 ms when every visit runs to local convergence)
 constexpr int kAutoVisit2d = 8;
 constexpr int kMaxK2 = 64;      // atoms (one bit each in a 64-bit mask)
 constexpr int kMaxWin = 4096;   // (2h-1)(2w-1) window positions
@@ -226,8 +226,8 @@ __global__ void __launch_bounds__(kB2, 3) tile_kernel(TileParams tp)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t i_lo = tp.row_s[m], i_hi = tp.row_s[m + 1];
     const int64_t j_lo = tp.col_s[n], j_hi = tp.col_s[n + 1];
-    const int tw = (int)(j_hi - j_lo);
-    const int npos = (int)(i_hi - i_lo) * tw;
+    const int th = (int)(i_hi - i_lo), tw = (int)(j_hi - j_lo);
+    const int npos = th * tw;
     const int64_t Wz = d.Wz, HWz = d.Hz * d.Wz;
     const int K = d.K, ks = K | 1;
     const int H2 = 2 * d.h - 1, W2 = 2 * d.w - 1, A = H2 * W2;
@@ -259,10 +259,13 @@ __global__ void __launch_bounds__(kB2, 3) tile_kernel(TileParams tp)
             }
         }
     __syncthreads();
-    // best coordinate over k of position p, cached as a key (|dZ| bits,
-    // ~(flat << 1 | sign of dZ)), flat = k npos + p: ties go to the lowest
-    // (k, i, j), i.e. the lowest (k Hz + i) Wz + j, and the key alone gives dZ
-    // exactly (flat < 2^31: K npos < 2^31)
+    // best coordinate over k of position p = (ii, jj) = (i - i_lo, j - j_lo),
+    // cached as a key (|dZ| bits, ~(idx << 1 | sign of dZ)) with the bit fields
+    // idx = k << (ib + jb) | ii << jb | jj (ib, jb: bits of th - 1 and tw - 1;
+    // 6 + ib + jb < 32, checked by the host): ties go to the lowest (k, i, j),
+    // i.e. the lowest (k Hz + i) Wz + j, and the key alone gives dZ exactly
+    const int jbits = tw > 1 ? 32 - __clz(tw - 1) : 0;
+    const int kshift = (th > 1 ? 32 - __clz(th - 1) : 0) + jbits;
     auto eval = [&](int p, int64_t i, int64_t j) {
         float best = -1.f, bz = 0.f, bd = 0.f;
         int bk = 0;
@@ -279,22 +282,38 @@ __global__ void __launch_bounds__(kB2, 3) tile_kernel(TileParams tp)
                 bd = dd;
             }
         }
-        const unsigned flat = (((unsigned)bk * (unsigned)npos + (unsigned)p) << 1) | (bd < 0.f ? 1u : 0u);
+        const unsigned idx = ((unsigned)bk << kshift) | ((unsigned)(i - i_lo) << jbits) | (unsigned)(j - j_lo);
+        const unsigned flat = (idx << 1) | (bd < 0.f ? 1u : 0u);
         key[p] = best > 0.f ? ((unsigned long long)__float_as_uint(best) << 32) | (unsigned)(~flat)
                             : 0ull;
         cz[p] = bz;
     };
-    // this thread's positions: slots q, q + kB2, ... < A; for slot (a, b) the
-    // rows i == a (mod H2) and columns j == b (mod W2) of the tile
-    auto first = [](int64_t lo, int res, int period) -> int64_t {
-        return lo + (((res - lo) % period) + period) % period;
+    // this thread's window slots q = tid, tid + kB2, ... < A as (a, b) =
+    // (q / W2, q % W2), stepped without dividing
+    const int a_step = kB2 / W2, b_step = kB2 - a_step * W2;
+    auto for_slots = [&](auto &&f) {
+        int a = tid / W2, b = tid - (tid / W2) * W2;
+        for (int q = tid; q < A; q += kB2) {
+            f(a, b);
+            a += a_step;
+            b += b_step;
+            if (b >= W2) {
+                b -= W2;
+                a++;
+            }
+        }
     };
-    for (int q = tid; q < A; q += kB2) {
-        const int a = q / W2, b = q % W2;
-        for (int64_t i = first(i_lo, a, H2); i < i_hi; i += H2)
-            for (int64_t j = first(j_lo, b, W2); j < j_hi; j += W2)
-                eval((int)(i - i_lo) * tw + (int)(j - j_lo), i, j);
-    }
+    // x mod m for x in [-m, 2m)
+    auto wrap = [](int x, int m) { return x < 0 ? x + m : (x >= m ? x - m : x); };
+    const int il = (int)(i_lo % H2), jl = (int)(j_lo % W2);
+    // slot (a, b) holds the tile's rows i == a (mod H2) and columns j == b
+    // (mod W2): ii from (a - i_lo) mod H2 in steps of H2, jj likewise
+    auto for_positions = [&](int a, int b, auto &&f) {
+        for (int ii = wrap(a - il, H2); ii < th; ii += H2)
+            for (int jj = wrap(b - jl, W2); jj < tw; jj += W2)
+                f(ii * tw + jj, i_lo + ii, j_lo + jj);
+    };
+    for_slots([&](int a, int b) { for_positions(a, b, eval); });
     int nupd = 0;
     int64_t imin = i_hi, imax = i_lo - 1, jmin = j_hi, jmax = j_lo - 1;
     float decrease = 0.f;
@@ -302,14 +321,12 @@ __global__ void __launch_bounds__(kB2, 3) tile_kernel(TileParams tp)
     const float4 *Ct4 = reinterpret_cast<const float4 *>(tp.Ct);
     for (int it = 0;; it++) {
         unsigned long long my = 0ull;
-        for (int q = tid; q < A; q += kB2) {
-            const int a = q / W2, b = q % W2;
-            for (int64_t i = first(i_lo, a, H2); i < i_hi; i += H2)
-                for (int64_t j = first(j_lo, b, W2); j < j_hi; j += W2) {
-                    const unsigned long long kk = key[(int)(i - i_lo) * tw + (int)(j - j_lo)];
-                    my = kk > my ? kk : my;
-                }
-        }
+        for_slots([&](int a, int b) {
+            for_positions(a, b, [&](int p, int64_t, int64_t) {
+                const unsigned long long kk = key[p];
+                my = kk > my ? kk : my;
+            });
+        });
         const unsigned long long wm = warp_max_u64(my);
         if (lane == 0 && wm != 0ull)
             atomicMax(&s_best[it & 3], wm);
@@ -327,19 +344,29 @@ __global__ void __launch_bounds__(kB2, 3) tile_kernel(TileParams tp)
         // the winner and dZ = +-|dZ| from its key.  Only the position's owner
         // reads Z' from the position cache: the owner rewrites that cache later
         // in this update, and another thread's read would race it
-        const unsigned flat = ~(unsigned)bk;
+        const unsigned flat = ~(unsigned)bk, idx = flat >> 1;
         const float delta = (flat & 1u) ? -adz : adz;
-        const int k0 = (int)((flat >> 1) / (unsigned)npos), p0 = (int)((flat >> 1) % (unsigned)npos);
-        const int64_t i0 = i_lo + p0 / tw, j0 = j_lo + p0 % tw;
+        const int k0 = (int)(idx >> kshift);
+        const int ii0 = (int)((idx & ((1u << kshift) - 1u)) >> jbits);
+        const int jj0 = (int)(idx & ((1u << jbits) - 1u));
+        const int64_t i0 = i_lo + ii0, j0 = j_lo + jj0;
         const int64_t ib = i0 - (d.h - 1), jb = j0 - (d.w - 1);
-        // Eq. beta_up (r form) on the window: slot q holds the window
-        // position (i, j) with i == a (mod H2), j == b (mod W2)
-        for (int q = tid; q < A; q += kB2) {
-            const int a = q / W2, b = q % W2;
-            const int64_t i = first(ib, a, H2), j = first(jb, b, W2);
+        // Eq. beta_up (r form) on the window: slot (a, b) holds the window
+        // position ib + oi, jb + oj with oi = (a - ib) mod H2 = (a - i_lo +
+        // h - 1 - ii0) mod H2 and oj likewise (ii0 < th <= H2 for the
+        // automatic tiles: one wrap; larger tiles take a remainder)
+        for_slots([&](int a, int b) {
+            int oi = wrap(a - il + d.h - 1, H2) - ii0, oj = wrap(b - jl + d.w - 1, W2) - jj0;
+            if (th > H2)
+                oi %= H2;
+            if (tw > W2)
+                oj %= W2;
+            oi = oi < 0 ? oi + H2 : oi;
+            oj = oj < 0 ? oj + W2 : oj;
+            const int64_t i = ib + oi, j = jb + oj;
             if (i < 0 || i >= d.Hz || j < 0 || j >= Wz)
-                continue;
-            const int lag = (int)(i - ib) * W2 + (int)(j - jb);
+                return;
+            const int lag = oi * W2 + oj;
             const bool own = i >= i_lo && i < i_hi && j >= j_lo && j < j_hi;
             const int p = own ? (int)(i - i_lo) * tw + (int)(j - j_lo) : 0;
             if (own && i == i0 && j == j0) {
@@ -370,7 +397,7 @@ __global__ void __launch_bounds__(kB2, 3) tile_kernel(TileParams tp)
             }
             if (own)
                 eval(p, i, j);
-        }
+        });
         nupd++;
         imin = i0 < imin ? i0 : imin;
         imax = i0 > imax ? i0 : imax;
@@ -779,7 +806,15 @@ int csc2d_solve(const float *D, int K, int P, int h, int w, const float *X, int6
     for (int q = 0; q < Nb; q++)
         wmax = std::max(wmax, cs[q + 1] - cs[q]);
     const int64_t max_pos = hmax * wmax;
-    if (max_pos >= ((int64_t)1 << 31) / 64)
+    // a tile block's key index holds k (6 bits), the row and the column in
+    // the tile and the sign of dZ in 32 bits
+    auto bits = [](int64_t x) {
+        int b = 0;
+        while (b < 63 && ((int64_t)1 << b) <= x)
+            b++;
+        return b;
+    };
+    if (max_pos >= ((int64_t)1 << 31) / 64 || bits(hmax - 1) + bits(wmax - 1) > 25)
         return csc_record_error(CSC_EINVAL, "csc2d_solve: tiles too large");
     // a tile's r and Z are staged in shared memory when they fit
     const bool stage = TileLayout(K, (int)max_pos, true).total <= (size_t)kMaxSmem;
