@@ -45,7 +45,9 @@ typedef struct csc2d_stats {
     double max_delta_z;      /* max over all coordinates of |Z - Sh(beta, lambda)/n| after
                                 the last exact refresh */
     double solve_ms;         /* device time from the setup kernels to the last refresh */
-    int64_t kernel_launches; /* kernels this call launched */
+    int64_t kernel_launches; /* kernels this call launched (sweeps go in batches of four per
+                                read-back; those after the settling sweep launch blocks that
+                                return at once) */
 } csc2d_stats;
 
 /* Host only: the cut of one axis, Hz activation rows (or columns), atoms of

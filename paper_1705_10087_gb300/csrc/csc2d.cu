@@ -59,6 +59,7 @@ constexpr int kB2 = 256;        // threads of a tile block
 // (8 x 8 atoms) in step (measured on an earlier build: 6.2 ms at 8, 6.6 at
 // 16, 8.1 at 32, 23 ms when every visit runs to local convergence)
 constexpr int kAutoVisit2d = 8;
+constexpr int kSweepBatch = 4;  // tile sweeps launched per read-back of their update counts
 constexpr int kMaxK2 = 64;      // atoms (one bit each in a 64-bit mask)
 constexpr int kMaxWin = 4096;   // (2h-1)(2w-1) window positions
 constexpr int kTile2 = 32;      // columns per resync / objective tile
@@ -720,7 +721,9 @@ int auto_bands(int64_t Hz, int h)
     return (int)std::max<int64_t>(1, std::min<int64_t>(Hz / bh, 1 << 20));
 }
 
+// Device buffers of one csc2d_solve call, carved from one allocation.
 struct Dev2 {
+    void *base = nullptr;
     float *D = nullptr, *X = nullptr, *Ct = nullptr, *norms = nullptr, *beta0 = nullptr,
           *r = nullptr, *Z = nullptr;
     int64_t *band_s = nullptr, *col_s = nullptr;
@@ -730,13 +733,7 @@ struct Dev2 {
     double *dec = nullptr, *x2 = nullptr, *partial = nullptr, *E = nullptr;
     unsigned *amax = nullptr;
     unsigned long long *red = nullptr;
-    ~Dev2()
-    {
-        void *p[] = {D, X, Ct, norms, beta0, r, Z, band_s, col_s, list, dirty, upd, dec, x2,
-                     partial, E, amax, red};
-        for (void *q : p)
-            cudaFree(q);
-    }
+    ~Dev2() { cudaFree(base); }
 };
 
 }  // namespace
@@ -837,25 +834,45 @@ int csc2d_solve(const float *D, int K, int P, int h, int w, const float *X, int6
     const int KQ = (K + 3) / 4;
     const int64_t nz = (int64_t)K * d.Hz * d.Wz;
     const int A = (2 * h - 1) * (2 * w - 1);
-    C2_CUDA(cudaMalloc(&g.D, sizeof(float) * K * P * h * w));
-    C2_CUDA(cudaMalloc(&g.X, sizeof(float) * P * H * W));
-    C2_CUDA(cudaMalloc(&g.Ct, sizeof(float) * K * KQ * 4 * A));
-    C2_CUDA(cudaMalloc(&g.norms, sizeof(float) * K));
-    C2_CUDA(cudaMalloc(&g.beta0, sizeof(float) * nz));
-    C2_CUDA(cudaMalloc(&g.r, sizeof(float) * nz));
-    C2_CUDA(cudaMalloc(&g.Z, sizeof(float) * nz));
-    C2_CUDA(cudaMalloc(&g.band_s, sizeof(int64_t) * (Mb + 1)));
-    C2_CUDA(cudaMalloc(&g.col_s, sizeof(int64_t) * (Nb + 1)));
-    C2_CUDA(cudaMalloc(&g.list, sizeof(int) * ntiles));
-    C2_CUDA(cudaMalloc(&g.dirty, ntiles));
-    C2_CUDA(cudaMalloc(&g.upd, sizeof(long long)));
-    C2_CUDA(cudaMalloc(&g.dec, sizeof(double)));
-    C2_CUDA(cudaMalloc(&g.x2, sizeof(double)));
-    C2_CUDA(cudaMalloc(&g.amax, sizeof(unsigned)));
-    C2_CUDA(cudaMalloc(&g.red, sizeof(unsigned long long) * 8));
-    C2_CUDA(cudaMalloc(&g.E, sizeof(double)));
     const int64_t ntile_o = H * ((W + kTile2 - 1) / kTile2);
-    C2_CUDA(cudaMalloc(&g.partial, sizeof(double) * 2 * ntile_o));
+    {
+        // one allocation, pieces on 256-byte boundaries
+        size_t arena = 0;
+        auto piece = [&arena](size_t bytes) {
+            const size_t o = arena;
+            arena += (bytes + 255) & ~(size_t)255;
+            return o;
+        };
+        const size_t oD = piece(sizeof(float) * K * P * h * w), oX = piece(sizeof(float) * P * H * W),
+                     oCt = piece(sizeof(float) * K * KQ * 4 * A), onorms = piece(sizeof(float) * K),
+                     obeta0 = piece(sizeof(float) * nz), o_r = piece(sizeof(float) * nz),
+                     oZ = piece(sizeof(float) * nz), oband = piece(sizeof(int64_t) * (Mb + 1)),
+                     ocol = piece(sizeof(int64_t) * (Nb + 1)), olist = piece(sizeof(int) * ntiles),
+                     odirty = piece((size_t)ntiles), oupd = piece(sizeof(long long) * kSweepBatch),
+                     odec = piece(sizeof(double)), ox2 = piece(sizeof(double)),
+                     oamax = piece(sizeof(unsigned)), ored = piece(sizeof(unsigned long long) * 8),
+                     oE = piece(sizeof(double)), opart = piece(sizeof(double) * 2 * ntile_o);
+        C2_CUDA(cudaMalloc(&g.base, arena));
+        char *b = static_cast<char *>(g.base);
+        g.D = reinterpret_cast<float *>(b + oD);
+        g.X = reinterpret_cast<float *>(b + oX);
+        g.Ct = reinterpret_cast<float *>(b + oCt);
+        g.norms = reinterpret_cast<float *>(b + onorms);
+        g.beta0 = reinterpret_cast<float *>(b + obeta0);
+        g.r = reinterpret_cast<float *>(b + o_r);
+        g.Z = reinterpret_cast<float *>(b + oZ);
+        g.band_s = reinterpret_cast<int64_t *>(b + oband);
+        g.col_s = reinterpret_cast<int64_t *>(b + ocol);
+        g.list = reinterpret_cast<int *>(b + olist);
+        g.dirty = reinterpret_cast<unsigned char *>(b + odirty);
+        g.upd = reinterpret_cast<long long *>(b + oupd);
+        g.dec = reinterpret_cast<double *>(b + odec);
+        g.x2 = reinterpret_cast<double *>(b + ox2);
+        g.amax = reinterpret_cast<unsigned *>(b + oamax);
+        g.red = reinterpret_cast<unsigned long long *>(b + ored);
+        g.E = reinterpret_cast<double *>(b + oE);
+        g.partial = reinterpret_cast<double *>(b + opart);
+    }
     int64_t launches = 0;
     C2_CUDA(copy_in(g.D, D, sizeof(float) * K * P * h * w, s));
     C2_CUDA(copy_in(g.X, X, sizeof(float) * P * H * W, s));
@@ -925,28 +942,39 @@ int csc2d_solve(const float *D, int K, int P, int h, int w, const float *X, int6
     double dz32 = 0.0, all = 0.0;
     for (;;) {
         bool settled = false;
-        for (;;) {
-            C2_CUDA(cudaMemsetAsync(g.upd, 0, sizeof(long long), s));
-            for (int p = 0; p < c; p++) {
-                const int cnt = off[p + 1] - off[p];
-                if (cnt == 0)
-                    continue;
-                tp.list = g.list + off[p];
-                tile_fn<<<cnt, kB2, smem, s>>>(tp);
-                C2_CUDA(cudaGetLastError());
-                launches++;
+        for (bool more = true; more;) {
+            // kSweepBatch sweeps per read-back when neither limit can be reached
+            // inside the batch (a visit applies at most u updates); after a
+            // sweep without updates no tile is dirty and the rest do nothing
+            const int64_t per_sweep = (int64_t)ntiles * tp.u;
+            const int nb = updates + kSweepBatch * per_sweep < max_updates &&
+                                   sweeps + kSweepBatch < 1000000
+                               ? kSweepBatch
+                               : 1;
+            C2_CUDA(cudaMemsetAsync(g.upd, 0, sizeof(long long) * nb, s));
+            for (int b = 0; b < nb; b++) {
+                tp.upd = g.upd + b;
+                for (int p = 0; p < c; p++) {
+                    const int cnt = off[p + 1] - off[p];
+                    if (cnt == 0)
+                        continue;
+                    tp.list = g.list + off[p];
+                    tile_fn<<<cnt, kB2, smem, s>>>(tp);
+                    C2_CUDA(cudaGetLastError());
+                    launches++;
+                }
             }
-            long long u = 0;
-            C2_CUDA(cudaMemcpyAsync(&u, g.upd, sizeof u, cudaMemcpyDeviceToHost, s));
+            long long u[kSweepBatch] = {};
+            C2_CUDA(cudaMemcpyAsync(u, g.upd, sizeof(long long) * nb, cudaMemcpyDeviceToHost, s));
             C2_CUDA(cudaStreamSynchronize(s));
-            sweeps++;
-            updates += u;
-            if (u == 0) {
-                settled = true;
-                break;
+            for (int b = 0; b < nb && more; b++) {
+                sweeps++;
+                updates += u[b];
+                if (u[b] == 0)
+                    settled = true;
+                if (settled || updates >= max_updates || sweeps >= 1000000)
+                    more = false;
             }
-            if (updates >= max_updates || sweeps >= 1000000)
-                break;
         }
         // exact refresh of r from Z and the report
         C2_CUDA(cudaMemsetAsync(g.red, 0, sizeof(unsigned long long) * 8, s));
