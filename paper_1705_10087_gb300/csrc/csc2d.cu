@@ -451,7 +451,8 @@ __global__ void __launch_bounds__(kB2, 3) tile_kernel(TileParams tp)
 // Nonzeros of Z in rows [r0, r1) x columns [c0, c1) (at most kList2
 // elements: the callers cut their regions into column chunks that fit), in
 // (k, row, column) order, compacted into list; returns the count (the same
-// in every thread).  Block-wide barriers.
+// in every thread).  Block-wide barriers.  The exact checks use it where the
+// nonzero buckets below cannot serve a region.
 struct NZ2 {
     int k;
     int i, j;
@@ -493,6 +494,108 @@ __device__ int compact2(const float *__restrict__ Z, const Dims &d, int64_t r0, 
     return base;
 }
 
+// Nonzero buckets of Z per (row i, kTile2-column tile t), bucket b = i ntc + t:
+// count[b] = the tile's nonzeros over all atoms (may exceed kBucket2), ent[b
+// kBucket2 + e] the first kBucket2 of them in (k, column) order.  Built once
+// per exact refresh; the final objective reads those of the last refresh (Z
+// is the same).
+constexpr int kBucket2 = 16;
+constexpr int kGather2 = 256;  // buckets one block gathers at most
+struct Buckets2 {
+    const int *count;
+    const NZ2 *ent;
+    int64_t ntc;  // tiles per row, ceil(Wz / kTile2)
+};
+
+// One warp per bucket (blocks of whole warps: a warp exits as a whole).
+__global__ void __launch_bounds__(256)
+    bucket2d_kernel(const float *__restrict__ Z, Dims d, int64_t ntc, int *__restrict__ count,
+                    NZ2 *__restrict__ ent)
+{
+    const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= d.Hz * ntc)
+        return;
+    const int64_t i = b / ntc, j = (b % ntc) * kTile2 + lane;
+    int n = 0;
+    for (int k = 0; k < d.K; k++) {
+        const float z = j < d.Wz ? Z[((int64_t)k * d.Hz + i) * d.Wz + j] : 0.f;
+        const unsigned m = __ballot_sync(0xffffffffu, z != 0.f);
+        const int pos = n + __popc(m & ((1u << lane) - 1u));
+        if (z != 0.f && pos < kBucket2)
+            ent[b * kBucket2 + pos] = NZ2{k, (int)i, (int)j, z};
+        n += __popc(m);
+    }
+    if (lane == 0)
+        count[b] = n;
+}
+
+// Fills list with the nonzeros of the buckets of rows [r0, r1) and of the
+// tiles holding columns [c0, c1) (r0 < r1, c0 < c1), in (row, tile, k,
+// column) order: a superset of the region's nonzeros (callers skip what lies
+// outside their windows).  Returns their count, or -1 when a bucket
+// overflowed or the buckets are more than kGather2 or the nonzeros more than
+// kList2; the same in every thread.  s_cnt [kGather2], s_off [kGather2 + 1],
+// s_flag: shared scratch.  Block-wide barriers.
+__device__ int gather2(const Buckets2 &bk, int64_t r0, int64_t r1, int64_t c0, int64_t c1,
+                       NZ2 *list, int *s_cnt, int *s_off, int *s_flag)
+{
+    const int tid = threadIdx.x;
+    const int64_t t0 = c0 / kTile2;
+    const int nt = (int)((c1 - 1) / kTile2 + 1 - t0);
+    if ((r1 - r0) * nt > kGather2)
+        return -1;
+    const int nb = (int)((r1 - r0) * nt);
+    auto bucket = [&](int q) { return (r0 + q / nt) * bk.ntc + t0 + q % nt; };
+    for (int q = tid; q < nb; q += blockDim.x)
+        s_cnt[q] = bk.count[bucket(q)];
+    __syncthreads();
+    if (tid < 32) {
+        // lane l takes buckets [l per, (l + 1) per): a sum, a warp scan, offsets
+        const int per = (nb + 31) / 32, qa = min(nb, tid * per), qb = min(nb, qa + per);
+        int sum = 0;
+        bool over = false;
+        for (int q = qa; q < qb; q++) {
+            over |= s_cnt[q] > kBucket2;
+            sum += s_cnt[q];
+        }
+        int incl = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (tid >= o)
+                incl += v;
+        }
+        over = __any_sync(0xffffffffu, over);
+        int run = incl - sum;
+        for (int q = qa; q < qb; q++) {
+            s_off[q] = run;
+            run += s_cnt[q];
+        }
+        if (tid == 31) {
+            s_off[nb] = incl;
+            *s_flag = over || incl > kList2 ? 1 : 0;
+        }
+    }
+    __syncthreads();
+    if (*s_flag)
+        return -1;
+    const int total = s_off[nb];
+    for (int q = tid; q < total; q += blockDim.x) {
+        // the bucket of entry q: the last b with s_off[b] <= q
+        int lo = 0, hi = nb - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= q)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        list[q] = bk.ent[bucket(lo) * kBucket2 + (q - s_off[lo])];
+    }
+    __syncthreads();
+    return total;
+}
+
 // r = beta0 - sum C Z (FP64 sums) on one row and kTile2 columns per block
 // (threads: 32 columns x 8 atom groups), and the optimality report as in 1-D:
 // red[0] drift, red[3] max |Delta Z| (no floor), red[4] the coordinate step on
@@ -501,11 +604,12 @@ __global__ void __launch_bounds__(256)
     resync2d_kernel(const float *__restrict__ beta0, float *__restrict__ r,
                     const float *__restrict__ Z, const float *__restrict__ Ct,
                     const float *__restrict__ norms, Dims d, int KQ, float lam, int write_r,
-                    unsigned long long *__restrict__ red)
+                    Buckets2 bk, unsigned long long *__restrict__ red)
 {
     __shared__ NZ2 list[kList2];
     __shared__ int wc[8];
     __shared__ float bred[3][8];
+    __shared__ int s_cnt[kGather2], s_off[kGather2 + 1], s_flag;
     const int tid = threadIdx.x, col = tid & 31, grp = tid >> 5;
     const int64_t ntc = (d.Wz + kTile2 - 1) / kTile2;
     const int64_t i = blockIdx.x / ntc, j0 = (blockIdx.x % ntc) * kTile2, j = j0 + col;
@@ -519,30 +623,39 @@ __global__ void __launch_bounds__(256)
         acc_hi[q] = 0.f;
         acc_lo[q] = 0.f;
     }
-    // the region's columns in chunks whose K x rows x chunk elements fit the list
-    const int64_t chunk = max((int64_t)1, (int64_t)kList2 / ((int64_t)d.K * (r1 - r0)));
-    for (int64_t ca = c0; ca < c1; ca += chunk) {
-        const int64_t cb = ca + chunk < c1 ? ca + chunk : c1;
-        const int n = compact2(Z, d, r0, r1, ca, cb, list, wc);
-        if (j < d.Wz) {
-            for (int q = 0; q < n; q++) {
-                const NZ2 e = list[q];
-                const int a = (int)(i - e.i) + (d.h - 1), b = (int)(j - e.j) + (d.w - 1);
-                if (a < 0 || a >= H2 || b < 0 || b >= W2)
-                    continue;
-                const int lag = a * W2 + b;
+    // sum C z over the listed nonzeros whose window holds (i, j)
+    auto accumulate = [&](int n) {
+        if (j >= d.Wz)
+            return;
+        for (int q = 0; q < n; q++) {
+            const NZ2 e = list[q];
+            const int a = (int)(i - e.i) + (d.h - 1), b = (int)(j - e.j) + (d.w - 1);
+            if (a < 0 || a >= H2 || b < 0 || b >= W2)
+                continue;
+            const int lag = a * W2 + b;
 #pragma unroll
-                for (int t = 0; t < kPer; t++) {
-                    const int k = grp + 8 * t;
-                    if (k < d.K)
-                        df_add_prod(acc_hi[t], acc_lo[t],
-                                    __ldg(Ct + ((((int64_t)e.k * KQ + (k >> 2)) * A + lag) << 2) +
-                                          (k & 3)),
-                                    e.z);
-                }
+            for (int t = 0; t < kPer; t++) {
+                const int k = grp + 8 * t;
+                if (k < d.K)
+                    df_add_prod(acc_hi[t], acc_lo[t],
+                                __ldg(Ct + ((((int64_t)e.k * KQ + (k >> 2)) * A + lag) << 2) +
+                                      (k & 3)),
+                                e.z);
             }
         }
-        __syncthreads();  // the list is rewritten by the next chunk
+    };
+    // the region's nonzeros from the buckets, else compacted from Z in column
+    // chunks whose K x rows x chunk elements fit the list
+    const int nl = bk.count ? gather2(bk, r0, r1, c0, c1, list, s_cnt, s_off, &s_flag) : -1;
+    if (nl >= 0) {
+        accumulate(nl);
+    } else {
+        const int64_t chunk = max((int64_t)1, (int64_t)kList2 / ((int64_t)d.K * (r1 - r0)));
+        for (int64_t ca = c0; ca < c1; ca += chunk) {
+            const int64_t cb = ca + chunk < c1 ? ca + chunk : c1;
+            accumulate(compact2(Z, d, r0, r1, ca, cb, list, wc));
+            __syncthreads();  // the list is rewritten by the next chunk
+        }
     }
     float drift = 0.f, all = 0.f, dz32 = 0.f;
     if (j < d.Wz) {
@@ -603,11 +716,13 @@ __global__ void __launch_bounds__(256)
 // block's own activation positions (rows < Hz, columns < Wz).
 __global__ void __launch_bounds__(256)
     objective2d_kernel(const float *__restrict__ D, const float *__restrict__ X,
-                       const float *__restrict__ Z, Dims d, double *__restrict__ partial)
+                       const float *__restrict__ Z, Dims d, Buckets2 bk,
+                       double *__restrict__ partial)
 {
     __shared__ NZ2 list[kList2];
     __shared__ int wc[8];
     __shared__ double bsum[2][8];
+    __shared__ int s_cnt[kGather2], s_off[kGather2 + 1], s_flag;
     const int tid = threadIdx.x, col = tid & 31, grp = tid >> 5;
     const int64_t ntc = (d.W + kTile2 - 1) / kTile2;
     const int64_t y = blockIdx.x / ntc, x0 = (blockIdx.x % ntc) * kTile2, x = x0 + col;
@@ -623,27 +738,36 @@ __global__ void __launch_bounds__(256)
         acc_hi[t] = 0.f;
         acc_lo[t] = 0.f;
     }
-    if (r0 < r1 && c0 < c1) {
-        const int64_t chunk = max((int64_t)1, (int64_t)kList2 / ((int64_t)d.K * (r1 - r0)));
-        for (int64_t ca = c0; ca < c1; ca += chunk) {
-            const int64_t cb = ca + chunk < c1 ? ca + chunk : c1;
-            const int n = compact2(Z, d, r0, r1, ca, cb, list, wc);
-            if (x < d.W)
-                for (int q = 0; q < n; q++) {
-                    const NZ2 e = list[q];
-                    const int64_t u = y - e.i, v = x - e.j;
-                    if (u < 0 || u >= d.h || v < 0 || v >= d.w)
-                        continue;
+    // sum D z over the listed nonzeros whose atom covers (y, x)
+    auto accumulate = [&](int n) {
+        if (x >= d.W)
+            return;
+        for (int q = 0; q < n; q++) {
+            const NZ2 e = list[q];
+            const int64_t u = y - e.i, v = x - e.j;
+            if (u < 0 || u >= d.h || v < 0 || v >= d.w)
+                continue;
 #pragma unroll
-                    for (int t = 0; t < kPm; t++) {
-                        const int p = grp + 8 * t;
-                        if (p < d.P)
-                            df_add_prod(acc_hi[t], acc_lo[t],
-                                        __ldg(D + (((int64_t)e.k * d.P + p) * d.h + u) * d.w + v),
-                                        e.z);
-                    }
-                }
-            __syncthreads();
+            for (int t = 0; t < kPm; t++) {
+                const int p = grp + 8 * t;
+                if (p < d.P)
+                    df_add_prod(acc_hi[t], acc_lo[t],
+                                __ldg(D + (((int64_t)e.k * d.P + p) * d.h + u) * d.w + v), e.z);
+            }
+        }
+    };
+    if (r0 < r1 && c0 < c1) {
+        // from the buckets, else compacted from Z in column chunks
+        const int nl = bk.count ? gather2(bk, r0, r1, c0, c1, list, s_cnt, s_off, &s_flag) : -1;
+        if (nl >= 0) {
+            accumulate(nl);
+        } else {
+            const int64_t chunk = max((int64_t)1, (int64_t)kList2 / ((int64_t)d.K * (r1 - r0)));
+            for (int64_t ca = c0; ca < c1; ca += chunk) {
+                const int64_t cb = ca + chunk < c1 ? ca + chunk : c1;
+                accumulate(compact2(Z, d, r0, r1, ca, cb, list, wc));
+                __syncthreads();
+            }
         }
     }
     if (x < d.W)
@@ -733,6 +857,8 @@ struct Dev2 {
     double *dec = nullptr, *x2 = nullptr, *partial = nullptr, *E = nullptr;
     unsigned *amax = nullptr;
     unsigned long long *red = nullptr;
+    int *bcount = nullptr;  // nonzero buckets of Z (bucket2d_kernel)
+    NZ2 *bent = nullptr;
     ~Dev2() { cudaFree(base); }
 };
 
@@ -835,6 +961,7 @@ int csc2d_solve(const float *D, int K, int P, int h, int w, const float *X, int6
     const int64_t nz = (int64_t)K * d.Hz * d.Wz;
     const int A = (2 * h - 1) * (2 * w - 1);
     const int64_t ntile_o = H * ((W + kTile2 - 1) / kTile2);
+    const int64_t ntc = (d.Wz + kTile2 - 1) / kTile2, nbk = d.Hz * ntc;
     {
         // one allocation, pieces on 256-byte boundaries
         size_t arena = 0;
@@ -851,7 +978,8 @@ int csc2d_solve(const float *D, int K, int P, int h, int w, const float *X, int6
                      odirty = piece((size_t)ntiles), oupd = piece(sizeof(long long) * kSweepBatch),
                      odec = piece(sizeof(double)), ox2 = piece(sizeof(double)),
                      oamax = piece(sizeof(unsigned)), ored = piece(sizeof(unsigned long long) * 8),
-                     oE = piece(sizeof(double)), opart = piece(sizeof(double) * 2 * ntile_o);
+                     oE = piece(sizeof(double)), opart = piece(sizeof(double) * 2 * ntile_o),
+                     obc = piece(sizeof(int) * nbk), obe = piece(sizeof(NZ2) * kBucket2 * nbk);
         C2_CUDA(cudaMalloc(&g.base, arena));
         char *b = static_cast<char *>(g.base);
         g.D = reinterpret_cast<float *>(b + oD);
@@ -872,6 +1000,8 @@ int csc2d_solve(const float *D, int K, int P, int h, int w, const float *X, int6
         g.red = reinterpret_cast<unsigned long long *>(b + ored);
         g.E = reinterpret_cast<double *>(b + oE);
         g.partial = reinterpret_cast<double *>(b + opart);
+        g.bcount = reinterpret_cast<int *>(b + obc);
+        g.bent = reinterpret_cast<NZ2 *>(b + obe);
     }
     int64_t launches = 0;
     C2_CUDA(copy_in(g.D, D, sizeof(float) * K * P * h * w, s));
@@ -937,8 +1067,8 @@ int csc2d_solve(const float *D, int K, int P, int h, int w, const float *X, int6
     int64_t updates = 0, sweeps = 0;
     int resyncs = 0;
     bool converged = false;
-    const int64_t ntc = (d.Wz + kTile2 - 1) / kTile2;
     const unsigned rgrid = (unsigned)(d.Hz * ntc);
+    const Buckets2 bk2{g.bcount, g.bent, ntc};
     double dz32 = 0.0, all = 0.0;
     for (;;) {
         bool settled = false;
@@ -978,10 +1108,13 @@ int csc2d_solve(const float *D, int K, int P, int h, int w, const float *X, int6
         }
         // exact refresh of r from Z and the report
         C2_CUDA(cudaMemsetAsync(g.red, 0, sizeof(unsigned long long) * 8, s));
-        resync2d_kernel<<<rgrid, 256, 0, s>>>(g.beta0, g.r, g.Z, g.Ct, g.norms, d, KQ,
-                                              (float)lambda, 1, g.red);
+        bucket2d_kernel<<<(unsigned)((nbk * 32 + 255) / 256), 256, 0, s>>>(g.Z, d, ntc, g.bcount,
+                                                                         g.bent);
         C2_CUDA(cudaGetLastError());
-        launches++;
+        resync2d_kernel<<<rgrid, 256, 0, s>>>(g.beta0, g.r, g.Z, g.Ct, g.norms, d, KQ,
+                                              (float)lambda, 1, bk2, g.red);
+        C2_CUDA(cudaGetLastError());
+        launches += 2;
         unsigned long long red[8];
         C2_CUDA(cudaMemcpyAsync(red, g.red, sizeof red, cudaMemcpyDeviceToHost, s));
         C2_CUDA(cudaStreamSynchronize(s));
@@ -1000,7 +1133,7 @@ int csc2d_solve(const float *D, int K, int P, int h, int w, const float *X, int6
     }
     C2_CUDA(cudaEventRecord(e1, s));
     const unsigned ogrid = (unsigned)ntile_o;
-    objective2d_kernel<<<ogrid, 256, 0, s>>>(g.D, g.X, g.Z, d, g.partial);
+    objective2d_kernel<<<ogrid, 256, 0, s>>>(g.D, g.X, g.Z, d, bk2, g.partial);  // Z as refreshed
     C2_CUDA(cudaGetLastError());
     sum_partials_kernel<<<1, 256, 0, s>>>(g.partial, ntile_o, lambda, g.E);
     C2_CUDA(cudaGetLastError());
