@@ -106,3 +106,42 @@ def test_rejects_bad_arguments(capi):
         capi.csc2d_solve(D, X, 0.1, 1e-6, N=9)  # more column blocks than columns
     with pytest.raises(capi.CscError):
         capi.csc2d_solve(D, X, 0.1, 1e-6, N=-1)
+
+
+def test_dense_refresh_mixes_buckets_and_compaction(capi):
+    """A dense optimum (lambda = 0.05 lambda_max): some (row, 32-column tile)
+    buckets of Z hold more than their 16 entries, so the exact refresh and the
+    objective compact Z per block around those and read the buckets elsewhere.
+    Both are checked on the returned Z itself: the reported max |Z - Sh(beta,
+    lambda)/n| against the FP64 oracle's beta at that Z (Sec. 2.1), and E
+    against the oracle's objective."""
+    pb = synth.make_problem2d(K=4, P=1, h=3, w=3, H=30, W=70, rho=0.06, sigma=0.05, seed=11)
+    K, P, h, w = pb.D.shape
+    Hz, Wz = pb.X.shape[1] - h + 1, pb.X.shape[2] - w + 1
+    lam = 0.05 * csc2d.lambda_max(pb.D, pb.X)
+    Z = torch.zeros((K, Hz, Wz), dtype=torch.float32, device="cuda")
+    status, E, st = capi.csc2d_solve(torch.from_numpy(pb.D).cuda(),
+                                     torch.from_numpy(pb.X).cuda(), lam, 1e-6, Z_out=Z)
+    assert status in (capi.CSC_OK, capi.CSC_NOT_CONVERGED), st
+    Zg = Z.cpu().numpy()
+    # both kinds of neighbourhood occur: the refresh block of row i and
+    # columns [j0, j0 + 32) reads the buckets of rows i +- (h-1) and of the
+    # tiles holding columns [j0 - (w-1), j0 + 32 + w - 1)
+    ntc = (Wz + 31) // 32
+    cnt = np.array([[np.count_nonzero(Zg[:, i, 32 * t:32 * t + 32]) for t in range(ntc)]
+                    for i in range(Hz)])
+    over = cnt > 16
+    kinds = set()
+    for i in range(Hz):
+        for t in range(ntc):
+            r0, r1 = max(0, i - (h - 1)), min(Hz, i + h)
+            c0, c1 = max(0, 32 * t - (w - 1)), min(Wz, 32 * t + 32 + w - 1)
+            kinds.add(bool(over[r0:r1, c0 // 32:(c1 - 1) // 32 + 1].any()))
+    assert kinds == {True, False}, cnt
+    beta = csc2d.beta_fresh(pb.D, pb.X, Zg)
+    n = csc2d.norms(pb.D)[:, None, None]
+    gap = np.abs(Zg - np.sign(beta) * np.maximum(np.abs(beta) - lam, 0.0) / n).max()
+    # the refresh rounds r once to float32 and evaluates the step in float32
+    assert abs(st["max_delta_z"] - gap) <= 1e-6 * float((np.abs(beta) / n).max()) + 1e-7, (
+        st["max_delta_z"], gap)
+    assert E == pytest.approx(csc2d.objective(pb.D, pb.X, Zg, lam), rel=1e-10)
